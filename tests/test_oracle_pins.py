@@ -1,0 +1,337 @@
+"""Pins for the FP64 oracle, against facts fixed by the paper and by
+mathematics rather than by the oracle itself: hand-derived closed forms
+(tests/golden/closed_forms.json), exact integer factorizations, brute force on
+tiny inputs, invariants, and library routines for special cases.
+
+Paper passages: Algorithm 1 (left: CG; right: blocked right-looking
+Cholesky), Sec. 2.1 (residual replacement), Sec. 2.2 (L L^T = A, forward and
+back substitution)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import sympy
+
+import oracle
+from paper_2605_13209_b300 import inputs
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+U = np.finfo(np.float64).eps / 2
+
+
+def ev(s):
+    return float(sympy.N(sympy.sympify(s), 30))
+
+
+def evm(rows):
+    return np.array([[ev(x) for x in r] for r in rows])
+
+
+def int_lower(n, rng, unit=False, lo=-3, hi=4):
+    """Random lower-triangular integer matrix with positive diagonal."""
+    L = np.tril(rng.integers(lo, hi, (n, n))).astype(np.float64)
+    d = np.ones(n) if unit else rng.integers(1, 5, n).astype(np.float64)
+    np.fill_diagonal(L, d)
+    return L
+
+
+# ---------------------------------------------------------------- Cholesky
+def test_chol_closed_form_i_plus_vvt():
+    g = GOLD["chol_i_plus_vvt"]
+    v = np.array([ev(x) for x in g["v"]])
+    A = np.eye(3) + np.outer(v, v)
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    np.testing.assert_allclose(L, evm(g["L"]), rtol=4 * U, atol=4 * U)
+    Lb, info = oracle.blocked_cholesky(A, 2)
+    np.testing.assert_allclose(Lb, evm(g["L"]), rtol=4 * U, atol=4 * U)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 40])
+def test_chol_exact_integer_factor(n):
+    """A = L0 L0^T with small integers: every intermediate is an integer, so
+    the factor must come back bit-exact (catches any index/transpose slip)."""
+    rng = np.random.default_rng(n)
+    L0 = int_lower(n, rng)
+    A = L0 @ L0.T
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    assert np.array_equal(L, L0)
+    for b in (1, 3, 8):
+        Lb, info = oracle.blocked_cholesky(A, b)
+        assert info == 0 and np.array_equal(Lb, L0), b
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_chol_brute_force_small(n):
+    rng = np.random.default_rng(100 + n)
+    X = rng.random((n, 8))
+    A = oracle.se_matrix(X, 1.0, 0.5, 1e-2)
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    assert np.all(np.triu(L, 1) == 0) and np.all(np.diag(L) > 0)
+    # entrywise brute force: (L L^T)_ij = sum_k L_ik L_jk
+    for i in range(n):
+        for j in range(n):
+            s = sum(L[i, k] * L[j, k] for k in range(n))
+            assert abs(s - A[i, j]) <= 8 * U * np.abs(A).max() * n
+    Lb, info = oracle.blocked_cholesky(A, 3)
+    assert info == 0 and np.max(np.abs(Lb - L)) <= 16 * U * n
+
+
+def test_chol_diagonal():
+    a = np.array([4.0, 9.0, 2.0, 0.25])
+    L, info = oracle.cholesky(np.diag(a))
+    assert info == 0
+    np.testing.assert_array_equal(L, np.diag(np.sqrt(a)))
+
+
+def test_chol_not_spd_info():
+    A = np.array([[1.0, 2.0], [2.0, 1.0]])  # eigenvalues 3, -1: column 2 fails
+    _, info = oracle.cholesky(A)
+    assert info == 2
+    A3 = np.diag([1.0, 1.0, -1.0])
+    assert oracle.cholesky(A3)[1] == 3
+    assert oracle.blocked_cholesky(A3, 2)[1] == 3
+    An = np.diag([1.0, np.nan])
+    assert oracle.cholesky(An)[1] == 2
+
+
+def test_chol_matches_lapack_se():
+    """Special case that reduces to a library routine: numpy's LAPACK potrf."""
+    sysm = inputs.gp_system(300, 8, 0.5, 1e-2, seed=7)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    assert oracle.factor_error(L, np.linalg.cholesky(A)) < 1e-12
+    Lb, _ = oracle.blocked_cholesky(A, 64)
+    assert oracle.factor_error(Lb, L) < 1e-12
+
+
+def test_chol_upper_untouched():
+    rng = np.random.default_rng(3)
+    L0 = int_lower(6, rng)
+    A = L0 @ L0.T
+    A[np.triu_indices(6, 1)] = 777.0  # upper triangle is not referenced
+    M = np.asfortranarray(A.copy())
+    info = oracle.lib().or_cholesky(6, oracle._p(M), 6)
+    assert info == 0
+    assert np.all(M[np.triu_indices(6, 1)] == 777.0)
+    assert np.array_equal(np.tril(M), L0)
+
+
+# ------------------------------------------------------ low-precision factor
+def test_round_bf16_matches_torch():
+    import torch
+    rng = np.random.default_rng(5)
+    vals = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-6, 6, 2000),
+                           [0.0, -0.0, 1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -7 + 2 ** -8,
+                            65504.0, 1e-30, -3.0e38]])
+    f32 = vals.astype(np.float32)
+    ref = torch.from_numpy(f32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([oracle.round_bf16(float(v)) for v in f32])
+    np.testing.assert_array_equal(got, ref)
+    assert oracle.round_bf16(1.0 + 2 ** -8) == 1.0          # tie -> even
+    assert oracle.round_bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6   # tie -> even (up)
+
+
+def test_mixed_factor_exact_on_representable_input():
+    """Unit-diagonal integer factor: every operand is exact in bfloat16 and
+    every product sum is exact, so every mode must return L0 exactly."""
+    rng = np.random.default_rng(11)
+    L0 = int_lower(24, rng, unit=True, lo=-2, hi=3)
+    A = L0 @ L0.T
+    for mode in ("fp32", "bf16", "split_bf16"):
+        Lt, info = oracle.mixed_factor(A, 8, mode)
+        assert info == 0 and np.array_equal(Lt, L0), mode
+
+
+def test_mixed_factor_error_ordering():
+    sysm = inputs.gp_system(192, 8, 0.5, 1e-1, seed=9)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    L, _ = oracle.cholesky(A)
+    errs = {}
+    for mode in ("fp32", "split_bf16", "bf16"):
+        Lt, info = oracle.mixed_factor(A, 64, mode)
+        assert info == 0
+        errs[mode] = oracle.factor_error(Lt, L)
+    assert errs["fp32"] < 1e-5
+    assert errs["fp32"] < errs["split_bf16"] < errs["bf16"] < 0.5
+    assert errs["bf16"] > 1e-4   # bfloat16 products really are rounded
+
+
+def test_mixed_factor_shift():
+    """A + delta I is what the shifted factor factors."""
+    rng = np.random.default_rng(12)
+    L0 = int_lower(10, rng, unit=True, lo=-1, hi=2)
+    A = L0 @ L0.T
+    Lt, info = oracle.mixed_factor(A - 0.5 * np.eye(10), 4, "fp32", shift=0.5)
+    assert info == 0 and np.array_equal(Lt, L0)
+
+
+# ----------------------------------------------------------- substitution
+@pytest.mark.parametrize("n", [1, 7, 33])
+def test_substitution_exact_integer(n):
+    rng = np.random.default_rng(20 + n)
+    L0 = int_lower(n, rng, unit=True)
+    x = rng.integers(-5, 6, (n, 3)).astype(np.float64)
+    np.testing.assert_array_equal(oracle.forward_sub(L0, L0 @ x), x)
+    np.testing.assert_array_equal(oracle.back_sub(L0, L0.T @ x), x)
+
+
+def test_solve_sherman_morrison():
+    g = GOLD["chol_i_plus_vvt"]
+    v = np.array([ev(x) for x in g["v"]])
+    A = np.eye(3) + np.outer(v, v)
+    b = np.array([ev(x) for x in g["b"]])
+    L, _ = oracle.cholesky(A)
+    x = oracle.chol_solve(L, b)
+    np.testing.assert_allclose(x, [ev(s) for s in g["x_sherman_morrison"]], rtol=1e-14, atol=1e-15)
+
+
+def test_solve_diagonal():
+    a = np.array([4.0, 16.0, 0.25])   # perfect squares: sqrt and both divisions exact
+    b = np.array([1.0, 1.0, 1.0])
+    L, _ = oracle.cholesky(np.diag(a))
+    np.testing.assert_array_equal(oracle.chol_solve(L, b), b / a)
+
+
+def test_solve_matches_library():
+    sysm = inputs.gp_system(200, 8, 0.5, 1e-2, nrhs=2, seed=8)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    L, _ = oracle.cholesky(A)
+    X = oracle.chol_solve(L, sysm.B)
+    ref = np.linalg.solve(A, sysm.B)
+    assert oracle.forward_error(X, ref) < 1e-9
+    for r in range(2):
+        assert oracle.backward_error(A, X[:, r], sysm.B[:, r]) < 1e-15
+
+
+# ---------------------------------------------------------------- SE matrix
+def test_se_two_points_closed_form():
+    g = GOLD["se_two_points"]
+    X = np.array([[ev(x) for x in g["x0"]], [ev(x) for x in g["x1"]]])
+    K = oracle.se_matrix(X, ev(g["sf2"]), ev(g["ell"]), ev(g["sn2"]))
+    np.testing.assert_allclose(K, evm(g["K"]), rtol=4 * U)
+
+
+def test_se_structure():
+    X = inputs.points(64, 8, 3)
+    K = oracle.se_matrix(X, 1.5, 0.4, 1e-3)
+    assert np.array_equal(K, K.T)
+    assert np.all(np.diag(K) == 1.5 + 1e-3)
+    assert np.all(K[~np.eye(64, dtype=bool)] < 1.5)
+    # far-apart points: K -> (sf2 + sn2) I
+    Xf = np.arange(5)[:, None] * np.ones((1, 8)) * 100.0
+    Kf = oracle.se_matrix(Xf, 2.0, 0.5, 0.1)
+    np.testing.assert_array_equal(Kf, 2.1 * np.eye(5))
+    # entry function agrees with the matrix
+    for i, j in [(0, 0), (3, 7), (63, 1)]:
+        assert oracle.se_entry(X[i], X[j], i == j, 1.5, 0.4, 1e-3) == K[i, j]
+
+
+# ---------------------------------------------------------------------- CG
+def test_cg_first_step_by_hand():
+    g = GOLD["cg_first_step"]
+    A = evm(g["A"])
+    b = np.array([ev(x) for x in g["b"]])
+    x1, it, _ = oracle.cg(A, b, 1e-14, 1, R=0)
+    assert it == 1
+    np.testing.assert_allclose(x1, [ev(s) for s in g["x1"]], rtol=4 * U)
+    x, it, rr = oracle.cg(A, b, 1e-12, 50, R=0)
+    assert it == g["iterations"]
+    np.testing.assert_allclose(x, [ev(s) for s in g["x"]], rtol=1e-14)
+
+
+def test_cg_diag_three_eigenvalues():
+    g = GOLD["cg_diag_123"]
+    A = np.diag([ev(x) for x in g["diag"]])
+    x, it, rr = oracle.cg(A, np.array([ev(s) for s in g["b"]]), 1e-12, 100, R=0)
+    assert it == g["iterations"]
+    np.testing.assert_allclose(x, [ev(s) for s in g["x"]], rtol=1e-14)
+
+
+def test_cg_scaled_identity_one_step():
+    b = inputs.rhs(50, 1, 1)[:, 0]
+    x, it, rr = oracle.cg(3.0 * np.eye(50), b, 1e-12, 100)
+    assert it == 1
+    np.testing.assert_allclose(x, b / 3.0, rtol=4 * U)
+
+
+@pytest.mark.parametrize("k", [2, 5, 9])
+def test_cg_k_distinct_eigenvalues(k):
+    """A = Q diag(lambda) Q^T, Q a Householder reflector (closed form), with
+    k distinct eigenvalues: CG ends within k iterations (exact arithmetic),
+    here within k + 1 at eps = 1e-10."""
+    n = 60
+    rng = np.random.default_rng(k)
+    w = rng.standard_normal(n)
+    Q = np.eye(n) - 2.0 * np.outer(w, w) / (w @ w)
+    lam = np.repeat(np.linspace(1.0, 4.0, k), int(np.ceil(n / k)))[:n]
+    A = Q @ np.diag(lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    b = rng.standard_normal(n)
+    x, it, rr = oracle.cg(A, b, 1e-10, 1000, R=0)
+    assert it <= k + 1 and rr <= 1e-10
+    np.testing.assert_allclose(x, Q @ ((Q.T @ b) / lam), rtol=1e-8, atol=1e-10)
+
+
+def test_cg_residual_replacement():
+    sysm = inputs.gp_system(120, 8, 0.5, 1e-1, seed=4)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    b = sysm.B[:, 0]
+    ref = np.linalg.solve(A, b)
+    for R in (0, 1, 7, 50):
+        x, it, rr = oracle.cg(A, b, 1e-10, 5000, R=R)
+        assert rr <= 1e-10, R
+        true_rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert true_rel <= 1e-9, R
+        assert oracle.forward_error(x, ref) < 1e-6
+    # with R = 1 the recurrence residual *is* the true residual each step
+    x, it, rr = oracle.cg(A, b, 1e-10, 5000, R=1)
+    assert abs(np.linalg.norm(b - A @ x) / np.linalg.norm(b) - rr) <= 1e-14
+
+
+def test_cg_maxit_and_start_vector():
+    sysm = inputs.gp_system(80, 8, 0.5, 1e-2, seed=5)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    b = sysm.B[:, 0]
+    x, it, rr = oracle.cg(A, b, 1e-14, 3)
+    assert it == 3 and rr > 1e-14
+    # start vector with an exactly zero residual: u0 = 0, the loop never runs
+    x, it, rr = oracle.cg(2.0 * np.eye(4), 2.0 * np.ones(4), 1e-10, 10, x0=np.ones(4))
+    assert it == 0 and np.array_equal(x, np.ones(4))
+
+
+# ----------------------------------------------------------- metrics / PCG
+def test_backward_error_closed_form():
+    A = np.eye(4)
+    b = np.ones(4)
+    assert oracle.backward_error(A, b, b) == 0.0
+    d = 1e-3
+    x = b.copy()
+    x[0] += d
+    assert abs(oracle.backward_error(A, x, b) - d / (2 + d)) < 1e-16
+
+
+def test_pcg_exact_preconditioner_one_step():
+    sysm = inputs.gp_system(100, 8, 0.5, 1e-2, seed=6)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    L, _ = oracle.cholesky(A)
+    x, it, be = oracle.pcg(A, L, sysm.B[:, 0], 1e-12)
+    assert it == 1 and be <= 1e-12
+
+
+def test_pcg_low_precision_preconditioner():
+    sysm = inputs.gp_system(256, 8, 0.5, 1e-3, seed=10)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    b = sysm.B[:, 0]
+    Lt, info = oracle.mixed_factor(A, 64, "split_bf16")
+    assert info == 0
+    x, it, be = oracle.pcg(A, Lt, b, 1e-12)
+    assert 1 <= it <= 30 and be <= 1e-12
+    _, it_cg, _ = oracle.cg(A, b, 1e-10, 10000)
+    assert it < it_cg
+    ref = np.linalg.solve(A, b)
+    assert oracle.forward_error(x, ref) < 1e-6
