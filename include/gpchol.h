@@ -1,0 +1,164 @@
+/*
+ * gpchol.h -- C ABI of the B300 (sm_103a) dense SPD solver library for
+ * Gaussian-process kernel systems A x = b.
+ *
+ * The operations are those of Thuering, Strack, Pflueger, "Comparing the
+ * Performance of Heterogeneous Conjugate Gradient and Cholesky Solvers on
+ * Various Hardware Using SYCL" (IWOCL '26):
+ *   - the blocked right-looking Cholesky factorization of Algorithm 1 (right),
+ *     steps 1-3 (Sec. 2.2, Sec. 3.2);
+ *   - forward and back substitution with the factor (Sec. 2.2);
+ *   - classic conjugate gradients, Algorithm 1 (left), with the residual
+ *     recomputed from scratch every few iterations (Sec. 2.1, Sec. 3.1);
+ * plus the entry points that build on them (the squared-exponential kernel
+ * matrix the solvers are applied to, a mixed-precision refined solve, a
+ * batched solve and a serving loop), each documented where it is declared.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with a leading dimension ld >= max(1, n);
+ *     element (i, j) of A is A[i + j*lda].  Only the lower triangle of a
+ *     symmetric matrix or of a factor is read or written unless stated.
+ *   - Matrix and vector pointers are DEVICE pointers owned by the caller,
+ *     unless a parameter says "host".  The library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; results in device memory are valid
+ *     once the stream reaches the point after the call.  Calls that return
+ *     host-side results (info, statistics) synchronize the stream first and
+ *     say so.
+ *   - Every call returns a gpch_status; no C++ exception crosses the ABI.
+ *     On failure gpch_last_error(ctx) holds a one-line message.  There is no
+ *     host fallback: without a usable GPU every compute call fails with
+ *     GPCH_CUDA_ERROR.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GPCHOL_H
+#define GPCHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GPCH_VERSION 1
+
+typedef enum gpch_status {
+    GPCH_OK = 0,
+    GPCH_INVALID_ARG = 1,    /* a size, pointer or option is out of range        */
+    GPCH_NOT_SPD = 2,        /* a pivot was not positive; *info = 1-based column */
+    GPCH_NOT_CONVERGED = 3,  /* iteration cap reached before the tolerance       */
+    GPCH_OOM_BUDGET = 4,     /* workspace would exceed the context's HBM budget  */
+    GPCH_TIMEOUT = 5,        /* a bounded device-side wait gave up               */
+    GPCH_CUDA_ERROR = 6      /* a CUDA runtime call failed                       */
+} gpch_status;
+
+/* Storage type of a matrix operand. */
+typedef enum gpch_dtype {
+    GPCH_F64 = 0,
+    GPCH_F32 = 1
+} gpch_dtype;
+
+/* Arithmetic of the factorization's trailing update (Algorithm 1, step 3). */
+typedef enum gpch_prec {
+    GPCH_PREC_FP64 = 0,        /* everything in FP64                              */
+    GPCH_PREC_BF16 = 1,        /* bf16 tensor-core products, FP32 accumulation     */
+    GPCH_PREC_SPLIT_BF16 = 2   /* head+tail bf16 split, three products, FP32 acc.  */
+} gpch_prec;
+
+typedef struct gpch_ctx gpch_ctx;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * workspace the context may allocate (0 = no cap beyond free memory).
+ * The caller's own matrices do not count against the budget. */
+gpch_status gpch_create(gpch_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Free the context's workspace (synchronizes the device). NULL is a no-op. */
+gpch_status gpch_destroy(gpch_ctx *ctx);
+
+/* Static strings; never NULL. */
+const char *gpch_status_string(gpch_status s);
+const char *gpch_last_error(const gpch_ctx *ctx);
+int gpch_version(void);
+
+/* Bytes of workspace currently held by the context. */
+size_t gpch_workspace_bytes(const gpch_ctx *ctx);
+
+/* ------------------------------------------------ A1: GP kernel matrix */
+
+/* Squared-exponential GP covariance of n points X (device, n x d,
+ * row-major: point i at X + i*d):
+ *     A_ij = sf2 * exp(-sum_k (X_ik - X_jk)^2 / (2 ell^2)) + sn2 * [i == j]
+ * written to the full n x n matrix A (both triangles), FP64.  The squared
+ * distance is summed term by term, so A is exactly symmetric and its
+ * diagonal is exactly sf2 + sn2.  The paper's systems are GP covariance
+ * matrices (Sec. 4.1); this is the synthetic kernel the solvers are run on.
+ * Errors: INVALID_ARG if n < 0, d < 1, d > 64, lda < n, ell <= 0. */
+gpch_status gpch_se_matrix(gpch_ctx *ctx, int64_t n, int d, const double *X,
+                           double sf2, double ell, double sn2,
+                           double *A, int64_t lda, void *stream);
+
+/* --------------------------------------- A2-A4: blocked Cholesky, FP64 */
+
+/* In-place blocked right-looking Cholesky, Algorithm 1 (right): for each
+ * block column j of width `tile`:
+ *   step 1  A_jj = chol(A_jj)                 (diagonal tile, FP64)
+ *   step 2  A_ij = A_ij A_jj^{-T}, i > j      (panel triangular solve)
+ *   step 3  A_ik -= A_ij A_kj^T, j < k <= i   (SYRK on k == i, GEMM below)
+ * A: device, n x n, lda >= n; on return its lower triangle holds L with
+ * L L^T = A (Sec. 2.2).  The strict upper triangle is not touched.
+ * tile: 64..1024, multiple of 64 (the paper's block size, Sec. 4.3).
+ * info (host): 0 on success, else the 1-based column whose pivot was not
+ * positive (LAPACK convention); the call then returns GPCH_NOT_SPD and the
+ * lower triangle holds a partial factor.  Synchronizes `stream`.
+ * Errors: INVALID_ARG (n < 0, lda < n, bad tile, info NULL). */
+gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, double *A,
+                             int64_t lda, void *stream, int64_t *info);
+
+/* ------------------------------------------- A5: substitution with L */
+
+/* Solve L L^T X = B in place: forward substitution L Y = B, then back
+ * substitution L^T X = Y (Sec. 2.2).  L: device, lower triangle of an
+ * n x n factor (as left by gpch_chol_factor), ldl >= n.  B: device,
+ * n x nrhs, ldb >= n, overwritten with X.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (n < 0, nrhs < 0, ldl < n, ldb < n). */
+gpch_status gpch_chol_solve(gpch_ctx *ctx, int64_t n, const double *L,
+                            int64_t ldl, double *B, int64_t ldb, int nrhs,
+                            void *stream);
+
+/* --------------------------------------------------- A6-A7: CG solve */
+
+typedef struct gpch_cg_stats {
+    int32_t iterations;   /* max over right-hand sides                       */
+    int32_t converged;    /* number of right-hand sides that met rtol         */
+    double relres_max;    /* max over RHS of sqrt(u/u0) at exit (recurrence)  */
+} gpch_cg_stats;
+
+/* Conjugate gradients, Algorithm 1 (left), per right-hand side:
+ *   s = r = b - A x;  u = u0 = r^T r
+ *   while u > rtol^2 u0:  t = A s;  alpha = u / s^T t;  x += alpha s;
+ *       r -= alpha t  (or r = b - A x on every replace_every-th iteration,
+ *       Sec. 2.1);  beta = r^T r / u;  u = r^T r;  s = r + beta s
+ * A: device, full symmetric n x n (both triangles stored), lda >= n, of
+ * storage type dtype (F32 values are widened exactly to FP64; all vectors,
+ * dot products and recurrences are FP64).  B: device n x nrhs (ldb); X:
+ * device n x nrhs (ldx), read as the start vector and overwritten with the
+ * solution.  The nrhs columns run independent recurrences that share one
+ * pass over A per iteration; a converged column is frozen.
+ * maxit: iteration cap (> 0).  replace_every: R > 0 replaces the residual
+ * on iterations R, 2R, ...; 0 never.  stats (host, may be NULL) is filled
+ * after the call synchronizes `stream`.
+ * Returns GPCH_NOT_CONVERGED if some column missed rtol within maxit. */
+gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A,
+                          gpch_dtype dtype, int64_t lda, const double *B,
+                          int64_t ldb, double *X, int64_t ldx, int nrhs,
+                          double rtol, int maxit, int replace_every,
+                          void *stream, gpch_cg_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPCHOL_H */

@@ -1,0 +1,105 @@
+// api.cu -- context lifetime, workspace arena, status strings.
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace gpch {
+
+gpch_status fail(gpch_ctx *ctx, gpch_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+gpch_status ws_reserve(gpch_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_bytes) return GPCH_OK;
+    if (ctx->budget && bytes > ctx->budget)
+        return fail(ctx, GPCH_OOM_BUDGET, "workspace of %zu bytes exceeds the budget of %zu bytes",
+                    bytes, ctx->budget);
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (ctx->ws) {
+        // Work queued on any stream may still use the old arena.
+        GPCH_CUDA(ctx, cudaDeviceSynchronize());
+        GPCH_CUDA(ctx, cudaFree(ctx->ws));
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t sz = bytes + (bytes >> 3);   // grow with some slack
+    if (ctx->budget && sz > ctx->budget) sz = ctx->budget;
+    cudaError_t e = cudaMalloc(&ctx->ws, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return fail(ctx, GPCH_OOM_BUDGET, "cudaMalloc(%zu) failed: %s", sz, cudaGetErrorString(e));
+    }
+    ctx->ws_bytes = sz;
+    return GPCH_OK;
+}
+
+}  // namespace gpch
+
+extern "C" {
+
+gpch_status gpch_create(gpch_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return GPCH_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return GPCH_CUDA_ERROR;
+    }
+    if (device < 0 || device >= count) return GPCH_INVALID_ARG;
+    gpch_ctx *ctx = new gpch_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaMallocHost(&ctx->pinned, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GPCH_CUDA_ERROR;
+    }
+    ctx->pinned_bytes = 4096;
+    *out = ctx;
+    return GPCH_OK;
+}
+
+gpch_status gpch_destroy(gpch_ctx *ctx)
+{
+    if (!ctx) return GPCH_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+    return GPCH_OK;
+}
+
+const char *gpch_status_string(gpch_status s)
+{
+    switch (s) {
+    case GPCH_OK: return "GPCH_OK";
+    case GPCH_INVALID_ARG: return "GPCH_INVALID_ARG";
+    case GPCH_NOT_SPD: return "GPCH_NOT_SPD";
+    case GPCH_NOT_CONVERGED: return "GPCH_NOT_CONVERGED";
+    case GPCH_OOM_BUDGET: return "GPCH_OOM_BUDGET";
+    case GPCH_TIMEOUT: return "GPCH_TIMEOUT";
+    case GPCH_CUDA_ERROR: return "GPCH_CUDA_ERROR";
+    }
+    return "GPCH_UNKNOWN";
+}
+
+const char *gpch_last_error(const gpch_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int gpch_version(void) { return GPCH_VERSION; }
+
+size_t gpch_workspace_bytes(const gpch_ctx *ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,410 @@
+// cg.cu -- A6/A7: conjugate gradients, Algorithm 1 (left), with residual
+// replacement every R iterations (Sec. 2.1), for up to 16 right-hand sides
+// that share one pass over the matrix per iteration.
+//
+// Per iteration three kernels run:
+//   matvec  t = A s and the partial sums of s^T t; the last CTA to finish
+//           reduces the partials in a fixed order and sets alpha = u / s^T t
+//   update  x += alpha s, r -= alpha t, partial sums of r^T r; the last CTA
+//           sets beta = u_new / u, u = u_new and retires converged columns
+//   dir     s = r + beta s
+// On a replacement iteration `update` is split into x += alpha s, a matvec
+// of x, and r = b - A x.  All scalars stay on the device; the host reads
+// one "all done" word every few iterations.  Reductions are two-phase with
+// a fixed order, so results do not depend on CTA scheduling.
+//
+// The matvec uses A = A^T: t_j = sum_i A_ij s_i is a dot product down column
+// j, which is contiguous in column-major storage.  A CTA owns W consecutive
+// columns and walks all rows; each thread keeps the s values of its rows in
+// registers and reuses them across the W columns and NR right-hand sides.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int ROWS_PER_THREAD = 2;
+constexpr int MAXRHS = 16;
+
+struct CGState {
+    double *u, *u0, *alpha, *beta;   // [MAXRHS]
+    int *active, *iters;            // [MAXRHS]
+    int *done;                      // [1]
+    unsigned *counter;              // [2]: matvec, update
+    double *part;                   // [max_ctas * MAXRHS]
+};
+
+__device__ inline double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Last-CTA election for a two-phase reduction: every CTA has written its
+// partials; returns true in exactly one CTA, after which all partials are
+// visible to it.
+__device__ inline bool last_cta(unsigned *counter)
+{
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ticket = atomicAdd(counter, 1u);
+        is_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+template <typename TA, int W, int NR>
+__global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int nrhs, const TA *__restrict__ A,
+                                                            int64_t lda, const double *__restrict__ S,
+                                                            int64_t lds, double *T, int64_t ldt, CGState st,
+                                                            int mode)
+{
+    // mode 0: t = A s, then alpha; mode 1: t = A s only (s is x here)
+    __shared__ double red[THREADS / 32][W * NR];
+    __shared__ double tcol[W * NR];
+    if (*st.done) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t j0 = (int64_t)blockIdx.x * W;
+    const int wcols = (int)((n - j0 < W) ? n - j0 : W);
+    double acc[W][NR];
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[c][r] = 0.0;
+
+    for (int64_t base = 0; base < n; base += (int64_t)THREADS * ROWS_PER_THREAD) {
+        double sv[ROWS_PER_THREAD][NR];
+        int64_t rows[ROWS_PER_THREAD];
+#pragma unroll
+        for (int q = 0; q < ROWS_PER_THREAD; ++q) {
+            rows[q] = base + tid + (int64_t)q * THREADS;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                sv[q][r] = (rows[q] < n && r < nrhs) ? S[rows[q] + r * lds] : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            if (c < wcols) {
+#pragma unroll
+                for (int q = 0; q < ROWS_PER_THREAD; ++q) {
+                    if (rows[q] < n) {
+                        const double a = (double)A[rows[q] + (j0 + c) * lda];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) acc[c][r] = fma(a, sv[q][r], acc[c][r]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            double v = warp_sum(acc[c][r]);
+            if (lane == 0) red[warp][c * NR + r] = v;
+        }
+    __syncthreads();
+    if (tid < W * NR) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; ++w) v += red[w][tid];
+        tcol[tid] = v;
+        const int c = tid / NR, r = tid % NR;
+        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = v;
+    }
+    if (mode != 0) return;
+    __syncthreads();
+    if (tid < NR) {
+        double p = 0.0;
+        for (int c = 0; c < wcols; ++c)
+            if (tid < nrhs) p = fma(S[(j0 + c) + tid * lds], tcol[c * NR + tid], p);
+        st.part[(size_t)blockIdx.x * MAXRHS + tid] = p;
+    }
+    if (last_cta(&st.counter[0])) {
+        if (tid < nrhs) {
+            double p = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) p += __ldcg(&st.part[(size_t)b * MAXRHS + tid]);
+            st.alpha[tid] = st.active[tid] ? st.u[tid] / p : 0.0;
+        }
+        if (tid == 0) st.counter[0] = 0;
+    }
+}
+
+// Tail of update/replace: reduce r^T r partials, set beta, retire columns.
+__device__ inline void finish_rr(CGState st, int nrhs, double rtol2, int maxit, bool count_iter)
+{
+    const int tid = threadIdx.x;
+    if (last_cta(&st.counter[1])) {
+        __shared__ int any_active;
+        if (tid == 0) any_active = 0;
+        __syncthreads();
+        if (tid < nrhs && st.active[tid]) {
+            double un = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) un += __ldcg(&st.part[(size_t)b * MAXRHS + tid]);
+            st.beta[tid] = un / st.u[tid];
+            st.u[tid] = un;
+            int it = st.iters[tid] + (count_iter ? 1 : 0);
+            st.iters[tid] = it;
+            if (un <= rtol2 * st.u0[tid] || it >= maxit) st.active[tid] = 0;
+            else atomicOr(&any_active, 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (!any_active) *st.done = 1;
+            st.counter[1] = 0;
+        }
+    }
+}
+
+// x += alpha s; r -= alpha t (or, with replace, r = b - t where t = A x and
+// x was already updated); partial r^T r per CTA.
+__global__ void __launch_bounds__(THREADS) cg_update_kernel(int64_t n, int nrhs, double *X, int64_t ldx,
+                                                            double *R, const double *S, const double *T,
+                                                            const double *B, int64_t ldb, int64_t ldv,
+                                                            CGState st, double rtol2, int maxit, int replace)
+{
+    __shared__ double red[THREADS / 32][MAXRHS];
+    if (*st.done) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
+    for (int r = 0; r < nrhs; ++r) {
+        double rr = 0.0;
+        if (st.active[r] && i < n) {
+            double ri;
+            if (replace) {
+                ri = B[i + r * ldb] - T[i + r * ldv];
+            } else {
+                const double a = st.alpha[r];
+                X[i + r * ldx] = fma(a, S[i + r * ldv], X[i + r * ldx]);
+                ri = fma(-a, T[i + r * ldv], R[i + r * ldv]);
+            }
+            R[i + r * ldv] = ri;
+            rr = ri * ri;
+        }
+        rr = warp_sum(rr);
+        if (lane == 0) red[warp][r] = rr;
+    }
+    __syncthreads();
+    if (tid < nrhs) {
+        double v = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) v += red[w][tid];
+        st.part[(size_t)blockIdx.x * MAXRHS + tid] = v;
+    }
+    finish_rr(st, nrhs, rtol2, maxit, true);
+}
+
+// x += alpha s only (first half of a replacement iteration).
+__global__ void __launch_bounds__(THREADS) cg_xupdate_kernel(int64_t n, int nrhs, double *X, int64_t ldx,
+                                                             const double *S, int64_t ldv, CGState st)
+{
+    if (*st.done) return;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    if (i >= n) return;
+    for (int r = 0; r < nrhs; ++r)
+        if (st.active[r]) X[i + r * ldx] = fma(st.alpha[r], S[i + r * ldv], X[i + r * ldx]);
+}
+
+__global__ void __launch_bounds__(THREADS) cg_dir_kernel(int64_t n, int nrhs, const double *R, double *S,
+                                                         int64_t ldv, CGState st)
+{
+    if (*st.done) return;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    if (i >= n) return;
+    for (int r = 0; r < nrhs; ++r)
+        if (st.active[r]) S[i + r * ldv] = fma(st.beta[r], S[i + r * ldv], R[i + r * ldv]);
+}
+
+// r = b - t (t = A x0), s = r, partial r^T r; last CTA sets u = u0 and the
+// initial active flags.
+__global__ void __launch_bounds__(THREADS) cg_init_kernel(int64_t n, int nrhs, double *R, double *S,
+                                                          const double *T, const double *B, int64_t ldb,
+                                                          int64_t ldv, CGState st)
+{
+    __shared__ double red[THREADS / 32][MAXRHS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
+    for (int r = 0; r < nrhs; ++r) {
+        double rr = 0.0;
+        if (i < n) {
+            double ri = B[i + r * ldb] - T[i + r * ldv];
+            R[i + r * ldv] = ri;
+            S[i + r * ldv] = ri;
+            rr = ri * ri;
+        }
+        rr = warp_sum(rr);
+        if (lane == 0) red[warp][r] = rr;
+    }
+    __syncthreads();
+    if (tid < nrhs) {
+        double v = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) v += red[w][tid];
+        st.part[(size_t)blockIdx.x * MAXRHS + tid] = v;
+    }
+    if (last_cta(&st.counter[1])) {
+        __shared__ int any_active;
+        if (tid == 0) any_active = 0;
+        __syncthreads();
+        if (tid < nrhs) {
+            double u = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) u += __ldcg(&st.part[(size_t)b * MAXRHS + tid]);
+            st.u[tid] = u;
+            st.u0[tid] = u;
+            st.iters[tid] = 0;
+            st.active[tid] = u > 0.0 ? 1 : 0;
+            if (u > 0.0) atomicOr(&any_active, 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            *st.done = any_active ? 0 : 1;
+            st.counter[1] = 0;
+        }
+    }
+}
+
+template <typename TA>
+gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64_t lda, const double *S,
+                          int64_t lds, double *T, int64_t ldt, const CGState &st, int mode, cudaStream_t s)
+{
+#define GPCH_MV(Wc, NRc)                                                                         \
+    cg_matvec_kernel<TA, Wc, NRc><<<(unsigned)((n + Wc - 1) / Wc), THREADS, 0, s>>>(n, nrhs, A, lda, S, \
+                                                                                    lds, T, ldt, st, mode)
+    if (nrhs <= 1) GPCH_MV(16, 1);
+    else if (nrhs <= 2) GPCH_MV(8, 2);
+    else if (nrhs <= 4) GPCH_MV(4, 4);
+    else if (nrhs <= 8) GPCH_MV(2, 8);
+    else GPCH_MV(2, 16);
+#undef GPCH_MV
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+inline int mv_width(int nrhs) { return nrhs <= 1 ? 16 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2; }
+
+template <typename TA>
+gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb,
+                     double *X, int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s,
+                     int *h_iters, double *h_relres)
+{
+    const int64_t ldv = n;
+    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
+    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
+    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
+    gpch::Carver dry(nullptr);
+    dry.take<double>((size_t)3 * n * nrhs);
+    dry.take<double>(4 * MAXRHS);
+    dry.take<int>(2 * MAXRHS + 1);
+    dry.take<unsigned>(2);
+    dry.take<double>(max_ctas * MAXRHS);
+    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
+    gpch::Carver cv(ctx->ws);
+    double *Rv = cv.take<double>((size_t)n * nrhs);
+    double *Sv = cv.take<double>((size_t)n * nrhs);
+    double *Tv = cv.take<double>((size_t)n * nrhs);
+    CGState st;
+    double *sc = cv.take<double>(4 * MAXRHS);
+    st.u = sc;
+    st.u0 = sc + MAXRHS;
+    st.alpha = sc + 2 * MAXRHS;
+    st.beta = sc + 3 * MAXRHS;
+    int *ic = cv.take<int>(2 * MAXRHS + 1);
+    st.active = ic;
+    st.iters = ic + MAXRHS;
+    st.done = ic + 2 * MAXRHS;
+    st.counter = cv.take<unsigned>(2);
+    st.part = cv.take<double>(max_ctas * MAXRHS);
+    GPCH_CUDA(ctx, cudaMemsetAsync(st.counter, 0, 2 * sizeof(unsigned), s));
+    GPCH_CUDA(ctx, cudaMemsetAsync(ic, 0, (2 * MAXRHS + 1) * sizeof(int), s));
+
+    // line 1: s = r = b - A x
+    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
+    cg_init_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, Sv, Tv, B, ldb, ldv, st);
+    GPCH_LAUNCH_CHECK(ctx);
+
+    int *h_done = static_cast<int *>(ctx->pinned);
+    const double rtol2 = rtol * rtol;
+    const int chunk = 16;
+    int it = 0;
+    while (it < maxit) {
+        const int k = (maxit - it < chunk) ? maxit - it : chunk;
+        for (int q = 0; q < k; ++q) {
+            const int iter = it + q + 1;   // 1-based number of the iteration being run
+            GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
+            if (R > 0 && iter % R == 0) {
+                cg_xupdate_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Sv, ldv, st);
+                GPCH_LAUNCH_CHECK(ctx);
+                GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
+                cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, B, ldb, ldv, st, rtol2,
+                                                              maxit, 1);
+            } else {
+                cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, B, ldb, ldv, st, rtol2,
+                                                              maxit, 0);
+            }
+            GPCH_LAUNCH_CHECK(ctx);
+            cg_dir_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, Sv, ldv, st);
+            GPCH_LAUNCH_CHECK(ctx);
+        }
+        it += k;
+        GPCH_CUDA(ctx, cudaMemcpyAsync(h_done, st.done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+        if (*h_done) break;
+    }
+    // statistics
+    double *h_sc = reinterpret_cast<double *>(static_cast<char *>(ctx->pinned) + 64);
+    int *h_ic = reinterpret_cast<int *>(static_cast<char *>(ctx->pinned) + 64 + 4 * MAXRHS * sizeof(double));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h_sc, sc, 4 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h_ic, ic, (2 * MAXRHS + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int r = 0; r < nrhs; ++r) {
+        h_iters[r] = h_ic[MAXRHS + r];
+        const double u = h_sc[r], u0 = h_sc[MAXRHS + r];
+        h_relres[r] = u0 > 0.0 ? sqrt(u / u0) : 0.0;
+    }
+    return GPCH_OK;
+}
+
+}  // namespace
+
+extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
+                                     const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol,
+                                     int maxit, int replace_every, void *stream, gpch_cg_stats *stats)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    if (stats) *stats = gpch_cg_stats{0, 0, 0.0};
+    GPCH_ARG(ctx, n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
+    GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
+    GPCH_ARG(ctx, dtype == GPCH_F64 || dtype == GPCH_F32, "bad dtype");
+    GPCH_ARG(ctx, maxit > 0 && replace_every >= 0 && rtol >= 0.0, "bad maxit / replace_every / rtol");
+    if (n == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, A && B && X, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int max_it = 0, conv = 0;
+    double rel_max = 0.0;
+    for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
+        const int g = (nrhs - r0 < MAXRHS) ? nrhs - r0 : MAXRHS;
+        int iters[MAXRHS];
+        double rel[MAXRHS];
+        gpch_status st;
+        if (dtype == GPCH_F64)
+            st = cg_group<double>(ctx, n, static_cast<const double *>(A), lda, B + r0 * ldb, ldb, X + r0 * ldx,
+                                  ldx, g, rtol, maxit, replace_every, s, iters, rel);
+        else
+            st = cg_group<float>(ctx, n, static_cast<const float *>(A), lda, B + r0 * ldb, ldb, X + r0 * ldx,
+                                 ldx, g, rtol, maxit, replace_every, s, iters, rel);
+        if (st != GPCH_OK) return st;
+        for (int r = 0; r < g; ++r) {
+            if (iters[r] > max_it) max_it = iters[r];
+            if (rel[r] > rel_max) rel_max = rel[r];
+            if (rel[r] <= rtol) ++conv;
+        }
+    }
+    if (stats) *stats = gpch_cg_stats{max_it, conv, rel_max};
+    if (conv < nrhs)
+        return gpch::fail(ctx, GPCH_NOT_CONVERGED, "%d of %d right-hand sides missed rtol within %d iterations",
+                          nrhs - conv, nrhs, maxit);
+    return GPCH_OK;
+}

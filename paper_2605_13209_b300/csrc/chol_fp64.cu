@@ -1,0 +1,287 @@
+// chol_fp64.cu -- A2-A4: FP64 blocked right-looking Cholesky, Algorithm 1
+// (right) of the paper, in place on the lower triangle of a column-major
+// matrix.
+//
+// Per block column j of width `tile`:
+//   step 1  the diagonal tile is factored as a nest of 64-wide leaf steps
+//           (potrf_leaf -> inverse-apply TRSM below it -> SYRK inside it);
+//   step 2  the panel below is solved against L_jj^T one 64-column chunk at
+//           a time: X_c = B_c inv(L_cc)^T, then B_{>c} -= X_c L_{>c,c}^T;
+//   step 3  one launch updates every 64 x 64 tile of the trailing lower
+//           triangle, A_ik -= A_ij A_kj^T with K = tile (SYRK on the
+//           diagonal tiles, GEMM below them).
+// A device-side info word stops all later kernels after a failed pivot.
+#include "dense_fp64.cuh"
+
+namespace {
+
+using gpch::LEAF;
+
+// Step 1 leaf: factor the nb x nb (nb <= 64) lower block at A in place and
+// write inv(L) of the unit-padded 64 x 64 block to Linv (column-major, ld 64).
+__global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *Linv,
+                                                         int64_t col0, int64_t *info)
+{
+    extern __shared__ double leaf_smem[];
+    double (*S)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem);
+    double (*Vi)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem + LEAF * (LEAF + 1));
+    __shared__ int bad;
+    if (*info != 0) return;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
+        int r = e % LEAF, c = e / LEAF;
+        double v = 0.0;
+        if (r < nb && c < nb) {
+            if (r >= c) v = A[r + c * lda];
+        } else if (r == c) {
+            v = 1.0;
+        }
+        S[r][c] = v;
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+            double a = S[j][j];
+            if (!(a > 0.0) || !isfinite(a)) bad = j + 1;
+            else S[j][j] = sqrt(a);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double ljj = S[j][j];
+        for (int i = j + 1 + tid; i < nb; i += blockDim.x) S[i][j] = S[i][j] / ljj;
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            int ii = e % m, kk = e / m;
+            if (ii >= kk) S[j + 1 + ii][j + 1 + kk] -= S[j + 1 + ii][j] * S[j + 1 + kk][j];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) *info = col0 + bad;
+        return;
+    }
+    gpch::invert_lower_64(S, Vi);
+    __syncthreads();
+    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
+        int r = e % LEAF, c = e / LEAF;
+        if (r < nb && c < nb && r >= c) A[r + c * lda] = S[r][c];
+        Linv[r + c * LEAF] = Vi[r][c];
+    }
+}
+
+// Step 2 leaf: X = B inv(L)^T in place on the m x nc panel B (nc <= 64);
+// every CTA owns 64 whole rows, so reading B and writing X never overlap
+// across CTAs.
+__global__ void __launch_bounds__(256) trsm_inv_kernel(double *B, int64_t ldb, int64_t m, int nc,
+                                                       const double *__restrict__ Linv,
+                                                       const int64_t *info)
+{
+    extern __shared__ double smem[];
+    double *Bs = smem;                 // Bs[k * 64 + r]
+    double *Ls = smem + LEAF * LEAF;   // Ls[k * 64 + c] = inv(L)[c][k]
+    if (*info != 0) return;
+    const int tid = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * LEAF;
+    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
+        int r = e % LEAF, k = e / LEAF;
+        Bs[k * LEAF + r] = (r0 + r < m && k < nc) ? B[(r0 + r) + k * ldb] : 0.0;
+        Ls[k * LEAF + r] = Linv[r + k * LEAF];
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    double acc[4][4] = {};
+    for (int k = 0; k < LEAF; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = Bs[k * LEAF + tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Ls[k * LEAF + ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t r = r0 + tx + 16 * i;
+            int c = ty + 16 * j;
+            if (r < m && c < nc) B[r + c * ldb] = acc[i][j];
+        }
+}
+
+// C[m x nn] -= A[m x k] B[nn x k]^T (FP64).  LOWER: C is square and only its
+// lower triangle is updated; the grid enumerates the lower 64 x 64 tiles.
+template <bool LOWER>
+__global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
+                                                            const double *__restrict__ A, int64_t lda,
+                                                            const double *__restrict__ B, int64_t ldb,
+                                                            double *C, int64_t ldc, const int64_t *info)
+{
+    constexpr int KC = 32;
+    __shared__ double As[KC][LEAF];
+    __shared__ double Bs[KC][LEAF];
+    if (info && *info != 0) return;
+    int64_t ti, tj;
+    if (LOWER) {
+        int64_t t = blockIdx.x;
+        ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+        tj = t - ti * (ti + 1) / 2;
+    } else {
+        ti = blockIdx.x;
+        tj = blockIdx.y;
+    }
+    const int64_t r0 = ti * LEAF, c0 = tj * LEAF;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < k; k0 += KC) {
+        for (int e = tid; e < KC * LEAF; e += blockDim.x) {
+            int r = e % LEAF, kk = e / LEAF;
+            bool kin = k0 + kk < k;
+            As[kk][r] = (kin && r0 + r < m) ? A[(r0 + r) + (int64_t)(k0 + kk) * lda] : 0.0;
+            Bs[kk][r] = (kin && c0 + r < nn) ? B[(c0 + r) + (int64_t)(k0 + kk) * ldb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KC; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
+            if (r < m && c < nn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
+        }
+}
+
+constexpr size_t TRSM_SMEM = 2 * LEAF * LEAF * sizeof(double);
+constexpr size_t LEAF_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
+
+gpch_status launch_gemm(gpch_ctx *ctx, bool lower, int64_t m, int64_t nn, int k, const double *A,
+                        int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
+                        const int64_t *info, cudaStream_t st)
+{
+    if (m <= 0 || nn <= 0 || k <= 0) return GPCH_OK;
+    if (lower) {
+        int64_t T = (m + LEAF - 1) / LEAF;
+        gemm_nt_minus_kernel<true><<<(unsigned)(T * (T + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C,
+                                                                                  ldc, info);
+    } else {
+        dim3 grid((unsigned)((m + LEAF - 1) / LEAF), (unsigned)((nn + LEAF - 1) / LEAF));
+        gemm_nt_minus_kernel<false><<<grid, 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C, ldc, info);
+    }
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+gpch_status launch_trsm(gpch_ctx *ctx, double *B, int64_t ldb, int64_t m, int nc, const double *Linv,
+                        const int64_t *info, cudaStream_t st)
+{
+    if (m <= 0) return GPCH_OK;
+    trsm_inv_kernel<<<(unsigned)((m + LEAF - 1) / LEAF), 256, TRSM_SMEM, st>>>(B, ldb, m, nc, Linv, info);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+}  // namespace
+
+namespace gpch {
+
+// Enqueue the FP64 factorization of the n x n lower triangle at A.
+// Linv: workspace of tile/64 * 64*64 doubles; info: device int64 (zeroed by
+// the caller).  Used by gpch_chol_factor and by the refined solve.
+gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *Linv,
+                              int64_t *info, cudaStream_t st)
+{
+    static bool attr_done = false;
+    if (!attr_done) {
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(trsm_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)TRSM_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(potrf_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)LEAF_SMEM));
+        attr_done = true;
+    }
+    for (int64_t j0 = 0; j0 < n; j0 += tile) {
+        const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
+        double *Ajj = A + j0 + j0 * lda;
+        // step 1: the diagonal tile, as a nest of 64-wide leaf steps
+        for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
+            const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
+            double *Lc = Linv + (c0 / LEAF) * LEAF * LEAF;
+            potrf_leaf_kernel<<<1, 256, LEAF_SMEM, st>>>(Ajj + c0 + c0 * lda, lda, nc, Lc, j0 + c0, info);
+            GPCH_LAUNCH_CHECK(ctx);
+            const int64_t mr = nj - c0 - nc;
+            if (mr > 0) {
+                double *P = Ajj + (c0 + nc) + c0 * lda;
+                GPCH_CHECK(launch_trsm(ctx, P, lda, mr, nc, Lc, info, st));
+                GPCH_CHECK(launch_gemm(ctx, true, mr, mr, nc, P, lda, P, lda, Ajj + (c0 + nc) * (1 + lda), lda,
+                                       info, st));
+            }
+        }
+        // step 2: panel below the tile, chunk by chunk
+        const int64_t m = n - j0 - nj;
+        if (m <= 0) continue;
+        double *Pan = A + (j0 + nj) + j0 * lda;
+        for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
+            const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
+            double *Xc = Pan + c0 * lda;
+            GPCH_CHECK(launch_trsm(ctx, Xc, lda, m, nc, Linv + (c0 / LEAF) * LEAF * LEAF, info, st));
+            const int64_t rest = nj - c0 - nc;
+            if (rest > 0)
+                GPCH_CHECK(launch_gemm(ctx, false, m, rest, nc, Xc, lda, Ajj + (c0 + nc) + c0 * lda, lda,
+                                       Pan + (c0 + nc) * lda, lda, info, st));
+        }
+        // step 3: trailing lower triangle, K = tile
+        GPCH_CHECK(launch_gemm(ctx, true, m, m, (int)nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda), lda,
+                               info, st));
+    }
+    return GPCH_OK;
+}
+
+}  // namespace gpch
+
+extern "C" gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda,
+                                        void *stream, int64_t *info)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, info != nullptr, "info must not be NULL");
+    *info = 0;
+    GPCH_ARG(ctx, n >= 0, "n < 0");
+    GPCH_ARG(ctx, lda >= (n > 0 ? n : 1), "lda < n");
+    GPCH_ARG(ctx, tile >= LEAF && tile <= 1024 && tile % LEAF == 0, "tile must be a multiple of 64 in [64, 1024]");
+    if (n == 0) return GPCH_OK;
+    GPCH_ARG(ctx, A != nullptr, "null A");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    gpch::Carver dry(nullptr);
+    dry.take<int64_t>(1);
+    dry.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
+    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
+    gpch::Carver cv(ctx->ws);
+    int64_t *d_info = cv.take<int64_t>(1);
+    double *Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
+    GPCH_CUDA(ctx, cudaMemsetAsync(d_info, 0, sizeof(int64_t), st));
+    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, Linv, d_info, st));
+    int64_t *h = static_cast<int64_t *>(ctx->pinned);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+    *info = *h;
+    if (*info != 0) return gpch::fail(ctx, GPCH_NOT_SPD, "pivot %lld not positive", (long long)*info);
+    return GPCH_OK;
+}

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libgpchol.so (C ABI in include/gpchol.h).
+
+Argument marshalling only: every step of every solve runs in the CUDA
+library.  Device matrices are torch tensors in column-major layout (stride
+(1, ld)); ``colmajor`` makes one.  The current torch CUDA stream is passed to
+each call.  If the library is missing, or there is no GPU, calls raise; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpchol.so")
+
+GPCH_OK, GPCH_INVALID_ARG, GPCH_NOT_SPD, GPCH_NOT_CONVERGED, GPCH_OOM_BUDGET, GPCH_TIMEOUT, GPCH_CUDA_ERROR = range(7)
+GPCH_F64, GPCH_F32 = 0, 1
+GPCH_PREC_FP64, GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 = 0, 1, 2
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_dbl = ctypes.c_double
+_int = ctypes.c_int
+
+
+class GpchError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class CGStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("relres_max", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgpchol.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2605_13209_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        L.gpch_create.argtypes = [ctypes.POINTER(_vp), _int, ctypes.c_size_t]
+        L.gpch_destroy.argtypes = [_vp]
+        L.gpch_status_string.argtypes = [_int]
+        L.gpch_status_string.restype = ctypes.c_char_p
+        L.gpch_last_error.argtypes = [_vp]
+        L.gpch_last_error.restype = ctypes.c_char_p
+        L.gpch_version.restype = _int
+        L.gpch_workspace_bytes.argtypes = [_vp]
+        L.gpch_workspace_bytes.restype = ctypes.c_size_t
+        L.gpch_se_matrix.argtypes = [_vp, _i64, _int, _vp, _dbl, _dbl, _dbl, _vp, _i64, _vp]
+        L.gpch_chol_factor.argtypes = [_vp, _i64, _int, _vp, _i64, _vp, ctypes.POINTER(_i64)]
+        L.gpch_chol_solve.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
+        L.gpch_cg_solve.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int, _vp,
+                                    ctypes.POINTER(CGStats)]
+        for name in ("gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
+                     "gpch_cg_solve"):
+            getattr(L, name).restype = _int
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().gpch_status_string(int(s)).decode()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def colmajor(n: int, m: int, dtype=torch.float64, device="cuda", ld: int | None = None) -> torch.Tensor:
+    """Empty n x m tensor in column-major layout (stride (1, ld))."""
+    ld = n if ld is None else ld
+    return torch.empty((m, ld), dtype=dtype, device=device).t()[:n]
+
+
+def as_colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Column-major copy of a 1-D or 2-D tensor (1-D becomes n x 1)."""
+    if t.dim() == 1:
+        t = t[:, None]
+    out = colmajor(t.shape[0], t.shape[1], t.dtype, t.device)
+    out.copy_(t)
+    return out
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.stride(0) != 1:
+        raise ValueError("expected a column-major 2-D tensor (stride(0) == 1); use colmajor()/as_colmajor()")
+    return max(t.stride(1), 1) if t.shape[1] > 1 else max(t.shape[0], 1)
+
+
+def _check_cuda(t: torch.Tensor, dtype):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+
+
+class Context:
+    """A library context (device, workspace arena, HBM budget)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._h = _vp()
+        st = lib().gpch_create(ctypes.byref(self._h), int(device), int(hbm_budget_bytes))
+        if st != GPCH_OK:
+            raise GpchError(st, "gpch_create failed (no usable CUDA device?)")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, st: int):
+        if st != GPCH_OK:
+            raise GpchError(st, lib().gpch_last_error(self._h).decode())
+
+    def workspace_bytes(self) -> int:
+        return int(lib().gpch_workspace_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            lib().gpch_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx: Context | None = None
+
+
+def default_context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context(torch.cuda.current_device())
+    return _default_ctx
+
+
+def se_matrix(X: torch.Tensor, sf2: float, ell: float, sn2: float, A: torch.Tensor | None = None,
+              ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """A1: squared-exponential covariance of the points X (n x d, row-major,
+    float64, CUDA) into a full n x n column-major A."""
+    ctx = ctx or default_context()
+    _check_cuda(X, torch.float64)
+    X = X.contiguous()
+    n, d = X.shape
+    if A is None:
+        A = colmajor(n, n, device=X.device)
+    ctx.check(lib().gpch_se_matrix(ctx.handle, n, d, X.data_ptr(), sf2, ell, sn2, A.data_ptr(), _ld(A),
+                                   _stream(stream)))
+    return A
+
+
+def chol_factor(A: torch.Tensor, tile: int = 256, ctx: Context | None = None, stream=None,
+                raise_on_not_spd: bool = True) -> int:
+    """A2-A4: in-place FP64 blocked Cholesky of the column-major A (lower
+    triangle).  Returns info (0 on success)."""
+    ctx = ctx or default_context()
+    _check_cuda(A, torch.float64)
+    info = _i64(0)
+    st = lib().gpch_chol_factor(ctx.handle, A.shape[0], int(tile), A.data_ptr(), _ld(A), _stream(stream),
+                                ctypes.byref(info))
+    if st == GPCH_NOT_SPD and not raise_on_not_spd:
+        return int(info.value)
+    ctx.check(st)
+    return int(info.value)
+
+
+def chol_solve(L: torch.Tensor, B: torch.Tensor, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """A5: solve L L^T X = B in place on the column-major B (n x nrhs)."""
+    ctx = ctx or default_context()
+    _check_cuda(L, torch.float64)
+    _check_cuda(B, torch.float64)
+    ctx.check(lib().gpch_chol_solve(ctx.handle, L.shape[0], L.data_ptr(), _ld(L), B.data_ptr(), _ld(B), B.shape[1],
+                                    _stream(stream)))
+    return B
+
+
+@dataclass
+class CGResult:
+    iterations: int
+    converged: int
+    relres_max: float
+    status: int
+
+
+def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e-10, maxit: int = 10000,
+             replace_every: int = 50, ctx: Context | None = None, stream=None,
+             raise_on_not_converged: bool = True) -> CGResult:
+    """A6-A7: CG (Algorithm 1, left) on the full column-major A (float64 or
+    float32), right-hand sides B and start/solution X (n x nrhs, float64)."""
+    ctx = ctx or default_context()
+    if A.dtype not in (torch.float64, torch.float32):
+        raise ValueError("A must be float64 or float32")
+    _check_cuda(A, A.dtype)
+    _check_cuda(B, torch.float64)
+    _check_cuda(X, torch.float64)
+    stats = CGStats()
+    dt = GPCH_F64 if A.dtype == torch.float64 else GPCH_F32
+    st = lib().gpch_cg_solve(ctx.handle, A.shape[0], A.data_ptr(), dt, _ld(A), B.data_ptr(), _ld(B), X.data_ptr(),
+                             _ld(X), B.shape[1], rtol, int(maxit), int(replace_every), _stream(stream),
+                             ctypes.byref(stats))
+    if st != GPCH_OK and not (st == GPCH_NOT_CONVERGED and not raise_on_not_converged):
+        ctx.check(st)
+    return CGResult(stats.iterations, stats.converged, stats.relres_max, st)
