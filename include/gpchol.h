@@ -86,6 +86,35 @@ int gpch_version(void);
 /* Bytes of workspace currently held by the context. */
 size_t gpch_workspace_bytes(const gpch_ctx *ctx);
 
+/* ------------------------------------------------------------ tracing */
+
+/* Phases whose kernels can be timed with CUDA events recorded on the
+ * launching stream around every launch of the phase. */
+typedef enum gpch_phase {
+    GPCH_PHASE_SE = 0,          /* A1 kernel matrix                               */
+    GPCH_PHASE_DIAG = 1,        /* Algorithm 1 step 1 (diagonal tile)             */
+    GPCH_PHASE_PANEL = 2,       /* Algorithm 1 step 2 (panel solve)               */
+    GPCH_PHASE_TRAILING = 3,    /* Algorithm 1 step 3, FP64 (SYRK/GEMM)            */
+    GPCH_PHASE_SOLVE = 4,       /* forward + back substitution                    */
+    GPCH_PHASE_CG_MATVEC = 5,   /* CG matrix-vector product (one pass over A)      */
+    GPCH_PHASE_CG_VECTOR = 6,   /* CG dot/axpy/xpay kernels                        */
+    GPCH_PHASE_MIXED_TRAILING = 7, /* step 3 on tensor cores (bf16 / split bf16)  */
+    GPCH_PHASE_COUNT = 8
+} gpch_phase;
+
+/* Turn event timing on or off (off by default; costs two event records per
+ * timed launch).  Turning it on clears the accumulated totals. */
+gpch_status gpch_timing_enable(gpch_ctx *ctx, int enable);
+
+/* Totals for one phase since timing was enabled: summed launch durations
+ * (ms), launches timed, and the algorithmic work of those launches (flops
+ * for factorization phases, bytes for CG phases; see the phase list).
+ * Synchronizes on the recorded events.  Any output pointer may be NULL. */
+gpch_status gpch_timing_read(gpch_ctx *ctx, int phase, double *total_ms, int64_t *launches, double *work);
+
+/* Number of kernels this context has launched since it was created. */
+int64_t gpch_launch_count(const gpch_ctx *ctx);
+
 /* ------------------------------------------------ A1: GP kernel matrix */
 
 /* Squared-exponential GP covariance of n points X (device, n x d,
@@ -156,6 +185,59 @@ gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A,
                           int64_t ldb, double *X, int64_t ldx, int nrhs,
                           double rtol, int maxit, int replace_every,
                           void *stream, gpch_cg_stats *stats);
+
+/* --------------------------- A4 (mixed): tensor-core trailing update */
+
+/* C -= P P^T on the lower triangle of the m x m FP32 matrix C (ldc), with
+ * P the m x k FP32 panel (ldp): the operation of Algorithm 1 step 3 for a
+ * whole trailing matrix, computed on the tensor cores from a bfloat16 copy
+ * of P (prec = GPCH_PREC_BF16) or from a bfloat16 head and tail of P with
+ * head*head^T + head*tail^T + tail*head^T (GPCH_PREC_SPLIT_BF16), FP32
+ * accumulation.  The strict upper triangle of C is not touched.  k <= 4096.
+ * Synchronizes `stream` (returns GPCH_TIMEOUT if a bounded pipeline wait
+ * gave up).  Mixed precision is the paper's future work (Sec. 5). */
+gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, const float *P, int64_t ldp, float *C,
+                              int64_t ldc, gpch_prec prec, void *stream);
+
+/* ------------------------------------- A8: low-precision factor */
+
+/* Low-precision Cholesky factor of A + shift I: Algorithm 1 (right) on an
+ * FP32 copy with step 1 in FP64, step 2 in FP32 and step 3 on the tensor
+ * cores as in gpch_syrk_lowprec.  A: device FP64 n x n (lower triangle
+ * read, not modified).  L: device FP32 n x n (ldl), receives the factor in
+ * its lower triangle.  prec: GPCH_PREC_BF16 or GPCH_PREC_SPLIT_BF16.
+ * info (host): 0, or the 1-based column of a non-positive pivot (returns
+ * GPCH_NOT_SPD).  Synchronizes `stream`. */
+gpch_status gpch_chol_factor_mixed(gpch_ctx *ctx, int64_t n, int tile, const double *A, int64_t lda,
+                                   gpch_prec prec, double shift, float *L, int64_t ldl, void *stream,
+                                   int64_t *info);
+
+/* --------------------------------------------- A9: refined solve */
+
+typedef struct gpch_refine_stats {
+    int32_t iterations;          /* PCG iterations (max over RHS groups)       */
+    int32_t factor_attempts;     /* low-precision factorizations run           */
+    double shift;                /* diagonal shift of the accepted factor      */
+    double backward_error_max;   /* max over RHS of the final true backward error */
+} gpch_refine_stats;
+
+/* Solve A X = B to a normwise backward error
+ *     ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= bwd_tol
+ * per column: low-precision factor Lt of A + delta I (gpch_chol_factor_mixed
+ * with the shift schedule delta_0 = 0 for SPLIT_BF16 and 2^-7 max_i A_ii for
+ * BF16, then delta <- max(4 delta, 2 u max_i A_ii) after each breakdown, at
+ * most 9 attempts), then preconditioned CG with M = Lt Lt^T in FP64 (A, x,
+ * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
+ * from x_0 = 0, replacing the recurrence residual by b - A x every 50
+ * iterations and whenever the recurrence estimate reaches bwd_tol.
+ * A: device FP64 full symmetric n x n (lda).  B: device n x nrhs (ldb).
+ * X: device n x nrhs (ldx), overwritten.  Workspace: about 4 n^2 bytes.
+ * stats (host, may be NULL).  Synchronizes `stream`.  Returns GPCH_NOT_SPD
+ * if every shifted factorization broke down, GPCH_NOT_CONVERGED if some
+ * column missed bwd_tol within maxit iterations. */
+gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *B,
+                               int64_t ldb, double *X, int64_t ldx, int nrhs, gpch_prec prec, int tile,
+                               double bwd_tol, int maxit, void *stream, gpch_refine_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -42,6 +42,21 @@ gpch_status ws_reserve(gpch_ctx *ctx, size_t bytes)
     return GPCH_OK;
 }
 
+cudaEvent_t take_event(gpch_ctx *ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
 }  // namespace gpch
 
 extern "C" {
@@ -76,6 +91,12 @@ gpch_status gpch_destroy(gpch_ctx *ctx)
     if (!ctx) return GPCH_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    for (auto &v : ctx->pending)
+        for (auto &t : v) {
+            cudaEventDestroy(t.start);
+            cudaEventDestroy(t.stop);
+        }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;
@@ -101,5 +122,49 @@ const char *gpch_last_error(const gpch_ctx *ctx) { return ctx ? ctx->err : "no c
 int gpch_version(void) { return GPCH_VERSION; }
 
 size_t gpch_workspace_bytes(const gpch_ctx *ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+int64_t gpch_launch_count(const gpch_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+static gpch_status drain_phase(gpch_ctx *ctx, int ph)
+{
+    for (auto &t : ctx->pending[ph]) {
+        float ms = 0.f;
+        GPCH_CUDA(ctx, cudaEventSynchronize(t.stop));
+        GPCH_CUDA(ctx, cudaEventElapsedTime(&ms, t.start, t.stop));
+        ctx->phase_ms[ph] += ms;
+        ctx->phase_launches[ph] += 1;
+        ctx->phase_work[ph] += t.work;
+        ctx->event_pool.push_back(t.start);
+        ctx->event_pool.push_back(t.stop);
+    }
+    ctx->pending[ph].clear();
+    return GPCH_OK;
+}
+
+gpch_status gpch_timing_enable(gpch_ctx *ctx, int enable)
+{
+    if (!ctx) return GPCH_INVALID_ARG;
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    for (int ph = 0; ph < GPCH_PHASE_COUNT; ++ph) {
+        GPCH_CHECK(drain_phase(ctx, ph));
+        ctx->phase_ms[ph] = 0.0;
+        ctx->phase_launches[ph] = 0;
+        ctx->phase_work[ph] = 0.0;
+    }
+    ctx->timing = enable != 0;
+    return GPCH_OK;
+}
+
+gpch_status gpch_timing_read(gpch_ctx *ctx, int phase, double *total_ms, int64_t *launches, double *work)
+{
+    if (!ctx) return GPCH_INVALID_ARG;
+    if (phase < 0 || phase >= GPCH_PHASE_COUNT) return gpch::fail(ctx, GPCH_INVALID_ARG, "bad phase %d", phase);
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    GPCH_CHECK(drain_phase(ctx, phase));
+    if (total_ms) *total_ms = ctx->phase_ms[phase];
+    if (launches) *launches = ctx->phase_launches[phase];
+    if (work) *work = ctx->phase_work[phase];
+    return GPCH_OK;
+}
 
 }  // extern "C"

@@ -17,7 +17,7 @@
 // j, which is contiguous in column-major storage.  A CTA owns W consecutive
 // columns and walks all rows; each thread keeps the s values of its rows in
 // registers and reuses them across the W columns and NR right-hand sides.
-#include "internal.cuh"
+#include "dense_fp64.cuh"
 
 namespace {
 
@@ -269,6 +269,8 @@ template <typename TA>
 gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64_t lda, const double *S,
                           int64_t lds, double *T, int64_t ldt, const CGState &st, int mode, cudaStream_t s)
 {
+    gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s,
+                        (double)n * n * sizeof(TA) + 2.0 * (double)n * nrhs * sizeof(double));
 #define GPCH_MV(Wc, NRc)                                                                         \
     cg_matvec_kernel<TA, Wc, NRc><<<(unsigned)((n + Wc - 1) / Wc), THREADS, 0, s>>>(n, nrhs, A, lda, S, \
                                                                                     lds, T, ldt, st, mode)
@@ -333,6 +335,7 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
         for (int q = 0; q < k; ++q) {
             const int iter = it + q + 1;   // 1-based number of the iteration being run
             GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
+            gpch::PhaseScope phv(ctx, GPCH_PHASE_CG_VECTOR, s, 9.0 * (double)n * nrhs * sizeof(double));
             if (R > 0 && iter % R == 0) {
                 cg_xupdate_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Sv, ldv, st);
                 GPCH_LAUNCH_CHECK(ctx);
@@ -363,6 +366,346 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
         const double u = h_sc[r], u0 = h_sc[MAXRHS + r];
         h_relres[r] = u0 > 0.0 ? sqrt(u / u0) : 0.0;
     }
+    return GPCH_OK;
+}
+
+// ------------------------------------------------------------ PCG (A9)
+//
+// Refined solve: preconditioned CG with M = Lt Lt^T, Lt the low-precision
+// factor (FP32 storage), applied by the forward/back substitution of
+// solve.cu.  A, x, r, dot products and recurrences stay in FP64.  The host
+// reads a few scalars per iteration (an iteration already costs two
+// substitution sweeps), decides when to replace the recurrence residual by
+// the true one, and stops each column when its true backward error
+// ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) meets the tolerance.
+
+// x += alpha s, r -= alpha t on active columns; per-CTA sum of r^2 and max
+// |x|; the last CTA stores rr[c] and xinf[c].
+__global__ void __launch_bounds__(THREADS) pcg_update_kernel(int64_t n, int nrhs, double *X, int64_t ldx, double *R,
+                                                             const double *S, const double *T, int64_t ldv,
+                                                             CGState st, double *rr_out, double *xinf_out)
+{
+    __shared__ double red[THREADS / 32][2 * MAXRHS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
+    for (int r = 0; r < nrhs; ++r) {
+        double rr = 0.0, xm = 0.0;
+        if (st.active[r] && i < n) {
+            const double a = st.alpha[r];
+            const double xi = fma(a, S[i + r * ldv], X[i + r * ldx]);
+            X[i + r * ldx] = xi;
+            const double ri = fma(-a, T[i + r * ldv], R[i + r * ldv]);
+            R[i + r * ldv] = ri;
+            rr = ri * ri;
+            xm = fabs(xi);
+        }
+        rr = warp_sum(rr);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+        if (lane == 0) {
+            red[warp][r] = rr;
+            red[warp][MAXRHS + r] = xm;
+        }
+    }
+    __syncthreads();
+    if (tid < nrhs) {
+        double v = 0.0, m = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) {
+            v += red[w][tid];
+            m = fmax(m, red[w][MAXRHS + tid]);
+        }
+        st.part[(size_t)blockIdx.x * 2 * MAXRHS + tid] = v;
+        st.part[(size_t)blockIdx.x * 2 * MAXRHS + MAXRHS + tid] = m;
+    }
+    if (last_cta(&st.counter[1])) {
+        if (tid < nrhs) {
+            double v = 0.0, m = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) {
+                v += __ldcg(&st.part[(size_t)b * 2 * MAXRHS + tid]);
+                m = fmax(m, __ldcg(&st.part[(size_t)b * 2 * MAXRHS + MAXRHS + tid]));
+            }
+            rr_out[tid] = v;
+            xinf_out[tid] = m;
+        }
+        if (tid == 0) st.counter[1] = 0;
+    }
+}
+
+// r = b - t (t = A x) on active columns; per-column max |r| and max |x|.
+__global__ void __launch_bounds__(THREADS) pcg_replace_kernel(int64_t n, int nrhs, const double *X, int64_t ldx,
+                                                              double *R, const double *T, const double *B,
+                                                              int64_t ldb, int64_t ldv, CGState st, double *rinf,
+                                                              double *xinf)
+{
+    __shared__ double red[THREADS / 32][2 * MAXRHS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
+    for (int r = 0; r < nrhs; ++r) {
+        double rm = 0.0, xm = 0.0;
+        if (st.active[r] && i < n) {
+            const double ri = B[i + r * ldb] - T[i + r * ldv];
+            R[i + r * ldv] = ri;
+            rm = fabs(ri);
+            xm = fabs(X[i + r * ldx]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, off));
+            xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+        }
+        if (lane == 0) {
+            red[warp][r] = rm;
+            red[warp][MAXRHS + r] = xm;
+        }
+    }
+    __syncthreads();
+    if (tid < nrhs) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) {
+            a = fmax(a, red[w][tid]);
+            b = fmax(b, red[w][MAXRHS + tid]);
+        }
+        st.part[(size_t)blockIdx.x * 2 * MAXRHS + tid] = a;
+        st.part[(size_t)blockIdx.x * 2 * MAXRHS + MAXRHS + tid] = b;
+    }
+    if (last_cta(&st.counter[1])) {
+        if (tid < nrhs) {
+            double a = 0.0, b = 0.0;
+            for (unsigned blk = 0; blk < gridDim.x; ++blk) {
+                a = fmax(a, __ldcg(&st.part[(size_t)blk * 2 * MAXRHS + tid]));
+                b = fmax(b, __ldcg(&st.part[(size_t)blk * 2 * MAXRHS + MAXRHS + tid]));
+            }
+            rinf[tid] = a;
+            xinf[tid] = b;
+        }
+        if (tid == 0) st.counter[1] = 0;
+    }
+}
+
+// out[c] = U_c^T V_c for every column; with set_beta, beta = out / u and
+// u = out on active columns (u starts as out when init is set).
+__global__ void __launch_bounds__(THREADS) pcg_dot_kernel(int64_t n, int nrhs, const double *U, int64_t ldu,
+                                                          const double *V, int64_t ldv, CGState st, double *out,
+                                                          int mode)
+{
+    // mode 0: store only; 1: u = out (init); 2: beta = out / u, u = out
+    __shared__ double red[THREADS / 32][MAXRHS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
+    for (int r = 0; r < nrhs; ++r) {
+        double p = (i < n) ? U[i + r * ldu] * V[i + r * ldv] : 0.0;
+        p = warp_sum(p);
+        if (lane == 0) red[warp][r] = p;
+    }
+    __syncthreads();
+    if (tid < nrhs) {
+        double v = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) v += red[w][tid];
+        st.part[(size_t)blockIdx.x * 2 * MAXRHS + tid] = v;
+    }
+    if (last_cta(&st.counter[1])) {
+        if (tid < nrhs) {
+            double v = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&st.part[(size_t)b * 2 * MAXRHS + tid]);
+            out[tid] = v;
+            if (mode == 1) st.u[tid] = v;
+            if (mode == 2 && st.active[tid]) {
+                st.beta[tid] = v / st.u[tid];
+                st.u[tid] = v;
+            }
+        }
+        if (tid == 0) st.counter[1] = 0;
+    }
+}
+
+// Order-independent maxima of non-negative doubles through their bit
+// patterns (which order like the values).
+__device__ inline void atomic_max_nonneg(double *addr, double v)
+{
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// out[0] = max_j sum_i |A_ij| (= ||A||_inf for symmetric A); out[1] = max_i A_ii.
+__global__ void __launch_bounds__(THREADS) norms_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
+                                                        double *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * THREADS) >> 5;
+    for (int64_t j = gw; j < n; j += nw) {
+        double s = 0.0;
+        for (int64_t i = lane; i < n; i += 32) s += fabs(A[i + j * lda]);
+        s = warp_sum(s);
+        if (lane == 0) {
+            atomic_max_nonneg(&out[0], s);
+            atomic_max_nonneg(&out[1], fmax(A[j + j * lda], 0.0));
+        }
+    }
+}
+
+// out[c] = max_i |V_ic|.
+__global__ void __launch_bounds__(THREADS) absmax_cols_kernel(int64_t n, int nrhs, const double *V, int64_t ldv,
+                                                              double *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    for (int r = 0; r < nrhs; ++r) {
+        double m = (i < n) ? fabs(V[i + r * ldv]) : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&out[r], m);
+    }
+}
+
+struct RefineResult {
+    int iterations = 0;
+    double bwd[MAXRHS] = {0};
+};
+
+// PCG on one group of <= 16 right-hand sides.  L: FP32 factor (ldl).
+gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const float *L, int64_t ldl,
+                      const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double bwd_tol, int maxit,
+                      int R, char *wsbase, cudaStream_t s, RefineResult &res)
+{
+    const int64_t ldv = n;
+    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
+    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
+    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
+    const int64_t NBk = (n + 63) / 64;
+    gpch::Carver cv(wsbase);
+    double *Rv = cv.take<double>((size_t)n * nrhs);
+    double *Zv = cv.take<double>((size_t)n * nrhs);
+    double *Sv = cv.take<double>((size_t)n * nrhs);
+    double *Tv = cv.take<double>((size_t)n * nrhs);
+    double *Yv = cv.take<double>((size_t)n * nrhs);
+    double *Linv = cv.take<double>((size_t)NBk * 64 * 64);
+    CGState st;
+    double *sc = cv.take<double>(4 * MAXRHS);
+    st.u = sc;
+    st.u0 = sc + MAXRHS;
+    st.alpha = sc + 2 * MAXRHS;
+    st.beta = sc + 3 * MAXRHS;
+    int *ic = cv.take<int>(2 * MAXRHS + 1);
+    st.active = ic;
+    st.iters = ic + MAXRHS;
+    st.done = ic + 2 * MAXRHS;
+    st.counter = cv.take<unsigned>(2);
+    st.part = cv.take<double>(max_ctas * 2 * MAXRHS);
+    // ex: rr[16] xinf[16] rinf[16] binf[16] bb[16] norms[2] dots[16]
+    double *ex = cv.take<double>(6 * MAXRHS + 2);
+    double *d_rr = ex, *d_xinf = ex + MAXRHS, *d_rinf = ex + 2 * MAXRHS, *d_binf = ex + 3 * MAXRHS;
+    double *d_bb = ex + 4 * MAXRHS, *d_norms = ex + 5 * MAXRHS, *d_dots = ex + 5 * MAXRHS + 2;
+
+    // host mirror in the pinned block: [0, 6*16+2) doubles, then ints
+    double *h = static_cast<double *>(ctx->pinned);
+    int *h_active = reinterpret_cast<int *>(h + 6 * MAXRHS + 2);
+
+    GPCH_CUDA(ctx, cudaMemsetAsync(st.counter, 0, 2 * sizeof(unsigned), s));
+    GPCH_CUDA(ctx, cudaMemsetAsync(ic, 0, (2 * MAXRHS + 1) * sizeof(int), s));
+    GPCH_CUDA(ctx, cudaMemsetAsync(ex, 0, (6 * MAXRHS + 2) * sizeof(double), s));
+    for (int c = 0; c < MAXRHS; ++c) h_active[c] = c < nrhs ? 1 : 0;
+    GPCH_CUDA(ctx, cudaMemcpyAsync(st.active, h_active, MAXRHS * sizeof(int), cudaMemcpyHostToDevice, s));
+    // x0 = 0, r = b, z = M^-1 r, s = z, u = r^T z
+    for (int c = 0; c < nrhs; ++c) {
+        GPCH_CUDA(ctx, cudaMemsetAsync(X + c * ldx, 0, n * sizeof(double), s));
+        GPCH_CUDA(ctx, cudaMemcpyAsync(Rv + c * ldv, B + c * ldb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    norms_kernel<<<(unsigned)((n * 32 + THREADS - 1) / THREADS < 4096 ? (n * 32 + THREADS - 1) / THREADS : 4096),
+                   THREADS, 0, s>>>(n, A, lda, d_norms);
+    GPCH_LAUNCH_CHECK(ctx);
+    absmax_cols_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, B, ldb, d_binf);
+    GPCH_LAUNCH_CHECK(ctx);
+    pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Rv, ldv, st, d_bb, 0);
+    GPCH_LAUNCH_CHECK(ctx);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(Zv, Rv, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    GPCH_CHECK(gpch::chol_solve_enqueue_f32(ctx, n, L, ldl, Zv, ldv, nrhs, Linv, Yv, s));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(Sv, Zv, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Zv, ldv, st, d_dots, 1);
+    GPCH_LAUNCH_CHECK(ctx);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h, ex, (6 * MAXRHS + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+    const double anorm = h[5 * MAXRHS];
+    double binf[MAXRHS], bb[MAXRHS];
+    for (int c = 0; c < MAXRHS; ++c) {
+        binf[c] = h[3 * MAXRHS + c];
+        bb[c] = h[4 * MAXRHS + c];
+        res.bwd[c] = c < nrhs ? (binf[c] > 0.0 ? 1.0 : 0.0) : 0.0;
+        if (c < nrhs && binf[c] == 0.0) h_active[c] = 0;   // b = 0: x = 0 is exact
+    }
+    GPCH_CUDA(ctx, cudaMemcpyAsync(st.active, h_active, MAXRHS * sizeof(int), cudaMemcpyHostToDevice, s));
+    int nactive = 0;
+    for (int c = 0; c < nrhs; ++c) nactive += h_active[c];
+    const double eps2 = 1e-30;
+    int it = 0;
+    while (nactive > 0 && it < maxit) {
+        GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
+        pcg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, ldv, st, d_rr, d_xinf);
+        GPCH_LAUNCH_CHECK(ctx);
+        ++it;
+        GPCH_CUDA(ctx, cudaMemcpyAsync(h, ex, 2 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+        bool replace = (R > 0 && it % R == 0);
+        for (int c = 0; c < nrhs && !replace; ++c) {
+            if (!h_active[c]) continue;
+            const double est = sqrt(h[c]) / (anorm * h[MAXRHS + c] + binf[c]);
+            if (est <= bwd_tol || h[c] <= eps2 * bb[c]) replace = true;
+        }
+        if (replace) {
+            GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
+            pcg_replace_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Tv, B, ldb, ldv, st, d_rinf,
+                                                            d_xinf);
+            GPCH_LAUNCH_CHECK(ctx);
+            GPCH_CUDA(ctx, cudaMemcpyAsync(h, ex, 3 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+            GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+            nactive = 0;
+            for (int c = 0; c < nrhs; ++c) {
+                if (!h_active[c]) continue;
+                const double den = anorm * h[MAXRHS + c] + binf[c];
+                res.bwd[c] = den > 0.0 ? h[2 * MAXRHS + c] / den : 0.0;
+                if (res.bwd[c] <= bwd_tol) h_active[c] = 0;
+                nactive += h_active[c];
+            }
+            GPCH_CUDA(ctx, cudaMemcpyAsync(st.active, h_active, MAXRHS * sizeof(int), cudaMemcpyHostToDevice, s));
+            if (nactive == 0) break;
+        }
+        GPCH_CUDA(ctx, cudaMemcpyAsync(Zv, Rv, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        GPCH_CHECK(gpch::chol_solve_enqueue_f32(ctx, n, L, ldl, Zv, ldv, nrhs, Linv, Yv, s));
+        pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Zv, ldv, st, d_dots, 2);
+        GPCH_LAUNCH_CHECK(ctx);
+        cg_dir_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Zv, Sv, ldv, st);
+        GPCH_LAUNCH_CHECK(ctx);
+    }
+    res.iterations = it;
+    return GPCH_OK;
+}
+
+size_t pcg_ws_bytes(int64_t n, int nrhs)
+{
+    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
+    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
+    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
+    gpch::Carver dry(nullptr);
+    for (int i = 0; i < 5; ++i) dry.take<double>((size_t)n * nrhs);
+    dry.take<double>((size_t)((n + 63) / 64) * 64 * 64);
+    dry.take<double>(4 * MAXRHS);
+    dry.take<int>(2 * MAXRHS + 1);
+    dry.take<unsigned>(2);
+    dry.take<double>(max_ctas * 2 * MAXRHS);
+    dry.take<double>(6 * MAXRHS + 2);
+    return dry.off;
+}
+
+// max_i A_ii (for the shift schedule), synchronously.
+gpch_status diag_max(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, double *dev2, cudaStream_t s,
+                     double *out)
+{
+    GPCH_CUDA(ctx, cudaMemsetAsync(dev2, 0, 2 * sizeof(double), s));
+    norms_kernel<<<(unsigned)((n * 32 + THREADS - 1) / THREADS < 4096 ? (n * 32 + THREADS - 1) / THREADS : 4096),
+                   THREADS, 0, s>>>(n, A, lda, dev2);
+    GPCH_LAUNCH_CHECK(ctx);
+    double *h = static_cast<double *>(ctx->pinned);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h, dev2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+    *out = h[1];
     return GPCH_OK;
 }
 
@@ -406,5 +749,87 @@ extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gp
     if (conv < nrhs)
         return gpch::fail(ctx, GPCH_NOT_CONVERGED, "%d of %d right-hand sides missed rtol within %d iterations",
                           nrhs - conv, nrhs, maxit);
+    return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *B,
+                                          int64_t ldb, double *X, int64_t ldx, int nrhs, gpch_prec prec, int tile,
+                                          double bwd_tol, int maxit, void *stream, gpch_refine_stats *stats)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    if (stats) *stats = gpch_refine_stats{0, 0, 0.0, 0.0};
+    GPCH_ARG(ctx, n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
+    GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
+    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16, "prec must be BF16 or SPLIT_BF16");
+    GPCH_ARG(ctx, tile >= 64 && tile <= 1024 && tile % 64 == 0, "tile must be a multiple of 64 in [64, 1024]");
+    GPCH_ARG(ctx, bwd_tol > 0.0 && maxit > 0, "bad bwd_tol / maxit");
+    GPCH_ARG(ctx, n < (int64_t)1 << 31, "n too large");
+    if (n == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, A && B && X, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t ldw = (n + 31) / 32 * 32;
+    const int g = nrhs < MAXRHS ? nrhs : MAXRHS;
+    gpch::Carver dry(nullptr);
+    dry.take<float>((size_t)ldw * n);
+    dry.take<double>(2);
+    const size_t fixed = dry.off;
+    const size_t mix = gpch::mixed_ws_bytes(n, tile), pcg = pcg_ws_bytes(n, g);
+    GPCH_CHECK(gpch::ws_reserve(ctx, fixed + 256 + (mix > pcg ? mix : pcg)));
+    gpch::Carver cv(ctx->ws);
+    float *W = cv.take<float>((size_t)ldw * n);
+    double *dev2 = cv.take<double>(2);
+    char *rest = static_cast<char *>(ctx->ws) + ((cv.off + 255) & ~size_t(255));
+
+    double dmax = 0.0;
+    GPCH_CHECK(diag_max(ctx, n, A, lda, dev2, s, &dmax));
+    const double ulow = (prec == GPCH_PREC_BF16) ? 1.0 / 256.0 : 1.0 / 65536.0;
+    double shift = (prec == GPCH_PREC_BF16) ? 2.0 * ulow * dmax : 0.0;
+    int attempts = 0;
+    int64_t info = 1;
+    for (; attempts < 9; ++attempts) {
+        GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, W, ldw, shift, s));
+        int64_t *d_info;
+        int *d_err;
+        GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, W, ldw, (int)prec, rest, &d_info, &d_err, s));
+        int64_t *h = static_cast<int64_t *>(ctx->pinned);
+        GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        GPCH_CUDA(ctx, cudaMemcpyAsync(h + 1, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+        if (reinterpret_cast<int *>(h + 1)[0] != 0)
+            return gpch::fail(ctx, GPCH_TIMEOUT, "tensor-core pipeline wait gave up");
+        info = h[0];
+        if (info == 0) break;
+        const double floor_shift = 2.0 * ulow * dmax;
+        shift = (4.0 * shift > floor_shift) ? 4.0 * shift : floor_shift;
+    }
+    if (stats) {
+        stats->factor_attempts = attempts + (info == 0 ? 1 : 0);
+        stats->shift = shift;
+    }
+    if (info != 0)
+        return gpch::fail(ctx, GPCH_NOT_SPD, "low-precision factor broke down after %d shifted attempts", attempts);
+
+    int it_max = 0;
+    double bwd_max = 0.0;
+    bool all_ok = true;
+    for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
+        const int gg = (nrhs - r0 < MAXRHS) ? nrhs - r0 : MAXRHS;
+        RefineResult rr;
+        GPCH_CHECK(pcg_group(ctx, n, A, lda, W, ldw, B + r0 * ldb, ldb, X + r0 * ldx, ldx, gg, bwd_tol, maxit, 50,
+                             rest, s, rr));
+        if (rr.iterations > it_max) it_max = rr.iterations;
+        for (int c = 0; c < gg; ++c) {
+            if (rr.bwd[c] > bwd_max) bwd_max = rr.bwd[c];
+            if (rr.bwd[c] > bwd_tol) all_ok = false;
+        }
+    }
+    if (stats) {
+        stats->iterations = it_max;
+        stats->backward_error_max = bwd_max;
+    }
+    if (!all_ok)
+        return gpch::fail(ctx, GPCH_NOT_CONVERGED, "refinement missed the backward error %.1e within %d iterations",
+                          bwd_tol, maxit);
     return GPCH_OK;
 }

@@ -71,133 +71,7 @@ __global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda,
     }
 }
 
-// Step 2 leaf: X = B inv(L)^T in place on the m x nc panel B (nc <= 64);
-// every CTA owns 64 whole rows, so reading B and writing X never overlap
-// across CTAs.
-__global__ void __launch_bounds__(256) trsm_inv_kernel(double *B, int64_t ldb, int64_t m, int nc,
-                                                       const double *__restrict__ Linv,
-                                                       const int64_t *info)
-{
-    extern __shared__ double smem[];
-    double *Bs = smem;                 // Bs[k * 64 + r]
-    double *Ls = smem + LEAF * LEAF;   // Ls[k * 64 + c] = inv(L)[c][k]
-    if (*info != 0) return;
-    const int tid = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * LEAF;
-    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
-        int r = e % LEAF, k = e / LEAF;
-        Bs[k * LEAF + r] = (r0 + r < m && k < nc) ? B[(r0 + r) + k * ldb] : 0.0;
-        Ls[k * LEAF + r] = Linv[r + k * LEAF];
-    }
-    __syncthreads();
-    const int tx = tid % 16, ty = tid / 16;
-    double acc[4][4] = {};
-    for (int k = 0; k < LEAF; ++k) {
-        double a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = Bs[k * LEAF + tx + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Ls[k * LEAF + ty + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t r = r0 + tx + 16 * i;
-            int c = ty + 16 * j;
-            if (r < m && c < nc) B[r + c * ldb] = acc[i][j];
-        }
-}
-
-// C[m x nn] -= A[m x k] B[nn x k]^T (FP64).  LOWER: C is square and only its
-// lower triangle is updated; the grid enumerates the lower 64 x 64 tiles.
-template <bool LOWER>
-__global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
-                                                            const double *__restrict__ A, int64_t lda,
-                                                            const double *__restrict__ B, int64_t ldb,
-                                                            double *C, int64_t ldc, const int64_t *info)
-{
-    constexpr int KC = 32;
-    __shared__ double As[KC][LEAF];
-    __shared__ double Bs[KC][LEAF];
-    if (info && *info != 0) return;
-    int64_t ti, tj;
-    if (LOWER) {
-        int64_t t = blockIdx.x;
-        ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-        while (ti * (ti + 1) / 2 > t) --ti;
-        tj = t - ti * (ti + 1) / 2;
-    } else {
-        ti = blockIdx.x;
-        tj = blockIdx.y;
-    }
-    const int64_t r0 = ti * LEAF, c0 = tj * LEAF;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    double acc[4][4] = {};
-    for (int k0 = 0; k0 < k; k0 += KC) {
-        for (int e = tid; e < KC * LEAF; e += blockDim.x) {
-            int r = e % LEAF, kk = e / LEAF;
-            bool kin = k0 + kk < k;
-            As[kk][r] = (kin && r0 + r < m) ? A[(r0 + r) + (int64_t)(k0 + kk) * lda] : 0.0;
-            Bs[kk][r] = (kin && c0 + r < nn) ? B[(c0 + r) + (int64_t)(k0 + kk) * ldb] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < KC; ++kk) {
-            double a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
-            if (r < m && c < nn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
-        }
-}
-
-constexpr size_t TRSM_SMEM = 2 * LEAF * LEAF * sizeof(double);
 constexpr size_t LEAF_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
-
-gpch_status launch_gemm(gpch_ctx *ctx, bool lower, int64_t m, int64_t nn, int k, const double *A,
-                        int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
-                        const int64_t *info, cudaStream_t st)
-{
-    if (m <= 0 || nn <= 0 || k <= 0) return GPCH_OK;
-    if (lower) {
-        int64_t T = (m + LEAF - 1) / LEAF;
-        gemm_nt_minus_kernel<true><<<(unsigned)(T * (T + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C,
-                                                                                  ldc, info);
-    } else {
-        dim3 grid((unsigned)((m + LEAF - 1) / LEAF), (unsigned)((nn + LEAF - 1) / LEAF));
-        gemm_nt_minus_kernel<false><<<grid, 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C, ldc, info);
-    }
-    GPCH_LAUNCH_CHECK(ctx);
-    return GPCH_OK;
-}
-
-gpch_status launch_trsm(gpch_ctx *ctx, double *B, int64_t ldb, int64_t m, int nc, const double *Linv,
-                        const int64_t *info, cudaStream_t st)
-{
-    if (m <= 0) return GPCH_OK;
-    trsm_inv_kernel<<<(unsigned)((m + LEAF - 1) / LEAF), 256, TRSM_SMEM, st>>>(B, ldb, m, nc, Linv, info);
-    GPCH_LAUNCH_CHECK(ctx);
-    return GPCH_OK;
-}
 
 }  // namespace
 
@@ -207,12 +81,10 @@ namespace gpch {
 // Linv: workspace of tile/64 * 64*64 doubles; info: device int64 (zeroed by
 // the caller).  Used by gpch_chol_factor and by the refined solve.
 gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *Linv,
-                              int64_t *info, cudaStream_t st)
+                              int64_t *info, cudaStream_t st, int64_t col_offset)
 {
     static bool attr_done = false;
     if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(trsm_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)TRSM_SMEM));
         GPCH_CUDA(ctx, cudaFuncSetAttribute(potrf_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)LEAF_SMEM));
         attr_done = true;
@@ -221,34 +93,42 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         double *Ajj = A + j0 + j0 * lda;
         // step 1: the diagonal tile, as a nest of 64-wide leaf steps
+        {
+        gpch::PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
         for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
             const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
             double *Lc = Linv + (c0 / LEAF) * LEAF * LEAF;
-            potrf_leaf_kernel<<<1, 256, LEAF_SMEM, st>>>(Ajj + c0 + c0 * lda, lda, nc, Lc, j0 + c0, info);
+            potrf_leaf_kernel<<<1, 256, LEAF_SMEM, st>>>(Ajj + c0 + c0 * lda, lda, nc, Lc, col_offset + j0 + c0,
+                                                         info);
             GPCH_LAUNCH_CHECK(ctx);
             const int64_t mr = nj - c0 - nc;
             if (mr > 0) {
                 double *P = Ajj + (c0 + nc) + c0 * lda;
-                GPCH_CHECK(launch_trsm(ctx, P, lda, mr, nc, Lc, info, st));
-                GPCH_CHECK(launch_gemm(ctx, true, mr, mr, nc, P, lda, P, lda, Ajj + (c0 + nc) * (1 + lda), lda,
+                GPCH_CHECK(launch_trsm<double>(ctx, P, lda, mr, nc, Lc, info, st));
+                GPCH_CHECK(launch_gemm<double>(ctx, true, mr, mr, nc, P, lda, P, lda, Ajj + (c0 + nc) * (1 + lda), lda,
                                        info, st));
             }
+        }
         }
         // step 2: panel below the tile, chunk by chunk
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         double *Pan = A + (j0 + nj) + j0 * lda;
+        {
+        gpch::PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
         for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
             const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
             double *Xc = Pan + c0 * lda;
-            GPCH_CHECK(launch_trsm(ctx, Xc, lda, m, nc, Linv + (c0 / LEAF) * LEAF * LEAF, info, st));
+            GPCH_CHECK(launch_trsm<double>(ctx, Xc, lda, m, nc, Linv + (c0 / LEAF) * LEAF * LEAF, info, st));
             const int64_t rest = nj - c0 - nc;
             if (rest > 0)
-                GPCH_CHECK(launch_gemm(ctx, false, m, rest, nc, Xc, lda, Ajj + (c0 + nc) + c0 * lda, lda,
+                GPCH_CHECK(launch_gemm<double>(ctx, false, m, rest, nc, Xc, lda, Ajj + (c0 + nc) + c0 * lda, lda,
                                        Pan + (c0 + nc) * lda, lda, info, st));
         }
+        }
         // step 3: trailing lower triangle, K = tile
-        GPCH_CHECK(launch_gemm(ctx, true, m, m, (int)nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda), lda,
+        gpch::PhaseScope ph3(ctx, GPCH_PHASE_TRAILING, st, (double)nj * m * (m + 1));
+        GPCH_CHECK(launch_gemm<double>(ctx, true, m, m, (int)nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda), lda,
                                info, st));
     }
     return GPCH_OK;
@@ -277,7 +157,7 @@ extern "C" gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, doub
     int64_t *d_info = cv.take<int64_t>(1);
     double *Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
     GPCH_CUDA(ctx, cudaMemsetAsync(d_info, 0, sizeof(int64_t), st));
-    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, Linv, d_info, st));
+    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, Linv, d_info, st, 0));
     int64_t *h = static_cast<int64_t *>(ctx->pinned);
     GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GPCH_CUDA(ctx, cudaStreamSynchronize(st));

@@ -6,8 +6,14 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "../../include/gpchol.h"
+
+struct gpch_timed_launch {
+    cudaEvent_t start, stop;
+    double work;
+};
 
 struct gpch_ctx {
     int device = 0;
@@ -17,6 +23,13 @@ struct gpch_ctx {
     void *pinned = nullptr;     // small pinned host block for flags / stats
     size_t pinned_bytes = 0;
     char err[512] = {0};
+    int64_t launches = 0;       // kernels launched through this context
+    bool timing = false;
+    std::vector<gpch_timed_launch> pending[GPCH_PHASE_COUNT];
+    std::vector<cudaEvent_t> event_pool;
+    double phase_ms[GPCH_PHASE_COUNT] = {0};
+    int64_t phase_launches[GPCH_PHASE_COUNT] = {0};
+    double phase_work[GPCH_PHASE_COUNT] = {0};
 };
 
 namespace gpch {
@@ -44,6 +57,35 @@ struct Carver {
 
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 
+cudaEvent_t take_event(gpch_ctx *ctx);
+
+// Records an event pair around the launches made while it is alive, when
+// timing is on; `work` is their algorithmic flops (or bytes).
+struct PhaseScope {
+    gpch_ctx *ctx;
+    int phase;
+    cudaStream_t st;
+    double work;
+    cudaEvent_t start = nullptr;
+    PhaseScope(gpch_ctx *c, int ph, cudaStream_t s, double w) : ctx(c), phase(ph), st(s), work(w)
+    {
+        if (ctx->timing) {
+            start = take_event(ctx);
+            if (start) cudaEventRecord(start, st);
+        }
+    }
+    ~PhaseScope()
+    {
+        if (start) {
+            cudaEvent_t stop = take_event(ctx);
+            if (stop) {
+                cudaEventRecord(stop, st);
+                ctx->pending[phase].push_back({start, stop, work});
+            }
+        }
+    }
+};
+
 }  // namespace gpch
 
 #define GPCH_CUDA(ctx, call)                                                        \
@@ -56,6 +98,7 @@ inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) 
 
 #define GPCH_LAUNCH_CHECK(ctx)                                                      \
     do {                                                                            \
+        ++(ctx)->launches;                                                          \
         cudaError_t e_ = cudaGetLastError();                                        \
         if (e_ != cudaSuccess)                                                      \
             return gpch::fail((ctx), GPCH_CUDA_ERROR, "kernel launch: %s (%s:%d)",  \

@@ -1,0 +1,420 @@
+// mixed.cu -- A8: the low-precision factor used as the preconditioner of the
+// refined solve.  Algorithm 1 (right) runs on an FP32 copy of the lower
+// triangle of A (+ shift * I):
+//   step 1  the diagonal tile is widened to FP64 and factored by the FP64
+//           nest (potrf leaf / inverse-apply TRSM / SYRK), then stored back
+//           in FP32;
+//   step 2  the panel solve runs in FP32 against the FP64 inverses of the
+//           64 x 64 diagonal blocks;
+//   step 3  the trailing update A_ik -= A_ij A_kj^T runs on the tensor cores:
+//           the panel is rounded to bf16 (or split into a bf16 head and a
+//           bf16 tail) in a K-major copy, TMA streams 128 x 64 tiles of it
+//           into shared memory, tcgen05.mma accumulates 128 x 128 FP32 tiles
+//           in TMEM, and the epilogue subtracts them from the FP32 matrix.
+// Mixed precision is the paper's stated future work (Sec. 5); the factor's
+// accuracy is recovered by the FP64 refinement in cg.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "dense_fp64.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+using gpch::LEAF;
+
+constexpr int BM = 128;            // rows of an output tile (TMEM lanes)
+constexpr int BN = 128;            // columns of an output tile (TMEM columns)
+constexpr int BK = 64;             // K per stage: one 128-byte swizzle row of bf16
+constexpr int STAGES = 3;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TILE_A_BYTES = BM * BK * 2;
+constexpr uint32_t TILE_B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr size_t TC_SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+// Trailing update C_lower -= P P^T on tensor cores.  P is the m x kp panel in
+// bf16, K-major (row i at P + i * kp), described by tm_hi (and its bf16
+// tail by tm_lo when split).  split = 0: one product head*head^T; split = 1:
+// head*head^T + head*tail^T + tail*head^T, run as one K loop of 3 * kp.
+// One CTA per lower 128 x 128 tile of C.  err: device status word (set to a
+// nonzero code if a bounded wait gives up).
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
+                   int kp, int split, float *C, int64_t ldc, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * TILE_A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accum = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t t = blockIdx.x;
+    int64_t ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int64_t tk = t - ti * (ti + 1) / 2;
+    const int64_t i0 = ti * BM, c0 = tk * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            gpch::tc::mbar_init(&full[s], 1);
+            gpch::tc::mbar_init(&empty[s], 1);
+        }
+        gpch::tc::mbar_init(accum, 1);
+        gpch::tc::fence_mbar_init();
+    }
+    if (warp == 1) gpch::tc::tmem_alloc<BN>(tmem_slot);
+    gpch::tc::tc_fence_before();
+    __syncthreads();
+    gpch::tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int nk1 = kp / BK;
+    const int NK = nk1 * (split ? 3 : 1);
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        gpch::tc::prefetch_tmap(&tm_hi);
+        if (split) gpch::tc::prefetch_tmap(&tm_lo);
+        for (int kc = 0; kc < NK; ++kc) {
+            const int s = kc % STAGES;
+            if (kc >= STAGES && !gpch::tc::mbar_wait(&empty[s], ((kc / STAGES) - 1) & 1, SPIN_LIMIT)) {
+                atomicExch(err, 1);
+                break;
+            }
+            const int prod = kc / nk1, kk = kc % nk1;
+            const CUtensorMap *ma = (prod == 2) ? &tm_lo : &tm_hi;
+            const CUtensorMap *mb = (prod == 1) ? &tm_lo : &tm_hi;
+            gpch::tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            gpch::tc::tma_load_2d(sA + s * TILE_A_BYTES, ma, &full[s], kk * BK, (int32_t)i0);
+            gpch::tc::tma_load_2d(sB + s * TILE_B_BYTES, mb, &full[s], kk * BK, (int32_t)c0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = gpch::tc::idesc_bf16_f32(BM, BN);
+        for (int kc = 0; kc < NK; ++kc) {
+            const int s = kc % STAGES;
+            if (!gpch::tc::mbar_wait(&full[s], (kc / STAGES) & 1, SPIN_LIMIT)) {
+                atomicExch(err, 2);
+                break;
+            }
+            gpch::tc::tc_fence_after();
+            const uint64_t ad = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sA + s * TILE_A_BYTES));
+            const uint64_t bd = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sB + s * TILE_B_BYTES));
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                gpch::tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kc | k) != 0 ? 1u : 0u);
+            gpch::tc::mma_commit(&empty[s]);
+        }
+        gpch::tc::mma_commit(accum);
+    }
+    __syncwarp();
+
+    // Epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
+    bool ok = gpch::tc::mbar_wait(accum, 0, 4 * SPIN_LIMIT);
+    ok = __all_sync(0xffffffffu, ok);
+    gpch::tc::tc_fence_after();
+    if (ok) {
+        const int64_t row = i0 + warp * 32 + lane;
+        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 16; ++cc) {
+            float v[16];
+            gpch::tc::tmem_ld16(tbase + cc * 16, v);
+            if (row < m) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = c0 + cc * 16 + j;
+                    if (col < m && col <= row) C[row + col * ldc] -= v[j];
+                }
+            }
+        }
+    } else if (lane == 0) {
+        atomicExch(err, 3);
+    }
+    gpch::tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        gpch::tc::tc_fence_after();
+        gpch::tc::tmem_dealloc<BN>(tmem);
+    }
+}
+
+// FP32 column-major panel (m x k, ld ldp) -> bf16 K-major head (and tail)
+// buffers of width kp (zero-padded beyond k).  64 x 64 tiles through shared
+// memory so that both the read and the write are coalesced.
+__global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restrict__ P, int64_t ldp, int64_t m,
+                                                            int k, int kp, __nv_bfloat16 *Hi, __nv_bfloat16 *Lo)
+{
+    __shared__ float tile[64][65];
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int k0 = blockIdx.y * 64;
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int r = e % 64, c = e / 64;
+        tile[r][c] = (r0 + r < m && k0 + c < k) ? P[(r0 + r) + (int64_t)(k0 + c) * ldp] : 0.0f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int c = e % 64, r = e / 64;
+        if (r0 + r < m && k0 + c < kp) {
+            const float v = tile[r][c];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            Hi[(r0 + r) * kp + k0 + c] = h;
+            if (Lo) Lo[(r0 + r) * kp + k0 + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// W (FP32, lower triangle) = A (FP64) + shift * I.
+__global__ void init_w_kernel(int64_t n, const double *__restrict__ A, int64_t lda, float *W, int64_t ldw,
+                              double shift)
+{
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
+        for (int64_t i = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            double v = A[i + j * lda];
+            if (i == j) v += shift;
+            W[i + j * ldw] = (float)v;
+        }
+}
+
+// Copy the nb x nb lower block between FP32 W and FP64 D (ld ldd).
+__global__ void tile_f32_to_f64(int64_t nb, const float *__restrict__ W, int64_t ldw, double *D, int64_t ldd)
+{
+    const int64_t j = blockIdx.y;
+    for (int64_t i = j + threadIdx.x; i < nb; i += blockDim.x) D[i + j * ldd] = (double)W[i + j * ldw];
+}
+
+__global__ void tile_f64_to_f32(int64_t nb, const double *__restrict__ D, int64_t ldd, float *W, int64_t ldw)
+{
+    const int64_t j = blockIdx.y;
+    for (int64_t i = j + threadIdx.x; i < nb; i += blockDim.x) W[i + j * ldw] = (float)D[i + j * ldd];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map over a K-major bf16 panel of m rows and kp columns (kp a
+// multiple of 64, so every TMA x coordinate is a multiple of 64 elements).
+gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int kp)
+{
+    auto enc = get_encode();
+    if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GPCH_OK;
+}
+
+struct LowprecBuffers {
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    int *err = nullptr;
+};
+
+// C_lower (m x m FP32) -= P P^T with P (m x k FP32) on tensor cores.
+gpch_status syrk_lowprec_enqueue(gpch_ctx *ctx, int64_t m, int k, const float *P, int64_t ldp, float *C,
+                                 int64_t ldc, int prec, const LowprecBuffers &buf, cudaStream_t st)
+{
+    if (m <= 0 || k <= 0) return GPCH_OK;
+    const int kp = (k + BK - 1) / BK * BK;
+    const bool split = prec == GPCH_PREC_SPLIT_BF16;
+    {
+        dim3 grid((unsigned)((m + 63) / 64), (unsigned)(kp / 64));
+        panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi, split ? buf.lo : nullptr);
+        GPCH_LAUNCH_CHECK(ctx);
+    }
+    CUtensorMap mhi, mlo;
+    GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, kp));
+    GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, kp));
+    static bool attr_done = false;
+    if (!attr_done) {
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        attr_done = true;
+    }
+    const int64_t T = (m + BM - 1) / BM;
+    const double work = 2.0 * (double)k * (double)m * (double)(m + 1) / 2.0 * (split ? 3.0 : 1.0);
+    gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
+    syrk_tc_kernel<<<(unsigned)(T * (T + 1) / 2), TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc,
+                                                                            buf.err);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+}  // namespace
+
+namespace gpch {
+
+// Workspace layout of the mixed factor for n, tile.
+struct MixedWs {
+    double *D, *Linv;
+    int64_t *info;
+    __nv_bfloat16 *hi, *lo;
+    int *err;
+};
+
+static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
+{
+    MixedWs w;
+    w.info = cv.take<int64_t>(1);
+    w.err = cv.take<int>(4);
+    w.D = cv.take<double>((size_t)tile * tile);
+    w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
+    w.hi = cv.take<__nv_bfloat16>((size_t)n * tile);
+    w.lo = cv.take<__nv_bfloat16>((size_t)n * tile);
+    return w;
+}
+
+size_t mixed_ws_bytes(int64_t n, int tile)
+{
+    Carver dry(nullptr);
+    carve_mixed(dry, n, tile);
+    return dry.off;
+}
+
+// Enqueue the low-precision factorization of W (FP32, n x n lower, ldw),
+// which already holds A + shift I.  info/err live in the workspace; the
+// caller reads them after the stream synchronizes.
+gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
+                                 int64_t **info_out, int **err_out, cudaStream_t st)
+{
+    Carver cv(wsbase);
+    MixedWs w = carve_mixed(cv, n, tile);
+    *info_out = w.info;
+    *err_out = w.err;
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.info, 0, sizeof(int64_t), st));
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), st));
+    LowprecBuffers buf{w.hi, w.lo, w.err};
+    for (int64_t j0 = 0; j0 < n; j0 += tile) {
+        const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
+        float *Wjj = W + j0 + j0 * ldw;
+        {
+            // step 1 in FP64
+            PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
+            tile_f32_to_f64<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, Wjj, ldw, w.D, tile);
+            GPCH_LAUNCH_CHECK(ctx);
+            GPCH_CHECK(chol_fp64_enqueue(ctx, nj, tile, w.D, tile, w.Linv, w.info, st, j0));
+            tile_f64_to_f32<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, w.D, tile, Wjj, ldw);
+            GPCH_LAUNCH_CHECK(ctx);
+        }
+        const int64_t m = n - j0 - nj;
+        if (m <= 0) continue;
+        float *Pan = W + (j0 + nj) + j0 * ldw;
+        {
+            // step 2 in FP32 against the FP64 inverses of the diagonal blocks
+            PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
+            for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
+                const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
+                float *Xc = Pan + c0 * ldw;
+                GPCH_CHECK(launch_trsm<float>(ctx, Xc, ldw, m, nc, w.Linv + (c0 / LEAF) * LEAF * LEAF, w.info, st));
+                const int64_t rest = nj - c0 - nc;
+                if (rest > 0)
+                    GPCH_CHECK(launch_gemm<float>(ctx, false, m, rest, nc, Xc, ldw, Wjj + (c0 + nc) + c0 * ldw, ldw,
+                                                  Pan + (c0 + nc) * ldw, ldw, w.info, st));
+            }
+        }
+        // step 3 on tensor cores
+        GPCH_CHECK(syrk_lowprec_enqueue(ctx, m, (int)nj, Pan, ldw, W + (j0 + nj) * (1 + ldw), ldw, prec, buf, st));
+    }
+    return GPCH_OK;
+}
+
+// W = A + shift I (FP32 lower triangle).
+gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
+                               double shift, cudaStream_t st)
+{
+    dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), (unsigned)(n < 65535 ? n : 65535));
+    init_w_kernel<<<grid, 256, 0, st>>>(n, A, lda, W, ldw, shift);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+}  // namespace gpch
+
+extern "C" gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, const float *P, int64_t ldp, float *C,
+                                         int64_t ldc, gpch_prec prec, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, m >= 0 && k >= 0 && k <= 4096, "need m >= 0 and 0 <= k <= 4096");
+    GPCH_ARG(ctx, ldp >= (m > 0 ? m : 1) && ldc >= (m > 0 ? m : 1), "ld < m");
+    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16, "prec must be BF16 or SPLIT_BF16");
+    GPCH_ARG(ctx, m < (int64_t)1 << 31, "m too large");
+    if (m == 0 || k == 0) return GPCH_OK;
+    GPCH_ARG(ctx, P && C, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int kp = (int)((k + BK - 1) / BK * BK);
+    gpch::Carver dry(nullptr);
+    dry.take<int>(4);
+    dry.take<__nv_bfloat16>((size_t)m * kp);
+    dry.take<__nv_bfloat16>((size_t)m * kp);
+    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
+    gpch::Carver cv(ctx->ws);
+    LowprecBuffers buf;
+    buf.err = cv.take<int>(4);
+    buf.hi = cv.take<__nv_bfloat16>((size_t)m * kp);
+    buf.lo = cv.take<__nv_bfloat16>((size_t)m * kp);
+    cudaStream_t st = (cudaStream_t)stream;
+    GPCH_CUDA(ctx, cudaMemsetAsync(buf.err, 0, 4 * sizeof(int), st));
+    GPCH_CHECK(syrk_lowprec_enqueue(ctx, m, (int)k, P, ldp, C, ldc, prec, buf, st));
+    int *h = static_cast<int *>(ctx->pinned);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h, buf.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+    if (*h != 0) return gpch::fail(ctx, GPCH_TIMEOUT, "tensor-core pipeline wait gave up (code %d)", *h);
+    return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_chol_factor_mixed(gpch_ctx *ctx, int64_t n, int tile, const double *A, int64_t lda,
+                                              gpch_prec prec, double shift, float *L, int64_t ldl, void *stream,
+                                              int64_t *info)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, info != nullptr, "info must not be NULL");
+    *info = 0;
+    GPCH_ARG(ctx, n >= 0 && lda >= (n > 0 ? n : 1) && ldl >= (n > 0 ? n : 1), "bad n / lda / ldl");
+    GPCH_ARG(ctx, tile >= LEAF && tile <= 1024 && tile % LEAF == 0, "tile must be a multiple of 64 in [64, 1024]");
+    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16, "prec must be BF16 or SPLIT_BF16");
+    GPCH_ARG(ctx, shift >= 0.0, "shift must be >= 0");
+    GPCH_ARG(ctx, n < (int64_t)1 << 31, "n too large");
+    if (n == 0) return GPCH_OK;
+    GPCH_ARG(ctx, A && L, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    GPCH_CHECK(gpch::ws_reserve(ctx, gpch::mixed_ws_bytes(n, tile)));
+    GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, L, ldl, shift, st));
+    int64_t *d_info;
+    int *d_err;
+    GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, L, ldl, (int)prec, ctx->ws, &d_info, &d_err, st));
+    int64_t *h = static_cast<int64_t *>(ctx->pinned);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h + 1, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+    const int e = (int)(reinterpret_cast<int *>(h + 1)[0]);
+    if (e != 0) return gpch::fail(ctx, GPCH_TIMEOUT, "tensor-core pipeline wait gave up (code %d)", e);
+    *info = h[0];
+    if (*info != 0) return gpch::fail(ctx, GPCH_NOT_SPD, "pivot %lld not positive", (long long)*info);
+    return GPCH_OK;
+}

@@ -69,6 +69,7 @@ extern "C" gpch_status gpch_se_matrix(gpch_ctx *ctx, int64_t n, int d, const dou
     int64_t T = (n + TS - 1) / TS;
     int64_t tiles = T * (T + 1) / 2;
     GPCH_ARG(ctx, tiles < (int64_t)0x7fffffff, "n too large");
+    gpch::PhaseScope ph(ctx, GPCH_PHASE_SE, (cudaStream_t)stream, 8.0 * (double)n * n);
     se_tile_kernel<<<(unsigned)tiles, 256, 0, (cudaStream_t)stream>>>(n, d, X, sf2, 1.0 / (2.0 * ell * ell),
                                                                        sn2, A, lda);
     GPCH_LAUNCH_CHECK(ctx);

@@ -14,7 +14,8 @@ namespace {
 
 using gpch::LEAF;
 
-__global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const double *__restrict__ L,
+template <typename TL>
+__global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const TL *__restrict__ L,
                                                               int64_t ldl, double *Linv)
 {
     extern __shared__ double inv_smem[];
@@ -26,7 +27,7 @@ __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const d
         int r = e % LEAF, c = e / LEAF;
         double v = 0.0;
         if (r < nb && c < nb) {
-            if (r >= c) v = L[(o + r) + (o + c) * ldl];
+            if (r >= c) v = (double)L[(o + r) + (o + c) * ldl];
         } else if (r == c) {
             v = 1.0;
         }
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const d
 // Forward step J.  W: working right-hand sides (rows > J updated here);
 // Y: output (rows of block J written by CTA 0).  Rows below the block are
 // split over CTAs, one row per thread.
-__global__ void __launch_bounds__(256) fwd_step_kernel(int64_t n, int64_t J, const double *__restrict__ L,
+template <typename TL>
+__global__ void __launch_bounds__(256) fwd_step_kernel(int64_t n, int64_t J, const TL *__restrict__ L,
                                                        int64_t ldl, const double *__restrict__ LinvJ,
                                                        double *W, int64_t ldw, double *Y, int64_t ldy,
                                                        int nrhs)
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(int64_t n, int64_t J, con
         __syncthreads();
         if (row < n) {
             double s = W[row + r * ldw];
-            for (int k = 0; k < nb; ++k) s = fma(-L[row + (o + k) * ldl], yj[k], s);
+            for (int k = 0; k < nb; ++k) s = fma(-(double)L[row + (o + k) * ldl], yj[k], s);
             W[row + r * ldw] = s;
         }
         __syncthreads();
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(int64_t n, int64_t J, con
 // Back step J.  W: working vectors (entries of blocks K < J updated here);
 // X: output (block J written by CTA 0).  Columns c < o are split over CTAs,
 // one warp per column, lanes over the 64 rows of block J.
-__global__ void __launch_bounds__(256) bwd_step_kernel(int64_t n, int64_t J, const double *__restrict__ L,
+template <typename TL>
+__global__ void __launch_bounds__(256) bwd_step_kernel(int64_t n, int64_t J, const TL *__restrict__ L,
                                                        int64_t ldl, const double *__restrict__ LinvJ,
                                                        double *W, int64_t ldw, double *X, int64_t ldx,
                                                        int nrhs)
@@ -104,8 +107,8 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(int64_t n, int64_t J, con
             const int64_t c = cbase + cc;
             if (c >= o) break;
             double s = 0.0;
-            if (lane < nb) s = L[(o + lane) + c * ldl] * xj[lane];
-            if (lane + 32 < nb) s = fma(L[(o + lane + 32) + c * ldl], xj[lane + 32], s);
+            if (lane < nb) s = (double)L[(o + lane) + c * ldl] * xj[lane];
+            if (lane + 32 < nb) s = fma((double)L[(o + lane + 32) + c * ldl], xj[lane + 32], s);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
             if (lane == 0) W[c + r * ldw] -= s;
@@ -119,15 +122,19 @@ __global__ void __launch_bounds__(256) bwd_step_kernel(int64_t n, int64_t J, con
 namespace gpch {
 
 // Enqueue the two sweeps on B (n x nrhs, in place).  Linv: n_blocks*64*64
-// doubles of workspace; Y: n x nrhs doubles of workspace (ld n).
-gpch_status chol_solve_enqueue(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb,
-                               int nrhs, double *Linv, double *Y, cudaStream_t st)
+// doubles of workspace; Y: n x nrhs doubles of workspace (ld n).  TL is the
+// storage type of L (FP64 factor, or the FP32 low-precision factor); the
+// arithmetic is FP64 either way.
+template <typename TL>
+gpch_status chol_solve_enqueue_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, double *B, int64_t ldb,
+                                 int nrhs, double *Linv, double *Y, cudaStream_t st)
 {
+    gpch::PhaseScope ph(ctx, GPCH_PHASE_SOLVE, st, 2.0 * (double)n * n * nrhs);
     const int64_t NBk = (n + LEAF - 1) / LEAF;
     constexpr size_t INV_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
     static bool attr_done = false;
     if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(inv_diag_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(inv_diag_blocks_kernel<TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)INV_SMEM));
         attr_done = true;
     }
@@ -146,6 +153,18 @@ gpch_status chol_solve_enqueue(gpch_ctx *ctx, int64_t n, const double *L, int64_
         GPCH_LAUNCH_CHECK(ctx);
     }
     return GPCH_OK;
+}
+
+gpch_status chol_solve_enqueue(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb,
+                               int nrhs, double *Linv, double *Y, cudaStream_t st)
+{
+    return chol_solve_enqueue_t<double>(ctx, n, L, ldl, B, ldb, nrhs, Linv, Y, st);
+}
+
+gpch_status chol_solve_enqueue_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, double *B, int64_t ldb,
+                                   int nrhs, double *Linv, double *Y, cudaStream_t st)
+{
+    return chol_solve_enqueue_t<float>(ctx, n, L, ldl, B, ldb, nrhs, Linv, Y, st);
 }
 
 }  // namespace gpch

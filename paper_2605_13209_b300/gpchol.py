@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libgpchol.so")
 
 GPCH_OK, GPCH_INVALID_ARG, GPCH_NOT_SPD, GPCH_NOT_CONVERGED, GPCH_OOM_BUDGET, GPCH_TIMEOUT, GPCH_CUDA_ERROR = range(7)
 GPCH_F64, GPCH_F32 = 0, 1
+(PHASE_SE, PHASE_DIAG, PHASE_PANEL, PHASE_TRAILING, PHASE_SOLVE, PHASE_CG_MATVEC, PHASE_CG_VECTOR,
+ PHASE_MIXED_TRAILING) = range(8)
 GPCH_PREC_FP64, GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 = 0, 1, 2
 
 _i64 = ctypes.c_int64
@@ -35,6 +37,11 @@ class GpchError(RuntimeError):
 
 class CGStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("relres_max", ctypes.c_double)]
+
+
+class RefineStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("factor_attempts", ctypes.c_int32), ("shift", ctypes.c_double),
+                ("backward_error_max", ctypes.c_double)]
 
 
 _lib = None
@@ -61,8 +68,18 @@ def lib() -> ctypes.CDLL:
         L.gpch_chol_solve.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_cg_solve.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int, _vp,
                                     ctypes.POINTER(CGStats)]
+        L.gpch_timing_enable.argtypes = [_vp, _int]
+        L.gpch_timing_read.argtypes = [_vp, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
+        L.gpch_launch_count.argtypes = [_vp]
+        L.gpch_launch_count.restype = _i64
+        L.gpch_syrk_lowprec.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _int, _vp]
+        L.gpch_chol_factor_mixed.argtypes = [_vp, _i64, _int, _vp, _i64, _int, _dbl, _vp, _i64, _vp,
+                                             ctypes.POINTER(_i64)]
+        L.gpch_solve_refined.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _int, _int, _dbl, _int,
+                                         _vp, ctypes.POINTER(RefineStats)]
         for name in ("gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
-                     "gpch_cg_solve"):
+                     "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
+                     "gpch_chol_factor_mixed", "gpch_solve_refined"):
             getattr(L, name).restype = _int
         _lib = L
     return _lib
@@ -125,6 +142,18 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(lib().gpch_workspace_bytes(self._h))
+
+    def timing_enable(self, on: bool = True):
+        self.check(lib().gpch_timing_enable(self._h, int(bool(on))))
+
+    def timing_read(self, phase: int):
+        """(total_ms, launches, work) of one phase since timing was enabled."""
+        ms, n, w = _dbl(0), _i64(0), _dbl(0)
+        self.check(lib().gpch_timing_read(self._h, int(phase), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+        return float(ms.value), int(n.value), float(w.value)
+
+    def launch_count(self) -> int:
+        return int(lib().gpch_launch_count(self._h))
 
     def close(self):
         if self._h:
@@ -215,3 +244,63 @@ def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e
     if st != GPCH_OK and not (st == GPCH_NOT_CONVERGED and not raise_on_not_converged):
         ctx.check(st)
     return CGResult(stats.iterations, stats.converged, stats.relres_max, st)
+
+
+_PREC = {"bf16": GPCH_PREC_BF16, "split_bf16": GPCH_PREC_SPLIT_BF16, GPCH_PREC_BF16: GPCH_PREC_BF16,
+         GPCH_PREC_SPLIT_BF16: GPCH_PREC_SPLIT_BF16}
+
+
+def syrk_lowprec(P: torch.Tensor, C: torch.Tensor, prec="bf16", ctx: Context | None = None,
+                 stream=None) -> torch.Tensor:
+    """A4 (mixed): C_lower -= P P^T on the tensor cores (bf16 or split bf16
+    products, FP32 accumulation).  P: m x k float32, C: m x m float32, both
+    column-major."""
+    ctx = ctx or default_context()
+    _check_cuda(P, torch.float32)
+    _check_cuda(C, torch.float32)
+    ctx.check(lib().gpch_syrk_lowprec(ctx.handle, P.shape[0], P.shape[1], P.data_ptr(), _ld(P), C.data_ptr(), _ld(C),
+                                      _PREC[prec], _stream(stream)))
+    return C
+
+
+def chol_factor_mixed(A: torch.Tensor, prec="bf16", tile: int = 512, shift: float = 0.0,
+                      L: torch.Tensor | None = None, ctx: Context | None = None, stream=None,
+                      raise_on_not_spd: bool = True):
+    """A8: low-precision factor (FP32 storage) of A + shift I.  Returns (L, info)."""
+    ctx = ctx or default_context()
+    _check_cuda(A, torch.float64)
+    n = A.shape[0]
+    if L is None:
+        L = colmajor(n, n, dtype=torch.float32, device=A.device)
+    info = _i64(0)
+    st = lib().gpch_chol_factor_mixed(ctx.handle, n, int(tile), A.data_ptr(), _ld(A), _PREC[prec], float(shift),
+                                      L.data_ptr(), _ld(L), _stream(stream), ctypes.byref(info))
+    if not (st == GPCH_NOT_SPD and not raise_on_not_spd):
+        ctx.check(st)
+    return L, int(info.value)
+
+
+@dataclass
+class RefineResult:
+    iterations: int
+    factor_attempts: int
+    shift: float
+    backward_error_max: float
+    status: int
+
+
+def solve_refined(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, prec="split_bf16", tile: int = 512,
+                  bwd_tol: float = 1e-12, maxit: int = 500, ctx: Context | None = None, stream=None,
+                  raise_on_error: bool = True) -> RefineResult:
+    """A8-A9: mixed-precision factor + FP64 PCG refinement to bwd_tol."""
+    ctx = ctx or default_context()
+    _check_cuda(A, torch.float64)
+    _check_cuda(B, torch.float64)
+    _check_cuda(X, torch.float64)
+    stats = RefineStats()
+    st = lib().gpch_solve_refined(ctx.handle, A.shape[0], A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), X.data_ptr(),
+                                  _ld(X), B.shape[1], _PREC[prec], int(tile), float(bwd_tol), int(maxit),
+                                  _stream(stream), ctypes.byref(stats))
+    if raise_on_error:
+        ctx.check(st)
+    return RefineResult(stats.iterations, stats.factor_attempts, stats.shift, stats.backward_error_max, st)
