@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // TMA producer
         gpch::tc::prefetch_tmap(&tm_hi);
         if (split) gpch::tc::prefetch_tmap(&tm_lo);
+        int issued = 0;
         for (int kc = 0; kc < NK; ++kc) {
             const int s = kc % STAGES;
             if (kc >= STAGES && !gpch::tc::mbar_wait(&empty[s], ((kc / STAGES) - 1) & 1, SPIN_LIMIT)) {
@@ -95,6 +96,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             gpch::tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
             gpch::tc::tma_load_2d(sA + s * TILE_A_BYTES, ma, &full[s], kk * BK, (int32_t)i0);
             gpch::tc::tma_load_2d(sB + s * TILE_B_BYTES, mb, &full[s], kk * BK, (int32_t)c0);
+            ++issued;
+        }
+        // Every copy this thread started has landed before the CTA may exit
+        // (immediate in normal operation: the MMA warp consumed them all).
+        for (int s = 0; s < STAGES && s < issued; ++s) {
+            const int uses = (issued - 1 - s) / STAGES + 1;
+            if (!gpch::tc::mbar_wait(&full[s], (uses - 1) & 1, SPIN_LIMIT)) atomicExch(err, 4);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
