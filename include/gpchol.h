@@ -186,6 +186,38 @@ gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A,
                           double rtol, int maxit, int replace_every,
                           void *stream, gpch_cg_stats *stats);
 
+/* ------------------------------------- allocation-free CG (no paper
+ * counterpart: the paper has no allocation-free variant; this is a
+ * service to callers of the library) */
+
+/* Largest n * nrhs gpch_cg_solve_noalloc accepts. */
+#define GPCH_NOALLOC_CG_MAX_ELEMS 262144
+
+/* The same conjugate-gradient solve as gpch_cg_solve, for callers that
+ * cannot allocate device memory: code that must not call cudaMalloc or
+ * cudaFree because it runs where the allocator is off limits (a host
+ * application or framework that owns the GPU's memory budget and forbids
+ * plugins from allocating, a real-time loop that cannot afford the
+ * allocator's implicit synchronization, or a caller without a context of
+ * this library, whose creation pins host memory).  It allocates nothing:
+ * its scratch (the CG vectors r, s, t, the device scalars and the partial
+ * sums) lives in one fixed 12 MiB file-scope device array that every GPU
+ * loading this library holds until the process exits, and its host
+ * staging is on the stack.  The caller still passes A, B and X.
+ *   - Runs on the caller's current device.  The first call on a device
+ *     looks up that array's device address (once per device); make that
+ *     first call before any stream capture.
+ *   - Limits: 0 <= nrhs <= 16 and n * nrhs <= GPCH_NOALLOC_CG_MAX_ELEMS;
+ *     larger problems return GPCH_INVALID_ARG.
+ *   - Every call shares the one array and leaves its contents behind; the
+ *     call clears what must start at zero.  Calls whose GPU work overlaps
+ *     (other streams, other host threads) race on the array: serialize them.
+ *   - Arguments, convergence rule and return codes as gpch_cg_solve; it
+ *     synchronizes `stream`.  No error message is kept (there is no context). */
+gpch_status gpch_cg_solve_noalloc(int64_t n, const void *A, gpch_dtype dtype, int64_t lda, const double *B,
+                                  int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol, int maxit,
+                                  int replace_every, void *stream, gpch_cg_stats *stats);
+
 /* --------------------------- A4 (mixed): tensor-core trailing update */
 
 /* C -= P P^T on the lower triangle of the m x m FP32 matrix C (ldc), with

@@ -17,6 +17,8 @@
 // j, which is contiguous in column-major storage.  A CTA owns W consecutive
 // columns and walks all rows; each thread keeps the s values of its rows in
 // registers and reuses them across the W columns and NR right-hand sides.
+#include <mutex>
+
 #include "dense_fp64.cuh"
 
 namespace {
@@ -286,12 +288,9 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
 
 inline int mv_width(int nrhs) { return nrhs <= 1 ? 16 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2; }
 
-template <typename TA>
-gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb,
-                     double *X, int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s,
-                     int *h_iters, double *h_relres)
+// Bytes of scratch one CG group of nrhs (<= 16) columns needs.
+size_t cg_scratch_bytes(int64_t n, int nrhs)
 {
-    const int64_t ldv = n;
     const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
     const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
@@ -301,8 +300,22 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
     dry.take<int>(2 * MAXRHS + 1);
     dry.take<unsigned>(2);
     dry.take<double>(max_ctas * MAXRHS);
-    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
-    gpch::Carver cv(ctx->ws);
+    return dry.off;
+}
+
+// One CG group on caller-provided scratch (cg_scratch_bytes(n, nrhs) bytes
+// of device memory at `scratch`) and a host staging block `hbuf` of at
+// least 64 + 4*16*8 + 33*4 bytes (pinned or pageable).
+template <typename TA>
+gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb, double *X,
+                   int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s, void *scratch, void *hbuf,
+                   int *h_iters, double *h_relres)
+{
+    const int64_t ldv = n;
+    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
+    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
+    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
+    gpch::Carver cv(scratch);
     double *Rv = cv.take<double>((size_t)n * nrhs);
     double *Sv = cv.take<double>((size_t)n * nrhs);
     double *Tv = cv.take<double>((size_t)n * nrhs);
@@ -326,7 +339,7 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
     cg_init_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, Sv, Tv, B, ldb, ldv, st);
     GPCH_LAUNCH_CHECK(ctx);
 
-    int *h_done = static_cast<int *>(ctx->pinned);
+    int *h_done = static_cast<int *>(hbuf);
     const double rtol2 = rtol * rtol;
     const int chunk = 16;
     int it = 0;
@@ -356,8 +369,8 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
         if (*h_done) break;
     }
     // statistics
-    double *h_sc = reinterpret_cast<double *>(static_cast<char *>(ctx->pinned) + 64);
-    int *h_ic = reinterpret_cast<int *>(static_cast<char *>(ctx->pinned) + 64 + 4 * MAXRHS * sizeof(double));
+    double *h_sc = reinterpret_cast<double *>(static_cast<char *>(hbuf) + 64);
+    int *h_ic = reinterpret_cast<int *>(static_cast<char *>(hbuf) + 64 + 4 * MAXRHS * sizeof(double));
     GPCH_CUDA(ctx, cudaMemcpyAsync(h_sc, sc, 4 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
     GPCH_CUDA(ctx, cudaMemcpyAsync(h_ic, ic, (2 * MAXRHS + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
     GPCH_CUDA(ctx, cudaStreamSynchronize(s));
@@ -367,6 +380,17 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
         h_relres[r] = u0 > 0.0 ? sqrt(u / u0) : 0.0;
     }
     return GPCH_OK;
+}
+
+// One CG group on the context's workspace arena and pinned block.
+template <typename TA>
+gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb,
+                     double *X, int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s,
+                     int *h_iters, double *h_relres)
+{
+    GPCH_CHECK(gpch::ws_reserve(ctx, cg_scratch_bytes(n, nrhs)));
+    return cg_run<TA>(ctx, n, A, lda, B, ldb, X, ldx, nrhs, rtol, maxit, R, s, ctx->ws, ctx->pinned, h_iters,
+                      h_relres);
 }
 
 // ------------------------------------------------------------ PCG (A9)
@@ -832,4 +856,84 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
         return gpch::fail(ctx, GPCH_NOT_CONVERGED, "refinement missed the backward error %.1e within %d iterations",
                           bwd_tol, maxit);
     return GPCH_OK;
+}
+
+// ------------------------------------------- allocation-free CG entry point
+
+namespace {
+
+// Scratch of gpch_cg_solve_noalloc: a fixed file-scope device array.  Every
+// GPU that loads this library holds it until the process exits.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(12) << 20;
+static __device__ __align__(256) unsigned char g_cg_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is asked
+// for once per device with that device current.
+gpch_status noalloc_scratch(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_cg_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return GPCH_CUDA_ERROR;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return GPCH_OK;
+}
+
+}  // namespace
+
+extern "C" gpch_status gpch_cg_solve_noalloc(int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
+                                             const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs,
+                                             double rtol, int maxit, int replace_every, void *stream,
+                                             gpch_cg_stats *stats)
+{
+    // Status plumbing only: this context owns no workspace and no pinned
+    // memory, and nothing in this call allocates.
+    thread_local gpch_ctx plumbing;
+    gpch_ctx *ctx = &plumbing;
+    if (stats) *stats = gpch_cg_stats{0, 0, 0.0};
+    GPCH_ARG(ctx, n >= 0 && nrhs >= 0 && nrhs <= MAXRHS, "need n >= 0 and 0 <= nrhs <= 16");
+    GPCH_ARG(ctx, n * (int64_t)nrhs <= GPCH_NOALLOC_CG_MAX_ELEMS, "n * nrhs exceeds GPCH_NOALLOC_CG_MAX_ELEMS");
+    GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
+    GPCH_ARG(ctx, dtype == GPCH_F64 || dtype == GPCH_F32, "bad dtype");
+    GPCH_ARG(ctx, maxit > 0 && replace_every >= 0 && rtol >= 0.0, "bad maxit / replace_every / rtol");
+    if (n == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, A && B && X, "null pointer");
+    GPCH_ARG(ctx, cg_scratch_bytes(n, nrhs) <= NOALLOC_SCRATCH_BYTES, "problem needs more than the fixed scratch");
+    int dev = 0;
+    GPCH_CUDA(ctx, cudaGetDevice(&dev));
+    GPCH_ARG(ctx, dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device ordinal out of range");
+    void *scratch = nullptr;
+    GPCH_CHECK(noalloc_scratch(dev, &scratch));
+    alignas(64) unsigned char hbuf[1024];   // host staging for a few scalars (pageable, on the stack)
+    int iters[MAXRHS];
+    double rel[MAXRHS];
+    cudaStream_t s = (cudaStream_t)stream;
+    gpch_status st;
+    if (dtype == GPCH_F64)
+        st = cg_run<double>(ctx, n, static_cast<const double *>(A), lda, B, ldb, X, ldx, nrhs, rtol, maxit,
+                            replace_every, s, scratch, hbuf, iters, rel);
+    else
+        st = cg_run<float>(ctx, n, static_cast<const float *>(A), lda, B, ldb, X, ldx, nrhs, rtol, maxit,
+                           replace_every, s, scratch, hbuf, iters, rel);
+    if (st != GPCH_OK) return st;
+    int max_it = 0, conv = 0;
+    double rel_max = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+        if (iters[r] > max_it) max_it = iters[r];
+        if (rel[r] > rel_max) rel_max = rel[r];
+        if (rel[r] <= rtol) ++conv;
+    }
+    if (stats) *stats = gpch_cg_stats{max_it, conv, rel_max};
+    return conv < nrhs ? GPCH_NOT_CONVERGED : GPCH_OK;
 }

@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
         L.gpch_timing_read.argtypes = [_vp, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
         L.gpch_launch_count.argtypes = [_vp]
         L.gpch_launch_count.restype = _i64
+        L.gpch_cg_solve_noalloc.argtypes = [_i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int,
+                                             _vp, ctypes.POINTER(CGStats)]
         L.gpch_syrk_lowprec.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_chol_factor_mixed.argtypes = [_vp, _i64, _int, _vp, _i64, _int, _dbl, _vp, _i64, _vp,
                                              ctypes.POINTER(_i64)]
@@ -79,7 +81,7 @@ def lib() -> ctypes.CDLL:
                                          _vp, ctypes.POINTER(RefineStats)]
         for name in ("gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
-                     "gpch_chol_factor_mixed", "gpch_solve_refined"):
+                     "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc"):
             getattr(L, name).restype = _int
         _lib = L
     return _lib
@@ -243,6 +245,26 @@ def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e
                              ctypes.byref(stats))
     if st != GPCH_OK and not (st == GPCH_NOT_CONVERGED and not raise_on_not_converged):
         ctx.check(st)
+    return CGResult(stats.iterations, stats.converged, stats.relres_max, st)
+
+
+def cg_solve_noalloc(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e-10, maxit: int = 10000,
+                     replace_every: int = 50, stream=None) -> CGResult:
+    """gpch_cg_solve_noalloc: the CG solve without any device allocation
+    (fixed library-owned scratch; n * nrhs <= 262144, nrhs <= 16).  Runs on
+    the current CUDA device; no context is involved."""
+    if A.dtype not in (torch.float64, torch.float32):
+        raise ValueError("A must be float64 or float32")
+    _check_cuda(A, A.dtype)
+    _check_cuda(B, torch.float64)
+    _check_cuda(X, torch.float64)
+    stats = CGStats()
+    dt = GPCH_F64 if A.dtype == torch.float64 else GPCH_F32
+    st = lib().gpch_cg_solve_noalloc(A.shape[0], A.data_ptr(), dt, _ld(A), B.data_ptr(), _ld(B), X.data_ptr(),
+                                     _ld(X), B.shape[1], rtol, int(maxit), int(replace_every), _stream(stream),
+                                     ctypes.byref(stats))
+    if st not in (GPCH_OK, GPCH_NOT_CONVERGED):
+        raise GpchError(st, "gpch_cg_solve_noalloc failed")
     return CGResult(stats.iterations, stats.converged, stats.relres_max, st)
 
 
