@@ -138,7 +138,7 @@ gpch_status gpch_se_matrix(gpch_ctx *ctx, int64_t n, int d, const double *X,
  *   step 3  A_ik -= A_ij A_kj^T, j < k <= i   (SYRK on k == i, GEMM below)
  * A: device, n x n, lda >= n; on return its lower triangle holds L with
  * L L^T = A (Sec. 2.2).  The strict upper triangle is not touched.
- * tile: 64..1024, multiple of 64 (the paper's block size, Sec. 4.3).
+ * tile: 64..1024, multiple of 64 (the paper's block size, Sec. 4.4).
  * info (host): 0 on success, else the 1-based column whose pivot was not
  * positive (LAPACK convention); the call then returns GPCH_NOT_SPD and the
  * lower triangle holds a partial factor.  Synchronizes `stream`.
