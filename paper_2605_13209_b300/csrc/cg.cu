@@ -594,14 +594,13 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
     const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
-    const int64_t NBk = (n + 63) / 64;
     gpch::Carver cv(wsbase);
     double *Rv = cv.take<double>((size_t)n * nrhs);
     double *Zv = cv.take<double>((size_t)n * nrhs);
     double *Sv = cv.take<double>((size_t)n * nrhs);
     double *Tv = cv.take<double>((size_t)n * nrhs);
-    double *Yv = cv.take<double>((size_t)n * nrhs);
-    double *Linv = cv.take<double>((size_t)NBk * 64 * 64);
+    char *solve_base = cv.take<char>(gpch::solve_ws_bytes(n, nrhs));
+    gpch::SolveWs sw = gpch::carve_solve(solve_base, n, nrhs);
     CGState st;
     double *sc = cv.take<double>(4 * MAXRHS);
     st.u = sc;
@@ -640,8 +639,9 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     GPCH_LAUNCH_CHECK(ctx);
     pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Rv, ldv, st, d_bb, 0);
     GPCH_LAUNCH_CHECK(ctx);
+    GPCH_CHECK(gpch::solve_prepare_f32(ctx, n, L, ldl, sw, s));
     GPCH_CUDA(ctx, cudaMemcpyAsync(Zv, Rv, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    GPCH_CHECK(gpch::chol_solve_enqueue_f32(ctx, n, L, ldl, Zv, ldv, nrhs, Linv, Yv, s));
+    GPCH_CHECK(gpch::solve_apply_f32(ctx, n, L, ldl, Zv, ldv, nrhs, sw, s));
     GPCH_CUDA(ctx, cudaMemcpyAsync(Sv, Zv, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
     pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Zv, ldv, st, d_dots, 1);
     GPCH_LAUNCH_CHECK(ctx);
@@ -692,13 +692,17 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
             if (nactive == 0) break;
         }
         GPCH_CUDA(ctx, cudaMemcpyAsync(Zv, Rv, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        GPCH_CHECK(gpch::chol_solve_enqueue_f32(ctx, n, L, ldl, Zv, ldv, nrhs, Linv, Yv, s));
+        GPCH_CHECK(gpch::solve_apply_f32(ctx, n, L, ldl, Zv, ldv, nrhs, sw, s));
         pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Zv, ldv, st, d_dots, 2);
         GPCH_LAUNCH_CHECK(ctx);
         cg_dir_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Zv, Sv, ldv, st);
         GPCH_LAUNCH_CHECK(ctx);
     }
     res.iterations = it;
+    int *h_err = reinterpret_cast<int *>(h_active + MAXRHS);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h_err, sw.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+    if (*h_err != 0) return gpch::fail(ctx, GPCH_TIMEOUT, "substitution sweep wait gave up");
     return GPCH_OK;
 }
 
@@ -708,8 +712,8 @@ size_t pcg_ws_bytes(int64_t n, int nrhs)
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
     const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
     gpch::Carver dry(nullptr);
-    for (int i = 0; i < 5; ++i) dry.take<double>((size_t)n * nrhs);
-    dry.take<double>((size_t)((n + 63) / 64) * 64 * 64);
+    for (int i = 0; i < 4; ++i) dry.take<double>((size_t)n * nrhs);
+    dry.take<char>(gpch::solve_ws_bytes(n, nrhs));
     dry.take<double>(4 * MAXRHS);
     dry.take<int>(2 * MAXRHS + 1);
     dry.take<unsigned>(2);

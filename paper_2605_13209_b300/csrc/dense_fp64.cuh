@@ -15,29 +15,57 @@ namespace gpch {
 
 constexpr int LEAF = 64;
 
-// Inverse of the unit-padded lower-triangular 64 x 64 block S (S[r][c],
-// row r, column c) into Vi (same layout), by forward substitution on the
-// columns of the identity: Vi[c][c] = 1/S[c][c],
-// Vi[i][c] = -(sum_{k=c}^{i-1} S[i][k] Vi[k][c]) / S[i][i] for i > c.
-// 256 threads: four lanes share one column and split the sum over k.
-// Entries above the diagonal are set to zero.
+// Inverse X = L^-1 of the unit-padded lower-triangular 64 x 64 block S
+// (S[r][c], row r, column c; 256 threads) into Vi (same layout), by forward
+// substitution on all columns of the identity at once: row j of X is final
+// once scaled by 1/L_jj, and is then eliminated from every row below it,
+// X[r][c] -= L[r][j] X[j][c].  Thread (tx, ty) keeps X entries
+// (tx + 16i, ty + 16jj) in registers; the finished row j goes through a
+// double-buffered shared row so one barrier per step suffices.  Entries
+// above the diagonal are zero.
 __device__ inline void invert_lower_64(const double (*S)[LEAF + 1], double (*Vi)[LEAF + 1])
 {
-    const int tid = threadIdx.x;
-    const int c = tid >> 2, q = tid & 3;
-    for (int i = 0; i < LEAF; ++i) {
-        double part = 0.0;
-        if (i > c)
-            for (int k = c + q; k < i; k += 4) part = fma(S[i][k], Vi[k][c], part);
-        part += __shfl_xor_sync(0xffffffffu, part, 1);
-        part += __shfl_xor_sync(0xffffffffu, part, 2);
-        if (q == 0) {
-            if (i < c) Vi[i][c] = 0.0;
-            else if (i == c) Vi[c][c] = 1.0 / S[c][c];
-            else Vi[i][c] = -part / S[i][i];
+    __shared__ double dinv[LEAF];
+    __shared__ double xrow[2][LEAF];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    double x[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) x[i][jj] = (tx + 16 * i == ty + 16 * jj) ? 1.0 : 0.0;
+    if (tid < LEAF) dinv[tid] = 1.0 / S[tid][tid];
+    __syncthreads();
+    for (int j = 0; j < LEAF; ++j) {
+        double *xr = xrow[j & 1];
+        if (tx == j % 16) {
+            const int i = j / 16;
+            const double d = dinv[j];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int c = ty + 16 * jj;
+                if (c <= j) {
+                    x[i][jj] *= d;
+                    xr[c] = x[i][jj];
+                }
+            }
         }
-        __syncwarp();
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = tx + 16 * i;
+            if (r <= j) continue;
+            const double l = S[r][j];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int c = ty + 16 * jj;
+                if (c <= j) x[i][jj] -= l * xr[c];
+            }
+        }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) Vi[tx + 16 * i][ty + 16 * jj] = x[i][jj];
 }
 
 }  // namespace gpch
@@ -50,58 +78,56 @@ using gpch::LEAF;
 
 // Panel leaf solve: X = B inv(L)^T in place on the m x nc panel B (nc <=
 // 64), inv(L) given as a 64 x 64 FP64 block (column-major, ld 64).  Every
-// CTA owns 64 whole rows, so reading B and writing X never overlap across
-// CTAs.  T is the storage and arithmetic type of B.
-template <typename T>
+// CTA owns ROWS whole rows, so reading B and writing X never overlap across
+// CTAs.  T is the storage and arithmetic type of B.  Thread t owns row
+// t % ROWS and every (256/ROWS)-th column from t / ROWS.
+template <typename T, int ROWS>
 __global__ void __launch_bounds__(256) trsm_inv_kernel(T *B, int64_t ldb, int64_t m, int nc,
                                                        const double *__restrict__ Linv, const int64_t *info)
 {
+    constexpr int G = 256 / ROWS, NC = LEAF / G;
     extern __shared__ __align__(16) unsigned char trsm_smem[];
-    T *Bs = reinterpret_cast<T *>(trsm_smem);   // Bs[k * 64 + r]
-    T *Ls = Bs + LEAF * LEAF;                   // Ls[k * 64 + c] = inv(L)[c][k]
+    T *Bs = reinterpret_cast<T *>(trsm_smem);   // Bs[k * ROWS + r]
+    T *Ls = Bs + LEAF * ROWS;                   // Ls[k * 64 + c] = inv(L)[c][k]
     if (info && *info != 0) return;
     const int tid = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * LEAF;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS;
+    for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
+        const int r = e % ROWS, k = e / ROWS;
+        Bs[k * ROWS + r] = (r0 + r < m && k < nc) ? B[(r0 + r) + k * ldb] : T(0);
+    }
     for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
-        int r = e % LEAF, k = e / LEAF;
-        Bs[k * LEAF + r] = (r0 + r < m && k < nc) ? B[(r0 + r) + k * ldb] : T(0);
-        Ls[k * LEAF + r] = (T)Linv[r + k * LEAF];
+        const int c = e % LEAF, k = e / LEAF;
+        Ls[k * LEAF + c] = (T)Linv[c + k * LEAF];
     }
     __syncthreads();
-    const int tx = tid % 16, ty = tid / 16;
-    T acc[4][4] = {};
+    const int r = tid % ROWS, g = tid / ROWS;
+    T acc[NC] = {};
     for (int k = 0; k < LEAF; ++k) {
-        T a[4], b[4];
+        const T b = Bs[k * ROWS + r];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = Bs[k * LEAF + tx + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Ls[k * LEAF + ty + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int u = 0; u < NC; ++u) acc[u] = fma(b, Ls[k * LEAF + g + G * u], acc[u]);
     }
+    if (r0 + r < m)
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t r = r0 + tx + 16 * i;
-            int c = ty + 16 * j;
-            if (r < m && c < nc) B[r + c * ldb] = acc[i][j];
+        for (int u = 0; u < NC; ++u) {
+            const int c = g + G * u;
+            if (c < nc) B[(r0 + r) + c * ldb] = acc[u];
         }
 }
 
 // C[m x nn] -= A[m x k] B[nn x k]^T.  LOWER: C is square and only its lower
-// triangle is updated; the grid enumerates the lower 64 x 64 tiles.
-template <typename T, bool LOWER>
+// triangle is updated; the grid enumerates the lower BT x BT tiles.  Thread
+// (tx, ty) owns entries (tx + 16i, ty + 16j) of the tile.
+template <typename T, bool LOWER, int BT>
 __global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
                                                                const T *__restrict__ A, int64_t lda,
                                                                const T *__restrict__ B, int64_t ldb, T *C,
                                                                int64_t ldc, const int64_t *info)
 {
-    constexpr int KC = 32;
-    __shared__ T As[KC][LEAF];
-    __shared__ T Bs[KC][LEAF];
+    constexpr int KC = 32, RT = BT / 16;
+    __shared__ T As[KC][BT];
+    __shared__ T Bs[KC][BT];
     if (info && *info != 0) return;
     int64_t ti, tj;
     if (LOWER) {
@@ -114,12 +140,12 @@ __global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_
         ti = blockIdx.x;
         tj = blockIdx.y;
     }
-    const int64_t r0 = ti * LEAF, c0 = tj * LEAF;
+    const int64_t r0 = ti * BT, c0 = tj * BT;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    T acc[4][4] = {};
+    T acc[RT][RT] = {};
     for (int k0 = 0; k0 < k; k0 += KC) {
-        for (int e = tid; e < KC * LEAF; e += blockDim.x) {
-            int r = e % LEAF, kk = e / LEAF;
+        for (int e = tid; e < KC * BT; e += blockDim.x) {
+            int r = e % BT, kk = e / BT;
             bool kin = k0 + kk < k;
             As[kk][r] = (kin && r0 + r < m) ? A[(r0 + r) + (int64_t)(k0 + kk) * lda] : T(0);
             Bs[kk][r] = (kin && c0 + r < nn) ? B[(c0 + r) + (int64_t)(k0 + kk) * ldb] : T(0);
@@ -127,46 +153,78 @@ __global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < KC; ++kk) {
-            T a[4], b[4];
+            T a[RT], b[RT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < RT; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+            for (int j = 0; j < RT; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < RT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RT; ++j) {
             int64_t r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
             if (r < m && c < nn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
         }
 }
 
-template <typename T>
+template <typename T, int ROWS>
 constexpr size_t trsm_smem_bytes()
 {
-    return 2 * LEAF * LEAF * sizeof(T);
+    return (size_t)(LEAF * ROWS + LEAF * LEAF) * sizeof(T);
 }
+
+// Below this many 64 x 64 tiles (two per SM) the small-tile variants are
+// used, so that small in-tile steps still spread over the whole GPU.
+constexpr int64_t SMALL_GRID = 296;
 
 template <typename T>
 inline gpch_status launch_gemm(gpch_ctx *ctx, bool lower, int64_t m, int64_t nn, int k, const T *A, int64_t lda,
                                const T *B, int64_t ldb, T *C, int64_t ldc, const int64_t *info, cudaStream_t st)
 {
     if (m <= 0 || nn <= 0 || k <= 0) return GPCH_OK;
+    const int64_t tm = (m + LEAF - 1) / LEAF, tn = (nn + LEAF - 1) / LEAF;
+    const bool small = (lower ? tm * (tm + 1) / 2 : tm * tn) < SMALL_GRID;
     if (lower) {
-        int64_t Tn = (m + LEAF - 1) / LEAF;
-        gemm_nt_minus_kernel<T, true><<<(unsigned)(Tn * (Tn + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C,
-                                                                                      ldc, info);
+        if (small) {
+            const int64_t Tn = (m + 31) / 32;
+            gemm_nt_minus_kernel<T, true, 32><<<(unsigned)(Tn * (Tn + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb,
+                                                                                           C, ldc, info);
+        } else {
+            gemm_nt_minus_kernel<T, true, 64><<<(unsigned)(tm * (tm + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb,
+                                                                                           C, ldc, info);
+        }
     } else {
-        dim3 grid((unsigned)((m + LEAF - 1) / LEAF), (unsigned)((nn + LEAF - 1) / LEAF));
-        gemm_nt_minus_kernel<T, false><<<grid, 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C, ldc, info);
+        if (small) {
+            dim3 grid((unsigned)((m + 31) / 32), (unsigned)((nn + 31) / 32));
+            gemm_nt_minus_kernel<T, false, 32><<<grid, 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C, ldc, info);
+        } else {
+            dim3 grid((unsigned)tm, (unsigned)tn);
+            gemm_nt_minus_kernel<T, false, 64><<<grid, 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C, ldc, info);
+        }
     }
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+template <typename T, int ROWS>
+inline gpch_status launch_trsm_rows(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int nc, const double *Linv,
+                                    const int64_t *info, cudaStream_t st)
+{
+    static bool attr_done = false;
+    if (!attr_done) {
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(trsm_inv_kernel<T, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)trsm_smem_bytes<T, ROWS>()));
+        attr_done = true;
+    }
+    trsm_inv_kernel<T, ROWS><<<(unsigned)((m + ROWS - 1) / ROWS), 256, trsm_smem_bytes<T, ROWS>(), st>>>(
+        B, ldb, m, nc, Linv, info);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -176,16 +234,8 @@ inline gpch_status launch_trsm(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int 
                                const int64_t *info, cudaStream_t st)
 {
     if (m <= 0) return GPCH_OK;
-    static bool attr_done = false;
-    if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(trsm_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)trsm_smem_bytes<T>()));
-        attr_done = true;
-    }
-    trsm_inv_kernel<T><<<(unsigned)((m + LEAF - 1) / LEAF), 256, trsm_smem_bytes<T>(), st>>>(B, ldb, m, nc, Linv,
-                                                                                          info);
-    GPCH_LAUNCH_CHECK(ctx);
-    return GPCH_OK;
+    if ((m + LEAF - 1) / LEAF < SMALL_GRID) return launch_trsm_rows<T, 16>(ctx, B, ldb, m, nc, Linv, info, st);
+    return launch_trsm_rows<T, 64>(ctx, B, ldb, m, nc, Linv, info, st);
 }
 
 }  // namespace
@@ -197,12 +247,25 @@ namespace gpch {
 gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *Linv,
                               int64_t *info, cudaStream_t st, int64_t col_offset);
 
-// Enqueue L L^T X = B (solve.cu); Linv (n_blocks*64*64 doubles) and Y
-// (n*nrhs doubles) are workspace.  The _f32 form takes an FP32 factor.
-gpch_status chol_solve_enqueue(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb,
-                               int nrhs, double *Linv, double *Y, cudaStream_t st);
-gpch_status chol_solve_enqueue_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, double *B, int64_t ldb,
-                                   int nrhs, double *Linv, double *Y, cudaStream_t st);
+// Forward/back substitution (solve.cu).  SolveWs is carved from
+// solve_ws_bytes(n, nrhs) bytes of workspace; solve_prepare inverts the
+// diagonal blocks of L once per factor, solve_apply then overwrites B
+// (n x nrhs) with (L L^T)^-1 B.  The _f32 forms take an FP32 factor.
+struct SolveWs {
+    double *Linv;
+    double *Y;
+    unsigned *flags;
+    int *err;
+    unsigned epoch;
+};
+size_t solve_ws_bytes(int64_t n, int nrhs);
+SolveWs carve_solve(void *base, int64_t n, int nrhs);
+gpch_status solve_prepare(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, SolveWs &w, cudaStream_t st);
+gpch_status solve_prepare_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, SolveWs &w, cudaStream_t st);
+gpch_status solve_apply(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb, int nrhs,
+                        SolveWs &w, cudaStream_t st);
+gpch_status solve_apply_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, double *B, int64_t ldb, int nrhs,
+                            SolveWs &w, cudaStream_t st);
 
 // Low-precision factor (mixed.cu): workspace size, W = A + shift I, and the
 // factorization of W in place (info / err device words returned).

@@ -43,7 +43,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // nonzero code if a bounded wait gives up).
 __global__ void __launch_bounds__(TC_THREADS, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
-                   int kp, int split, float *C, int64_t ldc, int *err)
+                   int kp, int split, float *__restrict__ C, int64_t ldc, int *err)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -125,23 +125,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     __syncwarp();
 
-    // Epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
+    // Epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31; lane l
+    // holds row i0 + 32w + l.  Columns go in chunks of 32: all 32 loads of
+    // a chunk are in flight before any store, and the first chunk is
+    // loaded while the MMAs are still running.
+    const int64_t row = i0 + warp * 32 + lane;
+    const bool row_ok = row < m;
+    float cv[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int64_t col = c0 + j;
+        cv[j] = (row_ok && col < m && col <= row) ? C[row + col * ldc] : 0.0f;
+    }
     bool ok = gpch::tc::mbar_wait(accum, 0, 4 * SPIN_LIMIT);
     ok = __all_sync(0xffffffffu, ok);
     gpch::tc::tc_fence_after();
     if (ok) {
-        const int64_t row = i0 + warp * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-        for (int cc = 0; cc < BN / 16; ++cc) {
-            float v[16];
-            gpch::tc::tmem_ld16(tbase + cc * 16, v);
-            if (row < m) {
+        for (int cc = 0; cc < BN / 32; ++cc) {
+            if (cc > 0) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t col = c0 + cc * 16 + j;
-                    if (col < m && col <= row) C[row + col * ldc] -= v[j];
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t col = c0 + cc * 32 + j;
+                    cv[j] = (row_ok && col < m && col <= row) ? C[row + col * ldc] : 0.0f;
                 }
+            }
+            float v[32];
+            gpch::tc::tmem_ld32(tbase + cc * 32, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t col = c0 + cc * 32 + j;
+                if (row_ok && col < m && col <= row) C[row + col * ldc] = cv[j] - v[j];
             }
         }
     } else if (lane == 0) {

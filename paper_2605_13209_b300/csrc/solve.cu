@@ -1,18 +1,30 @@
 // solve.cu -- A5: forward and back substitution with the Cholesky factor,
-// L Y = B then L^T X = Y (Sec. 2.2), FP64, blocked by 64.
+// L Y = B then L^T X = Y (Sec. 2.2), blocked by 64 rows.
 //
-// All 64 x 64 diagonal blocks of L are inverted first, in one launch.  Each
-// sweep then takes one launch per block row:
-//   forward, block J:  y_J = inv(L_JJ) b_J;  b_I -= L_IJ y_J  for I > J
-//   back,    block J:  x_J = inv(L_JJ)^T w_J;  w_K -= L_JK^T x_J  for K < J
-// Every CTA of a step recomputes the 64-entry y_J (x_J) itself, so no
-// launch waits on another CTA; the step's output goes to a second buffer so
-// that no CTA reads what another CTA of the same launch writes.
+// The 64 x 64 diagonal blocks of L are inverted once (one launch).  Each
+// sweep is then ONE cooperative launch of one CTA per SM.  Block row I is
+// owned by CTA I mod P and its partial sums live in the output rows of I.
+// Walking the blocks in sweep order, every CTA waits for the solved block J
+// (a flag word per block, bounded wait), adds L_IJ y_J (forward) or
+// L_JI^T x_J (back) to each block I it owns further down the sweep, and the
+// owner of the next block does that block first, solves it with its
+// inverted diagonal block and publishes it before touching its other
+// blocks, so the serial chain is one 64 x 64 update and one 64 x 64 solve
+// per block.  L is read once per sweep.  With an FP64 factor all products
+// are FP64; with the FP32 (preconditioner) factor each 64 x 64 block
+// product runs in FP32 and is added to FP64 partial sums, and the diagonal
+// block solves stay FP64.
+#include <type_traits>
+
 #include "dense_fp64.cuh"
 
 namespace {
 
 using gpch::LEAF;
+
+constexpr int SW_THREADS = 256;
+constexpr int SW_MAXRHS = 16;
+constexpr uint32_t FLAG_SPIN_LIMIT = 1u << 22;
 
 template <typename TL>
 __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const TL *__restrict__ L,
@@ -43,94 +55,344 @@ __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const T
     }
 }
 
-// Forward step J.  W: working right-hand sides (rows > J updated here);
-// Y: output (rows of block J written by CTA 0).  Rows below the block are
-// split over CTAs, one row per thread.
-template <typename TL>
-__global__ void __launch_bounds__(256) fwd_step_kernel(int64_t n, int64_t J, const TL *__restrict__ L,
-                                                       int64_t ldl, const double *__restrict__ LinvJ,
-                                                       double *W, int64_t ldw, double *Y, int64_t ldy,
-                                                       int nrhs)
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
-    __shared__ double bj[LEAF];
-    __shared__ double yj[LEAF];
-    const int tid = threadIdx.x;
-    const int64_t o = J * LEAF;
-    const int nb = (int)((n - o < LEAF) ? n - o : LEAF);
-    const int64_t row = o + nb + (int64_t)blockIdx.x * blockDim.x + tid;
-    for (int r = 0; r < nrhs; ++r) {
-        if (tid < LEAF) bj[tid] = (tid < nb) ? W[o + tid + r * ldw] : 0.0;
-        __syncthreads();
-        if (tid < LEAF) {
-            double s = 0.0;
-            for (int k = 0; k <= tid; ++k) s = fma(LinvJ[tid + k * LEAF], bj[k], s);
-            yj[tid] = s;
-            if (blockIdx.x == 0 && tid < nb) Y[o + tid + r * ldy] = s;
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int bytes)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr int SW_SLOTS = 4;   // 64 x 64 blocks of L staged per step
+
+template <typename TL>
+constexpr size_t sweep_smem_bytes()
+{
+    return (size_t)(2 + 4 + 2) * LEAF * SW_MAXRHS * sizeof(double) + (size_t)SW_SLOTS * LEAF * LEAF * sizeof(TL) +
+           (size_t)LEAF * LEAF * sizeof(double);
+}
+
+// One sweep.  FWD: Y = L^-1 B.  BWD: Y = L^-T B.  Y (n x nrhs, ldy) is
+// the output and, until a block is solved, its partial sums.  flags[J] ==
+// epoch marks block J solved.  nrhs <= 16.
+//
+// Per step J every CTA first starts copying into shared memory what it
+// will need (its blocks of L for this step; for the owner of the next
+// block also that block's inverse, right-hand side and partial sums), then
+// waits for block J.  The owner of the next block adds block J's
+// contribution to the staged partial sums in shared memory, solves the
+// block and publishes it before doing its other updates, so the serial
+// chain per block is: flag seen -> y_J read -> one 64 x 64 block product ->
+// one 64 x 64 inverse-block product -> publish.
+template <typename TL, bool FWD>
+__global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int nrhs, const TL *__restrict__ L,
+                                                                int64_t ldl, const double *__restrict__ Linv,
+                                                                const double *B, int64_t ldb, double *Y, int64_t ldy,
+                                                                unsigned *flags, unsigned epoch, int *err)
+{
+    extern __shared__ __align__(16) double sw_smem[];
+    double *yv = sw_smem;                          // solved block being applied [64 * 16]
+    double *vv = yv + LEAF * SW_MAXRHS;            // right-hand side of the block being solved
+    double *red = vv + LEAF * SW_MAXRHS;           // [4][64 * 16] partial products
+    double *bst = red + 4 * LEAF * SW_MAXRHS;      // staged B rows of the next block
+    double *yst = bst + LEAF * SW_MAXRHS;          // staged partial sums of the next block
+    TL *Ls = reinterpret_cast<TL *>(yst + LEAF * SW_MAXRHS);               // [SW_SLOTS][64 * 64]
+    double *Li = reinterpret_cast<double *>(Ls + SW_SLOTS * LEAF * LEAF);   // inverse of the next block
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t N = (n + LEAF - 1) / LEAF;
+    const int64_t P = gridDim.x, me = blockIdx.x;
+    if (tid == 0) abort_flag = 0;
+    using TM = typename std::conditional<sizeof(TL) == 4, float, double>::type;
+
+    auto rows_of = [&](int64_t J) { return (int)((n - J * LEAF < LEAF) ? n - J * LEAF : LEAF); };
+
+    // Stage the 64 x 64 block of L that block I needs from solved block J.
+    auto stage = [&](int slot, int64_t I, int64_t J) {
+        const int64_t r0 = FWD ? I * LEAF : J * LEAF, c0 = FWD ? J * LEAF : I * LEAF;
+        const int nr = rows_of(FWD ? I : J), nc = rows_of(FWD ? J : I);
+        TL *dst = Ls + slot * LEAF * LEAF;
+        for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) {
+            const int r = e % LEAF, c = e / LEAF;
+            if (r < nr && c < nc) cp_async_elem(dst + e, L + (r0 + r) + (c0 + c) * ldl, (int)sizeof(TL));
+            else dst[e] = TL(0);
         }
+    };
+    // Stage what solving block J needs: its inverse, B rows, partial sums.
+    auto stage_solve = [&](int64_t J) {
+        const double *src = Linv + J * LEAF * LEAF;
+        for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) cp_async_elem(Li + e, src + e, 8);
+        const int nb = rows_of(J);
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
+            const int r = e % LEAF, c = e / LEAF;
+            if (r < nb) {
+                cp_async_elem(bst + e, B + J * LEAF + r + c * ldb, 8);
+                cp_async_elem(yst + e, Y + J * LEAF + r + c * ldy, 8);
+            } else {
+                bst[e] = 0.0;
+                yst[e] = 0.0;
+            }
+        }
+    };
+
+    // partial sums start at zero
+    for (int64_t I = me; I < N; I += P) {
+        const int nb = rows_of(I);
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
+            const int r = e % LEAF, c = e / LEAF;
+            if (r < nb) Y[I * LEAF + r + c * ldy] = 0.0;
+        }
+    }
+
+    // Solve block J from vv (= B_J - partial sums); write and publish.
+    // Four lanes share one (row, rhs) item and split its 64-term sum.
+    auto finalize = [&](int64_t J) {
+        const int nb = rows_of(J);
+        const int p = tid & 3;
+        for (int item = tid >> 2; item < LEAF * nrhs; item += SW_THREADS / 4) {
+            const int r = item % LEAF, c = item / LEAF;
+            double s = 0.0;
+            if (FWD) {
+                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * LEAF], vv[k + c * LEAF], s);
+            } else {
+                for (int k = r + ((p - r) & 3); k < LEAF; k += 4) s = fma(Li[k + r * LEAF], vv[k + c * LEAF], s);
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            if (p == 0 && r < nb) Y[J * LEAF + r + c * ldy] = s;
+        }
+        __threadfence();
         __syncthreads();
-        if (row < n) {
-            double s = W[row + r * ldw];
-            for (int k = 0; k < nb; ++k) s = fma(-(double)L[row + (o + k) * ldl], yj[k], s);
-            W[row + r * ldw] = s;
+        if (tid == 0) st_release(&flags[J], epoch);
+    };
+
+    // Contribution of the solved block (in yv) to block I, from the staged
+    // block in `slot`, into red[0][r + c*64] (summed over the four partial
+    // rows for FWD).  With an FP32 factor the block product runs in FP32.
+    auto contribution = [&](int slot, int64_t I) {
+        const int nbI = rows_of(I);
+        const TL *Lb = Ls + slot * LEAF * LEAF;
+        if (FWD) {
+            // thread (r, q) owns row r, columns 16q..16q+15 of the block
+            const int r = tid % LEAF, q = tid / LEAF;
+            TM a[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = (TM)Lb[r + (q * 16 + k) * LEAF];
+            for (int c = 0; c < nrhs; ++c) {
+                TM pp = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) pp = fma(a[k], (TM)yv[q * 16 + k + c * LEAF], pp);
+                red[q * LEAF * SW_MAXRHS + r + c * LEAF] = (double)pp;
+            }
+            __syncthreads();
+            for (int e = tid; e < LEAF * nrhs; e += SW_THREADS)
+                red[e] = (e % LEAF < nbI) ? red[e] + red[LEAF * SW_MAXRHS + e] + red[2 * LEAF * SW_MAXRHS + e] +
+                                                red[3 * LEAF * SW_MAXRHS + e]
+                                          : 0.0;
+            __syncthreads();
+        } else {
+            // warp w owns columns w, w+8, ..., w+56 of block I; lanes hold
+            // rows lane and lane+32 of block J
+            for (int c = 0; c < nrhs; ++c) {
+                const TM y0 = (TM)yv[lane + c * LEAF], y1 = (TM)yv[lane + 32 + c * LEAF];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int i = warp + 8 * t;
+                    TM sum = fma((TM)Lb[lane + 32 + i * LEAF], y1, (TM)Lb[lane + i * LEAF] * y0);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+                    if (lane == 0) red[i + c * LEAF] = (i < nbI) ? (double)sum : 0.0;
+                }
+            }
+            __syncthreads();
+        }
+    };
+    auto add_to_Y = [&](int64_t I) {
+        const int nbI = rows_of(I);
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS)
+            if (e % LEAF < nbI) Y[I * LEAF + e % LEAF + (e / LEAF) * ldy] += red[e];
+        __syncthreads();
+    };
+
+    __syncthreads();
+    const int64_t first = FWD ? 0 : N - 1;
+    if (first % P == me) {
+        stage_solve(first);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = bst[e] - yst[e];
+        __syncthreads();
+        finalize(first);
+    }
+    for (int64_t s = 0; s < N; ++s) {
+        const int64_t J = FWD ? s : N - 1 - s;
+        const int64_t next = FWD ? J + 1 : J - 1;
+        const bool own_next = next >= 0 && next < N && next % P == me;
+        // Owned blocks to update with y_J, in sweep order: next first (if
+        // owned), then the rest.
+        int64_t cur = next;
+        if (!own_next) {
+            if (FWD) {
+                cur = me;
+                if (cur <= J) cur += ((J - cur) / P + 1) * P;
+            } else {
+                cur = me + ((N - 1 - me) / P) * P;
+                while (cur >= J && cur >= 0) cur -= P;
+            }
+        }
+        auto in_range = [&](int64_t I) { return FWD ? (I > J && I < N) : (I < J && I >= 0); };
+        int staged = 0;
+        int64_t chunk[SW_SLOTS];
+        while (staged < SW_SLOTS && in_range(cur)) {
+            chunk[staged] = cur;
+            stage(staged, cur, J);
+            ++staged;
+            cur = FWD ? cur + P : cur - P;
+        }
+        if (own_next) stage_solve(next);
+        cp_async_commit();
+        if (J % P != me) {
+            if (tid == 0) {
+                bool ok = false;
+                for (uint32_t it = 0; it < FLAG_SPIN_LIMIT; ++it) {
+                    if (ld_acquire(&flags[J]) == epoch) {
+                        ok = true;
+                        break;
+                    }
+                    if (it > 4096) __nanosleep(64);
+                }
+                if (!ok) {
+                    abort_flag = 1;
+                    atomicExch(err, 1);
+                }
+            }
+            __syncthreads();
+            if (abort_flag) {
+                cp_async_wait_all();
+                return;
+            }
+        }
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
+            const int r = e % LEAF, c = e / LEAF;
+            yv[e] = (r < rows_of(J)) ? __ldcg(&Y[J * LEAF + r + c * ldy]) : 0.0;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int q = 0; q < staged; ++q) {
+            contribution(q, chunk[q]);
+            if (q == 0 && own_next) {
+                for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = bst[e] - yst[e] - red[e];
+                __syncthreads();
+                finalize(next);
+            } else {
+                add_to_Y(chunk[q]);
+            }
+        }
+        // owned blocks beyond the first chunk
+        while (in_range(cur)) {
+            __syncthreads();
+            int cnt = 0;
+            while (cnt < SW_SLOTS && in_range(cur)) {
+                chunk[cnt] = cur;
+                stage(cnt, cur, J);
+                ++cnt;
+                cur = FWD ? cur + P : cur - P;
+            }
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
+            for (int q = 0; q < cnt; ++q) {
+                contribution(q, chunk[q]);
+                add_to_Y(chunk[q]);
+            }
         }
         __syncthreads();
     }
 }
 
-// Back step J.  W: working vectors (entries of blocks K < J updated here);
-// X: output (block J written by CTA 0).  Columns c < o are split over CTAs,
-// one warp per column, lanes over the 64 rows of block J.
-template <typename TL>
-__global__ void __launch_bounds__(256) bwd_step_kernel(int64_t n, int64_t J, const TL *__restrict__ L,
-                                                       int64_t ldl, const double *__restrict__ LinvJ,
-                                                       double *W, int64_t ldw, double *X, int64_t ldx,
-                                                       int nrhs)
+int sm_count(gpch_ctx *ctx)
 {
-    __shared__ double wj[LEAF];
-    __shared__ double xj[LEAF];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t o = J * LEAF;
-    const int nb = (int)((n - o < LEAF) ? n - o : LEAF);
-    for (int r = 0; r < nrhs; ++r) {
-        if (tid < LEAF) wj[tid] = (tid < nb) ? W[o + tid + r * ldw] : 0.0;
-        __syncthreads();
-        if (tid < LEAF) {
-            // x = inv(L_JJ)^T w: x[t] = sum_{k >= t} inv(L)[k][t] w[k]
-            double s = 0.0;
-            for (int k = tid; k < LEAF; ++k) s = fma(LinvJ[k + tid * LEAF], wj[k], s);
-            xj[tid] = s;
-            if (blockIdx.x == 0 && tid < nb) X[o + tid + r * ldx] = s;
+    static int cached = 0;
+    if (!cached) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
         }
-        __syncthreads();
-        const int64_t cbase = (int64_t)blockIdx.x * LEAF;
-        for (int cc = warp; cc < LEAF; cc += 8) {
-            const int64_t c = cbase + cc;
-            if (c >= o) break;
-            double s = 0.0;
-            if (lane < nb) s = (double)L[(o + lane) + c * ldl] * xj[lane];
-            if (lane + 32 < nb) s = fma((double)L[(o + lane + 32) + c * ldl], xj[lane + 32], s);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) W[c + r * ldw] -= s;
-        }
-        __syncthreads();
+        cached = v;
     }
+    return cached;
+}
+
+template <typename TL, bool FWD>
+gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_t ldl, const double *Linv,
+                         const double *B, int64_t ldb, double *Y, int64_t ldy, unsigned *flags, unsigned epoch,
+                         int *err, cudaStream_t st)
+{
+    static bool attr_done = false;
+    if (!attr_done) {
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sweep_smem_bytes<TL>()));
+        attr_done = true;
+    }
+    const int64_t N = (n + LEAF - 1) / LEAF;
+    const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
+    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &epoch, &err};
+    GPCH_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)trsv_sweep_kernel<TL, FWD>, dim3(P), dim3(SW_THREADS),
+                                               args, sweep_smem_bytes<TL>(), st));
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
 }
 
 }  // namespace
 
 namespace gpch {
 
-// Enqueue the two sweeps on B (n x nrhs, in place).  Linv: n_blocks*64*64
-// doubles of workspace; Y: n x nrhs doubles of workspace (ld n).  TL is the
-// storage type of L (FP64 factor, or the FP32 low-precision factor); the
-// arithmetic is FP64 either way.
-template <typename TL>
-gpch_status chol_solve_enqueue_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, double *B, int64_t ldb,
-                                 int nrhs, double *Linv, double *Y, cudaStream_t st)
+size_t solve_ws_bytes(int64_t n, int nrhs)
 {
-    gpch::PhaseScope ph(ctx, GPCH_PHASE_SOLVE, st, 2.0 * (double)n * n * nrhs);
-    const int64_t NBk = (n + LEAF - 1) / LEAF;
+    Carver dry(nullptr);
+    const int64_t N = (n + LEAF - 1) / LEAF;
+    dry.take<double>((size_t)N * LEAF * LEAF);
+    dry.take<double>((size_t)n * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
+    dry.take<unsigned>((size_t)2 * N);
+    dry.take<int>(4);
+    return dry.off;
+}
+
+SolveWs carve_solve(void *base, int64_t n, int nrhs)
+{
+    Carver cv(base);
+    const int64_t N = (n + LEAF - 1) / LEAF;
+    SolveWs w;
+    w.Linv = cv.take<double>((size_t)N * LEAF * LEAF);
+    w.Y = cv.take<double>((size_t)n * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
+    w.flags = cv.take<unsigned>((size_t)2 * N);
+    w.err = cv.take<int>(4);
+    w.epoch = 0;
+    return w;
+}
+
+// Invert the diagonal blocks of L and clear the flags (once per factor).
+template <typename TL>
+gpch_status solve_prepare_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, SolveWs &w, cudaStream_t st)
+{
+    const int64_t N = (n + LEAF - 1) / LEAF;
     constexpr size_t INV_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
     static bool attr_done = false;
     if (!attr_done) {
@@ -138,33 +400,50 @@ gpch_status chol_solve_enqueue_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t 
                                             (int)INV_SMEM));
         attr_done = true;
     }
-    inv_diag_blocks_kernel<<<(unsigned)NBk, 256, INV_SMEM, st>>>(n, L, ldl, Linv);
+    inv_diag_blocks_kernel<TL><<<(unsigned)N, 256, INV_SMEM, st>>>(n, L, ldl, w.Linv);
     GPCH_LAUNCH_CHECK(ctx);
-    for (int64_t J = 0; J < NBk; ++J) {
-        const int64_t below = n - (J + 1) * LEAF;
-        const unsigned grid = below > 0 ? (unsigned)((below + 255) / 256) : 1u;
-        fwd_step_kernel<<<grid, 256, 0, st>>>(n, J, L, ldl, Linv + J * LEAF * LEAF, B, ldb, Y, n, nrhs);
-        GPCH_LAUNCH_CHECK(ctx);
-    }
-    for (int64_t J = NBk - 1; J >= 0; --J) {
-        const int64_t above = J * LEAF;
-        const unsigned grid = above > 0 ? (unsigned)((above + LEAF - 1) / LEAF) : 1u;
-        bwd_step_kernel<<<grid, 256, 0, st>>>(n, J, L, ldl, Linv + J * LEAF * LEAF, Y, n, B, ldb, nrhs);
-        GPCH_LAUNCH_CHECK(ctx);
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.flags, 0, 2 * N * sizeof(unsigned), st));
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), st));
+    w.epoch = 0;
+    return GPCH_OK;
+}
+
+// B <- (L L^T)^-1 B, in place, after solve_prepare.
+template <typename TL>
+gpch_status solve_apply_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, double *B, int64_t ldb, int nrhs,
+                          SolveWs &w, cudaStream_t st)
+{
+    const int64_t N = (n + LEAF - 1) / LEAF;
+    PhaseScope ph(ctx, GPCH_PHASE_SOLVE, st, 2.0 * (double)n * n * nrhs);
+    for (int c0 = 0; c0 < nrhs; c0 += SW_MAXRHS) {
+        const int g = (nrhs - c0 < SW_MAXRHS) ? nrhs - c0 : SW_MAXRHS;
+        double *Bc = B + (int64_t)c0 * ldb;
+        ++w.epoch;
+        GPCH_CHECK((launch_sweep<TL, true>(ctx, n, g, L, ldl, w.Linv, Bc, ldb, w.Y, n, w.flags, w.epoch, w.err,
+                                           st)));
+        GPCH_CHECK((launch_sweep<TL, false>(ctx, n, g, L, ldl, w.Linv, w.Y, n, Bc, ldb, w.flags + N, w.epoch,
+                                            w.err, st)));
     }
     return GPCH_OK;
 }
 
-gpch_status chol_solve_enqueue(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb,
-                               int nrhs, double *Linv, double *Y, cudaStream_t st)
+gpch_status solve_prepare(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, SolveWs &w, cudaStream_t st)
 {
-    return chol_solve_enqueue_t<double>(ctx, n, L, ldl, B, ldb, nrhs, Linv, Y, st);
+    return solve_prepare_t<double>(ctx, n, L, ldl, w, st);
 }
-
-gpch_status chol_solve_enqueue_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, double *B, int64_t ldb,
-                                   int nrhs, double *Linv, double *Y, cudaStream_t st)
+gpch_status solve_prepare_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, SolveWs &w, cudaStream_t st)
 {
-    return chol_solve_enqueue_t<float>(ctx, n, L, ldl, B, ldb, nrhs, Linv, Y, st);
+    return solve_prepare_t<float>(ctx, n, L, ldl, w, st);
+}
+gpch_status solve_apply(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb, int nrhs,
+                        SolveWs &w, cudaStream_t st)
+{
+    return solve_apply_t<double>(ctx, n, L, ldl, B, ldb, nrhs, w, st);
+}
+gpch_status solve_apply_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, double *B, int64_t ldb, int nrhs,
+                            SolveWs &w, cudaStream_t st)
+{
+    return solve_apply_t<float>(ctx, n, L, ldl, B, ldb, nrhs, w, st);
 }
 
 }  // namespace gpch
@@ -178,13 +457,14 @@ extern "C" gpch_status gpch_chol_solve(gpch_ctx *ctx, int64_t n, const double *L
     if (n == 0 || nrhs == 0) return GPCH_OK;
     GPCH_ARG(ctx, L != nullptr && B != nullptr, "null pointer");
     GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
-    const int64_t NBk = (n + LEAF - 1) / LEAF;
-    gpch::Carver dry(nullptr);
-    dry.take<double>((size_t)NBk * LEAF * LEAF);
-    dry.take<double>((size_t)n * nrhs);
-    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
-    gpch::Carver cv(ctx->ws);
-    double *Linv = cv.take<double>((size_t)NBk * LEAF * LEAF);
-    double *Y = cv.take<double>((size_t)n * nrhs);
-    return gpch::chol_solve_enqueue(ctx, n, L, ldl, B, ldb, nrhs, Linv, Y, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    GPCH_CHECK(gpch::ws_reserve(ctx, gpch::solve_ws_bytes(n, nrhs)));
+    gpch::SolveWs w = gpch::carve_solve(ctx->ws, n, nrhs);
+    GPCH_CHECK(gpch::solve_prepare(ctx, n, L, ldl, w, st));
+    GPCH_CHECK(gpch::solve_apply(ctx, n, L, ldl, B, ldb, nrhs, w, st));
+    int *h = static_cast<int *>(ctx->pinned);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+    if (*h != 0) return gpch::fail(ctx, GPCH_TIMEOUT, "substitution sweep wait gave up");
+    return GPCH_OK;
 }
