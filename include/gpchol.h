@@ -99,7 +99,8 @@ typedef enum gpch_phase {
     GPCH_PHASE_CG_MATVEC = 5,   /* CG matrix-vector product (one pass over A)      */
     GPCH_PHASE_CG_VECTOR = 6,   /* CG dot/axpy/xpay kernels                        */
     GPCH_PHASE_MIXED_TRAILING = 7, /* step 3 on tensor cores (bf16 / split bf16)  */
-    GPCH_PHASE_COUNT = 8
+    GPCH_PHASE_BATCHED = 8,     /* a whole batched solve (one graph launch)       */
+    GPCH_PHASE_COUNT = 9
 } gpch_phase;
 
 /* Turn event timing on or off (off by default; costs two event records per
@@ -217,6 +218,36 @@ gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A,
 gpch_status gpch_cg_solve_noalloc(int64_t n, const void *A, gpch_dtype dtype, int64_t lda, const double *B,
                                   int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol, int maxit,
                                   int replace_every, void *stream, gpch_cg_stats *stats);
+
+/* ---------------------------------------------- A10: batched solve */
+
+/* One system of a batch: A (device, FP64, n x n, lda >= n; its lower
+ * triangle is overwritten by the factor L) and B (device, n x nrhs,
+ * ldb >= n; overwritten by the solution X). */
+typedef struct gpch_system {
+    int64_t n;
+    double *A;
+    int64_t lda;
+    double *B;
+    int64_t ldb;
+    int32_t nrhs;
+} gpch_system;
+
+/* Factor and solve `count` independent SPD systems A_s X_s = B_s in FP64:
+ * Algorithm 1 (right) with 64-wide blocks on every system, then forward
+ * and back substitution.  Step k of all systems runs in one grouped launch
+ * per kernel kind, and the whole launch sequence of a batch is captured
+ * once as a CUDA graph that later calls with the same systems (same sizes
+ * and pointers) replay as one graph launch.  Each system is tiled by its
+ * own size only, so its result does not depend on its batch-mates.
+ * systems: host array of count descriptors.  info: host array of count
+ * entries, 0 or the 1-based failing column of that system (the call then
+ * returns GPCH_NOT_SPD; the other systems are still solved).  The context
+ * keeps up to 8 captured batches (device tables and per-system workspace,
+ * counted against the HBM budget) until gpch_destroy.  Synchronizes
+ * `stream`. */
+gpch_status gpch_batched_solve(gpch_ctx *ctx, int count, const gpch_system *systems, void *stream,
+                               int64_t *info);
 
 /* --------------------------- A4 (mixed): tensor-core trailing update */
 

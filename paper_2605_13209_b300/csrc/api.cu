@@ -91,6 +91,7 @@ gpch_status gpch_destroy(gpch_ctx *ctx)
     if (!ctx) return GPCH_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    gpch::batched_release(ctx);
     for (auto &v : ctx->pending)
         for (auto &t : v) {
             cudaEventDestroy(t.start);

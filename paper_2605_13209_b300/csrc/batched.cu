@@ -1,0 +1,411 @@
+// batched.cu -- A10: many independent GP systems factored and solved
+// together (FP64 blocked Cholesky, Algorithm 1 right, with 64-wide blocks,
+// then forward/back substitution).
+//
+// The batch runs level-synchronously: step k of every system whose matrix
+// has more than k block columns is done by one grouped launch per kernel
+// kind (leaf POTRF + inverse of block (k,k), panel solve below it, SYRK/GEMM
+// update of the trailing lower triangle), and likewise one grouped launch
+// per block of each substitution sweep.  A per-step prefix table maps a CTA
+// to (system, local task), found by binary search.  Every system is cut into
+// tiles by its own size only, so its arithmetic does not depend on the
+// other systems in the batch.  The whole launch sequence of a batch is
+// captured once as a CUDA graph and replayed on later calls with the same
+// systems.
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "dense_fp64.cuh"
+
+namespace {
+
+using gpch::LEAF;
+
+struct BSys {
+    double *A;
+    int64_t lda;
+    int64_t n;
+    double *B;
+    int64_t ldb;
+    int nrhs;
+    double *Linv;    // nblocks x 64 x 64
+    double *Y;       // n x nrhs
+    int64_t *info;
+};
+
+// Per-step task table: `cnt` active systems, their indices, and prefix sums
+// of their task counts (length cnt + 1).
+struct StepTable {
+    const int *sys;
+    const int64_t *pref;
+    int cnt;
+};
+
+__device__ inline int find_task(const StepTable &t, int64_t task, int64_t &local)
+{
+    int lo = 0, hi = t.cnt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (t.pref[mid] <= task) lo = mid;
+        else hi = mid - 1;
+    }
+    local = task - t.pref[lo];
+    return t.sys[lo];
+}
+
+__device__ inline int64_t block_rows(int64_t n, int64_t k) { return (n - k * LEAF < LEAF) ? n - k * LEAF : LEAF; }
+
+__global__ void __launch_bounds__(256) bpotrf_kernel(const BSys *sys, StepTable t, int k)
+{
+    extern __shared__ double bsmem[];
+    int64_t local;
+    const BSys &S = sys[find_task(t, blockIdx.x, local)];
+    if (*S.info != 0) return;
+    const int64_t o = (int64_t)k * LEAF;
+    potrf_leaf_body(S.A + o + o * S.lda, S.lda, (int)block_rows(S.n, k), S.Linv + (int64_t)k * LEAF * LEAF, o,
+                    S.info, bsmem);
+}
+
+__global__ void __launch_bounds__(256) btrsm_kernel(const BSys *sys, StepTable t, int k)
+{
+    extern __shared__ __align__(16) unsigned char btsmem[];
+    int64_t local;
+    const BSys &S = sys[find_task(t, blockIdx.x, local)];
+    if (*S.info != 0) return;
+    const int64_t o = (int64_t)k * LEAF, m = S.n - o - LEAF;
+    trsm_inv_body<double, 64>(S.A + (o + LEAF) + o * S.lda, S.lda, m, LEAF, S.Linv + (int64_t)k * LEAF * LEAF,
+                              local * 64, btsmem);
+}
+
+__global__ void __launch_bounds__(256, 3) bgemm_kernel(const BSys *sys, StepTable t, int k)
+{
+    int64_t local;
+    const BSys &S = sys[find_task(t, blockIdx.x, local)];
+    if (*S.info != 0) return;
+    const int64_t o = (int64_t)k * LEAF, m = S.n - o - LEAF;
+    int64_t ti, tj;
+    tri_index(local, ti, tj);
+    const double *P = S.A + (o + LEAF) + o * S.lda;
+    gemm_nt_minus_body<double, true, 64>(m, m, LEAF, P, S.lda, P, S.lda, S.A + (o + LEAF) * (1 + S.lda), S.lda,
+                                         ti, tj);
+}
+
+// Forward step k: y_k = inv(L_kk) b_k (each CTA recomputes it), CTA 0 of the
+// system stores it in Y, every CTA updates 256 rows below the block.
+__global__ void __launch_bounds__(256) bfwd_kernel(const BSys *sys, StepTable t, int k)
+{
+    __shared__ double bj[LEAF], yj[LEAF];
+    int64_t local;
+    const BSys &S = sys[find_task(t, blockIdx.x, local)];
+    if (*S.info != 0) return;
+    const int tid = threadIdx.x;
+    const int64_t o = (int64_t)k * LEAF;
+    const int nb = (int)block_rows(S.n, k);
+    const double *Li = S.Linv + (int64_t)k * LEAF * LEAF;
+    const int64_t row = o + nb + local * 256 + tid;
+    for (int r = 0; r < S.nrhs; ++r) {
+        if (tid < LEAF) bj[tid] = (tid < nb) ? S.B[o + tid + r * S.ldb] : 0.0;
+        __syncthreads();
+        if (tid < LEAF) {
+            double s = 0.0;
+            for (int q = 0; q <= tid; ++q) s = fma(Li[tid + q * LEAF], bj[q], s);
+            yj[tid] = s;
+            if (local == 0 && tid < nb) S.Y[o + tid + r * S.n] = s;
+        }
+        __syncthreads();
+        if (row < S.n) {
+            double s = S.B[row + r * S.ldb];
+            for (int q = 0; q < nb; ++q) s = fma(-S.A[row + (o + q) * S.lda], yj[q], s);
+            S.B[row + r * S.ldb] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Back step k: x_k = inv(L_kk)^T w_k (w = Y), CTA 0 of the system stores it
+// in B, every CTA updates 64 earlier entries of w, one warp per entry.
+__global__ void __launch_bounds__(256) bbwd_kernel(const BSys *sys, StepTable t, int k)
+{
+    __shared__ double wj[LEAF], xj[LEAF];
+    int64_t local;
+    const BSys &S = sys[find_task(t, blockIdx.x, local)];
+    if (*S.info != 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t o = (int64_t)k * LEAF;
+    const int nb = (int)block_rows(S.n, k);
+    const double *Li = S.Linv + (int64_t)k * LEAF * LEAF;
+    for (int r = 0; r < S.nrhs; ++r) {
+        if (tid < LEAF) wj[tid] = (tid < nb) ? S.Y[o + tid + r * S.n] : 0.0;
+        __syncthreads();
+        if (tid < LEAF) {
+            double s = 0.0;
+            for (int q = tid; q < LEAF; ++q) s = fma(Li[q + tid * LEAF], wj[q], s);
+            xj[tid] = s;
+            if (local == 0 && tid < nb) S.B[o + tid + r * S.ldb] = s;
+        }
+        __syncthreads();
+        for (int cc = warp; cc < LEAF; cc += 8) {
+            const int64_t c = local * LEAF + cc;
+            if (c >= o) break;
+            double s = 0.0;
+            if (lane < nb) s = S.A[(o + lane) + c * S.lda] * xj[lane];
+            if (lane + 32 < nb) s = fma(S.A[(o + lane + 32) + c * S.lda], xj[lane + 32], s);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) S.Y[c + r * S.n] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+constexpr size_t BPOTRF_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
+constexpr size_t BTRSM_SMEM = trsm_smem_bytes<double, 64>();
+
+// One captured batch: device tables, per-system workspace, the graph.
+struct BatchPlan {
+    void *dev = nullptr;          // all device memory of the plan
+    size_t bytes = 0;
+    BSys *d_sys = nullptr;
+    int64_t *d_info = nullptr;
+    int count = 0;
+    int64_t launches = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> flops;   // per system n^3/3
+};
+
+struct PlanKey {
+    std::vector<int64_t> v;
+    bool operator<(const PlanKey &o) const { return v < o.v; }
+};
+
+struct PlanCache {
+    std::map<PlanKey, BatchPlan> plans;
+};
+
+std::map<gpch_ctx *, PlanCache> g_caches;   // per context
+
+void free_plan(BatchPlan &p)
+{
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    if (p.dev) cudaFree(p.dev);
+    p = BatchPlan();
+}
+
+// Host-side layout of all step tables, built from the sizes only.
+struct HostTables {
+    std::vector<int> sys;
+    std::vector<int64_t> pref;
+    struct Step {
+        size_t sys_off, pref_off;
+        int cnt;
+        int64_t tasks;
+    };
+    std::vector<Step> potrf, trsm, gemm, fwd, bwd;
+};
+
+template <typename F>
+HostTables::Step add_step(HostTables &h, int count, const int64_t *ns, F tasks_of)
+{
+    HostTables::Step st{h.sys.size(), h.pref.size(), 0, 0};
+    h.pref.push_back(0);
+    for (int s = 0; s < count; ++s) {
+        const int64_t t = tasks_of(ns[s]);
+        if (t <= 0) continue;
+        h.sys.push_back(s);
+        st.tasks += t;
+        h.pref.push_back(st.tasks);
+        ++st.cnt;
+    }
+    return st;
+}
+
+gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, BatchPlan &plan, cudaStream_t st)
+{
+    std::vector<int64_t> ns(count);
+    int64_t kmax = 0;
+    for (int s = 0; s < count; ++s) {
+        ns[s] = systems[s].n;
+        const int64_t nb = (ns[s] + LEAF - 1) / LEAF;
+        if (nb > kmax) kmax = nb;
+    }
+    HostTables h;
+    for (int64_t k = 0; k < kmax; ++k) {
+        h.potrf.push_back(add_step(h, count, ns.data(), [&](int64_t n) { return n > k * LEAF ? 1 : 0; }));
+        h.trsm.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+            const int64_t m = n - (k + 1) * LEAF;
+            return m > 0 ? (m + 63) / 64 : 0;
+        }));
+        h.gemm.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+            const int64_t m = n - (k + 1) * LEAF;
+            const int64_t T = m > 0 ? (m + 63) / 64 : 0;
+            return T * (T + 1) / 2;
+        }));
+        h.fwd.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+            if (n <= k * LEAF) return (int64_t)0;
+            const int64_t below = n - (k + 1) * LEAF;
+            return below > 0 ? (below + 255) / 256 : (int64_t)1;
+        }));
+        h.bwd.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+            if (n <= k * LEAF) return (int64_t)0;
+            return k > 0 ? k : (int64_t)1;   // k*64 columns above, 64 per CTA
+        }));
+    }
+    // device layout: systems, info, tables, then per-system Linv and Y
+    gpch::Carver dry(nullptr);
+    const size_t o_sys = dry.reserve(count * sizeof(BSys));
+    const size_t o_info = dry.reserve(count * sizeof(int64_t));
+    const size_t o_tsys = dry.reserve(h.sys.size() * sizeof(int));
+    const size_t o_pref = dry.reserve(h.pref.size() * sizeof(int64_t));
+    std::vector<size_t> o_linv(count), o_y(count);
+    for (int s = 0; s < count; ++s) {
+        o_linv[s] = dry.reserve((size_t)((ns[s] + LEAF - 1) / LEAF) * LEAF * LEAF * sizeof(double));
+        o_y[s] = dry.reserve((size_t)ns[s] * systems[s].nrhs * sizeof(double));
+    }
+    if (ctx->budget && ctx->ws_bytes + dry.off > ctx->budget)
+        return gpch::fail(ctx, GPCH_OOM_BUDGET, "batch plan of %zu bytes exceeds the HBM budget", dry.off);
+    GPCH_CUDA(ctx, cudaMalloc(&plan.dev, dry.off));
+    plan.bytes = dry.off;
+    char *base = static_cast<char *>(plan.dev);
+    plan.d_sys = reinterpret_cast<BSys *>(base + o_sys);
+    plan.d_info = reinterpret_cast<int64_t *>(base + o_info);
+    int *d_tsys = reinterpret_cast<int *>(base + o_tsys);
+    int64_t *d_pref = reinterpret_cast<int64_t *>(base + o_pref);
+    std::vector<BSys> hs(count);
+    for (int s = 0; s < count; ++s) {
+        hs[s] = BSys{systems[s].A, systems[s].lda, ns[s], systems[s].B, systems[s].ldb, systems[s].nrhs,
+                     reinterpret_cast<double *>(base + o_linv[s]), reinterpret_cast<double *>(base + o_y[s]),
+                     plan.d_info + s};
+    }
+    GPCH_CUDA(ctx, cudaMemcpyAsync(plan.d_sys, hs.data(), count * sizeof(BSys), cudaMemcpyHostToDevice, st));
+    if (!h.sys.empty())
+        GPCH_CUDA(ctx, cudaMemcpyAsync(d_tsys, h.sys.data(), h.sys.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(d_pref, h.pref.data(), h.pref.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                   st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));   // host vectors go out of scope
+
+    static bool attr_done = false;
+    if (!attr_done) {
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(bpotrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)BPOTRF_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(btrsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)BTRSM_SMEM));
+        attr_done = true;
+    }
+    auto table = [&](const HostTables::Step &x) { return StepTable{d_tsys + x.sys_off, d_pref + x.pref_off, x.cnt}; };
+
+    // capture the whole batch as one graph
+    cudaStream_t cs;
+    GPCH_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int64_t launches = 0;
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(plan.d_info, 0, count * sizeof(int64_t), cs);
+        for (int64_t k = 0; k < kmax; ++k) {
+            if (h.potrf[k].tasks)
+                bpotrf_kernel<<<(unsigned)h.potrf[k].tasks, 256, BPOTRF_SMEM, cs>>>(plan.d_sys, table(h.potrf[k]),
+                                                                                   (int)k);
+            if (h.trsm[k].tasks)
+                btrsm_kernel<<<(unsigned)h.trsm[k].tasks, 256, BTRSM_SMEM, cs>>>(plan.d_sys, table(h.trsm[k]), (int)k);
+            if (h.gemm[k].tasks)
+                bgemm_kernel<<<(unsigned)h.gemm[k].tasks, 256, 0, cs>>>(plan.d_sys, table(h.gemm[k]), (int)k);
+            launches += (h.potrf[k].tasks > 0) + (h.trsm[k].tasks > 0) + (h.gemm[k].tasks > 0);
+        }
+        for (int64_t k = 0; k < kmax; ++k)
+            if (h.fwd[k].tasks) {
+                bfwd_kernel<<<(unsigned)h.fwd[k].tasks, 256, 0, cs>>>(plan.d_sys, table(h.fwd[k]), (int)k);
+                ++launches;
+            }
+        for (int64_t k = kmax - 1; k >= 0; --k)
+            if (h.bwd[k].tasks) {
+                bbwd_kernel<<<(unsigned)h.bwd[k].tasks, 256, 0, cs>>>(plan.d_sys, table(h.bwd[k]), (int)k);
+                ++launches;
+            }
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(plan);
+        return gpch::fail(ctx, GPCH_CUDA_ERROR, "batch graph capture failed: %s", cudaGetErrorString(e));
+    }
+    plan.count = count;
+    plan.launches = launches;
+    plan.flops.resize(count);
+    for (int s = 0; s < count; ++s) plan.flops[s] = ns[s] * ns[s] * ns[s] / 3;
+    return GPCH_OK;
+}
+
+}  // namespace
+
+namespace gpch {
+
+void batched_release(gpch_ctx *ctx)
+{
+    auto it = g_caches.find(ctx);
+    if (it == g_caches.end()) return;
+    for (auto &kv : it->second.plans) free_plan(kv.second);
+    g_caches.erase(it);
+}
+
+}  // namespace gpch
+
+extern "C" gpch_status gpch_batched_solve(gpch_ctx *ctx, int count, const gpch_system *systems, void *stream,
+                                          int64_t *info)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, count >= 0, "count < 0");
+    if (count == 0) return GPCH_OK;
+    GPCH_ARG(ctx, systems != nullptr && info != nullptr, "null pointer");
+    for (int s = 0; s < count; ++s) {
+        const gpch_system &y = systems[s];
+        GPCH_ARG(ctx, y.n >= 1 && y.nrhs >= 1 && y.lda >= y.n && y.ldb >= y.n && y.A && y.B,
+                 "each system needs n >= 1, nrhs >= 1, lda >= n, ldb >= n and non-null A, B");
+        GPCH_ARG(ctx, y.n < ((int64_t)1 << 31), "n too large");
+    }
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanKey key;
+    key.v.reserve(count * 6);
+    for (int s = 0; s < count; ++s) {
+        const gpch_system &y = systems[s];
+        key.v.insert(key.v.end(), {y.n, (int64_t)(uintptr_t)y.A, y.lda, (int64_t)(uintptr_t)y.B, y.ldb, y.nrhs});
+    }
+    PlanCache &cache = g_caches[ctx];
+    auto it = cache.plans.find(key);
+    if (it == cache.plans.end()) {
+        if (cache.plans.size() >= 8) {   // bounded cache: drop the oldest-keyed plan
+            GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+            free_plan(cache.plans.begin()->second);
+            cache.plans.erase(cache.plans.begin());
+        }
+        BatchPlan plan;
+        GPCH_CHECK(build_plan(ctx, count, systems, plan, st));
+        it = cache.plans.emplace(key, plan).first;
+    }
+    BatchPlan &plan = it->second;
+    double work = 0.0;
+    for (int64_t f : plan.flops) work += (double)f;
+    {
+        gpch::PhaseScope ph(ctx, GPCH_PHASE_BATCHED, st, work);
+        GPCH_CUDA(ctx, cudaGraphLaunch(plan.exec, st));
+    }
+    ctx->launches += plan.launches;
+    int64_t *h = static_cast<int64_t *>(ctx->pinned);
+    const int chunk = (int)(ctx->pinned_bytes / sizeof(int64_t));
+    bool any_bad = false;
+    for (int s0 = 0; s0 < count; s0 += chunk) {
+        const int c = (count - s0 < chunk) ? count - s0 : chunk;
+        GPCH_CUDA(ctx, cudaMemcpyAsync(h, plan.d_info + s0, c * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int s = 0; s < c; ++s) {
+            info[s0 + s] = h[s];
+            if (h[s] != 0) any_bad = true;
+        }
+    }
+    if (any_bad) return gpch::fail(ctx, GPCH_NOT_SPD, "at least one system of the batch is not SPD (see info)");
+    return GPCH_OK;
+}

@@ -17,91 +17,12 @@ namespace {
 
 using gpch::LEAF;
 
-// Step 1 leaf: factor the nb x nb (nb <= 64) lower block at A in place and
-// write inv(L) of the unit-padded 64 x 64 block to Linv (column-major, ld 64).
-// Right-looking: thread (tx, ty) keeps the 4 x 4 entries (tx + 16i, ty + 16j)
-// in registers; per column j the owner of the pivot takes the square root,
-// the owners of column j scale it and publish it, and every thread updates
-// its own entries below and right of the pivot.
+// Step 1 leaf (see potrf_leaf_body).
 __global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *Linv,
                                                          int64_t col0, int64_t *info)
 {
     extern __shared__ double leaf_smem[];
-    double (*S)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem);
-    double (*Vi)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem + LEAF * (LEAF + 1));
-    __shared__ double lbuf[2][LEAF];   // column j of L, double-buffered by the parity of j
-    __shared__ int bad;
-    if (*info != 0) return;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    double a[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = tx + 16 * i, c = ty + 16 * j;
-            double v;
-            if (r < nb && c < nb) v = (r >= c) ? A[r + c * lda] : 0.0;
-            else v = (r == c) ? 1.0 : 0.0;
-            a[i][j] = v;
-        }
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-        const int jq = j / 16, jr = j % 16;
-        double *lcol = lbuf[j & 1];
-        // pivot owner: row j = tx + 16 jq, column j = ty + 16 jq
-        if (tx == jr && ty == jr) {
-            double d = a[jq][jq];
-            if (!(d > 0.0) || !isfinite(d)) {
-                bad = j + 1;
-            } else {
-                d = sqrt(d);
-                a[jq][jq] = d;
-                lcol[j] = 1.0 / d;   // the column is scaled by the reciprocal
-            }
-        }
-        __syncthreads();
-        if (bad) break;
-        if (ty == jr) {
-            const double rinv = lcol[j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = tx + 16 * i;
-                if (r > j) {
-                    a[i][jq] *= rinv;
-                    lcol[r] = a[i][jq];
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = tx + 16 * i;
-            if (r <= j) continue;
-            const double lr = lcol[r];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int c = ty + 16 * jj;
-                if (c > j && c <= r) a[i][jj] -= lr * lcol[c];
-            }
-        }
-    }
-    if (bad) {
-        if (tid == 0) *info = col0 + bad;
-        return;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) S[tx + 16 * i][ty + 16 * j] = a[i][j];
-    __syncthreads();
-    gpch::invert_lower_64(S, Vi);
-    __syncthreads();
-    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
-        int r = e % LEAF, c = e / LEAF;
-        if (r < nb && c < nb && r >= c) A[r + c * lda] = S[r][c];
-        Linv[r + c * LEAF] = Vi[r][c];
-    }
+    potrf_leaf_body(A, lda, nb, Linv, col0, info, leaf_smem);
 }
 
 constexpr size_t LEAF_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);

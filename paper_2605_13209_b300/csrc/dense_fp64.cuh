@@ -81,17 +81,101 @@ using gpch::LEAF;
 // CTA owns ROWS whole rows, so reading B and writing X never overlap across
 // CTAs.  T is the storage and arithmetic type of B.  Thread t owns row
 // t % ROWS and every (256/ROWS)-th column from t / ROWS.
+// Step 1 leaf: factor the nb x nb (nb <= 64) lower block at A in place and
+// write inv(L) of the unit-padded 64 x 64 block to Linv (column-major, ld 64).
+// leaf_smem: 2 * 64 * 65 doubles of shared memory.
+// Right-looking: thread (tx, ty) keeps the 4 x 4 entries (tx + 16i, ty + 16j)
+// in registers; per column j the owner of the pivot takes the square root,
+// the owners of column j scale it and publish it, and every thread updates
+// its own entries below and right of the pivot.
+__device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *Linv, int64_t col0, int64_t *info,
+                                       double *leaf_smem)
+{
+    double (*S)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem);
+    double (*Vi)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem + LEAF * (LEAF + 1));
+    __shared__ double lbuf[2][LEAF];   // column j of L, double-buffered by the parity of j
+    __shared__ int bad;
+    if (*info != 0) return;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    double a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = tx + 16 * i, c = ty + 16 * j;
+            double v;
+            if (r < nb && c < nb) v = (r >= c) ? A[r + c * lda] : 0.0;
+            else v = (r == c) ? 1.0 : 0.0;
+            a[i][j] = v;
+        }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        const int jq = j / 16, jr = j % 16;
+        double *lcol = lbuf[j & 1];
+        // pivot owner: row j = tx + 16 jq, column j = ty + 16 jq
+        if (tx == jr && ty == jr) {
+            double d = a[jq][jq];
+            if (!(d > 0.0) || !isfinite(d)) {
+                bad = j + 1;
+            } else {
+                d = sqrt(d);
+                a[jq][jq] = d;
+                lcol[j] = 1.0 / d;   // the column is scaled by the reciprocal
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        if (ty == jr) {
+            const double rinv = lcol[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = tx + 16 * i;
+                if (r > j) {
+                    a[i][jq] *= rinv;
+                    lcol[r] = a[i][jq];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = tx + 16 * i;
+            if (r <= j) continue;
+            const double lr = lcol[r];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int c = ty + 16 * jj;
+                if (c > j && c <= r) a[i][jj] -= lr * lcol[c];
+            }
+        }
+    }
+    if (bad) {
+        if (tid == 0) *info = col0 + bad;
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) S[tx + 16 * i][ty + 16 * j] = a[i][j];
+    __syncthreads();
+    gpch::invert_lower_64(S, Vi);
+    __syncthreads();
+    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
+        int r = e % LEAF, c = e / LEAF;
+        if (r < nb && c < nb && r >= c) A[r + c * lda] = S[r][c];
+        Linv[r + c * LEAF] = Vi[r][c];
+    }
+}
+
 template <typename T, int ROWS>
-__global__ void __launch_bounds__(256) trsm_inv_kernel(T *B, int64_t ldb, int64_t m, int nc,
-                                                       const double *__restrict__ Linv, const int64_t *info)
+__device__ inline void trsm_inv_body(T *B, int64_t ldb, int64_t m, int nc, const double *__restrict__ Linv,
+                                     int64_t r0, unsigned char *trsm_smem)
 {
     constexpr int G = 256 / ROWS, NC = LEAF / G;
-    extern __shared__ __align__(16) unsigned char trsm_smem[];
     T *Bs = reinterpret_cast<T *>(trsm_smem);   // Bs[k * ROWS + r]
     T *Ls = Bs + LEAF * ROWS;                   // Ls[k * 64 + c] = inv(L)[c][k]
-    if (info && *info != 0) return;
     const int tid = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * ROWS;
     for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
         const int r = e % ROWS, k = e / ROWS;
         Bs[k * ROWS + r] = (r0 + r < m && k < nc) ? B[(r0 + r) + k * ldb] : T(0);
@@ -116,30 +200,40 @@ __global__ void __launch_bounds__(256) trsm_inv_kernel(T *B, int64_t ldb, int64_
         }
 }
 
-// C[m x nn] -= A[m x k] B[nn x k]^T.  LOWER: C is square and only its lower
-// triangle is updated; the grid enumerates the lower BT x BT tiles.  Thread
-// (tx, ty) owns entries (tx + 16i, ty + 16j) of the tile.
+// Panel leaf solve: X = B inv(L)^T in place on the m x nc panel B (nc <=
+// 64), inv(L) given as a 64 x 64 FP64 block (column-major, ld 64).  Every
+// CTA owns ROWS whole rows, so reading B and writing X never overlap across
+// CTAs.  T is the storage and arithmetic type of B.  Thread t owns row
+// t % ROWS and every (256/ROWS)-th column from t / ROWS.
+template <typename T, int ROWS>
+__global__ void __launch_bounds__(256) trsm_inv_kernel(T *B, int64_t ldb, int64_t m, int nc,
+                                                       const double *__restrict__ Linv, const int64_t *info)
+{
+    extern __shared__ __align__(16) unsigned char trsm_smem[];
+    if (info && *info != 0) return;
+    trsm_inv_body<T, ROWS>(B, ldb, m, nc, Linv, (int64_t)blockIdx.x * ROWS, trsm_smem);
+}
+
+// Triangular tile index t -> (ti, tj), ti >= tj, t = ti (ti + 1) / 2 + tj.
+__device__ inline void tri_index(int64_t t, int64_t &ti, int64_t &tj)
+{
+    ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    tj = t - ti * (ti + 1) / 2;
+}
+
+// One BT x BT tile (ti, tj) of C[m x nn] -= A[m x k] B[nn x k]^T; LOWER
+// keeps only entries on or below the diagonal.  Thread (tx, ty) owns
+// entries (tx + 16i, ty + 16j) of the tile.
 template <typename T, bool LOWER, int BT>
-__global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
-                                                               const T *__restrict__ A, int64_t lda,
-                                                               const T *__restrict__ B, int64_t ldb, T *C,
-                                                               int64_t ldc, const int64_t *info)
+__device__ inline void gemm_nt_minus_body(int64_t m, int64_t nn, int k, const T *__restrict__ A, int64_t lda,
+                                          const T *__restrict__ B, int64_t ldb, T *C, int64_t ldc, int64_t ti,
+                                          int64_t tj)
 {
     constexpr int KC = 32, RT = BT / 16;
     __shared__ T As[KC][BT];
     __shared__ T Bs[KC][BT];
-    if (info && *info != 0) return;
-    int64_t ti, tj;
-    if (LOWER) {
-        int64_t t = blockIdx.x;
-        ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-        while (ti * (ti + 1) / 2 > t) --ti;
-        tj = t - ti * (ti + 1) / 2;
-    } else {
-        ti = blockIdx.x;
-        tj = blockIdx.y;
-    }
     const int64_t r0 = ti * BT, c0 = tj * BT;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     T acc[RT][RT] = {};
@@ -172,6 +266,25 @@ __global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_
             int64_t r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
             if (r < m && c < nn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
         }
+}
+
+// C[m x nn] -= A[m x k] B[nn x k]^T.  LOWER: C is square and only its lower
+// triangle is updated; the grid enumerates the lower BT x BT tiles.
+template <typename T, bool LOWER, int BT>
+__global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
+                                                               const T *__restrict__ A, int64_t lda,
+                                                               const T *__restrict__ B, int64_t ldb, T *C,
+                                                               int64_t ldc, const int64_t *info)
+{
+    if (info && *info != 0) return;
+    int64_t ti, tj;
+    if (LOWER) {
+        tri_index(blockIdx.x, ti, tj);
+    } else {
+        ti = blockIdx.x;
+        tj = blockIdx.y;
+    }
+    gemm_nt_minus_body<T, LOWER, BT>(m, nn, k, A, lda, B, ldb, C, ldc, ti, tj);
 }
 
 template <typename T, int ROWS>

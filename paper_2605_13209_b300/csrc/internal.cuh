@@ -46,6 +46,13 @@ struct Carver {
     char *base;
     size_t off = 0;
     explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    // Reserve `bytes` (256-byte aligned); returns the offset from the base.
+    size_t reserve(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        const size_t o = off;
+        off += bytes;
+        return o;
+    }
     template <typename T>
     T *take(size_t count) {
         off = (off + 255) & ~size_t(255);
@@ -58,6 +65,9 @@ struct Carver {
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 
 cudaEvent_t take_event(gpch_ctx *ctx);
+
+// Free the batched solver's cached plans of a context (batched.cu).
+void batched_release(gpch_ctx *ctx);
 
 // Records an event pair around the launches made while it is alive, when
 // timing is on; `work` is their algorithmic flops (or bytes).

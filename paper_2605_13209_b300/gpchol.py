@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgpchol.so")
 GPCH_OK, GPCH_INVALID_ARG, GPCH_NOT_SPD, GPCH_NOT_CONVERGED, GPCH_OOM_BUDGET, GPCH_TIMEOUT, GPCH_CUDA_ERROR = range(7)
 GPCH_F64, GPCH_F32 = 0, 1
 (PHASE_SE, PHASE_DIAG, PHASE_PANEL, PHASE_TRAILING, PHASE_SOLVE, PHASE_CG_MATVEC, PHASE_CG_VECTOR,
- PHASE_MIXED_TRAILING) = range(8)
+ PHASE_MIXED_TRAILING, PHASE_BATCHED) = range(9)
 GPCH_PREC_FP64, GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 = 0, 1, 2
 
 _i64 = ctypes.c_int64
@@ -37,6 +37,11 @@ class GpchError(RuntimeError):
 
 class CGStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("relres_max", ctypes.c_double)]
+
+
+class System(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("nrhs", ctypes.c_int32)]
 
 
 class RefineStats(ctypes.Structure):
@@ -74,6 +79,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_launch_count.restype = _i64
         L.gpch_cg_solve_noalloc.argtypes = [_i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int,
                                              _vp, ctypes.POINTER(CGStats)]
+        L.gpch_batched_solve.argtypes = [_vp, _int, ctypes.POINTER(System), _vp, ctypes.POINTER(_i64)]
         L.gpch_syrk_lowprec.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_chol_factor_mixed.argtypes = [_vp, _i64, _int, _vp, _i64, _int, _dbl, _vp, _i64, _vp,
                                              ctypes.POINTER(_i64)]
@@ -81,7 +87,8 @@ def lib() -> ctypes.CDLL:
                                          _vp, ctypes.POINTER(RefineStats)]
         for name in ("gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
-                     "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc"):
+                     "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
+                     "gpch_batched_solve"):
             getattr(L, name).restype = _int
         _lib = L
     return _lib
@@ -326,3 +333,22 @@ def solve_refined(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, prec="split
     if raise_on_error:
         ctx.check(st)
     return RefineResult(stats.iterations, stats.factor_attempts, stats.shift, stats.backward_error_max, st)
+
+
+def batched_solve(As, Bs, ctx: Context | None = None, stream=None, raise_on_not_spd: bool = True):
+    """A10: factor (in place) and solve a batch of FP64 systems.  As, Bs:
+    lists of column-major float64 CUDA tensors (n x n and n x nrhs); each B
+    is overwritten by its solution.  Returns the list of info values."""
+    ctx = ctx or default_context()
+    if len(As) != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    arr = (System * len(As))()
+    for i, (A, B) in enumerate(zip(As, Bs)):
+        _check_cuda(A, torch.float64)
+        _check_cuda(B, torch.float64)
+        arr[i] = System(A.shape[0], A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), B.shape[1])
+    info = (_i64 * max(len(As), 1))()
+    st = lib().gpch_batched_solve(ctx.handle, len(As), arr, _stream(stream), info)
+    if not (st == GPCH_NOT_SPD and not raise_on_not_spd):
+        ctx.check(st)
+    return [int(info[i]) for i in range(len(As))]
