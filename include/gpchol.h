@@ -249,6 +249,82 @@ typedef struct gpch_system {
 gpch_status gpch_batched_solve(gpch_ctx *ctx, int count, const gpch_system *systems, void *stream,
                                int64_t *info);
 
+/* -------------------------------------------------- A11: serving loop */
+
+typedef struct gpch_server gpch_server;
+
+typedef struct gpch_server_opts {
+    size_t hbm_budget;       /* device bytes that admitted, unfinished requests
+                                may hold (0 = no cap)                              */
+    int32_t lanes;           /* GPU lanes: host threads, each with its own
+                                context and CUDA stream (1..32)                    */
+    int32_t batch_max_count; /* at most this many requests per batched launch      */
+    int64_t batch_max_n;     /* requests with n <= batch_max_n go through the
+                                batched FP64 path (gpch_batched_solve's kernels)   */
+    gpch_prec solo_prec;     /* larger requests: GPCH_PREC_FP64 (factor + solve)
+                                or a mixed precision (gpch_solve_refined)          */
+    double bwd_tol;          /* backward-error target of the refined path          */
+} gpch_server_opts;
+
+/* One GP solve request; every pointer is HOST memory that the caller keeps
+ * alive (and Xout untouched) until the request completes. */
+typedef struct gpch_request {
+    int64_t n;
+    int32_t d;               /* point dimension, 1..64                             */
+    int32_t nrhs;
+    const double *X;         /* n x d points, row-major                            */
+    double sf2, ell, sn2;    /* squared-exponential hyper-parameters               */
+    const double *B;         /* n x nrhs right-hand sides, column-major            */
+    double *Xout;            /* n x nrhs solution, column-major (written on completion) */
+} gpch_request;
+
+typedef struct gpch_result {
+    gpch_status status;
+    int32_t path;            /* 1 batched FP64, 2 solo mixed refined, 3 solo FP64  */
+    int32_t iterations;      /* refinement iterations (path 2)                     */
+    double backward_error;   /* final backward error reported by the path 2 solve  */
+    double latency_ms;       /* completion minus submission                        */
+    double queue_ms;         /* start of GPU work minus submission                 */
+} gpch_result;
+
+typedef struct gpch_server_stats {
+    int64_t completed, failed, batches, batched_requests;
+    size_t peak_reserved_bytes;
+    double p50_ms, p99_ms, max_ms;   /* latency percentiles of completed requests */
+    double solves_per_s;             /* completed / (last completion - first submit) */
+} gpch_server_stats;
+
+/* Serving loop with continuous batching (the scope's serving pattern; the
+ * paper has no serving layer).  Each request builds its SE matrix (A1) on
+ * the device and is solved there.  A dispatcher admits queued requests in
+ * arrival order, first fit against hbm_budget, whenever a lane is free:
+ * up to batch_max_count small requests (n <= batch_max_n) are solved
+ * together by one batched FP64 launch sequence, a larger request runs alone
+ * on its lane.  Lanes run concurrently on their own streams, so requests
+ * that arrive while others are on the GPU start as soon as a lane and
+ * memory are free and their work overlaps.  A request's arithmetic depends
+ * only on its own data and the path its n selects.  Each lane keeps its
+ * largest device buffers and workspace until gpch_server_destroy. */
+gpch_status gpch_server_create(int device, const gpch_server_opts *opts, gpch_server **out);
+
+/* Queue a request (copied; its host buffers are not).  Returns
+ * GPCH_OOM_BUDGET if it could never fit the budget. */
+gpch_status gpch_server_submit(gpch_server *srv, const gpch_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_s for a request; on completion fills *res (may be NULL),
+ * forgets the ticket and returns the request's status (GPCH_TIMEOUT if it
+ * is still running; the ticket stays valid). */
+gpch_status gpch_server_wait(gpch_server *srv, uint64_t ticket, double timeout_s, gpch_result *res);
+
+/* Non-blocking: *done = 1 and *res filled once the request completed. */
+gpch_status gpch_server_poll(gpch_server *srv, uint64_t ticket, int *done, gpch_result *res);
+
+gpch_status gpch_server_get_stats(gpch_server *srv, gpch_server_stats *out);
+
+/* Stop the lanes after their current work; queued requests are dropped.
+ * No other call on `srv` may be in progress. */
+gpch_status gpch_server_destroy(gpch_server *srv);
+
 /* --------------------------- A4 (mixed): tensor-core trailing update */
 
 /* C -= P P^T on the lower triangle of the m x m FP32 matrix C (ldc), with

@@ -14,6 +14,7 @@
 // systems.
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "dense_fp64.cuh"
@@ -184,6 +185,7 @@ struct PlanCache {
 };
 
 std::map<gpch_ctx *, PlanCache> g_caches;   // per context
+std::mutex g_caches_mu;
 
 void free_plan(BatchPlan &p)
 {
@@ -220,70 +222,94 @@ HostTables::Step add_step(HostTables &h, int count, const int64_t *ns, F tasks_o
     return st;
 }
 
-gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, BatchPlan &plan, cudaStream_t st)
-{
-    std::vector<int64_t> ns(count);
-    int64_t kmax = 0;
-    for (int s = 0; s < count; ++s) {
-        ns[s] = systems[s].n;
-        const int64_t nb = (ns[s] + LEAF - 1) / LEAF;
-        if (nb > kmax) kmax = nb;
-    }
+// Sizes-only plan of a batch: the step tables and the device layout.
+struct Layout {
     HostTables h;
-    for (int64_t k = 0; k < kmax; ++k) {
-        h.potrf.push_back(add_step(h, count, ns.data(), [&](int64_t n) { return n > k * LEAF ? 1 : 0; }));
-        h.trsm.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+    std::vector<int64_t> ns;
+    int64_t kmax = 0;
+    size_t o_sys = 0, o_info = 0, o_tsys = 0, o_pref = 0, bytes = 0;
+    std::vector<size_t> o_linv, o_y;
+};
+
+Layout make_layout(int count, const gpch_system *systems)
+{
+    Layout L;
+    L.ns.resize(count);
+    for (int s = 0; s < count; ++s) {
+        L.ns[s] = systems[s].n;
+        const int64_t nb = (L.ns[s] + LEAF - 1) / LEAF;
+        if (nb > L.kmax) L.kmax = nb;
+    }
+    HostTables &h = L.h;
+    const int64_t *ns = L.ns.data();
+    for (int64_t k = 0; k < L.kmax; ++k) {
+        h.potrf.push_back(add_step(h, count, ns, [&](int64_t n) { return n > k * LEAF ? 1 : 0; }));
+        h.trsm.push_back(add_step(h, count, ns, [&](int64_t n) {
             const int64_t m = n - (k + 1) * LEAF;
             return m > 0 ? (m + 63) / 64 : 0;
         }));
-        h.gemm.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+        h.gemm.push_back(add_step(h, count, ns, [&](int64_t n) {
             const int64_t m = n - (k + 1) * LEAF;
             const int64_t T = m > 0 ? (m + 63) / 64 : 0;
             return T * (T + 1) / 2;
         }));
-        h.fwd.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+        h.fwd.push_back(add_step(h, count, ns, [&](int64_t n) {
             if (n <= k * LEAF) return (int64_t)0;
             const int64_t below = n - (k + 1) * LEAF;
             return below > 0 ? (below + 255) / 256 : (int64_t)1;
         }));
-        h.bwd.push_back(add_step(h, count, ns.data(), [&](int64_t n) {
+        h.bwd.push_back(add_step(h, count, ns, [&](int64_t n) {
             if (n <= k * LEAF) return (int64_t)0;
             return k > 0 ? k : (int64_t)1;   // k*64 columns above, 64 per CTA
         }));
     }
-    // device layout: systems, info, tables, then per-system Linv and Y
     gpch::Carver dry(nullptr);
-    const size_t o_sys = dry.reserve(count * sizeof(BSys));
-    const size_t o_info = dry.reserve(count * sizeof(int64_t));
-    const size_t o_tsys = dry.reserve(h.sys.size() * sizeof(int));
-    const size_t o_pref = dry.reserve(h.pref.size() * sizeof(int64_t));
-    std::vector<size_t> o_linv(count), o_y(count);
+    L.o_sys = dry.reserve(count * sizeof(BSys));
+    L.o_info = dry.reserve(count * sizeof(int64_t));
+    L.o_tsys = dry.reserve(h.sys.size() * sizeof(int));
+    L.o_pref = dry.reserve(h.pref.size() * sizeof(int64_t));
+    L.o_linv.resize(count);
+    L.o_y.resize(count);
     for (int s = 0; s < count; ++s) {
-        o_linv[s] = dry.reserve((size_t)((ns[s] + LEAF - 1) / LEAF) * LEAF * LEAF * sizeof(double));
-        o_y[s] = dry.reserve((size_t)ns[s] * systems[s].nrhs * sizeof(double));
+        L.o_linv[s] = dry.reserve((size_t)((ns[s] + LEAF - 1) / LEAF) * LEAF * LEAF * sizeof(double));
+        L.o_y[s] = dry.reserve((size_t)ns[s] * systems[s].nrhs * sizeof(double));
     }
-    if (ctx->budget && ctx->ws_bytes + dry.off > ctx->budget)
-        return gpch::fail(ctx, GPCH_OOM_BUDGET, "batch plan of %zu bytes exceeds the HBM budget", dry.off);
-    GPCH_CUDA(ctx, cudaMalloc(&plan.dev, dry.off));
-    plan.bytes = dry.off;
-    char *base = static_cast<char *>(plan.dev);
-    plan.d_sys = reinterpret_cast<BSys *>(base + o_sys);
-    plan.d_info = reinterpret_cast<int64_t *>(base + o_info);
-    int *d_tsys = reinterpret_cast<int *>(base + o_tsys);
-    int64_t *d_pref = reinterpret_cast<int64_t *>(base + o_pref);
-    std::vector<BSys> hs(count);
-    for (int s = 0; s < count; ++s) {
-        hs[s] = BSys{systems[s].A, systems[s].lda, ns[s], systems[s].B, systems[s].ldb, systems[s].nrhs,
-                     reinterpret_cast<double *>(base + o_linv[s]), reinterpret_cast<double *>(base + o_y[s]),
-                     plan.d_info + s};
-    }
-    GPCH_CUDA(ctx, cudaMemcpyAsync(plan.d_sys, hs.data(), count * sizeof(BSys), cudaMemcpyHostToDevice, st));
-    if (!h.sys.empty())
-        GPCH_CUDA(ctx, cudaMemcpyAsync(d_tsys, h.sys.data(), h.sys.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    GPCH_CUDA(ctx, cudaMemcpyAsync(d_pref, h.pref.data(), h.pref.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
-                                   st));
-    GPCH_CUDA(ctx, cudaStreamSynchronize(st));   // host vectors go out of scope
+    L.bytes = dry.off;
+    return L;
+}
 
+struct DevTables {
+    BSys *sys;
+    int64_t *info;
+    int *tsys;
+    int64_t *pref;
+};
+
+// Copy descriptors and tables to `base` (L.bytes of device memory) on st.
+gpch_status upload(gpch_ctx *ctx, const Layout &L, int count, const gpch_system *systems, char *base, DevTables &d,
+                   cudaStream_t st)
+{
+    d.sys = reinterpret_cast<BSys *>(base + L.o_sys);
+    d.info = reinterpret_cast<int64_t *>(base + L.o_info);
+    d.tsys = reinterpret_cast<int *>(base + L.o_tsys);
+    d.pref = reinterpret_cast<int64_t *>(base + L.o_pref);
+    std::vector<BSys> hs(count);
+    for (int s = 0; s < count; ++s)
+        hs[s] = BSys{systems[s].A, systems[s].lda, L.ns[s], systems[s].B, systems[s].ldb, systems[s].nrhs,
+                     reinterpret_cast<double *>(base + L.o_linv[s]), reinterpret_cast<double *>(base + L.o_y[s]),
+                     d.info + s};
+    GPCH_CUDA(ctx, cudaMemcpyAsync(d.sys, hs.data(), count * sizeof(BSys), cudaMemcpyHostToDevice, st));
+    if (!L.h.sys.empty())
+        GPCH_CUDA(ctx, cudaMemcpyAsync(d.tsys, L.h.sys.data(), L.h.sys.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                       st));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(d.pref, L.h.pref.data(), L.h.pref.size() * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));   // the host vectors go out of scope
+    return GPCH_OK;
+}
+
+gpch_status set_attrs(gpch_ctx *ctx)
+{
     static bool attr_done = false;
     if (!attr_done) {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(bpotrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -292,36 +318,67 @@ gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, Bat
                                             (int)BTRSM_SMEM));
         attr_done = true;
     }
-    auto table = [&](const HostTables::Step &x) { return StepTable{d_tsys + x.sys_off, d_pref + x.pref_off, x.cnt}; };
+    return GPCH_OK;
+}
 
-    // capture the whole batch as one graph
+// Enqueue the whole batch on st (directly or into a capturing stream);
+// returns the number of kernel launches.
+int64_t enqueue_batch(const Layout &L, const DevTables &d, int count, cudaStream_t st)
+{
+    const HostTables &h = L.h;
+    auto table = [&](const HostTables::Step &x) { return StepTable{d.tsys + x.sys_off, d.pref + x.pref_off, x.cnt}; };
+    int64_t launches = 0;
+    cudaMemsetAsync(d.info, 0, count * sizeof(int64_t), st);
+    for (int64_t k = 0; k < L.kmax; ++k) {
+        if (h.potrf[k].tasks) {
+            bpotrf_kernel<<<(unsigned)h.potrf[k].tasks, 256, BPOTRF_SMEM, st>>>(d.sys, table(h.potrf[k]), (int)k);
+            ++launches;
+        }
+        if (h.trsm[k].tasks) {
+            btrsm_kernel<<<(unsigned)h.trsm[k].tasks, 256, BTRSM_SMEM, st>>>(d.sys, table(h.trsm[k]), (int)k);
+            ++launches;
+        }
+        if (h.gemm[k].tasks) {
+            bgemm_kernel<<<(unsigned)h.gemm[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm[k]), (int)k);
+            ++launches;
+        }
+    }
+    for (int64_t k = 0; k < L.kmax; ++k)
+        if (h.fwd[k].tasks) {
+            bfwd_kernel<<<(unsigned)h.fwd[k].tasks, 256, 0, st>>>(d.sys, table(h.fwd[k]), (int)k);
+            ++launches;
+        }
+    for (int64_t k = L.kmax - 1; k >= 0; --k)
+        if (h.bwd[k].tasks) {
+            bbwd_kernel<<<(unsigned)h.bwd[k].tasks, 256, 0, st>>>(d.sys, table(h.bwd[k]), (int)k);
+            ++launches;
+        }
+    return launches;
+}
+
+gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, BatchPlan &plan, cudaStream_t st)
+{
+    Layout L = make_layout(count, systems);
+    if (ctx->budget && ctx->ws_bytes + L.bytes > ctx->budget)
+        return gpch::fail(ctx, GPCH_OOM_BUDGET, "batch plan of %zu bytes exceeds the HBM budget", L.bytes);
+    GPCH_CUDA(ctx, cudaMalloc(&plan.dev, L.bytes));
+    plan.bytes = L.bytes;
+    DevTables d;
+    gpch_status s0 = upload(ctx, L, count, systems, static_cast<char *>(plan.dev), d, st);
+    if (s0 != GPCH_OK) {
+        free_plan(plan);
+        return s0;
+    }
+    plan.d_sys = d.sys;
+    plan.d_info = d.info;
+    GPCH_CHECK(set_attrs(ctx));
     cudaStream_t cs;
     GPCH_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int64_t launches = 0;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(plan.d_info, 0, count * sizeof(int64_t), cs);
-        for (int64_t k = 0; k < kmax; ++k) {
-            if (h.potrf[k].tasks)
-                bpotrf_kernel<<<(unsigned)h.potrf[k].tasks, 256, BPOTRF_SMEM, cs>>>(plan.d_sys, table(h.potrf[k]),
-                                                                                   (int)k);
-            if (h.trsm[k].tasks)
-                btrsm_kernel<<<(unsigned)h.trsm[k].tasks, 256, BTRSM_SMEM, cs>>>(plan.d_sys, table(h.trsm[k]), (int)k);
-            if (h.gemm[k].tasks)
-                bgemm_kernel<<<(unsigned)h.gemm[k].tasks, 256, 0, cs>>>(plan.d_sys, table(h.gemm[k]), (int)k);
-            launches += (h.potrf[k].tasks > 0) + (h.trsm[k].tasks > 0) + (h.gemm[k].tasks > 0);
-        }
-        for (int64_t k = 0; k < kmax; ++k)
-            if (h.fwd[k].tasks) {
-                bfwd_kernel<<<(unsigned)h.fwd[k].tasks, 256, 0, cs>>>(plan.d_sys, table(h.fwd[k]), (int)k);
-                ++launches;
-            }
-        for (int64_t k = kmax - 1; k >= 0; --k)
-            if (h.bwd[k].tasks) {
-                bbwd_kernel<<<(unsigned)h.bwd[k].tasks, 256, 0, cs>>>(plan.d_sys, table(h.bwd[k]), (int)k);
-                ++launches;
-            }
+        launches = enqueue_batch(L, d, count, cs);
         e = cudaStreamEndCapture(cs, &graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&plan.exec, graph, 0);
@@ -335,7 +392,7 @@ gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, Bat
     plan.count = count;
     plan.launches = launches;
     plan.flops.resize(count);
-    for (int s = 0; s < count; ++s) plan.flops[s] = ns[s] * ns[s] * ns[s] / 3;
+    for (int s = 0; s < count; ++s) plan.flops[s] = L.ns[s] * L.ns[s] * L.ns[s] / 3;
     return GPCH_OK;
 }
 
@@ -343,8 +400,35 @@ gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, Bat
 
 namespace gpch {
 
+// A batch launched directly on `st` with its tables in the context's
+// workspace (no graph, nothing cached): the form a serving loop uses for
+// batches that are each seen once.  info: host array of count entries.
+gpch_status batched_solve_direct(gpch_ctx *ctx, int count, const gpch_system *systems, cudaStream_t st,
+                                 int64_t *info)
+{
+    Layout L = make_layout(count, systems);
+    GPCH_CHECK(ws_reserve(ctx, L.bytes));
+    DevTables d;
+    GPCH_CHECK(upload(ctx, L, count, systems, static_cast<char *>(ctx->ws), d, st));
+    GPCH_CHECK(set_attrs(ctx));
+    double work = 0.0;
+    for (int s = 0; s < count; ++s) work += (double)L.ns[s] * L.ns[s] * L.ns[s] / 3.0;
+    {
+        PhaseScope ph(ctx, GPCH_PHASE_BATCHED, st, work);
+        ctx->launches += enqueue_batch(L, d, count, st);
+    }
+    GPCH_LAUNCH_CHECK(ctx);
+    --ctx->launches;
+    std::vector<int64_t> h(count);
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h.data(), d.info, count * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GPCH_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int s = 0; s < count; ++s) info[s] = h[s];
+    return GPCH_OK;
+}
+
 void batched_release(gpch_ctx *ctx)
 {
+    std::lock_guard<std::mutex> lock(g_caches_mu);
     auto it = g_caches.find(ctx);
     if (it == g_caches.end()) return;
     for (auto &kv : it->second.plans) free_plan(kv.second);
@@ -374,6 +458,7 @@ extern "C" gpch_status gpch_batched_solve(gpch_ctx *ctx, int count, const gpch_s
         const gpch_system &y = systems[s];
         key.v.insert(key.v.end(), {y.n, (int64_t)(uintptr_t)y.A, y.lda, (int64_t)(uintptr_t)y.B, y.ldb, y.nrhs});
     }
+    std::lock_guard<std::mutex> lock(g_caches_mu);
     PlanCache &cache = g_caches[ctx];
     auto it = cache.plans.find(key);
     if (it == cache.plans.end()) {

@@ -69,6 +69,10 @@ cudaEvent_t take_event(gpch_ctx *ctx);
 // Free the batched solver's cached plans of a context (batched.cu).
 void batched_release(gpch_ctx *ctx);
 
+// Batched FP64 solve launched directly, tables in the context workspace.
+gpch_status batched_solve_direct(gpch_ctx *ctx, int count, const gpch_system *systems, cudaStream_t st,
+                                 int64_t *info);
+
 // Records an event pair around the launches made while it is alive, when
 // timing is on; `work` is their algorithmic flops (or bytes).
 struct PhaseScope {

@@ -44,6 +44,29 @@ class System(ctypes.Structure):
                 ("ldb", ctypes.c_int64), ("nrhs", ctypes.c_int32)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("lanes", ctypes.c_int32), ("batch_max_count", ctypes.c_int32),
+                ("batch_max_n", ctypes.c_int64), ("solo_prec", ctypes.c_int), ("bwd_tol", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("X", ctypes.c_void_p),
+                ("sf2", ctypes.c_double), ("ell", ctypes.c_double), ("sn2", ctypes.c_double), ("B", ctypes.c_void_p),
+                ("Xout", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("path", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("backward_error", ctypes.c_double), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batched_requests", ctypes.c_int64), ("peak_reserved_bytes", ctypes.c_size_t),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double)]
+
+
 class RefineStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("factor_attempts", ctypes.c_int32), ("shift", ctypes.c_double),
                 ("backward_error_max", ctypes.c_double)]
@@ -80,6 +103,12 @@ def lib() -> ctypes.CDLL:
         L.gpch_cg_solve_noalloc.argtypes = [_i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int,
                                              _vp, ctypes.POINTER(CGStats)]
         L.gpch_batched_solve.argtypes = [_vp, _int, ctypes.POINTER(System), _vp, ctypes.POINTER(_i64)]
+        L.gpch_server_create.argtypes = [_int, ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)]
+        L.gpch_server_submit.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+        L.gpch_server_wait.argtypes = [_vp, ctypes.c_uint64, _dbl, ctypes.POINTER(Result)]
+        L.gpch_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(Result)]
+        L.gpch_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+        L.gpch_server_destroy.argtypes = [_vp]
         L.gpch_syrk_lowprec.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_chol_factor_mixed.argtypes = [_vp, _i64, _int, _vp, _i64, _int, _dbl, _vp, _i64, _vp,
                                              ctypes.POINTER(_i64)]
@@ -88,7 +117,8 @@ def lib() -> ctypes.CDLL:
         for name in ("gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
-                     "gpch_batched_solve"):
+                     "gpch_batched_solve", "gpch_server_create", "gpch_server_submit", "gpch_server_wait",
+                     "gpch_server_poll", "gpch_server_get_stats", "gpch_server_destroy"):
             getattr(L, name).restype = _int
         _lib = L
     return _lib
@@ -352,3 +382,62 @@ def batched_solve(As, Bs, ctx: Context | None = None, stream=None, raise_on_not_
     if not (st == GPCH_NOT_SPD and not raise_on_not_spd):
         ctx.check(st)
     return [int(info[i]) for i in range(len(As))]
+
+
+class Server:
+    """A11: serving loop with continuous batching (gpch_server_*).  Requests
+    are host numpy arrays; the binding keeps them alive until collected."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, lanes: int = 4, batch_max_count: int = 32,
+                 batch_max_n: int = 2048, solo_prec="split_bf16", bwd_tol: float = 1e-12):
+        import numpy as np  # noqa: F401
+        prec = GPCH_PREC_FP64 if solo_prec in ("fp64", GPCH_PREC_FP64) else _PREC[solo_prec]
+        self._opts = ServerOpts(int(hbm_budget), int(lanes), int(batch_max_count), int(batch_max_n), prec,
+                                float(bwd_tol))
+        self._h = _vp()
+        st = lib().gpch_server_create(int(device), ctypes.byref(self._opts), ctypes.byref(self._h))
+        if st != GPCH_OK:
+            raise GpchError(st, "gpch_server_create failed")
+        self._keep = {}
+
+    def submit(self, X, B, sf2: float, ell: float, sn2: float) -> int:
+        import numpy as np
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        B = np.asfortranarray(np.atleast_2d(np.asarray(B, dtype=np.float64).T).T)
+        out = np.zeros_like(B, order="F")
+        n, d = X.shape
+        req = Request(n, d, B.shape[1], X.ctypes.data, sf2, ell, sn2, B.ctypes.data, out.ctypes.data)
+        t = ctypes.c_uint64(0)
+        st = lib().gpch_server_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        if st != GPCH_OK:
+            raise GpchError(st, "gpch_server_submit failed")
+        self._keep[int(t.value)] = (X, B, out)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        """Returns (solution n x nrhs, result dict)."""
+        res = Result()
+        st = lib().gpch_server_wait(self._h, ticket, timeout_s, ctypes.byref(res))
+        if st == GPCH_TIMEOUT:
+            raise GpchError(st, "request still running")
+        _, _, out = self._keep.pop(ticket)
+        return out, {"status": res.status, "path": res.path, "iterations": res.iterations,
+                     "backward_error": res.backward_error, "latency_ms": res.latency_ms, "queue_ms": res.queue_ms}
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        st = lib().gpch_server_get_stats(self._h, ctypes.byref(s))
+        if st != GPCH_OK:
+            raise GpchError(st, "gpch_server_get_stats failed")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().gpch_server_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
