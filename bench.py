@@ -207,6 +207,10 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-nmax", type=int, default=8192)
+    ap.add_argument("--serve-rates", default="20,80")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -341,6 +345,84 @@ def main():
               "matvec_roofline": roofline_of("cg_matvec", *mv, n, 1, pk),
               "what": "Algorithm 1 (left), FP64 full matrix, one RHS, fixed iteration count"}
 
+    # ---------------------------------------------------------- batched leg
+    batched = None
+    if args.batch_count > 0:
+        spec = inputs.batch_spec(count=args.batch_count, nmin=256, nmax=4096, seed=4)
+        Ab, Bb, Bb0, Xp = [], [], [], []
+        for k in range(args.batch_count):
+            sk = spec.system(k, d=8) if rank == 0 else inputs.gp_system(int(spec.ns[k]), 8, float(spec.ells[k]),
+                                                                         float(spec.sn2s[k]), seed=7 + 97 * k + rank)
+            Xp.append((torch.from_numpy(sk.X).cuda(), sk.sf2, sk.ell, sk.sn2))
+            Ab.append(gpchol.colmajor(sk.n, sk.n))
+            Bb0.append(gpchol.as_colmajor(torch.from_numpy(sk.B).cuda()))
+            Bb.append(gpchol.colmajor(sk.n, 1))
+
+        def refill():
+            for (xd, sf2, ell, sn2), a, b, b0 in zip(Xp, Ab, Bb, Bb0):
+                gpchol.se_matrix(xd, sf2, ell, sn2, A=a, ctx=ctx)
+                b.copy_(b0)
+
+        bflops = float(sum(int(n) ** 3 for n in spec.ns)) / 3.0
+        refill()
+        gpchol.batched_solve(Ab, Bb, ctx=ctx)        # first call captures the graph
+        times = []
+        for _ in range(3):
+            refill()
+            torch.cuda.synchronize()
+            ctx.timing_enable(True)
+            gpchol.batched_solve(Ab, Bb, ctx=ctx)
+            times.append(ctx.timing_read(gpchol.PHASE_BATCHED)[0])
+            ctx.timing_enable(False)
+        bms = max_over_ranks(min(times))
+        xk = Bb[0][:, 0]
+        A0b = gpchol.se_matrix(Xp[0][0], Xp[0][1], Xp[0][2], Xp[0][3], ctx=ctx)
+        rk = Bb0[0][:, 0] - torch.mv(A0b, xk)
+        bwd_b = float(rk.abs().max() / (A0b.abs().sum(dim=1).max() * xk.abs().max() + Bb0[0].abs().max()))
+        batched = {"systems": args.batch_count, "n_range": [int(spec.ns.min()), int(spec.ns.max())],
+                   "ms_per_batch": round(bms, 2), "gflops": round(world * bflops / (bms / 1e3) / 1e9, 2),
+                   "frac_of_fp64_peak": round(bflops / (bms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
+                   "backward_error_system0": bwd_b,
+                   "what": "FP64 batched factor + solve of 256 SE systems, n log-uniform [256, 4096], one graph launch"}
+        del Ab, Bb, Bb0, Xp
+
+    # ---------------------------------------------------------- serving leg
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        serving = {}
+        rates = [float(r) for r in args.serve_rates.split(",") if r]
+        for label, solo in (("mixed", "split_bf16"), ("fp64_only", "fp64")):
+            for rate in rates:
+                rs = inputs.request_stream(count=args.serve_requests, rate_per_s=rate, nmin=512, nmax=args.serve_nmax)
+                reqs = []
+                for i in range(args.serve_requests):
+                    nq = int(rs.ns[i])
+                    reqs.append((inputs.points(nq, 8, int(rs.seeds[i])), inputs.rhs(nq, int(rs.nrhs[i]),
+                                 int(rs.seeds[i]) + 1), float(rs.ells[i]), float(rs.sn2s[i])))
+                srv = gpchol.Server(local, hbm_budget=160 << 30, lanes=4, batch_max_count=32, batch_max_n=2048,
+                                    solo_prec=solo)
+                t0 = time.perf_counter()
+                tickets = []
+                for i, (Xr, Br, ell, sn2) in enumerate(reqs):
+                    delay = t0 + float(rs.arrival_s[i]) - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    tickets.append(srv.submit(Xr, Br, 1.0, ell, sn2))
+                worst = 0.0
+                for t in tickets:
+                    _, r = srv.wait(t)
+                    worst = max(worst, r["backward_error"])
+                st = srv.stats()
+                srv.close()
+                serving[f"{label}@{rate:g}/s"] = {
+                    "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+                    "solves_per_s": round(st["solves_per_s"], 2), "completed": st["completed"],
+                    "failed": st["failed"], "batches": st["batches"], "batched_requests": st["batched_requests"],
+                    "max_refined_backward_error": worst}
+        serving["what"] = (f"{args.serve_requests} Poisson requests per rate, n log-uniform [512, {args.serve_nmax}], "
+                           "1-8 RHS, 160 GB budget, 4 lanes, n <= 2048 batched (FP64); larger solo: mixed "
+                           "split-bf16 refined vs FP64-only")
+
     # ---------------------------------------------------------- e2e
     Xh = torch.from_numpy(sysm.X).pin_memory()
     bh = torch.from_numpy(np.ascontiguousarray(sysm.B[:, 0])).pin_memory()
@@ -394,6 +476,8 @@ def main():
                    "backward_error_lib": res.backward_error_max},
         "fp64": fp64,
         "cg": cg,
+        "batched": batched,
+        "serving": serving,
         "phases": phases,
         "check": {"backward_error": bwd},
     }

@@ -368,7 +368,9 @@ typedef struct gpch_refine_stats {
  * most 9 attempts), then preconditioned CG with M = Lt Lt^T in FP64 (A, x,
  * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
  * from x_0 = 0, replacing the recurrence residual by b - A x every 50
- * iterations and whenever the recurrence estimate reaches bwd_tol.
+ * iterations and whenever an estimate of the backward error from the
+ * recurrence residual (||r||_2 / sqrt(n) in place of ||r||_inf, scaled by
+ * the truth-to-estimate ratio seen at the previous check) reaches bwd_tol.
  * A: device FP64 full symmetric n x n (lda).  B: device n x nrhs (ldb).
  * X: device n x nrhs (ldx), overwritten.  Workspace: about 4 n^2 bytes.
  * stats (host, may be NULL).  Synchronizes `stream`.  Returns GPCH_NOT_SPD

@@ -659,6 +659,13 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     int nactive = 0;
     for (int c = 0; c < nrhs; ++c) nactive += h_active[c];
     const double eps2 = 1e-30;
+    // The recurrence gives ||r||_2; ||r||_2 / sqrt(n) <= ||r||_inf <= ||r||_2.
+    // The true residual is checked once the lower estimate, scaled by the
+    // ratio of truth to estimate seen at the last failed check, meets tol.
+    double ratio[MAXRHS];
+    for (int c = 0; c < MAXRHS; ++c) ratio[c] = 1.0;
+    double est_at_check[MAXRHS] = {0};
+    const double inv_sqrt_n = 1.0 / sqrt((double)n);
     int it = 0;
     while (nactive > 0 && it < maxit) {
         GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
@@ -668,10 +675,11 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
         GPCH_CUDA(ctx, cudaMemcpyAsync(h, ex, 2 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
         GPCH_CUDA(ctx, cudaStreamSynchronize(s));
         bool replace = (R > 0 && it % R == 0);
-        for (int c = 0; c < nrhs && !replace; ++c) {
+        for (int c = 0; c < nrhs; ++c) {
             if (!h_active[c]) continue;
-            const double est = sqrt(h[c]) / (anorm * h[MAXRHS + c] + binf[c]);
-            if (est <= bwd_tol || h[c] <= eps2 * bb[c]) replace = true;
+            const double est = sqrt(h[c]) * inv_sqrt_n / (anorm * h[MAXRHS + c] + binf[c]);
+            est_at_check[c] = est;
+            if (est * ratio[c] <= bwd_tol || h[c] <= eps2 * bb[c]) replace = true;
         }
         if (replace) {
             GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
@@ -686,6 +694,8 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
                 const double den = anorm * h[MAXRHS + c] + binf[c];
                 res.bwd[c] = den > 0.0 ? h[2 * MAXRHS + c] / den : 0.0;
                 if (res.bwd[c] <= bwd_tol) h_active[c] = 0;
+                else if (est_at_check[c] > 0.0 && res.bwd[c] / est_at_check[c] > ratio[c])
+                    ratio[c] = res.bwd[c] / est_at_check[c];
                 nactive += h_active[c];
             }
             GPCH_CUDA(ctx, cudaMemcpyAsync(st.active, h_active, MAXRHS * sizeof(int), cudaMemcpyHostToDevice, s));
