@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) bpotrf_kernel(const BSys *sys, StepTable 
     const BSys &S = sys[find_task(t, blockIdx.x, local)];
     if (*S.info != 0) return;
     const int64_t o = (int64_t)k * LEAF;
-    potrf_leaf_body(S.A + o + o * S.lda, S.lda, (int)block_rows(S.n, k), S.Linv + (int64_t)k * LEAF * LEAF, o,
-                    S.info, bsmem);
+    potrf_leaf_body<LEAF>(S.A + o + o * S.lda, S.lda, (int)block_rows(S.n, k), nullptr,
+                          S.Linv + (int64_t)k * LEAF * LEAF, o, S.info, bsmem);
 }
 
 __global__ void __launch_bounds__(256) btrsm_kernel(const BSys *sys, StepTable t, int k)

@@ -17,13 +17,21 @@ namespace {
 
 using gpch::LEAF;
 
-// Step 1 leaf (see potrf_leaf_body).
-__global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *Linv,
-                                                         int64_t col0, int64_t *info)
+// Step 1 leaf (see potrf_leaf_body): factor of an nb x nb block, nb <= W.
+template <int W>
+__global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *rinv, int64_t col0,
+                                                         int64_t *info)
 {
     extern __shared__ double leaf_smem[];
-    potrf_leaf_body(A, lda, nb, Linv, col0, info, leaf_smem);
+    if (*info != 0) return;
+    potrf_leaf_body<W>(A, lda, nb, rinv, nullptr, col0, info, leaf_smem);
 }
+
+// Width of the leaf factorizations inside a diagonal tile.  Each leaf runs
+// on one SM and its FP64 work grows with the cube of its width, so narrow
+// leaves keep the serial chain short; the panel below a tile is still
+// solved in 64-column chunks.
+constexpr int DIAG_LEAF = 32;
 
 constexpr size_t LEAF_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
 
@@ -34,56 +42,57 @@ namespace gpch {
 // Enqueue the FP64 factorization of the n x n lower triangle at A.
 // Linv: workspace of tile/64 * 64*64 doubles; info: device int64 (zeroed by
 // the caller).  Used by gpch_chol_factor and by the refined solve.
-gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *Linv,
+gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *rinv,
                               int64_t *info, cudaStream_t st, int64_t col_offset)
 {
     static bool attr_done = false;
     if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(potrf_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)LEAF_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(potrf_leaf_kernel<DIAG_LEAF>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM));
         attr_done = true;
     }
     for (int64_t j0 = 0; j0 < n; j0 += tile) {
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         double *Ajj = A + j0 + j0 * lda;
-        // step 1: the diagonal tile, as a nest of 64-wide leaf steps
+        // step 1: the diagonal tile, as a nest of DIAG_LEAF-wide leaf steps
         {
-        gpch::PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
-        for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
-            const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
-            double *Lc = Linv + (c0 / LEAF) * LEAF * LEAF;
-            potrf_leaf_kernel<<<1, 256, LEAF_SMEM, st>>>(Ajj + c0 + c0 * lda, lda, nc, Lc, col_offset + j0 + c0,
-                                                         info);
-            GPCH_LAUNCH_CHECK(ctx);
-            const int64_t mr = nj - c0 - nc;
-            if (mr > 0) {
-                double *P = Ajj + (c0 + nc) + c0 * lda;
-                GPCH_CHECK(launch_trsm<double>(ctx, P, lda, mr, nc, Lc, info, st));
-                GPCH_CHECK(launch_gemm<double>(ctx, true, mr, mr, nc, P, lda, P, lda, Ajj + (c0 + nc) * (1 + lda), lda,
-                                       info, st));
+            gpch::PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
+            for (int64_t c0 = 0; c0 < nj; c0 += DIAG_LEAF) {
+                const int nc = (int)((nj - c0 < DIAG_LEAF) ? nj - c0 : DIAG_LEAF);
+                double *Lcc = Ajj + c0 + c0 * lda;
+                potrf_leaf_kernel<DIAG_LEAF><<<1, 256, LEAF_SMEM, st>>>(Lcc, lda, nc, rinv + c0,
+                                                                        col_offset + j0 + c0, info);
+                GPCH_LAUNCH_CHECK(ctx);
+                const int64_t mr = nj - c0 - nc;
+                if (mr > 0) {
+                    double *P = Ajj + (c0 + nc) + c0 * lda;
+                    GPCH_CHECK(launch_trsm_sub<double>(ctx, P, lda, mr, nc, Lcc, lda, rinv + c0, info, st));
+                    GPCH_CHECK(launch_gemm<double>(ctx, true, mr, mr, nc, P, lda, P, lda,
+                                                   Ajj + (c0 + nc) * (1 + lda), lda, info, st));
+                }
             }
         }
-        }
-        // step 2: panel below the tile, chunk by chunk
+        // step 2: panel below the tile, 64-column chunks solved by substitution
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         double *Pan = A + (j0 + nj) + j0 * lda;
         {
-        gpch::PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
-        for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
-            const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
-            double *Xc = Pan + c0 * lda;
-            GPCH_CHECK(launch_trsm<double>(ctx, Xc, lda, m, nc, Linv + (c0 / LEAF) * LEAF * LEAF, info, st));
-            const int64_t rest = nj - c0 - nc;
-            if (rest > 0)
-                GPCH_CHECK(launch_gemm<double>(ctx, false, m, rest, nc, Xc, lda, Ajj + (c0 + nc) + c0 * lda, lda,
-                                       Pan + (c0 + nc) * lda, lda, info, st));
-        }
+            gpch::PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
+            for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
+                const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
+                double *Xc = Pan + c0 * lda;
+                GPCH_CHECK(launch_trsm_sub<double>(ctx, Xc, lda, m, nc, Ajj + c0 + c0 * lda, lda, rinv + c0, info,
+                                                   st));
+                const int64_t rest = nj - c0 - nc;
+                if (rest > 0)
+                    GPCH_CHECK(launch_gemm<double>(ctx, false, m, rest, nc, Xc, lda, Ajj + (c0 + nc) + c0 * lda,
+                                                   lda, Pan + (c0 + nc) * lda, lda, info, st));
+            }
         }
         // step 3: trailing lower triangle, K = tile
         gpch::PhaseScope ph3(ctx, GPCH_PHASE_TRAILING, st, (double)nj * m * (m + 1));
         GPCH_CHECK(launch_gemm<double>(ctx, true, m, m, (int)nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda), lda,
-                               info, st));
+                                       info, st));
     }
     return GPCH_OK;
 }
@@ -105,13 +114,13 @@ extern "C" gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, doub
     cudaStream_t st = (cudaStream_t)stream;
     gpch::Carver dry(nullptr);
     dry.take<int64_t>(1);
-    dry.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
+    dry.take<double>((size_t)tile);
     GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
     gpch::Carver cv(ctx->ws);
     int64_t *d_info = cv.take<int64_t>(1);
-    double *Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
+    double *rinv = cv.take<double>((size_t)tile);
     GPCH_CUDA(ctx, cudaMemsetAsync(d_info, 0, sizeof(int64_t), st));
-    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, Linv, d_info, st, 0));
+    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, rinv, d_info, st, 0));
     int64_t *h = static_cast<int64_t *>(ctx->pinned);
     GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GPCH_CUDA(ctx, cudaStreamSynchronize(st));

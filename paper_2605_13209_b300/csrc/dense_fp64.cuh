@@ -81,27 +81,30 @@ using gpch::LEAF;
 // CTA owns ROWS whole rows, so reading B and writing X never overlap across
 // CTAs.  T is the storage and arithmetic type of B.  Thread t owns row
 // t % ROWS and every (256/ROWS)-th column from t / ROWS.
-// Step 1 leaf: factor the nb x nb (nb <= 64) lower block at A in place and
-// write inv(L) of the unit-padded 64 x 64 block to Linv (column-major, ld 64).
-// leaf_smem: 2 * 64 * 65 doubles of shared memory.
-// Right-looking: thread (tx, ty) keeps the 4 x 4 entries (tx + 16i, ty + 16j)
-// in registers; per column j the owner of the pivot takes the square root,
-// the owners of column j scale it and publish it, and every thread updates
-// its own entries below and right of the pivot.
-__device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *Linv, int64_t col0, int64_t *info,
-                                       double *leaf_smem)
+// Step 1 leaf: factor the nb x nb (nb <= W, W = 32 or 64) lower block at A
+// in place.  Right-looking: thread (tx, ty) keeps the (W/16)^2 entries
+// (tx + 16i, ty + 16j) in registers; per column j the owner of the pivot
+// takes the square root, the owners of column j scale it by the reciprocal
+// and publish it, and every thread updates its own entries below and right
+// of the pivot.  Outputs: rinv[c] = 1 / L_cc (c < W; 1 in the padding) and,
+// when Linv is not null (W = 64 only), inv(L) of the unit-padded block
+// (column-major, ld 64).  leaf_smem: 2 * 64 * 65 doubles.
+template <int W>
+__device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *rinv, double *Linv, int64_t col0,
+                                       int64_t *info, double *leaf_smem)
 {
+    constexpr int RT = W / 16;
     double (*S)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem);
     double (*Vi)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem + LEAF * (LEAF + 1));
     __shared__ double lbuf[2][LEAF];   // column j of L, double-buffered by the parity of j
+    __shared__ double rbuf[LEAF];
     __shared__ int bad;
-    if (*info != 0) return;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    double a[4][4];
+    double a[RT][RT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RT; ++j) {
             const int r = tx + 16 * i, c = ty + 16 * j;
             double v;
             if (r < nb && c < nb) v = (r >= c) ? A[r + c * lda] : 0.0;
@@ -109,6 +112,7 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *L
             a[i][j] = v;
         }
     if (tid == 0) bad = 0;
+    if (tid < LEAF) rbuf[tid] = 1.0;
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
         const int jq = j / 16, jr = j % 16;
@@ -122,29 +126,30 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *L
                 d = sqrt(d);
                 a[jq][jq] = d;
                 lcol[j] = 1.0 / d;   // the column is scaled by the reciprocal
+                rbuf[j] = lcol[j];
             }
         }
         __syncthreads();
         if (bad) break;
         if (ty == jr) {
-            const double rinv = lcol[j];
+            const double rr = lcol[j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < RT; ++i) {
                 const int r = tx + 16 * i;
                 if (r > j) {
-                    a[i][jq] *= rinv;
+                    a[i][jq] *= rr;
                     lcol[r] = a[i][jq];
                 }
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < RT; ++i) {
             const int r = tx + 16 * i;
             if (r <= j) continue;
             const double lr = lcol[r];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
+            for (int jj = 0; jj < RT; ++jj) {
                 const int c = ty + 16 * jj;
                 if (c > j && c <= r) a[i][jj] -= lr * lcol[c];
             }
@@ -155,16 +160,90 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *L
         return;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) S[tx + 16 * i][ty + 16 * j] = a[i][j];
+        for (int j = 0; j < RT; ++j) {
+            const int r = tx + 16 * i, c = ty + 16 * j;
+            if (r < nb && c < nb && r >= c) A[r + c * lda] = a[i][j];
+        }
+    if (rinv && tid < W) rinv[tid] = rbuf[tid];
+    if (Linv == nullptr) return;
+    // inverse of the unit-padded 64 x 64 block (W == 64)
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int j = 0; j < RT; ++j) S[tx + 16 * i][ty + 16 * j] = a[i][j];
     __syncthreads();
     gpch::invert_lower_64(S, Vi);
     __syncthreads();
     for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
-        int r = e % LEAF, c = e / LEAF;
-        if (r < nb && c < nb && r >= c) A[r + c * lda] = S[r][c];
+        const int r = e % LEAF, c = e / LEAF;
         Linv[r + c * LEAF] = Vi[r][c];
+    }
+}
+
+// Panel solve by substitution: X = B L^-T in place on the m x nc panel B
+// (nc <= 64): x_c = (b_c - sum_{k<c} x_k L[c][k]) / L[c][c], with L a lower
+// nc x nc FP64 block (ld ldl) and rinv its diagonal reciprocals.  One warp
+// per RPW rows; lane l holds columns l and l + 32 of each of its rows, the
+// sum over k is a warp reduction.  The CTA's 8 * RPW rows are staged through
+// shared memory so the global reads and writes stay coalesced.  T is the
+// storage and arithmetic type of B.
+template <typename T, int RPW>
+__global__ void __launch_bounds__(256) trsm_sub_kernel(T *B, int64_t ldb, int64_t m, int nc,
+                                                       const double *__restrict__ L, int64_t ldl,
+                                                       const double *__restrict__ rinv, const int64_t *info)
+{
+    constexpr int ROWS = 8 * RPW;
+    __shared__ double Ls[LEAF][LEAF + 1];
+    __shared__ double rs[LEAF];
+    __shared__ T Bs[LEAF][ROWS + 1];
+    if (info && *info != 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS;
+    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
+        const int k = e % LEAF, c = e / LEAF;   // column-major walk: coalesced
+        Ls[c][k] = (k <= c && c < nc) ? L[c + (int64_t)k * ldl] : 0.0;
+    }
+    if (tid < LEAF) rs[tid] = tid < nc ? rinv[tid] : 1.0;
+    for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
+        const int r = e % ROWS, k = e / ROWS;
+        Bs[k][r] = (r0 + r < m && k < nc) ? B[(r0 + r) + (int64_t)k * ldb] : T(0);
+    }
+    __syncthreads();
+    T x0[RPW], x1[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        x0[q] = Bs[lane][warp * RPW + q];
+        x1[q] = Bs[lane + 32][warp * RPW + q];
+    }
+    for (int c = 0; c < nc; ++c) {
+        const T l0 = (lane < c) ? (T)Ls[c][lane] : T(0);
+        const T l1 = (lane + 32 < c) ? (T)Ls[c][lane + 32] : T(0);
+        const T rc = (T)rs[c];
+        const int src = c & 31;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            T s = fma(x1[q], l1, x0[q] * l0);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            const T bc = __shfl_sync(0xffffffffu, c < 32 ? x0[q] : x1[q], src);
+            const T xc = (bc - s) * rc;
+            if (lane == src) {
+                if (c < 32) x0[q] = xc;
+                else x1[q] = xc;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        Bs[lane][warp * RPW + q] = x0[q];
+        Bs[lane + 32][warp * RPW + q] = x1[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
+        const int r = e % ROWS, k = e / ROWS;
+        if (r0 + r < m && k < nc) B[(r0 + r) + (int64_t)k * ldb] = Bs[k][r];
     }
 }
 
@@ -342,6 +421,20 @@ inline gpch_status launch_trsm_rows(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m,
     return GPCH_OK;
 }
 
+// X = B L^-T by substitution (trsm_sub_kernel); FP64 panels take one row
+// per warp (their cost is FP64 issue), FP32 panels four.
+template <typename T>
+inline gpch_status launch_trsm_sub(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int nc, const double *L,
+                                   int64_t ldl, const double *rinv, const int64_t *info, cudaStream_t st)
+{
+    if (m <= 0 || nc <= 0) return GPCH_OK;
+    constexpr int RPW = sizeof(T) == 4 ? 4 : 1;
+    trsm_sub_kernel<T, RPW><<<(unsigned)((m + 8 * RPW - 1) / (8 * RPW)), 256, 0, st>>>(B, ldb, m, nc, L, ldl, rinv,
+                                                                                     info);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
 template <typename T>
 inline gpch_status launch_trsm(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int nc, const double *Linv,
                                const int64_t *info, cudaStream_t st)
@@ -355,9 +448,11 @@ inline gpch_status launch_trsm(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int 
 
 namespace gpch {
 
-// Enqueue the FP64 blocked factorization (chol_fp64.cu).  A failed pivot
-// at local column c sets *info = col_offset + c + 1.
-gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *Linv,
+// Enqueue the FP64 blocked factorization (chol_fp64.cu).  rinv: workspace
+// of `tile` doubles that receives 1 / L_cc of the last diagonal tile
+// factored (a caller that factors one tile reads it afterwards).  A failed
+// pivot at local column c sets *info = col_offset + c + 1.
+gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *rinv,
                               int64_t *info, cudaStream_t st, int64_t col_offset);
 
 // Forward/back substitution (solve.cu).  SolveWs is carved from

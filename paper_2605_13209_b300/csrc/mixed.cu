@@ -4,8 +4,8 @@
 //   step 1  the diagonal tile is widened to FP64 and factored by the FP64
 //           nest (potrf leaf / inverse-apply TRSM / SYRK), then stored back
 //           in FP32;
-//   step 2  the panel solve runs in FP32 against the FP64 inverses of the
-//           64 x 64 diagonal blocks;
+//   step 2  the panel is solved in FP32, 64 columns at a time, against FP32
+//           inverses of the diagonal tile's 64 x 64 blocks;
 //   step 3  the trailing update A_ik -= A_ij A_kj^T runs on the tensor cores:
 //           the panel is rounded to bf16 (or split into a bf16 head and a
 //           bf16 tail) in a K-major copy, TMA streams 128 x 64 tiles of it
@@ -195,6 +195,68 @@ __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restr
     }
 }
 
+// FP32 inverses of the 64 x 64 diagonal blocks of the factored FP64 tile D
+// (nj x nj, ld ldd), for the FP32 panel solve: block b of the grid inverts
+// rows/columns [64b, 64b + 64), unit-padded, by right-looking substitution
+// on all columns of the identity (thread (tx, ty) keeps entries (tx + 16i,
+// ty + 16jj)).  Stored widened to FP64 (column-major, ld 64).
+__global__ void __launch_bounds__(256) inv_blocks_f32_kernel(const double *__restrict__ D, int64_t ldd, int64_t nj,
+                                                             double *Linv)
+{
+    __shared__ float S[LEAF][LEAF + 1];
+    __shared__ float dinv[LEAF];
+    __shared__ float xrow[2][LEAF];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t o = (int64_t)blockIdx.x * LEAF;
+    const int nb = (int)((nj - o < LEAF) ? nj - o : LEAF);
+    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
+        const int r = e % LEAF, c = e / LEAF;
+        float v;
+        if (r < nb && c < nb) v = (r >= c) ? (float)D[(o + r) + (o + c) * ldd] : 0.0f;
+        else v = (r == c) ? 1.0f : 0.0f;
+        S[r][c] = v;
+    }
+    __syncthreads();
+    if (tid < LEAF) dinv[tid] = 1.0f / S[tid][tid];
+    float x[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) x[i][jj] = (tx + 16 * i == ty + 16 * jj) ? 1.0f : 0.0f;
+    __syncthreads();
+    for (int j = 0; j < LEAF; ++j) {
+        float *xr = xrow[j & 1];
+        if (tx == j % 16) {
+            const int i = j / 16;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int c = ty + 16 * jj;
+                if (c <= j) {
+                    x[i][jj] *= dinv[j];
+                    xr[c] = x[i][jj];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = tx + 16 * i;
+            if (r <= j) continue;
+            const float l = S[r][j];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int c = ty + 16 * jj;
+                if (c <= j) x[i][jj] -= l * xr[c];
+            }
+        }
+    }
+    double *dst = Linv + (int64_t)blockIdx.x * LEAF * LEAF;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) dst[(tx + 16 * i) + (ty + 16 * jj) * LEAF] = (double)x[i][jj];
+}
+
 // W (FP32, lower triangle) = A (FP64) + shift * I.
 __global__ void init_w_kernel(int64_t n, const double *__restrict__ A, int64_t lda, float *W, int64_t ldw,
                               double shift)
@@ -294,7 +356,7 @@ namespace gpch {
 
 // Workspace layout of the mixed factor for n, tile.
 struct MixedWs {
-    double *D, *Linv;
+    double *D, *rinv, *Linv;
     int64_t *info;
     __nv_bfloat16 *hi, *lo;
     int *err;
@@ -306,6 +368,7 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.info = cv.take<int64_t>(1);
     w.err = cv.take<int>(4);
     w.D = cv.take<double>((size_t)tile * tile);
+    w.rinv = cv.take<double>((size_t)tile);
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
     w.hi = cv.take<__nv_bfloat16>((size_t)n * tile);
     w.lo = cv.take<__nv_bfloat16>((size_t)n * tile);
@@ -336,11 +399,10 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         float *Wjj = W + j0 + j0 * ldw;
         {
-            // step 1 in FP64
-            PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
+            // step 1 in FP64 (timed inside chol_fp64_enqueue)
             tile_f32_to_f64<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, Wjj, ldw, w.D, tile);
             GPCH_LAUNCH_CHECK(ctx);
-            GPCH_CHECK(chol_fp64_enqueue(ctx, nj, tile, w.D, tile, w.Linv, w.info, st, j0));
+            GPCH_CHECK(chol_fp64_enqueue(ctx, nj, tile, w.D, tile, w.rinv, w.info, st, j0));
             tile_f64_to_f32<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, w.D, tile, Wjj, ldw);
             GPCH_LAUNCH_CHECK(ctx);
         }
@@ -348,8 +410,11 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         if (m <= 0) continue;
         float *Pan = W + (j0 + nj) + j0 * ldw;
         {
-            // step 2 in FP32 against the FP64 inverses of the diagonal blocks
+            // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
+            // diagonal blocks (computed from the FP64 factor)
             PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
+            inv_blocks_f32_kernel<<<(unsigned)((nj + LEAF - 1) / LEAF), 256, 0, st>>>(w.D, tile, nj, w.Linv);
+            GPCH_LAUNCH_CHECK(ctx);
             for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
                 const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
                 float *Xc = Pan + c0 * ldw;
