@@ -68,6 +68,27 @@ __device__ inline void invert_lower_64(const double (*S)[LEAF + 1], double (*Vi)
         for (int jj = 0; jj < 4; ++jj) Vi[tx + 16 * i][ty + 16 * jj] = x[i][jj];
 }
 
+// Square root and reciprocal square root of a positive pivot d, by Newton
+// iteration on y = 1/sqrt(d) from an FP32 seed: each step
+// y <- y (3 - d y^2) / 2 doubles the correct bits (24 -> 48 -> full), then
+// s = d y is corrected once by s <- s + y (d - s^2) / 2.  Both results are
+// within a few units in the last place; the exact cases (d = 1, perfect
+// squares of small integers) come out exact.  Outside the FP32 range the
+// division-based form is used.
+__device__ inline void pivot_sqrt(double d, double &s, double &y)
+{
+    if (d > 1e-30 && d < 1e30) {
+        y = (double)__frsqrt_rn((float)d);
+        y = y * fma(-0.5 * d, y * y, 1.5);
+        y = y * fma(-0.5 * d, y * y, 1.5);
+        s = d * y;
+        s = fma(0.5 * y, fma(-s, s, d), s);
+    } else {
+        s = sqrt(d);
+        y = 1.0 / s;
+    }
+}
+
 }  // namespace gpch
 
 // Kernels and their launchers have internal linkage: every translation unit
@@ -123,10 +144,11 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
             if (!(d > 0.0) || !isfinite(d)) {
                 bad = j + 1;
             } else {
-                d = sqrt(d);
-                a[jq][jq] = d;
-                lcol[j] = 1.0 / d;   // the column is scaled by the reciprocal
-                rbuf[j] = lcol[j];
+                double sq, rs;
+                gpch::pivot_sqrt(d, sq, rs);
+                a[jq][jq] = sq;
+                lcol[j] = rs;   // the column is scaled by the reciprocal
+                rbuf[j] = rs;
             }
         }
         __syncthreads();
@@ -183,62 +205,60 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
 }
 
 // Panel solve by substitution: X = B L^-T in place on the m x nc panel B
-// (nc <= 64): x_c = (b_c - sum_{k<c} x_k L[c][k]) / L[c][c], with L a lower
-// nc x nc FP64 block (ld ldl) and rinv its diagonal reciprocals.  One warp
-// per RPW rows; lane l holds columns l and l + 32 of each of its rows, the
-// sum over k is a warp reduction.  The CTA's 8 * RPW rows are staged through
-// shared memory so the global reads and writes stay coalesced.  T is the
-// storage and arithmetic type of B.
+// (nc <= 64), with L a lower nc x nc FP64 block (ld ldl) and rinv its
+// diagonal reciprocals.  Column-oriented (right-looking): x_c = b_c / L_cc,
+// then b_k -= x_c L[k][c] for every k > c.  One warp per RPW rows; lane l
+// holds columns l and l + 32 of each of its rows, so a column costs one
+// shuffle and three FMA-class instructions per row.  The CTA's 8 * RPW rows
+// are staged through shared memory so that global reads and writes stay
+// coalesced.  T is the storage and arithmetic type of B.
 template <typename T, int RPW>
 __global__ void __launch_bounds__(256) trsm_sub_kernel(T *B, int64_t ldb, int64_t m, int nc,
                                                        const double *__restrict__ L, int64_t ldl,
                                                        const double *__restrict__ rinv, const int64_t *info)
 {
     constexpr int ROWS = 8 * RPW;
-    __shared__ double Ls[LEAF][LEAF + 1];
-    __shared__ double rs[LEAF];
+    __shared__ T Ls[LEAF][LEAF + 1];   // Ls[k][c] = L[k][c]
+    __shared__ T rs[LEAF];
     __shared__ T Bs[LEAF][ROWS + 1];
     if (info && *info != 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * ROWS;
     for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
         const int k = e % LEAF, c = e / LEAF;   // column-major walk: coalesced
-        Ls[c][k] = (k <= c && c < nc) ? L[c + (int64_t)k * ldl] : 0.0;
+        Ls[k][c] = (k > c && k < nc && c < nc) ? (T)L[k + (int64_t)c * ldl] : T(0);
     }
-    if (tid < LEAF) rs[tid] = tid < nc ? rinv[tid] : 1.0;
+    if (tid < LEAF) rs[tid] = tid < nc ? (T)rinv[tid] : T(1);
     for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
         const int r = e % ROWS, k = e / ROWS;
         Bs[k][r] = (r0 + r < m && k < nc) ? B[(r0 + r) + (int64_t)k * ldb] : T(0);
     }
     __syncthreads();
-    T x0[RPW], x1[RPW];
+    T b0[RPW], b1[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-        x0[q] = Bs[lane][warp * RPW + q];
-        x1[q] = Bs[lane + 32][warp * RPW + q];
+        b0[q] = Bs[lane][warp * RPW + q];
+        b1[q] = Bs[lane + 32][warp * RPW + q];
     }
     for (int c = 0; c < nc; ++c) {
-        const T l0 = (lane < c) ? (T)Ls[c][lane] : T(0);
-        const T l1 = (lane + 32 < c) ? (T)Ls[c][lane + 32] : T(0);
-        const T rc = (T)rs[c];
+        const T l0 = Ls[lane][c], l1 = Ls[lane + 32][c];   // zero on and above the diagonal
+        const T rc = rs[c];
         const int src = c & 31;
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
-            T s = fma(x1[q], l1, x0[q] * l0);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            const T bc = __shfl_sync(0xffffffffu, c < 32 ? x0[q] : x1[q], src);
-            const T xc = (bc - s) * rc;
+            const T xc = __shfl_sync(0xffffffffu, c < 32 ? b0[q] : b1[q], src) * rc;
             if (lane == src) {
-                if (c < 32) x0[q] = xc;
-                else x1[q] = xc;
+                if (c < 32) b0[q] = xc;
+                else b1[q] = xc;
             }
+            b0[q] = fma(-xc, l0, b0[q]);
+            b1[q] = fma(-xc, l1, b1[q]);
         }
     }
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-        Bs[lane][warp * RPW + q] = x0[q];
-        Bs[lane + 32][warp * RPW + q] = x1[q];
+        Bs[lane][warp * RPW + q] = b0[q];
+        Bs[lane + 32][warp * RPW + q] = b1[q];
     }
     __syncthreads();
     for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
@@ -383,7 +403,12 @@ inline gpch_status launch_gemm(gpch_ctx *ctx, bool lower, int64_t m, int64_t nn,
     if (m <= 0 || nn <= 0 || k <= 0) return GPCH_OK;
     const int64_t tm = (m + LEAF - 1) / LEAF, tn = (nn + LEAF - 1) / LEAF;
     const bool small = (lower ? tm * (tm + 1) / 2 : tm * tn) < SMALL_GRID;
-    if (lower) {
+    const int64_t t32 = (m + 31) / 32;
+    if (lower && t32 * (t32 + 1) / 2 < SMALL_GRID / 2) {
+        const int64_t Tn = (m + 15) / 16;
+        gemm_nt_minus_kernel<T, true, 16><<<(unsigned)(Tn * (Tn + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb,
+                                                                                       C, ldc, info);
+    } else if (lower) {
         if (small) {
             const int64_t Tn = (m + 31) / 32;
             gemm_nt_minus_kernel<T, true, 32><<<(unsigned)(Tn * (Tn + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb,
