@@ -42,6 +42,17 @@ gpch_status ws_reserve(gpch_ctx *ctx, size_t bytes)
     return GPCH_OK;
 }
 
+gpch_status aux_stream(gpch_ctx *ctx)
+{
+    if (ctx->aux) return GPCH_OK;
+    int least = 0, greatest = 0;
+    GPCH_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GPCH_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, least));
+    GPCH_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->crit, cudaStreamNonBlocking, greatest));
+    for (auto &e : ctx->aux_ev) GPCH_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return GPCH_OK;
+}
+
 cudaEvent_t take_event(gpch_ctx *ctx)
 {
     if (!ctx->event_pool.empty()) {
@@ -98,6 +109,10 @@ gpch_status gpch_destroy(gpch_ctx *ctx)
             cudaEventDestroy(t.stop);
         }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto e : ctx->aux_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->crit) cudaStreamDestroy(ctx->crit);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;

@@ -33,7 +33,6 @@ __global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda,
 // solved in 64-column chunks.
 constexpr int DIAG_LEAF = 32;
 
-constexpr size_t LEAF_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
 
 }  // namespace
 
@@ -45,12 +44,6 @@ namespace gpch {
 gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *rinv,
                               int64_t *info, cudaStream_t st, int64_t col_offset)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(potrf_leaf_kernel<DIAG_LEAF>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM));
-        attr_done = true;
-    }
     for (int64_t j0 = 0; j0 < n; j0 += tile) {
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         double *Ajj = A + j0 + j0 * lda;
@@ -60,7 +53,7 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
             for (int64_t c0 = 0; c0 < nj; c0 += DIAG_LEAF) {
                 const int nc = (int)((nj - c0 < DIAG_LEAF) ? nj - c0 : DIAG_LEAF);
                 double *Lcc = Ajj + c0 + c0 * lda;
-                potrf_leaf_kernel<DIAG_LEAF><<<1, 256, LEAF_SMEM, st>>>(Lcc, lda, nc, rinv + c0,
+                potrf_leaf_kernel<DIAG_LEAF><<<1, 256, 0, st>>>(Lcc, lda, nc, rinv + c0,
                                                                         col_offset + j0 + c0, info);
                 GPCH_LAUNCH_CHECK(ctx);
                 const int64_t mr = nj - c0 - nc;

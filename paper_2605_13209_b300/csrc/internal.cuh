@@ -30,6 +30,9 @@ struct gpch_ctx {
     double phase_ms[GPCH_PHASE_COUNT] = {0};
     int64_t phase_launches[GPCH_PHASE_COUNT] = {0};
     double phase_work[GPCH_PHASE_COUNT] = {0};
+    cudaStream_t aux = nullptr;          // low-priority stream for bulk overlapped work
+    cudaStream_t crit = nullptr;         // high-priority stream for the critical chain
+    cudaEvent_t aux_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace gpch {
@@ -65,6 +68,10 @@ struct Carver {
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
 
 cudaEvent_t take_event(gpch_ctx *ctx);
+
+// Create the context's two internal streams (bulk at the lowest priority,
+// critical chain at the highest) and their ordering events (once).
+gpch_status aux_stream(gpch_ctx *ctx);
 
 // Free the batched solver's cached plans of a context (batched.cu).
 void batched_release(gpch_ctx *ctx);

@@ -43,7 +43,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // nonzero code if a bounded wait gives up).
 __global__ void __launch_bounds__(TC_THREADS, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
-                   int kp, int split, float *__restrict__ C, int64_t ldc, int *err)
+                   int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -55,11 +55,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t t = blockIdx.x;
-    int64_t ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-    while (ti * (ti + 1) / 2 > t) --ti;
-    const int64_t tk = t - ti * (ti + 1) / 2;
+    // Tiles of the lower triangle of the T x T tile grid, column by column,
+    // restricted to tile columns [tk0, tk1): column tk holds tiles
+    // ti = tk .. T-1 and starts at offset(tk) = tk T - tk (tk - 1) / 2.
+    const int64_t T = (m + BM - 1) / BM;
+    auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
+    const int64_t t = (int64_t)blockIdx.x + offset(tk0);
+    int64_t lo = tk0, hi = tk1 - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (offset(mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t tk = lo, ti = tk + (t - offset(tk));
     const int64_t i0 = ti * BM, c0 = tk * BN;
 
     if (threadIdx.x == 0) {
@@ -321,18 +329,27 @@ struct LowprecBuffers {
     int *err = nullptr;
 };
 
-// C_lower (m x m FP32) -= P P^T with P (m x k FP32) on tensor cores.
-gpch_status syrk_lowprec_enqueue(gpch_ctx *ctx, int64_t m, int k, const float *P, int64_t ldp, float *C,
-                                 int64_t ldc, int prec, const LowprecBuffers &buf, cudaStream_t st)
+// Round the FP32 panel P (m x k) to its bf16 K-major head/tail copies.
+gpch_status panel_convert(gpch_ctx *ctx, int64_t m, int k, const float *P, int64_t ldp, int prec,
+                          const LowprecBuffers &buf, cudaStream_t st)
 {
-    if (m <= 0 || k <= 0) return GPCH_OK;
+    const int kp = (k + BK - 1) / BK * BK;
+    dim3 grid((unsigned)((m + 63) / 64), (unsigned)(kp / 64));
+    panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi, prec == GPCH_PREC_SPLIT_BF16 ? buf.lo : nullptr);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+// C_lower (m x m FP32) -= P P^T on the tile columns [tk0, tk1) of the
+// 128 x 128 tile grid (tk1 < 0: to the end), from the bf16 copies in buf.
+gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ldc, int prec, const LowprecBuffers &buf,
+                           int64_t tk0, int64_t tk1, cudaStream_t st)
+{
     const int kp = (k + BK - 1) / BK * BK;
     const bool split = prec == GPCH_PREC_SPLIT_BF16;
-    {
-        dim3 grid((unsigned)((m + 63) / 64), (unsigned)(kp / 64));
-        panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi, split ? buf.lo : nullptr);
-        GPCH_LAUNCH_CHECK(ctx);
-    }
+    const int64_t T = (m + BM - 1) / BM;
+    if (tk1 < 0 || tk1 > T) tk1 = T;
+    if (tk0 >= tk1) return GPCH_OK;
     CUtensorMap mhi, mlo;
     GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, kp));
     GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, kp));
@@ -341,13 +358,26 @@ gpch_status syrk_lowprec_enqueue(gpch_ctx *ctx, int64_t m, int k, const float *P
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         attr_done = true;
     }
-    const int64_t T = (m + BM - 1) / BM;
-    const double work = 2.0 * (double)k * (double)m * (double)(m + 1) / 2.0 * (split ? 3.0 : 1.0);
+    auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
+    const int64_t tiles = offset(tk1) - offset(tk0);
+    // algorithmic work: the lower-triangle entries of the updated columns
+    const int64_t cA = tk0 * BN, cB = (tk1 * BN < m) ? tk1 * BN : m;
+    const double cols_entries = (double)(cB - cA) * (double)m - ((double)cB * (cB - 1) - (double)cA * (cA - 1)) / 2.0;
+    const double work = 2.0 * (double)k * cols_entries * (split ? 3.0 : 1.0);
     gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
-    syrk_tc_kernel<<<(unsigned)(T * (T + 1) / 2), TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc,
-                                                                            buf.err);
+    syrk_tc_kernel<<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
+                                                               buf.err);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
+}
+
+// C_lower (m x m FP32) -= P P^T with P (m x k FP32) on tensor cores.
+gpch_status syrk_lowprec_enqueue(gpch_ctx *ctx, int64_t m, int k, const float *P, int64_t ldp, float *C,
+                                 int64_t ldc, int prec, const LowprecBuffers &buf, cudaStream_t st)
+{
+    if (m <= 0 || k <= 0) return GPCH_OK;
+    GPCH_CHECK(panel_convert(ctx, m, k, P, ldp, prec, buf, st));
+    return syrk_tc_launch(ctx, m, k, C, ldc, prec, buf, 0, -1, st);
 }
 
 }  // namespace
@@ -358,7 +388,7 @@ namespace gpch {
 struct MixedWs {
     double *D, *rinv, *Linv;
     int64_t *info;
-    __nv_bfloat16 *hi, *lo;
+    __nv_bfloat16 *hi[2], *lo[2];   // bf16 panel copies, by column parity
     int *err;
 };
 
@@ -370,8 +400,10 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.D = cv.take<double>((size_t)tile * tile);
     w.rinv = cv.take<double>((size_t)tile);
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
-    w.hi = cv.take<__nv_bfloat16>((size_t)n * tile);
-    w.lo = cv.take<__nv_bfloat16>((size_t)n * tile);
+    for (int q = 0; q < 2; ++q) {
+        w.hi[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
+        w.lo[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
+    }
     return w;
 }
 
@@ -385,6 +417,15 @@ size_t mixed_ws_bytes(int64_t n, int tile)
 // Enqueue the low-precision factorization of W (FP32, n x n lower, ldw),
 // which already holds A + shift I.  info/err live in the workspace; the
 // caller reads them after the stream synchronizes.
+//
+// Lookahead: the trailing update of block column j is split into the tile
+// columns that cover block column j+1 (on the critical chain, a
+// highest-priority stream of the context) and the rest (on its lowest-
+// priority stream), so that the FP64 factorization of
+// the next diagonal tile and its panel solve run while the bulk of the
+// tensor-core update is still going.  Events keep every read and write of a
+// block column in order; the bf16 panel copies alternate between two
+// buffers.
 gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
                                  int64_t **info_out, int **err_out, cudaStream_t st)
 {
@@ -392,23 +433,32 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     MixedWs w = carve_mixed(cv, n, tile);
     *info_out = w.info;
     *err_out = w.err;
-    GPCH_CUDA(ctx, cudaMemsetAsync(w.info, 0, sizeof(int64_t), st));
-    GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), st));
-    LowprecBuffers buf{w.hi, w.lo, w.err};
-    for (int64_t j0 = 0; j0 < n; j0 += tile) {
+    GPCH_CHECK(aux_stream(ctx));
+    cudaStream_t caller = st, sb = ctx->aux;
+    st = ctx->crit;   // the critical chain runs at the highest priority
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.info, 0, sizeof(int64_t), caller));
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), caller));
+    const int64_t ncols = (n + tile - 1) / tile;
+    cudaEvent_t ev_panel = ctx->aux_ev[0], ev_rest = ctx->aux_ev[1], ev_start = ctx->aux_ev[2],
+                ev_done = ctx->aux_ev[3];
+    bool rest_pending = false;
+    GPCH_CUDA(ctx, cudaEventRecord(ev_start, caller));
+    GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_start, 0));
+    GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
+    for (int64_t J = 0; J < ncols; ++J) {
+        const int64_t j0 = J * tile;
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         float *Wjj = W + j0 + j0 * ldw;
-        {
-            // step 1 in FP64 (timed inside chol_fp64_enqueue)
-            tile_f32_to_f64<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, Wjj, ldw, w.D, tile);
-            GPCH_LAUNCH_CHECK(ctx);
-            GPCH_CHECK(chol_fp64_enqueue(ctx, nj, tile, w.D, tile, w.rinv, w.info, st, j0));
-            tile_f64_to_f32<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, w.D, tile, Wjj, ldw);
-            GPCH_LAUNCH_CHECK(ctx);
-        }
+        // step 1 in FP64 (timed inside chol_fp64_enqueue)
+        tile_f32_to_f64<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, Wjj, ldw, w.D, tile);
+        GPCH_LAUNCH_CHECK(ctx);
+        GPCH_CHECK(chol_fp64_enqueue(ctx, nj, tile, w.D, tile, w.rinv, w.info, st, j0));
+        tile_f64_to_f32<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, w.D, tile, Wjj, ldw);
+        GPCH_LAUNCH_CHECK(ctx);
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         float *Pan = W + (j0 + nj) + j0 * ldw;
+        LowprecBuffers buf{w.hi[J & 1], w.lo[J & 1], w.err};
         {
             // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
             // diagonal blocks (computed from the FP64 factor)
@@ -425,9 +475,22 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                                                   Pan + (c0 + nc) * ldw, ldw, w.info, st));
             }
         }
-        // step 3 on tensor cores
-        GPCH_CHECK(syrk_lowprec_enqueue(ctx, m, (int)nj, Pan, ldw, W + (j0 + nj) * (1 + ldw), ldw, prec, buf, st));
+        // step 3 on tensor cores: bf16 copies of the panel, then the tile
+        // columns of block column J+1 here and the rest on the second stream
+        GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, buf, st));
+        if (rest_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_rest, 0));
+        float *Ct = W + (j0 + nj) * (1 + ldw);
+        const int64_t next_cols = (tile + BN - 1) / BN;
+        GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, Ct, ldw, prec, buf, 0, next_cols, st));
+        GPCH_CUDA(ctx, cudaEventRecord(ev_panel, st));
+        GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_panel, 0));
+        GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, Ct, ldw, prec, buf, next_cols, -1, sb));
+        GPCH_CUDA(ctx, cudaEventRecord(ev_rest, sb));
+        rest_pending = true;
     }
+    if (rest_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_rest, 0));
+    GPCH_CUDA(ctx, cudaEventRecord(ev_done, st));
+    GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_done, 0));
     return GPCH_OK;
 }
 
