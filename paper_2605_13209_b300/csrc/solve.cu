@@ -3,7 +3,7 @@
 //
 // The 64 x 64 diagonal blocks of L are inverted once (one launch).  Each
 // sweep is then ONE cooperative launch of one CTA per SM.  Block row I is
-// owned by CTA I mod P and its partial sums live in the output rows of I.
+// owned by CTA I mod P, which keeps its partial sums in shared memory.
 // Walking the blocks in sweep order, every CTA waits for the solved block J
 // (a flag word per block, bounded wait), adds L_IJ y_J (forward) or
 // L_JI^T x_J (back) to each block I it owns further down the sweep, and the
@@ -78,89 +78,104 @@ __device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int by
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-constexpr int SW_SLOTS = 4;   // 64 x 64 blocks of L staged per step
-
+// Blocks of L staged per step (FP32 factor: 4, FP64: 2, so both fit).
 template <typename TL>
-constexpr size_t sweep_smem_bytes()
+constexpr int sweep_slots()
 {
-    return (size_t)(2 + 4 + 2) * LEAF * SW_MAXRHS * sizeof(double) + (size_t)SW_SLOTS * LEAF * LEAF * sizeof(TL) +
-           (size_t)LEAF * LEAF * sizeof(double);
+    return sizeof(TL) == 4 ? 4 : 2;
+}
+// Staged block of L: entry (t, k) at k * 65 + (k / 16) * PADQ + t.  The
+// four lanes that share an item t read k-ranges 16 apart; the extra PADQ
+// per 16 rows puts them in different banks (FP32: 8 words, FP64: 4 words).
+template <typename TL>
+constexpr int padq()
+{
+    return sizeof(TL) == 4 ? 8 : 4;
+}
+constexpr int LSTRIDE = LEAF * (LEAF + 1) + 32;
+constexpr int YSTRIDE = 4 * 17;   // solved block: rhs c, row r at c * 68 + (r / 16) * 17 + r % 16
+constexpr int ISTRIDE = LEAF + 4; // inverse block, column stride
+
+// Dynamic shared memory of one sweep CTA owning `nown` blocks.
+template <typename TL>
+size_t sweep_smem_bytes(int nown, int nrhs)
+{
+    return (size_t)SW_MAXRHS * (YSTRIDE + 2 * LEAF) * sizeof(double) + (size_t)LEAF * ISTRIDE * sizeof(double) +
+           (size_t)sweep_slots<TL>() * LSTRIDE * sizeof(TL) + (size_t)nown * LEAF * nrhs * sizeof(double);
 }
 
-// One sweep.  FWD: Y = L^-1 B.  BWD: Y = L^-T B.  Y (n x nrhs, ldy) is
-// the output and, until a block is solved, its partial sums.  flags[J] ==
-// epoch marks block J solved.  nrhs <= 16.
+// One sweep.  FWD: Y = L^-1 B.  BWD: Y = L^-T B.  Y (n x nrhs, ldy) gets
+// the solved blocks; flags[J] == epoch marks block J solved.  nrhs <= 16.
 //
-// Per step J every CTA first starts copying into shared memory what it
-// will need (its blocks of L for this step; for the owner of the next
-// block also that block's inverse, right-hand side and partial sums), then
-// waits for block J.  The owner of the next block adds block J's
-// contribution to the staged partial sums in shared memory, solves the
-// block and publishes it before doing its other updates, so the serial
-// chain per block is: flag seen -> y_J read -> one 64 x 64 block product ->
-// one 64 x 64 inverse-block product -> publish.
+// CTA `me` owns blocks me, me + P, ... and keeps their partial sums in
+// shared memory.  Per step J every CTA first starts copying into shared
+// memory the blocks of L it will need (staged so that entry k * 65 + t
+// multiplies y_J[k] for item t of the owned block: row t of L_IJ forward,
+// column t of L_JI back), plus, for the owner of the next block, that
+// block's inverse and right-hand side; then it waits for block J.  Each
+// (item, rhs) sum of 64 terms is split over four adjacent lanes and joined
+// by two shuffles, so updates need no barrier of their own.  The owner of
+// the next block updates, solves and publishes it before its other updates,
+// so the serial chain per block is: flag seen -> y_J read -> one 64 x 64
+// block product -> one 64 x 64 inverse-block product -> publish.
 template <typename TL, bool FWD>
 __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int nrhs, const TL *__restrict__ L,
                                                                 int64_t ldl, const double *__restrict__ Linv,
                                                                 const double *B, int64_t ldb, double *Y, int64_t ldy,
                                                                 unsigned *flags, unsigned epoch, int *err)
 {
+    constexpr int SLOTS = sweep_slots<TL>();
     extern __shared__ __align__(16) double sw_smem[];
-    double *yv = sw_smem;                          // solved block being applied [64 * 16]
-    double *vv = yv + LEAF * SW_MAXRHS;            // right-hand side of the block being solved
-    double *red = vv + LEAF * SW_MAXRHS;           // [4][64 * 16] partial products
-    double *bst = red + 4 * LEAF * SW_MAXRHS;      // staged B rows of the next block
-    double *yst = bst + LEAF * SW_MAXRHS;          // staged partial sums of the next block
-    TL *Ls = reinterpret_cast<TL *>(yst + LEAF * SW_MAXRHS);               // [SW_SLOTS][64 * 64]
-    double *Li = reinterpret_cast<double *>(Ls + SW_SLOTS * LEAF * LEAF);   // inverse of the next block
+    constexpr int PQ = padq<TL>();
+    double *yv = sw_smem;                          // solved block being applied [16 * 68]
+    double *vv = yv + YSTRIDE * SW_MAXRHS;         // right-hand side of the block being solved
+    double *bst = vv + LEAF * SW_MAXRHS;           // staged B rows of the next block
+    double *Li = bst + LEAF * SW_MAXRHS;           // inverse of the next block, (r, k) at r + k * 68
+    TL *Ls = reinterpret_cast<TL *>(Li + LEAF * ISTRIDE);                    // [SLOTS][LSTRIDE]
+    double *acc = reinterpret_cast<double *>(Ls + SLOTS * LSTRIDE);         // [owned][64 * nrhs]
     __shared__ int abort_flag;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int64_t N = (n + LEAF - 1) / LEAF;
     const int64_t P = gridDim.x, me = blockIdx.x;
+    const int nown = (int)((N - me + P - 1) / P);
     if (tid == 0) abort_flag = 0;
     using TM = typename std::conditional<sizeof(TL) == 4, float, double>::type;
 
     auto rows_of = [&](int64_t J) { return (int)((n - J * LEAF < LEAF) ? n - J * LEAF : LEAF); };
+    auto own_index = [&](int64_t I) { return (int)((I - me) / P); };
 
-    // Stage the 64 x 64 block of L that block I needs from solved block J.
     auto stage = [&](int slot, int64_t I, int64_t J) {
-        const int64_t r0 = FWD ? I * LEAF : J * LEAF, c0 = FWD ? J * LEAF : I * LEAF;
-        const int nr = rows_of(FWD ? I : J), nc = rows_of(FWD ? J : I);
-        TL *dst = Ls + slot * LEAF * LEAF;
+        const int nI = rows_of(I), nJ = rows_of(J);
+        TL *dst = Ls + slot * LSTRIDE;
         for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) {
-            const int r = e % LEAF, c = e / LEAF;
-            if (r < nr && c < nc) cp_async_elem(dst + e, L + (r0 + r) + (c0 + c) * ldl, (int)sizeof(TL));
-            else dst[e] = TL(0);
+            // walk the global block down its columns (coalesced)
+            const int a = e % LEAF, b = e / LEAF;
+            const int t = FWD ? a : b, k = FWD ? b : a;
+            TL *d = dst + k * (LEAF + 1) + (k >> 4) * PQ + t;
+            const TL *src = FWD ? L + (I * LEAF + t) + (J * LEAF + k) * ldl : L + (J * LEAF + k) + (I * LEAF + t) * ldl;
+            if (t < nI && k < nJ) cp_async_elem(d, src, (int)sizeof(TL));
+            else *d = TL(0);
         }
     };
-    // Stage what solving block J needs: its inverse, B rows, partial sums.
+    // Both sweeps read the inverse block as Li[r + k * 68], the weight of
+    // v[k] in item r: forward that is (L_JJ^-1)(r, k), back (L_JJ^-1)(k, r).
     auto stage_solve = [&](int64_t J) {
         const double *src = Linv + J * LEAF * LEAF;
-        for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) cp_async_elem(Li + e, src + e, 8);
+        for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) {
+            const int a = e % LEAF, b = e / LEAF;
+            cp_async_elem(Li + (FWD ? a + b * ISTRIDE : b + a * ISTRIDE), src + e, 8);
+        }
         const int nb = rows_of(J);
         for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
             const int r = e % LEAF, c = e / LEAF;
-            if (r < nb) {
-                cp_async_elem(bst + e, B + J * LEAF + r + c * ldb, 8);
-                cp_async_elem(yst + e, Y + J * LEAF + r + c * ldy, 8);
-            } else {
-                bst[e] = 0.0;
-                yst[e] = 0.0;
-            }
+            if (r < nb) cp_async_elem(bst + e, B + J * LEAF + r + c * ldb, 8);
+            else bst[e] = 0.0;
         }
     };
 
-    // partial sums start at zero
-    for (int64_t I = me; I < N; I += P) {
-        const int nb = rows_of(I);
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
-            const int r = e % LEAF, c = e / LEAF;
-            if (r < nb) Y[I * LEAF + r + c * ldy] = 0.0;
-        }
-    }
+    for (int e = tid; e < nown * LEAF * nrhs; e += SW_THREADS) acc[e] = 0.0;
 
     // Solve block J from vv (= B_J - partial sums); write and publish.
-    // Four lanes share one (row, rhs) item and split its 64-term sum.
     auto finalize = [&](int64_t J) {
         const int nb = rows_of(J);
         const int p = tid & 3;
@@ -168,9 +183,9 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
             const int r = item % LEAF, c = item / LEAF;
             double s = 0.0;
             if (FWD) {
-                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * LEAF], vv[k + c * LEAF], s);
+                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * ISTRIDE], vv[k + c * LEAF], s);
             } else {
-                for (int k = r + ((p - r) & 3); k < LEAF; k += 4) s = fma(Li[k + r * LEAF], vv[k + c * LEAF], s);
+                for (int k = r + ((p - r) & 3); k < LEAF; k += 4) s = fma(Li[r + k * ISTRIDE], vv[k + c * LEAF], s);
             }
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
@@ -181,52 +196,32 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         if (tid == 0) st_release(&flags[J], epoch);
     };
 
-    // Contribution of the solved block (in yv) to block I, from the staged
-    // block in `slot`, into red[0][r + c*64] (summed over the four partial
-    // rows for FWD).  With an FP32 factor the block product runs in FP32.
-    auto contribution = [&](int slot, int64_t I) {
-        const int nbI = rows_of(I);
-        const TL *Lb = Ls + slot * LEAF * LEAF;
-        if (FWD) {
-            // thread (r, q) owns row r, columns 16q..16q+15 of the block
-            const int r = tid % LEAF, q = tid / LEAF;
-            TM a[16];
+    // Contribution of the solved block (in yv) to owned block I from the
+    // staged block in `slot`.  critical: vv = B_I - (partial sums + it);
+    // otherwise it is added to the partial sums.
+    auto contribution = [&](int slot, int64_t I, bool critical) {
+        const TL *Lb = Ls + slot * LSTRIDE;
+        double *a = acc + (size_t)own_index(I) * LEAF * nrhs;
+        const int nI = rows_of(I);
+        const int q = tid & 3;
+        for (int item = tid >> 2; item < LEAF * nrhs; item += SW_THREADS / 4) {
+            const int t = item % LEAF, c = item / LEAF;
+            const double *y = yv + c * YSTRIDE + q * 17;
+            const TL *l = Lb + (q * 16) * (LEAF + 1) + q * PQ + t;
+            TM s0 = 0, s1 = 0;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) a[k] = (TM)Lb[r + (q * 16 + k) * LEAF];
-            for (int c = 0; c < nrhs; ++c) {
-                TM pp = 0;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) pp = fma(a[k], (TM)yv[q * 16 + k + c * LEAF], pp);
-                red[q * LEAF * SW_MAXRHS + r + c * LEAF] = (double)pp;
+            for (int k = 0; k < 16; k += 2) {
+                s0 = fma((TM)l[k * (LEAF + 1)], (TM)y[k], s0);
+                s1 = fma((TM)l[(k + 1) * (LEAF + 1)], (TM)y[k + 1], s1);
             }
-            __syncthreads();
-            for (int e = tid; e < LEAF * nrhs; e += SW_THREADS)
-                red[e] = (e % LEAF < nbI) ? red[e] + red[LEAF * SW_MAXRHS + e] + red[2 * LEAF * SW_MAXRHS + e] +
-                                                red[3 * LEAF * SW_MAXRHS + e]
-                                          : 0.0;
-            __syncthreads();
-        } else {
-            // warp w owns columns w, w+8, ..., w+56 of block I; lanes hold
-            // rows lane and lane+32 of block J
-            for (int c = 0; c < nrhs; ++c) {
-                const TM y0 = (TM)yv[lane + c * LEAF], y1 = (TM)yv[lane + 32 + c * LEAF];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int i = warp + 8 * t;
-                    TM sum = fma((TM)Lb[lane + 32 + i * LEAF], y1, (TM)Lb[lane + i * LEAF] * y0);
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-                    if (lane == 0) red[i + c * LEAF] = (i < nbI) ? (double)sum : 0.0;
-                }
+            double s = (double)(s0 + s1);
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            if (q == 0) {
+                if (critical) vv[item] = (t < nI) ? bst[item] - (a[item] + s) : 0.0;
+                else a[item] += s;
             }
-            __syncthreads();
         }
-    };
-    auto add_to_Y = [&](int64_t I) {
-        const int nbI = rows_of(I);
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS)
-            if (e % LEAF < nbI) Y[I * LEAF + e % LEAF + (e / LEAF) * ldy] += red[e];
-        __syncthreads();
     };
 
     __syncthreads();
@@ -236,7 +231,7 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = bst[e] - yst[e];
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = bst[e];
         __syncthreads();
         finalize(first);
     }
@@ -244,8 +239,6 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         const int64_t J = FWD ? s : N - 1 - s;
         const int64_t next = FWD ? J + 1 : J - 1;
         const bool own_next = next >= 0 && next < N && next % P == me;
-        // Owned blocks to update with y_J, in sweep order: next first (if
-        // owned), then the rest.
         int64_t cur = next;
         if (!own_next) {
             if (FWD) {
@@ -258,8 +251,8 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         }
         auto in_range = [&](int64_t I) { return FWD ? (I > J && I < N) : (I < J && I >= 0); };
         int staged = 0;
-        int64_t chunk[SW_SLOTS];
-        while (staged < SW_SLOTS && in_range(cur)) {
+        int64_t chunk[SLOTS];
+        while (staged < SLOTS && in_range(cur)) {
             chunk[staged] = cur;
             stage(staged, cur, J);
             ++staged;
@@ -290,25 +283,23 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         }
         for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
             const int r = e % LEAF, c = e / LEAF;
-            yv[e] = (r < rows_of(J)) ? __ldcg(&Y[J * LEAF + r + c * ldy]) : 0.0;
+            yv[c * YSTRIDE + (r >> 4) * 17 + (r & 15)] = (r < rows_of(J)) ? __ldcg(&Y[J * LEAF + r + c * ldy]) : 0.0;
         }
         cp_async_wait_all();
         __syncthreads();
         for (int q = 0; q < staged; ++q) {
-            contribution(q, chunk[q]);
-            if (q == 0 && own_next) {
-                for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = bst[e] - yst[e] - red[e];
+            const bool crit = (q == 0 && own_next);
+            contribution(q, chunk[q], crit);
+            if (crit) {
                 __syncthreads();
                 finalize(next);
-            } else {
-                add_to_Y(chunk[q]);
             }
         }
         // owned blocks beyond the first chunk
         while (in_range(cur)) {
             __syncthreads();
             int cnt = 0;
-            while (cnt < SW_SLOTS && in_range(cur)) {
+            while (cnt < SLOTS && in_range(cur)) {
                 chunk[cnt] = cur;
                 stage(cnt, cur, J);
                 ++cnt;
@@ -317,10 +308,7 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
             cp_async_commit();
             cp_async_wait_all();
             __syncthreads();
-            for (int q = 0; q < cnt; ++q) {
-                contribution(q, chunk[q]);
-                add_to_Y(chunk[q]);
-            }
+            for (int q = 0; q < cnt; ++q) contribution(q, chunk[q], false);
         }
         __syncthreads();
     }
@@ -345,17 +333,19 @@ gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_
                          const double *B, int64_t ldb, double *Y, int64_t ldy, unsigned *flags, unsigned epoch,
                          int *err, cudaStream_t st)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)sweep_smem_bytes<TL>()));
-        attr_done = true;
-    }
     const int64_t N = (n + LEAF - 1) / LEAF;
     const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
+    const int nown = (int)((N + P - 1) / P);
+    const size_t smem = sweep_smem_bytes<TL>(nown, nrhs);
+    int maxsmem = 0;
+    GPCH_CUDA(ctx, cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (smem + 1024 > (size_t)maxsmem)
+        return gpch::fail(ctx, GPCH_INVALID_ARG, "substitution sweep: n * nrhs too large for shared memory");
+    GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
     void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &epoch, &err};
     GPCH_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)trsv_sweep_kernel<TL, FWD>, dim3(P), dim3(SW_THREADS),
-                                               args, sweep_smem_bytes<TL>(), st));
+                                               args, smem, st));
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -415,8 +405,14 @@ gpch_status solve_apply_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, do
 {
     const int64_t N = (n + LEAF - 1) / LEAF;
     PhaseScope ph(ctx, GPCH_PHASE_SOLVE, st, 2.0 * (double)n * n * nrhs);
-    for (int c0 = 0; c0 < nrhs; c0 += SW_MAXRHS) {
-        const int g = (nrhs - c0 < SW_MAXRHS) ? nrhs - c0 : SW_MAXRHS;
+    // right-hand sides per sweep: at most 16, fewer if the owned blocks'
+    // partial sums would not fit in shared memory
+    const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
+    const int nown = (int)((N + P - 1) / P);
+    int gmax = SW_MAXRHS;
+    while (gmax > 1 && sweep_smem_bytes<TL>(nown, gmax) > 200 * 1024) gmax /= 2;
+    for (int c0 = 0; c0 < nrhs; c0 += gmax) {
+        const int g = (nrhs - c0 < gmax) ? nrhs - c0 : gmax;
         double *Bc = B + (int64_t)c0 * ldb;
         ++w.epoch;
         GPCH_CHECK((launch_sweep<TL, true>(ctx, n, g, L, ldl, w.Linv, Bc, ldb, w.Y, n, w.flags, w.epoch, w.err,
