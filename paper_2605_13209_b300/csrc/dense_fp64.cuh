@@ -485,9 +485,11 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
 // diagonal blocks of L once per factor, solve_apply then overwrites B
 // (n x nrhs) with (L L^T)^-1 B.  The _f32 forms take an FP32 factor.
 struct SolveWs {
-    double *Linv;
-    double *Y;
-    unsigned *flags;
+    double *Linv;                   // inverted diagonal blocks (FP32 values for an FP32 factor)
+    double *Y;                      // forward-sweep result
+    unsigned *flags;                // per-block "solved" flags, FP64 sweeps
+    unsigned long long *tagw;       // tagged (value, tag) words, FP32 sweeps
+    size_t tagw_words;
     int *err;
     unsigned epoch;
 };

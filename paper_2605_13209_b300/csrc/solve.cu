@@ -14,6 +14,7 @@
 // are FP64; with the FP32 (preconditioner) factor each 64 x 64 block
 // product runs in FP32 and is added to FP64 partial sums, and the diagonal
 // block solves stay FP64.
+#include <mutex>
 #include <type_traits>
 
 #include "dense_fp64.cuh"
@@ -26,9 +27,16 @@ constexpr int SW_THREADS = 256;
 constexpr int SW_MAXRHS = 16;
 constexpr uint32_t FLAG_SPIN_LIMIT = 1u << 22;
 
+// Arithmetic type of the sweep: FP32 products for an FP32 factor, FP64
+// for an FP64 factor.
+template <typename TL>
+using sweep_math_t = typename std::conditional<sizeof(TL) == 4, float, double>::type;
+
+// Inverts the 64 x 64 diagonal blocks of L in FP64 and stores them in the
+// sweep's arithmetic type.
 template <typename TL>
 __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const TL *__restrict__ L,
-                                                              int64_t ldl, double *Linv)
+                                                              int64_t ldl, sweep_math_t<TL> *Linv)
 {
     extern __shared__ double inv_smem[];
     double (*S)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(inv_smem);
@@ -48,10 +56,10 @@ __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const T
     __syncthreads();
     gpch::invert_lower_64(S, Vi);
     __syncthreads();
-    double *dst = Linv + J * LEAF * LEAF;
+    sweep_math_t<TL> *dst = Linv + J * LEAF * LEAF;
     for (int e = threadIdx.x; e < LEAF * LEAF; e += blockDim.x) {
         int r = e % LEAF, c = e / LEAF;
-        dst[r + c * LEAF] = Vi[r][c];
+        dst[r + c * LEAF] = (sweep_math_t<TL>)Vi[r][c];
     }
 }
 
@@ -65,6 +73,18 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int bytes)
@@ -94,18 +114,26 @@ constexpr int padq()
 }
 constexpr int LSTRIDE = LEAF * (LEAF + 1) + 32;
 constexpr int YSTRIDE = 4 * 17;   // solved block: rhs c, row r at c * 68 + (r / 16) * 17 + r % 16
-constexpr int ISTRIDE = LEAF + 4; // inverse block, column stride
+// Inverse block, column stride: r + 4p (FP64, half-warp) or r + 8p (FP32,
+// warp) then fall in distinct banks.
+template <typename TL>
+constexpr int istride()
+{
+    return sizeof(TL) == 4 ? LEAF + 8 : LEAF + 4;
+}
 
 // Dynamic shared memory of one sweep CTA owning `nown` blocks.
 template <typename TL>
 size_t sweep_smem_bytes(int nown, int nrhs)
 {
-    return (size_t)SW_MAXRHS * (YSTRIDE + 2 * LEAF) * sizeof(double) + (size_t)LEAF * ISTRIDE * sizeof(double) +
-           (size_t)sweep_slots<TL>() * LSTRIDE * sizeof(TL) + (size_t)nown * LEAF * nrhs * sizeof(double);
+    using TM = sweep_math_t<TL>;
+    return (size_t)SW_MAXRHS * LEAF * sizeof(double) + (size_t)SW_MAXRHS * (YSTRIDE + LEAF) * sizeof(TM) +
+           (size_t)LEAF * istride<TL>() * sizeof(TM) + (size_t)sweep_slots<TL>() * LSTRIDE * sizeof(TL) +
+           (size_t)nown * LEAF * nrhs * sizeof(double);
 }
 
 // One sweep.  FWD: Y = L^-1 B.  BWD: Y = L^-T B.  Y (n x nrhs, ldy) gets
-// the solved blocks; flags[J] == epoch marks block J solved.  nrhs <= 16.
+// the solved blocks.  nrhs <= 16.
 //
 // CTA `me` owns blocks me, me + P, ... and keeps their partial sums in
 // shared memory.  Per step J every CTA first starts copying into shared
@@ -116,30 +144,40 @@ size_t sweep_smem_bytes(int nown, int nrhs)
 // (item, rhs) sum of 64 terms is split over four adjacent lanes and joined
 // by two shuffles, so updates need no barrier of their own.  The owner of
 // the next block updates, solves and publishes it before its other updates,
-// so the serial chain per block is: flag seen -> y_J read -> one 64 x 64
-// block product -> one 64 x 64 inverse-block product -> publish.
+// so the serial chain per block is: y_J seen -> one 64 x 64 block product
+// -> one 64 x 64 inverse-block product -> publish.
+//
+// Publishing.  FP32 factor: each solved value goes out as one 64-bit word,
+// its FP32 value in the low half and the sweep's tag in the high half, so
+// a reader polls the words themselves and needs no flag, fence or second
+// read (the products use the FP32 value; Y gets the FP64 one).  FP64
+// factor: Y is written, then flags[J] = tag with release semantics; readers
+// acquire the flag and read Y.
 template <typename TL, bool FWD>
 __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int nrhs, const TL *__restrict__ L,
-                                                                int64_t ldl, const double *__restrict__ Linv,
+                                                                int64_t ldl, const sweep_math_t<TL> *__restrict__ Linv,
                                                                 const double *B, int64_t ldb, double *Y, int64_t ldy,
-                                                                unsigned *flags, unsigned epoch, int *err)
+                                                                unsigned *flags, unsigned long long *tagw,
+                                                                unsigned tag, int *err)
 {
+    using TM = sweep_math_t<TL>;
+    constexpr bool TAGGED = sizeof(TL) == 4;
     constexpr int SLOTS = sweep_slots<TL>();
-    extern __shared__ __align__(16) double sw_smem[];
     constexpr int PQ = padq<TL>();
-    double *yv = sw_smem;                          // solved block being applied [16 * 68]
-    double *vv = yv + YSTRIDE * SW_MAXRHS;         // right-hand side of the block being solved
-    double *bst = vv + LEAF * SW_MAXRHS;           // staged B rows of the next block
-    double *Li = bst + LEAF * SW_MAXRHS;           // inverse of the next block, (r, k) at r + k * 68
-    TL *Ls = reinterpret_cast<TL *>(Li + LEAF * ISTRIDE);                    // [SLOTS][LSTRIDE]
-    double *acc = reinterpret_cast<double *>(Ls + SLOTS * LSTRIDE);         // [owned][64 * nrhs]
+    constexpr int IS = istride<TL>();
+    extern __shared__ __align__(16) double sw_smem[];
+    double *bst = sw_smem;                                        // staged B rows of the next block
+    TM *yv = reinterpret_cast<TM *>(bst + LEAF * SW_MAXRHS);      // solved block being applied [16 * 68]
+    TM *vv = yv + YSTRIDE * SW_MAXRHS;                            // right-hand side of the block being solved
+    TM *Li = vv + LEAF * SW_MAXRHS;                               // inverse of the next block, (r, k) at r + k * IS
+    TL *Ls = reinterpret_cast<TL *>(Li + LEAF * IS);              // [SLOTS][LSTRIDE]
+    double *acc = reinterpret_cast<double *>(Ls + SLOTS * LSTRIDE);  // [owned][64 * nrhs]
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
     const int64_t N = (n + LEAF - 1) / LEAF;
     const int64_t P = gridDim.x, me = blockIdx.x;
     const int nown = (int)((N - me + P - 1) / P);
     if (tid == 0) abort_flag = 0;
-    using TM = typename std::conditional<sizeof(TL) == 4, float, double>::type;
 
     auto rows_of = [&](int64_t J) { return (int)((n - J * LEAF < LEAF) ? n - J * LEAF : LEAF); };
     auto own_index = [&](int64_t I) { return (int)((I - me) / P); };
@@ -157,13 +195,13 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
             else *d = TL(0);
         }
     };
-    // Both sweeps read the inverse block as Li[r + k * 68], the weight of
+    // Both sweeps read the inverse block as Li[r + k * IS], the weight of
     // v[k] in item r: forward that is (L_JJ^-1)(r, k), back (L_JJ^-1)(k, r).
     auto stage_solve = [&](int64_t J) {
-        const double *src = Linv + J * LEAF * LEAF;
+        const TM *src = Linv + J * LEAF * LEAF;
         for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) {
             const int a = e % LEAF, b = e / LEAF;
-            cp_async_elem(Li + (FWD ? a + b * ISTRIDE : b + a * ISTRIDE), src + e, 8);
+            cp_async_elem(Li + (FWD ? a + b * IS : b + a * IS), src + e, (int)sizeof(TM));
         }
         const int nb = rows_of(J);
         for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
@@ -181,19 +219,26 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         const int p = tid & 3;
         for (int item = tid >> 2; item < LEAF * nrhs; item += SW_THREADS / 4) {
             const int r = item % LEAF, c = item / LEAF;
-            double s = 0.0;
+            TM s = 0;
             if (FWD) {
-                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * ISTRIDE], vv[k + c * LEAF], s);
+                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * IS], vv[k + c * LEAF], s);
             } else {
-                for (int k = r + ((p - r) & 3); k < LEAF; k += 4) s = fma(Li[r + k * ISTRIDE], vv[k + c * LEAF], s);
+                for (int k = r + ((p - r) & 3); k < LEAF; k += 4) s = fma(Li[r + k * IS], vv[k + c * LEAF], s);
             }
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
-            if (p == 0 && r < nb) Y[J * LEAF + r + c * ldy] = s;
+            if (p == 0) {
+                if (r < nb) Y[J * LEAF + r + c * ldy] = (double)s;
+                if constexpr (TAGGED)
+                    st_relaxed_u64(tagw + J * LEAF * nrhs + item,
+                                   ((unsigned long long)tag << 32) | __float_as_uint(r < nb ? (float)s : 0.0f));
+            }
         }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) st_release(&flags[J], epoch);
+        if constexpr (!TAGGED) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_release(&flags[J], tag);
+        }
     };
 
     // Contribution of the solved block (in yv) to owned block I from the
@@ -206,21 +251,70 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         const int q = tid & 3;
         for (int item = tid >> 2; item < LEAF * nrhs; item += SW_THREADS / 4) {
             const int t = item % LEAF, c = item / LEAF;
-            const double *y = yv + c * YSTRIDE + q * 17;
+            const TM *y = yv + c * YSTRIDE + q * 17;
             const TL *l = Lb + (q * 16) * (LEAF + 1) + q * PQ + t;
             TM s0 = 0, s1 = 0;
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
-                s0 = fma((TM)l[k * (LEAF + 1)], (TM)y[k], s0);
-                s1 = fma((TM)l[(k + 1) * (LEAF + 1)], (TM)y[k + 1], s1);
+                s0 = fma((TM)l[k * (LEAF + 1)], y[k], s0);
+                s1 = fma((TM)l[(k + 1) * (LEAF + 1)], y[k + 1], s1);
             }
-            double s = (double)(s0 + s1);
+            TM s = s0 + s1;
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
             if (q == 0) {
-                if (critical) vv[item] = (t < nI) ? bst[item] - (a[item] + s) : 0.0;
-                else a[item] += s;
+                if (critical) vv[item] = (t < nI) ? (TM)(bst[item] - (a[item] + (double)s)) : TM(0);
+                else a[item] += (double)s;
             }
+        }
+    };
+
+    // Wait for block J and load it into yv.  False: a wait gave up.
+    auto receive = [&](int64_t J) {
+        bool ok = true;
+        if constexpr (TAGGED) {
+            for (int e = tid; e < LEAF * nrhs && ok; e += SW_THREADS) {
+                const unsigned long long *w = tagw + J * LEAF * nrhs + e;
+                unsigned long long v = ld_relaxed_u64(w);
+                for (uint32_t it = 0; (unsigned)(v >> 32) != tag; ++it) {
+                    if (it >= FLAG_SPIN_LIMIT) {
+                        ok = false;
+                        break;
+                    }
+                    if (it > 4096) __nanosleep(64);
+                    v = ld_relaxed_u64(w);
+                }
+                const int r = e % LEAF, c = e / LEAF;
+                yv[c * YSTRIDE + (r >> 4) * 17 + (r & 15)] = __uint_as_float((unsigned)v);
+            }
+            if (!ok) {
+                abort_flag = 1;
+                atomicExch(err, 1);
+            }
+            return ok;
+        } else {
+            if (J % P != me && tid == 0) {
+                ok = false;
+                for (uint32_t it = 0; it < FLAG_SPIN_LIMIT; ++it) {
+                    if (ld_acquire(&flags[J]) == tag) {
+                        ok = true;
+                        break;
+                    }
+                    if (it > 4096) __nanosleep(64);
+                }
+                if (!ok) {
+                    abort_flag = 1;
+                    atomicExch(err, 1);
+                }
+            }
+            __syncthreads();
+            if (abort_flag) return false;
+            for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
+                const int r = e % LEAF, c = e / LEAF;
+                yv[c * YSTRIDE + (r >> 4) * 17 + (r & 15)] =
+                    (r < rows_of(J)) ? __ldcg(&Y[J * LEAF + r + c * ldy]) : 0.0;
+            }
+            return true;
         }
     };
 
@@ -231,9 +325,10 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = bst[e];
+        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = (TM)bst[e];
         __syncthreads();
         finalize(first);
+        __syncthreads();
     }
     for (int64_t s = 0; s < N; ++s) {
         const int64_t J = FWD ? s : N - 1 - s;
@@ -260,33 +355,10 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         }
         if (own_next) stage_solve(next);
         cp_async_commit();
-        if (J % P != me) {
-            if (tid == 0) {
-                bool ok = false;
-                for (uint32_t it = 0; it < FLAG_SPIN_LIMIT; ++it) {
-                    if (ld_acquire(&flags[J]) == epoch) {
-                        ok = true;
-                        break;
-                    }
-                    if (it > 4096) __nanosleep(64);
-                }
-                if (!ok) {
-                    abort_flag = 1;
-                    atomicExch(err, 1);
-                }
-            }
-            __syncthreads();
-            if (abort_flag) {
-                cp_async_wait_all();
-                return;
-            }
-        }
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
-            const int r = e % LEAF, c = e / LEAF;
-            yv[c * YSTRIDE + (r >> 4) * 17 + (r & 15)] = (r < rows_of(J)) ? __ldcg(&Y[J * LEAF + r + c * ldy]) : 0.0;
-        }
+        receive(J);
         cp_async_wait_all();
         __syncthreads();
+        if (abort_flag) return;
         for (int q = 0; q < staged; ++q) {
             const bool crit = (q == 0 && own_next);
             contribution(q, chunk[q], crit);
@@ -329,10 +401,11 @@ int sm_count(gpch_ctx *ctx)
 }
 
 template <typename TL, bool FWD>
-gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_t ldl, const double *Linv,
-                         const double *B, int64_t ldb, double *Y, int64_t ldy, unsigned *flags, unsigned epoch,
-                         int *err, cudaStream_t st)
+gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_t ldl, const double *Linv_ws,
+                         const double *B, int64_t ldb, double *Y, int64_t ldy, unsigned *flags,
+                         unsigned long long *tagw, unsigned tag, int *err, cudaStream_t st)
 {
+    const sweep_math_t<TL> *Linv = reinterpret_cast<const sweep_math_t<TL> *>(Linv_ws);
     const int64_t N = (n + LEAF - 1) / LEAF;
     const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
     const int nown = (int)((N + P - 1) / P);
@@ -341,9 +414,20 @@ gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_
     GPCH_CUDA(ctx, cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (smem + 1024 > (size_t)maxsmem)
         return gpch::fail(ctx, GPCH_INVALID_ARG, "substitution sweep: n * nrhs too large for shared memory");
-    GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &epoch, &err};
+    {
+        // Raised once per device to the largest size any launch may ask for:
+        // the needed size varies with n and nrhs, and contexts on other host
+        // threads launch this kernel concurrently.
+        static std::mutex mu;
+        static bool done[64] = {};
+        std::lock_guard<std::mutex> lock(mu);
+        if (ctx->device >= 64 || !done[ctx->device]) {
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - 1024));
+            if (ctx->device < 64) done[ctx->device] = true;
+        }
+    }
+    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &tagw, &tag, &err};
     GPCH_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)trsv_sweep_kernel<TL, FWD>, dim3(P), dim3(SW_THREADS),
                                                args, smem, st));
     GPCH_LAUNCH_CHECK(ctx);
@@ -361,6 +445,7 @@ size_t solve_ws_bytes(int64_t n, int nrhs)
     dry.take<double>((size_t)N * LEAF * LEAF);
     dry.take<double>((size_t)n * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
     dry.take<unsigned>((size_t)2 * N);
+    dry.take<unsigned long long>((size_t)N * LEAF * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
     dry.take<int>(4);
     return dry.off;
 }
@@ -373,6 +458,8 @@ SolveWs carve_solve(void *base, int64_t n, int nrhs)
     w.Linv = cv.take<double>((size_t)N * LEAF * LEAF);
     w.Y = cv.take<double>((size_t)n * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
     w.flags = cv.take<unsigned>((size_t)2 * N);
+    w.tagw_words = (size_t)N * LEAF * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS);
+    w.tagw = cv.take<unsigned long long>(w.tagw_words);
     w.err = cv.take<int>(4);
     w.epoch = 0;
     return w;
@@ -390,9 +477,11 @@ gpch_status solve_prepare_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, 
                                             (int)INV_SMEM));
         attr_done = true;
     }
-    inv_diag_blocks_kernel<TL><<<(unsigned)N, 256, INV_SMEM, st>>>(n, L, ldl, w.Linv);
+    inv_diag_blocks_kernel<TL>
+        <<<(unsigned)N, 256, INV_SMEM, st>>>(n, L, ldl, reinterpret_cast<sweep_math_t<TL> *>(w.Linv));
     GPCH_LAUNCH_CHECK(ctx);
     GPCH_CUDA(ctx, cudaMemsetAsync(w.flags, 0, 2 * N * sizeof(unsigned), st));
+    GPCH_CUDA(ctx, cudaMemsetAsync(w.tagw, 0, w.tagw_words * sizeof(unsigned long long), st));
     GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), st));
     w.epoch = 0;
     return GPCH_OK;
@@ -414,11 +503,13 @@ gpch_status solve_apply_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, do
     for (int c0 = 0; c0 < nrhs; c0 += gmax) {
         const int g = (nrhs - c0 < gmax) ? nrhs - c0 : gmax;
         double *Bc = B + (int64_t)c0 * ldb;
+        // tags 2e (forward) and 2e + 1 (back) of epoch e >= 1 never match
+        // the cleared words or an earlier sweep's
         ++w.epoch;
-        GPCH_CHECK((launch_sweep<TL, true>(ctx, n, g, L, ldl, w.Linv, Bc, ldb, w.Y, n, w.flags, w.epoch, w.err,
-                                           st)));
-        GPCH_CHECK((launch_sweep<TL, false>(ctx, n, g, L, ldl, w.Linv, w.Y, n, Bc, ldb, w.flags + N, w.epoch,
-                                            w.err, st)));
+        GPCH_CHECK((launch_sweep<TL, true>(ctx, n, g, L, ldl, w.Linv, Bc, ldb, w.Y, n, w.flags, w.tagw, 2 * w.epoch,
+                                           w.err, st)));
+        GPCH_CHECK((launch_sweep<TL, false>(ctx, n, g, L, ldl, w.Linv, w.Y, n, Bc, ldb, w.flags + N, w.tagw,
+                                            2 * w.epoch + 1, w.err, st)));
     }
     return GPCH_OK;
 }
