@@ -89,6 +89,23 @@ __device__ inline void pivot_sqrt(double d, double &s, double &y)
     }
 }
 
+// Reciprocal of a positive pivot d: FP32 seed y0 (rcp.approx), then one
+// Newton-Raphson step taken to third order, y = y0 (1 + e + e^2) with
+// e = 1 - d y0 (the truncated series of 1 / (1 - e)); with |e| < 2^-21 the
+// truncation error is below 2^-63, so the result is within about one unit
+// in the last place.  Outside the FP32 range the division is used.
+__device__ inline double pivot_rcp(double d)
+{
+    if (d > 1e-30 && d < 1e30) {
+        float yf;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)d));
+        const double y0 = (double)yf;
+        const double e = fma(-d, y0, 1.0);
+        return fma(y0, fma(e, e, e), y0);
+    }
+    return 1.0 / d;
+}
+
 }  // namespace gpch
 
 // Kernels and their launchers have internal linkage: every translation unit
@@ -97,19 +114,19 @@ namespace {
 
 using gpch::LEAF;
 
-// Panel leaf solve: X = B inv(L)^T in place on the m x nc panel B (nc <=
-// 64), inv(L) given as a 64 x 64 FP64 block (column-major, ld 64).  Every
-// CTA owns ROWS whole rows, so reading B and writing X never overlap across
-// CTAs.  T is the storage and arithmetic type of B.  Thread t owns row
-// t % ROWS and every (256/ROWS)-th column from t / ROWS.
 // Step 1 leaf: factor the nb x nb (nb <= W, W = 32 or 64) lower block at A
-// in place.  Right-looking: thread (tx, ty) keeps the (W/16)^2 entries
-// (tx + 16i, ty + 16j) in registers; per column j the owner of the pivot
-// takes the square root, the owners of column j scale it by the reciprocal
-// and publish it, and every thread updates its own entries below and right
-// of the pivot.  Outputs: rinv[c] = 1 / L_cc (c < W; 1 in the padding) and,
-// when Linv is not null (W = 64 only), inv(L) of the unit-padded block
-// (column-major, ld 64).  leaf_smem: 2 * 64 * 65 doubles.
+// in place.  Thread (tx, ty) keeps the (W/16)^2 entries (tx + 16i, ty + 16j)
+// in registers.  The column sweep is square-root free: step j subtracts
+// a_rj * (a_cj / d_j) from every entry (r, c) with r >= c > j, which is the
+// right-looking Cholesky update l_rj l_cj written with the unscaled column
+// (a_rj = l_rj sqrt(d_j)).  The entries of column j are final after step
+// j - 1 and are never touched again, so at the end L_rc = a_rc / sqrt(d_c)
+// and L_cc = sqrt(d_c), with all square roots taken at once.  Per step one
+// barrier: the owner of the next pivot updates it, takes its reciprocal and
+// publishes it together with the next column while the other threads finish
+// their updates (one-column lookahead).  Outputs: rinv[c] = 1 / L_cc (c < W;
+// 1 in the padding) and, when Linv is not null (W = 64 only), inv(L) of the
+// unit-padded block (column-major, ld 64).  leaf_smem: 2 * 64 * 65 doubles.
 template <int W>
 __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *rinv, double *Linv, int64_t col0,
                                        int64_t *info, double *leaf_smem)
@@ -117,8 +134,10 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
     constexpr int RT = W / 16;
     double (*S)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem);
     double (*Vi)[LEAF + 1] = reinterpret_cast<double (*)[LEAF + 1]>(leaf_smem + LEAF * (LEAF + 1));
-    __shared__ double lbuf[2][LEAF];   // column j of L, double-buffered by the parity of j
-    __shared__ double rbuf[LEAF];
+    __shared__ double ucol[2][LEAF];   // column j before scaling, by the parity of j
+    __shared__ double rdb[2];          // 1 / d_j, by the parity of j
+    __shared__ double dpiv[LEAF];      // pivots d_j
+    __shared__ double sqv[LEAF], rsv[LEAF];
     __shared__ int bad;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     double a[RT][RT];
@@ -133,62 +152,75 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
             a[i][j] = v;
         }
     if (tid == 0) bad = 0;
-    if (tid < LEAF) rbuf[tid] = 1.0;
+    __syncthreads();
+    if (ty == 0) {
+#pragma unroll
+        for (int i = 0; i < RT; ++i) ucol[0][tx + 16 * i] = a[i][0];
+    }
+    if (tid == 0) {
+        const double d = a[0][0];
+        dpiv[0] = d;
+        if (!(d > 0.0) || !isfinite(d)) bad = 1;
+        else rdb[0] = gpch::pivot_rcp(d);
+    }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        const int jq = j / 16, jr = j % 16;
-        double *lcol = lbuf[j & 1];
-        // pivot owner: row j = tx + 16 jq, column j = ty + 16 jq
-        if (tx == jr && ty == jr) {
-            double d = a[jq][jq];
-            if (!(d > 0.0) || !isfinite(d)) {
-                bad = j + 1;
-            } else {
-                double sq, rs;
-                gpch::pivot_sqrt(d, sq, rs);
-                a[jq][jq] = sq;
-                lcol[j] = rs;   // the column is scaled by the reciprocal
-                rbuf[j] = rs;
-            }
-        }
-        __syncthreads();
         if (bad) break;
-        if (ty == jr) {
-            const double rr = lcol[j];
+        const double rd = rdb[j & 1];
+        const double *uc = ucol[j & 1];
+        const int j1 = j + 1;
+        const bool more = j1 < nb;
+        const int jq = j1 / 16, jr = j1 % 16;
+#pragma unroll
+        for (int jj = 0; jj < RT; ++jj) {
+            const int c = ty + 16 * jj;
+            if (c <= j) continue;
+            const double lc = uc[c] * rd;
 #pragma unroll
             for (int i = 0; i < RT; ++i) {
                 const int r = tx + 16 * i;
-                if (r > j) {
-                    a[i][jq] *= rr;
-                    lcol[r] = a[i][jq];
+                if (r >= c) a[i][jj] = fma(-uc[r], lc, a[i][jj]);
+            }
+        }
+        if (more && ty == jr) {
+#pragma unroll
+            for (int jj = 0; jj < RT; ++jj) {
+                if (jj != jq) continue;
+#pragma unroll
+                for (int i = 0; i < RT; ++i) {
+                    const int r = tx + 16 * i;
+                    if (r > j1) ucol[j1 & 1][r] = a[i][jj];
+                    if (r == j1) {
+                        const double d = a[i][jj];
+                        dpiv[j1] = d;
+                        if (!(d > 0.0) || !isfinite(d)) bad = j1 + 1;
+                        else rdb[j1 & 1] = gpch::pivot_rcp(d);
+                    }
                 }
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < RT; ++i) {
-            const int r = tx + 16 * i;
-            if (r <= j) continue;
-            const double lr = lcol[r];
-#pragma unroll
-            for (int jj = 0; jj < RT; ++jj) {
-                const int c = ty + 16 * jj;
-                if (c > j && c <= r) a[i][jj] -= lr * lcol[c];
-            }
-        }
     }
     if (bad) {
         if (tid == 0) *info = col0 + bad;
         return;
     }
+    if (tid < W) {
+        double sq = 1.0, rs = 1.0;
+        if (tid < nb) gpch::pivot_sqrt(dpiv[tid], sq, rs);
+        sqv[tid] = sq;
+        rsv[tid] = rs;
+    }
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int j = 0; j < RT; ++j) {
             const int r = tx + 16 * i, c = ty + 16 * j;
+            a[i][j] = (r > c) ? a[i][j] * rsv[c] : (r == c ? sqv[c] : 0.0);
             if (r < nb && c < nb && r >= c) A[r + c * lda] = a[i][j];
         }
-    if (rinv && tid < W) rinv[tid] = rbuf[tid];
+    if (rinv && tid < W) rinv[tid] = rsv[tid];
     if (Linv == nullptr) return;
     // inverse of the unit-padded 64 x 64 block (W == 64)
 #pragma unroll
@@ -299,11 +331,6 @@ __device__ inline void trsm_inv_body(T *B, int64_t ldb, int64_t m, int nc, const
         }
 }
 
-// Panel leaf solve: X = B inv(L)^T in place on the m x nc panel B (nc <=
-// 64), inv(L) given as a 64 x 64 FP64 block (column-major, ld 64).  Every
-// CTA owns ROWS whole rows, so reading B and writing X never overlap across
-// CTAs.  T is the storage and arithmetic type of B.  Thread t owns row
-// t % ROWS and every (256/ROWS)-th column from t / ROWS.
 template <typename T, int ROWS>
 __global__ void __launch_bounds__(256) trsm_inv_kernel(T *B, int64_t ldb, int64_t m, int nc,
                                                        const double *__restrict__ Linv, const int64_t *info)
