@@ -240,28 +240,30 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
 // (nc <= 64), with L a lower nc x nc FP64 block (ld ldl) and rinv its
 // diagonal reciprocals.  Column-oriented (right-looking): x_c = b_c / L_cc,
 // then b_k -= x_c L[k][c] for every k > c.  One warp per RPW rows; lane l
-// holds columns l and l + 32 of each of its rows, so a column costs one
-// shuffle and three FMA-class instructions per row.  The CTA's 8 * RPW rows
-// are staged through shared memory so that global reads and writes stay
-// coalesced.  T is the storage and arithmetic type of B.
-template <typename T, int RPW>
-__global__ void __launch_bounds__(256) trsm_sub_kernel(T *B, int64_t ldb, int64_t m, int nc,
-                                                       const double *__restrict__ L, int64_t ldl,
-                                                       const double *__restrict__ rinv, const int64_t *info)
+// holds columns l and l + 32 of each of its rows (NARROW, nc <= 32: column
+// l only), so a column costs one shuffle and three (NARROW: two) FMA-class
+// instructions per row.  The CTA's WARPS * RPW rows are staged through
+// shared memory so that global reads and writes stay coalesced.  T is the
+// storage and arithmetic type of B.
+template <typename T, int RPW, int WARPS = 8, bool NARROW = false>
+__global__ void __launch_bounds__(WARPS * 32) trsm_sub_kernel(T *B, int64_t ldb, int64_t m, int nc,
+                                                              const double *__restrict__ L, int64_t ldl,
+                                                              const double *__restrict__ rinv, const int64_t *info)
 {
-    constexpr int ROWS = 8 * RPW;
-    __shared__ T Ls[LEAF][LEAF + 1];   // Ls[k][c] = L[k][c]
-    __shared__ T rs[LEAF];
-    __shared__ T Bs[LEAF][ROWS + 1];
+    constexpr int ROWS = WARPS * RPW;
+    constexpr int KR = NARROW ? 32 : LEAF;   // columns held
+    __shared__ T Ls[KR][KR + 1];   // Ls[k][c] = L[k][c]
+    __shared__ T rs[KR];
+    __shared__ T Bs[KR][ROWS + 1];
     if (info && *info != 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * ROWS;
-    for (int e = tid; e < LEAF * LEAF; e += blockDim.x) {
-        const int k = e % LEAF, c = e / LEAF;   // column-major walk: coalesced
+    for (int e = tid; e < KR * KR; e += blockDim.x) {
+        const int k = e % KR, c = e / KR;   // column-major walk: coalesced
         Ls[k][c] = (k > c && k < nc && c < nc) ? (T)L[k + (int64_t)c * ldl] : T(0);
     }
-    if (tid < LEAF) rs[tid] = tid < nc ? (T)rinv[tid] : T(1);
-    for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
+    if (tid < KR) rs[tid] = tid < nc ? (T)rinv[tid] : T(1);
+    for (int e = tid; e < KR * ROWS; e += blockDim.x) {
         const int r = e % ROWS, k = e / ROWS;
         Bs[k][r] = (r0 + r < m && k < nc) ? B[(r0 + r) + (int64_t)k * ldb] : T(0);
     }
@@ -270,12 +272,22 @@ __global__ void __launch_bounds__(256) trsm_sub_kernel(T *B, int64_t ldb, int64_
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
         b0[q] = Bs[lane][warp * RPW + q];
-        b1[q] = Bs[lane + 32][warp * RPW + q];
+        b1[q] = NARROW ? T(0) : Bs[lane + 32 - (NARROW ? 32 : 0)][warp * RPW + q];
     }
     for (int c = 0; c < nc; ++c) {
-        const T l0 = Ls[lane][c], l1 = Ls[lane + 32][c];   // zero on and above the diagonal
+        const T l0 = Ls[lane][c];   // zero on and above the diagonal
         const T rc = rs[c];
         const int src = c & 31;
+        if (NARROW) {
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const T xc = __shfl_sync(0xffffffffu, b0[q], src) * rc;
+                if (lane == src) b0[q] = xc;
+                b0[q] = fma(-xc, l0, b0[q]);
+            }
+            continue;
+        }
+        const T l1 = Ls[lane + 32 - (NARROW ? 32 : 0)][c];
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
             const T xc = __shfl_sync(0xffffffffu, c < 32 ? b0[q] : b1[q], src) * rc;
@@ -290,10 +302,10 @@ __global__ void __launch_bounds__(256) trsm_sub_kernel(T *B, int64_t ldb, int64_
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
         Bs[lane][warp * RPW + q] = b0[q];
-        Bs[lane + 32][warp * RPW + q] = b1[q];
+        if (!NARROW) Bs[lane + 32 - (NARROW ? 32 : 0)][warp * RPW + q] = b1[q];
     }
     __syncthreads();
-    for (int e = tid; e < LEAF * ROWS; e += blockDim.x) {
+    for (int e = tid; e < KR * ROWS; e += blockDim.x) {
         const int r = e % ROWS, k = e / ROWS;
         if (r0 + r < m && k < nc) B[(r0 + r) + (int64_t)k * ldb] = Bs[k][r];
     }
@@ -481,6 +493,13 @@ inline gpch_status launch_trsm_sub(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, 
 {
     if (m <= 0 || nc <= 0) return GPCH_OK;
     constexpr int RPW = sizeof(T) == 4 ? 4 : 1;
+    if (sizeof(T) == 8 && nc <= 32) {
+        // narrow FP64 blocks: one warp per SM sub-partition, so each row's
+        // chain of FP64 instructions is not interleaved with another warp's
+        trsm_sub_kernel<T, 1, 4, true><<<(unsigned)((m + 3) / 4), 128, 0, st>>>(B, ldb, m, nc, L, ldl, rinv, info);
+        GPCH_LAUNCH_CHECK(ctx);
+        return GPCH_OK;
+    }
     trsm_sub_kernel<T, RPW><<<(unsigned)((m + 8 * RPW - 1) / (8 * RPW)), 256, 0, st>>>(B, ldb, m, nc, L, ldl, rinv,
                                                                                      info);
     GPCH_LAUNCH_CHECK(ctx);
