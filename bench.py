@@ -42,6 +42,10 @@ METRIC = "Cholesky GFLOP/s & CG GB/s, mixed vs FP64 at ≤1e-12 bwd err; served 
 FP64_PEAK_GFLOPS = 1250.0   # nominal B300 FP64 (DFMA): 148 SMs x 2 FMA/clk x 2 flop x clock
 FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032    # FFMA: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 CPU_SAMPLE_N = 4096
+# DRAM bytes per algorithmic flop of syrk_tc_kernel (split-bf16, K = 512),
+# from one ncu capture (see profiles/syrk_tc_split_bf16_n8192.md); None
+# until a capture of the current kernel exists.
+SYRK_DRAM_BYTES_PER_FLOP = None
 
 
 def peaks():
@@ -286,12 +290,18 @@ def main():
     r = bd[:, 0] - torch.mv(A0, x)
     bwd = float(r.abs().max() / (A0.abs().sum(dim=1).max() * x.abs().max() + bd.abs().max()))
 
-    # dominant kernel of the step and its roofline
-    dom = max(phase, key=lambda k: phase[k][0])
+    # dominant kernel of the step (syrk_tc_kernel: the largest share of the
+    # ncu launch list of this workload) and its roofline
+    dom = "mixed_trailing"
     roof = roofline_of(dom, *phase[dom], n, 1, pk)
     if roof is not None:
-        roof = {"kernel": dom, **roof, "launches": phase[dom][1],
-                "avg_launch_ms": round(phase[dom][0] / max(phase[dom][1], 1), 4), "traffic": None}
+        work_per_launch = phase[dom][2] / max(phase[dom][1], 1)
+        roof = {"kernel": "syrk_tc_kernel", **roof, "launches": phase[dom][1],
+                "avg_launch_ms": round(phase[dom][0] / max(phase[dom][1], 1), 4),
+                "traffic": (round(SYRK_DRAM_BYTES_PER_FLOP * work_per_launch)
+                            if SYRK_DRAM_BYTES_PER_FLOP is not None and args.prec == "split_bf16" else None),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one syrk_tc_kernel launch "
+                                  "at n=8192 (profiles/syrk_tc_split_bf16_n8192.md), scaled by the launch's work"}
     phases = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] / args.steps,
                   "roofline": roofline_of(k, *v, n, 1, pk)} for k, v in phase.items()}
 
