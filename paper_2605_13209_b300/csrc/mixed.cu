@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restr
 // on all columns of the identity (thread (tx, ty) keeps entries (tx + 16i,
 // ty + 16jj)).  Stored widened to FP64 (column-major, ld 64).
 __global__ void __launch_bounds__(256) inv_blocks_f32_kernel(const double *__restrict__ D, int64_t ldd, int64_t nj,
-                                                             double *Linv)
+                                                             double *Linv, float *Linv32)
 {
     __shared__ float S[LEAF][LEAF + 1];
     __shared__ float dinv[LEAF];
@@ -262,7 +262,124 @@ __global__ void __launch_bounds__(256) inv_blocks_f32_kernel(const double *__res
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) dst[(tx + 16 * i) + (ty + 16 * jj) * LEAF] = (double)x[i][jj];
+        for (int jj = 0; jj < 4; ++jj) {
+            dst[(tx + 16 * i) + (ty + 16 * jj) * LEAF] = (double)x[i][jj];
+            Linv32[(int64_t)blockIdx.x * LEAF * LEAF + (tx + 16 * i) + (ty + 16 * jj) * LEAF] = x[i][jj];
+        }
+}
+
+// Step 2 of the mixed factor for a whole block column in one launch:
+// X = P L_jj^-T on the m x nj panel P (nj <= PN_MAXK), FP32.  Each CTA owns
+// PN_ROWS rows of the panel, keeps them in shared memory and runs the
+// blocked substitution over the 64-column chunks of L_jj:
+//   for c: X_c = P_c inv(L_cc)^T;  for d > c: P_d -= X_c L_dc^T
+// (inv(L_cc): the FP32 inverses of the 64 x 64 diagonal blocks, computed
+// from the FP64 factor).  The 64 x 64 blocks of L are read through L2 and
+// double-buffered in shared memory with cp.async; thread (tr, tc) keeps a
+// 4 x 4 register tile (rows 4 tr.., columns 4 tc..) of every block product.
+constexpr int PN_ROWS = 64;
+constexpr int PN_MAXK = 512;
+constexpr size_t PN_SMEM = (size_t)(PN_MAXK * PN_ROWS + 2 * LEAF * LEAF) * sizeof(float);
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_t ldp, int64_t m, int nj,
+                                                                const float *__restrict__ L, int64_t ldl,
+                                                                const float *__restrict__ Linv32,
+                                                                const int64_t *info)
+{
+    extern __shared__ __align__(16) float pn_smem[];
+    float *Xs = pn_smem;                         // Xs[k * PN_ROWS + r]
+    float *Lb = pn_smem + PN_MAXK * PN_ROWS;     // 2 buffers, [k * 64 + j]
+    if (info && *info != 0) return;
+    const int tid = threadIdx.x, tr = tid % 16, tc = tid / 16;
+    const int64_t r0 = (int64_t)blockIdx.x * PN_ROWS;
+    const int nch = (nj + LEAF - 1) / LEAF;
+    const int nops = nch + nch * (nch - 1) / 2;
+
+    // op q -> (c, d): d == c is the inverse product of chunk c, d > c the
+    // update of chunk d by chunk c; ops run c-major.
+    auto op_cd = [&](int q, int &c, int &d) {
+        c = 0;
+        int left = q;
+        while (left >= nch - c) {
+            left -= nch - c;
+            ++c;
+        }
+        d = c + left;
+    };
+    auto stage = [&](int q, int buf) {
+        int c, d;
+        op_cd(q, c, d);
+        float *dst = Lb + buf * LEAF * LEAF;
+        for (int e = tid; e < LEAF * LEAF / 4; e += 256) {
+            const int j4 = (e % 16) * 4, k = e / 16;
+            if (c == d) {
+                cp_async16(dst + k * LEAF + j4, Linv32 + (int64_t)c * LEAF * LEAF + j4 + k * LEAF, 16);
+            } else {
+                const int row = d * LEAF + j4;   // rows of L_dc; columns of chunk c are all inside L_jj
+                const int valid = nj - row;
+                const float *src = L + row + (int64_t)(c * LEAF + k) * ldl;
+                cp_async16(dst + k * LEAF + j4, valid > 0 ? src : L, valid >= 4 ? 16 : (valid > 0 ? valid * 4 : 0));
+            }
+        }
+    };
+
+    stage(0, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int e = tid; e < nch * LEAF * PN_ROWS; e += 256) {
+        const int r = e % PN_ROWS, k = e / PN_ROWS;
+        Xs[e] = (r0 + r < m && k < nj) ? P[(r0 + r) + (int64_t)k * ldp] : 0.0f;
+    }
+    for (int q = 0; q < nops; ++q) {
+        int c, d;
+        op_cd(q, c, d);
+        if (q + 1 < nops) stage(q + 1, (q + 1) & 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        const float *Lq = Lb + (q & 1) * LEAF * LEAF;
+        const float *xc = Xs + (c * LEAF) * PN_ROWS + 4 * tr;
+        float acc[4][4] = {};
+#pragma unroll 8
+        for (int k = 0; k < LEAF; ++k) {
+            const float4 x = *reinterpret_cast<const float4 *>(xc + k * PN_ROWS);
+            const float4 l = *reinterpret_cast<const float4 *>(Lq + k * LEAF + 4 * tc);
+            const float xv[4] = {x.x, x.y, x.z, x.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(xv[i], lv[jj], acc[i][jj]);
+        }
+        float *xd = Xs + (d * LEAF + 4 * tc) * PN_ROWS + 4 * tr;
+        if (c == d) {
+            __syncthreads();   // every thread has read chunk c
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                *reinterpret_cast<float4 *>(xd + jj * PN_ROWS) =
+                    make_float4(acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]);
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                float4 v = *reinterpret_cast<float4 *>(xd + jj * PN_ROWS);
+                v.x -= acc[0][jj];
+                v.y -= acc[1][jj];
+                v.z -= acc[2][jj];
+                v.w -= acc[3][jj];
+                *reinterpret_cast<float4 *>(xd + jj * PN_ROWS) = v;
+            }
+        }
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    for (int e = tid; e < nch * LEAF * PN_ROWS; e += 256) {
+        const int r = e % PN_ROWS, k = e / PN_ROWS;
+        if (r0 + r < m && k < nj) P[(r0 + r) + (int64_t)k * ldp] = Xs[e];
+    }
 }
 
 // W (FP32, lower triangle) = A (FP64) + shift * I.
@@ -387,6 +504,7 @@ namespace gpch {
 // Workspace layout of the mixed factor for n, tile.
 struct MixedWs {
     double *D, *rinv, *Linv;
+    float *Linv32;
     int64_t *info;
     __nv_bfloat16 *hi[2], *lo[2];   // bf16 panel copies, by column parity
     int *err;
@@ -400,6 +518,7 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.D = cv.take<double>((size_t)tile * tile);
     w.rinv = cv.take<double>((size_t)tile);
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
+    w.Linv32 = cv.take<float>((size_t)(tile / LEAF) * LEAF * LEAF);
     for (int q = 0; q < 2; ++q) {
         w.hi[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
         w.lo[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
@@ -439,6 +558,11 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     GPCH_CUDA(ctx, cudaMemsetAsync(w.info, 0, sizeof(int64_t), caller));
     GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), caller));
     const int64_t ncols = (n + tile - 1) / tile;
+    // the fused panel kernel needs 16-byte aligned columns of W
+    const bool panel_fused = ((uintptr_t)W % 16 == 0) && (ldw % 4 == 0);
+    if (panel_fused)
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)PN_SMEM));
     cudaEvent_t ev_panel = ctx->aux_ev[0], ev_rest = ctx->aux_ev[1], ev_start = ctx->aux_ev[2],
                 ev_done = ctx->aux_ev[3];
     bool rest_pending = false;
@@ -463,9 +587,14 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
             // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
             // diagonal blocks (computed from the FP64 factor)
             PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
-            inv_blocks_f32_kernel<<<(unsigned)((nj + LEAF - 1) / LEAF), 256, 0, st>>>(w.D, tile, nj, w.Linv);
+            inv_blocks_f32_kernel<<<(unsigned)((nj + LEAF - 1) / LEAF), 256, 0, st>>>(w.D, tile, nj, w.Linv,
+                                                                                     w.Linv32);
             GPCH_LAUNCH_CHECK(ctx);
-            for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
+            if (panel_fused && nj <= PN_MAXK) {
+                panel_trsm_f32_kernel<<<(unsigned)((m + PN_ROWS - 1) / PN_ROWS), 256, PN_SMEM, st>>>(
+                    Pan, ldw, m, (int)nj, Wjj, ldw, w.Linv32, w.info);
+                GPCH_LAUNCH_CHECK(ctx);
+            } else for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
                 const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
                 float *Xc = Pan + c0 * ldw;
                 GPCH_CHECK(launch_trsm<float>(ctx, Xc, ldw, m, nc, w.Linv + (c0 / LEAF) * LEAF * LEAF, w.info, st));
