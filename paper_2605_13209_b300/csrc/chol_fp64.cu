@@ -23,6 +23,8 @@ __global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda,
                                                          int64_t *info)
 {
     extern __shared__ double leaf_smem[];
+    gpch::pdl_wait();
+    gpch::pdl_trigger();
     if (*info != 0) return;
     potrf_leaf_body<W>(A, lda, nb, rinv, nullptr, col0, info, leaf_smem);
 }
@@ -53,15 +55,18 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
             for (int64_t c0 = 0; c0 < nj; c0 += DIAG_LEAF) {
                 const int nc = (int)((nj - c0 < DIAG_LEAF) ? nj - c0 : DIAG_LEAF);
                 double *Lcc = Ajj + c0 + c0 * lda;
-                potrf_leaf_kernel<DIAG_LEAF><<<1, 256, 0, st>>>(Lcc, lda, nc, rinv + c0,
-                                                                        col_offset + j0 + c0, info);
+                // the leaf, substitution and update kernels of this chain
+                // are launched as programmatic dependents of their
+                // predecessor (each waits for it before reading memory)
+                GPCH_CUDA(ctx, gpch::launch_pdl(potrf_leaf_kernel<DIAG_LEAF>, dim3(1), dim3(256), 0, st, Lcc, lda,
+                                                nc, rinv + c0, col_offset + j0 + c0, info));
                 GPCH_LAUNCH_CHECK(ctx);
                 const int64_t mr = nj - c0 - nc;
                 if (mr > 0) {
                     double *P = Ajj + (c0 + nc) + c0 * lda;
-                    GPCH_CHECK(launch_trsm_sub<double>(ctx, P, lda, mr, nc, Lcc, lda, rinv + c0, info, st));
+                    GPCH_CHECK(launch_trsm_sub<double>(ctx, P, lda, mr, nc, Lcc, lda, rinv + c0, info, st, true));
                     GPCH_CHECK(launch_gemm<double>(ctx, true, mr, mr, nc, P, lda, P, lda,
-                                                   Ajj + (c0 + nc) * (1 + lda), lda, info, st));
+                                                   Ajj + (c0 + nc) * (1 + lda), lda, info, st, true));
                 }
             }
         }

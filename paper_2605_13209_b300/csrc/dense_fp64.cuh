@@ -106,6 +106,34 @@ __device__ inline double pivot_rcp(double d)
     return 1.0 / d;
 }
 
+// Programmatic dependent launch.  A kernel of the step-1 chain calls
+// pdl_wait() before touching memory (it returns once the preceding kernel
+// of the stream has finished and its writes are visible; immediately when
+// the launch was an ordinary one) and pdl_trigger() to let the next kernel
+// be scheduled while this one runs, which hides the launch latency of the
+// chain's many small dependent launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kern` on `st` allowing it to start before the previous kernel of
+// the stream has finished (the kernel must begin with pdl_wait()).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 }  // namespace gpch
 
 // Kernels and their launchers have internal linkage: every translation unit
@@ -255,6 +283,8 @@ __global__ void __launch_bounds__(WARPS * 32) trsm_sub_kernel(T *B, int64_t ldb,
     __shared__ T Ls[KR][KR + 1];   // Ls[k][c] = L[k][c]
     __shared__ T rs[KR];
     __shared__ T Bs[KR][ROWS + 1];
+    gpch::pdl_wait();
+    gpch::pdl_trigger();
     if (info && *info != 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * ROWS;
@@ -414,6 +444,8 @@ __global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_
                                                                const T *__restrict__ B, int64_t ldb, T *C,
                                                                int64_t ldc, const int64_t *info)
 {
+    gpch::pdl_wait();
+    gpch::pdl_trigger();
     if (info && *info != 0) return;
     int64_t ti, tj;
     if (LOWER) {
@@ -437,7 +469,8 @@ constexpr int64_t SMALL_GRID = 296;
 
 template <typename T>
 inline gpch_status launch_gemm(gpch_ctx *ctx, bool lower, int64_t m, int64_t nn, int k, const T *A, int64_t lda,
-                               const T *B, int64_t ldb, T *C, int64_t ldc, const int64_t *info, cudaStream_t st)
+                               const T *B, int64_t ldb, T *C, int64_t ldc, const int64_t *info, cudaStream_t st,
+                               bool pdl = false)
 {
     if (m <= 0 || nn <= 0 || k <= 0) return GPCH_OK;
     const int64_t tm = (m + LEAF - 1) / LEAF, tn = (nn + LEAF - 1) / LEAF;
@@ -445,8 +478,12 @@ inline gpch_status launch_gemm(gpch_ctx *ctx, bool lower, int64_t m, int64_t nn,
     const int64_t t32 = (m + 31) / 32;
     if (lower && t32 * (t32 + 1) / 2 < SMALL_GRID / 2) {
         const int64_t Tn = (m + 15) / 16;
-        gemm_nt_minus_kernel<T, true, 16><<<(unsigned)(Tn * (Tn + 1) / 2), 256, 0, st>>>(m, nn, k, A, lda, B, ldb,
-                                                                                       C, ldc, info);
+        const dim3 grid((unsigned)(Tn * (Tn + 1) / 2));
+        if (pdl)
+            GPCH_CUDA(ctx, gpch::launch_pdl(gemm_nt_minus_kernel<T, true, 16>, grid, dim3(256), 0, st, m, nn, k, A,
+                                            lda, B, ldb, C, ldc, info));
+        else
+            gemm_nt_minus_kernel<T, true, 16><<<grid, 256, 0, st>>>(m, nn, k, A, lda, B, ldb, C, ldc, info);
     } else if (lower) {
         if (small) {
             const int64_t Tn = (m + 31) / 32;
@@ -489,14 +526,20 @@ inline gpch_status launch_trsm_rows(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m,
 // per warp (their cost is FP64 issue), FP32 panels four.
 template <typename T>
 inline gpch_status launch_trsm_sub(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int nc, const double *L,
-                                   int64_t ldl, const double *rinv, const int64_t *info, cudaStream_t st)
+                                   int64_t ldl, const double *rinv, const int64_t *info, cudaStream_t st,
+                                   bool pdl = false)
 {
     if (m <= 0 || nc <= 0) return GPCH_OK;
     constexpr int RPW = sizeof(T) == 4 ? 4 : 1;
     if (sizeof(T) == 8 && nc <= 32) {
         // narrow FP64 blocks: one warp per SM sub-partition, so each row's
         // chain of FP64 instructions is not interleaved with another warp's
-        trsm_sub_kernel<T, 1, 4, true><<<(unsigned)((m + 3) / 4), 128, 0, st>>>(B, ldb, m, nc, L, ldl, rinv, info);
+        const dim3 grid((unsigned)((m + 3) / 4));
+        if (pdl)
+            GPCH_CUDA(ctx, gpch::launch_pdl(trsm_sub_kernel<T, 1, 4, true>, grid, dim3(128), 0, st, B, ldb, m, nc, L,
+                                            ldl, rinv, info));
+        else
+            trsm_sub_kernel<T, 1, 4, true><<<grid, 128, 0, st>>>(B, ldb, m, nc, L, ldl, rinv, info);
         GPCH_LAUNCH_CHECK(ctx);
         return GPCH_OK;
     }

@@ -277,6 +277,8 @@ __global__ void __launch_bounds__(256) inv_blocks_f32_kernel(const double *__res
 // from the FP64 factor).  The 64 x 64 blocks of L are read through L2 and
 // double-buffered in shared memory with cp.async; thread (tr, tc) keeps a
 // 4 x 4 register tile (rows 4 tr.., columns 4 tc..) of every block product.
+// A warp covers 8 values of tr and 4 of tc, so per k its two 16-byte
+// shared-memory loads touch 128 B (rows) and 64 B (columns).
 constexpr int PN_ROWS = 64;
 constexpr int PN_MAXK = 512;
 constexpr size_t PN_SMEM = (size_t)(PN_MAXK * PN_ROWS + 2 * LEAF * LEAF) * sizeof(float);
@@ -296,7 +298,8 @@ __global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_
     float *Xs = pn_smem;                         // Xs[k * PN_ROWS + r]
     float *Lb = pn_smem + PN_MAXK * PN_ROWS;     // 2 buffers, [k * 64 + j]
     if (info && *info != 0) return;
-    const int tid = threadIdx.x, tr = tid % 16, tc = tid / 16;
+    const int tid = threadIdx.x, warp = tid / 32;
+    const int tr = (tid % 8) + 8 * (warp % 2), tc = (tid / 8) % 4 + 4 * (warp / 2);
     const int64_t r0 = (int64_t)blockIdx.x * PN_ROWS;
     const int nch = (nj + LEAF - 1) / LEAF;
     const int nops = nch + nch * (nch - 1) / 2;
@@ -329,12 +332,16 @@ __global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_
         }
     };
 
+    // the CTA's rows, 16 bytes at a time (rows past m and columns past nj
+    // are zero-filled)
+    for (int e = tid; e < nch * LEAF * (PN_ROWS / 4); e += 256) {
+        const int r4 = (e % (PN_ROWS / 4)) * 4, k = e / (PN_ROWS / 4);
+        const int64_t rows = m - r0 - r4;
+        const int bytes = (k >= nj || rows <= 0) ? 0 : (rows >= 4 ? 16 : (int)rows * 4);
+        cp_async16(Xs + k * PN_ROWS + r4, bytes ? P + (r0 + r4) + (int64_t)k * ldp : P, bytes);
+    }
     stage(0, 0);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int e = tid; e < nch * LEAF * PN_ROWS; e += 256) {
-        const int r = e % PN_ROWS, k = e / PN_ROWS;
-        Xs[e] = (r0 + r < m && k < nj) ? P[(r0 + r) + (int64_t)k * ldp] : 0.0f;
-    }
     for (int q = 0; q < nops; ++q) {
         int c, d;
         op_cd(q, c, d);
