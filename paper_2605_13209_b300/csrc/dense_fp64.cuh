@@ -579,6 +579,7 @@ struct SolveWs {
     unsigned *flags;                // per-block "solved" flags, FP64 sweeps
     unsigned long long *tagw;       // tagged (value, tag) words, FP32 sweeps
     size_t tagw_words;
+    float *Linv128;                 // 128 x 128 diagonal-block inverses, FP32 factor
     int *err;
     unsigned epoch;
 };

@@ -63,6 +63,68 @@ __global__ void __launch_bounds__(256) inv_diag_blocks_kernel(int64_t n, const T
     }
 }
 
+// 128 x 128 inverses of the diagonal blocks of an FP32 factor, from the
+// 64 x 64 ones: inv([L11 0; L21 L22]) = [inv11 0; -inv22 L21 inv11 inv22],
+// the off-diagonal block in FP32 arithmetic (the sweeps that use these
+// blocks compute in FP32).  One CTA per 128-block; padding past n is the
+// identity.  Out: column-major, ld 128.
+__global__ void __launch_bounds__(256) inv128_kernel(int64_t n, const float *__restrict__ L, int64_t ldl,
+                                                     const float *__restrict__ Linv64, float *Linv128)
+{
+    __shared__ float A[64][65], Bm[64][65];
+    const int tid = threadIdx.x;
+    const int64_t B = blockIdx.x, o = B * 128;
+    const int64_t N64 = (n + LEAF - 1) / LEAF;
+    const bool has2 = 2 * B + 1 < N64;
+    const float *inv11 = Linv64 + (2 * B) * LEAF * LEAF;
+    const float *inv22 = Linv64 + (2 * B + 1) * LEAF * LEAF;
+    float *dst = Linv128 + B * 128 * 128;
+    // T = L21 inv11: A = L21, Bm = inv11
+    for (int e = tid; e < LEAF * LEAF; e += 256) {
+        const int r = e % LEAF, c = e / LEAF;
+        const int64_t row = o + LEAF + r;
+        A[r][c] = (has2 && row < n) ? L[row + (o + c) * ldl] : 0.0f;
+        Bm[r][c] = inv11[e];
+    }
+    __syncthreads();
+    const int tr = tid % 16, tc = tid / 16;   // 4 x 4 outputs: rows tr + 16i, columns tc + 16j
+    float t[4][4] = {};
+    for (int k = 0; k < LEAF; ++k)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[i][j] = fmaf(A[tr + 16 * i][k], Bm[k][tc + 16 * j], t[i][j]);
+    __syncthreads();
+    // X = -inv22 T: A = inv22, Bm = T
+    for (int e = tid; e < LEAF * LEAF; e += 256) {
+        const int r = e % LEAF, c = e / LEAF;
+        A[r][c] = has2 ? inv22[e] : (r == c ? 1.0f : 0.0f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Bm[tr + 16 * i][tc + 16 * j] = t[i][j];
+    __syncthreads();
+    float x[4][4] = {};
+    for (int k = 0; k < LEAF; ++k)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[i][j] = fmaf(A[tr + 16 * i][k], Bm[k][tc + 16 * j], x[i][j]);
+    for (int e = tid; e < 128 * 128; e += 256) {
+        const int r = e % 128, c = e / 128;
+        float v = 0.0f;
+        if (r < LEAF && c < LEAF) v = inv11[r + c * LEAF];
+        else if (r >= LEAF && c >= LEAF) v = has2 ? inv22[(r - LEAF) + (c - LEAF) * LEAF] : (r == c ? 1.0f : 0.0f);
+        dst[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[(LEAF + tr + 16 * i) + (tc + 16 * j) * 128] = -x[i][j];
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
     unsigned v;
@@ -98,38 +160,49 @@ __device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int by
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Blocks of L staged per step (FP32 factor: 4, FP64: 2, so both fit).
-template <typename TL>
+// Sweep block size BS: 64 for every factor; 128 for an FP32 factor with at
+// most two right-hand sides, which halves the serial steps of a sweep.
+// Blocks of L staged per step: BS = 64: 4 (FP32) or 2 (FP64); BS = 128: 2.
+template <typename TL, int BS>
 constexpr int sweep_slots()
 {
-    return sizeof(TL) == 4 ? 4 : 2;
+    return BS == 128 ? 2 : (sizeof(TL) == 4 ? 4 : 2);
 }
-// Staged block of L: entry (t, k) at k * 65 + (k / 16) * PADQ + t.  The
-// four lanes that share an item t read k-ranges 16 apart; the extra PADQ
-// per 16 rows puts them in different banks (FP32: 8 words, FP64: 4 words).
+// Staged block of L: entry (t, k) at k * (BS + 1) + (k / (BS / 4)) * PADQ + t.
+// The four lanes that share an item t read k-ranges BS/4 apart; the extra
+// PADQ per range puts them in different banks (FP32: 8 words, FP64: 4).
 template <typename TL>
 constexpr int padq()
 {
     return sizeof(TL) == 4 ? 8 : 4;
 }
-constexpr int LSTRIDE = LEAF * (LEAF + 1) + 32;
-constexpr int YSTRIDE = 4 * 17;   // solved block: rhs c, row r at c * 68 + (r / 16) * 17 + r % 16
+template <int BS>
+constexpr int lstride()
+{
+    return BS * (BS + 1) + 32;
+}
+// Solved block: rhs c, row r at c * YSTRIDE + (r / (BS/4)) * (BS/4 + 1) + r % (BS/4).
+template <int BS>
+constexpr int ystride()
+{
+    return 4 * (BS / 4 + 1);
+}
 // Inverse block, column stride: r + 4p (FP64, half-warp) or r + 8p (FP32,
 // warp) then fall in distinct banks.
-template <typename TL>
+template <typename TL, int BS>
 constexpr int istride()
 {
-    return sizeof(TL) == 4 ? LEAF + 8 : LEAF + 4;
+    return sizeof(TL) == 4 ? BS + 8 : BS + 4;
 }
 
 // Dynamic shared memory of one sweep CTA owning `nown` blocks.
-template <typename TL>
-size_t sweep_smem_bytes(int nown, int nrhs)
+template <typename TL, int BS>
+size_t sweep_smem_bytes(int nown, int nrhs, int maxrhs)
 {
     using TM = sweep_math_t<TL>;
-    return (size_t)SW_MAXRHS * LEAF * sizeof(double) + (size_t)SW_MAXRHS * (YSTRIDE + LEAF) * sizeof(TM) +
-           (size_t)LEAF * istride<TL>() * sizeof(TM) + (size_t)sweep_slots<TL>() * LSTRIDE * sizeof(TL) +
-           (size_t)nown * LEAF * nrhs * sizeof(double);
+    return (size_t)maxrhs * BS * sizeof(double) + (size_t)maxrhs * (ystride<BS>() + BS) * sizeof(TM) +
+           (size_t)BS * istride<TL, BS>() * sizeof(TM) + (size_t)sweep_slots<TL, BS>() * lstride<BS>() * sizeof(TL) +
+           (size_t)nown * BS * nrhs * sizeof(double);
 }
 
 // One sweep.  FWD: Y = L^-1 B.  BWD: Y = L^-T B.  Y (n x nrhs, ldy) gets
@@ -153,44 +226,47 @@ size_t sweep_smem_bytes(int nown, int nrhs)
 // read (the products use the FP32 value; Y gets the FP64 one).  FP64
 // factor: Y is written, then flags[J] = tag with release semantics; readers
 // acquire the flag and read Y.
-template <typename TL, bool FWD>
+template <typename TL, bool FWD, int BS>
 __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int nrhs, const TL *__restrict__ L,
                                                                 int64_t ldl, const sweep_math_t<TL> *__restrict__ Linv,
                                                                 const double *B, int64_t ldb, double *Y, int64_t ldy,
                                                                 unsigned *flags, unsigned long long *tagw,
-                                                                unsigned tag, int *err)
+                                                                unsigned tag, int *err, int maxrhs)
 {
     using TM = sweep_math_t<TL>;
     constexpr bool TAGGED = sizeof(TL) == 4;
-    constexpr int SLOTS = sweep_slots<TL>();
+    constexpr int SLOTS = sweep_slots<TL, BS>();
     constexpr int PQ = padq<TL>();
-    constexpr int IS = istride<TL>();
+    constexpr int IS = istride<TL, BS>();
+    constexpr int LSTRIDE = lstride<BS>();
+    constexpr int YSTRIDE = ystride<BS>();
+    constexpr int QK = BS / 4;   // k-range of one of the four lanes of an item
     extern __shared__ __align__(16) double sw_smem[];
     double *bst = sw_smem;                                        // staged B rows of the next block
-    TM *yv = reinterpret_cast<TM *>(bst + LEAF * SW_MAXRHS);      // solved block being applied [16 * 68]
-    TM *vv = yv + YSTRIDE * SW_MAXRHS;                            // right-hand side of the block being solved
-    TM *Li = vv + LEAF * SW_MAXRHS;                               // inverse of the next block, (r, k) at r + k * IS
-    TL *Ls = reinterpret_cast<TL *>(Li + LEAF * IS);              // [SLOTS][LSTRIDE]
+    TM *yv = reinterpret_cast<TM *>(bst + BS * maxrhs);           // solved block being applied
+    TM *vv = yv + YSTRIDE * maxrhs;                               // right-hand side of the block being solved
+    TM *Li = vv + BS * maxrhs;                                    // inverse of the next block, (r, k) at r + k * IS
+    TL *Ls = reinterpret_cast<TL *>(Li + BS * IS);                // [SLOTS][LSTRIDE]
     double *acc = reinterpret_cast<double *>(Ls + SLOTS * LSTRIDE);  // [owned][64 * nrhs]
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
-    const int64_t N = (n + LEAF - 1) / LEAF;
+    const int64_t N = (n + BS - 1) / BS;
     const int64_t P = gridDim.x, me = blockIdx.x;
     const int nown = (int)((N - me + P - 1) / P);
     if (tid == 0) abort_flag = 0;
 
-    auto rows_of = [&](int64_t J) { return (int)((n - J * LEAF < LEAF) ? n - J * LEAF : LEAF); };
+    auto rows_of = [&](int64_t J) { return (int)((n - J * BS < BS) ? n - J * BS : BS); };
     auto own_index = [&](int64_t I) { return (int)((I - me) / P); };
 
     auto stage = [&](int slot, int64_t I, int64_t J) {
         const int nI = rows_of(I), nJ = rows_of(J);
         TL *dst = Ls + slot * LSTRIDE;
-        for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) {
+        for (int e = tid; e < BS * BS; e += SW_THREADS) {
             // walk the global block down its columns (coalesced)
-            const int a = e % LEAF, b = e / LEAF;
+            const int a = e % BS, b = e / BS;
             const int t = FWD ? a : b, k = FWD ? b : a;
-            TL *d = dst + k * (LEAF + 1) + (k >> 4) * PQ + t;
-            const TL *src = FWD ? L + (I * LEAF + t) + (J * LEAF + k) * ldl : L + (J * LEAF + k) + (I * LEAF + t) * ldl;
+            TL *d = dst + k * (BS + 1) + (k / QK) * PQ + t;
+            const TL *src = FWD ? L + (I * BS + t) + (J * BS + k) * ldl : L + (J * BS + k) + (I * BS + t) * ldl;
             if (t < nI && k < nJ) cp_async_elem(d, src, (int)sizeof(TL));
             else *d = TL(0);
         }
@@ -198,39 +274,39 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
     // Both sweeps read the inverse block as Li[r + k * IS], the weight of
     // v[k] in item r: forward that is (L_JJ^-1)(r, k), back (L_JJ^-1)(k, r).
     auto stage_solve = [&](int64_t J) {
-        const TM *src = Linv + J * LEAF * LEAF;
-        for (int e = tid; e < LEAF * LEAF; e += SW_THREADS) {
-            const int a = e % LEAF, b = e / LEAF;
+        const TM *src = Linv + J * BS * BS;
+        for (int e = tid; e < BS * BS; e += SW_THREADS) {
+            const int a = e % BS, b = e / BS;
             cp_async_elem(Li + (FWD ? a + b * IS : b + a * IS), src + e, (int)sizeof(TM));
         }
         const int nb = rows_of(J);
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
-            const int r = e % LEAF, c = e / LEAF;
-            if (r < nb) cp_async_elem(bst + e, B + J * LEAF + r + c * ldb, 8);
+        for (int e = tid; e < BS * nrhs; e += SW_THREADS) {
+            const int r = e % BS, c = e / BS;
+            if (r < nb) cp_async_elem(bst + e, B + J * BS + r + c * ldb, 8);
             else bst[e] = 0.0;
         }
     };
 
-    for (int e = tid; e < nown * LEAF * nrhs; e += SW_THREADS) acc[e] = 0.0;
+    for (int e = tid; e < nown * BS * nrhs; e += SW_THREADS) acc[e] = 0.0;
 
     // Solve block J from vv (= B_J - partial sums); write and publish.
     auto finalize = [&](int64_t J) {
         const int nb = rows_of(J);
         const int p = tid & 3;
-        for (int item = tid >> 2; item < LEAF * nrhs; item += SW_THREADS / 4) {
-            const int r = item % LEAF, c = item / LEAF;
+        for (int item = tid >> 2; item < BS * nrhs; item += SW_THREADS / 4) {
+            const int r = item % BS, c = item / BS;
             TM s = 0;
             if (FWD) {
-                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * IS], vv[k + c * LEAF], s);
+                for (int k = p; k <= r; k += 4) s = fma(Li[r + k * IS], vv[k + c * BS], s);
             } else {
-                for (int k = r + ((p - r) & 3); k < LEAF; k += 4) s = fma(Li[r + k * IS], vv[k + c * LEAF], s);
+                for (int k = r + ((p - r) & 3); k < BS; k += 4) s = fma(Li[r + k * IS], vv[k + c * BS], s);
             }
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
             if (p == 0) {
-                if (r < nb) Y[J * LEAF + r + c * ldy] = (double)s;
+                if (r < nb) Y[J * BS + r + c * ldy] = (double)s;
                 if constexpr (TAGGED)
-                    st_relaxed_u64(tagw + J * LEAF * nrhs + item,
+                    st_relaxed_u64(tagw + J * BS * nrhs + item,
                                    ((unsigned long long)tag << 32) | __float_as_uint(r < nb ? (float)s : 0.0f));
             }
         }
@@ -246,18 +322,18 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
     // otherwise it is added to the partial sums.
     auto contribution = [&](int slot, int64_t I, bool critical) {
         const TL *Lb = Ls + slot * LSTRIDE;
-        double *a = acc + (size_t)own_index(I) * LEAF * nrhs;
+        double *a = acc + (size_t)own_index(I) * BS * nrhs;
         const int nI = rows_of(I);
         const int q = tid & 3;
-        for (int item = tid >> 2; item < LEAF * nrhs; item += SW_THREADS / 4) {
-            const int t = item % LEAF, c = item / LEAF;
-            const TM *y = yv + c * YSTRIDE + q * 17;
-            const TL *l = Lb + (q * 16) * (LEAF + 1) + q * PQ + t;
+        for (int item = tid >> 2; item < BS * nrhs; item += SW_THREADS / 4) {
+            const int t = item % BS, c = item / BS;
+            const TM *y = yv + c * YSTRIDE + q * (QK + 1);
+            const TL *l = Lb + (q * QK) * (BS + 1) + q * PQ + t;
             TM s0 = 0, s1 = 0;
 #pragma unroll
-            for (int k = 0; k < 16; k += 2) {
-                s0 = fma((TM)l[k * (LEAF + 1)], y[k], s0);
-                s1 = fma((TM)l[(k + 1) * (LEAF + 1)], y[k + 1], s1);
+            for (int k = 0; k < QK; k += 2) {
+                s0 = fma((TM)l[k * (BS + 1)], y[k], s0);
+                s1 = fma((TM)l[(k + 1) * (BS + 1)], y[k + 1], s1);
             }
             TM s = s0 + s1;
             s += __shfl_xor_sync(0xffffffffu, s, 1);
@@ -273,8 +349,8 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
     auto receive = [&](int64_t J) {
         bool ok = true;
         if constexpr (TAGGED) {
-            for (int e = tid; e < LEAF * nrhs && ok; e += SW_THREADS) {
-                const unsigned long long *w = tagw + J * LEAF * nrhs + e;
+            for (int e = tid; e < BS * nrhs && ok; e += SW_THREADS) {
+                const unsigned long long *w = tagw + J * BS * nrhs + e;
                 unsigned long long v = ld_relaxed_u64(w);
                 for (uint32_t it = 0; (unsigned)(v >> 32) != tag; ++it) {
                     if (it >= FLAG_SPIN_LIMIT) {
@@ -284,8 +360,8 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
                     if (it > 4096) __nanosleep(64);
                     v = ld_relaxed_u64(w);
                 }
-                const int r = e % LEAF, c = e / LEAF;
-                yv[c * YSTRIDE + (r >> 4) * 17 + (r & 15)] = __uint_as_float((unsigned)v);
+                const int r = e % BS, c = e / BS;
+                yv[c * YSTRIDE + (r / QK) * (QK + 1) + r % QK] = __uint_as_float((unsigned)v);
             }
             if (!ok) {
                 abort_flag = 1;
@@ -309,10 +385,10 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
             }
             __syncthreads();
             if (abort_flag) return false;
-            for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) {
-                const int r = e % LEAF, c = e / LEAF;
-                yv[c * YSTRIDE + (r >> 4) * 17 + (r & 15)] =
-                    (r < rows_of(J)) ? __ldcg(&Y[J * LEAF + r + c * ldy]) : 0.0;
+            for (int e = tid; e < BS * nrhs; e += SW_THREADS) {
+                const int r = e % BS, c = e / BS;
+                yv[c * YSTRIDE + (r / QK) * (QK + 1) + r % QK] =
+                    (r < rows_of(J)) ? __ldcg(&Y[J * BS + r + c * ldy]) : 0.0;
             }
             return true;
         }
@@ -325,7 +401,7 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        for (int e = tid; e < LEAF * nrhs; e += SW_THREADS) vv[e] = (TM)bst[e];
+        for (int e = tid; e < BS * nrhs; e += SW_THREADS) vv[e] = (TM)bst[e];
         __syncthreads();
         finalize(first);
         __syncthreads();
@@ -400,16 +476,17 @@ int sm_count(gpch_ctx *ctx)
     return cached;
 }
 
-template <typename TL, bool FWD>
+template <typename TL, bool FWD, int BS>
 gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_t ldl, const double *Linv_ws,
                          const double *B, int64_t ldb, double *Y, int64_t ldy, unsigned *flags,
                          unsigned long long *tagw, unsigned tag, int *err, cudaStream_t st)
 {
     const sweep_math_t<TL> *Linv = reinterpret_cast<const sweep_math_t<TL> *>(Linv_ws);
-    const int64_t N = (n + LEAF - 1) / LEAF;
+    const int64_t N = (n + BS - 1) / BS;
     const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
     const int nown = (int)((N + P - 1) / P);
-    const size_t smem = sweep_smem_bytes<TL>(nown, nrhs);
+    const int maxrhs = BS == 128 ? 2 : SW_MAXRHS;
+    const size_t smem = sweep_smem_bytes<TL, BS>(nown, nrhs, maxrhs);
     int maxsmem = 0;
     GPCH_CUDA(ctx, cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (smem + 1024 > (size_t)maxsmem)
@@ -422,13 +499,14 @@ gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_
         static bool done[64] = {};
         std::lock_guard<std::mutex> lock(mu);
         if (ctx->device >= 64 || !done[ctx->device]) {
-            GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD>,
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(trsv_sweep_kernel<TL, FWD, BS>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem - 1024));
             if (ctx->device < 64) done[ctx->device] = true;
         }
     }
-    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &tagw, &tag, &err};
-    GPCH_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)trsv_sweep_kernel<TL, FWD>, dim3(P), dim3(SW_THREADS),
+    int maxrhs_arg = maxrhs;
+    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &tagw, &tag, &err, &maxrhs_arg};
+    GPCH_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)trsv_sweep_kernel<TL, FWD, BS>, dim3(P), dim3(SW_THREADS),
                                                args, smem, st));
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
@@ -445,7 +523,8 @@ size_t solve_ws_bytes(int64_t n, int nrhs)
     dry.take<double>((size_t)N * LEAF * LEAF);
     dry.take<double>((size_t)n * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
     dry.take<unsigned>((size_t)2 * N);
-    dry.take<unsigned long long>((size_t)N * LEAF * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
+    dry.take<unsigned long long>((size_t)(N + 1) * LEAF * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
+    dry.take<float>((size_t)((n + 127) / 128) * 128 * 128);
     dry.take<int>(4);
     return dry.off;
 }
@@ -458,8 +537,9 @@ SolveWs carve_solve(void *base, int64_t n, int nrhs)
     w.Linv = cv.take<double>((size_t)N * LEAF * LEAF);
     w.Y = cv.take<double>((size_t)n * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS));
     w.flags = cv.take<unsigned>((size_t)2 * N);
-    w.tagw_words = (size_t)N * LEAF * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS);
+    w.tagw_words = (size_t)(N + 1) * LEAF * (nrhs < SW_MAXRHS ? nrhs : SW_MAXRHS);
     w.tagw = cv.take<unsigned long long>(w.tagw_words);
+    w.Linv128 = cv.take<float>((size_t)((n + 127) / 128) * 128 * 128);
     w.err = cv.take<int>(4);
     w.epoch = 0;
     return w;
@@ -480,6 +560,11 @@ gpch_status solve_prepare_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, 
     inv_diag_blocks_kernel<TL>
         <<<(unsigned)N, 256, INV_SMEM, st>>>(n, L, ldl, reinterpret_cast<sweep_math_t<TL> *>(w.Linv));
     GPCH_LAUNCH_CHECK(ctx);
+    if (sizeof(TL) == 4) {
+        inv128_kernel<<<(unsigned)((n + 127) / 128), 256, 0, st>>>(
+            n, reinterpret_cast<const float *>(L), ldl, reinterpret_cast<const float *>(w.Linv), w.Linv128);
+        GPCH_LAUNCH_CHECK(ctx);
+    }
     GPCH_CUDA(ctx, cudaMemsetAsync(w.flags, 0, 2 * N * sizeof(unsigned), st));
     GPCH_CUDA(ctx, cudaMemsetAsync(w.tagw, 0, w.tagw_words * sizeof(unsigned long long), st));
     GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), st));
@@ -494,22 +579,40 @@ gpch_status solve_apply_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, do
 {
     const int64_t N = (n + LEAF - 1) / LEAF;
     PhaseScope ph(ctx, GPCH_PHASE_SOLVE, st, 2.0 * (double)n * n * nrhs);
+    // FP32 factor, one or two right-hand sides: 128-row blocks when their
+    // shared memory fits
+    if (sizeof(TL) == 4 && nrhs <= 2) {
+        const int64_t N2 = (n + 127) / 128;
+        const int P2 = (int)(N2 < sm_count(ctx) ? N2 : sm_count(ctx));
+        const int nown2 = (int)((N2 + P2 - 1) / P2);
+        int maxsmem = 0;
+        GPCH_CUDA(ctx, cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        if (sweep_smem_bytes<TL, 128>(nown2, nrhs, 2) + 1024 <= (size_t)maxsmem) {
+            ++w.epoch;
+            const double *Li = reinterpret_cast<const double *>(w.Linv128);
+            GPCH_CHECK((launch_sweep<TL, true, 128>(ctx, n, nrhs, L, ldl, Li, B, ldb, w.Y, n, w.flags, w.tagw,
+                                                    2 * w.epoch, w.err, st)));
+            GPCH_CHECK((launch_sweep<TL, false, 128>(ctx, n, nrhs, L, ldl, Li, w.Y, n, B, ldb, w.flags + N, w.tagw,
+                                                     2 * w.epoch + 1, w.err, st)));
+            return GPCH_OK;
+        }
+    }
     // right-hand sides per sweep: at most 16, fewer if the owned blocks'
     // partial sums would not fit in shared memory
     const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
     const int nown = (int)((N + P - 1) / P);
     int gmax = SW_MAXRHS;
-    while (gmax > 1 && sweep_smem_bytes<TL>(nown, gmax) > 200 * 1024) gmax /= 2;
+    while (gmax > 1 && sweep_smem_bytes<TL, 64>(nown, gmax, SW_MAXRHS) > 200 * 1024) gmax /= 2;
     for (int c0 = 0; c0 < nrhs; c0 += gmax) {
         const int g = (nrhs - c0 < gmax) ? nrhs - c0 : gmax;
         double *Bc = B + (int64_t)c0 * ldb;
         // tags 2e (forward) and 2e + 1 (back) of epoch e >= 1 never match
         // the cleared words or an earlier sweep's
         ++w.epoch;
-        GPCH_CHECK((launch_sweep<TL, true>(ctx, n, g, L, ldl, w.Linv, Bc, ldb, w.Y, n, w.flags, w.tagw, 2 * w.epoch,
-                                           w.err, st)));
-        GPCH_CHECK((launch_sweep<TL, false>(ctx, n, g, L, ldl, w.Linv, w.Y, n, Bc, ldb, w.flags + N, w.tagw,
-                                            2 * w.epoch + 1, w.err, st)));
+        GPCH_CHECK((launch_sweep<TL, true, 64>(ctx, n, g, L, ldl, w.Linv, Bc, ldb, w.Y, n, w.flags, w.tagw,
+                                               2 * w.epoch, w.err, st)));
+        GPCH_CHECK((launch_sweep<TL, false, 64>(ctx, n, g, L, ldl, w.Linv, w.Y, n, Bc, ldb, w.flags + N, w.tagw,
+                                                2 * w.epoch + 1, w.err, st)));
     }
     return GPCH_OK;
 }
