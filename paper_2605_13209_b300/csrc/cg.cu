@@ -32,7 +32,7 @@ struct CGState {
     int *active, *iters;            // [MAXRHS]
     int *done;                      // [1]
     unsigned *counter;              // [2]: matvec, update
-    double *part;                   // [max_ctas * MAXRHS]
+    double *part;                   // per-CTA partials, part_doubles(n, nrhs)
 };
 
 __device__ inline double warp_sum(double v)
@@ -124,13 +124,23 @@ __global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int nrhs,
         double p = 0.0;
         for (int c = 0; c < wcols; ++c)
             if (tid < nrhs) p = fma(S[(j0 + c) + tid * lds], tcol[c * NR + tid], p);
-        st.part[(size_t)blockIdx.x * MAXRHS + tid] = p;
+        st.part[(size_t)blockIdx.x * NR + tid] = p;
     }
     if (last_cta(&st.counter[0])) {
-        if (tid < nrhs) {
+        // every thread sums a fixed strided subset of the CTA partials, then
+        // one block reduction (a fixed order, so the result is reproducible)
+        for (int r = 0; r < nrhs; ++r) {
             double p = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) p += __ldcg(&st.part[(size_t)b * MAXRHS + tid]);
-            st.alpha[tid] = st.active[tid] ? st.u[tid] / p : 0.0;
+            for (unsigned b = tid; b < gridDim.x; b += THREADS) p += __ldcg(&st.part[(size_t)b * NR + r]);
+            p = warp_sum(p);
+            if (lane == 0) red[warp][0] = p;
+            __syncthreads();
+            if (tid == 0) {
+                double q = 0.0;
+                for (int w = 0; w < THREADS / 32; ++w) q += red[w][0];
+                st.alpha[r] = st.active[r] ? st.u[r] / q : 0.0;
+            }
+            __syncthreads();
         }
         if (tid == 0) st.counter[0] = 0;
     }
@@ -276,7 +286,9 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
 #define GPCH_MV(Wc, NRc)                                                                         \
     cg_matvec_kernel<TA, Wc, NRc><<<(unsigned)((n + Wc - 1) / Wc), THREADS, 0, s>>>(n, nrhs, A, lda, S, \
                                                                                     lds, T, ldt, st, mode)
-    if (nrhs <= 1) GPCH_MV(16, 1);
+    // narrow column blocks make many CTAs (n / 4 for one right-hand side), so
+    // the last partial wave of CTAs is a small share of the launch
+    if (nrhs <= 1) GPCH_MV(4, 1);
     else if (nrhs <= 2) GPCH_MV(8, 2);
     else if (nrhs <= 4) GPCH_MV(4, 4);
     else if (nrhs <= 8) GPCH_MV(2, 8);
@@ -286,20 +298,27 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
     return GPCH_OK;
 }
 
-inline int mv_width(int nrhs) { return nrhs <= 1 ? 16 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2; }
+inline int mv_width(int nrhs) { return nrhs <= 1 ? 4 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2; }
+inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
+
+// Doubles of per-CTA partials: the matvec stores mv_nr per CTA, the vector
+// kernels (one CTA per THREADS rows) up to 2 * MAXRHS.
+inline size_t part_doubles(int64_t n, int nrhs)
+{
+    const size_t mv = (size_t)((n + mv_width(nrhs) - 1) / mv_width(nrhs)) * mv_nr(nrhs);
+    const size_t vec = (size_t)((n + THREADS - 1) / THREADS) * 2 * MAXRHS;
+    return mv > vec ? mv : vec;
+}
 
 // Bytes of scratch one CG group of nrhs (<= 16) columns needs.
 size_t cg_scratch_bytes(int64_t n, int nrhs)
 {
-    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
-    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
-    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
     gpch::Carver dry(nullptr);
     dry.take<double>((size_t)3 * n * nrhs);
     dry.take<double>(4 * MAXRHS);
     dry.take<int>(2 * MAXRHS + 1);
     dry.take<unsigned>(2);
-    dry.take<double>(max_ctas * MAXRHS);
+    dry.take<double>(part_doubles(n, nrhs));
     return dry.off;
 }
 
@@ -312,9 +331,7 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
                    int *h_iters, double *h_relres)
 {
     const int64_t ldv = n;
-    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
-    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
     gpch::Carver cv(scratch);
     double *Rv = cv.take<double>((size_t)n * nrhs);
     double *Sv = cv.take<double>((size_t)n * nrhs);
@@ -330,7 +347,7 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
     st.iters = ic + MAXRHS;
     st.done = ic + 2 * MAXRHS;
     st.counter = cv.take<unsigned>(2);
-    st.part = cv.take<double>(max_ctas * MAXRHS);
+    st.part = cv.take<double>(part_doubles(n, nrhs));
     GPCH_CUDA(ctx, cudaMemsetAsync(st.counter, 0, 2 * sizeof(unsigned), s));
     GPCH_CUDA(ctx, cudaMemsetAsync(ic, 0, (2 * MAXRHS + 1) * sizeof(int), s));
 
@@ -611,9 +628,7 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
                       int R, char *wsbase, cudaStream_t s, RefineResult &res)
 {
     const int64_t ldv = n;
-    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
-    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
     gpch::Carver cv(wsbase);
     double *Rv = cv.take<double>((size_t)n * nrhs);
     double *Zv = cv.take<double>((size_t)n * nrhs);
@@ -632,7 +647,7 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     st.iters = ic + MAXRHS;
     st.done = ic + 2 * MAXRHS;
     st.counter = cv.take<unsigned>(2);
-    st.part = cv.take<double>(max_ctas * 2 * MAXRHS);
+    st.part = cv.take<double>(part_doubles(n, nrhs));
     // ex: rr[16] xinf[16] rinf[16] binf[16] bb[16] norms[2] dots[16]
     double *ex = cv.take<double>(6 * MAXRHS + 2);
     double *d_rr = ex, *d_xinf = ex + MAXRHS, *d_rinf = ex + 2 * MAXRHS, *d_binf = ex + 3 * MAXRHS;
@@ -738,16 +753,13 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
 
 size_t pcg_ws_bytes(int64_t n, int nrhs)
 {
-    const unsigned mv_ctas = (unsigned)((n + mv_width(nrhs) - 1) / mv_width(nrhs));
-    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
-    const size_t max_ctas = mv_ctas > vec_ctas ? mv_ctas : vec_ctas;
     gpch::Carver dry(nullptr);
     for (int i = 0; i < 4; ++i) dry.take<double>((size_t)n * nrhs);
     dry.take<char>(gpch::solve_ws_bytes(n, nrhs));
     dry.take<double>(4 * MAXRHS);
     dry.take<int>(2 * MAXRHS + 1);
     dry.take<unsigned>(2);
-    dry.take<double>(max_ctas * 2 * MAXRHS);
+    dry.take<double>(part_doubles(n, nrhs));
     dry.take<double>(6 * MAXRHS + 2);
     return dry.off;
 }

@@ -43,7 +43,8 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 // nonzero code if a bounded wait gives up).
 __global__ void __launch_bounds__(TC_THREADS, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
-                   int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err)
+                   int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
+                   int prefetch_c)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -111,6 +112,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int s = 0; s < STAGES && s < issued; ++s) {
             const int uses = (issued - 1 - s) / STAGES + 1;
             if (!gpch::tc::mbar_wait(&full[s], (uses - 1) & 1, SPIN_LIMIT)) atomicExch(err, 4);
+        }
+    } else if (warp >= 2 && prefetch_c) {
+        // Warps 2 and 3 are idle until the epilogue: pull the C tile's
+        // columns into L2 now, so that the epilogue's read-modify-write hits
+        // L2 instead of waiting on HBM.
+        const int64_t rows = (m - i0 < BM) ? m - i0 : BM;
+        const uint32_t bytes = (uint32_t)(rows & ~int64_t(3)) * 4u;
+        for (int j = (warp - 2) * 32 + lane; j < BN && bytes > 0; j += 64) {
+            const int64_t col = c0 + j;
+            if (col < m)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(C + i0 + col * ldc), "r"(bytes)
+                             : "memory");
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -489,8 +502,10 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ld
     const double cols_entries = (double)(cB - cA) * (double)m - ((double)cB * (cB - 1) - (double)cA * (cA - 1)) / 2.0;
     const double work = 2.0 * (double)k * cols_entries * (split ? 3.0 : 1.0);
     gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
+    // the C-tile prefetch needs 16-byte aligned columns
+    const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
     syrk_tc_kernel<<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
-                                                               buf.err);
+                                                               buf.err, prefetch_c);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
