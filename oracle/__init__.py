@@ -58,6 +58,8 @@ def lib():
         L.or_round_bf16.restype = ctypes.c_double
         L.or_round_f32.argtypes = [ctypes.c_double]
         L.or_round_f32.restype = ctypes.c_double
+        L.or_round_f16.argtypes = [ctypes.c_double]
+        L.or_round_f16.restype = ctypes.c_double
         L.or_mixed_factor.argtypes = [_c_i64, _c_i64, _c_dp, _c_i64, ctypes.c_int, ctypes.c_double,
                                       _c_dp, _c_i64]
         L.or_mixed_factor.restype = _c_i64
@@ -125,7 +127,11 @@ def round_f32(x: float) -> float:
     return lib().or_round_f32(float(x))
 
 
-MIXED_MODES = {"fp32": 0, "bf16": 1, "split_bf16": 2}
+def round_f16(x: float) -> float:
+    return lib().or_round_f16(float(x))
+
+
+MIXED_MODES = {"fp32": 0, "bf16": 1, "split_bf16": 2, "split_f16": 3}
 
 
 def mixed_factor(A, b: int, mode: str = "bf16", shift: float = 0.0):

@@ -182,14 +182,47 @@ static double or_round_bf16_f(float f)
 double or_round_bf16(double x) { return or_round_bf16_f((float)x); }
 double or_round_f32(double x) { return (double)(float)x; }
 
+/* IEEE binary16, round to nearest even, from the definition: the spacing of
+ * binary16 numbers at |x| is 2^(E - 10) for a leading-bit exponent E >= -14
+ * and 2^-24 below (subnormals); |x| >= 65520 overflows to infinity. */
+double or_round_f16(double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    double a = fabs(x);
+    if (a >= 65520.0) return x > 0.0 ? INFINITY : -INFINITY;
+    int ex;
+    frexp(a, &ex);   /* a = m 2^ex, m in [0.5, 1): leading bit 2^(ex - 1) */
+    int E = ex - 1;
+    if (E < -14) E = -14;
+    double q = ldexp(1.0, E - 10);
+    double r = rint(a / q) * q;   /* default rounding mode: ties to even */
+    return x > 0.0 ? r : -r;
+}
+
+/* Power-of-two scale exponent of a panel whose largest |entry| is mx: the
+ * scaled maximum lies in [2^14, 2^15); clamped to [-60, 60]. */
+static int or_f16_scale_exp(double mx)
+{
+    if (!(mx > 0.0)) return 0;
+    int ex;
+    frexp(mx, &ex);
+    int e = 14 - (ex - 1);
+    if (e < -60) e = -60;
+    if (e > 60) e = 60;
+    return e;
+}
+
 /* Emulated mixed-precision factor (the preconditioner of the refined solve):
  * Algorithm 1 (right) on a binary32 copy of A where
  *   step 1 factors the diagonal block in FP64 (from the binary32 values),
  *   step 2 solves in FP64 and stores the panel rounded to binary32,
  *   step 3 multiplies operands rounded to bfloat16 (mode 1) or split into a
  *          bfloat16 head plus a bfloat16 tail, keeping head*head + head*tail +
- *          tail*head (mode 2), sums the products in FP64 and stores the
- *          updated block rounded to binary32.
+ *          tail*head (mode 2), or, mode 3, split into a binary16 head and
+ *          tail after scaling the block column's panel by 2^e (its largest
+ *          |entry| scaled into [2^14, 2^15)), the three products divided by
+ *          2^2e; the products are summed in FP64 and the updated block is
+ *          stored rounded to binary32.
  * mode 0 keeps step 3's operands in binary32.  Lt receives the factor as
  * doubles (lower triangle).  Returns 0 or the 1-based failing column. */
 int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
@@ -217,6 +250,16 @@ int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
                 Lt[IDX(i, j0 + c, ldl)] = or_round_f32(Lt[IDX(i, j0 + c, ldl)]);
         }
         /* step 3 over the whole trailing lower triangle */
+        double sc = 1.0;
+        if (mode == 3) {
+            double mx = 0.0;
+            for (int64_t c = 0; c < nj; ++c)
+                for (int64_t i = j0 + nj; i < n; ++i) {
+                    double v = fabs(Lt[IDX(i, j0 + c, ldl)]);
+                    if (v > mx) mx = v;
+                }
+            sc = ldexp(1.0, or_f16_scale_exp(mx));
+        }
         for (int64_t k = j0 + nj; k < n; ++k) {
             for (int64_t i = k; i < n; ++i) {
                 double s = 0.0;
@@ -228,6 +271,11 @@ int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
                         double ah = or_round_bf16(a), bh = or_round_bf16(bb);
                         double at = or_round_bf16(a - ah), bt = or_round_bf16(bb - bh);
                         s += ah * bh + ah * bt + at * bh;
+                    } else if (mode == 3) {
+                        double as = a * sc, bs = bb * sc;
+                        double ah = or_round_f16(as), bh = or_round_f16(bs);
+                        double at = or_round_f16(as - ah), bt = or_round_f16(bs - bh);
+                        s += (ah * bh + ah * bt + at * bh) / (sc * sc);
                     } else {
                         s += a * bb;
                     }

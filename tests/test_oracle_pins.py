@@ -136,13 +136,30 @@ def test_round_bf16_matches_torch():
     assert oracle.round_bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6   # tie -> even (up)
 
 
+def test_round_f16_matches_numpy():
+    """IEEE binary16 round-to-nearest-even, against numpy's float16
+    conversion (normals, subnormals, ties, overflow)."""
+    rng = np.random.default_rng(6)
+    vals = np.concatenate([rng.standard_normal(3000) * 10.0 ** rng.integers(-9, 5, 3000),
+                           [0.0, -0.0, 1.0, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, 2.0 ** -24, 2.0 ** -25,
+                            3 * 2.0 ** -26, 2.0 ** -14, 2.0 ** -14 - 2.0 ** -25, 65504.0, 65519.99, 65520.0,
+                            -70000.0, 1e-9]])
+    with np.errstate(over="ignore"):
+        ref = vals.astype(np.float16).astype(np.float64)
+    got = np.array([oracle.round_f16(float(v)) for v in vals])
+    np.testing.assert_array_equal(got, ref)
+    assert oracle.round_f16(1.0 + 2 ** -11) == 1.0                  # tie -> even
+    assert oracle.round_f16(1.0 + 3 * 2 ** -11) == 1.0 + 2 ** -9    # tie -> even (up)
+    assert oracle.round_f16(2.0 ** -25) == 0.0                      # half the smallest subnormal -> 0
+
+
 def test_mixed_factor_exact_on_representable_input():
     """Unit-diagonal integer factor: every operand is exact in bfloat16 and
     every product sum is exact, so every mode must return L0 exactly."""
     rng = np.random.default_rng(11)
     L0 = int_lower(24, rng, unit=True, lo=-2, hi=3)
     A = L0 @ L0.T
-    for mode in ("fp32", "bf16", "split_bf16"):
+    for mode in ("fp32", "bf16", "split_bf16", "split_f16"):
         Lt, info = oracle.mixed_factor(A, 8, mode)
         assert info == 0 and np.array_equal(Lt, L0), mode
 
@@ -152,13 +169,15 @@ def test_mixed_factor_error_ordering():
     A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
     L, _ = oracle.cholesky(A)
     errs = {}
-    for mode in ("fp32", "split_bf16", "bf16"):
+    for mode in ("fp32", "split_f16", "split_bf16", "bf16"):
         Lt, info = oracle.mixed_factor(A, 64, mode)
         assert info == 0
         errs[mode] = oracle.factor_error(Lt, L)
     assert errs["fp32"] < 1e-5
     assert errs["fp32"] < errs["split_bf16"] < errs["bf16"] < 0.5
     assert errs["bf16"] > 1e-4   # bfloat16 products really are rounded
+    # a scaled binary16 head + tail carries ~22 bits against ~16 for bfloat16
+    assert errs["split_f16"] < errs["split_bf16"] / 4 and errs["split_f16"] < 1e-5
 
 
 def test_mixed_factor_shift():
