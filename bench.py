@@ -3,8 +3,10 @@
 ell=0.5, sn2=1e-3, one RHS), solved from the device-resident FP64 matrix.
 
 One step = one refined solve to backward error <= 1e-12: low-precision
-Cholesky factor (FP64 diagonal tiles, FP32 panel, split-bf16 tensor-core
-trailing update, tile 512) + FP64 preconditioned CG.  The metric is the
+Cholesky factor (FP64 diagonal tiles, FP32 panel, tensor-core trailing
+update from a scaled binary16 head + tail of the panel (--prec split_f16,
+the default; split_bf16 and bf16 selectable), tile 512) + FP64
+preconditioned CG.  The metric is the
 factorization-equivalent rate n^3/3 / step time (GFLOP/s).  Beside it, in
 the same JSON line:
   fp64     the plain FP64 blocked Cholesky (tile 512) + substitution, timed once
@@ -42,8 +44,8 @@ METRIC = "Cholesky GFLOP/s & CG GB/s, mixed vs FP64 at ≤1e-12 bwd err; served 
 FP64_PEAK_GFLOPS = 1250.0   # nominal B300 FP64 (DFMA): 148 SMs x 2 FMA/clk x 2 flop x clock
 FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032    # FFMA: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 CPU_SAMPLE_N = 4096
-# DRAM bytes per algorithmic flop of syrk_tc_kernel (split-bf16, K = 512),
-# from one ncu capture (see profiles/syrk_tc_split_bf16_n8192.md); None
+# DRAM bytes per algorithmic flop of syrk_tc_kernel (split modes, K = 512),
+# from one ncu capture (see profiles/syrk_tc_split_f16_n16384.md); None
 # until a capture of the current kernel exists.
 SYRK_DRAM_BYTES_PER_FLOP = None
 
@@ -205,7 +207,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--tile", type=int, default=512)
-    ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "bf16"])
+    ap.add_argument("--prec", default="split_f16", choices=["split_f16", "split_bf16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cg-iters", type=int, default=100)
     ap.add_argument("--cpu-sample-n", type=int, default=CPU_SAMPLE_N)
@@ -299,9 +301,9 @@ def main():
         roof = {"kernel": "syrk_tc_kernel", **roof, "launches": phase[dom][1],
                 "avg_launch_ms": round(phase[dom][0] / max(phase[dom][1], 1), 4),
                 "traffic": (round(SYRK_DRAM_BYTES_PER_FLOP * work_per_launch)
-                            if SYRK_DRAM_BYTES_PER_FLOP is not None and args.prec == "split_bf16" else None),
+                            if SYRK_DRAM_BYTES_PER_FLOP is not None and args.prec != "bf16" else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one syrk_tc_kernel launch "
-                                  "at n=8192 (profiles/syrk_tc_split_bf16_n8192.md), scaled by the launch's work"}
+                                  "at n=16384 (profiles/syrk_tc_split_f16_n16384.md), scaled by the launch's work"}
     phases = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] / args.steps,
                   "roofline": roofline_of(k, *v, n, 1, pk)} for k, v in phase.items()}
 
@@ -401,7 +403,7 @@ def main():
     if args.serve_requests > 0 and rank == 0:
         serving = {}
         rates = [float(r) for r in args.serve_rates.split(",") if r]
-        for label, solo in (("mixed", "split_bf16"), ("fp64_only", "fp64")):
+        for label, solo in (("mixed", args.prec), ("fp64_only", "fp64")):
             for rate in rates:
                 rs = inputs.request_stream(count=args.serve_requests, rate_per_s=rate, nmin=512, nmax=args.serve_nmax)
                 reqs = []
@@ -431,7 +433,7 @@ def main():
                     "max_refined_backward_error": worst}
         serving["what"] = (f"{args.serve_requests} Poisson requests per rate, n log-uniform [512, {args.serve_nmax}], "
                            "1-8 RHS, 160 GB budget, 4 lanes, n <= 2048 batched (FP64); larger solo: mixed "
-                           "split-bf16 refined vs FP64-only")
+                           f"{args.prec} refined vs FP64-only")
 
     # ---------------------------------------------------------- e2e
     Xh = torch.from_numpy(sysm.X).pin_memory()

@@ -63,7 +63,10 @@ typedef enum gpch_dtype {
 typedef enum gpch_prec {
     GPCH_PREC_FP64 = 0,        /* everything in FP64                              */
     GPCH_PREC_BF16 = 1,        /* bf16 tensor-core products, FP32 accumulation     */
-    GPCH_PREC_SPLIT_BF16 = 2   /* head+tail bf16 split, three products, FP32 acc.  */
+    GPCH_PREC_SPLIT_BF16 = 2,  /* head+tail bf16 split, three products, FP32 acc.  */
+    GPCH_PREC_SPLIT_F16 = 3    /* head+tail binary16 split of the panel scaled by a
+                                  power of two (largest |entry| into [2^14, 2^15)),
+                                  three products, FP32 acc.                       */
 } gpch_prec;
 
 typedef struct gpch_ctx gpch_ctx;
@@ -98,7 +101,7 @@ typedef enum gpch_phase {
     GPCH_PHASE_SOLVE = 4,       /* forward + back substitution                    */
     GPCH_PHASE_CG_MATVEC = 5,   /* CG matrix-vector product (one pass over A)      */
     GPCH_PHASE_CG_VECTOR = 6,   /* CG dot/axpy/xpay kernels                        */
-    GPCH_PHASE_MIXED_TRAILING = 7, /* step 3 on tensor cores (bf16 / split bf16)  */
+    GPCH_PHASE_MIXED_TRAILING = 7, /* step 3 on tensor cores (bf16 / split)       */
     GPCH_PHASE_BATCHED = 8,     /* a whole batched solve (one graph launch)       */
     GPCH_PHASE_COUNT = 9
 } gpch_phase;
@@ -330,9 +333,12 @@ gpch_status gpch_server_destroy(gpch_server *srv);
 /* C -= P P^T on the lower triangle of the m x m FP32 matrix C (ldc), with
  * P the m x k FP32 panel (ldp): the operation of Algorithm 1 step 3 for a
  * whole trailing matrix, computed on the tensor cores from a bfloat16 copy
- * of P (prec = GPCH_PREC_BF16) or from a bfloat16 head and tail of P with
- * head*head^T + head*tail^T + tail*head^T (GPCH_PREC_SPLIT_BF16), FP32
- * accumulation.  The strict upper triangle of C is not touched.  k <= 4096.
+ * of P (prec = GPCH_PREC_BF16), from a bfloat16 head and tail of P with
+ * head*head^T + head*tail^T + tail*head^T (GPCH_PREC_SPLIT_BF16), or from a
+ * binary16 head and tail of 2^e P, e chosen so that the largest |entry|
+ * lands in [2^14, 2^15), with the three products scaled back by 2^-2e
+ * (GPCH_PREC_SPLIT_F16); FP32 accumulation.  The strict upper triangle of
+ * C is not touched.  k <= 4096.
  * Synchronizes `stream` (returns GPCH_TIMEOUT if a bounded pipeline wait
  * gave up).  Mixed precision is the paper's future work (Sec. 5). */
 gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, const float *P, int64_t ldp, float *C,
@@ -344,7 +350,8 @@ gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, const float *
  * FP32 copy with step 1 in FP64, step 2 in FP32 and step 3 on the tensor
  * cores as in gpch_syrk_lowprec.  A: device FP64 n x n (lower triangle
  * read, not modified).  L: device FP32 n x n (ldl), receives the factor in
- * its lower triangle.  prec: GPCH_PREC_BF16 or GPCH_PREC_SPLIT_BF16.
+ * its lower triangle.  prec: GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 or
+ * GPCH_PREC_SPLIT_F16 (the scale of step 3 is chosen per block column).
  * info (host): 0, or the 1-based column of a non-positive pivot (returns
  * GPCH_NOT_SPD).  Synchronizes `stream`. */
 gpch_status gpch_chol_factor_mixed(gpch_ctx *ctx, int64_t n, int tile, const double *A, int64_t lda,
@@ -363,8 +370,9 @@ typedef struct gpch_refine_stats {
 /* Solve A X = B to a normwise backward error
  *     ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= bwd_tol
  * per column: low-precision factor Lt of A + delta I (gpch_chol_factor_mixed
- * with the shift schedule delta_0 = 0 for SPLIT_BF16 and 2^-7 max_i A_ii for
- * BF16, then delta <- max(4 delta, 2 u max_i A_ii) after each breakdown, at
+ * with the shift schedule delta_0 = 0 for SPLIT_BF16 and SPLIT_F16 and
+ * 2^-7 max_i A_ii for BF16, then delta <- max(4 delta, 2 u max_i A_ii) after
+ * each breakdown, u = 2^-8, 2^-16, 2^-22 for BF16, SPLIT_BF16, SPLIT_F16; at
  * most 9 attempts), then preconditioned CG with M = Lt Lt^T in FP64 (A, x,
  * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
  * from x_0 = 0, replacing the recurrence residual by b - A x every 50

@@ -830,7 +830,8 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     if (stats) *stats = gpch_refine_stats{0, 0, 0.0, 0.0};
     GPCH_ARG(ctx, n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
     GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
-    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16, "prec must be BF16 or SPLIT_BF16");
+    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16 || prec == GPCH_PREC_SPLIT_F16,
+             "prec must be BF16, SPLIT_BF16 or SPLIT_F16");
     GPCH_ARG(ctx, tile >= 64 && tile <= 1024 && tile % 64 == 0, "tile must be a multiple of 64 in [64, 1024]");
     GPCH_ARG(ctx, bwd_tol > 0.0 && maxit > 0, "bad bwd_tol / maxit");
     GPCH_ARG(ctx, n < (int64_t)1 << 31, "n too large");
@@ -853,7 +854,11 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
 
     double dmax = 0.0;
     GPCH_CHECK(diag_max(ctx, n, A, lda, dev2, s, &dmax));
-    const double ulow = (prec == GPCH_PREC_BF16) ? 1.0 / 256.0 : 1.0 / 65536.0;
+    // unit roundoff of the step-3 operands: bf16 8 bits, split bf16 ~16 bits,
+    // scaled split binary16 ~22 bits
+    const double ulow = (prec == GPCH_PREC_BF16) ? 1.0 / 256.0
+                        : (prec == GPCH_PREC_SPLIT_BF16) ? 1.0 / 65536.0
+                                                         : 1.0 / 4194304.0;
     double shift = (prec == GPCH_PREC_BF16) ? 2.0 * ulow * dmax : 0.0;
     int attempts = 0;
     int64_t info = 1;

@@ -16,6 +16,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "dense_fp64.cuh"
 #include "tc_ptx.cuh"
@@ -44,7 +45,7 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 __global__ void __launch_bounds__(TC_THREADS, 1)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
                    int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
-                   int prefetch_c)
+                   int prefetch_c, int f16, const int *scale)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = gpch::tc::idesc_bf16_f32(BM, BN);
+        const uint32_t idesc = f16 ? gpch::tc::idesc_f16_f32(BM, BN) : gpch::tc::idesc_bf16_f32(BM, BN);
         for (int kc = 0; kc < NK; ++kc) {
             const int s = kc % STAGES;
             if (!gpch::tc::mbar_wait(&full[s], (kc / STAGES) & 1, SPIN_LIMIT)) {
@@ -152,6 +153,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // loaded while the MMAs are still running.
     const int64_t row = i0 + warp * 32 + lane;
     const bool row_ok = row < m;
+    // scaled binary16 operands: the products carry 2^(2e); undo it exactly
+    const float unscale = scale ? __int_as_float((127 - 2 * scale[1]) << 23) : 1.0f;
     float cv[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int64_t col = c0 + cc * 32 + j;
-                if (row_ok && col < m && col <= row) C[row + col * ldc] = cv[j] - v[j];
+                if (row_ok && col < m && col <= row) C[row + col * ldc] = cv[j] - v[j] * unscale;
             }
         }
     } else if (lane == 0) {
@@ -212,6 +215,63 @@ __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restr
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
             Hi[(r0 + r) * kp + k0 + c] = h;
             if (Lo) Lo[(r0 + r) * kp + k0 + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// Power-of-two scale exponent e of a panel whose largest |entry| has the
+// FP32 bit pattern `bits`: the scaled maximum lies in [2^14, 2^15) (below
+// binary16's 65504); clamped to [-60, 60].
+__device__ inline int f16_scale_exp(unsigned bits)
+{
+    if (bits == 0) return 0;
+    const int e = 14 - ((int)((bits >> 23) & 0xffu) - 127);
+    return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+
+// Largest |entry| of the m x k FP32 panel, as FP32 bits (non-negative floats
+// order like their bit patterns), into *absmax (zeroed by the caller).
+__global__ void __launch_bounds__(256) panel_absmax_kernel(const float *__restrict__ P, int64_t ldp, int64_t m, int k,
+                                                           unsigned *absmax)
+{
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int k0 = blockIdx.y * 64;
+    float mx = 0.0f;
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int r = e % 64, c = e / 64;
+        if (r0 + r < m && k0 + c < k) mx = fmaxf(mx, fabsf(P[(r0 + r) + (int64_t)(k0 + c) * ldp]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(mx));
+}
+
+// FP32 panel -> binary16 K-major head and tail of the panel scaled by 2^e
+// (scale[0]: the panel's largest |entry| as FP32 bits; block (0, 0) writes e
+// to scale[1] for the update's epilogue).  The scaling is exact, the head is
+// the round-to-nearest binary16 value and the tail that of the (exact)
+// remainder.
+__global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restrict__ P, int64_t ldp, int64_t m, int k,
+                                                           int kp, __half *Hi, __half *Lo, int *scale)
+{
+    __shared__ float tile[64][65];
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int k0 = blockIdx.y * 64;
+    const int e = f16_scale_exp((unsigned)scale[0]);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) scale[1] = e;
+    const float sc = __int_as_float((127 + e) << 23);
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int r = i % 64, c = i / 64;
+        tile[r][c] = (r0 + r < m && k0 + c < k) ? P[(r0 + r) + (int64_t)(k0 + c) * ldp] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int c = i % 64, r = i / 64;
+        if (r0 + r < m && k0 + c < kp) {
+            const float v = tile[r][c] * sc;
+            const __half h = __float2half_rn(v);
+            Hi[(r0 + r) * kp + k0 + c] = h;
+            Lo[(r0 + r) * kp + k0 + c] = __float2half_rn(v - __half2float(h));
         }
     }
 }
@@ -446,7 +506,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 // Tensor map over a K-major bf16 panel of m rows and kp columns (kp a
 // multiple of 64, so every TMA x coordinate is a multiple of 64 elements).
-gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int kp)
+gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int kp, bool f16)
 {
     auto enc = get_encode();
     if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
@@ -454,7 +514,7 @@ gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, in
     cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -462,8 +522,9 @@ gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, in
 }
 
 struct LowprecBuffers {
-    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;   // binary16 data under SPLIT_F16
     int *err = nullptr;
+    int *scale = nullptr;   // SPLIT_F16: [0] largest |entry| (FP32 bits), [1] scale exponent
 };
 
 // Round the FP32 panel P (m x k) to its bf16 K-major head/tail copies.
@@ -472,6 +533,15 @@ gpch_status panel_convert(gpch_ctx *ctx, int64_t m, int k, const float *P, int64
 {
     const int kp = (k + BK - 1) / BK * BK;
     dim3 grid((unsigned)((m + 63) / 64), (unsigned)(kp / 64));
+    if (prec == GPCH_PREC_SPLIT_F16) {
+        GPCH_CUDA(ctx, cudaMemsetAsync(buf.scale, 0, 2 * sizeof(int), st));
+        panel_absmax_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, reinterpret_cast<unsigned *>(buf.scale));
+        GPCH_LAUNCH_CHECK(ctx);
+        panel_to_f16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, reinterpret_cast<__half *>(buf.hi),
+                                                  reinterpret_cast<__half *>(buf.lo), buf.scale);
+        GPCH_LAUNCH_CHECK(ctx);
+        return GPCH_OK;
+    }
     panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi, prec == GPCH_PREC_SPLIT_BF16 ? buf.lo : nullptr);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
@@ -483,13 +553,14 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ld
                            int64_t tk0, int64_t tk1, cudaStream_t st)
 {
     const int kp = (k + BK - 1) / BK * BK;
-    const bool split = prec == GPCH_PREC_SPLIT_BF16;
+    const bool split = prec != GPCH_PREC_BF16;
+    const bool f16 = prec == GPCH_PREC_SPLIT_F16;
     const int64_t T = (m + BM - 1) / BM;
     if (tk1 < 0 || tk1 > T) tk1 = T;
     if (tk0 >= tk1) return GPCH_OK;
     CUtensorMap mhi, mlo;
-    GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, kp));
-    GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, kp));
+    GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, kp, f16));
+    GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, kp, f16));
     static bool attr_done = false;
     if (!attr_done) {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
@@ -505,7 +576,8 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ld
     // the C-tile prefetch needs 16-byte aligned columns
     const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
     syrk_tc_kernel<<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
-                                                               buf.err, prefetch_c);
+                                                               buf.err, prefetch_c, f16 ? 1 : 0,
+                                                               f16 ? buf.scale : nullptr);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -530,6 +602,7 @@ struct MixedWs {
     int64_t *info;
     __nv_bfloat16 *hi[2], *lo[2];   // bf16 panel copies, by column parity
     int *err;
+    int *scale[2];                  // SPLIT_F16 panel scale words, by column parity
 };
 
 static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
@@ -544,6 +617,7 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     for (int q = 0; q < 2; ++q) {
         w.hi[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
         w.lo[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
+        w.scale[q] = cv.take<int>(2);
     }
     return w;
 }
@@ -604,7 +678,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         float *Pan = W + (j0 + nj) + j0 * ldw;
-        LowprecBuffers buf{w.hi[J & 1], w.lo[J & 1], w.err};
+        LowprecBuffers buf{w.hi[J & 1], w.lo[J & 1], w.err, w.scale[J & 1]};
         {
             // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
             // diagonal blocks (computed from the FP64 factor)
@@ -663,7 +737,8 @@ extern "C" gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, co
     GPCH_ARG(ctx, ctx != nullptr, "null context");
     GPCH_ARG(ctx, m >= 0 && k >= 0 && k <= 4096, "need m >= 0 and 0 <= k <= 4096");
     GPCH_ARG(ctx, ldp >= (m > 0 ? m : 1) && ldc >= (m > 0 ? m : 1), "ld < m");
-    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16, "prec must be BF16 or SPLIT_BF16");
+    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16 || prec == GPCH_PREC_SPLIT_F16,
+             "prec must be BF16, SPLIT_BF16 or SPLIT_F16");
     GPCH_ARG(ctx, m < (int64_t)1 << 31, "m too large");
     if (m == 0 || k == 0) return GPCH_OK;
     GPCH_ARG(ctx, P && C, "null pointer");
@@ -673,12 +748,14 @@ extern "C" gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, co
     dry.take<int>(4);
     dry.take<__nv_bfloat16>((size_t)m * kp);
     dry.take<__nv_bfloat16>((size_t)m * kp);
+    dry.take<int>(2);
     GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
     gpch::Carver cv(ctx->ws);
     LowprecBuffers buf;
     buf.err = cv.take<int>(4);
     buf.hi = cv.take<__nv_bfloat16>((size_t)m * kp);
     buf.lo = cv.take<__nv_bfloat16>((size_t)m * kp);
+    buf.scale = cv.take<int>(2);
     cudaStream_t st = (cudaStream_t)stream;
     GPCH_CUDA(ctx, cudaMemsetAsync(buf.err, 0, 4 * sizeof(int), st));
     GPCH_CHECK(syrk_lowprec_enqueue(ctx, m, (int)k, P, ldp, C, ldc, prec, buf, st));
@@ -698,7 +775,8 @@ extern "C" gpch_status gpch_chol_factor_mixed(gpch_ctx *ctx, int64_t n, int tile
     *info = 0;
     GPCH_ARG(ctx, n >= 0 && lda >= (n > 0 ? n : 1) && ldl >= (n > 0 ? n : 1), "bad n / lda / ldl");
     GPCH_ARG(ctx, tile >= LEAF && tile <= 1024 && tile % LEAF == 0, "tile must be a multiple of 64 in [64, 1024]");
-    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16, "prec must be BF16 or SPLIT_BF16");
+    GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16 || prec == GPCH_PREC_SPLIT_F16,
+             "prec must be BF16, SPLIT_BF16 or SPLIT_F16");
     GPCH_ARG(ctx, shift >= 0.0, "shift must be >= 0");
     GPCH_ARG(ctx, n < (int64_t)1 << 31, "n too large");
     if (n == 0) return GPCH_OK;

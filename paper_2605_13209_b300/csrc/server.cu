@@ -297,7 +297,7 @@ gpch_status gpch_server_create(int device, const gpch_server_opts *opts, gpch_se
         opts->bwd_tol <= 0.0)
         return GPCH_INVALID_ARG;
     if (opts->solo_prec != GPCH_PREC_FP64 && opts->solo_prec != GPCH_PREC_BF16 &&
-        opts->solo_prec != GPCH_PREC_SPLIT_BF16)
+        opts->solo_prec != GPCH_PREC_SPLIT_BF16 && opts->solo_prec != GPCH_PREC_SPLIT_F16)
         return GPCH_INVALID_ARG;
     gpch_server *S = new gpch_server();
     S->device = device;

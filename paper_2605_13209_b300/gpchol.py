@@ -21,7 +21,7 @@ GPCH_OK, GPCH_INVALID_ARG, GPCH_NOT_SPD, GPCH_NOT_CONVERGED, GPCH_OOM_BUDGET, GP
 GPCH_F64, GPCH_F32 = 0, 1
 (PHASE_SE, PHASE_DIAG, PHASE_PANEL, PHASE_TRAILING, PHASE_SOLVE, PHASE_CG_MATVEC, PHASE_CG_VECTOR,
  PHASE_MIXED_TRAILING, PHASE_BATCHED) = range(9)
-GPCH_PREC_FP64, GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 = 0, 1, 2
+GPCH_PREC_FP64, GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16, GPCH_PREC_SPLIT_F16 = 0, 1, 2, 3
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -305,8 +305,9 @@ def cg_solve_noalloc(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: fl
     return CGResult(stats.iterations, stats.converged, stats.relres_max, st)
 
 
-_PREC = {"bf16": GPCH_PREC_BF16, "split_bf16": GPCH_PREC_SPLIT_BF16, GPCH_PREC_BF16: GPCH_PREC_BF16,
-         GPCH_PREC_SPLIT_BF16: GPCH_PREC_SPLIT_BF16}
+_PREC = {"bf16": GPCH_PREC_BF16, "split_bf16": GPCH_PREC_SPLIT_BF16, "split_f16": GPCH_PREC_SPLIT_F16,
+         GPCH_PREC_BF16: GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16: GPCH_PREC_SPLIT_BF16,
+         GPCH_PREC_SPLIT_F16: GPCH_PREC_SPLIT_F16}
 
 
 def syrk_lowprec(P: torch.Tensor, C: torch.Tensor, prec="bf16", ctx: Context | None = None,
