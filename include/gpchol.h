@@ -351,7 +351,11 @@ gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, const float *
  * cores as in gpch_syrk_lowprec.  A: device FP64 n x n (lower triangle
  * read, not modified).  L: device FP32 n x n (ldl), receives the factor in
  * its lower triangle.  prec: GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 or
- * GPCH_PREC_SPLIT_F16 (the scale of step 3 is chosen per block column).
+ * GPCH_PREC_SPLIT_F16 (one power-of-two scale for the whole factor, from
+ * |L_ij| <= sqrt(max_i (A_ii + shift))).  Step 3 is applied left-looking:
+ * each block column receives the products of all earlier panels just
+ * before its diagonal tile is factored.  Workspace: about 4 n^2 bytes for
+ * the 16-bit panel copies.
  * info (host): 0, or the 1-based column of a non-positive pivot (returns
  * GPCH_NOT_SPD).  Synchronizes `stream`. */
 gpch_status gpch_chol_factor_mixed(gpch_ctx *ctx, int64_t n, int tile, const double *A, int64_t lda,

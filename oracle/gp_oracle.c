@@ -199,8 +199,8 @@ double or_round_f16(double x)
     return x > 0.0 ? r : -r;
 }
 
-/* Power-of-two scale exponent of a panel whose largest |entry| is mx: the
- * scaled maximum lies in [2^14, 2^15); clamped to [-60, 60]. */
+/* Power-of-two scale exponent for values bounded by mx: the scaled bound
+ * lies in [2^14, 2^15); clamped to [-60, 60]. */
 static int or_f16_scale_exp(double mx)
 {
     if (!(mx > 0.0)) return 0;
@@ -219,10 +219,11 @@ static int or_f16_scale_exp(double mx)
  *   step 3 multiplies operands rounded to bfloat16 (mode 1) or split into a
  *          bfloat16 head plus a bfloat16 tail, keeping head*head + head*tail +
  *          tail*head (mode 2), or, mode 3, split into a binary16 head and
- *          tail after scaling the block column's panel by 2^e (its largest
- *          |entry| scaled into [2^14, 2^15)), the three products divided by
- *          2^2e; the products are summed in FP64 and the updated block is
- *          stored rounded to binary32.
+ *          tail after scaling by 2^e, the three products divided by 2^2e;
+ *          one e for the whole factor, from the bound |L_ij| <= sqrt(W_ii)
+ *          of an SPD W = L L^T: sqrt(max_i W_ii) (rounded to binary32) is
+ *          scaled into [2^14, 2^15); the products are summed in FP64 and the
+ *          updated block is stored rounded to binary32.
  * mode 0 keeps step 3's operands in binary32.  Lt receives the factor as
  * doubles (lower triangle).  Returns 0 or the 1-based failing column. */
 int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
@@ -231,6 +232,13 @@ int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
     for (int64_t j = 0; j < n; ++j)
         for (int64_t i = j; i < n; ++i)
             Lt[IDX(i, j, ldl)] = or_round_f32(A[IDX(i, j, lda)] + (i == j ? shift : 0.0));
+    double sc = 1.0;
+    if (mode == 3) {
+        double dm = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            if (Lt[IDX(i, i, ldl)] > dm) dm = Lt[IDX(i, i, ldl)];
+        sc = ldexp(1.0, or_f16_scale_exp((double)(float)sqrt(dm)));
+    }
     int64_t N = (n + b - 1) / b;
     for (int64_t J = 0; J < N; ++J) {
         int64_t j0 = J * b, nj = (n - j0 < b) ? n - j0 : b;
@@ -250,16 +258,6 @@ int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
                 Lt[IDX(i, j0 + c, ldl)] = or_round_f32(Lt[IDX(i, j0 + c, ldl)]);
         }
         /* step 3 over the whole trailing lower triangle */
-        double sc = 1.0;
-        if (mode == 3) {
-            double mx = 0.0;
-            for (int64_t c = 0; c < nj; ++c)
-                for (int64_t i = j0 + nj; i < n; ++i) {
-                    double v = fabs(Lt[IDX(i, j0 + c, ldl)]);
-                    if (v > mx) mx = v;
-                }
-            sc = ldexp(1.0, or_f16_scale_exp(mx));
-        }
         for (int64_t k = j0 + nj; k < n; ++k) {
             for (int64_t i = k; i < n; ++i) {
                 double s = 0.0;

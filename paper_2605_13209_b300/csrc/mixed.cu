@@ -29,23 +29,34 @@ constexpr int BM = 128;            // rows of an output tile (TMEM lanes)
 constexpr int BN = 128;            // columns of an output tile (TMEM columns)
 constexpr int BK = 64;             // K per stage: one 128-byte swizzle row of bf16
 constexpr int STAGES = 3;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 192;   // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr uint32_t TILE_A_BYTES = BM * BK * 2;
 constexpr uint32_t TILE_B_BYTES = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
 constexpr size_t TC_SMEM = 1024 + STAGES * STAGE_BYTES + 256;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
+constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators (two CTAs fill an SM's TMEM)
 
-// Trailing update C_lower -= P P^T on tensor cores.  P is the m x kp panel in
-// bf16, K-major (row i at P + i * kp), described by tm_hi (and its bf16
-// tail by tm_lo when split).  split = 0: one product head*head^T; split = 1:
-// head*head^T + head*tail^T + tail*head^T, run as one K loop of 3 * kp.
-// One CTA per lower 128 x 128 tile of C.  err: device status word (set to a
-// nonzero code if a bounded wait gives up).
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// Trailing update C_lower -= P P^T on tensor cores.  P is the m x kp panel,
+// 16-bit, K-major, described by tm_hi (and its tail by tm_lo when split);
+// its K columns start at column k_off of the maps (a multiple of 64).
+// split = 0: one product head*head^T; split = 1: head*head^T + head*tail^T
+// + tail*head^T.  Only columns below ncol are written.
+//
+// The K range is a sequence of panels of panel_k columns (panel_k divides
+// kp).  Each panel's product is summed on its own in a TMEM accumulator and
+// subtracted from C before the next panel's, exactly as if the panels were
+// applied by separate updates: the FP32 sums stay one panel long while C is
+// read and written through L2 between panels.  Two accumulators alternate,
+// so the MMAs of one panel overlap the subtraction of the previous one.
+// Roles: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs (warp 1
+// owns the TMEM allocation), warps 2-5 subtract (warp w: tile rows
+// 32 (w % 4) .. +31, its TMEM lanes).  One CTA per lower 128 x 128 tile of
+// C.  err: device status word, nonzero if a bounded wait gave up.
+__global__ void __launch_bounds__(TC_THREADS, 3)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
                    int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
-                   int prefetch_c, int f16, const int *scale)
+                   int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -53,8 +64,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t *sB = smem + STAGES * TILE_A_BYTES;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *accum = empty + STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Tiles of the lower triangle of the T x T tile grid, column by column,
@@ -77,120 +89,147 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             gpch::tc::mbar_init(&full[s], 1);
             gpch::tc::mbar_init(&empty[s], 1);
         }
-        gpch::tc::mbar_init(accum, 1);
+        for (int a = 0; a < 2; ++a) {
+            gpch::tc::mbar_init(&tfull[a], 1);
+            gpch::tc::mbar_init(&tempty[a], 4);
+        }
         gpch::tc::fence_mbar_init();
     }
-    if (warp == 1) gpch::tc::tmem_alloc<BN>(tmem_slot);
+    if (warp == 1) gpch::tc::tmem_alloc<TMEM_COLS>(tmem_slot);
     gpch::tc::tc_fence_before();
     __syncthreads();
     gpch::tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int nk1 = kp / BK;
-    const int NK = nk1 * (split ? 3 : 1);
+    const int nkp = panel_k / BK;                // k-blocks per panel
+    const int np = kp / panel_k;                 // panels
+    const int nprod = split ? 3 : 1;
+    const int NK = np * nprod * nkp;             // k-block steps, panel by panel, product by product
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        gpch::tc::prefetch_tmap(&tm_hi);
-        if (split) gpch::tc::prefetch_tmap(&tm_lo);
-        int issued = 0;
-        for (int kc = 0; kc < NK; ++kc) {
-            const int s = kc % STAGES;
-            if (kc >= STAGES && !gpch::tc::mbar_wait(&empty[s], ((kc / STAGES) - 1) & 1, SPIN_LIMIT)) {
-                atomicExch(err, 1);
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            gpch::tc::prefetch_tmap(&tm_hi);
+            if (split) gpch::tc::prefetch_tmap(&tm_lo);
+            int issued = 0;
+            for (int kc = 0; kc < NK; ++kc) {
+                const int s = kc % STAGES;
+                if (kc >= STAGES && !gpch::tc::mbar_wait(&empty[s], ((kc / STAGES) - 1) & 1, SPIN_LIMIT)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                const int p = kc / (nprod * nkp), prod = (kc / nkp) % nprod;
+                const int kk = p * nkp + kc % nkp;
+                const CUtensorMap *ma = (prod == 2) ? &tm_lo : &tm_hi;
+                const CUtensorMap *mb = (prod == 1) ? &tm_lo : &tm_hi;
+                gpch::tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                gpch::tc::tma_load_2d(sA + s * TILE_A_BYTES, ma, &full[s], k_off + kk * BK, (int32_t)i0);
+                gpch::tc::tma_load_2d(sB + s * TILE_B_BYTES, mb, &full[s], k_off + kk * BK, (int32_t)c0);
+                ++issued;
             }
-            const int prod = kc / nk1, kk = kc % nk1;
-            const CUtensorMap *ma = (prod == 2) ? &tm_lo : &tm_hi;
-            const CUtensorMap *mb = (prod == 1) ? &tm_lo : &tm_hi;
-            gpch::tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-            gpch::tc::tma_load_2d(sA + s * TILE_A_BYTES, ma, &full[s], kk * BK, (int32_t)i0);
-            gpch::tc::tma_load_2d(sB + s * TILE_B_BYTES, mb, &full[s], kk * BK, (int32_t)c0);
-            ++issued;
+            // Every copy this thread started has landed before the CTA may
+            // exit (immediate in normal operation: the MMAs consumed them).
+            for (int s = 0; s < STAGES && s < issued; ++s) {
+                const int uses = (issued - 1 - s) / STAGES + 1;
+                if (!gpch::tc::mbar_wait(&full[s], (uses - 1) & 1, SPIN_LIMIT)) atomicExch(err, 4);
+            }
         }
-        // Every copy this thread started has landed before the CTA may exit
-        // (immediate in normal operation: the MMA warp consumed them all).
-        for (int s = 0; s < STAGES && s < issued; ++s) {
-            const int uses = (issued - 1 - s) / STAGES + 1;
-            if (!gpch::tc::mbar_wait(&full[s], (uses - 1) & 1, SPIN_LIMIT)) atomicExch(err, 4);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: panel p accumulates into accumulator p & 1 once
+            // the epilogue has released it
+            const uint32_t idesc = f16 ? gpch::tc::idesc_f16_f32(BM, BN) : gpch::tc::idesc_bf16_f32(BM, BN);
+            int kc = 0;
+            bool ok = true;
+            for (int p = 0; p < np && ok; ++p) {
+                const int a = p & 1;
+                if (p >= 2 && !gpch::tc::mbar_wait(&tempty[a], ((p >> 1) - 1) & 1, 4 * SPIN_LIMIT)) {
+                    atomicExch(err, 2);
+                    break;
+                }
+                gpch::tc::tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(a * BN);
+                for (int q = 0; q < nprod * nkp; ++q, ++kc) {
+                    const int s = kc % STAGES;
+                    if (!gpch::tc::mbar_wait(&full[s], (kc / STAGES) & 1, SPIN_LIMIT)) {
+                        atomicExch(err, 2);
+                        ok = false;
+                        break;
+                    }
+                    gpch::tc::tc_fence_after();
+                    const uint64_t ad = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sA + s * TILE_A_BYTES));
+                    const uint64_t bd = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sB + s * TILE_B_BYTES));
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        gpch::tc::mma_bf16(acc, ad + 2 * k, bd + 2 * k, idesc, (q | k) != 0 ? 1u : 0u);
+                    gpch::tc::mma_commit(&empty[s]);
+                }
+                if (ok) gpch::tc::mma_commit(&tfull[a]);
+            }
         }
-    } else if (warp >= 2 && prefetch_c) {
-        // Warps 2 and 3 are idle until the epilogue: pull the C tile's
-        // columns into L2 now, so that the epilogue's read-modify-write hits
-        // L2 instead of waiting on HBM.
-        const int64_t rows = (m - i0 < BM) ? m - i0 : BM;
-        const uint32_t bytes = (uint32_t)(rows & ~int64_t(3)) * 4u;
-        for (int j = (warp - 2) * 32 + lane; j < BN && bytes > 0; j += 64) {
-            const int64_t col = c0 + j;
-            if (col < m)
+        __syncwarp();
+    } else {
+        // Epilogue: lane l of warp w holds tile row 32 (w % 4) + l.
+        const int qw = warp & 3;
+        const int64_t row = i0 + qw * 32 + lane;
+        const bool row_ok = row < m;
+        // scaled binary16 operands: the products carry 2^(2e); undo it exactly
+        const float unscale = scale ? __int_as_float((127 - 2 * scale[1]) << 23) : 1.0f;
+        if (prefetch_c) {
+            // pull the C tile's columns into L2 while the first MMAs run
+            const int64_t rows = (m - i0 < BM) ? m - i0 : BM;
+            const uint32_t bytes = (uint32_t)(rows & ~int64_t(3)) * 4u;
+            const int64_t col = c0 + (warp - 2) * 32 + lane;
+            if (col < m && bytes > 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(C + i0 + col * ldc), "r"(bytes)
                              : "memory");
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        const uint32_t idesc = f16 ? gpch::tc::idesc_f16_f32(BM, BN) : gpch::tc::idesc_bf16_f32(BM, BN);
-        for (int kc = 0; kc < NK; ++kc) {
-            const int s = kc % STAGES;
-            if (!gpch::tc::mbar_wait(&full[s], (kc / STAGES) & 1, SPIN_LIMIT)) {
-                atomicExch(err, 2);
+        // columns c0 + j with j < jn are in C's lower triangle (and < ncol)
+        const int64_t lim = (row < ncol - 1 ? row : ncol - 1) - c0 + 1;
+        const int jn = !row_ok ? 0 : (lim > BN ? BN : (lim < 0 ? 0 : (int)lim));
+        for (int p = 0; p < np; ++p) {
+            const int a = p & 1;
+            float *crow = C + row + c0 * ldc;
+            float cv[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cv[j] = (j < jn) ? crow[(int64_t)j * ldc] : 0.0f;
+            bool ok = gpch::tc::mbar_wait(&tfull[a], (p >> 1) & 1, 4 * SPIN_LIMIT);
+            ok = __all_sync(0xffffffffu, ok);
+            gpch::tc::tc_fence_after();
+            if (!ok) {
+                if (lane == 0) atomicExch(err, 3);
                 break;
             }
-            gpch::tc::tc_fence_after();
-            const uint64_t ad = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sA + s * TILE_A_BYTES));
-            const uint64_t bd = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sB + s * TILE_B_BYTES));
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-                gpch::tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kc | k) != 0 ? 1u : 0u);
-            gpch::tc::mma_commit(&empty[s]);
-        }
-        gpch::tc::mma_commit(accum);
-    }
-    __syncwarp();
-
-    // Epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31; lane l
-    // holds row i0 + 32w + l.  Columns go in chunks of 32: all 32 loads of
-    // a chunk are in flight before any store, and the first chunk is
-    // loaded while the MMAs are still running.
-    const int64_t row = i0 + warp * 32 + lane;
-    const bool row_ok = row < m;
-    // scaled binary16 operands: the products carry 2^(2e); undo it exactly
-    const float unscale = scale ? __int_as_float((127 - 2 * scale[1]) << 23) : 1.0f;
-    float cv[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int64_t col = c0 + j;
-        cv[j] = (row_ok && col < m && col <= row) ? C[row + col * ldc] : 0.0f;
-    }
-    bool ok = gpch::tc::mbar_wait(accum, 0, 4 * SPIN_LIMIT);
-    ok = __all_sync(0xffffffffu, ok);
-    gpch::tc::tc_fence_after();
-    if (ok) {
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+            const uint32_t tbase = tmem + (uint32_t)(a * BN) + ((uint32_t)(qw * 32) << 16);
 #pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-            if (cc > 0) {
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                float *cb = C + row + (c0 + cc * 32) * ldc;
+                // keep the column addresses from living across the loops
+                asm volatile("" : "+l"(cb));
+                if (cc > 0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = c0 + cc * 32 + j;
-                    cv[j] = (row_ok && col < m && col <= row) ? C[row + col * ldc] : 0.0f;
+                    for (int j = 0; j < 32; ++j) cv[j] = (cc * 32 + j < jn) ? cb[(int64_t)j * ldc] : 0.0f;
                 }
-            }
-            float v[32];
-            gpch::tc::tmem_ld32(tbase + cc * 32, v);
+                float v[32];
+                gpch::tc::tmem_ld32(tbase + cc * 32, v);
+                if (cc == BN / 32 - 1) {
+                    // the accumulator is read: the next-but-one panel may use it
+                    gpch::tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) gpch::tc::mbar_arrive(&tempty[a]);
+                }
+                asm volatile("" : "+l"(cb));
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int64_t col = c0 + cc * 32 + j;
-                if (row_ok && col < m && col <= row) C[row + col * ldc] = cv[j] - v[j] * unscale;
+                for (int j = 0; j < 32; ++j)
+                    if (cc * 32 + j < jn) cb[(int64_t)j * ldc] = cv[j] - v[j] * unscale;
             }
         }
-    } else if (lane == 0) {
-        atomicExch(err, 3);
     }
     gpch::tc::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         gpch::tc::tc_fence_after();
-        gpch::tc::tmem_dealloc<BN>(tmem);
+        gpch::tc::tmem_dealloc<TMEM_COLS>(tmem);
     }
 }
 
@@ -198,7 +237,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // buffers of width kp (zero-padded beyond k).  64 x 64 tiles through shared
 // memory so that both the read and the write are coalesced.
 __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restrict__ P, int64_t ldp, int64_t m,
-                                                            int k, int kp, __nv_bfloat16 *Hi, __nv_bfloat16 *Lo)
+                                                            int k, int kp, __nv_bfloat16 *Hi, __nv_bfloat16 *Lo,
+                                                            int64_t ldo)
 {
     __shared__ float tile[64][65];
     const int64_t r0 = (int64_t)blockIdx.x * 64;
@@ -213,8 +253,8 @@ __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restr
         if (r0 + r < m && k0 + c < kp) {
             const float v = tile[r][c];
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            Hi[(r0 + r) * kp + k0 + c] = h;
-            if (Lo) Lo[(r0 + r) * kp + k0 + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+            Hi[(r0 + r) * ldo + k0 + c] = h;
+            if (Lo) Lo[(r0 + r) * ldo + k0 + c] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
     }
 }
@@ -252,7 +292,7 @@ __global__ void __launch_bounds__(256) panel_absmax_kernel(const float *__restri
 // the round-to-nearest binary16 value and the tail that of the (exact)
 // remainder.
 __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restrict__ P, int64_t ldp, int64_t m, int k,
-                                                           int kp, __half *Hi, __half *Lo, int *scale)
+                                                           int kp, __half *Hi, __half *Lo, int *scale, int64_t ldo)
 {
     __shared__ float tile[64][65];
     const int64_t r0 = (int64_t)blockIdx.x * 64;
@@ -270,9 +310,31 @@ __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restri
         if (r0 + r < m && k0 + c < kp) {
             const float v = tile[r][c] * sc;
             const __half h = __float2half_rn(v);
-            Hi[(r0 + r) * kp + k0 + c] = h;
-            Lo[(r0 + r) * kp + k0 + c] = __float2half_rn(v - __half2float(h));
+            Hi[(r0 + r) * ldo + k0 + c] = h;
+            Lo[(r0 + r) * ldo + k0 + c] = __float2half_rn(v - __half2float(h));
         }
+    }
+}
+
+// Scale word of a whole split-f16 factor from the a-priori bound
+// |L_ij| <= sqrt(max_i W_ii) (W = A + shift I, SPD): scale[0] = FP32 bits of
+// sqrt(max_i W_ii), from which the conversions derive the exponent.
+__global__ void __launch_bounds__(256) factor_scale_kernel(int64_t n, const float *__restrict__ W, int64_t ldw,
+                                                           int *scale)
+{
+    __shared__ float red[8];
+    float mx = 0.0f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, W[i + i * ldw]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+        mx = fmaxf(mx, red[0]);
+        const float r = sqrtf(mx);
+        scale[0] = (int)__float_as_uint(r);
+        scale[1] = f16_scale_exp(__float_as_uint(r));
     }
 }
 
@@ -504,14 +566,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-// Tensor map over a K-major bf16 panel of m rows and kp columns (kp a
-// multiple of 64, so every TMA x coordinate is a multiple of 64 elements).
-gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int kp, bool f16)
+// Tensor map over a K-major 16-bit panel of m rows and kcols columns with
+// row stride ld elements (kcols and ld multiples of 64, so every TMA x
+// coordinate used is a multiple of 64 elements).
+gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int64_t kcols, int64_t ld,
+                           bool f16)
 {
     auto enc = get_encode();
     if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
-    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)m};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint64_t dims[2] = {(cuuint64_t)kcols, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
@@ -525,33 +589,46 @@ struct LowprecBuffers {
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;   // binary16 data under SPLIT_F16
     int *err = nullptr;
     int *scale = nullptr;   // SPLIT_F16: [0] largest |entry| (FP32 bits), [1] scale exponent
+    int64_t ld = 0;         // row stride (elements) of hi / lo
+    bool fixed_scale = false;   // scale[0] already holds the bound; do not rescan the panel
 };
 
-// Round the FP32 panel P (m x k) to its bf16 K-major head/tail copies.
+// Round the FP32 panel P (m x k) to its 16-bit K-major head/tail copies:
+// row i, column c goes to hi/lo[i * buf.ld + col0 + c] (zero-padded up to a
+// multiple of 64 columns).
 gpch_status panel_convert(gpch_ctx *ctx, int64_t m, int k, const float *P, int64_t ldp, int prec,
-                          const LowprecBuffers &buf, cudaStream_t st)
+                          const LowprecBuffers &buf, int64_t col0, cudaStream_t st)
 {
     const int kp = (k + BK - 1) / BK * BK;
     dim3 grid((unsigned)((m + 63) / 64), (unsigned)(kp / 64));
     if (prec == GPCH_PREC_SPLIT_F16) {
-        GPCH_CUDA(ctx, cudaMemsetAsync(buf.scale, 0, 2 * sizeof(int), st));
-        panel_absmax_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, reinterpret_cast<unsigned *>(buf.scale));
-        GPCH_LAUNCH_CHECK(ctx);
-        panel_to_f16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, reinterpret_cast<__half *>(buf.hi),
-                                                  reinterpret_cast<__half *>(buf.lo), buf.scale);
+        if (!buf.fixed_scale) {
+            GPCH_CUDA(ctx, cudaMemsetAsync(buf.scale, 0, 2 * sizeof(int), st));
+            panel_absmax_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, reinterpret_cast<unsigned *>(buf.scale));
+            GPCH_LAUNCH_CHECK(ctx);
+        }
+        panel_to_f16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, reinterpret_cast<__half *>(buf.hi) + col0,
+                                                  reinterpret_cast<__half *>(buf.lo) + col0, buf.scale, buf.ld);
         GPCH_LAUNCH_CHECK(ctx);
         return GPCH_OK;
     }
-    panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi, prec == GPCH_PREC_SPLIT_BF16 ? buf.lo : nullptr);
+    panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi + col0,
+                                               prec == GPCH_PREC_SPLIT_BF16 ? buf.lo + col0 : nullptr, buf.ld);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
 
 // C_lower (m x m FP32) -= P P^T on the tile columns [tk0, tk1) of the
-// 128 x 128 tile grid (tk1 < 0: to the end), from the bf16 copies in buf.
-gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ldc, int prec, const LowprecBuffers &buf,
-                           int64_t tk0, int64_t tk1, cudaStream_t st)
+// 128 x 128 tile grid (tk1 < 0: to the end), from the 16-bit copies in buf:
+// rows 0 .. m-1 of hi/lo (row stride buf.ld), K columns [k_off, k_off + k);
+// only C columns below ncol (< 0: m) are written.  panel_k > 0: the K range
+// is a sequence of panels of that many columns, subtracted one at a time
+// (panel_k must divide the padded k).
+gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float *C, int64_t ldc, int prec,
+                           const LowprecBuffers &buf, int64_t tk0, int64_t tk1, cudaStream_t st, int64_t ncol = -1,
+                           int panel_k = 0)
 {
+    if (ncol < 0 || ncol > m) ncol = m;
     const int kp = (k + BK - 1) / BK * BK;
     const bool split = prec != GPCH_PREC_BF16;
     const bool f16 = prec == GPCH_PREC_SPLIT_F16;
@@ -559,8 +636,8 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ld
     if (tk1 < 0 || tk1 > T) tk1 = T;
     if (tk0 >= tk1) return GPCH_OK;
     CUtensorMap mhi, mlo;
-    GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, kp, f16));
-    GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, kp, f16));
+    GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, k_off + kp, buf.ld, f16));
+    GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, k_off + kp, buf.ld, f16));
     static bool attr_done = false;
     if (!attr_done) {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
@@ -569,7 +646,7 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ld
     auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
     const int64_t tiles = offset(tk1) - offset(tk0);
     // algorithmic work: the lower-triangle entries of the updated columns
-    const int64_t cA = tk0 * BN, cB = (tk1 * BN < m) ? tk1 * BN : m;
+    const int64_t cA = tk0 * BN, cB = (tk1 * BN < ncol) ? tk1 * BN : ncol;
     const double cols_entries = (double)(cB - cA) * (double)m - ((double)cB * (cB - 1) - (double)cA * (cA - 1)) / 2.0;
     const double work = 2.0 * (double)k * cols_entries * (split ? 3.0 : 1.0);
     gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
@@ -577,7 +654,8 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, float *C, int64_t ld
     const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
     syrk_tc_kernel<<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
                                                                buf.err, prefetch_c, f16 ? 1 : 0,
-                                                               f16 ? buf.scale : nullptr);
+                                                               f16 ? buf.scale : nullptr, (int)k_off, ncol,
+                                                               panel_k > 0 ? panel_k : kp);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -587,8 +665,8 @@ gpch_status syrk_lowprec_enqueue(gpch_ctx *ctx, int64_t m, int k, const float *P
                                  int64_t ldc, int prec, const LowprecBuffers &buf, cudaStream_t st)
 {
     if (m <= 0 || k <= 0) return GPCH_OK;
-    GPCH_CHECK(panel_convert(ctx, m, k, P, ldp, prec, buf, st));
-    return syrk_tc_launch(ctx, m, k, C, ldc, prec, buf, 0, -1, st);
+    GPCH_CHECK(panel_convert(ctx, m, k, P, ldp, prec, buf, 0, st));
+    return syrk_tc_launch(ctx, m, k, 0, C, ldc, prec, buf, 0, -1, st);
 }
 
 }  // namespace
@@ -600,9 +678,9 @@ struct MixedWs {
     double *D, *rinv, *Linv;
     float *Linv32;
     int64_t *info;
-    __nv_bfloat16 *hi[2], *lo[2];   // bf16 panel copies, by column parity
+    __nv_bfloat16 *hi, *lo;   // 16-bit copies of all panels: row i, K column c at i * kpa + c
     int *err;
-    int *scale[2];                  // SPLIT_F16 panel scale words, by column parity
+    int *scale;               // SPLIT_F16 scale word of the whole factor
 };
 
 static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
@@ -614,11 +692,10 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.rinv = cv.take<double>((size_t)tile);
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
     w.Linv32 = cv.take<float>((size_t)(tile / LEAF) * LEAF * LEAF);
-    for (int q = 0; q < 2; ++q) {
-        w.hi[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
-        w.lo[q] = cv.take<__nv_bfloat16>((size_t)n * tile);
-        w.scale[q] = cv.take<int>(2);
-    }
+    const int64_t kpa = (n + BK - 1) / BK * BK;
+    w.hi = cv.take<__nv_bfloat16>((size_t)n * kpa);
+    w.lo = cv.take<__nv_bfloat16>((size_t)n * kpa);
+    w.scale = cv.take<int>(2);
     return w;
 }
 
@@ -633,14 +710,17 @@ size_t mixed_ws_bytes(int64_t n, int tile)
 // which already holds A + shift I.  info/err live in the workspace; the
 // caller reads them after the stream synchronizes.
 //
-// Lookahead: the trailing update of block column j is split into the tile
-// columns that cover block column j+1 (on the critical chain, a
-// highest-priority stream of the context) and the rest (on its lowest-
-// priority stream), so that the FP64 factorization of
-// the next diagonal tile and its panel solve run while the bulk of the
-// tensor-core update is still going.  Events keep every read and write of a
-// block column in order; the bf16 panel copies alternate between two
-// buffers.
+// Step 3 is applied left-looking, one block column at a time, split over two
+// streams.  Block column J+1 receives panel J's product on the critical
+// stream (highest priority) right after that panel is solved and copied, so
+// that its diagonal tile can be factored next.  Block column J+2 receives
+// the products of all panels 0..J in one long-K pass on the second stream
+// (lowest priority), which runs while the critical stream factors and
+// solves block column J+1.  Every panel's 16-bit copy stays in one n x kpa
+// buffer (row i, K column c at i * kpa + c), so a pass reads the panels it
+// needs as one K range.  Each entry of C is read and written twice (once per
+// stream) instead of once per panel, and the critical stream waits only for
+// the block it needs next.
 gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
                                  int64_t **info_out, int **err_out, cudaStream_t st)
 {
@@ -654,17 +734,32 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     GPCH_CUDA(ctx, cudaMemsetAsync(w.info, 0, sizeof(int64_t), caller));
     GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), caller));
     const int64_t ncols = (n + tile - 1) / tile;
+    const int64_t kpa = (n + BK - 1) / BK * BK;
+    LowprecBuffers all;
+    all.hi = w.hi;
+    all.lo = w.lo;
+    all.err = w.err;
+    all.scale = w.scale;
+    all.ld = kpa;
+    if (prec == GPCH_PREC_SPLIT_F16) {
+        // one scale for every panel, from |L_ij| <= sqrt(max_i W_ii)
+        factor_scale_kernel<<<1, 256, 0, caller>>>(n, W, ldw, w.scale);
+        GPCH_LAUNCH_CHECK(ctx);
+        all.fixed_scale = true;
+    }
     // the fused panel kernel needs 16-byte aligned columns of W
     const bool panel_fused = ((uintptr_t)W % 16 == 0) && (ldw % 4 == 0);
     if (panel_fused)
         GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)PN_SMEM));
-    cudaEvent_t ev_panel = ctx->aux_ev[0], ev_rest = ctx->aux_ev[1], ev_start = ctx->aux_ev[2],
+    cudaEvent_t ev_conv = ctx->aux_ev[0], ev_left = ctx->aux_ev[1], ev_start = ctx->aux_ev[2],
                 ev_done = ctx->aux_ev[3];
-    bool rest_pending = false;
+    bool left_pending = false;
     GPCH_CUDA(ctx, cudaEventRecord(ev_start, caller));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
+    const int64_t blk_cols = (tile + BN - 1) / BN;   // tile columns of one block column
+    const int64_t LEFT_K = 4 * (int64_t)tile;         // K columns (whole panels) per launch of the long pass
     for (int64_t J = 0; J < ncols; ++J) {
         const int64_t j0 = J * tile;
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
@@ -678,7 +773,6 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         float *Pan = W + (j0 + nj) + j0 * ldw;
-        LowprecBuffers buf{w.hi[J & 1], w.lo[J & 1], w.err, w.scale[J & 1]};
         {
             // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
             // diagonal blocks (computed from the FP64 factor)
@@ -700,20 +794,34 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                                                   Pan + (c0 + nc) * ldw, ldw, w.info, st));
             }
         }
-        // step 3 on tensor cores: bf16 copies of the panel, then the tile
-        // columns of block column J+1 here and the rest on the second stream
-        GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, buf, st));
-        if (rest_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_rest, 0));
-        float *Ct = W + (j0 + nj) * (1 + ldw);
-        const int64_t next_cols = (tile + BN - 1) / BN;
-        GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, Ct, ldw, prec, buf, 0, next_cols, st));
-        GPCH_CUDA(ctx, cudaEventRecord(ev_panel, st));
-        GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_panel, 0));
-        GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, Ct, ldw, prec, buf, next_cols, -1, sb));
-        GPCH_CUDA(ctx, cudaEventRecord(ev_rest, sb));
-        rest_pending = true;
+        // step 3: the panel's 16-bit copy (rows j0 + nj.., K columns j0..)
+        LowprecBuffers pb = all;
+        pb.hi = all.hi + (j0 + nj) * kpa;
+        pb.lo = all.lo + (j0 + nj) * kpa;
+        GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, pb, j0, st));
+        GPCH_CUDA(ctx, cudaEventRecord(ev_conv, st));
+        // block column J+1 <- panel J, after it received panels 0..J-1
+        if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_left, 0));
+        left_pending = false;
+        GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, j0, W + (j0 + nj) * (1 + ldw), ldw, prec, pb, 0, blk_cols, st,
+                                  tile));
+        // block column J+2 <- panels 0..J on the second stream
+        if (m > tile) {
+            const int64_t r2 = j0 + nj + tile, m2 = n - r2, K = j0 + nj;
+            LowprecBuffers qb = all;
+            qb.hi = all.hi + r2 * kpa;
+            qb.lo = all.lo + r2 * kpa;
+            GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_conv, 0));
+            for (int64_t k0 = 0; k0 < K; k0 += LEFT_K) {
+                const int64_t kk = (K - k0 < LEFT_K) ? K - k0 : LEFT_K;
+                GPCH_CHECK(syrk_tc_launch(ctx, m2, (int)kk, k0, W + r2 * (1 + ldw), ldw, prec, qb, 0, blk_cols, sb,
+                                          tile, tile));
+            }
+            GPCH_CUDA(ctx, cudaEventRecord(ev_left, sb));
+            left_pending = true;
+        }
     }
-    if (rest_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_rest, 0));
+    if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_left, 0));
     GPCH_CUDA(ctx, cudaEventRecord(ev_done, st));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_done, 0));
     return GPCH_OK;
@@ -756,6 +864,7 @@ extern "C" gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, co
     buf.hi = cv.take<__nv_bfloat16>((size_t)m * kp);
     buf.lo = cv.take<__nv_bfloat16>((size_t)m * kp);
     buf.scale = cv.take<int>(2);
+    buf.ld = kp;
     cudaStream_t st = (cudaStream_t)stream;
     GPCH_CUDA(ctx, cudaMemsetAsync(buf.err, 0, 4 * sizeof(int), st));
     GPCH_CHECK(syrk_lowprec_enqueue(ctx, m, (int)k, P, ldp, C, ldc, prec, buf, st));

@@ -87,7 +87,11 @@ size_t request_bytes(const gpch_request &r, bool solo_mixed, int tile)
 {
     const size_t n = (size_t)r.n;
     size_t b = round_up(n * n * 8) + round_up(n * (size_t)r.d * 8) + 2 * round_up(n * (size_t)r.nrhs * 8);
-    if (solo_mixed) b += round_up(((n + 31) / 32 * 32) * n * 4) + 2 * round_up(n * (size_t)tile * 2) + 12 * n * 8 * r.nrhs;
+    // mixed solo path: FP32 factor, 16-bit head and tail copies of every
+    // panel (n x n each), vectors
+    if (solo_mixed)
+        b += round_up(((n + 31) / 32 * 32) * n * 4) + 2 * round_up(n * ((n + 63) / 64 * 64) * 2) +
+             round_up((size_t)tile * tile * 8) + 12 * n * 8 * r.nrhs;
     return b;
 }
 
