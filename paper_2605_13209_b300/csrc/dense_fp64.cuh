@@ -439,7 +439,7 @@ __device__ inline void gemm_nt_minus_body(int64_t m, int64_t nn, int k, const T 
 // C[m x nn] -= A[m x k] B[nn x k]^T.  LOWER: C is square and only its lower
 // triangle is updated; the grid enumerates the lower BT x BT tiles.
 template <typename T, bool LOWER, int BT>
-__global__ void __launch_bounds__(256, 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
+__global__ void __launch_bounds__(256, BT == 16 ? 6 : 3) gemm_nt_minus_kernel(int64_t m, int64_t nn, int k,
                                                                const T *__restrict__ A, int64_t lda,
                                                                const T *__restrict__ B, int64_t ldb, T *C,
                                                                int64_t ldc, const int64_t *info)

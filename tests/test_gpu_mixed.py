@@ -65,9 +65,11 @@ def test_syrk_lowprec_parity(ctx, m, k, prec):
     assert np.array_equal(got[iu], C0.astype(np.float64)[iu])   # upper triangle untouched
 
 
-@pytest.mark.parametrize("n,tile", [(64, 64), (200, 64), (513, 128), (1000, 256)])
+@pytest.mark.parametrize("n,tile", [(64, 64), (200, 64), (513, 128), (1000, 256), (777, 192), (1100, 320)])
 @pytest.mark.parametrize("prec", ["bf16", "split_bf16", "split_f16"])
 def test_mixed_factor_vs_emulation(ctx, n, tile, prec):
+    # tiles that are not multiples of the 128-column tensor-core tile (64,
+    # 192, 320) exercise the column limit of the block-column updates
     s = inputs.gp_system(n, 8, 0.5, 1e-1, seed=n)
     A = oracle.se_matrix(s.X, s.sf2, s.ell, s.sn2)
     Lexact, _ = oracle.cholesky(A)
