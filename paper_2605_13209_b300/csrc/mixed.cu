@@ -413,8 +413,11 @@ __global__ void __launch_bounds__(256) inv_blocks_f32_kernel(const double *__res
 // double-buffered in shared memory with cp.async; thread (tr, tc) keeps a
 // 4 x 4 register tile (rows 4 tr.., columns 4 tc..) of every block product.
 // A warp covers 8 values of tr and 4 of tc, so per k its two 16-byte
-// shared-memory loads touch 128 B (rows) and 64 B (columns).
-constexpr int PN_ROWS = 64;
+// shared-memory loads touch 128 B (rows) and 64 B (columns).  32 rows per
+// CTA keep its shared memory (96 KB) small enough to share an SM with a CTA
+// of the tensor-core update running on the other stream.
+constexpr int PN_ROWS = 32;
+constexpr int PN_THREADS = 128;
 constexpr int PN_MAXK = 512;
 constexpr size_t PN_SMEM = (size_t)(PN_MAXK * PN_ROWS + 2 * LEAF * LEAF) * sizeof(float);
 
@@ -424,7 +427,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_b
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_t ldp, int64_t m, int nj,
+__global__ void __launch_bounds__(PN_THREADS, 2) panel_trsm_f32_kernel(float *P, int64_t ldp, int64_t m, int nj,
                                                                 const float *__restrict__ L, int64_t ldl,
                                                                 const float *__restrict__ Linv32,
                                                                 const int64_t *info)
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_
     float *Lb = pn_smem + PN_MAXK * PN_ROWS;     // 2 buffers, [k * 64 + j]
     if (info && *info != 0) return;
     const int tid = threadIdx.x, warp = tid / 32;
-    const int tr = (tid % 8) + 8 * (warp % 2), tc = (tid / 8) % 4 + 4 * (warp / 2);
+    const int tr = tid % 8, tc = (tid / 8) % 4 + 4 * warp;
     const int64_t r0 = (int64_t)blockIdx.x * PN_ROWS;
     const int nch = (nj + LEAF - 1) / LEAF;
     const int nops = nch + nch * (nch - 1) / 2;
@@ -454,7 +457,7 @@ __global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_
         int c, d;
         op_cd(q, c, d);
         float *dst = Lb + buf * LEAF * LEAF;
-        for (int e = tid; e < LEAF * LEAF / 4; e += 256) {
+        for (int e = tid; e < LEAF * LEAF / 4; e += PN_THREADS) {
             const int j4 = (e % 16) * 4, k = e / 16;
             if (c == d) {
                 cp_async16(dst + k * LEAF + j4, Linv32 + (int64_t)c * LEAF * LEAF + j4 + k * LEAF, 16);
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_
 
     // the CTA's rows, 16 bytes at a time (rows past m and columns past nj
     // are zero-filled)
-    for (int e = tid; e < nch * LEAF * (PN_ROWS / 4); e += 256) {
+    for (int e = tid; e < nch * LEAF * (PN_ROWS / 4); e += PN_THREADS) {
         const int r4 = (e % (PN_ROWS / 4)) * 4, k = e / (PN_ROWS / 4);
         const int64_t rows = m - r0 - r4;
         const int bytes = (k >= nj || rows <= 0) ? 0 : (rows >= 4 ? 16 : (int)rows * 4);
@@ -518,7 +521,7 @@ __global__ void __launch_bounds__(256, 1) panel_trsm_f32_kernel(float *P, int64_
         __syncthreads();
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-    for (int e = tid; e < nch * LEAF * PN_ROWS; e += 256) {
+    for (int e = tid; e < nch * LEAF * PN_ROWS; e += PN_THREADS) {
         const int r = e % PN_ROWS, k = e / PN_ROWS;
         if (r0 + r < m && k < nj) P[(r0 + r) + (int64_t)k * ldp] = Xs[e];
     }
@@ -781,7 +784,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                                                                                      w.Linv32);
             GPCH_LAUNCH_CHECK(ctx);
             if (panel_fused && nj <= PN_MAXK) {
-                panel_trsm_f32_kernel<<<(unsigned)((m + PN_ROWS - 1) / PN_ROWS), 256, PN_SMEM, st>>>(
+                panel_trsm_f32_kernel<<<(unsigned)((m + PN_ROWS - 1) / PN_ROWS), PN_THREADS, PN_SMEM, st>>>(
                     Pan, ldw, m, (int)nj, Wjj, ldw, w.Linv32, w.info);
                 GPCH_LAUNCH_CHECK(ctx);
             } else for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
