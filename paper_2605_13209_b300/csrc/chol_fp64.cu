@@ -3,7 +3,7 @@
 // matrix.
 //
 // Per block column j of width `tile`:
-//   step 1  the diagonal tile is factored as a nest of 64-wide leaf steps
+//   step 1  the diagonal tile is factored as a nest of 32-wide leaf steps
 //           (potrf_leaf -> inverse-apply TRSM below it -> SYRK inside it);
 //   step 2  the panel below is solved against L_jj^T one 64-column chunk at
 //           a time: X_c = B_c inv(L_cc)^T, then B_{>c} -= X_c L_{>c,c}^T;
@@ -17,22 +17,23 @@ namespace {
 
 using gpch::LEAF;
 
-// Step 1 leaf (see potrf_leaf_body): factor of an nb x nb block, nb <= W.
+// Step 1 leaf (see potrf_leaf_chain): factor of an nb x nb block, nb <= W.
 template <int W>
 __global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *rinv, int64_t col0,
                                                          int64_t *info)
 {
-    extern __shared__ double leaf_smem[];
     gpch::pdl_wait();
     gpch::pdl_trigger();
     if (*info != 0) return;
-    potrf_leaf_body<W>(A, lda, nb, rinv, nullptr, col0, info, leaf_smem);
+    potrf_leaf_chain<W, 256>(A, lda, nb, rinv, col0, info);
 }
 
-// Width of the leaf factorizations inside a diagonal tile.  Each leaf runs
-// on one SM and its FP64 work grows with the cube of its width, so narrow
-// leaves keep the serial chain short; the panel below a tile is still
-// solved in 64-column chunks.
+// Width of the leaf factorizations inside a diagonal tile.  A leaf runs on
+// one SM: its time is its serial chain (one pivot per column) plus the
+// FP64 update of its trailing part, which grows with the cube of the width
+// (a 64-wide leaf takes four times as long as a 32-wide one), so narrow
+// leaves keep the chain short; the panel below a tile is still solved in
+// 64-column chunks.
 constexpr int DIAG_LEAF = 32;
 
 

@@ -106,6 +106,32 @@ __device__ inline double pivot_rcp(double d)
     return 1.0 / d;
 }
 
+// Pivot test and reciprocal for the critical chain of a leaf, with as few
+// FP64-pipe instructions as possible (on this GPU each one occupies the
+// sub-partition's FP64 unit for many cycles, so the chain's length is their
+// count).  The positivity / range test reads the exponent bits with integer
+// instructions.  For 2^-100 <= d <= 2^100 the reciprocal is the hardware
+// approximation (rcp.approx.ftz.f64) refined by the truncated series
+// y0 (1 + e + e^2 + e^3), e = 1 - d y0, whose error is e^4; other positive
+// finite pivots take the division.  Returns false for d <= 0, inf or NaN.
+__device__ inline bool pivot_rcp_chain(double d, double &rd)
+{
+    const long long bits = __double_as_longlong(d);
+    const int ex = (int)(bits >> 52);   // exponent field when the sign bit is clear, < 0 otherwise
+    if (ex >= 1023 - 100 && ex <= 1023 + 100) {
+        double y0;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(d));
+        const double e = fma(-d, y0, 1.0);
+        rd = fma(y0, fma(e, fma(e, e, e), e), y0);
+        return true;
+    }
+    if (bits > 0 && ex < 2047) {
+        rd = 1.0 / d;
+        return true;
+    }
+    return false;
+}
+
 // Programmatic dependent launch.  A kernel of the step-1 chain calls
 // pdl_wait() before touching memory (it returns once the preceding kernel
 // of the stream has finished and its writes are visible; immediately when
@@ -262,6 +288,117 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
         const int r = e % LEAF, c = e / LEAF;
         Linv[r + c * LEAF] = Vi[r][c];
     }
+}
+
+// Step 1 leaf of width W (32 or 64), one CTA of THREADS threads: the same
+// square-root-free sweep as potrf_leaf_body, laid out for the FP64 units.
+// The W x W block lives in shared memory.  Warp 0 (alone on SM
+// sub-partition 0; the other warps there only take part in the barriers)
+// owns the serial chain: at step j it applies column j to column j+1 (lane
+// l holds rows l, l + 32, ...), takes the reciprocal of the new pivot and
+// publishes l_c = a_c,j+1 / d_j+1 for the next step.  The warps on
+// sub-partitions 1-3 update every column beyond j+1, PER entries per thread
+// taken in column-major order of the lower triangle, so whole warps fall
+// idle as the sweep moves right.  One barrier per column.  Outputs as
+// potrf_leaf_body: A (lower nb x nb, nb <= W) overwritten by L, rinv[c] =
+// 1 / L_cc (1 in the padding), *info = col0 + c + 1 on a failed pivot.
+template <int W, int THREADS>
+__device__ inline void potrf_leaf_chain(double *A, int64_t lda, int nb, double *rinv, int64_t col0, int64_t *info)
+{
+    constexpr int RH = W / 32;                                  // rows per lane of warp 0
+    constexpr int BULK = THREADS / 4 * 3;                       // threads on sub-partitions 1-3
+    constexpr int PER = (W * (W + 1) / 2 + BULK - 1) / BULK;    // lower-triangle entries per bulk thread
+    __shared__ double S[W][W + 1];   // S[r][c]
+    __shared__ double lcb[2][W];     // l_c of the current step, by parity
+    __shared__ double dpiv[W], sqv[W], rsv[W];
+    __shared__ int bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < W * W; e += THREADS) {
+        const int r = e % W, c = e / W;
+        double v;
+        if (r < nb && c < nb) v = (r >= c) ? A[r + c * lda] : 0.0;
+        else v = (r == c) ? 1.0 : 0.0;
+        S[r][c] = v;
+    }
+    if (tid == 0) bad = 0;
+    const int sp = warp & 3;
+    const int b = (sp != 0) ? ((warp >> 2) * 3 + (sp - 1)) * 32 + lane : -1;
+    int er[PER], ec[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        er[q] = -1;
+        ec[q] = W;   // never active
+        const int e = PER * b + q;
+        if (b >= 0 && e < W * (W + 1) / 2) {
+            int c = 0, off = 0;
+            while (e >= off + (W - c)) {
+                off += W - c;
+                ++c;
+            }
+            er[q] = c + (e - off);
+            ec[q] = c;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double rd = 0.0;
+        if (lane == 0) {
+            dpiv[0] = S[0][0];
+            if (!gpch::pivot_rcp_chain(S[0][0], rd)) bad = 1;
+        }
+        rd = __shfl_sync(0xffffffffu, rd, 0);
+#pragma unroll
+        for (int h = 0; h < RH; ++h) lcb[0][lane + 32 * h] = S[lane + 32 * h][0] * rd;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (bad) break;
+        const double *lc = lcb[j & 1];
+        const int j1 = j + 1;
+        if (warp == 0) {
+            if (j1 < nb) {
+                // column j1 <- column j1 - column j * l_j1 (rows above j1 are zero)
+                const int hp = j1 / 32, lp = j1 % 32;   // holder of the pivot row
+                double a[RH];
+#pragma unroll
+                for (int h = 0; h < RH; ++h) a[h] = fma(-S[lane + 32 * h][j], lc[j1], S[lane + 32 * h][j1]);
+                double rd = 0.0;
+                if (lane == lp) {
+                    const double d = a[hp];
+                    dpiv[j1] = d;
+                    if (!gpch::pivot_rcp_chain(d, rd)) bad = j1 + 1;
+                }
+                rd = __shfl_sync(0xffffffffu, rd, lp);
+#pragma unroll
+                for (int h = 0; h < RH; ++h) {
+                    const int r = lane + 32 * h;
+                    if (r >= j1) S[r][j1] = a[h];
+                    lcb[j1 & 1][r] = a[h] * rd;
+                }
+            }
+        } else if (b >= 0) {
+#pragma unroll
+            for (int q = 0; q < PER; ++q)
+                if (ec[q] > j1) S[er[q]][ec[q]] = fma(-S[er[q]][j], lc[ec[q]], S[er[q]][ec[q]]);
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) *info = col0 + bad;
+        return;
+    }
+    if (tid < W) {
+        double sq = 1.0, rs = 1.0;
+        if (tid < nb) gpch::pivot_sqrt(dpiv[tid], sq, rs);
+        sqv[tid] = sq;
+        rsv[tid] = rs;
+    }
+    __syncthreads();
+    for (int e = tid; e < W * W; e += THREADS) {
+        const int r = e % W, c = e / W;
+        if (r < nb && c < nb && r >= c) A[r + c * lda] = (r == c) ? sqv[c] : S[r][c] * rsv[c];
+    }
+    if (rinv && tid < W) rinv[tid] = rsv[tid];
 }
 
 // Panel solve by substitution: X = B L^-T in place on the m x nc panel B

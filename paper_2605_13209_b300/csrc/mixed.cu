@@ -527,17 +527,24 @@ __global__ void __launch_bounds__(PN_THREADS, 2) panel_trsm_f32_kernel(float *P,
     }
 }
 
-// W (FP32, lower triangle) = A (FP64) + shift * I.
-__global__ void init_w_kernel(int64_t n, const double *__restrict__ A, int64_t lda, float *W, int64_t ldw,
-                              double shift)
+// W (FP32, lower triangle) = A (FP64) + shift * I.  One CTA per column j;
+// the threads walk rows j.. of it, four at a time per thread.
+__global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__restrict__ A, int64_t lda, float *W,
+                                                     int64_t ldw, double shift)
 {
-    for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
-        for (int64_t i = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            double v = A[i + j * lda];
-            if (i == j) v += shift;
-            W[i + j * ldw] = (float)v;
-        }
+    const int64_t j = blockIdx.x;
+    const double *a = A + j * lda;
+    float *w = W + j * ldw;
+    if (threadIdx.x == 0) w[j] = (float)(a[j] + shift);
+    int64_t i = j + 1 + threadIdx.x;
+    for (; i + 3 * 256 < n; i += 4 * 256) {
+        const double v0 = a[i], v1 = a[i + 256], v2 = a[i + 512], v3 = a[i + 768];
+        w[i] = (float)v0;
+        w[i + 256] = (float)v1;
+        w[i + 512] = (float)v2;
+        w[i + 768] = (float)v3;
+    }
+    for (; i < n; i += 256) w[i] = (float)a[i];
 }
 
 // Copy the nb x nb lower block between FP32 W and FP64 D (ld ldd).
@@ -834,8 +841,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
 gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
                                double shift, cudaStream_t st)
 {
-    dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), (unsigned)(n < 65535 ? n : 65535));
-    init_w_kernel<<<grid, 256, 0, st>>>(n, A, lda, W, ldw, shift);
+    init_w_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, W, ldw, shift);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
