@@ -17,23 +17,23 @@ namespace {
 
 using gpch::LEAF;
 
-// Step 1 leaf (see potrf_leaf_chain): factor of an nb x nb block, nb <= W.
+// Step 1 leaf (see potrf_leaf_pipe): factor of an nb x nb block, nb <= W.
 template <int W>
-__global__ void __launch_bounds__(256) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *rinv, int64_t col0,
+__global__ void __launch_bounds__(128) potrf_leaf_kernel(double *A, int64_t lda, int nb, double *rinv, int64_t col0,
                                                          int64_t *info)
 {
     gpch::pdl_wait();
     gpch::pdl_trigger();
     if (*info != 0) return;
-    potrf_leaf_chain<W, 256>(A, lda, nb, rinv, col0, info);
+    potrf_leaf_pipe<W>(A, lda, nb, rinv, col0, info);
 }
 
 // Width of the leaf factorizations inside a diagonal tile.  A leaf runs on
-// one SM: its time is its serial chain (one pivot per column) plus the
-// FP64 update of its trailing part, which grows with the cube of the width
-// (a 64-wide leaf takes four times as long as a 32-wide one), so narrow
-// leaves keep the chain short; the panel below a tile is still solved in
-// 64-column chunks.
+// one SM: its serial pivot chain costs ~5 FP64 instructions per column and
+// its bulk update grows with the cube of the width on that SM's FP64 units
+// (a 64-wide leaf measured 3.2x a 32-wide one), while every leaf step also
+// pays a substitution and an update launch over the rest of the tile.
+// 32-wide leaves are the faster of the two.
 constexpr int DIAG_LEAF = 32;
 
 
@@ -59,13 +59,13 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
                 // the leaf, substitution and update kernels of this chain
                 // are launched as programmatic dependents of their
                 // predecessor (each waits for it before reading memory)
-                GPCH_CUDA(ctx, gpch::launch_pdl(potrf_leaf_kernel<DIAG_LEAF>, dim3(1), dim3(256), 0, st, Lcc, lda,
+                GPCH_CUDA(ctx, gpch::launch_pdl(potrf_leaf_kernel<DIAG_LEAF>, dim3(1), dim3(128), 0, st, Lcc, lda,
                                                 nc, rinv + c0, col_offset + j0 + c0, info));
                 GPCH_LAUNCH_CHECK(ctx);
                 const int64_t mr = nj - c0 - nc;
                 if (mr > 0) {
                     double *P = Ajj + (c0 + nc) + c0 * lda;
-                    GPCH_CHECK(launch_trsm_sub<double>(ctx, P, lda, mr, nc, Lcc, lda, rinv + c0, info, st, true));
+                    GPCH_CHECK(launch_trsm_sub(ctx, P, lda, mr, nc, Lcc, lda, rinv + c0, info, st, true));
                     GPCH_CHECK(launch_gemm<double>(ctx, true, mr, mr, nc, P, lda, P, lda,
                                                    Ajj + (c0 + nc) * (1 + lda), lda, info, st, true));
                 }
@@ -80,7 +80,7 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
             for (int64_t c0 = 0; c0 < nj; c0 += LEAF) {
                 const int nc = (int)((nj - c0 < LEAF) ? nj - c0 : LEAF);
                 double *Xc = Pan + c0 * lda;
-                GPCH_CHECK(launch_trsm_sub<double>(ctx, Xc, lda, m, nc, Ajj + c0 + c0 * lda, lda, rinv + c0, info,
+                GPCH_CHECK(launch_trsm_sub(ctx, Xc, lda, m, nc, Ajj + c0 + c0 * lda, lda, rinv + c0, info,
                                                    st));
                 const int64_t rest = nj - c0 - nc;
                 if (rest > 0)

@@ -68,24 +68,46 @@ __device__ inline void invert_lower_64(const double (*S)[LEAF + 1], double (*Vi)
         for (int jj = 0; jj < 4; ++jj) Vi[tx + 16 * i][ty + 16 * jj] = x[i][jj];
 }
 
+// FP64 code that a branch skips still costs its issue time on this GPU when
+// the compiler predicates it instead of branching around it (an FP64
+// instruction holds its warp for about 64 cycles whether or not any lane
+// executes it).  The rare paths of the pivot helpers below are therefore
+// kept out of line, behind a branch that is almost never taken.
+static __device__ __noinline__ double pivot_div_slow(double d) { return 1.0 / d; }
+
+static __device__ __noinline__ double2 pivot_sqrt_slow(double d)
+{
+    const double s = sqrt(d);
+    return make_double2(s, 1.0 / s);
+}
+
+// True when d is positive, finite and within 2^-100 .. 2^101 (exponent bits
+// read with integer instructions, no FP64 compare).
+__device__ __forceinline__ bool pivot_in_fast_range(double d)
+{
+    const int ex = (int)(__double_as_longlong(d) >> 52);   // < 0 when the sign bit is set
+    return ex >= 1023 - 100 && ex <= 1023 + 100;
+}
+
 // Square root and reciprocal square root of a positive pivot d, by Newton
 // iteration on y = 1/sqrt(d) from an FP32 seed: each step
 // y <- y (3 - d y^2) / 2 doubles the correct bits (24 -> 48 -> full), then
 // s = d y is corrected once by s <- s + y (d - s^2) / 2.  Both results are
 // within a few units in the last place; the exact cases (d = 1, perfect
-// squares of small integers) come out exact.  Outside the FP32 range the
+// squares of small integers) come out exact.  Outside 2^-100 .. 2^101 the
 // division-based form is used.
 __device__ inline void pivot_sqrt(double d, double &s, double &y)
 {
-    if (d > 1e-30 && d < 1e30) {
+    if (pivot_in_fast_range(d)) {
         y = (double)__frsqrt_rn((float)d);
         y = y * fma(-0.5 * d, y * y, 1.5);
         y = y * fma(-0.5 * d, y * y, 1.5);
         s = d * y;
         s = fma(0.5 * y, fma(-s, s, d), s);
     } else {
-        s = sqrt(d);
-        y = 1.0 / s;
+        const double2 r = pivot_sqrt_slow(d);
+        s = r.x;
+        y = r.y;
     }
 }
 
@@ -93,43 +115,17 @@ __device__ inline void pivot_sqrt(double d, double &s, double &y)
 // Newton-Raphson step taken to third order, y = y0 (1 + e + e^2) with
 // e = 1 - d y0 (the truncated series of 1 / (1 - e)); with |e| < 2^-21 the
 // truncation error is below 2^-63, so the result is within about one unit
-// in the last place.  Outside the FP32 range the division is used.
+// in the last place.  Outside 2^-100 .. 2^101 the division is used.
 __device__ inline double pivot_rcp(double d)
 {
-    if (d > 1e-30 && d < 1e30) {
+    if (pivot_in_fast_range(d)) {
         float yf;
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)d));
         const double y0 = (double)yf;
         const double e = fma(-d, y0, 1.0);
         return fma(y0, fma(e, e, e), y0);
     }
-    return 1.0 / d;
-}
-
-// Pivot test and reciprocal for the critical chain of a leaf, with as few
-// FP64-pipe instructions as possible (on this GPU each one occupies the
-// sub-partition's FP64 unit for many cycles, so the chain's length is their
-// count).  The positivity / range test reads the exponent bits with integer
-// instructions.  For 2^-100 <= d <= 2^100 the reciprocal is the hardware
-// approximation (rcp.approx.ftz.f64) refined by the truncated series
-// y0 (1 + e + e^2 + e^3), e = 1 - d y0, whose error is e^4; other positive
-// finite pivots take the division.  Returns false for d <= 0, inf or NaN.
-__device__ inline bool pivot_rcp_chain(double d, double &rd)
-{
-    const long long bits = __double_as_longlong(d);
-    const int ex = (int)(bits >> 52);   // exponent field when the sign bit is clear, < 0 otherwise
-    if (ex >= 1023 - 100 && ex <= 1023 + 100) {
-        double y0;
-        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(d));
-        const double e = fma(-d, y0, 1.0);
-        rd = fma(y0, fma(e, fma(e, e, e), e), y0);
-        return true;
-    }
-    if (bits > 0 && ex < 2047) {
-        rd = 1.0 / d;
-        return true;
-    }
-    return false;
+    return pivot_div_slow(d);
 }
 
 // Programmatic dependent launch.  A kernel of the step-1 chain calls
@@ -158,6 +154,33 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Pivot test and reciprocal for the critical chain of a leaf, with as few
+// FP64 instructions as possible (each one occupies its warp for about 64
+// cycles, so the chain's length is their count).  The positivity / range
+// test reads the exponent bits with integer instructions.  For
+// 2^-100 <= d < 2^101: y0 = rcp.approx.ftz.f64(d), e = 1 - d y0,
+// 1/d ~ y0 (1 + e + e^2).  The seed's relative error measured on this GPU is
+// below 2^-19.9 (4M samples over 2^-100..2^100), so the truncation term e^3
+// is below 2^-59 and the result is within one unit in the last place of the
+// correctly rounded quotient.  Other positive finite pivots take the
+// out-of-line division.  Returns false for d <= 0, inf or NaN.
+__device__ inline bool pivot_rcp_short(double d, double &rd)
+{
+    if (pivot_in_fast_range(d)) {
+        double y0;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(d));
+        const double e = fma(-d, y0, 1.0);
+        rd = fma(y0, fma(e, e, e), y0);
+        return true;
+    }
+    const long long bits = __double_as_longlong(d);
+    if (bits > 0 && (int)(bits >> 52) < 2047) {
+        rd = pivot_div_slow(d);
+        return true;
+    }
+    return false;
 }
 
 }  // namespace gpch
@@ -290,27 +313,99 @@ __device__ inline void potrf_leaf_body(double *A, int64_t lda, int nb, double *r
     }
 }
 
-// Step 1 leaf of width W (32 or 64), one CTA of THREADS threads: the same
-// square-root-free sweep as potrf_leaf_body, laid out for the FP64 units.
-// The W x W block lives in shared memory.  Warp 0 (alone on SM
-// sub-partition 0; the other warps there only take part in the barriers)
-// owns the serial chain: at step j it applies column j to column j+1 (lane
-// l holds rows l, l + 32, ...), takes the reciprocal of the new pivot and
-// publishes l_c = a_c,j+1 / d_j+1 for the next step.  The warps on
-// sub-partitions 1-3 update every column beyond j+1, PER entries per thread
-// taken in column-major order of the lower triangle, so whole warps fall
-// idle as the sweep moves right.  One barrier per column.  Outputs as
-// potrf_leaf_body: A (lower nb x nb, nb <= W) overwritten by L, rinv[c] =
-// 1 / L_cc (1 in the padding), *info = col0 + c + 1 on a failed pivot.
-template <int W, int THREADS>
-__device__ inline void potrf_leaf_chain(double *A, int64_t lda, int nb, double *rinv, int64_t col0, int64_t *info)
+// Position p of the W-wide leaf's entry order -> (row, column).  The order
+// runs over columns W-1, W-2, ..., 0 (column c holds W - c entries) and,
+// inside a column, over rows W-1 down to c, so the diagonal entry closes
+// its column.  Block k = W - c starts at (k - 1) k / 2.
+template <int W>
+__device__ __forceinline__ void leaf_entry(int p, int &r, int &c)
 {
-    constexpr int RH = W / 32;                                  // rows per lane of warp 0
-    constexpr int BULK = THREADS / 4 * 3;                       // threads on sub-partitions 1-3
-    constexpr int PER = (W * (W + 1) / 2 + BULK - 1) / BULK;    // lower-triangle entries per bulk thread
+    const int k = (int)((1.0f + sqrtf((float)(8 * p + 1))) * 0.5f);   // exact: 8p + 1 < 2^24
+    const int i = p - (k - 1) * k / 2;
+    c = W - k;
+    r = W - 1 - i;
+}
+
+// One bulk step of potrf_leaf_pipe with NQ live slots in this warp: apply
+// column j - 1 to this thread's live entries, S[r][c] -= S[r][j-1] l_c, with
+// l_c = S[c][j-1] / D_{j-1} in lw.  Operands are read first and stores come
+// last, so the NQ FP64 instructions issue back to back; an entry at or past
+// `active` (the diagonal (j, j), finished by the chain) is computed but not
+// stored.  rc[q] packs slot q's entry as row | column << 8.
+template <int W, int NQ>
+__device__ __forceinline__ void leaf_bulk(double (*S)[W + 1], const double *lw, int j, int b, int active,
+                                          const int *rc)
+{
+    double x[NQ], y[NQ], l[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int r = rc[q] & 0xff, c = rc[q] >> 8;
+        x[q] = S[r][j - 1];
+        y[q] = S[r][c];
+        l[q] = lw[c];
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) y[q] = fma(-x[q], l[q], y[q]);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        if (q * 96 + b < active) S[rc[q] & 0xff][rc[q] >> 8] = y[q];
+}
+
+// The bulk warps' steps, one loop per live-slot count: the loop for NQ runs
+// while this warp has exactly NQ slots with a live lane (the count only
+// falls as j grows), then hands over to NQ - 1.  Every iteration ends with
+// the CTA barrier of its step.
+template <int W, int NQ>
+__device__ __forceinline__ void leaf_bulk_phases(double (*S)[W + 1], double *lw, const double *rdv, const int *rc,
+                                                 const int *bad, int &j, int nb, int b, int bw, int lane,
+                                                 bool &stop)
+{
+    for (; !stop && j < nb; ++j) {
+        const int live = (W - j) * (W - j + 1) / 2 - 1;
+        if ((live - bw + 95) / 96 < NQ) break;
+        const double rd = rdv[j - 1];
+#pragma unroll
+        for (int c = lane; c < W; c += 32) lw[c] = S[c][j - 1] * rd;
+        __syncwarp();
+        leaf_bulk<W, NQ>(S, lw, j, b, live, rc);
+        __syncthreads();
+        const int f = *bad;
+        stop = (f != 0 && f <= j + 1);
+    }
+    if constexpr (NQ > 1) leaf_bulk_phases<W, NQ - 1>(S, lw, rdv, rc, bad, j, nb, b, bw, lane, stop);
+}
+
+// Step 1 leaf of width W (32 or 64), one CTA of 128 threads.
+// Square-root-free sweep (the block is reduced to L' D L'^T with
+// S[r][c] = L_rc sqrt(D_c) below the diagonal; the square roots are taken
+// once at the end), pipelined so that the serial pivot chain is as short as
+// the FP64 units allow.  On this GPU each SM sub-partition retires one FP64
+// warp instruction per ~64 cycles, whatever the number of active lanes (an
+// instruction predicated off for every lane costs the same), and warp w
+// runs on sub-partition w % 4.  Hence:
+//   warp 0 (the chain), step j:  D_j = s_j - u_j (u_j / D_{j-1}) with
+//       u_j = S[j][j-1] (final) and s_j = S[j][j] (updated through column
+//       j-2), then 1 / D_j (pivot_rcp_short): five FP64 instructions;
+//   warps 1-3 (the bulk, one per remaining sub-partition), step j: apply
+//       column j-1 to every entry (r, c) with r >= c >= j except (j, j).
+// The W(W-1)/2 updatable entries (1 <= c <= r < W) are dealt to the 96
+// bulk threads cyclically in the order of leaf_entry, so the entries live
+// at step j form a prefix of that order whose last element is (j, j); each
+// warp runs a loop per live-slot count, so no FP64 instruction is issued
+// for a slot without a live lane.  One barrier per column.  Outputs as
+// potrf_leaf_body: A (lower nb x nb, nb <= W) overwritten by L,
+// rinv[c] = 1 / L_cc (1 in the padding), *info = col0 + c + 1 on a failed
+// pivot (D_c <= 0 or not finite).
+template <int W>
+__device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *rinv, int64_t col0, int64_t *info)
+{
+    static_assert(W == 32 || W == 64, "leaf width");
+    constexpr int THREADS = 128, NBULK = 96;
+    constexpr int NE = W * (W - 1) / 2;                  // entries with 1 <= c <= r < W
+    constexpr int PER = (NE + NBULK - 1) / NBULK;        // 6 (W = 32) or 21 (W = 64)
     __shared__ double S[W][W + 1];   // S[r][c]
-    __shared__ double lcb[2][W];     // l_c of the current step, by parity
-    __shared__ double dpiv[W], sqv[W], rsv[W];
+    __shared__ double rdv[W], dpiv[W], sqv[W], rsv[W];
+    __shared__ double lws[3][W];     // l_c of the current step, one copy per bulk warp
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < W * W; e += THREADS) {
@@ -321,158 +416,163 @@ __device__ inline void potrf_leaf_chain(double *A, int64_t lda, int nb, double *
         S[r][c] = v;
     }
     if (tid == 0) bad = 0;
-    const int sp = warp & 3;
-    const int b = (sp != 0) ? ((warp >> 2) * 3 + (sp - 1)) * 32 + lane : -1;
-    int er[PER], ec[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        er[q] = -1;
-        ec[q] = W;   // never active
-        const int e = PER * b + q;
-        if (b >= 0 && e < W * (W + 1) / 2) {
-            int c = 0, off = 0;
-            while (e >= off + (W - c)) {
-                off += W - c;
-                ++c;
-            }
-            er[q] = c + (e - off);
-            ec[q] = c;
-        }
-    }
     __syncthreads();
     if (warp == 0) {
-        double rd = 0.0;
-        if (lane == 0) {
-            dpiv[0] = S[0][0];
-            if (!gpch::pivot_rcp_chain(S[0][0], rd)) bad = 1;
-        }
-        rd = __shfl_sync(0xffffffffu, rd, 0);
-#pragma unroll
-        for (int h = 0; h < RH; ++h) lcb[0][lane + 32 * h] = S[lane + 32 * h][0] * rd;
-    }
-    __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-        if (bad) break;
-        const double *lc = lcb[j & 1];
-        const int j1 = j + 1;
-        if (warp == 0) {
-            if (j1 < nb) {
-                // column j1 <- column j1 - column j * l_j1 (rows above j1 are zero)
-                const int hp = j1 / 32, lp = j1 % 32;   // holder of the pivot row
-                double a[RH];
-#pragma unroll
-                for (int h = 0; h < RH; ++h) a[h] = fma(-S[lane + 32 * h][j], lc[j1], S[lane + 32 * h][j1]);
-                double rd = 0.0;
-                if (lane == lp) {
-                    const double d = a[hp];
-                    dpiv[j1] = d;
-                    if (!gpch::pivot_rcp_chain(d, rd)) bad = j1 + 1;
-                }
-                rd = __shfl_sync(0xffffffffu, rd, lp);
-#pragma unroll
-                for (int h = 0; h < RH; ++h) {
-                    const int r = lane + 32 * h;
-                    if (r >= j1) S[r][j1] = a[h];
-                    lcb[j1 & 1][r] = a[h] * rd;
-                }
+        double rdp = 0.0;   // 1 / D_{j-1}
+        for (int j = 0; j < nb; ++j) {
+            double d;
+            if (j == 0) {
+                d = S[0][0];
+            } else {
+                const double u = S[j][j - 1];
+                d = fma(-u * rdp, u, S[j][j]);
             }
-        } else if (b >= 0) {
-#pragma unroll
-            for (int q = 0; q < PER; ++q)
-                if (ec[q] > j1) S[er[q]][ec[q]] = fma(-S[er[q]][j], lc[ec[q]], S[er[q]][ec[q]]);
+            double rd = 0.0;
+            const bool ok = gpch::pivot_rcp_short(d, rd);
+            if (lane == 0) {
+                if (!ok) bad = j + 1;
+                dpiv[j] = d;
+                rdv[j] = rd;
+            }
+            rdp = rd;
+            __syncthreads();
+            // a failure of step j is seen by every thread after this barrier
+            const int f = bad;
+            if (f != 0 && f <= j + 1) break;
         }
+    } else {
+        const int b = tid - 32;          // bulk index, 0..95
+        const int bw = (warp - 1) * 32;  // first bulk index of this warp
+        int rc[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int p = q * NBULK + b;
+            int r = 1, c = 1;
+            if (p < NE) leaf_entry<W>(p, r, c);
+            rc[q] = r | (c << 8);
+        }
+        bool stop = false;
+        // step 0 has no bulk work
         __syncthreads();
+        {
+            const int f = bad;
+            stop = (f != 0 && f <= 1);
+        }
+        int j = 1;
+        leaf_bulk_phases<W, PER>(S, lws[warp - 1], rdv, rc, &bad, j, nb, b, bw, lane, stop);
+        for (; !stop && j < nb; ++j) {
+            __syncthreads();
+            const int f = bad;
+            stop = (f != 0 && f <= j + 1);
+        }
     }
     if (bad) {
         if (tid == 0) *info = col0 + bad;
         return;
     }
-    if (tid < W) {
+    for (int c = tid; c < W; c += THREADS) {
         double sq = 1.0, rs = 1.0;
-        if (tid < nb) gpch::pivot_sqrt(dpiv[tid], sq, rs);
-        sqv[tid] = sq;
-        rsv[tid] = rs;
+        if (c < nb) gpch::pivot_sqrt(dpiv[c], sq, rs);
+        sqv[c] = sq;
+        rsv[c] = rs;
     }
     __syncthreads();
-    for (int e = tid; e < W * W; e += THREADS) {
-        const int r = e % W, c = e / W;
-        if (r < nb && c < nb && r >= c) A[r + c * lda] = (r == c) ? sqv[c] : S[r][c] * rsv[c];
+    // the lower triangle including the diagonal: the positions of
+    // leaf_entry extended by column 0 (block k = W)
+    for (int p = tid; p < W * (W + 1) / 2; p += THREADS) {
+        int r, c;
+        leaf_entry<W>(p, r, c);
+        if (r < nb && c < nb) A[r + c * lda] = (r == c) ? sqv[c] : S[r][c] * rsv[c];
     }
-    if (rinv && tid < W) rinv[tid] = rsv[tid];
+    if (rinv) for (int c = tid; c < W; c += THREADS) rinv[c] = rsv[c];
 }
 
-// Panel solve by substitution: X = B L^-T in place on the m x nc panel B
-// (nc <= 64), with L a lower nc x nc FP64 block (ld ldl) and rinv its
-// diagonal reciprocals.  Column-oriented (right-looking): x_c = b_c / L_cc,
-// then b_k -= x_c L[k][c] for every k > c.  One warp per RPW rows; lane l
-// holds columns l and l + 32 of each of its rows (NARROW, nc <= 32: column
-// l only), so a column costs one shuffle and three (NARROW: two) FMA-class
-// instructions per row.  The CTA's WARPS * RPW rows are staged through
-// shared memory so that global reads and writes stay coalesced.  T is the
-// storage and arithmetic type of B.
-template <typename T, int RPW, int WARPS = 8, bool NARROW = false>
-__global__ void __launch_bounds__(WARPS * 32) trsm_sub_kernel(T *B, int64_t ldb, int64_t m, int nc,
-                                                              const double *__restrict__ L, int64_t ldl,
-                                                              const double *__restrict__ rinv, const int64_t *info)
+// Panel solve by substitution: X = B L^-T in place on the m x nc FP64 panel
+// B (nc <= NC, NC = 32 or 64), with L a lower nc x nc block (ld ldl) and
+// rinv its diagonal reciprocals.  Row by row, x L^T = b is solved with the
+// unit lower L' = L diag(rinv) (L'_kc = L_kc / L_cc): the running values y
+// start as b, column c takes y_c as it stands and subtracts y_c L'_kc from
+// every y_k, k > c, and x = y diag(rinv) at the end; the same products as
+// the textbook x_c = b_c / L_cc form, without a multiplication on the
+// per-column chain.  One warp per RPW rows, four warps (one per SM
+// sub-partition, so a row's chain of FP64 instructions is not interleaved
+// with another warp's); lane l holds columns l and l + 32.  Columns are
+// walked with runtime trip counts, so no FP64 instruction is issued for a
+// column that does not exist (on this GPU an FP64 instruction costs its
+// issue time even when every lane is predicated off).
+template <int NC, int RPW>
+__global__ void __launch_bounds__(128) trsm_unit_kernel(double *B, int64_t ldb, int64_t m, int nc,
+                                                        const double *__restrict__ L, int64_t ldl,
+                                                        const double *__restrict__ rinv, const int64_t *info)
 {
-    constexpr int ROWS = WARPS * RPW;
-    constexpr int KR = NARROW ? 32 : LEAF;   // columns held
-    __shared__ T Ls[KR][KR + 1];   // Ls[k][c] = L[k][c]
-    __shared__ T rs[KR];
-    __shared__ T Bs[KR][ROWS + 1];
+    static_assert(NC == 32 || NC == 64, "block width");
+    constexpr int WARPS = 4, ROWS = WARPS * RPW, H = NC / 32;
+    __shared__ double Ls[NC][NC + 1];   // Ls[k][c] = L'_kc for k > c, else 0
+    __shared__ double rs[NC];
+    __shared__ double Bs[NC][ROWS + 1];
     gpch::pdl_wait();
     gpch::pdl_trigger();
     if (info && *info != 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * ROWS;
-    for (int e = tid; e < KR * KR; e += blockDim.x) {
-        const int k = e % KR, c = e / KR;   // column-major walk: coalesced
-        Ls[k][c] = (k > c && k < nc && c < nc) ? (T)L[k + (int64_t)c * ldl] : T(0);
+#pragma unroll 8
+    for (int e = tid; e < NC * NC; e += 128) {
+        const int k = e % NC, c = e / NC;   // column-major walk: coalesced
+        Ls[k][c] = (k > c && k < nc && c < nc) ? L[k + (int64_t)c * ldl] : 0.0;
     }
-    if (tid < KR) rs[tid] = tid < nc ? (T)rinv[tid] : T(1);
-    for (int e = tid; e < KR * ROWS; e += blockDim.x) {
+    if (tid < NC) rs[tid] = tid < nc ? rinv[tid] : 1.0;
+#pragma unroll 4
+    for (int e = tid; e < NC * ROWS; e += 128) {
         const int r = e % ROWS, k = e / ROWS;
-        Bs[k][r] = (r0 + r < m && k < nc) ? B[(r0 + r) + (int64_t)k * ldb] : T(0);
+        Bs[k][r] = (r0 + r < m && k < nc) ? B[(r0 + r) + (int64_t)k * ldb] : 0.0;
     }
     __syncthreads();
-    T b0[RPW], b1[RPW];
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-        b0[q] = Bs[lane][warp * RPW + q];
-        b1[q] = NARROW ? T(0) : Bs[lane + 32 - (NARROW ? 32 : 0)][warp * RPW + q];
+    // L' = L diag(rinv) over the lower triangle (positions of leaf_entry;
+    // the diagonal and the padding hold zeros, so every product is issued
+    // without a predicate)
+#pragma unroll 4
+    for (int p = tid; p < NC * (NC + 1) / 2; p += 128) {
+        int k, c;
+        leaf_entry<NC>(p, k, c);
+        Ls[k][c] *= rs[c];
     }
-    for (int c = 0; c < nc; ++c) {
-        const T l0 = Ls[lane][c];   // zero on and above the diagonal
-        const T rc = rs[c];
-        const int src = c & 31;
-        if (NARROW) {
+    __syncthreads();
+    double y[H][RPW];
 #pragma unroll
-            for (int q = 0; q < RPW; ++q) {
-                const T xc = __shfl_sync(0xffffffffu, b0[q], src) * rc;
-                if (lane == src) b0[q] = xc;
-                b0[q] = fma(-xc, l0, b0[q]);
-            }
-            continue;
-        }
-        const T l1 = Ls[lane + 32 - (NARROW ? 32 : 0)][c];
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) y[h][q] = Bs[lane + 32 * h][warp * RPW + q];
+    const int n0 = nc < 32 ? nc : 32;
+    for (int c = 0; c < n0; ++c) {
+        double l[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) l[h] = Ls[lane + 32 * h][c];
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
-            const T xc = __shfl_sync(0xffffffffu, c < 32 ? b0[q] : b1[q], src) * rc;
-            if (lane == src) {
-                if (c < 32) b0[q] = xc;
-                else b1[q] = xc;
+            const double yc = __shfl_sync(0xffffffffu, y[0][q], c);
+#pragma unroll
+            for (int h = 0; h < H; ++h) y[h][q] = fma(-yc, l[h], y[h][q]);
+        }
+    }
+    if (H == 2) {
+        for (int c = 32; c < nc; ++c) {
+            const double l1 = Ls[lane + 32][c];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const double yc = __shfl_sync(0xffffffffu, y[H - 1][q], c - 32);
+                y[H - 1][q] = fma(-yc, l1, y[H - 1][q]);
             }
-            b0[q] = fma(-xc, l0, b0[q]);
-            b1[q] = fma(-xc, l1, b1[q]);
         }
     }
 #pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-        Bs[lane][warp * RPW + q] = b0[q];
-        if (!NARROW) Bs[lane + 32 - (NARROW ? 32 : 0)][warp * RPW + q] = b1[q];
+    for (int h = 0; h < H; ++h) {
+        const double r = rs[lane + 32 * h];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) Bs[lane + 32 * h][warp * RPW + q] = y[h][q] * r;
     }
     __syncthreads();
-    for (int e = tid; e < KR * ROWS; e += blockDim.x) {
+#pragma unroll 4
+    for (int e = tid; e < NC * ROWS; e += 128) {
         const int r = e % ROWS, k = e / ROWS;
         if (r0 + r < m && k < nc) B[(r0 + r) + (int64_t)k * ldb] = Bs[k][r];
     }
@@ -659,31 +759,28 @@ inline gpch_status launch_trsm_rows(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m,
     return GPCH_OK;
 }
 
-// X = B L^-T by substitution (trsm_sub_kernel); FP64 panels take one row
-// per warp (their cost is FP64 issue), FP32 panels four.
-template <typename T>
-inline gpch_status launch_trsm_sub(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int nc, const double *L,
+// X = B L^-T by substitution (trsm_unit_kernel) for an FP64 panel of
+// m x nc, nc <= 64.  Short panels (the steps inside a diagonal tile) take
+// one row per warp, so the chain of each row starts at once on its own
+// sub-partition; long panels take four rows per warp, which spreads the
+// shared prologue over more rows.
+inline gpch_status launch_trsm_sub(gpch_ctx *ctx, double *B, int64_t ldb, int64_t m, int nc, const double *L,
                                    int64_t ldl, const double *rinv, const int64_t *info, cudaStream_t st,
                                    bool pdl = false)
 {
     if (m <= 0 || nc <= 0) return GPCH_OK;
-    constexpr int RPW = sizeof(T) == 4 ? 4 : 1;
-    if (sizeof(T) == 8 && nc <= 32) {
-        // narrow FP64 blocks: one warp per SM sub-partition, so each row's
-        // chain of FP64 instructions is not interleaved with another warp's
-        const dim3 grid((unsigned)((m + 3) / 4));
+    const bool wide = nc > 32, many = m > 1024;
+    auto go = [&](auto kern, int rows) -> gpch_status {
+        const dim3 grid((unsigned)((m + rows - 1) / rows));
         if (pdl)
-            GPCH_CUDA(ctx, gpch::launch_pdl(trsm_sub_kernel<T, 1, 4, true>, grid, dim3(128), 0, st, B, ldb, m, nc, L,
-                                            ldl, rinv, info));
+            GPCH_CUDA(ctx, gpch::launch_pdl(kern, grid, dim3(128), 0, st, B, ldb, m, nc, L, ldl, rinv, info));
         else
-            trsm_sub_kernel<T, 1, 4, true><<<grid, 128, 0, st>>>(B, ldb, m, nc, L, ldl, rinv, info);
+            kern<<<grid, 128, 0, st>>>(B, ldb, m, nc, L, ldl, rinv, info);
         GPCH_LAUNCH_CHECK(ctx);
         return GPCH_OK;
-    }
-    trsm_sub_kernel<T, RPW><<<(unsigned)((m + 8 * RPW - 1) / (8 * RPW)), 256, 0, st>>>(B, ldb, m, nc, L, ldl, rinv,
-                                                                                     info);
-    GPCH_LAUNCH_CHECK(ctx);
-    return GPCH_OK;
+    };
+    if (wide) return many ? go(trsm_unit_kernel<64, 4>, 16) : go(trsm_unit_kernel<64, 1>, 4);
+    return many ? go(trsm_unit_kernel<32, 4>, 16) : go(trsm_unit_kernel<32, 1>, 4);
 }
 
 template <typename T>
