@@ -35,7 +35,7 @@ constexpr uint32_t TILE_B_BYTES = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
 constexpr size_t TC_SMEM = 1024 + STAGES * STAGE_BYTES + 256;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
-constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators (two CTAs fill an SM's TMEM)
+constexpr uint32_t TMEM_COLS = 2 * BN;   // accumulator + running sum (two CTAs fill an SM's TMEM)
 
 // Trailing update C_lower -= P P^T on tensor cores.  P is the m x kp panel,
 // 16-bit, K-major, described by tm_hi (and its tail by tm_lo when split);
@@ -44,16 +44,19 @@ constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators (two CTAs fill an S
 // + tail*head^T.  Only columns below ncol are written.
 //
 // The K range is a sequence of panels of panel_k columns (panel_k divides
-// kp).  Each panel's product is summed on its own in a TMEM accumulator and
-// subtracted from C before the next panel's, exactly as if the panels were
-// applied by separate updates: the FP32 sums stay one panel long while C is
-// read and written through L2 between panels.  Two accumulators alternate,
-// so the MMAs of one panel overlap the subtraction of the previous one.
-// Roles: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs (warp 1
-// owns the TMEM allocation), warps 2-5 subtract (warp w: tile rows
+// kp).  Each panel's product is summed on its own in the TMEM accumulator
+// (the tensor-core sums stay one panel long), and the epilogue adds it in
+// FP32, rounding to nearest, into a running sum kept in a second TMEM
+// region; the last panel's sum is subtracted from C.  The result is that
+// of subtracting the panels one by one (up to the order of the FP32
+// additions) while C is read and written once per launch instead of once
+// per panel.  The accumulator is released as soon as the epilogue has read
+// it, so the next panel's MMAs wait only for that read.  Roles: warp 0
+// lane 0 issues the TMA loads, warp 1 lane 0 the MMAs (warp 1 owns the
+// TMEM allocation), warps 2-5 run the epilogue (warp w: tile rows
 // 32 (w % 4) .. +31, its TMEM lanes).  One CTA per lower 128 x 128 tile of
 // C.  err: device status word, nonzero if a bounded wait gave up.
-__global__ void __launch_bounds__(TC_THREADS, 3)
+__global__ void __maxnreg__(112)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
                    int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
                    int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k)
@@ -69,19 +72,24 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // Tiles of the lower triangle of the T x T tile grid, column by column,
-    // restricted to tile columns [tk0, tk1): column tk holds tiles
-    // ti = tk .. T-1 and starts at offset(tk) = tk T - tk (tk - 1) / 2.
-    const int64_t T = (m + BM - 1) / BM;
-    auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
-    const int64_t t = (int64_t)blockIdx.x + offset(tk0);
-    int64_t lo = tk0, hi = tk1 - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) / 2;
-        if (offset(mid) <= t) lo = mid;
-        else hi = mid - 1;
+    // Tiles of the lower triangle of the T x T tile grid restricted to tile
+    // columns [tk0, tk1), row by row with the column varying fastest, so the
+    // CTAs that read the same rows of P run at the same time and share them
+    // through L2.  Rows tk0 .. tk1-2 hold 1, 2, ..., nc-1 tiles (the
+    // triangle), every later row nc = tk1 - tk0 tiles.
+    const int64_t nc = tk1 - tk0, tri = nc * (nc - 1) / 2;
+    const int64_t t = (int64_t)blockIdx.x;
+    int64_t ti, tk;
+    if (t < tri) {
+        int64_t r = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (r * (r + 1) / 2 > t) --r;
+        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+        ti = tk0 + r;
+        tk = tk0 + (t - r * (r + 1) / 2);
+    } else {
+        ti = tk1 - 1 + (t - tri) / nc;
+        tk = tk0 + (t - tri) % nc;
     }
-    const int64_t tk = lo, ti = tk + (t - offset(tk));
     const int64_t i0 = ti * BM, c0 = tk * BN;
 
     if (threadIdx.x == 0) {
@@ -136,19 +144,18 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer: panel p accumulates into accumulator p & 1 once
-            // the epilogue has released it
+            // MMA issuer: panel p accumulates into the accumulator once the
+            // epilogue has read panel p - 1 out of it
             const uint32_t idesc = f16 ? gpch::tc::idesc_f16_f32(BM, BN) : gpch::tc::idesc_bf16_f32(BM, BN);
             int kc = 0;
             bool ok = true;
             for (int p = 0; p < np && ok; ++p) {
-                const int a = p & 1;
-                if (p >= 2 && !gpch::tc::mbar_wait(&tempty[a], ((p >> 1) - 1) & 1, 4 * SPIN_LIMIT)) {
+                if (p >= 1 && !gpch::tc::mbar_wait(&tempty[0], (p - 1) & 1, 4 * SPIN_LIMIT)) {
                     atomicExch(err, 2);
                     break;
                 }
                 gpch::tc::tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(a * BN);
+                const uint32_t acc = tmem;
                 for (int q = 0; q < nprod * nkp; ++q, ++kc) {
                     const int s = kc % STAGES;
                     if (!gpch::tc::mbar_wait(&full[s], (kc / STAGES) & 1, SPIN_LIMIT)) {
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
                         gpch::tc::mma_bf16(acc, ad + 2 * k, bd + 2 * k, idesc, (q | k) != 0 ? 1u : 0u);
                     gpch::tc::mma_commit(&empty[s]);
                 }
-                if (ok) gpch::tc::mma_commit(&tfull[a]);
+                if (ok) gpch::tc::mma_commit(&tfull[0]);
             }
         }
         __syncwarp();
@@ -187,36 +194,51 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
         // columns c0 + j with j < jn are in C's lower triangle (and < ncol)
         const int64_t lim = (row < ncol - 1 ? row : ncol - 1) - c0 + 1;
         const int jn = !row_ok ? 0 : (lim > BN ? BN : (lim < 0 ? 0 : (int)lim));
+        const uint32_t tacc = tmem + ((uint32_t)(qw * 32) << 16), tsum = tacc + (uint32_t)BN;
         for (int p = 0; p < np; ++p) {
-            const int a = p & 1;
+            const bool last = p == np - 1;
             float *crow = C + row + c0 * ldc;
             float cv[32];
+            if (last) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) cv[j] = (j < jn) ? crow[(int64_t)j * ldc] : 0.0f;
-            bool ok = gpch::tc::mbar_wait(&tfull[a], (p >> 1) & 1, 4 * SPIN_LIMIT);
+                for (int j = 0; j < 32; ++j) cv[j] = (j < jn) ? crow[(int64_t)j * ldc] : 0.0f;
+            }
+            bool ok = gpch::tc::mbar_wait(&tfull[0], p & 1, 4 * SPIN_LIMIT);
             ok = __all_sync(0xffffffffu, ok);
             gpch::tc::tc_fence_after();
             if (!ok) {
                 if (lane == 0) atomicExch(err, 3);
                 break;
             }
-            const uint32_t tbase = tmem + (uint32_t)(a * BN) + ((uint32_t)(qw * 32) << 16);
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
                 float *cb = C + row + (c0 + cc * 32) * ldc;
                 // keep the column addresses from living across the loops
                 asm volatile("" : "+l"(cb));
-                if (cc > 0) {
+                if (last && cc > 0) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) cv[j] = (cc * 32 + j < jn) ? cb[(int64_t)j * ldc] : 0.0f;
                 }
                 float v[32];
-                gpch::tc::tmem_ld32(tbase + cc * 32, v);
+                gpch::tc::tmem_ld32(tacc + cc * 32, v);
                 if (cc == BN / 32 - 1) {
-                    // the accumulator is read: the next-but-one panel may use it
+                    // the accumulator is read: the next panel may use it
                     gpch::tc::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) gpch::tc::mbar_arrive(&tempty[a]);
+                    if (lane == 0) gpch::tc::mbar_arrive(&tempty[0]);
+                }
+                if (p > 0) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float s[16];
+                        gpch::tc::tmem_ld16(tsum + cc * 32 + h * 16, s);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[h * 16 + j] += s[j];
+                    }
+                }
+                if (!last) {
+                    gpch::tc::tmem_st32_wait(tsum + cc * 32, v);
+                    continue;
                 }
                 asm volatile("" : "+l"(cb));
 #pragma unroll
