@@ -56,11 +56,25 @@ constexpr uint32_t TMEM_COLS = 2 * BN;   // accumulator + running sum (two CTAs 
 // TMEM allocation), warps 2-5 run the epilogue (warp w: tile rows
 // 32 (w % 4) .. +31, its TMEM lanes).  One CTA per lower 128 x 128 tile of
 // C.  err: device status word, nonzero if a bounded wait gave up.
+//
+// RECT turns the kernel into the panel product C = P Q^T (overwrite):
+// P (rows of tm_hi / tm_lo) is m x kp, Q (rows of tmb_hi / tmb_lo) is
+// ncol x kp, every tile of the m x ncol rectangle (tile columns tk0 .. tk1-1)
+// is computed, and binary16 operands carry the scales 2^scale[1] (P) and
+// 2^scale_b[1] (Q).  Otherwise both operands are read through tm_hi / tm_lo
+// (the tmb maps are not used).  With ohi != nullptr (RECT only) the result
+// is also written as a binary16 head and tail scaled by 2^oscale[1]: row r,
+// column c at ohi[r * ldo + c] (the 16-bit copy the later updates read;
+// ohi and ldo must make every row 16-byte aligned).
+template <bool RECT>
 __global__ void __maxnreg__(112)
-    syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int64_t m,
+    syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                   const __grid_constant__ CUtensorMap tmb_hi, const __grid_constant__ CUtensorMap tmb_lo, int64_t m,
                    int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
-                   int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k)
+                   int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k,
+                   const int *scale_b, __half *ohi, __half *olo, int64_t ldo, const int *oscale)
 {
+    constexpr bool rect = RECT;
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
@@ -80,7 +94,10 @@ __global__ void __maxnreg__(112)
     const int64_t nc = tk1 - tk0, tri = nc * (nc - 1) / 2;
     const int64_t t = (int64_t)blockIdx.x;
     int64_t ti, tk;
-    if (t < tri) {
+    if constexpr (RECT) {
+        ti = t / nc;
+        tk = tk0 + t % nc;
+    } else if (t < tri) {
         int64_t r = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
         while (r * (r + 1) / 2 > t) --r;
         while ((r + 1) * (r + 2) / 2 <= t) ++r;
@@ -119,6 +136,10 @@ __global__ void __maxnreg__(112)
             // TMA producer
             gpch::tc::prefetch_tmap(&tm_hi);
             if (split) gpch::tc::prefetch_tmap(&tm_lo);
+            if constexpr (RECT) {
+                gpch::tc::prefetch_tmap(&tmb_hi);
+                if (split) gpch::tc::prefetch_tmap(&tmb_lo);
+            }
             int issued = 0;
             for (int kc = 0; kc < NK; ++kc) {
                 const int s = kc % STAGES;
@@ -129,7 +150,7 @@ __global__ void __maxnreg__(112)
                 const int p = kc / (nprod * nkp), prod = (kc / nkp) % nprod;
                 const int kk = p * nkp + kc % nkp;
                 const CUtensorMap *ma = (prod == 2) ? &tm_lo : &tm_hi;
-                const CUtensorMap *mb = (prod == 1) ? &tm_lo : &tm_hi;
+                const CUtensorMap *mb = rect ? ((prod == 1) ? &tmb_lo : &tmb_hi) : ((prod == 1) ? &tm_lo : &tm_hi);
                 gpch::tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                 gpch::tc::tma_load_2d(sA + s * TILE_A_BYTES, ma, &full[s], k_off + kk * BK, (int32_t)i0);
                 gpch::tc::tma_load_2d(sB + s * TILE_B_BYTES, mb, &full[s], k_off + kk * BK, (int32_t)c0);
@@ -181,8 +202,9 @@ __global__ void __maxnreg__(112)
         const int64_t row = i0 + qw * 32 + lane;
         const bool row_ok = row < m;
         // scaled binary16 operands: the products carry 2^(2e); undo it exactly
-        const float unscale = scale ? __int_as_float((127 - 2 * scale[1]) << 23) : 1.0f;
-        if (prefetch_c) {
+        const float unscale =
+            scale ? __int_as_float((127 - (rect ? scale[1] + scale_b[1] : 2 * scale[1])) << 23) : 1.0f;
+        if (prefetch_c && !rect) {
             // pull the C tile's columns into L2 while the first MMAs run
             const int64_t rows = (m - i0 < BM) ? m - i0 : BM;
             const uint32_t bytes = (uint32_t)(rows & ~int64_t(3)) * 4u;
@@ -192,14 +214,14 @@ __global__ void __maxnreg__(112)
                              : "memory");
         }
         // columns c0 + j with j < jn are in C's lower triangle (and < ncol)
-        const int64_t lim = (row < ncol - 1 ? row : ncol - 1) - c0 + 1;
+        const int64_t lim = rect ? ncol - c0 : (row < ncol - 1 ? row : ncol - 1) - c0 + 1;
         const int jn = !row_ok ? 0 : (lim > BN ? BN : (lim < 0 ? 0 : (int)lim));
         const uint32_t tacc = tmem + ((uint32_t)(qw * 32) << 16), tsum = tacc + (uint32_t)BN;
         for (int p = 0; p < np; ++p) {
             const bool last = p == np - 1;
             float *crow = C + row + c0 * ldc;
             float cv[32];
-            if (last) {
+            if (last && !rect) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) cv[j] = (j < jn) ? crow[(int64_t)j * ldc] : 0.0f;
             }
@@ -215,7 +237,7 @@ __global__ void __maxnreg__(112)
                 float *cb = C + row + (c0 + cc * 32) * ldc;
                 // keep the column addresses from living across the loops
                 asm volatile("" : "+l"(cb));
-                if (last && cc > 0) {
+                if (last && cc > 0 && !rect) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) cv[j] = (cc * 32 + j < jn) ? cb[(int64_t)j * ldc] : 0.0f;
                 }
@@ -241,9 +263,41 @@ __global__ void __maxnreg__(112)
                     continue;
                 }
                 asm volatile("" : "+l"(cb));
+                if constexpr (RECT) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (cc * 32 + j < jn) cb[(int64_t)j * ldc] = cv[j] - v[j] * unscale;
+                    for (int j = 0; j < 32; ++j) {
+                        v[j] *= unscale;
+                        if (cc * 32 + j < jn) cb[(int64_t)j * ldc] = v[j];
+                    }
+                    if (ohi && jn > 0) {
+                        // 16-byte stores: each lane writes its row's 32 values
+                        // (64 bytes per copy); columns at or past jn are zero
+                        const float osc = __int_as_float((127 + oscale[1]) << 23);
+                        uint4 *oh = reinterpret_cast<uint4 *>(ohi + row * ldo + c0 + cc * 32);
+                        uint4 *ol = reinterpret_cast<uint4 *>(olo + row * ldo + c0 + cc * 32);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            uint32_t hw[4], lw[4];
+#pragma unroll
+                            for (int h2 = 0; h2 < 4; ++h2) {
+                                const int j = 8 * q + 2 * h2;
+                                const float x0 = (cc * 32 + j < jn) ? v[j] * osc : 0.0f;
+                                const float x1 = (cc * 32 + j + 1 < jn) ? v[j + 1] * osc : 0.0f;
+                                const __half a0 = __float2half_rn(x0), a1 = __float2half_rn(x1);
+                                const __half b0 = __float2half_rn(x0 - __half2float(a0));
+                                const __half b1 = __float2half_rn(x1 - __half2float(a1));
+                                hw[h2] = (uint32_t)__half_as_ushort(a0) | ((uint32_t)__half_as_ushort(a1) << 16);
+                                lw[h2] = (uint32_t)__half_as_ushort(b0) | ((uint32_t)__half_as_ushort(b1) << 16);
+                            }
+                            oh[q] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            ol[q] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (cc * 32 + j < jn) cb[(int64_t)j * ldc] = cv[j] - v[j] * unscale;
+                }
             }
         }
     }
@@ -338,11 +392,128 @@ __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restri
     }
 }
 
+// Y = L^-1 for the nb x nb lower triangle L (FP32, column-major, ld ldl),
+// nb <= 512 with nb % 32 == 0, L and ldl 16-byte aligned, into Y
+// (column-major, ld ldy; zero above the diagonal; other sizes are left
+// untouched).  CTA b owns the 8 columns 8b .. 8b+7 of Y (L y = e_c, forward
+// substitution) and keeps them in shared memory, rows in blocks of 32.
+// Block column K of L (rows 32K .. nb-1) is copied in by 32 bulk copies
+// (one per column, completing on an mbarrier; bounded waits set *err = 5)
+// two blocks ahead of its use (three buffers).  Per
+// block: warp w solves the 32 x 32 diagonal block for column w (lane = row;
+// one shuffle and one FMA per row), then the later rows are updated as a
+// GEMM, rows x 8 columns x 32, in 4 x 4 register tiles (two 16-byte loads
+// feed 16 FMAs).
+constexpr int TI_COLS = 8;
+constexpr int TI_MAXN = 512;
+constexpr int TI_THREADS = 256;
+constexpr int TI_BUFS = 3;
+constexpr size_t TI_SMEM = (size_t)(TI_BUFS * TI_MAXN * 32 + TI_MAXN * TI_COLS) * sizeof(float);
+__global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const float *__restrict__ L, int64_t ldl, int nb,
+                                                                 float *Y, int64_t ldy, int *err)
+{
+    extern __shared__ __align__(16) float ti_smem[];
+    __shared__ __align__(8) uint64_t bar[TI_BUFS];
+    if (nb % 32 != 0 || nb > TI_MAXN) return;
+    float *Ts = ti_smem + TI_BUFS * TI_MAXN * 32;   // Ts[r * TI_COLS + c]: row r of this CTA's columns
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.x * TI_COLS;
+    const int nK = nb / 32, K0 = c0 / 32;
+    if (tid == 0) {
+        for (int b = 0; b < TI_BUFS; ++b) gpch::tc::mbar_init(&bar[b], 1);
+        gpch::tc::fence_mbar_init();
+    }
+    __syncthreads();
+    // block column K into buffer K % 3: (row r, col 32K + kk) at kk * TI_MAXN + r,
+    // one bulk copy per column by the lanes of warp 0
+    auto stage = [&](int K) {
+        if (warp != 0) return;
+        const uint32_t bytes = (uint32_t)(nb - 32 * K) * 4u;
+        float *Ls = ti_smem + (K % TI_BUFS) * TI_MAXN * 32;
+        if (lane == 0) gpch::tc::mbar_arrive_expect_tx(&bar[K % TI_BUFS], 32u * bytes);
+        __syncwarp();
+        gpch::tc::bulk_g2s(Ls + lane * TI_MAXN + 32 * K, L + 32 * K + (int64_t)(32 * K + lane) * ldl, bytes,
+                           &bar[K % TI_BUFS]);
+    };
+    uint32_t phases = 0;   // bit b: parity of buffer b's next phase
+    bool ok = true;
+    if (K0 < nK) stage(K0);
+    if (K0 + 1 < nK) stage(K0 + 1);
+    for (int e = tid; e < TI_MAXN * TI_COLS; e += TI_THREADS) {
+        const int r = e / TI_COLS, cc = e % TI_COLS;
+        Ts[e] = (r == c0 + cc) ? 1.0f : 0.0f;
+    }
+    for (int K = K0; K < nK && ok; ++K) {
+        if (K + 2 < nK) stage(K + 2);
+        const int bk = K % TI_BUFS;
+        ok = gpch::tc::mbar_wait(&bar[bk], (phases >> bk) & 1u, 1u << 24);
+        phases ^= 1u << bk;
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (tid == 0) atomicExch(err, 5);
+            // let every copy this CTA started land before it exits
+            gpch::tc::mbar_wait(&bar[bk], ((phases >> bk) & 1u) ^ 1u, 1u << 24);
+            for (int k2 = K + 1; k2 < nK && k2 <= K + 2; ++k2)
+                gpch::tc::mbar_wait(&bar[k2 % TI_BUFS], (phases >> (k2 % TI_BUFS)) & 1u, 1u << 24);
+            break;
+        }
+        const float *Ls = ti_smem + bk * TI_MAXN * 32;
+        {
+            // diagonal block, column c0 + warp, row 32K + lane
+            const int r = 32 * K + lane;
+            float t = Ts[r * TI_COLS + warp];
+            const float rp = 1.0f / Ls[lane * TI_MAXN + r];
+#pragma unroll 8
+            for (int kk = 0; kk < 32; ++kk) {
+                const float l = Ls[kk * TI_MAXN + r];
+                const float y = __shfl_sync(0xffffffffu, t * rp, kk);
+                const float tn = fmaf(-l, y, t);
+                t = (lane == kk) ? y : ((lane > kk) ? tn : t);
+            }
+            Ts[r * TI_COLS + warp] = t;
+        }
+        __syncthreads();
+        // later rows: T[r][:] -= L[r][32K..32K+31] Y[32K..32K+31][:]
+        const int rbeg = 32 * (K + 1), ntiles = (nb - rbeg) / 4 * (TI_COLS / 4);
+        for (int tile = tid; tile < ntiles; tile += TI_THREADS) {
+            const int r0 = rbeg + 4 * (tile / (TI_COLS / 4)), cg = 4 * (tile % (TI_COLS / 4));
+            float acc[4][4] = {};
+#pragma unroll 8
+            for (int kk = 0; kk < 32; ++kk) {
+                const float4 lv = *reinterpret_cast<const float4 *>(Ls + kk * TI_MAXN + r0);
+                const float4 yv = *reinterpret_cast<const float4 *>(Ts + (32 * K + kk) * TI_COLS + cg);
+                const float la[4] = {lv.x, lv.y, lv.z, lv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(la[a], ya[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float4 *tp = reinterpret_cast<float4 *>(Ts + (r0 + a) * TI_COLS + cg);
+                float4 v = *tp;
+                v.x -= acc[a][0];
+                v.y -= acc[a][1];
+                v.z -= acc[a][2];
+                v.w -= acc[a][3];
+                *tp = v;
+            }
+        }
+        __syncthreads();   // the buffer is refilled at the next step; Ts rows are read next block
+    }
+    for (int e = tid; e < nb * TI_COLS; e += TI_THREADS) {
+        const int r = e % nb, cc = e / nb;
+        Y[r + (int64_t)(c0 + cc) * ldy] = Ts[r * TI_COLS + cc];
+    }
+}
+
 // Scale word of a whole split-f16 factor from the a-priori bound
 // |L_ij| <= sqrt(max_i W_ii) (W = A + shift I, SPD): scale[0] = FP32 bits of
 // sqrt(max_i W_ii), from which the conversions derive the exponent.
+// pscale (optional): the same for the panels before their solve, bounded
+// by max_i W_ii.
 __global__ void __launch_bounds__(256) factor_scale_kernel(int64_t n, const float *__restrict__ W, int64_t ldw,
-                                                           int *scale)
+                                                           int *scale, int *pscale)
 {
     __shared__ float red[8];
     float mx = 0.0f;
@@ -357,6 +528,11 @@ __global__ void __launch_bounds__(256) factor_scale_kernel(int64_t n, const floa
         const float r = sqrtf(mx);
         scale[0] = (int)__float_as_uint(r);
         scale[1] = f16_scale_exp(__float_as_uint(r));
+        if (pscale) {
+            // entries of an SPD trailing matrix S obey |S_ij| <= max_i S_ii <= max_i W_ii
+            pscale[0] = (int)__float_as_uint(mx);
+            pscale[1] = f16_scale_exp(__float_as_uint(mx));
+        }
     }
 }
 
@@ -392,13 +568,18 @@ __global__ void __launch_bounds__(256) inv_blocks_f32_kernel(const double *__res
     for (int j = 0; j < LEAF; ++j) {
         float *xr = xrow[j & 1];
         if (tx == j % 16) {
-            const int i = j / 16;
+            // row j is x[j / 16]: selected with compile-time indices so that
+            // x stays in registers
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int c = ty + 16 * jj;
-                if (c <= j) {
-                    x[i][jj] *= dinv[j];
-                    xr[c] = x[i][jj];
+            for (int i = 0; i < 4; ++i) {
+                if (i != j / 16) continue;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int c = ty + 16 * jj;
+                    if (c <= j) {
+                        x[i][jj] *= dinv[j];
+                        xr[c] = x[i][jj];
+                    }
                 }
             }
         }
@@ -672,7 +853,7 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, k_off + kp, buf.ld, f16));
     static bool attr_done = false;
     if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         attr_done = true;
     }
     auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
@@ -684,10 +865,44 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
     // the C-tile prefetch needs 16-byte aligned columns
     const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-    syrk_tc_kernel<<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
-                                                               buf.err, prefetch_c, f16 ? 1 : 0,
+    syrk_tc_kernel<false><<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0,
+                                                               tk1, buf.err, prefetch_c, f16 ? 1 : 0,
                                                                f16 ? buf.scale : nullptr, (int)k_off, ncol,
-                                                               panel_k > 0 ? panel_k : kp);
+                                                               panel_k > 0 ? panel_k : kp, nullptr, nullptr,
+                                                               nullptr, 0, nullptr);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+// C (m x nq FP32, ldc) = P Q^T on tensor cores from split-f16 copies: P in
+// pb (rows 0 .. m-1, K columns 0 .. k-1, row stride pb.ld, scale word
+// pb.scale), Q in qb likewise (nq rows); nq <= k.  One CTA per 128 x 128
+// tile of C.  out (optional): C's own split-f16 copy, row r and column c at
+// out->hi[r * out->ld + out_col + c], scaled by out->scale.
+gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, float *C, int64_t ldc,
+                                 const LowprecBuffers &pb, const LowprecBuffers &qb, cudaStream_t st,
+                                 const LowprecBuffers *out = nullptr, int64_t out_col = 0)
+{
+    if (m <= 0 || nq <= 0) return GPCH_OK;
+    const int kp = (k + BK - 1) / BK * BK;
+    CUtensorMap phi, plo, qhi, qlo;
+    GPCH_CHECK(make_panel_map(ctx, &phi, pb.hi, m, kp, pb.ld, true));
+    GPCH_CHECK(make_panel_map(ctx, &plo, pb.lo, m, kp, pb.ld, true));
+    GPCH_CHECK(make_panel_map(ctx, &qhi, qb.hi, nq, kp, qb.ld, true));
+    GPCH_CHECK(make_panel_map(ctx, &qlo, qb.lo, nq, kp, qb.ld, true));
+    static bool attr_done = false;
+    if (!attr_done) {
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        attr_done = true;
+    }
+    const int64_t tr = (m + BM - 1) / BM, tc = (nq + BN - 1) / BN;
+    syrk_tc_kernel<true><<<(unsigned)(tr * tc), TC_THREADS, TC_SMEM, st>>>(phi, plo, qhi, qlo, m, kp, 1, C, ldc, 0, tc,
+                                                                   pb.err, 0, 1, pb.scale, 0, nq, kp, qb.scale,
+                                                                   out ? reinterpret_cast<__half *>(out->hi) + out_col
+                                                                       : nullptr,
+                                                                   out ? reinterpret_cast<__half *>(out->lo) + out_col
+                                                                       : nullptr,
+                                                                   out ? out->ld : 0, out ? out->scale : nullptr);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -713,6 +928,11 @@ struct MixedWs {
     __nv_bfloat16 *hi, *lo;   // 16-bit copies of all panels: row i, K column c at i * kpa + c
     int *err;
     int *scale;               // SPLIT_F16 scale word of the whole factor
+    // step 2 on tensor cores (SPLIT_F16): L_jj^-T, 16-bit copies of its
+    // transpose's rows and of the panel before the solve, their scale words
+    float *Tid;
+    __nv_bfloat16 *thi, *tlo, *phi, *plo;
+    int *tscale, *pscale;
 };
 
 static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
@@ -728,6 +948,13 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.hi = cv.take<__nv_bfloat16>((size_t)n * kpa);
     w.lo = cv.take<__nv_bfloat16>((size_t)n * kpa);
     w.scale = cv.take<int>(2);
+    w.Tid = cv.take<float>((size_t)tile * tile);
+    w.thi = cv.take<__nv_bfloat16>((size_t)tile * tile);
+    w.tlo = cv.take<__nv_bfloat16>((size_t)tile * tile);
+    w.phi = cv.take<__nv_bfloat16>((size_t)n * tile);
+    w.plo = cv.take<__nv_bfloat16>((size_t)n * tile);
+    w.tscale = cv.take<int>(2);
+    w.pscale = cv.take<int>(2);
     return w;
 }
 
@@ -775,12 +1002,19 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     all.ld = kpa;
     if (prec == GPCH_PREC_SPLIT_F16) {
         // one scale for every panel, from |L_ij| <= sqrt(max_i W_ii)
-        factor_scale_kernel<<<1, 256, 0, caller>>>(n, W, ldw, w.scale);
+        factor_scale_kernel<<<1, 256, 0, caller>>>(n, W, ldw, w.scale, w.pscale);
         GPCH_LAUNCH_CHECK(ctx);
         all.fixed_scale = true;
     }
     // the fused panel kernel needs 16-byte aligned columns of W
     const bool panel_fused = ((uintptr_t)W % 16 == 0) && (ldw % 4 == 0);
+    // step 2 as a tensor-core product (SPLIT_F16; the identity solve uses
+    // the fused panel kernel, and the 16-bit panel copies have a row stride
+    // of `tile` elements, a multiple of 64)
+    const bool tc_panel = prec == GPCH_PREC_SPLIT_F16 && panel_fused && tile <= TI_MAXN && tile % BK == 0;
+    if (tc_panel)
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(tri_inv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)TI_SMEM));
     if (panel_fused)
         GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)PN_SMEM));
@@ -809,10 +1043,47 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
             // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
             // diagonal blocks (computed from the FP64 factor)
             PhaseScope ph2(ctx, GPCH_PHASE_PANEL, st, (double)m * nj * nj);
-            inv_blocks_f32_kernel<<<(unsigned)((nj + LEAF - 1) / LEAF), 256, 0, st>>>(w.D, tile, nj, w.Linv,
-                                                                                     w.Linv32);
-            GPCH_LAUNCH_CHECK(ctx);
-            if (panel_fused && nj <= PN_MAXK) {
+            if (!tc_panel) {
+                inv_blocks_f32_kernel<<<(unsigned)((nj + LEAF - 1) / LEAF), 256, 0, st>>>(w.D, tile, nj, w.Linv,
+                                                                                         w.Linv32);
+                GPCH_LAUNCH_CHECK(ctx);
+            }
+            if (tc_panel) {
+                // X = P L_jj^-T as one tensor-core product: L_jj^-T by the
+                // FP32 solve of the identity (column-major, so its columns
+                // are the rows of L_jj^-1, the K-major right operand), both
+                // operands split into scaled binary16 head and tail
+                const int kpj = (int)((nj + BK - 1) / BK * BK);
+                tri_inv_f32_kernel<<<(unsigned)((nj + TI_COLS - 1) / TI_COLS), TI_THREADS, TI_SMEM, st>>>(
+                    Wjj, ldw, (int)nj, w.Tid, tile, w.err);
+                GPCH_LAUNCH_CHECK(ctx);
+                GPCH_CUDA(ctx, cudaMemsetAsync(w.tscale, 0, 2 * sizeof(int), st));
+                panel_absmax_kernel<<<dim3((unsigned)((nj + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
+                    w.Tid, tile, nj, (int)nj, reinterpret_cast<unsigned *>(w.tscale));
+                GPCH_LAUNCH_CHECK(ctx);
+                // rows of L_jj^-1 (stored column-major) become the K-major rows
+                panel_to_f16_kernel<<<dim3((unsigned)((nj + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
+                    w.Tid, tile, nj, (int)nj, kpj, reinterpret_cast<__half *>(w.thi),
+                    reinterpret_cast<__half *>(w.tlo), w.tscale, tile);
+                GPCH_LAUNCH_CHECK(ctx);
+                panel_to_f16_kernel<<<dim3((unsigned)((m + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
+                    Pan, ldw, m, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), reinterpret_cast<__half *>(w.plo),
+                    w.pscale, tile);
+                GPCH_LAUNCH_CHECK(ctx);
+                LowprecBuffers pbuf = all, qbuf = all;
+                pbuf.hi = w.phi;
+                pbuf.lo = w.plo;
+                pbuf.scale = w.pscale;
+                pbuf.ld = tile;
+                qbuf.hi = w.thi;
+                qbuf.lo = w.tlo;
+                qbuf.scale = w.tscale;
+                qbuf.ld = tile;
+                LowprecBuffers obuf = all;   // the panel's 16-bit copy, written by the product
+                obuf.hi = all.hi + (j0 + nj) * kpa;
+                obuf.lo = all.lo + (j0 + nj) * kpa;
+                GPCH_CHECK(panel_gemm_tc_launch(ctx, m, nj, (int)nj, Pan, ldw, pbuf, qbuf, st, &obuf, j0));
+            } else if (panel_fused && nj <= PN_MAXK) {
                 panel_trsm_f32_kernel<<<(unsigned)((m + PN_ROWS - 1) / PN_ROWS), PN_THREADS, PN_SMEM, st>>>(
                     Pan, ldw, m, (int)nj, Wjj, ldw, w.Linv32, w.info);
                 GPCH_LAUNCH_CHECK(ctx);
@@ -830,7 +1101,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         LowprecBuffers pb = all;
         pb.hi = all.hi + (j0 + nj) * kpa;
         pb.lo = all.lo + (j0 + nj) * kpa;
-        GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, pb, j0, st));
+        if (!tc_panel) GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, pb, j0, st));
         GPCH_CUDA(ctx, cudaEventRecord(ev_conv, st));
         // block column J+1 <- panel J, after it received panels 0..J-1
         if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_left, 0));

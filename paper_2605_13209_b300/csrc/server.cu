@@ -91,7 +91,9 @@ size_t request_bytes(const gpch_request &r, bool solo_mixed, int tile)
     // panel (n x n each), vectors
     if (solo_mixed)
         b += round_up(((n + 31) / 32 * 32) * n * 4) + 2 * round_up(n * ((n + 63) / 64 * 64) * 2) +
-             round_up((size_t)tile * tile * 8) + 12 * n * 8 * r.nrhs;
+             round_up((size_t)tile * tile * 8) + 12 * n * 8 * r.nrhs +
+             // panel solve on tensor cores: L_jj^-T, its 16-bit copies, the panel's
+             3 * round_up((size_t)tile * tile * 4) + 2 * round_up(n * (size_t)tile * 2);
     return b;
 }
 
