@@ -306,7 +306,7 @@ inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 
 inline size_t part_doubles(int64_t n, int nrhs)
 {
     const size_t mv = (size_t)((n + mv_width(nrhs) - 1) / mv_width(nrhs)) * mv_nr(nrhs);
-    const size_t vec = (size_t)((n + THREADS - 1) / THREADS) * 2 * MAXRHS;
+    const size_t vec = (size_t)((n + THREADS - 1) / THREADS) * 3 * MAXRHS;
     return mv > vec ? mv : vec;
 }
 
@@ -424,13 +424,14 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
 // |x|; the last CTA stores rr[c] and xinf[c].
 __global__ void __launch_bounds__(THREADS) pcg_update_kernel(int64_t n, int nrhs, double *X, int64_t ldx, double *R,
                                                              const double *S, const double *T, int64_t ldv,
-                                                             CGState st, double *rr_out, double *xinf_out)
+                                                             CGState st, double *rr_out, double *xinf_out,
+                                                             double *rinf_out)
 {
-    __shared__ double red[THREADS / 32][2 * MAXRHS];
+    __shared__ double red[THREADS / 32][3 * MAXRHS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
     for (int r = 0; r < nrhs; ++r) {
-        double rr = 0.0, xm = 0.0;
+        double rr = 0.0, xm = 0.0, rm = 0.0;
         if (st.active[r] && i < n) {
             const double a = st.alpha[r];
             const double xi = fma(a, S[i + r * ldv], X[i + r * ldx]);
@@ -439,34 +440,43 @@ __global__ void __launch_bounds__(THREADS) pcg_update_kernel(int64_t n, int nrhs
             R[i + r * ldv] = ri;
             rr = ri * ri;
             xm = fabs(xi);
+            rm = fabs(ri);
         }
         rr = warp_sum(rr);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+        for (int off = 16; off > 0; off >>= 1) {
+            xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+            rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, off));
+        }
         if (lane == 0) {
             red[warp][r] = rr;
             red[warp][MAXRHS + r] = xm;
+            red[warp][2 * MAXRHS + r] = rm;
         }
     }
     __syncthreads();
     if (tid < nrhs) {
-        double v = 0.0, m = 0.0;
+        double v = 0.0, m = 0.0, q = 0.0;
         for (int w = 0; w < THREADS / 32; ++w) {
             v += red[w][tid];
             m = fmax(m, red[w][MAXRHS + tid]);
+            q = fmax(q, red[w][2 * MAXRHS + tid]);
         }
-        st.part[(size_t)blockIdx.x * 2 * MAXRHS + tid] = v;
-        st.part[(size_t)blockIdx.x * 2 * MAXRHS + MAXRHS + tid] = m;
+        st.part[(size_t)blockIdx.x * 3 * MAXRHS + tid] = v;
+        st.part[(size_t)blockIdx.x * 3 * MAXRHS + MAXRHS + tid] = m;
+        st.part[(size_t)blockIdx.x * 3 * MAXRHS + 2 * MAXRHS + tid] = q;
     }
     if (last_cta(&st.counter[1])) {
         if (tid < nrhs) {
-            double v = 0.0, m = 0.0;
+            double v = 0.0, m = 0.0, q = 0.0;
             for (unsigned b = 0; b < gridDim.x; ++b) {
-                v += __ldcg(&st.part[(size_t)b * 2 * MAXRHS + tid]);
-                m = fmax(m, __ldcg(&st.part[(size_t)b * 2 * MAXRHS + MAXRHS + tid]));
+                v += __ldcg(&st.part[(size_t)b * 3 * MAXRHS + tid]);
+                m = fmax(m, __ldcg(&st.part[(size_t)b * 3 * MAXRHS + MAXRHS + tid]));
+                q = fmax(q, __ldcg(&st.part[(size_t)b * 3 * MAXRHS + 2 * MAXRHS + tid]));
             }
             rr_out[tid] = v;
             xinf_out[tid] = m;
+            rinf_out[tid] = q;
         }
         if (tid == 0) st.counter[1] = 0;
     }
@@ -694,25 +704,24 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     int nactive = 0;
     for (int c = 0; c < nrhs; ++c) nactive += h_active[c];
     const double eps2 = 1e-30;
-    // The recurrence gives ||r||_2; ||r||_2 / sqrt(n) <= ||r||_inf <= ||r||_2.
-    // The true residual is checked once the lower estimate, scaled by the
+    // The recurrence residual's ||r||_inf gives the backward-error estimate;
+    // the true residual b - A x is computed once that estimate, scaled by the
     // ratio of truth to estimate seen at the last failed check, meets tol.
     double ratio[MAXRHS];
     for (int c = 0; c < MAXRHS; ++c) ratio[c] = 1.0;
     double est_at_check[MAXRHS] = {0};
-    const double inv_sqrt_n = 1.0 / sqrt((double)n);
     int it = 0;
     while (nactive > 0 && it < maxit) {
         GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
-        pcg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, ldv, st, d_rr, d_xinf);
+        pcg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, ldv, st, d_rr, d_xinf, d_rinf);
         GPCH_LAUNCH_CHECK(ctx);
         ++it;
-        GPCH_CUDA(ctx, cudaMemcpyAsync(h, ex, 2 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GPCH_CUDA(ctx, cudaMemcpyAsync(h, ex, 3 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
         GPCH_CUDA(ctx, cudaStreamSynchronize(s));
         bool replace = (R > 0 && it % R == 0);
         for (int c = 0; c < nrhs; ++c) {
             if (!h_active[c]) continue;
-            const double est = sqrt(h[c]) * inv_sqrt_n / (anorm * h[MAXRHS + c] + binf[c]);
+            const double est = h[2 * MAXRHS + c] / (anorm * h[MAXRHS + c] + binf[c]);
             est_at_check[c] = est;
             if (est * ratio[c] <= bwd_tol || h[c] <= eps2 * bb[c]) replace = true;
         }
