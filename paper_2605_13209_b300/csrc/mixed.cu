@@ -763,29 +763,13 @@ __global__ void tile_f64_to_f32(int64_t nb, const double *__restrict__ D, int64_
     for (int64_t i = j + threadIdx.x; i < nb; i += blockDim.x) W[i + j * ldw] = (float)D[i + j * ldd];
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
 // Tensor map over a K-major 16-bit panel of m rows and kcols columns with
 // row stride ld elements (kcols and ld multiples of 64, so every TMA x
 // coordinate used is a multiple of 64 elements).
 gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int64_t kcols, int64_t ld,
                            bool f16)
 {
-    auto enc = get_encode();
+    auto enc = gpch::tc::tmap_encoder();
     if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
     cuuint64_t dims[2] = {(cuuint64_t)kcols, (cuuint64_t)m};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};

@@ -14,10 +14,12 @@
 // are FP64; with the FP32 (preconditioner) factor each 64 x 64 block
 // product runs in FP32 and is added to FP64 partial sums, and the diagonal
 // block solves stay FP64.
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
 #include "dense_fp64.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -195,11 +197,32 @@ constexpr int istride()
     return sizeof(TL) == 4 ? BS + 8 : BS + 4;
 }
 
-// Dynamic shared memory of one sweep CTA owning `nown` blocks.
+// FP32 factor, 128-row blocks: the blocks of L and the inverse blocks are
+// copied in by TMA as 2-D tiles whose inner (contiguous) extent is padded
+// to 136 (forward) or 132 (back) rows, which spreads the four lanes that
+// share an item over all banks.  Other variants stage element by element.
 template <typename TL, int BS>
+constexpr bool sweep_tma()
+{
+    return sizeof(TL) == 4 && BS == 128;
+}
+template <bool FWD>
+constexpr int tma_pad()
+{
+    return FWD ? 136 : 132;
+}
+
+// Dynamic shared memory of one sweep CTA owning `nown` blocks.
+template <typename TL, int BS, bool FWD = true>
 size_t sweep_smem_bytes(int nown, int nrhs, int maxrhs)
 {
     using TM = sweep_math_t<TL>;
+    if (sweep_tma<TL, BS>()) {
+        const int P = tma_pad<FWD>();
+        return 128 + (size_t)sweep_slots<TL, BS>() * P * BS * sizeof(TL) + (size_t)P * BS * sizeof(TM) +
+               (size_t)maxrhs * BS * sizeof(double) + (size_t)maxrhs * 2 * BS * sizeof(TM) +
+               (size_t)nown * BS * nrhs * sizeof(double);
+    }
     return (size_t)maxrhs * BS * sizeof(double) + (size_t)maxrhs * (ystride<BS>() + BS) * sizeof(TM) +
            (size_t)BS * istride<TL, BS>() * sizeof(TM) + (size_t)sweep_slots<TL, BS>() * lstride<BS>() * sizeof(TL) +
            (size_t)nown * BS * nrhs * sizeof(double);
@@ -231,33 +254,72 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
                                                                 int64_t ldl, const sweep_math_t<TL> *__restrict__ Linv,
                                                                 const double *B, int64_t ldb, double *Y, int64_t ldy,
                                                                 unsigned *flags, unsigned long long *tagw,
-                                                                unsigned tag, int *err, int maxrhs)
+                                                                unsigned tag, int *err, int maxrhs,
+                                                                const __grid_constant__ CUtensorMap tmL,
+                                                                const __grid_constant__ CUtensorMap tmI)
 {
     using TM = sweep_math_t<TL>;
     constexpr bool TAGGED = sizeof(TL) == 4;
+    constexpr bool TMAV = sweep_tma<TL, BS>();
     constexpr int SLOTS = sweep_slots<TL, BS>();
     constexpr int PQ = padq<TL>();
-    constexpr int IS = istride<TL, BS>();
-    constexpr int LSTRIDE = lstride<BS>();
-    constexpr int YSTRIDE = ystride<BS>();
-    constexpr int QK = BS / 4;   // k-range of one of the four lanes of an item
+    constexpr int TP = tma_pad<FWD>();                       // TMA variant: padded inner extent
+    constexpr int IS = TMAV ? TP : istride<TL, BS>();
+    constexpr int LSTRIDE = TMAV ? TP * BS : lstride<BS>();   // one staged block
+    constexpr int YSTRIDE = TMAV ? BS : ystride<BS>();
+    constexpr int QK = BS / 4;   // k-range of one of the four lanes of an item (element-staged variants)
     extern __shared__ __align__(16) double sw_smem[];
-    double *bst = sw_smem;                                        // staged B rows of the next block
-    TM *yv = reinterpret_cast<TM *>(bst + BS * maxrhs);           // solved block being applied
-    TM *vv = yv + YSTRIDE * maxrhs;                               // right-hand side of the block being solved
-    TM *Li = vv + BS * maxrhs;                                    // inverse of the next block, (r, k) at r + k * IS
-    TL *Ls = reinterpret_cast<TL *>(Li + BS * IS);                // [SLOTS][LSTRIDE]
-    double *acc = reinterpret_cast<double *>(Ls + SLOTS * LSTRIDE);  // [owned][64 * nrhs]
+    double *bst;   // staged B rows of the next block
+    TM *yv, *vv, *Li;
+    TL *Ls;
+    double *acc;
+    if constexpr (TMAV) {
+        // the TMA destinations first, 128-byte aligned
+        uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sw_smem) + 127) & ~uintptr_t(127));
+        Ls = reinterpret_cast<TL *>(base);                     // [SLOTS][TP * BS]: block (t, k) at
+        Li = reinterpret_cast<TM *>(Ls + SLOTS * LSTRIDE);     //   t + k * TP (fwd) or k + t * TP (back)
+        bst = reinterpret_cast<double *>(Li + TP * BS);        // inverse (r', k') at r' + k' * TP
+        yv = reinterpret_cast<TM *>(bst + BS * maxrhs);
+        vv = yv + BS * maxrhs;
+        acc = reinterpret_cast<double *>(vv + BS * maxrhs);
+    } else {
+        bst = sw_smem;
+        yv = reinterpret_cast<TM *>(bst + BS * maxrhs);            // solved block being applied
+        vv = yv + YSTRIDE * maxrhs;                                // right-hand side of the block being solved
+        Li = vv + BS * maxrhs;                                     // inverse of the next block, (r, k) at r + k * IS
+        Ls = reinterpret_cast<TL *>(Li + BS * IS);                 // [SLOTS][LSTRIDE]
+        acc = reinterpret_cast<double *>(Ls + SLOTS * LSTRIDE);    // [owned][64 * nrhs]
+    }
     __shared__ int abort_flag;
+    __shared__ __align__(8) uint64_t tbar;   // TMA variant: completion of a staging batch
+    uint32_t tphase = 0;
     const int tid = threadIdx.x;
     const int64_t N = (n + BS - 1) / BS;
     const int64_t P = gridDim.x, me = blockIdx.x;
     const int nown = (int)((N - me + P - 1) / P);
-    if (tid == 0) abort_flag = 0;
+    if (tid == 0) {
+        abort_flag = 0;
+        if constexpr (TMAV) {
+            gpch::tc::mbar_init(&tbar, 1);
+            gpch::tc::fence_mbar_init();
+        }
+    }
 
     auto rows_of = [&](int64_t J) { return (int)((n - J * BS < BS) ? n - J * BS : BS); };
     auto own_index = [&](int64_t I) { return (int)((I - me) / P); };
 
+    // TMA variant: thread 0 issues the tile copies of a batch after
+    // announcing its byte count; batch_wait() waits for all of them.
+    auto tma_block = [&](int slot, int64_t I, int64_t J) {
+        // forward: block (I, J) of L, x = rows of I; back: block (J, I), x = rows of J
+        gpch::tc::tma_load_2d(Ls + slot * LSTRIDE, &tmL, &tbar, (int32_t)((FWD ? I : J) * BS),
+                              (int32_t)((FWD ? J : I) * BS));
+    };
+    auto batch_wait = [&]() -> bool {
+        const bool ok = gpch::tc::mbar_wait(&tbar, tphase, FLAG_SPIN_LIMIT);
+        tphase ^= 1u;
+        return ok;
+    };
     auto stage = [&](int slot, int64_t I, int64_t J) {
         const int nI = rows_of(I), nJ = rows_of(J);
         TL *dst = Ls + slot * LSTRIDE;
@@ -275,9 +337,11 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
     // v[k] in item r: forward that is (L_JJ^-1)(r, k), back (L_JJ^-1)(k, r).
     auto stage_solve = [&](int64_t J) {
         const TM *src = Linv + J * BS * BS;
-        for (int e = tid; e < BS * BS; e += SW_THREADS) {
-            const int a = e % BS, b = e / BS;
-            cp_async_elem(Li + (FWD ? a + b * IS : b + a * IS), src + e, (int)sizeof(TM));
+        if constexpr (!TMAV) {
+            for (int e = tid; e < BS * BS; e += SW_THREADS) {
+                const int a = e % BS, b = e / BS;
+                cp_async_elem(Li + (FWD ? a + b * IS : b + a * IS), src + e, (int)sizeof(TM));
+            }
         }
         const int nb = rows_of(J);
         for (int e = tid; e < BS * nrhs; e += SW_THREADS) {
@@ -298,6 +362,9 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
             TM s = 0;
             if (FWD) {
                 for (int k = p; k <= r; k += 4) s = fma(Li[r + k * IS], vv[k + c * BS], s);
+            } else if constexpr (TMAV) {
+                // the inverse block is staged untransposed: (L^-1)(k, r) at k + r * IS
+                for (int k = r + ((p - r) & 3); k < BS; k += 4) s = fma(Li[k + r * IS], vv[k + c * BS], s);
             } else {
                 for (int k = r + ((p - r) & 3); k < BS; k += 4) s = fma(Li[r + k * IS], vv[k + c * BS], s);
             }
@@ -327,13 +394,25 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         const int q = tid & 3;
         for (int item = tid >> 2; item < BS * nrhs; item += SW_THREADS / 4) {
             const int t = item % BS, c = item / BS;
-            const TM *y = yv + c * YSTRIDE + q * (QK + 1);
-            const TL *l = Lb + (q * QK) * (BS + 1) + q * PQ + t;
             TM s0 = 0, s1 = 0;
+            if constexpr (TMAV) {
+                // lane q takes k = q, q + 4, ... (conflict-free with the padded tiles)
+                const TM *y = yv + c * BS + q;
+                const TL *l = FWD ? Lb + t + q * TP : Lb + t * TP + q;
+                constexpr int KS = FWD ? 4 * TP : 4;   // step of k by 4
+#pragma unroll 8
+                for (int j = 0; j < BS / 4; j += 2) {
+                    s0 = fma((TM)l[j * KS], y[4 * j], s0);
+                    s1 = fma((TM)l[(j + 1) * KS], y[4 * j + 4], s1);
+                }
+            } else {
+                const TM *y = yv + c * YSTRIDE + q * (QK + 1);
+                const TL *l = Lb + (q * QK) * (BS + 1) + q * PQ + t;
 #pragma unroll
-            for (int k = 0; k < QK; k += 2) {
-                s0 = fma((TM)l[k * (BS + 1)], y[k], s0);
-                s1 = fma((TM)l[(k + 1) * (BS + 1)], y[k + 1], s1);
+                for (int k = 0; k < QK; k += 2) {
+                    s0 = fma((TM)l[k * (BS + 1)], y[k], s0);
+                    s1 = fma((TM)l[(k + 1) * (BS + 1)], y[k + 1], s1);
+                }
             }
             TM s = s0 + s1;
             s += __shfl_xor_sync(0xffffffffu, s, 1);
@@ -361,7 +440,8 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
                     v = ld_relaxed_u64(w);
                 }
                 const int r = e % BS, c = e / BS;
-                yv[c * YSTRIDE + (r / QK) * (QK + 1) + r % QK] = __uint_as_float((unsigned)v);
+                if constexpr (TMAV) yv[c * BS + r] = __uint_as_float((unsigned)v);
+                else yv[c * YSTRIDE + (r / QK) * (QK + 1) + r % QK] = __uint_as_float((unsigned)v);
             }
             if (!ok) {
                 abort_flag = 1;
@@ -394,13 +474,34 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         }
     };
 
+    // TMA variant: thread 0 announces the bytes of a batch of tile copies
+    // (cnt blocks of L for step J, plus the inverse of block Jinv) and
+    // issues them; every thread then waits with batch_wait().
+    auto issue_batch = [&](int cnt, const int64_t *ch, int64_t J, bool with_inv, int64_t Jinv) {
+        if constexpr (TMAV) {
+            if (tid == 0) {
+                const uint32_t bytes = (uint32_t)(cnt + (with_inv ? 1 : 0)) * (uint32_t)(TP * BS * sizeof(TL));
+                gpch::tc::mbar_arrive_expect_tx(&tbar, bytes);
+                for (int i = 0; i < cnt; ++i) tma_block(i, ch[i], J);
+                if (with_inv) gpch::tc::tma_load_2d(Li, &tmI, &tbar, 0, (int32_t)(Jinv * BS));
+            }
+        }
+    };
     __syncthreads();
     const int64_t first = FWD ? 0 : N - 1;
     if (first % P == me) {
         stage_solve(first);
         cp_async_commit();
+        issue_batch(0, nullptr, 0, true, first);
         cp_async_wait_all();
+        if constexpr (TMAV) {
+            if (!batch_wait()) {
+                abort_flag = 1;
+                atomicExch(err, 1);
+            }
+        }
         __syncthreads();
+        if (abort_flag) return;
         for (int e = tid; e < BS * nrhs; e += SW_THREADS) vv[e] = (TM)bst[e];
         __syncthreads();
         finalize(first);
@@ -425,14 +526,22 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         int64_t chunk[SLOTS];
         while (staged < SLOTS && in_range(cur)) {
             chunk[staged] = cur;
-            stage(staged, cur, J);
+            if constexpr (!TMAV) stage(staged, cur, J);
             ++staged;
             cur = FWD ? cur + P : cur - P;
         }
         if (own_next) stage_solve(next);
         cp_async_commit();
+        const bool batch = staged > 0 || own_next;
+        if (batch) issue_batch(staged, chunk, J, own_next, next);
         receive(J);
         cp_async_wait_all();
+        if constexpr (TMAV) {
+            if (batch && !batch_wait()) {
+                abort_flag = 1;
+                atomicExch(err, 1);
+            }
+        }
         __syncthreads();
         if (abort_flag) return;
         for (int q = 0; q < staged; ++q) {
@@ -449,13 +558,21 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
             int cnt = 0;
             while (cnt < SLOTS && in_range(cur)) {
                 chunk[cnt] = cur;
-                stage(cnt, cur, J);
+                if constexpr (!TMAV) stage(cnt, cur, J);
                 ++cnt;
                 cur = FWD ? cur + P : cur - P;
             }
             cp_async_commit();
+            issue_batch(cnt, chunk, J, false, 0);
             cp_async_wait_all();
+            if constexpr (TMAV) {
+                if (!batch_wait()) {
+                    abort_flag = 1;
+                    atomicExch(err, 1);
+                }
+            }
             __syncthreads();
+            if (abort_flag) return;
             for (int q = 0; q < cnt; ++q) contribution(q, chunk[q], false);
         }
         __syncthreads();
@@ -486,7 +603,32 @@ gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_
     const int P = (int)(N < sm_count(ctx) ? N : sm_count(ctx));
     const int nown = (int)((N + P - 1) / P);
     const int maxrhs = BS == 128 ? 2 : SW_MAXRHS;
-    const size_t smem = sweep_smem_bytes<TL, BS>(nown, nrhs, maxrhs);
+    const size_t smem = sweep_smem_bytes<TL, BS, FWD>(nown, nrhs, maxrhs);
+    CUtensorMap tmL, tmI;
+    memset(&tmL, 0, sizeof tmL);
+    memset(&tmI, 0, sizeof tmI);
+    if (sweep_tma<TL, BS>()) {
+        // L as an n x n FP32 matrix (box: TP rows x BS columns), and the
+        // inverse blocks as a BS x (N BS) matrix (box: TP x BS); rows past
+        // the ends read as zeros
+        auto enc = gpch::tc::tmap_encoder();
+        if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
+        const cuuint32_t box[2] = {(cuuint32_t)tma_pad<FWD>(), (cuuint32_t)BS};
+        const cuuint32_t estr[2] = {1, 1};
+        const cuuint64_t dl[2] = {(cuuint64_t)n, (cuuint64_t)n};
+        const cuuint64_t sl[1] = {(cuuint64_t)ldl * sizeof(TL)};
+        CUresult r = enc(&tmL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<TL *>(L), dl, sl, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return gpch::fail(ctx, GPCH_CUDA_ERROR, "tensor map of L failed (%d)", (int)r);
+        const cuuint64_t di[2] = {(cuuint64_t)BS, (cuuint64_t)(N * BS)};
+        const cuuint64_t si[1] = {(cuuint64_t)BS * sizeof(sweep_math_t<TL>)};
+        r = enc(&tmI, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<sweep_math_t<TL> *>(Linv), di, si, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return gpch::fail(ctx, GPCH_CUDA_ERROR, "tensor map of the inverse blocks failed (%d)", (int)r);
+    }
     int maxsmem = 0;
     GPCH_CUDA(ctx, cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (smem + 1024 > (size_t)maxsmem)
@@ -505,7 +647,7 @@ gpch_status launch_sweep(gpch_ctx *ctx, int64_t n, int nrhs, const TL *L, int64_
         }
     }
     int maxrhs_arg = maxrhs;
-    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &tagw, &tag, &err, &maxrhs_arg};
+    void *args[] = {&n, &nrhs, &L, &ldl, &Linv, &B, &ldb, &Y, &ldy, &flags, &tagw, &tag, &err, &maxrhs_arg, &tmL, &tmI};
     GPCH_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)trsv_sweep_kernel<TL, FWD, BS>, dim3(P), dim3(SW_THREADS),
                                                args, smem, st));
     GPCH_LAUNCH_CHECK(ctx);
@@ -581,7 +723,8 @@ gpch_status solve_apply_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, do
     PhaseScope ph(ctx, GPCH_PHASE_SOLVE, st, 2.0 * (double)n * n * nrhs);
     // FP32 factor, one or two right-hand sides: 128-row blocks when their
     // shared memory fits
-    if (sizeof(TL) == 4 && nrhs <= 2) {
+    // (the TMA copies of that variant need a 16-byte aligned L and ldl)
+    if (sizeof(TL) == 4 && nrhs <= 2 && (uintptr_t)L % 16 == 0 && (ldl * sizeof(TL)) % 16 == 0) {
         const int64_t N2 = (n + 127) / 128;
         const int P2 = (int)(N2 < sm_count(ctx) ? N2 : sm_count(ctx));
         const int nown2 = (int)((N2 + P2 - 1) / P2);
