@@ -534,6 +534,23 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
         cp_async_commit();
         const bool batch = staged > 0 || own_next;
         if (batch) issue_batch(staged, chunk, J, own_next, next);
+        if constexpr (TMAV) {
+            // the tiles this CTA copies at the next step, into L2 now: its
+            // blocks of step J' = next, and the inverse it solves with then
+            const int64_t Jn = next, Jnn = FWD ? J + 2 : J - 2;
+            if (tid == 0 && Jn >= 0 && Jn < N) {
+                int64_t I = me;
+                if (FWD) {
+                    if (I <= Jn) I += ((Jn - I) / P + 1) * P;
+                } else {
+                    I = me + ((N - 1 - me) / P) * P;
+                    while (I >= Jn && I >= 0) I -= P;
+                }
+                for (int q = 0; q < SLOTS && (FWD ? I < N : I >= 0); ++q, I = FWD ? I + P : I - P)
+                    gpch::tc::tma_prefetch_2d(&tmL, (int32_t)((FWD ? I : Jn) * BS), (int32_t)((FWD ? Jn : I) * BS));
+                if (Jnn >= 0 && Jnn < N && Jnn % P == me) gpch::tc::tma_prefetch_2d(&tmI, 0, (int32_t)(Jnn * BS));
+            }
+        }
         receive(J);
         cp_async_wait_all();
         if constexpr (TMAV) {

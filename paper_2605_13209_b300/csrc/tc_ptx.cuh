@@ -93,6 +93,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
+// Prefetch the 2-D tile at (x, y) of a tensor map into L2 (a hint; no
+// completion to wait for).  Same coordinate rules as tma_load_2d.
+__device__ __forceinline__ void tma_prefetch_2d(const void *tmap, int32_t x, int32_t y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap), "r"(x), "r"(y)
+                 : "memory");
+}
+
 // 2-D tiled TMA load global -> shared, completing on `bar` (tx bytes).
 // x is the innermost coordinate (elements); it must be a multiple of
 // 16 bytes / element size.
