@@ -1010,6 +1010,10 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
     const int64_t blk_cols = (tile + BN - 1) / BN;   // tile columns of one block column
     const int64_t LEFT_K = 4 * (int64_t)tile;         // K columns (whole panels) per launch of the long pass
+    // products summed in the tensor-core accumulator before they are added
+    // (in FP32, rounding to nearest) to the running sum: half a panel when
+    // that is a whole number of 64-column K blocks
+    const int acc_k = (tile % (2 * BK) == 0) ? tile / 2 : tile;
     for (int64_t J = 0; J < ncols; ++J) {
         const int64_t j0 = J * tile;
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
@@ -1091,7 +1095,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_left, 0));
         left_pending = false;
         GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, j0, W + (j0 + nj) * (1 + ldw), ldw, prec, pb, 0, blk_cols, st,
-                                  tile));
+                                  tile, acc_k));
         // block column J+2 <- panels 0..J on the second stream
         if (m > tile) {
             const int64_t r2 = j0 + nj + tile, m2 = n - r2, K = j0 + nj;
@@ -1102,7 +1106,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
             for (int64_t k0 = 0; k0 < K; k0 += LEFT_K) {
                 const int64_t kk = (K - k0 < LEFT_K) ? K - k0 : LEFT_K;
                 GPCH_CHECK(syrk_tc_launch(ctx, m2, (int)kk, k0, W + r2 * (1 + ldw), ldw, prec, qb, 0, blk_cols, sb,
-                                          tile, tile));
+                                          tile, acc_k));
             }
             GPCH_CUDA(ctx, cudaEventRecord(ev_left, sb));
             left_pending = true;
