@@ -358,7 +358,7 @@ __device__ __forceinline__ void leaf_bulk(double (*S)[W + 1], const double *lw, 
 template <int W, int NQ>
 __device__ __forceinline__ void leaf_bulk_phases(double (*S)[W + 1], double *lw, const double *rdv, const int *rc,
                                                  const int *bad, int &j, int nb, int b, int bw, int lane,
-                                                 bool &stop)
+                                                 bool &stop, double *u2v)
 {
     for (; !stop && j < nb; ++j) {
         const int live = (W - j) * (W - j + 1) / 2 - 1;
@@ -368,11 +368,24 @@ __device__ __forceinline__ void leaf_bulk_phases(double (*S)[W + 1], double *lw,
         for (int c = lane; c < W; c += 32) lw[c] = S[c][j - 1] * rd;
         __syncwarp();
         leaf_bulk<W, NQ>(S, lw, j, b, live, rc);
+        if (j + 1 < W) {
+            // entry (j+1, j) is final now; the warp that updated it squares it
+            // for the chain's next pivot (position of the entry in the order
+            // of leaf_entry: column j's block, second to last)
+            const int p = (W - 1 - j) * (W - j) / 2 + (W - 2 - j);
+            if ((p % 96) / 32 == (b >> 5)) {
+                __syncwarp();
+                if (lane == 0) {
+                    const double u = S[j + 1][j];
+                    u2v[j + 1] = u * u;
+                }
+            }
+        }
         __syncthreads();
         const int f = *bad;
         stop = (f != 0 && f <= j + 1);
     }
-    if constexpr (NQ > 1) leaf_bulk_phases<W, NQ - 1>(S, lw, rdv, rc, bad, j, nb, b, bw, lane, stop);
+    if constexpr (NQ > 1) leaf_bulk_phases<W, NQ - 1>(S, lw, rdv, rc, bad, j, nb, b, bw, lane, stop, u2v);
 }
 
 // Step 1 leaf of width W (32 or 64), one CTA of 128 threads.
@@ -406,14 +419,23 @@ __device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *r
     __shared__ double S[W][W + 1];   // S[r][c]
     __shared__ double rdv[W], dpiv[W], sqv[W], rsv[W];
     __shared__ double lws[3][W];     // l_c of the current step, one copy per bulk warp
+    __shared__ double u2v[W];        // u2v[j] = S[j][j-1]^2 (final), left by the bulk for the chain
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < W * W; e += THREADS) {
-        const int r = e % W, c = e / W;
-        double v;
-        if (r < nb && c < nb) v = (r >= c) ? A[r + c * lda] : 0.0;
-        else v = (r == c) ? 1.0 : 0.0;
-        S[r][c] = v;
+    {
+        // all loads of a thread in flight at once
+        constexpr int NL = W * W / THREADS;
+        double v[NL];
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int e = tid + i * THREADS, r = e % W, c = e / W;
+            v[i] = (r < nb && c < nb && r >= c) ? A[r + c * lda] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int e = tid + i * THREADS, r = e % W, c = e / W;
+            S[r][c] = (r < nb && c < nb) ? v[i] : ((r == c) ? 1.0 : 0.0);
+        }
     }
     if (tid == 0) bad = 0;
     __syncthreads();
@@ -421,12 +443,8 @@ __device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *r
         double rdp = 0.0;   // 1 / D_{j-1}
         for (int j = 0; j < nb; ++j) {
             double d;
-            if (j == 0) {
-                d = S[0][0];
-            } else {
-                const double u = S[j][j - 1];
-                d = fma(-u * rdp, u, S[j][j]);
-            }
+            if (j == 0) d = S[0][0];
+            else d = fma(-u2v[j], rdp, S[j][j]);
             double rd = 0.0;
             const bool ok = gpch::pivot_rcp_short(d, rd);
             if (lane == 0) {
@@ -437,8 +455,8 @@ __device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *r
             rdp = rd;
             __syncthreads();
             // a failure of step j is seen by every thread after this barrier
-            const int f = bad;
-            if (f != 0 && f <= j + 1) break;
+            // (the chain warp knows its own outcome)
+            if (!ok) break;
         }
     } else {
         const int b = tid - 32;          // bulk index, 0..95
@@ -452,14 +470,15 @@ __device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *r
             rc[q] = r | (c << 8);
         }
         bool stop = false;
-        // step 0 has no bulk work
+        // step 0 has no bulk work but the chain's input of step 1
+        if (tid == 32) u2v[1] = S[1][0] * S[1][0];
         __syncthreads();
         {
             const int f = bad;
             stop = (f != 0 && f <= 1);
         }
         int j = 1;
-        leaf_bulk_phases<W, PER>(S, lws[warp - 1], rdv, rc, &bad, j, nb, b, bw, lane, stop);
+        leaf_bulk_phases<W, PER>(S, lws[warp - 1], rdv, rc, &bad, j, nb, b, bw, lane, stop, u2v);
         for (; !stop && j < nb; ++j) {
             __syncthreads();
             const int f = bad;
