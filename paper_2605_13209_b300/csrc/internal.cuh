@@ -32,7 +32,8 @@ struct gpch_ctx {
     double phase_work[GPCH_PHASE_COUNT] = {0};
     cudaStream_t aux = nullptr;          // low-priority stream for bulk overlapped work
     cudaStream_t crit = nullptr;         // high-priority stream for the critical chain
-    cudaEvent_t aux_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t side = nullptr;         // middle priority: work the critical chain needs one step later
+    cudaEvent_t aux_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace gpch {

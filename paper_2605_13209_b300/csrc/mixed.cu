@@ -57,16 +57,17 @@ constexpr uint32_t TMEM_COLS = 2 * BN;   // accumulator + running sum (two CTAs 
 // 32 (w % 4) .. +31, its TMEM lanes).  One CTA per lower 128 x 128 tile of
 // C.  err: device status word, nonzero if a bounded wait gave up.
 //
-// RECT turns the kernel into the panel product C = P Q^T (overwrite):
+// MODE 0 is the update above.  MODE 1 is the product C = P Q^T
+// (overwrite), MODE 2 the update C -= P Q^T, both over a rectangle:
 // P (rows of tm_hi / tm_lo) is m x kp, Q (rows of tmb_hi / tmb_lo) is
 // ncol x kp, every tile of the m x ncol rectangle (tile columns tk0 .. tk1-1)
 // is computed, and binary16 operands carry the scales 2^scale[1] (P) and
-// 2^scale_b[1] (Q).  Otherwise both operands are read through tm_hi / tm_lo
-// (the tmb maps are not used).  With ohi != nullptr (RECT only) the result
-// is also written as a binary16 head and tail scaled by 2^oscale[1]: row r,
+// 2^scale_b[1] (Q).  MODE 0 reads both operands through tm_hi / tm_lo (the
+// tmb maps are not used).  With ohi != nullptr (MODE 1 only) the result is
+// also written as a binary16 head and tail scaled by 2^oscale[1]: row r,
 // column c at ohi[r * ldo + c] (the 16-bit copy the later updates read;
 // ohi and ldo must make every row 16-byte aligned).
-template <bool RECT>
+template <int MODE>
 __global__ void __maxnreg__(112)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                    const __grid_constant__ CUtensorMap tmb_hi, const __grid_constant__ CUtensorMap tmb_lo, int64_t m,
@@ -74,7 +75,8 @@ __global__ void __maxnreg__(112)
                    int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k,
                    const int *scale_b, __half *ohi, __half *olo, int64_t ldo, const int *oscale)
 {
-    constexpr bool rect = RECT;
+    constexpr bool rect = MODE != 0;   // rectangle of P Q^T
+    constexpr bool sub = MODE != 1;    // C -= (else C = )
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
@@ -94,7 +96,7 @@ __global__ void __maxnreg__(112)
     const int64_t nc = tk1 - tk0, tri = nc * (nc - 1) / 2;
     const int64_t t = (int64_t)blockIdx.x;
     int64_t ti, tk;
-    if constexpr (RECT) {
+    if constexpr (rect) {
         ti = t / nc;
         tk = tk0 + t % nc;
     } else if (t < tri) {
@@ -136,7 +138,7 @@ __global__ void __maxnreg__(112)
             // TMA producer
             gpch::tc::prefetch_tmap(&tm_hi);
             if (split) gpch::tc::prefetch_tmap(&tm_lo);
-            if constexpr (RECT) {
+            if constexpr (rect) {
                 gpch::tc::prefetch_tmap(&tmb_hi);
                 if (split) gpch::tc::prefetch_tmap(&tmb_lo);
             }
@@ -204,12 +206,12 @@ __global__ void __maxnreg__(112)
         // scaled binary16 operands: the products carry 2^(2e); undo it exactly
         const float unscale =
             scale ? __int_as_float((127 - (rect ? scale[1] + scale_b[1] : 2 * scale[1])) << 23) : 1.0f;
-        if (prefetch_c && !rect) {
+        if (prefetch_c && sub) {
             // pull the C tile's columns into L2 while the first MMAs run
             const int64_t rows = (m - i0 < BM) ? m - i0 : BM;
             const uint32_t bytes = (uint32_t)(rows & ~int64_t(3)) * 4u;
             const int64_t col = c0 + (warp - 2) * 32 + lane;
-            if (col < m && bytes > 0)
+            if (col < (rect ? ncol : m) && bytes > 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(C + i0 + col * ldc), "r"(bytes)
                              : "memory");
         }
@@ -221,7 +223,7 @@ __global__ void __maxnreg__(112)
             const bool last = p == np - 1;
             float *crow = C + row + c0 * ldc;
             float cv[32];
-            if (last && !rect) {
+            if (last && sub) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) cv[j] = (j < jn) ? crow[(int64_t)j * ldc] : 0.0f;
             }
@@ -237,7 +239,7 @@ __global__ void __maxnreg__(112)
                 float *cb = C + row + (c0 + cc * 32) * ldc;
                 // keep the column addresses from living across the loops
                 asm volatile("" : "+l"(cb));
-                if (last && cc > 0 && !rect) {
+                if (last && cc > 0 && sub) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) cv[j] = (cc * 32 + j < jn) ? cb[(int64_t)j * ldc] : 0.0f;
                 }
@@ -263,7 +265,7 @@ __global__ void __maxnreg__(112)
                     continue;
                 }
                 asm volatile("" : "+l"(cb));
-                if constexpr (RECT) {
+                if constexpr (!sub) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         v[j] *= unscale;
@@ -837,7 +839,7 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, k_off + kp, buf.ld, f16));
     static bool attr_done = false;
     if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         attr_done = true;
     }
     auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
@@ -849,7 +851,7 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
     // the C-tile prefetch needs 16-byte aligned columns
     const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-    syrk_tc_kernel<false><<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0,
+    syrk_tc_kernel<0><<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0,
                                                                tk1, buf.err, prefetch_c, f16 ? 1 : 0,
                                                                f16 ? buf.scale : nullptr, (int)k_off, ncol,
                                                                panel_k > 0 ? panel_k : kp, nullptr, nullptr,
@@ -862,10 +864,14 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
 // pb (rows 0 .. m-1, K columns 0 .. k-1, row stride pb.ld, scale word
 // pb.scale), Q in qb likewise (nq rows); nq <= k.  One CTA per 128 x 128
 // tile of C.  out (optional): C's own split-f16 copy, row r and column c at
-// out->hi[r * out->ld + out_col + c], scaled by out->scale.
+// out->hi[r * out->ld + out_col + c], scaled by out->scale.  subtract:
+// C -= P Q^T instead (no copy is written).  acc_k > 0 (dividing the padded
+// k): products summed in the tensor-core accumulator per piece of acc_k
+// before the FP32 running sum.
 gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, float *C, int64_t ldc,
                                  const LowprecBuffers &pb, const LowprecBuffers &qb, cudaStream_t st,
-                                 const LowprecBuffers *out = nullptr, int64_t out_col = 0)
+                                 const LowprecBuffers *out = nullptr, int64_t out_col = 0, bool subtract = false,
+                                 int acc_k = 0)
 {
     if (m <= 0 || nq <= 0) return GPCH_OK;
     const int kp = (k + BK - 1) / BK * BK;
@@ -876,12 +882,16 @@ gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, fl
     GPCH_CHECK(make_panel_map(ctx, &qlo, qb.lo, nq, kp, qb.ld, true));
     static bool attr_done = false;
     if (!attr_done) {
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         attr_done = true;
     }
     const int64_t tr = (m + BM - 1) / BM, tc = (nq + BN - 1) / BN;
-    syrk_tc_kernel<true><<<(unsigned)(tr * tc), TC_THREADS, TC_SMEM, st>>>(phi, plo, qhi, qlo, m, kp, 1, C, ldc, 0, tc,
-                                                                   pb.err, 0, 1, pb.scale, 0, nq, kp, qb.scale,
+    auto kern = subtract ? syrk_tc_kernel<2> : syrk_tc_kernel<1>;
+    const int prefetch_c = (subtract && (uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
+    kern<<<(unsigned)(tr * tc), TC_THREADS, TC_SMEM, st>>>(phi, plo, qhi, qlo, m, kp, 1, C, ldc, 0, tc,
+                                                                   pb.err, prefetch_c, 1, pb.scale, 0, nq,
+                                                                   (acc_k > 0 && kp % acc_k == 0) ? acc_k : kp, qb.scale,
                                                                    out ? reinterpret_cast<__half *>(out->hi) + out_col
                                                                        : nullptr,
                                                                    out ? reinterpret_cast<__half *>(out->lo) + out_col
@@ -1003,11 +1013,13 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)PN_SMEM));
     cudaEvent_t ev_conv = ctx->aux_ev[0], ev_left = ctx->aux_ev[1], ev_start = ctx->aux_ev[2],
-                ev_done = ctx->aux_ev[3];
-    bool left_pending = false;
+                ev_done = ctx->aux_ev[3], ev_side = ctx->aux_ev[4], ev_pan1 = ctx->aux_ev[5];
+    cudaStream_t sc = ctx->side;
+    bool left_pending = false, side_pending = false;
     GPCH_CUDA(ctx, cudaEventRecord(ev_start, caller));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
+    GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_start, 0));
     const int64_t blk_cols = (tile + BN - 1) / BN;   // tile columns of one block column
     const int64_t LEFT_K = 4 * (int64_t)tile;         // K columns (whole panels) per launch of the long pass
     // products summed in the tensor-core accumulator before they are added
@@ -1027,6 +1039,14 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         float *Pan = W + (j0 + nj) + j0 * ldw;
+        // the panel's rows below block column J's... the side stream's part
+        // of step J-1 (block column J below its tile) must be complete
+        if (side_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_side, 0));
+        side_pending = false;
+        // tensor-core panel with look-ahead: rows [0, m1) of the panel (the
+        // rows of block column J+1) on the critical stream, the others on
+        // the side stream
+        const int64_t m1 = tc_panel ? (m < nj ? m : nj) : m, mr = m - m1;
         {
             // step 2 in FP32 against FP32 inverses of the tile's 64 x 64
             // diagonal blocks (computed from the FP64 factor)
@@ -1054,8 +1074,8 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                     w.Tid, tile, nj, (int)nj, kpj, reinterpret_cast<__half *>(w.thi),
                     reinterpret_cast<__half *>(w.tlo), w.tscale, tile);
                 GPCH_LAUNCH_CHECK(ctx);
-                panel_to_f16_kernel<<<dim3((unsigned)((m + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
-                    Pan, ldw, m, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), reinterpret_cast<__half *>(w.plo),
+                panel_to_f16_kernel<<<dim3((unsigned)((m1 + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
+                    Pan, ldw, m1, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), reinterpret_cast<__half *>(w.plo),
                     w.pscale, tile);
                 GPCH_LAUNCH_CHECK(ctx);
                 LowprecBuffers pbuf = all, qbuf = all;
@@ -1070,7 +1090,37 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                 LowprecBuffers obuf = all;   // the panel's 16-bit copy, written by the product
                 obuf.hi = all.hi + (j0 + nj) * kpa;
                 obuf.lo = all.lo + (j0 + nj) * kpa;
-                GPCH_CHECK(panel_gemm_tc_launch(ctx, m, nj, (int)nj, Pan, ldw, pbuf, qbuf, st, &obuf, j0));
+                GPCH_CHECK(panel_gemm_tc_launch(ctx, m1, nj, (int)nj, Pan, ldw, pbuf, qbuf, st, &obuf, j0));
+                if (mr > 0) {
+                    // side stream: the other rows of the panel, then their
+                    // product with block column J+1 (after the second
+                    // stream's update of that block column, which writes
+                    // the same entries)
+                    GPCH_CUDA(ctx, cudaEventRecord(ev_pan1, st));
+                    GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_pan1, 0));
+                    PhaseScope phs(ctx, GPCH_PHASE_PANEL, sc, (double)mr * nj * nj);
+                    panel_to_f16_kernel<<<dim3((unsigned)((mr + 63) / 64), (unsigned)(kpj / 64)), 256, 0, sc>>>(
+                        Pan + m1, ldw, mr, (int)nj, kpj, reinterpret_cast<__half *>(w.phi) + m1 * tile,
+                        reinterpret_cast<__half *>(w.plo) + m1 * tile, w.pscale, tile);
+                    GPCH_LAUNCH_CHECK(ctx);
+                    LowprecBuffers pr = pbuf, orr = obuf;
+                    pr.hi = w.phi + m1 * tile;
+                    pr.lo = w.plo + m1 * tile;
+                    orr.hi = obuf.hi + m1 * kpa;
+                    orr.lo = obuf.lo + m1 * kpa;
+                    GPCH_CHECK(panel_gemm_tc_launch(ctx, mr, nj, (int)nj, Pan + m1, ldw, pr, qbuf, sc, &orr, j0));
+                    if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_left, 0));
+                    // block column J+1, rows below its tile, -= (panel rows m1..) (panel rows 0..m1)^T
+                    LowprecBuffers rb = all, cb = all;
+                    rb.hi = all.hi + (j0 + nj + m1) * kpa + j0;
+                    rb.lo = all.lo + (j0 + nj + m1) * kpa + j0;
+                    cb.hi = all.hi + (j0 + nj) * kpa + j0;
+                    cb.lo = all.lo + (j0 + nj) * kpa + j0;
+                    GPCH_CHECK(panel_gemm_tc_launch(ctx, mr, m1, (int)nj, W + (j0 + nj + m1) + (j0 + nj) * ldw, ldw,
+                                                    rb, cb, sc, nullptr, 0, true, acc_k));
+                    GPCH_CUDA(ctx, cudaEventRecord(ev_side, sc));
+                    side_pending = true;
+                }
             } else if (panel_fused && nj <= PN_MAXK) {
                 panel_trsm_f32_kernel<<<(unsigned)((m + PN_ROWS - 1) / PN_ROWS), PN_THREADS, PN_SMEM, st>>>(
                     Pan, ldw, m, (int)nj, Wjj, ldw, w.Linv32, w.info);
@@ -1090,11 +1140,13 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         pb.hi = all.hi + (j0 + nj) * kpa;
         pb.lo = all.lo + (j0 + nj) * kpa;
         if (!tc_panel) GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, pb, j0, st));
-        GPCH_CUDA(ctx, cudaEventRecord(ev_conv, st));
-        // block column J+1 <- panel J, after it received panels 0..J-1
+        GPCH_CUDA(ctx, cudaEventRecord(ev_conv, side_pending ? sc : st));
+        // block column J+1 <- panel J, after it received panels 0..J-1 (with
+        // the look-ahead only its diagonal tile here; the side stream does
+        // the rows below)
         if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_left, 0));
         left_pending = false;
-        GPCH_CHECK(syrk_tc_launch(ctx, m, (int)nj, j0, W + (j0 + nj) * (1 + ldw), ldw, prec, pb, 0, blk_cols, st,
+        GPCH_CHECK(syrk_tc_launch(ctx, m1, (int)nj, j0, W + (j0 + nj) * (1 + ldw), ldw, prec, pb, 0, blk_cols, st,
                                   tile, acc_k));
         // block column J+2 <- panels 0..J on the second stream
         if (m > tile) {
@@ -1113,6 +1165,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         }
     }
     if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_left, 0));
+    if (side_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_side, 0));
     GPCH_CUDA(ctx, cudaEventRecord(ev_done, st));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_done, 0));
     return GPCH_OK;
