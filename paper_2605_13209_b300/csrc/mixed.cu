@@ -8,7 +8,7 @@
 //           inverses of the diagonal tile's 64 x 64 blocks;
 //   step 3  the trailing update A_ik -= A_ij A_kj^T runs on the tensor cores:
 //           the panel is rounded to bf16 (or split into a bf16 head and a
-//           bf16 tail) in a K-major copy, TMA streams 128 x 64 tiles of it
+//           bf16 tail) in a K-major copy, TMA streams 128 x 16 tiles of it
 //           into shared memory, tcgen05.mma accumulates 128 x 128 FP32 tiles
 //           in TMEM, and the epilogue subtracts them from the FP32 matrix.
 // Mixed precision is the paper's stated future work (Sec. 5); the factor's
@@ -27,21 +27,31 @@ using gpch::LEAF;
 
 constexpr int BM = 128;            // rows of an output tile (TMEM lanes)
 constexpr int BN = 128;            // columns of an output tile (TMEM columns)
-constexpr int BK = 64;             // K per stage: one 128-byte swizzle row of bf16
+constexpr int BK = 64;             // K granularity of the 16-bit panel copies (zero-padded to it)
+constexpr int BOX_K = 64;          // 16-bit values per box row: one 128-byte swizzle row
 constexpr int STAGES = 3;
 constexpr int TC_THREADS = 192;   // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
-constexpr uint32_t TILE_A_BYTES = BM * BK * 2;
-constexpr uint32_t TILE_B_BYTES = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = TILE_A_BYTES + TILE_B_BYTES;
+constexpr uint32_t BOX_BYTES = BM * BOX_K * 2;   // one 128-row box (BM == BN)
+constexpr uint32_t STAGE_BYTES = 2 * BOX_BYTES;  // row tile and column tile
 constexpr size_t TC_SMEM = 1024 + STAGES * STAGE_BYTES + 256;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 constexpr uint32_t TMEM_COLS = 2 * BN;   // accumulator + running sum (two CTAs fill an SM's TMEM)
 
+// Layout of the 16-bit panel copies.  A copy is K-major: row r holds the
+// K columns of panel row r.  With one product (BF16) K column c sits at
+// position c of the row.  Split copies interleave head and tail in chunks
+// of 32 columns: the head of column c at (c / 32) * 64 + c % 32 and its tail
+// 32 positions later, so that one 128-byte box row carries the head and the
+// tail of 32 columns and a single TMA box feeds all three products.  Row
+// strides are multiples of 64 positions; column offsets used are multiples
+// of 32 (their position is 2c).
+__host__ __device__ constexpr int64_t kpos(bool split, int64_t c) { return split ? 2 * c : c; }
+
 // Trailing update C_lower -= P P^T on tensor cores.  P is the m x kp panel,
-// 16-bit, K-major, described by tm_hi (and its tail by tm_lo when split);
-// its K columns start at column k_off of the maps (a multiple of 64).
-// split = 0: one product head*head^T; split = 1: head*head^T + head*tail^T
-// + tail*head^T.  Only columns below ncol are written.
+// a 16-bit copy described by tm_a (rows of the copy; K positions from
+// kpos(k_off), k_off a multiple of 64).  split = 0: one product
+// head*head^T; split = 1: head*head^T + head*tail^T + tail*head^T.  Only
+// columns below ncol are written.
 //
 // The K range is a sequence of panels of panel_k columns (panel_k divides
 // kp).  Each panel's product is summed on its own in the TMEM accumulator
@@ -55,32 +65,34 @@ constexpr uint32_t TMEM_COLS = 2 * BN;   // accumulator + running sum (two CTAs 
 // lane 0 issues the TMA loads, warp 1 lane 0 the MMAs (warp 1 owns the
 // TMEM allocation), warps 2-5 run the epilogue (warp w: tile rows
 // 32 (w % 4) .. +31, its TMEM lanes).  One CTA per lower 128 x 128 tile of
-// C.  err: device status word, nonzero if a bounded wait gave up.
+// C.  A pipeline stage holds one 128 x 64 box of the row tile's copy and
+// one of the column tile's (a diagonal tile loads its rows once): 32 K
+// columns (head and tail) when split, 64 otherwise.  err: device status
+// word, nonzero if a bounded wait gave up.
 //
 // MODE 0 is the update above.  MODE 1 is the product C = P Q^T
-// (overwrite), MODE 2 the update C -= P Q^T, both over a rectangle:
-// P (rows of tm_hi / tm_lo) is m x kp, Q (rows of tmb_hi / tmb_lo) is
+// (overwrite), MODE 2 the update C -= P Q^T, both over a rectangle of
+// split-f16 operands: P (rows of tm_a) is m x kp, Q (rows of tm_b) is
 // ncol x kp, every tile of the m x ncol rectangle (tile columns tk0 .. tk1-1)
-// is computed, and binary16 operands carry the scales 2^scale[1] (P) and
-// 2^scale_b[1] (Q).  MODE 0 reads both operands through tm_hi / tm_lo (the
-// tmb maps are not used).  With ohi != nullptr (MODE 1 only) the result is
-// also written as a binary16 head and tail scaled by 2^oscale[1]: row r,
-// column c at ohi[r * ldo + c] (the 16-bit copy the later updates read;
-// ohi and ldo must make every row 16-byte aligned).
+// is computed, and the operands carry the scales 2^scale[1] (P) and
+// 2^scale_b[1] (Q).  MODE 0 reads both operands through tm_a (tm_b is not
+// used).  With ohi != nullptr (MODE 1 only) the result is also written as
+// a split-f16 copy scaled by 2^oscale[1]: row r, column c at position
+// kpos(true, c) of ohi + r * ldo (the copy the later updates read; ohi and
+// ldo must make every row 16-byte aligned).
 template <int MODE>
 __global__ void __maxnreg__(112)
-    syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-                   const __grid_constant__ CUtensorMap tmb_hi, const __grid_constant__ CUtensorMap tmb_lo, int64_t m,
+    syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, int64_t m,
                    int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
                    int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k,
-                   const int *scale_b, __half *ohi, __half *olo, int64_t ldo, const int *oscale)
+                   const int *scale_b, __half *ohi, int64_t ldo, const int *oscale)
 {
     constexpr bool rect = MODE != 0;   // rectangle of P Q^T
     constexpr bool sub = MODE != 1;    // C -= (else C = )
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * TILE_A_BYTES;
+    // stage s: the row tile's box at smem + s * STAGE_BYTES, the column
+    // tile's BOX_BYTES after it
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
@@ -110,6 +122,9 @@ __global__ void __maxnreg__(112)
         tk = tk0 + (t - tri) % nc;
     }
     const int64_t i0 = ti * BM, c0 = tk * BN;
+    // a diagonal tile of the triangle multiplies its rows by themselves:
+    // they are loaded once and serve as both operands
+    const bool diag = !rect && ti == tk;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -128,20 +143,18 @@ __global__ void __maxnreg__(112)
     gpch::tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int nkp = panel_k / BK;                // k-blocks per panel
+    const int kstage = split ? BOX_K / 2 : BOX_K;   // K columns per stage
+    const int spp = panel_k / kstage;            // stages per panel
     const int np = kp / panel_k;                 // panels
-    const int nprod = split ? 3 : 1;
-    const int NK = np * nprod * nkp;             // k-block steps, panel by panel, product by product
+    const int NK = np * spp;                     // stages, panel by panel
 
     if (warp == 0) {
         if (lane == 0) {
             // TMA producer
-            gpch::tc::prefetch_tmap(&tm_hi);
-            if (split) gpch::tc::prefetch_tmap(&tm_lo);
-            if constexpr (rect) {
-                gpch::tc::prefetch_tmap(&tmb_hi);
-                if (split) gpch::tc::prefetch_tmap(&tmb_lo);
-            }
+            gpch::tc::prefetch_tmap(&tm_a);
+            if constexpr (rect) gpch::tc::prefetch_tmap(&tm_b);
+            const CUtensorMap *mb = rect ? &tm_b : &tm_a;
+            const uint32_t bytes = diag ? BOX_BYTES : STAGE_BYTES;
             int issued = 0;
             for (int kc = 0; kc < NK; ++kc) {
                 const int s = kc % STAGES;
@@ -149,13 +162,11 @@ __global__ void __maxnreg__(112)
                     atomicExch(err, 1);
                     break;
                 }
-                const int p = kc / (nprod * nkp), prod = (kc / nkp) % nprod;
-                const int kk = p * nkp + kc % nkp;
-                const CUtensorMap *ma = (prod == 2) ? &tm_lo : &tm_hi;
-                const CUtensorMap *mb = rect ? ((prod == 1) ? &tmb_lo : &tmb_hi) : ((prod == 1) ? &tm_lo : &tm_hi);
-                gpch::tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                gpch::tc::tma_load_2d(sA + s * TILE_A_BYTES, ma, &full[s], k_off + kk * BK, (int32_t)i0);
-                gpch::tc::tma_load_2d(sB + s * TILE_B_BYTES, mb, &full[s], k_off + kk * BK, (int32_t)c0);
+                const int32_t x = (int32_t)kpos(split, k_off + (kc / spp) * panel_k + (kc % spp) * kstage);
+                uint8_t *st = smem + s * STAGE_BYTES;
+                gpch::tc::mbar_arrive_expect_tx(&full[s], bytes);
+                gpch::tc::tma_load_2d(st, &tm_a, &full[s], x, (int32_t)i0);
+                if (!diag) gpch::tc::tma_load_2d(st + BOX_BYTES, mb, &full[s], x, (int32_t)c0);
                 ++issued;
             }
             // Every copy this thread started has landed before the CTA may
@@ -179,7 +190,7 @@ __global__ void __maxnreg__(112)
                 }
                 gpch::tc::tc_fence_after();
                 const uint32_t acc = tmem;
-                for (int q = 0; q < nprod * nkp; ++q, ++kc) {
+                for (int q = 0; q < spp; ++q, ++kc) {
                     const int s = kc % STAGES;
                     if (!gpch::tc::mbar_wait(&full[s], (kc / STAGES) & 1, SPIN_LIMIT)) {
                         atomicExch(err, 2);
@@ -187,11 +198,24 @@ __global__ void __maxnreg__(112)
                         break;
                     }
                     gpch::tc::tc_fence_after();
-                    const uint64_t ad = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sA + s * TILE_A_BYTES));
-                    const uint64_t bd = gpch::tc::sdesc_sw128(gpch::tc::smem_u32(sB + s * TILE_B_BYTES));
+                    const uint32_t sa = gpch::tc::smem_u32(smem + s * STAGE_BYTES);
+                    const uint64_t a = gpch::tc::sdesc_sw128(sa);
+                    const uint64_t b = diag ? a : gpch::tc::sdesc_sw128(sa + BOX_BYTES);
+                    // a K step of 16 values advances the start address by 32
+                    // bytes (2 in the descriptor); the tail of a split box
+                    // row starts 64 bytes (4) after its head
+                    if (split) {
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        gpch::tc::mma_bf16(acc, ad + 2 * k, bd + 2 * k, idesc, (q | k) != 0 ? 1u : 0u);
+                        for (int k = 0; k < 2; ++k) {
+                            gpch::tc::mma_bf16(acc, a + 2 * k, b + 2 * k, idesc, (q | k) != 0 ? 1u : 0u);
+                            gpch::tc::mma_bf16(acc, a + 2 * k, b + 4 + 2 * k, idesc, 1u);
+                            gpch::tc::mma_bf16(acc, a + 4 + 2 * k, b + 2 * k, idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            gpch::tc::mma_bf16(acc, a + 2 * k, b + 2 * k, idesc, (q | k) != 0 ? 1u : 0u);
+                    }
                     gpch::tc::mma_commit(&empty[s]);
                 }
                 if (ok) gpch::tc::mma_commit(&tfull[0]);
@@ -275,8 +299,8 @@ __global__ void __maxnreg__(112)
                         // 16-byte stores: each lane writes its row's 32 values
                         // (64 bytes per copy); columns at or past jn are zero
                         const float osc = __int_as_float((127 + oscale[1]) << 23);
-                        uint4 *oh = reinterpret_cast<uint4 *>(ohi + row * ldo + c0 + cc * 32);
-                        uint4 *ol = reinterpret_cast<uint4 *>(olo + row * ldo + c0 + cc * 32);
+                        uint4 *oh = reinterpret_cast<uint4 *>(ohi + row * ldo + kpos(true, c0 + cc * 32));
+                        uint4 *ol = oh + 4;   // the tail, 32 positions later
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             uint32_t hw[4], lw[4];
@@ -311,12 +335,12 @@ __global__ void __maxnreg__(112)
     }
 }
 
-// FP32 column-major panel (m x k, ld ldp) -> bf16 K-major head (and tail)
-// buffers of width kp (zero-padded beyond k).  64 x 64 tiles through shared
-// memory so that both the read and the write are coalesced.
+// FP32 column-major panel (m x k, ld ldp) -> bf16 K-major copy of width kp
+// (zero-padded beyond k), row r at H + r * ldo: the head alone, or (split)
+// head and tail interleaved as kpos() describes.  64 x 64 tiles through
+// shared memory so that both the read and the write are coalesced.
 __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restrict__ P, int64_t ldp, int64_t m,
-                                                            int k, int kp, __nv_bfloat16 *Hi, __nv_bfloat16 *Lo,
-                                                            int64_t ldo)
+                                                            int k, int kp, __nv_bfloat16 *H, int split, int64_t ldo)
 {
     __shared__ float tile[64][65];
     const int64_t r0 = (int64_t)blockIdx.x * 64;
@@ -331,8 +355,13 @@ __global__ void __launch_bounds__(256) panel_to_bf16_kernel(const float *__restr
         if (r0 + r < m && k0 + c < kp) {
             const float v = tile[r][c];
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            Hi[(r0 + r) * ldo + k0 + c] = h;
-            if (Lo) Lo[(r0 + r) * ldo + k0 + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+            if (split) {
+                __nv_bfloat16 *o = H + (r0 + r) * ldo + 2 * k0 + (c >> 5) * 64 + (c & 31);
+                o[0] = h;
+                o[32] = __float2bfloat16_rn(v - __bfloat162float(h));
+            } else {
+                H[(r0 + r) * ldo + k0 + c] = h;
+            }
         }
     }
 }
@@ -364,13 +393,14 @@ __global__ void __launch_bounds__(256) panel_absmax_kernel(const float *__restri
     if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(mx));
 }
 
-// FP32 panel -> binary16 K-major head and tail of the panel scaled by 2^e
+// FP32 panel -> split binary16 K-major copy (head and tail interleaved as
+// kpos() describes, row r at H + r * ldo) of the panel scaled by 2^e
 // (scale[0]: the panel's largest |entry| as FP32 bits; block (0, 0) writes e
 // to scale[1] for the update's epilogue).  The scaling is exact, the head is
 // the round-to-nearest binary16 value and the tail that of the (exact)
 // remainder.
 __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restrict__ P, int64_t ldp, int64_t m, int k,
-                                                           int kp, __half *Hi, __half *Lo, int *scale, int64_t ldo)
+                                                           int kp, __half *H, int *scale, int64_t ldo)
 {
     __shared__ float tile[64][65];
     const int64_t r0 = (int64_t)blockIdx.x * 64;
@@ -388,8 +418,9 @@ __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restri
         if (r0 + r < m && k0 + c < kp) {
             const float v = tile[r][c] * sc;
             const __half h = __float2half_rn(v);
-            Hi[(r0 + r) * ldo + k0 + c] = h;
-            Lo[(r0 + r) * ldo + k0 + c] = __float2half_rn(v - __half2float(h));
+            __half *o = H + (r0 + r) * ldo + 2 * k0 + (c >> 5) * 64 + (c & 31);
+            o[0] = h;
+            o[32] = __float2half_rn(v - __half2float(h));
         }
     }
 }
@@ -765,17 +796,18 @@ __global__ void tile_f64_to_f32(int64_t nb, const double *__restrict__ D, int64_
     for (int64_t i = j + threadIdx.x; i < nb; i += blockDim.x) W[i + j * ldw] = (float)D[i + j * ldd];
 }
 
-// Tensor map over a K-major 16-bit panel of m rows and kcols columns with
-// row stride ld elements (kcols and ld multiples of 64, so every TMA x
-// coordinate used is a multiple of 64 elements).
-gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int64_t kcols, int64_t ld,
+// Tensor map over a K-major 16-bit panel copy of m rows, `width` positions
+// per row (kpos() of the K columns used) and row stride ld positions (both
+// multiples of 64): 128-row boxes of BOX_K positions with 128-byte
+// swizzling.  Every TMA x coordinate used is a multiple of 64 positions.
+gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t m, int64_t width, int64_t ld,
                            bool f16)
 {
     auto enc = gpch::tc::tmap_encoder();
     if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
-    cuuint64_t dims[2] = {(cuuint64_t)kcols, (cuuint64_t)m};
+    cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)m};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t box[2] = {(cuuint32_t)BOX_K, (cuuint32_t)BM};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -785,16 +817,16 @@ gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, in
 }
 
 struct LowprecBuffers {
-    __nv_bfloat16 *hi = nullptr, *lo = nullptr;   // binary16 data under SPLIT_F16
+    __nv_bfloat16 *hi = nullptr;   // the 16-bit copy (binary16 data under SPLIT_F16), layout of kpos()
     int *err = nullptr;
     int *scale = nullptr;   // SPLIT_F16: [0] largest |entry| (FP32 bits), [1] scale exponent
-    int64_t ld = 0;         // row stride (elements) of hi / lo
+    int64_t ld = 0;         // row stride (positions) of hi
     bool fixed_scale = false;   // scale[0] already holds the bound; do not rescan the panel
 };
 
-// Round the FP32 panel P (m x k) to its 16-bit K-major head/tail copies:
-// row i, column c goes to hi/lo[i * buf.ld + col0 + c] (zero-padded up to a
-// multiple of 64 columns).
+// Round the FP32 panel P (m x k) to its 16-bit K-major copy: row i, K
+// column col0 + c at position kpos(col0 + c) of hi + i * buf.ld
+// (zero-padded up to a multiple of 64 columns; col0 a multiple of 64).
 gpch_status panel_convert(gpch_ctx *ctx, int64_t m, int k, const float *P, int64_t ldp, int prec,
                           const LowprecBuffers &buf, int64_t col0, cudaStream_t st)
 {
@@ -806,20 +838,20 @@ gpch_status panel_convert(gpch_ctx *ctx, int64_t m, int k, const float *P, int64
             panel_absmax_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, reinterpret_cast<unsigned *>(buf.scale));
             GPCH_LAUNCH_CHECK(ctx);
         }
-        panel_to_f16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, reinterpret_cast<__half *>(buf.hi) + col0,
-                                                  reinterpret_cast<__half *>(buf.lo) + col0, buf.scale, buf.ld);
+        panel_to_f16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, reinterpret_cast<__half *>(buf.hi) + 2 * col0,
+                                                  buf.scale, buf.ld);
         GPCH_LAUNCH_CHECK(ctx);
         return GPCH_OK;
     }
-    panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi + col0,
-                                               prec == GPCH_PREC_SPLIT_BF16 ? buf.lo + col0 : nullptr, buf.ld);
+    const bool split = prec == GPCH_PREC_SPLIT_BF16;
+    panel_to_bf16_kernel<<<grid, 256, 0, st>>>(P, ldp, m, k, kp, buf.hi + kpos(split, col0), split ? 1 : 0, buf.ld);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
 
 // C_lower (m x m FP32) -= P P^T on the tile columns [tk0, tk1) of the
-// 128 x 128 tile grid (tk1 < 0: to the end), from the 16-bit copies in buf:
-// rows 0 .. m-1 of hi/lo (row stride buf.ld), K columns [k_off, k_off + k);
+// 128 x 128 tile grid (tk1 < 0: to the end), from the 16-bit copy in buf:
+// rows 0 .. m-1 (row stride buf.ld), K columns [k_off, k_off + k);
 // only C columns below ncol (< 0: m) are written.  panel_k > 0: the K range
 // is a sequence of panels of that many columns, subtracted one at a time
 // (panel_k must divide the padded k).
@@ -834,9 +866,8 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     const int64_t T = (m + BM - 1) / BM;
     if (tk1 < 0 || tk1 > T) tk1 = T;
     if (tk0 >= tk1) return GPCH_OK;
-    CUtensorMap mhi, mlo;
-    GPCH_CHECK(make_panel_map(ctx, &mhi, buf.hi, m, k_off + kp, buf.ld, f16));
-    GPCH_CHECK(make_panel_map(ctx, &mlo, split ? buf.lo : buf.hi, m, k_off + kp, buf.ld, f16));
+    CUtensorMap ma;
+    GPCH_CHECK(make_panel_map(ctx, &ma, buf.hi, m, kpos(split, k_off + kp), buf.ld, f16));
     static bool attr_done = false;
     if (!attr_done) {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
@@ -851,11 +882,11 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
     // the C-tile prefetch needs 16-byte aligned columns
     const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-    syrk_tc_kernel<0><<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(mhi, mlo, mhi, mlo, m, kp, split ? 1 : 0, C, ldc, tk0,
-                                                               tk1, buf.err, prefetch_c, f16 ? 1 : 0,
+    syrk_tc_kernel<0><<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(ma, ma, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
+                                                               buf.err, prefetch_c, f16 ? 1 : 0,
                                                                f16 ? buf.scale : nullptr, (int)k_off, ncol,
-                                                               panel_k > 0 ? panel_k : kp, nullptr, nullptr,
-                                                               nullptr, 0, nullptr);
+                                                               panel_k > 0 ? panel_k : kp, nullptr, nullptr, 0,
+                                                               nullptr);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -864,7 +895,8 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
 // pb (rows 0 .. m-1, K columns 0 .. k-1, row stride pb.ld, scale word
 // pb.scale), Q in qb likewise (nq rows); nq <= k.  One CTA per 128 x 128
 // tile of C.  out (optional): C's own split-f16 copy, row r and column c at
-// out->hi[r * out->ld + out_col + c], scaled by out->scale.  subtract:
+// position kpos(out_col + c) of out->hi + r * out->ld (out_col a multiple of
+// 32), scaled by out->scale.  subtract:
 // C -= P Q^T instead (no copy is written).  acc_k > 0 (dividing the padded
 // k): products summed in the tensor-core accumulator per piece of acc_k
 // before the FP32 running sum.
@@ -875,11 +907,9 @@ gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, fl
 {
     if (m <= 0 || nq <= 0) return GPCH_OK;
     const int kp = (k + BK - 1) / BK * BK;
-    CUtensorMap phi, plo, qhi, qlo;
-    GPCH_CHECK(make_panel_map(ctx, &phi, pb.hi, m, kp, pb.ld, true));
-    GPCH_CHECK(make_panel_map(ctx, &plo, pb.lo, m, kp, pb.ld, true));
-    GPCH_CHECK(make_panel_map(ctx, &qhi, qb.hi, nq, kp, qb.ld, true));
-    GPCH_CHECK(make_panel_map(ctx, &qlo, qb.lo, nq, kp, qb.ld, true));
+    CUtensorMap mp, mq;
+    GPCH_CHECK(make_panel_map(ctx, &mp, pb.hi, m, kpos(true, kp), pb.ld, true));
+    GPCH_CHECK(make_panel_map(ctx, &mq, qb.hi, nq, kpos(true, kp), qb.ld, true));
     static bool attr_done = false;
     if (!attr_done) {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
@@ -889,14 +919,11 @@ gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, fl
     const int64_t tr = (m + BM - 1) / BM, tc = (nq + BN - 1) / BN;
     auto kern = subtract ? syrk_tc_kernel<2> : syrk_tc_kernel<1>;
     const int prefetch_c = (subtract && (uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-    kern<<<(unsigned)(tr * tc), TC_THREADS, TC_SMEM, st>>>(phi, plo, qhi, qlo, m, kp, 1, C, ldc, 0, tc,
-                                                                   pb.err, prefetch_c, 1, pb.scale, 0, nq,
-                                                                   (acc_k > 0 && kp % acc_k == 0) ? acc_k : kp, qb.scale,
-                                                                   out ? reinterpret_cast<__half *>(out->hi) + out_col
-                                                                       : nullptr,
-                                                                   out ? reinterpret_cast<__half *>(out->lo) + out_col
-                                                                       : nullptr,
-                                                                   out ? out->ld : 0, out ? out->scale : nullptr);
+    kern<<<(unsigned)(tr * tc), TC_THREADS, TC_SMEM, st>>>(
+        mp, mq, m, kp, 1, C, ldc, 0, tc, pb.err, prefetch_c, 1, pb.scale, 0, nq,
+        (acc_k > 0 && kp % acc_k == 0) ? acc_k : kp, qb.scale,
+        out ? reinterpret_cast<__half *>(out->hi) + kpos(true, out_col) : nullptr, out ? out->ld : 0,
+        out ? out->scale : nullptr);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -919,13 +946,13 @@ struct MixedWs {
     double *D, *rinv, *Linv;
     float *Linv32;
     int64_t *info;
-    __nv_bfloat16 *hi, *lo;   // 16-bit copies of all panels: row i, K column c at i * kpa + c
+    __nv_bfloat16 *hi;        // 16-bit copies of all panels: row i, K column c at kpos(c) of hi + i * kpos(kpa)
     int *err;
     int *scale;               // SPLIT_F16 scale word of the whole factor
     // step 2 on tensor cores (SPLIT_F16): L_jj^-T, 16-bit copies of its
     // transpose's rows and of the panel before the solve, their scale words
     float *Tid;
-    __nv_bfloat16 *thi, *tlo, *phi, *plo;
+    __nv_bfloat16 *thi, *phi;   // split-f16 copies, row stride 2 * tile
     int *tscale, *pscale;
 };
 
@@ -939,14 +966,11 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
     w.Linv32 = cv.take<float>((size_t)(tile / LEAF) * LEAF * LEAF);
     const int64_t kpa = (n + BK - 1) / BK * BK;
-    w.hi = cv.take<__nv_bfloat16>((size_t)n * kpa);
-    w.lo = cv.take<__nv_bfloat16>((size_t)n * kpa);
+    w.hi = cv.take<__nv_bfloat16>((size_t)n * 2 * kpa);
     w.scale = cv.take<int>(2);
     w.Tid = cv.take<float>((size_t)tile * tile);
-    w.thi = cv.take<__nv_bfloat16>((size_t)tile * tile);
-    w.tlo = cv.take<__nv_bfloat16>((size_t)tile * tile);
-    w.phi = cv.take<__nv_bfloat16>((size_t)n * tile);
-    w.plo = cv.take<__nv_bfloat16>((size_t)n * tile);
+    w.thi = cv.take<__nv_bfloat16>((size_t)tile * 2 * tile);
+    w.phi = cv.take<__nv_bfloat16>((size_t)n * 2 * tile);
     w.tscale = cv.take<int>(2);
     w.pscale = cv.take<int>(2);
     return w;
@@ -969,8 +993,8 @@ size_t mixed_ws_bytes(int64_t n, int tile)
 // that its diagonal tile can be factored next.  Block column J+2 receives
 // the products of all panels 0..J in one long-K pass on the second stream
 // (lowest priority), which runs while the critical stream factors and
-// solves block column J+1.  Every panel's 16-bit copy stays in one n x kpa
-// buffer (row i, K column c at i * kpa + c), so a pass reads the panels it
+// solves block column J+1.  Every panel's 16-bit copy stays in one buffer
+// of n rows (row i, K column c at kpos(c) of row i), so a pass reads the panels it
 // needs as one K range.  Each entry of C is read and written twice (once per
 // stream) instead of once per panel, and the critical stream waits only for
 // the block it needs next.
@@ -988,12 +1012,12 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     GPCH_CUDA(ctx, cudaMemsetAsync(w.err, 0, 4 * sizeof(int), caller));
     const int64_t ncols = (n + tile - 1) / tile;
     const int64_t kpa = (n + BK - 1) / BK * BK;
+    const bool split = prec != GPCH_PREC_BF16;
     LowprecBuffers all;
     all.hi = w.hi;
-    all.lo = w.lo;
     all.err = w.err;
     all.scale = w.scale;
-    all.ld = kpa;
+    all.ld = kpos(split, kpa);
     if (prec == GPCH_PREC_SPLIT_F16) {
         // one scale for every panel, from |L_ij| <= sqrt(max_i W_ii)
         factor_scale_kernel<<<1, 256, 0, caller>>>(n, W, ldw, w.scale, w.pscale);
@@ -1071,25 +1095,20 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                 GPCH_LAUNCH_CHECK(ctx);
                 // rows of L_jj^-1 (stored column-major) become the K-major rows
                 panel_to_f16_kernel<<<dim3((unsigned)((nj + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
-                    w.Tid, tile, nj, (int)nj, kpj, reinterpret_cast<__half *>(w.thi),
-                    reinterpret_cast<__half *>(w.tlo), w.tscale, tile);
+                    w.Tid, tile, nj, (int)nj, kpj, reinterpret_cast<__half *>(w.thi), w.tscale, 2 * tile);
                 GPCH_LAUNCH_CHECK(ctx);
                 panel_to_f16_kernel<<<dim3((unsigned)((m1 + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
-                    Pan, ldw, m1, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), reinterpret_cast<__half *>(w.plo),
-                    w.pscale, tile);
+                    Pan, ldw, m1, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), w.pscale, 2 * tile);
                 GPCH_LAUNCH_CHECK(ctx);
                 LowprecBuffers pbuf = all, qbuf = all;
                 pbuf.hi = w.phi;
-                pbuf.lo = w.plo;
                 pbuf.scale = w.pscale;
-                pbuf.ld = tile;
+                pbuf.ld = 2 * tile;
                 qbuf.hi = w.thi;
-                qbuf.lo = w.tlo;
                 qbuf.scale = w.tscale;
-                qbuf.ld = tile;
+                qbuf.ld = 2 * tile;
                 LowprecBuffers obuf = all;   // the panel's 16-bit copy, written by the product
-                obuf.hi = all.hi + (j0 + nj) * kpa;
-                obuf.lo = all.lo + (j0 + nj) * kpa;
+                obuf.hi = all.hi + (j0 + nj) * all.ld;
                 GPCH_CHECK(panel_gemm_tc_launch(ctx, m1, nj, (int)nj, Pan, ldw, pbuf, qbuf, st, &obuf, j0));
                 if (mr > 0) {
                     // side stream: the other rows of the panel, then their
@@ -1100,22 +1119,18 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                     GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_pan1, 0));
                     PhaseScope phs(ctx, GPCH_PHASE_PANEL, sc, (double)mr * nj * nj);
                     panel_to_f16_kernel<<<dim3((unsigned)((mr + 63) / 64), (unsigned)(kpj / 64)), 256, 0, sc>>>(
-                        Pan + m1, ldw, mr, (int)nj, kpj, reinterpret_cast<__half *>(w.phi) + m1 * tile,
-                        reinterpret_cast<__half *>(w.plo) + m1 * tile, w.pscale, tile);
+                        Pan + m1, ldw, mr, (int)nj, kpj, reinterpret_cast<__half *>(w.phi) + m1 * 2 * tile, w.pscale,
+                        2 * tile);
                     GPCH_LAUNCH_CHECK(ctx);
                     LowprecBuffers pr = pbuf, orr = obuf;
-                    pr.hi = w.phi + m1 * tile;
-                    pr.lo = w.plo + m1 * tile;
-                    orr.hi = obuf.hi + m1 * kpa;
-                    orr.lo = obuf.lo + m1 * kpa;
+                    pr.hi = w.phi + m1 * 2 * tile;
+                    orr.hi = obuf.hi + m1 * all.ld;
                     GPCH_CHECK(panel_gemm_tc_launch(ctx, mr, nj, (int)nj, Pan + m1, ldw, pr, qbuf, sc, &orr, j0));
                     if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_left, 0));
                     // block column J+1, rows below its tile, -= (panel rows m1..) (panel rows 0..m1)^T
                     LowprecBuffers rb = all, cb = all;
-                    rb.hi = all.hi + (j0 + nj + m1) * kpa + j0;
-                    rb.lo = all.lo + (j0 + nj + m1) * kpa + j0;
-                    cb.hi = all.hi + (j0 + nj) * kpa + j0;
-                    cb.lo = all.lo + (j0 + nj) * kpa + j0;
+                    rb.hi = all.hi + (j0 + nj + m1) * all.ld + kpos(true, j0);
+                    cb.hi = all.hi + (j0 + nj) * all.ld + kpos(true, j0);
                     GPCH_CHECK(panel_gemm_tc_launch(ctx, mr, m1, (int)nj, W + (j0 + nj + m1) + (j0 + nj) * ldw, ldw,
                                                     rb, cb, sc, nullptr, 0, true, acc_k));
                     GPCH_CUDA(ctx, cudaEventRecord(ev_side, sc));
@@ -1137,8 +1152,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         }
         // step 3: the panel's 16-bit copy (rows j0 + nj.., K columns j0..)
         LowprecBuffers pb = all;
-        pb.hi = all.hi + (j0 + nj) * kpa;
-        pb.lo = all.lo + (j0 + nj) * kpa;
+        pb.hi = all.hi + (j0 + nj) * all.ld;
         if (!tc_panel) GPCH_CHECK(panel_convert(ctx, m, (int)nj, Pan, ldw, prec, pb, j0, st));
         GPCH_CUDA(ctx, cudaEventRecord(ev_conv, side_pending ? sc : st));
         // block column J+1 <- panel J, after it received panels 0..J-1 (with
@@ -1152,8 +1166,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         if (m > tile) {
             const int64_t r2 = j0 + nj + tile, m2 = n - r2, K = j0 + nj;
             LowprecBuffers qb = all;
-            qb.hi = all.hi + r2 * kpa;
-            qb.lo = all.lo + r2 * kpa;
+            qb.hi = all.hi + r2 * all.ld;
             GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_conv, 0));
             for (int64_t k0 = 0; k0 < K; k0 += LEFT_K) {
                 const int64_t kk = (K - k0 < LEFT_K) ? K - k0 : LEFT_K;
@@ -1197,17 +1210,15 @@ extern "C" gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, co
     const int kp = (int)((k + BK - 1) / BK * BK);
     gpch::Carver dry(nullptr);
     dry.take<int>(4);
-    dry.take<__nv_bfloat16>((size_t)m * kp);
-    dry.take<__nv_bfloat16>((size_t)m * kp);
+    dry.take<__nv_bfloat16>((size_t)m * 2 * kp);
     dry.take<int>(2);
     GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
     gpch::Carver cv(ctx->ws);
     LowprecBuffers buf;
     buf.err = cv.take<int>(4);
-    buf.hi = cv.take<__nv_bfloat16>((size_t)m * kp);
-    buf.lo = cv.take<__nv_bfloat16>((size_t)m * kp);
+    buf.hi = cv.take<__nv_bfloat16>((size_t)m * 2 * kp);
     buf.scale = cv.take<int>(2);
-    buf.ld = kp;
+    buf.ld = kpos(prec != GPCH_PREC_BF16, kp);
     cudaStream_t st = (cudaStream_t)stream;
     GPCH_CUDA(ctx, cudaMemsetAsync(buf.err, 0, 4 * sizeof(int), st));
     GPCH_CHECK(syrk_lowprec_enqueue(ctx, m, (int)k, P, ldp, C, ldc, prec, buf, st));
