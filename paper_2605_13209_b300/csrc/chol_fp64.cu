@@ -24,8 +24,7 @@ __global__ void __launch_bounds__(128) potrf_leaf_kernel(double *A, int64_t lda,
 {
     gpch::pdl_wait();
     gpch::pdl_trigger();
-    if (*info != 0) return;
-    potrf_leaf_pipe<W>(A, lda, nb, rinv, col0, info);
+    potrf_leaf_pipe<W>(A, lda, nb, rinv, col0, info);   // returns at once after an earlier failed pivot
 }
 
 // Width of the leaf factorizations inside a diagonal tile.  A leaf runs on

@@ -422,6 +422,9 @@ __device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *r
     __shared__ double u2v[W];        // u2v[j] = S[j][j-1]^2 (final), left by the bulk for the chain
     __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // an earlier failed pivot stops the chain; the word is read together
+    // with the block and tested once the block is in shared memory
+    const int64_t info0 = *info;
     {
         // all loads of a thread in flight at once
         constexpr int NL = W * W / THREADS;
@@ -437,6 +440,7 @@ __device__ inline void potrf_leaf_pipe(double *A, int64_t lda, int nb, double *r
             S[r][c] = (r < nb && c < nb) ? v[i] : ((r == c) ? 1.0 : 0.0);
         }
     }
+    if (info0 != 0) return;   // the same value in every thread
     if (tid == 0) bad = 0;
     __syncthreads();
     if (warp == 0) {
@@ -531,7 +535,8 @@ __global__ void __launch_bounds__(128) trsm_unit_kernel(double *B, int64_t ldb, 
     __shared__ double Bs[NC][ROWS + 1];
     gpch::pdl_wait();
     gpch::pdl_trigger();
-    if (info && *info != 0) return;
+    // read with the operands, tested before the first barrier
+    const int64_t info0 = info ? *info : 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * ROWS;
 #pragma unroll 8
@@ -545,6 +550,7 @@ __global__ void __launch_bounds__(128) trsm_unit_kernel(double *B, int64_t ldb, 
         const int r = e % ROWS, k = e / ROWS;
         Bs[k][r] = (r0 + r < m && k < nc) ? B[(r0 + r) + (int64_t)k * ldb] : 0.0;
     }
+    if (info0 != 0) return;   // the same value in every thread
     __syncthreads();
     // L' = L diag(rinv) over the lower triangle (positions of leaf_entry;
     // the diagonal and the padding hold zeros, so every product is issued
@@ -653,7 +659,7 @@ __device__ inline void tri_index(int64_t t, int64_t &ti, int64_t &tj)
 template <typename T, bool LOWER, int BT>
 __device__ inline void gemm_nt_minus_body(int64_t m, int64_t nn, int k, const T *__restrict__ A, int64_t lda,
                                           const T *__restrict__ B, int64_t ldb, T *C, int64_t ldc, int64_t ti,
-                                          int64_t tj)
+                                          int64_t tj, bool stop = false)
 {
     constexpr int KC = 32, RT = BT / 16;
     __shared__ T As[KC][BT];
@@ -661,6 +667,20 @@ __device__ inline void gemm_nt_minus_body(int64_t m, int64_t nn, int k, const T 
     const int64_t r0 = ti * BT, c0 = tj * BT;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     T acc[RT][RT] = {};
+    // small tiles (the latency-bound steps inside a diagonal tile) load
+    // their C entries together with the first operands instead of after
+    // the product
+    constexpr bool early_c = BT <= 32;
+    T cold[early_c ? RT : 1][early_c ? RT : 1];
+    if constexpr (early_c) {
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int j = 0; j < RT; ++j) {
+                const int64_t r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
+                cold[i][j] = (r < m && c < nn && (!LOWER || r >= c)) ? C[r + c * ldc] : T(0);
+            }
+    }
     for (int k0 = 0; k0 < k; k0 += KC) {
         for (int e = tid; e < KC * BT; e += blockDim.x) {
             int r = e % BT, kk = e / BT;
@@ -668,6 +688,7 @@ __device__ inline void gemm_nt_minus_body(int64_t m, int64_t nn, int k, const T 
             As[kk][r] = (kin && r0 + r < m) ? A[(r0 + r) + (int64_t)(k0 + kk) * lda] : T(0);
             Bs[kk][r] = (kin && c0 + r < nn) ? B[(c0 + r) + (int64_t)(k0 + kk) * ldb] : T(0);
         }
+        if (stop) return;   // the same value in every thread, before the first barrier
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < KC; ++kk) {
@@ -688,7 +709,12 @@ __device__ inline void gemm_nt_minus_body(int64_t m, int64_t nn, int k, const T 
 #pragma unroll
         for (int j = 0; j < RT; ++j) {
             int64_t r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
-            if (r < m && c < nn && (!LOWER || r >= c)) C[r + c * ldc] -= acc[i][j];
+            if (r < m && c < nn && (!LOWER || r >= c)) {
+                if constexpr (early_c)
+                    C[r + c * ldc] = cold[i][j] - acc[i][j];
+                else
+                    C[r + c * ldc] -= acc[i][j];
+            }
         }
 }
 
@@ -702,7 +728,9 @@ __global__ void __launch_bounds__(256, BT == 16 ? 6 : 3) gemm_nt_minus_kernel(in
 {
     gpch::pdl_wait();
     gpch::pdl_trigger();
-    if (info && *info != 0) return;
+    // an earlier failed pivot stops the kernel: the word is read here and
+    // tested once the first operands are in flight
+    const bool stop = info && *info != 0;
     int64_t ti, tj;
     if (LOWER) {
         tri_index(blockIdx.x, ti, tj);
@@ -710,7 +738,7 @@ __global__ void __launch_bounds__(256, BT == 16 ? 6 : 3) gemm_nt_minus_kernel(in
         ti = blockIdx.x;
         tj = blockIdx.y;
     }
-    gemm_nt_minus_body<T, LOWER, BT>(m, nn, k, A, lda, B, ldb, C, ldc, ti, tj);
+    gemm_nt_minus_body<T, LOWER, BT>(m, nn, k, A, lda, B, ldb, C, ldc, ti, tj, stop);
 }
 
 template <typename T, int ROWS>
