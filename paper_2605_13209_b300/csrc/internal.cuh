@@ -33,7 +33,7 @@ struct gpch_ctx {
     cudaStream_t aux = nullptr;          // low-priority stream for bulk overlapped work
     cudaStream_t crit = nullptr;         // high-priority stream for the critical chain
     cudaStream_t side = nullptr;         // middle priority: work the critical chain needs one step later
-    cudaEvent_t aux_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t aux_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace gpch {

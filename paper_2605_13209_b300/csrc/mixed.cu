@@ -1036,10 +1036,12 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     if (panel_fused)
         GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)PN_SMEM));
-    cudaEvent_t ev_conv = ctx->aux_ev[0], ev_left = ctx->aux_ev[1], ev_start = ctx->aux_ev[2],
-                ev_done = ctx->aux_ev[3], ev_side = ctx->aux_ev[4], ev_pan1 = ctx->aux_ev[5];
+    cudaEvent_t ev_conv = ctx->aux_ev[0], ev_start = ctx->aux_ev[2], ev_done = ctx->aux_ev[3],
+                ev_side = ctx->aux_ev[4], ev_pan1 = ctx->aux_ev[5];
+    // ev_ready[X % 2]: the second stream's passes over block column X are done
+    cudaEvent_t ev_ready[2] = {ctx->aux_ev[1], ctx->aux_ev[6]};
     cudaStream_t sc = ctx->side;
-    bool left_pending = false, side_pending = false;
+    bool side_pending = false;
     GPCH_CUDA(ctx, cudaEventRecord(ev_start, caller));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
@@ -1126,7 +1128,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                     pr.hi = w.phi + m1 * 2 * tile;
                     orr.hi = obuf.hi + m1 * all.ld;
                     GPCH_CHECK(panel_gemm_tc_launch(ctx, mr, nj, (int)nj, Pan + m1, ldw, pr, qbuf, sc, &orr, j0));
-                    if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_left, 0));
+                    if (J >= 1) GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_ready[(J + 1) % 2], 0));
                     // block column J+1, rows below its tile, -= (panel rows m1..) (panel rows 0..m1)^T
                     LowprecBuffers rb = all, cb = all;
                     rb.hi = all.hi + (j0 + nj + m1) * all.ld + kpos(true, j0);
@@ -1158,26 +1160,35 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         // block column J+1 <- panel J, after it received panels 0..J-1 (with
         // the look-ahead only its diagonal tile here; the side stream does
         // the rows below)
-        if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_left, 0));
-        left_pending = false;
+        if (J >= 1) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_ready[(J + 1) % 2], 0));
         GPCH_CHECK(syrk_tc_launch(ctx, m1, (int)nj, j0, W + (j0 + nj) * (1 + ldw), ldw, prec, pb, 0, blk_cols, st,
                                   tile, acc_k));
-        // block column J+2 <- panels 0..J on the second stream
+        // second stream, two block columns ahead of the critical stream:
+        // block column J+2 <- panel J (it already has panels 0..J-1), then
+        // block column J+3 <- panels 0..J in one long-K pass
         if (m > tile) {
-            const int64_t r2 = j0 + nj + tile, m2 = n - r2, K = j0 + nj;
+            GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_conv, 0));
+            const int64_t r2 = j0 + nj + tile, m2 = n - r2;
             LowprecBuffers qb = all;
             qb.hi = all.hi + r2 * all.ld;
-            GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_conv, 0));
-            for (int64_t k0 = 0; k0 < K; k0 += LEFT_K) {
-                const int64_t kk = (K - k0 < LEFT_K) ? K - k0 : LEFT_K;
-                GPCH_CHECK(syrk_tc_launch(ctx, m2, (int)kk, k0, W + r2 * (1 + ldw), ldw, prec, qb, 0, blk_cols, sb,
-                                          tile, acc_k));
+            GPCH_CHECK(syrk_tc_launch(ctx, m2, (int)nj, j0, W + r2 * (1 + ldw), ldw, prec, qb, 0, blk_cols, sb, tile,
+                                      acc_k));
+            GPCH_CUDA(ctx, cudaEventRecord(ev_ready[(J + 2) % 2], sb));
+            if (m > 2 * tile) {
+                const int64_t r3 = r2 + tile, m3 = n - r3, K = j0 + nj;
+                LowprecBuffers qb3 = all;
+                qb3.hi = all.hi + r3 * all.ld;
+                for (int64_t k0 = 0; k0 < K; k0 += LEFT_K) {
+                    const int64_t kk = (K - k0 < LEFT_K) ? K - k0 : LEFT_K;
+                    GPCH_CHECK(syrk_tc_launch(ctx, m3, (int)kk, k0, W + r3 * (1 + ldw), ldw, prec, qb3, 0, blk_cols,
+                                              sb, tile, acc_k));
+                }
             }
-            GPCH_CUDA(ctx, cudaEventRecord(ev_left, sb));
-            left_pending = true;
         }
     }
-    if (left_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_left, 0));
+    // the second stream's last pass (and the side stream) before the caller
+    GPCH_CUDA(ctx, cudaEventRecord(ev_ready[0], sb));
+    GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_ready[0], 0));
     if (side_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_side, 0));
     GPCH_CUDA(ctx, cudaEventRecord(ev_done, st));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_done, 0));
