@@ -635,7 +635,7 @@ struct RefineResult {
 // PCG on one group of <= 16 right-hand sides.  L: FP32 factor (ldl).
 gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const float *L, int64_t ldl,
                       const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double bwd_tol, int maxit,
-                      int R, char *wsbase, cudaStream_t s, RefineResult &res)
+                      int R, char *wsbase, cudaStream_t s, RefineResult &res, const double *anorm_dev)
 {
     const int64_t ldv = n;
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
@@ -677,9 +677,14 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
         GPCH_CUDA(ctx, cudaMemsetAsync(X + c * ldx, 0, n * sizeof(double), s));
         GPCH_CUDA(ctx, cudaMemcpyAsync(Rv + c * ldv, B + c * ldb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    norms_kernel<<<(unsigned)((n * 32 + THREADS - 1) / THREADS < 4096 ? (n * 32 + THREADS - 1) / THREADS : 4096),
-                   THREADS, 0, s>>>(n, A, lda, d_norms);
-    GPCH_LAUNCH_CHECK(ctx);
+    // ||A||_inf: computed with the factor's copy of A when anorm_dev is given
+    if (anorm_dev) {
+        GPCH_CUDA(ctx, cudaMemcpyAsync(d_norms, anorm_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        norms_kernel<<<(unsigned)((n * 32 + THREADS - 1) / THREADS < 4096 ? (n * 32 + THREADS - 1) / THREADS : 4096),
+                       THREADS, 0, s>>>(n, A, lda, d_norms);
+        GPCH_LAUNCH_CHECK(ctx);
+    }
     absmax_cols_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, B, ldb, d_binf);
     GPCH_LAUNCH_CHECK(ctx);
     pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Rv, ldv, st, d_bb, 0);
@@ -852,13 +857,13 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     const int g = nrhs < MAXRHS ? nrhs : MAXRHS;
     gpch::Carver dry(nullptr);
     dry.take<float>((size_t)ldw * n);
-    dry.take<double>(2);
+    dry.take<double>(3);
     const size_t fixed = dry.off;
     const size_t mix = gpch::mixed_ws_bytes(n, tile), pcg = pcg_ws_bytes(n, g);
     GPCH_CHECK(gpch::ws_reserve(ctx, fixed + 256 + (mix > pcg ? mix : pcg)));
     gpch::Carver cv(ctx->ws);
     float *W = cv.take<float>((size_t)ldw * n);
-    double *dev2 = cv.take<double>(2);
+    double *dev2 = cv.take<double>(3);   // [0, 2): diag_max, [2]: ||A||_inf
     char *rest = static_cast<char *>(ctx->ws) + ((cv.off + 255) & ~size_t(255));
 
     double dmax = 0.0;
@@ -872,7 +877,7 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     int attempts = 0;
     int64_t info = 1;
     for (; attempts < 9; ++attempts) {
-        GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, W, ldw, shift, s));
+        GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, W, ldw, shift, s, dev2 + 2));
         int64_t *d_info;
         int *d_err;
         GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, W, ldw, (int)prec, rest, &d_info, &d_err, s));
@@ -901,7 +906,7 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
         const int gg = (nrhs - r0 < MAXRHS) ? nrhs - r0 : MAXRHS;
         RefineResult rr;
         GPCH_CHECK(pcg_group(ctx, n, A, lda, W, ldw, B + r0 * ldb, ldb, X + r0 * ldx, ldx, gg, bwd_tol, maxit, 50,
-                             rest, s, rr));
+                             rest, s, rr, dev2 + 2));
         if (rr.iterations > it_max) it_max = rr.iterations;
         for (int c = 0; c < gg; ++c) {
             if (rr.bwd[c] > bwd_max) bwd_max = rr.bwd[c];

@@ -765,13 +765,26 @@ __global__ void __launch_bounds__(PN_THREADS, 2) panel_trsm_f32_kernel(float *P,
 
 // W (FP32, lower triangle) = A (FP64) + shift * I.  One CTA per column j;
 // the threads walk rows j.. of it, four at a time per thread.
+// With anorm != nullptr the CTA also reads the part of column j above the
+// diagonal and folds max_j sum_i |A_ij| (= ||A||_inf for symmetric A) into
+// *anorm (a non-negative double compared through its bit pattern; zeroed by
+// the caller).  The column sums are accumulated in FP32 per thread (the norm
+// only scales the refinement's stopping test and reported backward error;
+// FP64 adds would make the pass FP64-bound instead of memory-bound).
 __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__restrict__ A, int64_t lda, float *W,
-                                                     int64_t ldw, double shift)
+                                                     int64_t ldw, double shift, double *anorm)
 {
+    __shared__ float red[8];
     const int64_t j = blockIdx.x;
     const double *a = A + j * lda;
     float *w = W + j * ldw;
-    if (threadIdx.x == 0) w[j] = (float)(a[j] + shift);
+    float acc = 0.0f;
+    if (anorm)
+        for (int64_t i = threadIdx.x; i < j; i += 256) acc += (float)fabs(a[i]);
+    if (threadIdx.x == 0) {
+        w[j] = (float)(a[j] + shift);
+        acc += (float)fabs(a[j]);
+    }
     int64_t i = j + 1 + threadIdx.x;
     for (; i + 3 * 256 < n; i += 4 * 256) {
         const double v0 = a[i], v1 = a[i + 256], v2 = a[i + 512], v3 = a[i + 768];
@@ -779,8 +792,23 @@ __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__
         w[i + 256] = (float)v1;
         w[i + 512] = (float)v2;
         w[i + 768] = (float)v3;
+        acc += ((float)fabs(v0) + (float)fabs(v1)) + ((float)fabs(v2) + (float)fabs(v3));
     }
-    for (; i < n; i += 256) w[i] = (float)a[i];
+    for (; i < n; i += 256) {
+        const double v = a[i];
+        w[i] = (float)v;
+        acc += (float)fabs(v);
+    }
+    if (!anorm) return;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += (double)red[k];
+        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(t));
+    }
 }
 
 // Copy the nb x nb lower block between FP32 W and FP64 D (ld ldd).
@@ -1195,11 +1223,13 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     return GPCH_OK;
 }
 
-// W = A + shift I (FP32 lower triangle).
+// W = A + shift I (FP32 lower triangle); with anorm, also ||A||_inf into
+// *anorm (zeroed here).
 gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
-                               double shift, cudaStream_t st)
+                               double shift, cudaStream_t st, double *anorm)
 {
-    init_w_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, W, ldw, shift);
+    if (anorm) GPCH_CUDA(ctx, cudaMemsetAsync(anorm, 0, sizeof(double), st));
+    init_w_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, W, ldw, shift, anorm);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
