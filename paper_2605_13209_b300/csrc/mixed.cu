@@ -778,36 +778,34 @@ __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__
     const int64_t j = blockIdx.x;
     const double *a = A + j * lda;
     float *w = W + j * ldw;
-    float acc = 0.0f;
-    if (anorm)
-        for (int64_t i = threadIdx.x; i < j; i += 256) acc += (float)fabs(a[i]);
-    if (threadIdx.x == 0) {
-        w[j] = (float)(a[j] + shift);
-        acc += (float)fabs(a[j]);
-    }
-    int64_t i = j + 1 + threadIdx.x;
-    for (; i + 3 * 256 < n; i += 4 * 256) {
-        const double v0 = a[i], v1 = a[i + 256], v2 = a[i + 512], v3 = a[i + 768];
-        w[i] = (float)v0;
-        w[i + 256] = (float)v1;
-        w[i + 512] = (float)v2;
-        w[i + 768] = (float)v3;
-        acc += ((float)fabs(v0) + (float)fabs(v1)) + ((float)fabs(v2) + (float)fabs(v3));
-    }
-    for (; i < n; i += 256) {
-        const double v = a[i];
-        w[i] = (float)v;
-        acc += (float)fabs(v);
-    }
-    if (!anorm) return;
+    const bool full = anorm != nullptr;
+    // eight loads of a thread in flight per step (the pass is bound by HBM)
+    constexpr int U = 8;
+    float acc[U] = {};
+    for (int64_t i0 = (full ? 0 : (j & ~int64_t(255))) + threadIdx.x; i0 < n; i0 += U * 256) {
+        double v[U];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * 256;
+            v[u] = (i < n && (full || i >= j)) ? a[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * 256;
+            acc[u] += (float)fabs(v[u]);   // zero past n and, without the norm, above the diagonal
+            if (i >= j && i < n) w[i] = (float)(i == j ? v[u] + shift : v[u]);
+        }
+    }
+    if (!full) return;
+    float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < 8; ++k) t += (double)red[k];
-        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(t));
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += (double)red[k];
+        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(s));
     }
 }
 
