@@ -45,9 +45,9 @@ FP64_PEAK_GFLOPS = 1250.0   # nominal B300 FP64 (DFMA): 148 SMs x 2 FMA/clk x 2 
 FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032    # FFMA: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 CPU_SAMPLE_N = 4096
 # DRAM bytes per algorithmic flop of syrk_tc_kernel (split-f16 update, a
-# K = 2048 pass): 162.4 MB over 8.536e10 flop in one ncu capture at n=16384
+# K = 2048 pass): 91.9 MB over 4.993e10 flop in one ncu capture at n=16384
 # (profiles/syrk_tc_split_f16_n16384.md).
-SYRK_DRAM_BYTES_PER_FLOP = 1.902e-3
+SYRK_DRAM_BYTES_PER_FLOP = 1.841e-3
 
 
 def peaks():
