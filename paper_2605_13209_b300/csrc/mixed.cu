@@ -430,9 +430,10 @@ __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restri
 // (column-major, ld ldy; zero above the diagonal; other sizes are left
 // untouched).  CTA b owns the 8 columns 8b .. 8b+7 of Y (L y = e_c, forward
 // substitution) and keeps them in shared memory, rows in blocks of 32.
-// Block column K of L (rows 32K .. nb-1) is copied in by 32 bulk copies
-// (one per column, completing on an mbarrier; bounded waits set *err = 5)
-// two blocks ahead of its use (three buffers).  Per
+// Block column K of L (rows 32K .. nb-1) is copied in by one or two 2-D
+// TMA boxes of 256 rows x 32 columns through tmL (L as an nb x nb FP32
+// tensor; completion on an mbarrier; bounded waits set *err = 5) two
+// blocks ahead of its use (three buffers).  Per
 // block: warp w solves the 32 x 32 diagonal block for column w (lane = row;
 // one shuffle and one FMA per row), then the later rows are updated as a
 // GEMM, rows x 8 columns x 32, in 4 x 4 register tiles (two 16-byte loads
@@ -441,11 +442,13 @@ constexpr int TI_COLS = 8;
 constexpr int TI_MAXN = 512;
 constexpr int TI_THREADS = 256;
 constexpr int TI_BUFS = 3;
-constexpr size_t TI_SMEM = (size_t)(TI_BUFS * TI_MAXN * 32 + TI_MAXN * TI_COLS) * sizeof(float);
-__global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const float *__restrict__ L, int64_t ldl, int nb,
+constexpr int TI_BOX = 256;                     // rows of one TMA box
+constexpr size_t TI_SMEM = 128 + (size_t)(TI_BUFS * TI_MAXN * 32 + TI_MAXN * TI_COLS) * sizeof(float);
+__global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_constant__ CUtensorMap tmL, int nb,
                                                                  float *Y, int64_t ldy, int *err)
 {
-    extern __shared__ __align__(16) float ti_smem[];
+    extern __shared__ __align__(128) float ti_smem_raw[];
+    float *ti_smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(ti_smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t bar[TI_BUFS];
     if (nb % 32 != 0 || nb > TI_MAXN) return;
     float *Ts = ti_smem + TI_BUFS * TI_MAXN * 32;   // Ts[r * TI_COLS + c]: row r of this CTA's columns
@@ -457,16 +460,19 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const float *__
         gpch::tc::fence_mbar_init();
     }
     __syncthreads();
-    // block column K into buffer K % 3: (row r, col 32K + kk) at kk * TI_MAXN + r,
-    // one bulk copy per column by the lanes of warp 0
+    // block column K into buffer K % 3: rows 32K.. (q = row - 32K) of
+    // columns 32K + kk, box h = q / 256 at h * 32 * 256 + kk * 256 + q % 256
+    // (rows past nb read as zeros)
     auto stage = [&](int K) {
-        if (warp != 0) return;
-        const uint32_t bytes = (uint32_t)(nb - 32 * K) * 4u;
+        if (tid != 0) return;
+        const bool two = 32 * K + TI_BOX < nb;
         float *Ls = ti_smem + (K % TI_BUFS) * TI_MAXN * 32;
-        if (lane == 0) gpch::tc::mbar_arrive_expect_tx(&bar[K % TI_BUFS], 32u * bytes);
-        __syncwarp();
-        gpch::tc::bulk_g2s(Ls + lane * TI_MAXN + 32 * K, L + 32 * K + (int64_t)(32 * K + lane) * ldl, bytes,
-                           &bar[K % TI_BUFS]);
+        gpch::tc::mbar_arrive_expect_tx(&bar[K % TI_BUFS], (two ? 2u : 1u) * TI_BOX * 32u * 4u);
+        gpch::tc::tma_load_2d(Ls, &tmL, &bar[K % TI_BUFS], 32 * K, 32 * K);
+        if (two) gpch::tc::tma_load_2d(Ls + 32 * TI_BOX, &tmL, &bar[K % TI_BUFS], 32 * K + TI_BOX, 32 * K);
+    };
+    auto lsat = [&](const float *Ls, int kk, int q) -> const float * {
+        return Ls + (q / TI_BOX) * (32 * TI_BOX) + kk * TI_BOX + (q % TI_BOX);
     };
     uint32_t phases = 0;   // bit b: parity of buffer b's next phase
     bool ok = true;
@@ -495,10 +501,10 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const float *__
             // diagonal block, column c0 + warp, row 32K + lane
             const int r = 32 * K + lane;
             float t = Ts[r * TI_COLS + warp];
-            const float rp = 1.0f / Ls[lane * TI_MAXN + r];
+            const float rp = 1.0f / *lsat(Ls, lane, lane);
 #pragma unroll 8
             for (int kk = 0; kk < 32; ++kk) {
-                const float l = Ls[kk * TI_MAXN + r];
+                const float l = *lsat(Ls, kk, lane);
                 const float y = __shfl_sync(0xffffffffu, t * rp, kk);
                 const float tn = fmaf(-l, y, t);
                 t = (lane == kk) ? y : ((lane > kk) ? tn : t);
@@ -513,7 +519,7 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const float *__
             float acc[4][4] = {};
 #pragma unroll 8
             for (int kk = 0; kk < 32; ++kk) {
-                const float4 lv = *reinterpret_cast<const float4 *>(Ls + kk * TI_MAXN + r0);
+                const float4 lv = *reinterpret_cast<const float4 *>(lsat(Ls, kk, r0 - 32 * K));
                 const float4 yv = *reinterpret_cast<const float4 *>(Ts + (32 * K + kk) * TI_COLS + cg);
                 const float la[4] = {lv.x, lv.y, lv.z, lv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
@@ -842,6 +848,24 @@ gpch_status make_panel_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, in
     return GPCH_OK;
 }
 
+// Tensor map over the nb x nb FP32 tile at L (column-major, ld ldl; L and
+// ldl * 4 multiples of 16 bytes) in boxes of TI_BOX rows x 32 columns, no
+// swizzle; rows and columns past nb read as zeros.
+gpch_status make_tile_map_f32(gpch_ctx *ctx, CUtensorMap *map, const float *L, int64_t nb, int64_t ldl)
+{
+    auto enc = gpch::tc::tmap_encoder();
+    if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
+    cuuint64_t dims[2] = {(cuuint64_t)nb, (cuuint64_t)nb};
+    cuuint64_t strides[1] = {(cuuint64_t)ldl * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TI_BOX, 32u};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(L), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GPCH_OK;
+}
+
 struct LowprecBuffers {
     __nv_bfloat16 *hi = nullptr;   // the 16-bit copy (binary16 data under SPLIT_F16), layout of kpos()
     int *err = nullptr;
@@ -1114,8 +1138,10 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                 // are the rows of L_jj^-1, the K-major right operand), both
                 // operands split into scaled binary16 head and tail
                 const int kpj = (int)((nj + BK - 1) / BK * BK);
+                CUtensorMap tmT;
+                GPCH_CHECK(make_tile_map_f32(ctx, &tmT, Wjj, nj, ldw));
                 tri_inv_f32_kernel<<<(unsigned)((nj + TI_COLS - 1) / TI_COLS), TI_THREADS, TI_SMEM, st>>>(
-                    Wjj, ldw, (int)nj, w.Tid, tile, w.err);
+                    tmT, (int)nj, w.Tid, tile, w.err);
                 GPCH_LAUNCH_CHECK(ctx);
                 GPCH_CUDA(ctx, cudaMemsetAsync(w.tscale, 0, 2 * sizeof(int), st));
                 panel_absmax_kernel<<<dim3((unsigned)((nj + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
