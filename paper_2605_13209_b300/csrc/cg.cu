@@ -858,12 +858,14 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     gpch::Carver dry(nullptr);
     dry.take<float>((size_t)ldw * n);
     dry.take<double>(3);
+    dry.take<float>(gpch::anorm_ws_floats(n));
     const size_t fixed = dry.off;
     const size_t mix = gpch::mixed_ws_bytes(n, tile), pcg = pcg_ws_bytes(n, g);
     GPCH_CHECK(gpch::ws_reserve(ctx, fixed + 256 + (mix > pcg ? mix : pcg)));
     gpch::Carver cv(ctx->ws);
     float *W = cv.take<float>((size_t)ldw * n);
     double *dev2 = cv.take<double>(3);   // [0, 2): diag_max, [2]: ||A||_inf
+    float *norm_ws = cv.take<float>(gpch::anorm_ws_floats(n));
     char *rest = static_cast<char *>(ctx->ws) + ((cv.off + 255) & ~size_t(255));
 
     double dmax = 0.0;
@@ -877,7 +879,7 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     int attempts = 0;
     int64_t info = 1;
     for (; attempts < 9; ++attempts) {
-        GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, W, ldw, shift, s, dev2 + 2));
+        GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, W, ldw, shift, s, dev2 + 2, norm_ws));
         int64_t *d_info;
         int *d_err;
         GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, W, ldw, (int)prec, rest, &d_info, &d_err, s));

@@ -874,11 +874,12 @@ gpch_status solve_apply_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ld
                             SolveWs &w, cudaStream_t st);
 
 // Low-precision factor (mixed.cu): workspace size, W = A + shift I (and,
-// with anorm, ||A||_inf of the symmetric A into *anorm), and the
+// with anorm and norm_ws, ||A||_inf of the symmetric A into *anorm), and the
 // factorization of W in place (info / err device words returned).
 size_t mixed_ws_bytes(int64_t n, int tile);
 gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
-                               double shift, cudaStream_t st, double *anorm = nullptr);
+                               double shift, cudaStream_t st, double *anorm = nullptr, float *norm_ws = nullptr);
+size_t anorm_ws_floats(int64_t n);   // workspace of the ||A||_inf pieces (floats)
 gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
                                  int64_t **info_out, int **err_out, cudaStream_t st);
 

@@ -784,34 +784,139 @@ __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__
     const int64_t j = blockIdx.x;
     const double *a = A + j * lda;
     float *w = W + j * ldw;
-    const bool full = anorm != nullptr;
-    // eight loads of a thread in flight per step (the pass is bound by HBM)
-    constexpr int U = 8;
-    float acc[U] = {};
-    for (int64_t i0 = (full ? 0 : (j & ~int64_t(255))) + threadIdx.x; i0 < n; i0 += U * 256) {
-        double v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = i0 + u * 256;
-            v[u] = (i < n && (full || i >= j)) ? a[i] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = i0 + u * 256;
-            acc[u] += (float)fabs(v[u]);   // zero past n and, without the norm, above the diagonal
-            if (i >= j && i < n) w[i] = (float)(i == j ? v[u] + shift : v[u]);
-        }
+    float acc = 0.0f;
+    if (anorm)
+        for (int64_t i = threadIdx.x; i < j; i += 256) acc += (float)fabs(a[i]);
+    if (threadIdx.x == 0) {
+        w[j] = (float)(a[j] + shift);
+        acc += (float)fabs(a[j]);
     }
-    if (!full) return;
-    float t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    int64_t i = j + 1 + threadIdx.x;
+    for (; i + 3 * 256 < n; i += 4 * 256) {
+        const double v0 = a[i], v1 = a[i + 256], v2 = a[i + 512], v3 = a[i + 768];
+        w[i] = (float)v0;
+        w[i + 256] = (float)v1;
+        w[i + 512] = (float)v2;
+        w[i + 768] = (float)v3;
+        acc += ((float)fabs(v0) + (float)fabs(v1)) + ((float)fabs(v2) + (float)fabs(v3));
+    }
+    for (; i < n; i += 256) {
+        const double v = a[i];
+        w[i] = (float)v;
+        acc += (float)fabs(v);
+    }
+    if (!anorm) return;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < 8; ++k) s += (double)red[k];
-        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(s));
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += (double)red[k];
+        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(t));
+    }
+}
+
+// W = A + shift I on the lower triangle (FP32) together with the pieces of
+// ||A||_inf (= max_i sum_j |A_ij| for symmetric A), from the lower triangle
+// only: row i's sum is its part left of and on the diagonal plus, by
+// symmetry, column i's part below the diagonal.  CTA (b, q) covers the
+// NW_COLS columns of strip b (c0 = NW_COLS b ..) and the NW_ROWS rows of
+// chunk q (r0 = NW_ROWS q ..), walking the strip column by column so that
+// each column piece streams contiguously from HBM; thread t owns the rows
+// r0 + t + 256 k.
+// * part[b * n + row]: the row's sum over the strip (registers across the
+//   columns);
+// * colpart[q * n + col]: the column's sum over the chunk's rows below the
+//   diagonal (a fixed-order CTA reduction).
+// CTAs whose chunk lies above the strip leave at once.  The magnitudes come
+// from the FP32 values written to W (one conversion per entry, which the
+// FP64 pipe performs); the norm only scales the refinement's stopping test
+// and reported backward error.
+constexpr int NW_COLS = 64;
+constexpr int NW_ROWS = 4096;
+constexpr int NW_THREADS = 256;
+constexpr int NW_PER = NW_ROWS / NW_THREADS;   // rows of a thread
+__global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, const double *__restrict__ A,
+                                                                 int64_t lda, float *W, int64_t ldw, double shift,
+                                                                 float *part, float *colpart)
+{
+    __shared__ float red[NW_THREADS / 32][NW_COLS];
+    const int64_t c0 = (int64_t)blockIdx.x * NW_COLS, r0 = (int64_t)blockIdx.y * NW_ROWS;
+    if (r0 + NW_ROWS <= c0) return;   // the chunk lies above the strip
+    const int cw = (int)((n - c0 < NW_COLS) ? n - c0 : NW_COLS);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float racc[NW_PER];
+#pragma unroll
+    for (int k = 0; k < NW_PER; ++k) racc[k] = 0.0f;
+    for (int c = 0; c < cw; ++c) {
+        const int64_t col = c0 + c;
+        const double *a = A + col * lda;
+        float *w = W + col * ldw;
+        double v[NW_PER];
+#pragma unroll
+        for (int k = 0; k < NW_PER; ++k) {
+            const int64_t row = r0 + threadIdx.x + NW_THREADS * k;
+            v[k] = (row >= col && row < n) ? a[row] : 0.0;
+        }
+        float cacc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NW_PER; ++k) {
+            const int64_t row = r0 + threadIdx.x + NW_THREADS * k;
+            if (row > col && row < n) {
+                const float f = (float)v[k];
+                w[row] = f;
+                racc[k] += fabsf(f);
+                cacc += fabsf(f);
+            } else if (row == col) {
+                w[row] = (float)(v[k] + shift);
+                racc[k] += fabsf((float)v[k]);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
+        if (lane == 0) red[warp][c] = cacc;
+    }
+    float *prow = part + (int64_t)blockIdx.x * n;
+#pragma unroll
+    for (int k = 0; k < NW_PER; ++k) {
+        const int64_t row = r0 + threadIdx.x + NW_THREADS * k;
+        if (row < n) prow[row] = racc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < cw) {
+        float t = 0.0f;
+        for (int w2 = 0; w2 < NW_THREADS / 32; ++w2) t += red[w2][threadIdx.x];
+        colpart[(int64_t)blockIdx.y * n + c0 + threadIdx.x] = t;
+    }
+}
+
+// *anorm = max_i (sum over the strips b <= i / NW_COLS of part[b * n + i]
+// + sum over the chunks q >= (NW_COLS (i / NW_COLS)) / NW_ROWS of
+// colpart[q * n + i]), each row summed in a fixed order; *anorm holds a
+// non-negative double compared through its bit pattern (zeroed by the
+// caller).
+__global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float *__restrict__ part,
+                                                          const float *__restrict__ colpart, double *anorm)
+{
+    __shared__ double red[8];
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double m = 0.0;
+    if (i < n) {
+        float s = 0.0f;
+        const int64_t nb = i / NW_COLS, nq = (n + NW_ROWS - 1) / NW_ROWS;
+        for (int64_t b = 0; b <= nb; ++b) s += part[b * n + i];
+        for (int64_t q = (nb * NW_COLS) / NW_ROWS; q < nq; ++q) s += colpart[q * n + i];
+        m = (double)s;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w2 = 1; w2 < 8; ++w2) m = fmax(m, red[w2]);
+        m = fmax(m, red[0]);
+        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(m));
     }
 }
 
@@ -1247,12 +1352,27 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     return GPCH_OK;
 }
 
-// W = A + shift I (FP32 lower triangle); with anorm, also ||A||_inf into
-// *anorm (zeroed here).
-gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
-                               double shift, cudaStream_t st, double *anorm)
+size_t anorm_ws_floats(int64_t n)
 {
-    if (anorm) GPCH_CUDA(ctx, cudaMemsetAsync(anorm, 0, sizeof(double), st));
+    return (size_t)((n + NW_COLS - 1) / NW_COLS + (n + NW_ROWS - 1) / NW_ROWS) * (size_t)n;
+}
+
+// W = A + shift I (FP32 lower triangle); with anorm, also ||A||_inf into
+// *anorm (zeroed here), through norm_ws (anorm_ws_floats(n) floats).
+gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
+                               double shift, cudaStream_t st, double *anorm, float *norm_ws)
+{
+    if (anorm && norm_ws) {
+        GPCH_CUDA(ctx, cudaMemsetAsync(anorm, 0, sizeof(double), st));
+        const int64_t nstrip = (n + NW_COLS - 1) / NW_COLS, nchunk = (n + NW_ROWS - 1) / NW_ROWS;
+        float *part = norm_ws, *colpart = norm_ws + nstrip * n;
+        init_w_norm_kernel<<<dim3((unsigned)nstrip, (unsigned)nchunk), NW_THREADS, 0, st>>>(n, A, lda, W, ldw, shift,
+                                                                                           part, colpart);
+        GPCH_LAUNCH_CHECK(ctx);
+        norm_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, part, colpart, anorm);
+        GPCH_LAUNCH_CHECK(ctx);
+        return GPCH_OK;
+    }
     init_w_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, W, ldw, shift, anorm);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;

@@ -93,7 +93,10 @@ size_t request_bytes(const gpch_request &r, bool solo_mixed, int tile)
         b += round_up(((n + 31) / 32 * 32) * n * 4) + 2 * round_up(n * ((n + 63) / 64 * 64) * 2) +
              round_up((size_t)tile * tile * 8) + 12 * n * 8 * r.nrhs +
              // panel solve on tensor cores: L_jj^-T, its 16-bit copies, the panel's
-             3 * round_up((size_t)tile * tile * 4) + 2 * round_up(n * (size_t)tile * 2);
+             3 * round_up((size_t)tile * tile * 4) + 2 * round_up(n * (size_t)tile * 2) +
+             // pieces of ||A||_inf: a row sum per 64-column strip, a column sum
+             // per 4096-row chunk
+             round_up(((n + 63) / 64 + (n + 4095) / 4096) * n * 4);
     return b;
 }
 
