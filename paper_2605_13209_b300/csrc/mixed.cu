@@ -428,7 +428,9 @@ __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restri
 // Y = L^-1 for the nb x nb lower triangle L (FP32, column-major, ld ldl),
 // nb <= 512 with nb % 32 == 0, L and ldl 16-byte aligned, into Y
 // (column-major, ld ldy; zero above the diagonal; other sizes are left
-// untouched).  CTA b owns the 8 columns 8b .. 8b+7 of Y (L y = e_c, forward
+// untouched; absmax, if given, gets the largest |entry| of Y as FP32 bits
+// by atomicMax, so it must start at 0).  CTA b owns the 8 columns
+// 8b .. 8b+7 of Y (L y = e_c, forward
 // substitution) and keeps them in shared memory, rows in blocks of 32.
 // Block column K of L (rows 32K .. nb-1) is copied in by one or two 2-D
 // TMA boxes of 256 rows x 32 columns through tmL (L as an nb x nb FP32
@@ -445,7 +447,7 @@ constexpr int TI_BUFS = 3;
 constexpr int TI_BOX = 256;                     // rows of one TMA box
 constexpr size_t TI_SMEM = 128 + (size_t)(TI_BUFS * TI_MAXN * 32 + TI_MAXN * TI_COLS) * sizeof(float);
 __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_constant__ CUtensorMap tmL, int nb,
-                                                                 float *Y, int64_t ldy, int *err)
+                                                                 float *Y, int64_t ldy, int *err, unsigned *absmax)
 {
     extern __shared__ __align__(128) float ti_smem_raw[];
     float *ti_smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(ti_smem_raw) + 127) & ~uintptr_t(127));
@@ -540,9 +542,18 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_co
         }
         __syncthreads();   // the buffer is refilled at the next step; Ts rows are read next block
     }
+    float mx = 0.0f;
     for (int e = tid; e < nb * TI_COLS; e += TI_THREADS) {
         const int r = e % nb, cc = e / nb;
-        Y[r + (int64_t)(c0 + cc) * ldy] = Ts[r * TI_COLS + cc];
+        const float v = Ts[r * TI_COLS + cc];
+        Y[r + (int64_t)(c0 + cc) * ldy] = v;
+        mx = fmaxf(mx, fabsf(v));
+    }
+    if (absmax) {
+        // largest |entry| as FP32 bits (non-negative floats order like their bits)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) atomicMax(absmax, __float_as_uint(mx));
     }
 }
 
@@ -1196,7 +1207,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     // ev_ready[X % 2]: the second stream's passes over block column X are done
     cudaEvent_t ev_ready[2] = {ctx->aux_ev[1], ctx->aux_ev[6]};
     cudaStream_t sc = ctx->side;
-    bool side_pending = false;
+    bool side_pending = false, next_pre_conv = false;
     GPCH_CUDA(ctx, cudaEventRecord(ev_start, caller));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
@@ -1224,6 +1235,8 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         // of step J-1 (block column J below its tile) must be complete
         if (side_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_side, 0));
         side_pending = false;
+        const bool pre_conv = next_pre_conv;   // the side stream made this panel's first 16-bit rows
+        next_pre_conv = false;
         // tensor-core panel with look-ahead: rows [0, m1) of the panel (the
         // rows of block column J+1) on the critical stream, the others on
         // the side stream
@@ -1245,20 +1258,21 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                 const int kpj = (int)((nj + BK - 1) / BK * BK);
                 CUtensorMap tmT;
                 GPCH_CHECK(make_tile_map_f32(ctx, &tmT, Wjj, nj, ldw));
+                // the inverse's scale word starts at 0 (cleared by the side
+                // stream at the end of the previous step when it ran)
+                if (!pre_conv) GPCH_CUDA(ctx, cudaMemsetAsync(w.tscale, 0, 2 * sizeof(int), st));
                 tri_inv_f32_kernel<<<(unsigned)((nj + TI_COLS - 1) / TI_COLS), TI_THREADS, TI_SMEM, st>>>(
-                    tmT, (int)nj, w.Tid, tile, w.err);
-                GPCH_LAUNCH_CHECK(ctx);
-                GPCH_CUDA(ctx, cudaMemsetAsync(w.tscale, 0, 2 * sizeof(int), st));
-                panel_absmax_kernel<<<dim3((unsigned)((nj + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
-                    w.Tid, tile, nj, (int)nj, reinterpret_cast<unsigned *>(w.tscale));
+                    tmT, (int)nj, w.Tid, tile, w.err, reinterpret_cast<unsigned *>(w.tscale));
                 GPCH_LAUNCH_CHECK(ctx);
                 // rows of L_jj^-1 (stored column-major) become the K-major rows
                 panel_to_f16_kernel<<<dim3((unsigned)((nj + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
                     w.Tid, tile, nj, (int)nj, kpj, reinterpret_cast<__half *>(w.thi), w.tscale, 2 * tile);
                 GPCH_LAUNCH_CHECK(ctx);
-                panel_to_f16_kernel<<<dim3((unsigned)((m1 + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
-                    Pan, ldw, m1, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), w.pscale, 2 * tile);
-                GPCH_LAUNCH_CHECK(ctx);
+                if (!pre_conv) {
+                    panel_to_f16_kernel<<<dim3((unsigned)((m1 + 63) / 64), (unsigned)(kpj / 64)), 256, 0, st>>>(
+                        Pan, ldw, m1, (int)nj, kpj, reinterpret_cast<__half *>(w.phi), w.pscale, 2 * tile);
+                    GPCH_LAUNCH_CHECK(ctx);
+                }
                 LowprecBuffers pbuf = all, qbuf = all;
                 pbuf.hi = w.phi;
                 pbuf.scale = w.pscale;
@@ -1292,6 +1306,21 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
                     cb.hi = all.hi + (j0 + nj) * all.ld + kpos(true, j0);
                     GPCH_CHECK(panel_gemm_tc_launch(ctx, mr, m1, (int)nj, W + (j0 + nj + m1) + (j0 + nj) * ldw, ldw,
                                                     rb, cb, sc, nullptr, 0, true, acc_k));
+                    // block column J+1 below its tile is final now: the
+                    // 16-bit copy of its first rows (panel J+1 before the
+                    // solve) and the clearing of the next inverse's scale
+                    // word leave the critical stream
+                    const int64_t j1 = j0 + nj, nj1 = (n - j1 < tile) ? n - j1 : tile, mn = n - j1 - nj1;
+                    next_pre_conv = mn > 0;
+                    if (next_pre_conv) {
+                        const int64_t m1n = (mn < nj1) ? mn : nj1;
+                        const int kpn = (int)((nj1 + BK - 1) / BK * BK);
+                        GPCH_CUDA(ctx, cudaMemsetAsync(w.tscale, 0, 2 * sizeof(int), sc));
+                        panel_to_f16_kernel<<<dim3((unsigned)((m1n + 63) / 64), (unsigned)(kpn / 64)), 256, 0, sc>>>(
+                            W + (j1 + nj1) + j1 * ldw, ldw, m1n, (int)nj1, kpn, reinterpret_cast<__half *>(w.phi),
+                            w.pscale, 2 * tile);
+                        GPCH_LAUNCH_CHECK(ctx);
+                    }
                     GPCH_CUDA(ctx, cudaEventRecord(ev_side, sc));
                     side_pending = true;
                 }
