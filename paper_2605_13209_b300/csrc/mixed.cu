@@ -782,26 +782,14 @@ __global__ void __launch_bounds__(PN_THREADS, 2) panel_trsm_f32_kernel(float *P,
 
 // W (FP32, lower triangle) = A (FP64) + shift * I.  One CTA per column j;
 // the threads walk rows j.. of it, four at a time per thread.
-// With anorm != nullptr the CTA also reads the part of column j above the
-// diagonal and folds max_j sum_i |A_ij| (= ||A||_inf for symmetric A) into
-// *anorm (a non-negative double compared through its bit pattern; zeroed by
-// the caller).  The column sums are accumulated in FP32 per thread (the norm
-// only scales the refinement's stopping test and reported backward error;
-// FP64 adds would make the pass FP64-bound instead of memory-bound).
+// W = A + shift I on the lower triangle (FP32), one CTA per column.
 __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__restrict__ A, int64_t lda, float *W,
-                                                     int64_t ldw, double shift, double *anorm)
+                                                     int64_t ldw, double shift)
 {
-    __shared__ float red[8];
     const int64_t j = blockIdx.x;
     const double *a = A + j * lda;
     float *w = W + j * ldw;
-    float acc = 0.0f;
-    if (anorm)
-        for (int64_t i = threadIdx.x; i < j; i += 256) acc += (float)fabs(a[i]);
-    if (threadIdx.x == 0) {
-        w[j] = (float)(a[j] + shift);
-        acc += (float)fabs(a[j]);
-    }
+    if (threadIdx.x == 0) w[j] = (float)(a[j] + shift);
     int64_t i = j + 1 + threadIdx.x;
     for (; i + 3 * 256 < n; i += 4 * 256) {
         const double v0 = a[i], v1 = a[i + 256], v2 = a[i + 512], v3 = a[i + 768];
@@ -809,23 +797,8 @@ __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__
         w[i + 256] = (float)v1;
         w[i + 512] = (float)v2;
         w[i + 768] = (float)v3;
-        acc += ((float)fabs(v0) + (float)fabs(v1)) + ((float)fabs(v2) + (float)fabs(v3));
     }
-    for (; i < n; i += 256) {
-        const double v = a[i];
-        w[i] = (float)v;
-        acc += (float)fabs(v);
-    }
-    if (!anorm) return;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < 8; ++k) t += (double)red[k];
-        atomicMax(reinterpret_cast<unsigned long long *>(anorm), (unsigned long long)__double_as_longlong(t));
-    }
+    for (; i < n; i += 256) w[i] = (float)a[i];
 }
 
 // W = A + shift I on the lower triangle (FP32) together with the pieces of
@@ -1386,12 +1359,15 @@ size_t anorm_ws_floats(int64_t n)
     return (size_t)((n + NW_COLS - 1) / NW_COLS + (n + NW_ROWS - 1) / NW_ROWS) * (size_t)n;
 }
 
-// W = A + shift I (FP32 lower triangle); with anorm, also ||A||_inf into
-// *anorm (zeroed here), through norm_ws (anorm_ws_floats(n) floats).
+// W = A + shift I (FP32 lower triangle); with anorm and norm_ws, also
+// ||A||_inf into *anorm (zeroed here), through norm_ws (anorm_ws_floats(n)
+// floats).
 gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
                                double shift, cudaStream_t st, double *anorm, float *norm_ws)
 {
-    if (anorm && norm_ws) {
+    if ((anorm == nullptr) != (norm_ws == nullptr))
+        return gpch::fail(ctx, GPCH_INVALID_ARG, "the norm needs both its output and its workspace");
+    if (anorm) {
         GPCH_CUDA(ctx, cudaMemsetAsync(anorm, 0, sizeof(double), st));
         const int64_t nstrip = (n + NW_COLS - 1) / NW_COLS, nchunk = (n + NW_ROWS - 1) / NW_ROWS;
         float *part = norm_ws, *colpart = norm_ws + nstrip * n;
@@ -1402,7 +1378,7 @@ gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_
         GPCH_LAUNCH_CHECK(ctx);
         return GPCH_OK;
     }
-    init_w_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, W, ldw, shift, anorm);
+    init_w_kernel<<<(unsigned)n, 256, 0, st>>>(n, A, lda, W, ldw, shift);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
