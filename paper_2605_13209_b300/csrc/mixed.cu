@@ -2,15 +2,17 @@
 // refined solve.  Algorithm 1 (right) runs on an FP32 copy of the lower
 // triangle of A (+ shift * I):
 //   step 1  the diagonal tile is widened to FP64 and factored by the FP64
-//           nest (potrf leaf / inverse-apply TRSM / SYRK), then stored back
-//           in FP32;
-//   step 2  the panel is solved in FP32, 64 columns at a time, against FP32
-//           inverses of the diagonal tile's 64 x 64 blocks;
+//           nest (potrf leaf / unit-lower substitution / SYRK), then stored
+//           back in FP32;
+//   step 2  SPLIT_F16: the panel is the tensor-core product A_ij L_jj^-T,
+//           with L_jj^-1 from an FP32 forward substitution; the bf16 modes
+//           solve it in FP32, 64 columns at a time, against FP32 inverses
+//           of the diagonal tile's 64 x 64 blocks;
 //   step 3  the trailing update A_ik -= A_ij A_kj^T runs on the tensor cores:
-//           the panel is rounded to bf16 (or split into a bf16 head and a
-//           bf16 tail) in a K-major copy, TMA streams 128 x 16 tiles of it
-//           into shared memory, tcgen05.mma accumulates 128 x 128 FP32 tiles
-//           in TMEM, and the epilogue subtracts them from the FP32 matrix.
+//           the panel is rounded to 16 bits (or split into a head and a
+//           tail) in a K-major copy, TMA streams 128 x 64 boxes of it into
+//           shared memory, tcgen05.mma accumulates 128 x 128 FP32 tiles in
+//           TMEM, and the epilogue subtracts them from the FP32 matrix.
 // Mixed precision is the paper's stated future work (Sec. 5); the factor's
 // accuracy is recovered by the FP64 refinement in cg.cu.
 #include <cuda.h>
