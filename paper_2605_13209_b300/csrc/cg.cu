@@ -576,32 +576,6 @@ __device__ inline void atomic_max_nonneg(double *addr, double v)
     atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// out[0] = max_j sum_i |A_ij| (= ||A||_inf for symmetric A), one warp per
-// column.  The column sums are accumulated in FP32 (eight partial sums per
-// lane, relative error ~1e-6): the norm only scales the stopping test and
-// the reported backward error, and FP32 adds keep this pass at memory speed
-// where FP64 adds would be bound by the FP64 pipe.
-__global__ void __launch_bounds__(THREADS) norms_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
-                                                        double *out)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * THREADS + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * THREADS) >> 5;
-    for (int64_t j = gw; j < n; j += nw) {
-        const double *col = A + j * lda;
-        float p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int64_t i = lane;
-        for (; i + 7 * 32 < n; i += 8 * 32) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) p[u] += (float)fabs(col[i + u * 32]);
-        }
-        for (; i < n; i += 32) p[0] += (float)fabs(col[i]);
-        double s = (double)(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
-        s = warp_sum(s);
-        if (lane == 0) atomic_max_nonneg(&out[0], s);
-    }
-}
-
 // *out = max(0, max_i A_ii).
 __global__ void __launch_bounds__(THREADS) diag_max_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
                                                            double *out)
@@ -632,7 +606,8 @@ struct RefineResult {
     double bwd[MAXRHS] = {0};
 };
 
-// PCG on one group of <= 16 right-hand sides.  L: FP32 factor (ldl).
+// PCG on one group of <= 16 right-hand sides.  L: FP32 factor (ldl);
+// anorm_dev: ||A||_inf on the device (from mixed_init_enqueue).
 gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const float *L, int64_t ldl,
                       const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double bwd_tol, int maxit,
                       int R, char *wsbase, cudaStream_t s, RefineResult &res, const double *anorm_dev)
@@ -677,14 +652,8 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
         GPCH_CUDA(ctx, cudaMemsetAsync(X + c * ldx, 0, n * sizeof(double), s));
         GPCH_CUDA(ctx, cudaMemcpyAsync(Rv + c * ldv, B + c * ldb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    // ||A||_inf: computed with the factor's copy of A when anorm_dev is given
-    if (anorm_dev) {
-        GPCH_CUDA(ctx, cudaMemcpyAsync(d_norms, anorm_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
-        norms_kernel<<<(unsigned)((n * 32 + THREADS - 1) / THREADS < 4096 ? (n * 32 + THREADS - 1) / THREADS : 4096),
-                       THREADS, 0, s>>>(n, A, lda, d_norms);
-        GPCH_LAUNCH_CHECK(ctx);
-    }
+    // ||A||_inf, made by the pass that built the factor's copy of A
+    GPCH_CUDA(ctx, cudaMemcpyAsync(d_norms, anorm_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
     absmax_cols_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, B, ldb, d_binf);
     GPCH_LAUNCH_CHECK(ctx);
     pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Rv, ldv, st, d_bb, 0);
