@@ -334,6 +334,19 @@ def test_backward_error_closed_form():
     assert abs(oracle.backward_error(A, x, b) - d / (2 + d)) < 1e-16
 
 
+def test_backward_error_nonsymmetric_hand_value():
+    """A nonsymmetric 2 x 2 case worked by hand, where the usual slips give
+    other values: A = [[1, 4], [2, 0]], x = (1, -2), b = (-6, 2.5).
+    Ax - b = (-1, -0.5), so ||r||_inf = 1; ||A||_inf = 5 (row sums 5, 2),
+    ||x||_inf = 2, ||b||_inf = 6, and the error is 1 / (5 * 2 + 6) = 1/16
+    exactly.  The 1-norm of A would give 1/14, A^T x 3/16, ||x||_1 1/21 and
+    a dropped ||b|| term 1/10."""
+    A = np.array([[1.0, 4.0], [2.0, 0.0]])
+    x = np.array([1.0, -2.0])
+    b = np.array([-6.0, 2.5])
+    assert oracle.backward_error(A, x, b) == 1.0 / 16.0
+
+
 def test_pcg_exact_preconditioner_one_step():
     sysm = inputs.gp_system(100, 8, 0.5, 1e-2, seed=6)
     A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
