@@ -381,10 +381,14 @@ typedef struct gpch_refine_stats {
  * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
  * from x_0 = 0, replacing the recurrence residual by b - A x every 50
  * iterations and whenever an estimate of the backward error from the
- * recurrence residual (||r||_2 / sqrt(n) in place of ||r||_inf, scaled by
- * the truth-to-estimate ratio seen at the previous check) reaches bwd_tol.
- * A: device FP64 full symmetric n x n (lda).  B: device n x nrhs (ldb).
- * X: device n x nrhs (ldx), overwritten.  Workspace: about 4 n^2 bytes.
+ * recurrence residual (its ||r||_inf in place of the true residual's,
+ * scaled by the truth-to-estimate ratio seen at the previous check)
+ * reaches bwd_tol.
+ * A: device FP64 full symmetric n x n (lda); the factor and ||A||_inf read
+ * its lower triangle, the residual b - A x all of it.  B: device n x nrhs
+ * (ldb).  X: device n x nrhs (ldx), overwritten.  Workspace (context
+ * arena): about 8 n^2 bytes, the FP32 factor and the 16-bit copies of its
+ * panels.
  * stats (host, may be NULL).  Synchronizes `stream`.  Returns GPCH_NOT_SPD
  * if every shifted factorization broke down, GPCH_NOT_CONVERGED if some
  * column missed bwd_tol within maxit iterations. */
