@@ -347,8 +347,10 @@ gpch_status gpch_syrk_lowprec(gpch_ctx *ctx, int64_t m, int64_t k, const float *
 /* ------------------------------------- A8: low-precision factor */
 
 /* Low-precision Cholesky factor of A + shift I: Algorithm 1 (right) on an
- * FP32 copy with step 1 in FP64, step 2 in FP32 and step 3 on the tensor
- * cores as in gpch_syrk_lowprec.  A: device FP64 n x n (lower triangle
+ * FP32 copy with step 1 in FP64, step 2 in FP32 (for GPCH_PREC_SPLIT_F16
+ * the tensor-core product of the panel with L_jj^-T, split-f16 operands,
+ * L_jj^-1 from an FP32 substitution) and step 3 on the tensor cores as in
+ * gpch_syrk_lowprec.  A: device FP64 n x n (lower triangle
  * read, not modified).  L: device FP32 n x n (ldl), receives the factor in
  * its lower triangle.  prec: GPCH_PREC_BF16, GPCH_PREC_SPLIT_BF16 or
  * GPCH_PREC_SPLIT_F16 (one power-of-two scale for the whole factor, from
