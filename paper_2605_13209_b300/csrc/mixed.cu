@@ -1188,7 +1188,12 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_start, 0));
     const int64_t blk_cols = (tile + BN - 1) / BN;   // tile columns of one block column
-    const int64_t LEFT_K = 4 * (int64_t)tile;         // K columns (whole panels) per launch of the long pass
+    // K columns (whole panels) per launch of the long pass: longer launches
+    // read and write C fewer times and leave fewer partial waves (at
+    // n = 32768, 2 panels: 76.7 ms per solve, 4: 69, 8 to 64: 65-68), while
+    // a bound keeps a CTA's lifetime, and so the wait of the critical
+    // stream's tensor-core launches for a free slot, bounded at large n
+    const int64_t LEFT_K = 16 * (int64_t)tile;
     // products summed in the tensor-core accumulator before they are added
     // (in FP32, rounding to nearest) to the running sum: half a panel when
     // that is a whole number of 64-column K blocks
