@@ -347,6 +347,33 @@ def test_backward_error_nonsymmetric_hand_value():
     assert oracle.backward_error(A, x, b) == 1.0 / 16.0
 
 
+def test_pcg_iterates_equal_cg_on_the_transformed_system():
+    """Preconditioned CG with M = L L^T on A x = b is CG on the transformed
+    system (L^-1 A L^-T) y = L^-1 b with x = L^-T y, iterate by iterate.
+    With no stop test and no residual replacement (bwd_tol = eps = 0,
+    R = 0) both run exactly k steps; x_k and L^-T y_k must agree to
+    rounding for k = 1..4 and a general (non-diagonal) L.  A beta from
+    r^T r instead of r^T z, M^-1 applied as L^-1 alone, or a search
+    direction built from r instead of z each break the agreement (checked
+    by planting each slip in a copy of the oracle)."""
+    rng = np.random.default_rng(17)
+    n = 8
+    G = rng.standard_normal((n, n))
+    A = G @ G.T + n * np.eye(n)
+    L = np.tril(rng.standard_normal((n, n)) * 0.3) + np.diag(1.0 + rng.random(n))
+    b = rng.standard_normal(n)
+    Li = np.linalg.inv(L)
+    Ah = Li @ A @ Li.T
+    Ah = 0.5 * (Ah + Ah.T)
+    bh = Li @ b
+    for k in range(1, 5):
+        x, it, _ = oracle.pcg(A, L, b, bwd_tol=0.0, eps=0.0, maxit=k, R=0)
+        y, itc, _ = oracle.cg(Ah, bh, 0.0, k, R=0)
+        assert it == -k and itc == k
+        xr = Li.T @ y
+        assert np.abs(x - xr).max() <= 1e-11 * np.abs(xr).max()
+
+
 def test_pcg_exact_preconditioner_one_step():
     sysm = inputs.gp_system(100, 8, 0.5, 1e-2, seed=6)
     A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
