@@ -50,6 +50,23 @@ CPU_SAMPLE_N = 4096
 SYRK_DRAM_BYTES_PER_FLOP = 1.841e-3
 
 
+def ranks_max(v: float, dist=None, device: str = "cuda") -> float:
+    """Largest v over the ranks of the default process group (v itself
+    without one): a replicated step takes as long as its slowest rank."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job rate of `world` replicas that each did units_per_rank of
+    work in at most `seconds` (the slowest rank's time): weak scaling."""
+    return world * units_per_rank / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -238,11 +255,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks_max(v, dist, "cuda")
 
     n, tile = args.n, args.tile
     sysm = inputs.config2(n) if rank == 0 else inputs.gp_system(n, 8, 0.5, 1e-3, nrhs=1, seed=2 + 1000 * rank)
@@ -284,7 +297,7 @@ def main():
              "solve": gpchol.PHASE_SOLVE, "cg_matvec": gpchol.PHASE_CG_MATVEC}
     phase = {k: ctx.timing_read(v) for k, v in names.items()}
     ctx.timing_enable(False)
-    value = world * flops / (ms / 1e3) / 1e9
+    value = replica_rate(flops, ms / 1e3, world) / 1e9
     res = last["res"]
 
     # result check outside the timed region: FP64 backward error of x
