@@ -310,14 +310,14 @@ gpch_status upload(gpch_ctx *ctx, const Layout &L, int count, const gpch_system 
 
 gpch_status set_attrs(gpch_ctx *ctx)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static gpch::DeviceOnce attr_once;
+    GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(bpotrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)BPOTRF_SMEM));
         GPCH_CUDA(ctx, cudaFuncSetAttribute(btrsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)BTRSM_SMEM));
-        attr_done = true;
-    }
+        return GPCH_OK;
+    }));
     return GPCH_OK;
 }
 

@@ -794,12 +794,12 @@ template <typename T, int ROWS>
 inline gpch_status launch_trsm_rows(gpch_ctx *ctx, T *B, int64_t ldb, int64_t m, int nc, const double *Linv,
                                     const int64_t *info, cudaStream_t st)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static gpch::DeviceOnce attr_once;
+    GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(trsm_inv_kernel<T, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)trsm_smem_bytes<T, ROWS>()));
-        attr_done = true;
-    }
+        return GPCH_OK;
+    }));
     trsm_inv_kernel<T, ROWS><<<(unsigned)((m + ROWS - 1) / ROWS), 256, trsm_smem_bytes<T, ROWS>(), st>>>(
         B, ldb, m, nc, Linv, info);
     GPCH_LAUNCH_CHECK(ctx);

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "../../include/gpchol.h"
@@ -137,3 +138,30 @@ struct PhaseScope {
     do {                                                                            \
         if (!(cond)) return gpch::fail((ctx), GPCH_INVALID_ARG, "%s", (msg));       \
     } while (0)
+
+namespace gpch {
+
+// One-time set-up per device for one call site (a kernel's shared-memory
+// limit, say): cudaFuncSetAttribute applies to the current device only,
+// and contexts on several host threads may reach the site together.  set()
+// runs under the site's mutex the first time a context of a device gets
+// here (every time for device numbers past 63); a failure leaves the device
+// unmarked.
+struct DeviceOnce {
+    std::mutex mu;
+    bool done[64] = {};
+};
+
+template <typename F>
+inline gpch_status once_per_device(gpch_ctx *ctx, DeviceOnce &once, F &&set)
+{
+    std::lock_guard<std::mutex> lock(once.mu);
+    const int d = ctx->device;
+    const bool tracked = d >= 0 && d < 64;
+    if (tracked && once.done[d]) return GPCH_OK;
+    GPCH_CHECK(set());
+    if (tracked) once.done[d] = true;
+    return GPCH_OK;
+}
+
+}  // namespace gpch

@@ -1009,11 +1009,11 @@ gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float
     if (tk0 >= tk1) return GPCH_OK;
     CUtensorMap ma;
     GPCH_CHECK(make_panel_map(ctx, &ma, buf.hi, m, kpos(split, k_off + kp), buf.ld, f16));
-    static bool attr_done = false;
-    if (!attr_done) {
+    static gpch::DeviceOnce attr_once;
+    GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        attr_done = true;
-    }
+        return GPCH_OK;
+    }));
     auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
     const int64_t tiles = offset(tk1) - offset(tk0);
     // algorithmic work: the lower-triangle entries of the updated columns
@@ -1051,12 +1051,12 @@ gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, fl
     CUtensorMap mp, mq;
     GPCH_CHECK(make_panel_map(ctx, &mp, pb.hi, m, kpos(true, kp), pb.ld, true));
     GPCH_CHECK(make_panel_map(ctx, &mq, qb.hi, nq, kpos(true, kp), qb.ld, true));
-    static bool attr_done = false;
-    if (!attr_done) {
+    static gpch::DeviceOnce attr_once;
+    GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        attr_done = true;
-    }
+        return GPCH_OK;
+    }));
     const int64_t tr = (m + BM - 1) / BM, tc = (nq + BN - 1) / BN;
     auto kern = subtract ? syrk_tc_kernel<2> : syrk_tc_kernel<1>;
     const int prefetch_c = (subtract && (uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;

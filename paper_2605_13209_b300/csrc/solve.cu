@@ -710,12 +710,12 @@ gpch_status solve_prepare_t(gpch_ctx *ctx, int64_t n, const TL *L, int64_t ldl, 
 {
     const int64_t N = (n + LEAF - 1) / LEAF;
     constexpr size_t INV_SMEM = 2 * LEAF * (LEAF + 1) * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
+    static gpch::DeviceOnce attr_once;
+    GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(inv_diag_blocks_kernel<TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)INV_SMEM));
-        attr_done = true;
-    }
+        return GPCH_OK;
+    }));
     inv_diag_blocks_kernel<TL>
         <<<(unsigned)N, 256, INV_SMEM, st>>>(n, L, ldl, reinterpret_cast<sweep_math_t<TL> *>(w.Linv));
     GPCH_LAUNCH_CHECK(ctx);
