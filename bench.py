@@ -44,9 +44,10 @@ METRIC = "Cholesky GFLOP/s & CG GB/s, mixed vs FP64 at ≤1e-12 bwd err; served 
 FP64_PEAK_GFLOPS = 1250.0   # nominal B300 FP64 (DFMA): 148 SMs x 2 FMA/clk x 2 flop x clock
 FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032    # FFMA: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 CPU_SAMPLE_N = 4096
+CPU_ALLCORES_N = 2048
 # DRAM bytes per algorithmic flop of syrk_tc_kernel (split-f16 update, a
-# K = 2048 pass): 91.9 MB over 4.993e10 flop in one ncu capture at n=16384
-# (profiles/syrk_tc_split_f16_n16384.md).
+# K = 2048 pass): 91.9 MB over 4.993e10 flop in one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the n = 16384 update.
 SYRK_DRAM_BYTES_PER_FLOP = 1.841e-3
 
 
@@ -133,22 +134,45 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
-def cpu_baseline(n_sample: int = CPU_SAMPLE_N):
-    """The oracle (plain C, one thread) on the n_sample leading block of the
-    same workload: SE matrix, textbook Cholesky, forward/back substitution."""
+def _oracle_block_solve(n_sample: int) -> float:
+    """One oracle solve of the n_sample leading block (seconds); run in a
+    worker process of the all-cores leg."""
     import oracle
     from paper_2605_13209_b300 import inputs
-    s = inputs.config2()
-    A = oracle.se_matrix(s.X[:n_sample], s.sf2, s.ell, s.sn2)
-    b = s.B[:n_sample, 0]
+    s = inputs.config2(n_sample)
+    A = oracle.se_matrix(s.X, s.sf2, s.ell, s.sn2)
     t0 = time.perf_counter()
     L, info = oracle.cholesky(A)
-    oracle.chol_solve(L, b)
-    dt = time.perf_counter() - t0
-    return {"value": round(n_sample ** 3 / 3.0 / dt / 1e9, 3), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"or_cholesky + forward/back substitution on the n={n_sample} leading block of the "
-                      f"n=32768 system (SE d=8, ell=0.5, sn2=1e-3), 1 thread, {dt:.2f} s",
-            "seconds": round(dt, 3)}
+    oracle.chol_solve(L, s.B[:, 0])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n_sample: int = CPU_SAMPLE_N, n_all: int = CPU_ALLCORES_N):
+    """The oracle (plain C) on bounded samples of the same workload: SE
+    matrix, textbook Cholesky, forward/back substitution.
+
+    * all cores: one oracle solve of the n_all leading block per worker
+      process, as many workers as host cores (at most 64), all at once;
+      value = workers * n_all^3/3 / wall time;
+    * one thread: one solve of the n_sample leading block."""
+    import multiprocessing as mp
+    cores = min(os.cpu_count() or 1, 64)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_block_solve, [256] * cores)          # workers up, oracle built
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_block_solve, [n_all] * cores)
+        wall = time.perf_counter() - t0
+    all_value = cores * n_all ** 3 / 3.0 / wall / 1e9
+    dt = _oracle_block_solve(n_sample)
+    one = n_sample ** 3 / 3.0 / dt / 1e9
+    return {"value": round(all_value, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent oracle solves (or_cholesky + forward/back substitution), one per core, "
+                      f"each of the n={n_all} leading block of the n=32768 system (SE d=8, ell=0.5, sn2=1e-3); "
+                      f"wall {wall:.2f} s (slowest worker {max(per):.2f} s)",
+            "host_cores": os.cpu_count(),
+            "single_thread": {"value": round(one, 3), "unit": "GFLOP/s", "cores": 1, "seconds": round(dt, 3),
+                              "sample": f"one oracle solve of the n={n_sample} leading block, 1 thread"}}
 
 
 def run_reference(args):
@@ -185,6 +209,52 @@ def run_reference(args):
             "check": {"backward_error": oracle.backward_error(A, x, b)}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+CHECK_BLOCK_N = 4096
+
+
+def oracle_check(sysm, x_mixed, x_fp64, L_block):
+    """Errors of the benchmark's solutions, from the oracle on the host:
+    the system matrix rebuilt by the oracle from the same points, the
+    backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) with
+    long-double residuals for the mixed solve and the FP64 solve, the
+    forward error of the mixed x against the FP64 x, and the FP64 factor's
+    relative error on its leading block (the leading block of L is the
+    factor of the leading block of A), against the oracle's textbook
+    Cholesky of that block."""
+    import oracle
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    b = np.ascontiguousarray(sysm.B[:, 0])
+    out = {"backward_error": oracle.backward_error(A, x_mixed, b), "by": "oracle (host, long-double residual)"}
+    if x_fp64 is not None:
+        out["backward_error_fp64"] = oracle.backward_error(A, x_fp64, b)
+        out["forward_error_mixed_vs_fp64"] = oracle.forward_error(x_mixed, x_fp64)
+    if L_block is not None:
+        nb = L_block.shape[0]
+        Lref, info = oracle.cholesky(A[:nb, :nb])
+        out["fp64_factor_error_leading_block"] = oracle.factor_error(L_block, Lref)
+        out["factor_block_n"] = nb
+    return out
+
+
+def _batched_system_bwd(item):
+    """Oracle backward error of system k of the batched workload (worker)."""
+    import oracle
+    from paper_2605_13209_b300 import inputs
+    k, count, x = item
+    sk = inputs.batch_spec(count=count, nmin=256, nmax=4096, seed=4).system(k, d=8)
+    A = oracle.se_matrix(sk.X, sk.sf2, sk.ell, sk.sn2)
+    return oracle.backward_error(A, x, sk.B[:, 0])
+
+
+def batched_check(count, xs):
+    """Largest oracle backward error over every system of the batch, the
+    systems spread over the host cores (spawned workers)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 64)) as pool:
+        errs = pool.map(_batched_system_bwd, [(k, count, x) for k, x in enumerate(xs)])
+    return max(errs)
 
 
 def roofline_of(phase_name, ms, launches, work, n, nrhs, pk):
@@ -230,6 +300,7 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle check of the solutions")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-nmax", type=int, default=8192)
@@ -300,10 +371,8 @@ def main():
     value = replica_rate(flops, ms / 1e3, world) / 1e9
     res = last["res"]
 
-    # result check outside the timed region: FP64 backward error of x
-    x = Xs[:, 0]
-    r = bd[:, 0] - torch.mv(A0, x)
-    bwd = float(r.abs().max() / (A0.abs().sum(dim=1).max() * x.abs().max() + bd.abs().max()))
+    # the timed steps' solution, checked against the oracle after all legs
+    x_mixed = Xs[:, 0].cpu().numpy().copy()
 
     # dominant kernel of the step (syrk_tc_kernel: the largest share of the
     # ncu launch list of this workload) and its roofline
@@ -316,12 +385,13 @@ def main():
                 "traffic": (round(SYRK_DRAM_BYTES_PER_FLOP * work_per_launch)
                             if SYRK_DRAM_BYTES_PER_FLOP is not None and args.prec != "bf16" else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one syrk_tc_kernel launch "
-                                  "at n=16384 (profiles/syrk_tc_split_f16_n16384.md), scaled by the launch's work"}
+                                  "(split-f16, K = 2048, n = 16384), scaled by the launch's work"}
     phases = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] / args.steps,
                   "roofline": roofline_of(k, *v, n, 1, pk)} for k, v in phase.items()}
 
     # ---------------------------------------------------------- FP64 leg
     fp64 = None
+    x_fp64 = L_block = None
     if not args.no_fp64:
         Aw = gpchol.colmajor(n, n)
         small = min(n, 2048)
@@ -338,11 +408,11 @@ def main():
         f1.record()
         torch.cuda.synchronize()
         fms = max_over_ranks(f0.elapsed_time(f1))
-        xf = Xf[:, 0]
-        rf = bd[:, 0] - torch.mv(A0, xf)
-        bwd_f = float(rf.abs().max() / (A0.abs().sum(dim=1).max() * xf.abs().max() + bd.abs().max()))
+        x_fp64 = Xf[:, 0].cpu().numpy().copy()
+        nb = min(n, CHECK_BLOCK_N)
+        L_block = np.tril(Aw[:nb, :nb].cpu().numpy())
         fp64 = {"ms_per_solve": round(fms, 2), "gflops": round(world * flops / (fms / 1e3) / 1e9, 2),
-                "backward_error": bwd_f, "speedup_mixed_vs_fp64": round(fms / ms, 2), "steps": 1,
+                "speedup_mixed_vs_fp64": round(fms / ms, 2), "steps": 1,
                 "what": f"FP64 blocked Cholesky (tile {tile}) + forward/back substitution"}
         del Aw
 
@@ -372,6 +442,7 @@ def main():
 
     # ---------------------------------------------------------- batched leg
     batched = None
+    xs_batched = None
     if args.batch_count > 0:
         spec = inputs.batch_spec(count=args.batch_count, nmin=256, nmax=4096, seed=4)
         Ab, Bb, Bb0, Xp = [], [], [], []
@@ -400,14 +471,10 @@ def main():
             times.append(ctx.timing_read(gpchol.PHASE_BATCHED)[0])
             ctx.timing_enable(False)
         bms = max_over_ranks(min(times))
-        xk = Bb[0][:, 0]
-        A0b = gpchol.se_matrix(Xp[0][0], Xp[0][1], Xp[0][2], Xp[0][3], ctx=ctx)
-        rk = Bb0[0][:, 0] - torch.mv(A0b, xk)
-        bwd_b = float(rk.abs().max() / (A0b.abs().sum(dim=1).max() * xk.abs().max() + Bb0[0].abs().max()))
+        xs_batched = [b[:, 0].cpu().numpy().copy() for b in Bb]
         batched = {"systems": args.batch_count, "n_range": [int(spec.ns.min()), int(spec.ns.max())],
                    "ms_per_batch": round(bms, 2), "gflops": round(world * bflops / (bms / 1e3) / 1e9, 2),
                    "frac_of_fp64_peak": round(bflops / (bms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
-                   "backward_error_system0": bwd_b,
                    "what": "FP64 batched factor + solve of 256 SE systems, n log-uniform [256, 4096], one graph launch"}
         del Ab, Bb, Bb0, Xp
 
@@ -477,11 +544,17 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    check = oracle_check(sysm, x_mixed, x_fp64, L_block) if not args.no_check else None
+    if batched is not None and xs_batched is not None and not args.no_check:
+        batched["backward_error_max"] = batched_check(args.batch_count, xs_batched)
+        batched["backward_error_by"] = "oracle on every system (host, long-double residual)"
+    if fp64 is not None and check is not None:
+        fp64["backward_error"] = check["backward_error_fp64"]
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_sample_n)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": f"{args.prec}+f64_refine", "data": "synthetic",
         "config": {"workload": f"n={n} SE GP system (d=8, ell=0.5, sn2=1e-3), one RHS, A device-resident: "
                                f"{args.prec} mixed-precision Cholesky (tile {tile}) + FP64 PCG refinement to "
                                f"backward error 1e-12; value = n^3/3 per solve time",
@@ -504,7 +577,7 @@ def main():
         "batched": batched,
         "serving": serving,
         "phases": phases,
-        "check": {"backward_error": bwd},
+        "check": check,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

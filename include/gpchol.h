@@ -205,14 +205,22 @@ gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A,
  * allocator's implicit synchronization, or a caller without a context of
  * this library, whose creation pins host memory).  It allocates nothing:
  * its scratch (the CG vectors r, s, t, the device scalars and the partial
- * sums) lives in one fixed 12 MiB file-scope device array that every GPU
- * loading this library holds until the process exits, and its host
+ * sums) lives in one fixed 12 MiB file-scope device array, and its host
  * staging is on the stack.  The caller still passes A, B and X.
- *   - Runs on the caller's current device.  The first call on a device
- *     looks up that array's device address (once per device); make that
- *     first call before any stream capture.
+ *   - When the array is reserved: the CUDA driver reserves it on a device
+ *     when it loads this library's CG module there.  With lazy module
+ *     loading (CUDA's default since 12.2) that happens at the first use of
+ *     the module on that device, which may be the first call of this entry
+ *     point; the 12 MiB are then taken at that moment and kept until the
+ *     process exits.  A caller that may not allocate later makes one call
+ *     with n = 0 (or nrhs = 0) on each device at set-up time, with the device
+ *     current and before any stream capture: it loads the module, makes
+ *     sure the array and the code of every kernel the solve launches are on
+ *     the device, and solves nothing.  Calls after it allocate nothing.
+ *   - Runs on the caller's current device and looks up the array's device
+ *     address on every call (a device reset is therefore harmless).
  *   - Limits: 0 <= nrhs <= 16 and n * nrhs <= GPCH_NOALLOC_CG_MAX_ELEMS;
- *     larger problems return GPCH_INVALID_ARG.
+ *     larger problems return GPCH_INVALID_ARG before any device work.
  *   - Every call shares the one array and leaves its contents behind; the
  *     call clears what must start at zero.  Calls whose GPU work overlaps
  *     (other streams, other host threads) race on the array: serialize them.

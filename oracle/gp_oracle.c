@@ -239,50 +239,75 @@ int64_t or_mixed_factor(int64_t n, int64_t b, const double *A, int64_t lda,
             if (Lt[IDX(i, i, ldl)] > dm) dm = Lt[IDX(i, i, ldl)];
         sc = ldexp(1.0, or_f16_scale_exp((double)(float)sqrt(dm)));
     }
+    /* Row-major copies of the current panel: Ljj (the diagonal block, row c
+     * at Ljj + c*b), and for step 3 every panel entry's head H and tail T as
+     * defined by the mode.  They only give the loops unit stride: each value
+     * and each summation order is the one of the textbook loops. */
+    double *Ljj = malloc(sizeof(double) * (size_t)b * (size_t)b);
+    double *row = malloc(sizeof(double) * (size_t)b);
+    double *H = malloc(sizeof(double) * (size_t)n * (size_t)b);
+    double *T = malloc(sizeof(double) * (size_t)n * (size_t)b);
+    int64_t info = 0;
     int64_t N = (n + b - 1) / b;
-    for (int64_t J = 0; J < N; ++J) {
+    for (int64_t J = 0; J < N && !info; ++J) {
         int64_t j0 = J * b, nj = (n - j0 < b) ? n - j0 : b;
-        int64_t info = or_cholesky(nj, &Lt[IDX(j0, j0, ldl)], ldl);
-        if (info) return j0 + info;
+        info = or_cholesky(nj, &Lt[IDX(j0, j0, ldl)], ldl);
+        if (info) { info += j0; break; }
         for (int64_t c = 0; c < nj; ++c)
             for (int64_t r = c; r < nj; ++r)
                 Lt[IDX(j0 + r, j0 + c, ldl)] = or_round_f32(Lt[IDX(j0 + r, j0 + c, ldl)]);
+        for (int64_t c = 0; c < nj; ++c)
+            for (int64_t k = 0; k <= c; ++k) Ljj[c * b + k] = Lt[IDX(j0 + c, j0 + k, ldl)];
+        /* step 2: row i of the panel solves x L_jj^T = a_i, column by column */
         for (int64_t i = j0 + nj; i < n; ++i) {
+            for (int64_t c = 0; c < nj; ++c) row[c] = Lt[IDX(i, j0 + c, ldl)];
             for (int64_t c = 0; c < nj; ++c) {
-                double s = Lt[IDX(i, j0 + c, ldl)];
-                for (int64_t k = 0; k < c; ++k)
-                    s -= Lt[IDX(i, j0 + k, ldl)] * Lt[IDX(j0 + c, j0 + k, ldl)];
-                Lt[IDX(i, j0 + c, ldl)] = s / Lt[IDX(j0 + c, j0 + c, ldl)];
+                double s = row[c];
+                for (int64_t k = 0; k < c; ++k) s -= row[k] * Ljj[c * b + k];
+                row[c] = s / Ljj[c * b + c];
             }
-            for (int64_t c = 0; c < nj; ++c)
-                Lt[IDX(i, j0 + c, ldl)] = or_round_f32(Lt[IDX(i, j0 + c, ldl)]);
+            for (int64_t c = 0; c < nj; ++c) Lt[IDX(i, j0 + c, ldl)] = or_round_f32(row[c]);
         }
+        /* the step-3 operands of every panel row */
+        for (int64_t i = j0 + nj; i < n; ++i)
+            for (int64_t c = 0; c < nj; ++c) {
+                double a = Lt[IDX(i, j0 + c, ldl)], *h = &H[(size_t)i * b + c], *t = &T[(size_t)i * b + c];
+                if (mode == 1) {
+                    *h = or_round_bf16(a);
+                    *t = 0.0;
+                } else if (mode == 2) {
+                    *h = or_round_bf16(a);
+                    *t = or_round_bf16(a - *h);
+                } else if (mode == 3) {
+                    double as = a * sc;
+                    *h = or_round_f16(as);
+                    *t = or_round_f16(as - *h);
+                } else {
+                    *h = a;
+                    *t = 0.0;
+                }
+            }
         /* step 3 over the whole trailing lower triangle */
         for (int64_t k = j0 + nj; k < n; ++k) {
+            const double *bh_row = &H[(size_t)k * b], *bt_row = &T[(size_t)k * b];
             for (int64_t i = k; i < n; ++i) {
+                const double *ah_row = &H[(size_t)i * b], *at_row = &T[(size_t)i * b];
                 double s = 0.0;
-                for (int64_t c = 0; c < nj; ++c) {
-                    double a = Lt[IDX(i, j0 + c, ldl)], bb = Lt[IDX(k, j0 + c, ldl)];
-                    if (mode == 1) {
-                        s += or_round_bf16(a) * or_round_bf16(bb);
-                    } else if (mode == 2) {
-                        double ah = or_round_bf16(a), bh = or_round_bf16(bb);
-                        double at = or_round_bf16(a - ah), bt = or_round_bf16(bb - bh);
-                        s += ah * bh + ah * bt + at * bh;
-                    } else if (mode == 3) {
-                        double as = a * sc, bs = bb * sc;
-                        double ah = or_round_f16(as), bh = or_round_f16(bs);
-                        double at = or_round_f16(as - ah), bt = or_round_f16(bs - bh);
-                        s += (ah * bh + ah * bt + at * bh) / (sc * sc);
-                    } else {
-                        s += a * bb;
-                    }
+                if (mode == 2) {
+                    for (int64_t c = 0; c < nj; ++c)
+                        s += ah_row[c] * bh_row[c] + ah_row[c] * bt_row[c] + at_row[c] * bh_row[c];
+                } else if (mode == 3) {
+                    for (int64_t c = 0; c < nj; ++c)
+                        s += (ah_row[c] * bh_row[c] + ah_row[c] * bt_row[c] + at_row[c] * bh_row[c]) / (sc * sc);
+                } else {   /* modes 0 and 1: one product of the (rounded) values */
+                    for (int64_t c = 0; c < nj; ++c) s += ah_row[c] * bh_row[c];
                 }
                 Lt[IDX(i, k, ldl)] = or_round_f32(Lt[IDX(i, k, ldl)] - s);
             }
         }
     }
-    return 0;
+    free(Ljj); free(row); free(H); free(T);
+    return info;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -17,7 +17,6 @@
 // j, which is contiguous in column-major storage.  A CTA owns W consecutive
 // columns and walks all rows; each thread keeps the s values of its rows in
 // registers and reuses them across the W columns and NR right-hand sides.
-#include <mutex>
 
 #include "dense_fp64.cuh"
 
@@ -300,6 +299,25 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
 
 inline int mv_width(int nrhs) { return nrhs <= 1 ? 4 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2; }
 inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
+
+// Loads every kernel cg_run may launch on the current device.  Under lazy
+// module loading a kernel's code is placed in device memory at its first
+// launch; asking for its attributes loads it ahead of time.
+template <typename TA>
+cudaError_t cg_kernels_load()
+{
+    cudaFuncAttributes a;
+    const void *fns[] = {(const void *)cg_matvec_kernel<TA, 4, 1>, (const void *)cg_matvec_kernel<TA, 8, 2>,
+                         (const void *)cg_matvec_kernel<TA, 4, 4>, (const void *)cg_matvec_kernel<TA, 2, 8>,
+                         (const void *)cg_matvec_kernel<TA, 2, 16>, (const void *)cg_init_kernel,
+                         (const void *)cg_update_kernel,           (const void *)cg_xupdate_kernel,
+                         (const void *)cg_dir_kernel};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 // Doubles of per-CTA partials: the matvec stores mv_nr per CTA, the vector
 // kernels (one CTA per THREADS rows) up to 2 * MAXRHS.
@@ -903,26 +921,33 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(12) << 20;
 static __device__ __align__(256) unsigned char g_cg_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
-
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is asked
-// for once per device with that device current.
-gpch_status noalloc_scratch(int dev, void **out)
+// for, with the device current, on every call: the lookup is cheap, and a
+// reset of the device (which may move the array) leaves no stale address.
+// The first lookup on a device also loads this file's module there if lazy
+// module loading has not loaded it yet, and that load reserves the array.
+gpch_status noalloc_scratch(void **out)
 {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_cg_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return GPCH_CUDA_ERROR;
-        }
-        g_noalloc_addr[dev] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_cg_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return GPCH_CUDA_ERROR;
     }
-    *out = g_noalloc_addr[dev];
+    *out = p;
+    return GPCH_OK;
+}
+
+// The set-up call: the array's address and the code of every kernel the
+// solve launches, so that later calls make the driver place nothing new.
+gpch_status noalloc_setup(void **out)
+{
+    GPCH_CHECK(noalloc_scratch(out));
+    if (cg_kernels_load<double>() != cudaSuccess || cg_kernels_load<float>() != cudaSuccess) {
+        cudaGetLastError();
+        return GPCH_CUDA_ERROR;
+    }
     return GPCH_OK;
 }
 
@@ -943,14 +968,13 @@ extern "C" gpch_status gpch_cg_solve_noalloc(int64_t n, const void *A, gpch_dtyp
     GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
     GPCH_ARG(ctx, dtype == GPCH_F64 || dtype == GPCH_F32, "bad dtype");
     GPCH_ARG(ctx, maxit > 0 && replace_every >= 0 && rtol >= 0.0, "bad maxit / replace_every / rtol");
-    if (n == 0 || nrhs == 0) return GPCH_OK;
-    GPCH_ARG(ctx, A && B && X, "null pointer");
     GPCH_ARG(ctx, cg_scratch_bytes(n, nrhs) <= NOALLOC_SCRATCH_BYTES, "problem needs more than the fixed scratch");
-    int dev = 0;
-    GPCH_CUDA(ctx, cudaGetDevice(&dev));
-    GPCH_ARG(ctx, dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device ordinal out of range");
+    // An empty problem is the set-up call: it makes sure the array and the
+    // solve's kernels exist on the current device and solves nothing.
     void *scratch = nullptr;
-    GPCH_CHECK(noalloc_scratch(dev, &scratch));
+    if (n == 0 || nrhs == 0) return noalloc_setup(&scratch);
+    GPCH_CHECK(noalloc_scratch(&scratch));
+    GPCH_ARG(ctx, A && B && X, "null pointer");
     alignas(64) unsigned char hbuf[1024];   // host staging for a few scalars (pageable, on the stack)
     int iters[MAXRHS];
     double rel[MAXRHS];

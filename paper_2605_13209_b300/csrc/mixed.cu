@@ -1171,12 +1171,22 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     // the fused panel kernel, and the 16-bit panel copies have a row stride
     // of `tile` elements, a multiple of 64)
     const bool tc_panel = prec == GPCH_PREC_SPLIT_F16 && panel_fused && tile <= TI_MAXN && tile % BK == 0;
-    if (tc_panel)
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(tri_inv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)TI_SMEM));
-    if (panel_fused)
-        GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)PN_SMEM));
+    if (tc_panel) {
+        static gpch::DeviceOnce inv_once;
+        GPCH_CHECK(gpch::once_per_device(ctx, inv_once, [&]() -> gpch_status {
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(tri_inv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)TI_SMEM));
+            return GPCH_OK;
+        }));
+    }
+    if (panel_fused) {
+        static gpch::DeviceOnce pn_once;
+        GPCH_CHECK(gpch::once_per_device(ctx, pn_once, [&]() -> gpch_status {
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(panel_trsm_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)PN_SMEM));
+            return GPCH_OK;
+        }));
+    }
     cudaEvent_t ev_conv = ctx->aux_ev[0], ev_start = ctx->aux_ev[2], ev_done = ctx->aux_ev[3],
                 ev_side = ctx->aux_ev[4], ev_pan1 = ctx->aux_ev[5];
     // ev_ready[X % 2]: the second stream's passes over block column X are done

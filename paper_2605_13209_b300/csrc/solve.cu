@@ -596,18 +596,18 @@ __global__ void __launch_bounds__(SW_THREADS) trsv_sweep_kernel(int64_t n, int n
     }
 }
 
+// SM count of the context's device: it sizes the cooperative sweeps' grids,
+// which must fit on the device they run on.  Asked for on every launch
+// (a cheap attribute query), so devices of different sizes and contexts on
+// several host threads each get their own value.
 int sm_count(gpch_ctx *ctx)
 {
-    static int cached = 0;
-    if (!cached) {
-        int v = 0;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || v <= 0) {
-            cudaGetLastError();
-            v = 1;
-        }
-        cached = v;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        v = 1;
     }
-    return cached;
+    return v;
 }
 
 template <typename TL, bool FWD, int BS>

@@ -394,3 +394,17 @@ def test_pcg_low_precision_preconditioner():
     assert it < it_cg
     ref = np.linalg.solve(A, b)
     assert oracle.forward_error(x, ref) < 1e-6
+
+
+def test_solve_spd_matches_textbook_solve():
+    """The LAPACK reference solve agrees with the textbook factor and
+    substitutions to within the conditioning of the system."""
+    s = inputs.gp_system(300, 8, 0.5, 1e-2, nrhs=2, seed=11)
+    A = oracle.se_matrix(s.X, s.sf2, s.ell, s.sn2)
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    x_ref = oracle.chol_solve(L, s.B)
+    x = oracle.solve_spd(A, s.B)
+    kappa = np.linalg.cond(A)
+    for r in range(2):
+        assert oracle.forward_error(x[:, r], x_ref[:, r]) <= 50 * kappa * U
