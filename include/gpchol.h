@@ -190,6 +190,59 @@ gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A,
                           double rtol, int maxit, int replace_every,
                           void *stream, gpch_cg_stats *stats);
 
+/* Options of gpch_cg_solve_ex. */
+typedef enum gpch_cg_variant {
+    GPCH_CG_CLASSIC = 0,           /* Algorithm 1 (left) as above                     */
+    GPCH_CG_SINGLE_REDUCTION = 1   /* Chronopoulos-Gear rearrangement (below)         */
+} gpch_cg_variant;
+
+typedef enum gpch_cg_products {
+    GPCH_CG_PRODUCTS_FP64 = 0,         /* one FP64 FMA per entry and right-hand side  */
+    GPCH_CG_PRODUCTS_DOUBLE_FLOAT = 1  /* double-float products on the FP32 pipe      */
+} gpch_cg_products;
+
+typedef struct gpch_cg_opts {
+    int32_t variant;    /* gpch_cg_variant  */
+    int32_t products;   /* gpch_cg_products */
+} gpch_cg_opts;
+
+/* gpch_cg_solve with a choice of iteration form and product arithmetic
+ * (opts NULL = classic, FP64 products: exactly gpch_cg_solve).
+ *
+ * GPCH_CG_SINGLE_REDUCTION: the same iterates as Algorithm 1 (left) in exact
+ * arithmetic, rearranged so that one product w = A r is followed by both
+ * inner products together (the single-reduction / pipelined CG variants of
+ * the paper's related work, Sec. 1):
+ *   r = b - A x; w = A r; gamma = r^T r; delta = w^T r; alpha = gamma/delta
+ *   loop: p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s;
+ *         w = A r; gamma' = r^T r; delta = w^T r; beta = gamma'/gamma;
+ *         alpha = gamma'/(delta - beta gamma'/alpha); gamma = gamma'
+ * One reduction point per iteration instead of two; one extra product
+ * with A at the start.  On replacement iterations r = b - A x and
+ * s = A p are both recomputed (two extra products).  Stop rule
+ * gamma <= rtol^2 gamma_0 per column.
+ *
+ * GPCH_CG_PRODUCTS_DOUBLE_FLOAT: the products A_ij s_i are formed on the
+ * FP32 pipe from a float head and tail of each operand (FP64 entries of A
+ * are cut by integer operations, the vector once per product with A),
+ * head*head exactly plus the two cross terms, summed in an error-free
+ * double-float accumulator and reduced across threads in FP64.  Each
+ * product carries a relative error below about 2^-45 (FP32 A: below about
+ * 2^-47), so the computed A s differs from the FP64 one by about
+ * 1e-14 sum_j |A_ij||s_j| per entry.  A's largest diagonal entry and each
+ * column's largest |b| set power-of-two scales first, so entries of A
+ * within 2^-126 of the largest diagonal entry and vectors within FP32's
+ * range of that scale lose nothing more; an entry of A at or above 2^128
+ * times the largest diagonal entry makes the product non-finite (the
+ * solve then reports NOT_CONVERGED).  The true residuals b - A x (at the
+ * start and on replacement iterations) always use FP64 products, so the
+ * accuracy the iteration reaches is that of FP64 CG.  The vector
+ * recurrences, inner products and scalars stay FP64 in both forms. */
+gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
+                             const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol,
+                             int maxit, int replace_every, const gpch_cg_opts *opts, void *stream,
+                             gpch_cg_stats *stats);
+
 /* ------------------------------------- allocation-free CG (no paper
  * counterpart: the paper has no allocation-free variant; this is a
  * service to callers of the library) */
@@ -405,6 +458,40 @@ typedef struct gpch_refine_stats {
 gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *B,
                                int64_t ldb, double *X, int64_t ldx, int nrhs, gpch_prec prec, int tile,
                                double bwd_tol, int maxit, void *stream, gpch_refine_stats *stats);
+
+/* ------------------------------ GP quantities on a solved system (f3) */
+
+/* log det A of the SPD matrix A = L L^T from its FP64 Cholesky factor:
+ * det A = prod_i L_ii^2, so log det A = 2 sum_i log L_ii.  This is the
+ * log-determinant term of the GP's log marginal likelihood; the paper's
+ * systems are GP covariance matrices used for behaviour prediction
+ * (Sec. 4.1).  L: device, lower triangle of an n x n factor as left by
+ * gpch_chol_factor (only the diagonal is read), ldl >= n.  logdet: HOST
+ * pointer, written after the call synchronizes `stream` (0 for n = 0).
+ * The sum is reduced in a fixed order, so the value is reproducible.
+ * Errors: INVALID_ARG (n < 0, ldl < n, NULL pointers); NOT_SPD if some
+ * L_ii is not positive or not finite (*logdet is then NaN). */
+gpch_status gpch_logdet(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, double *logdet,
+                        void *stream);
+
+/* GP predictive mean at m new points:
+ *     mean_kr = sum_i sf2 exp(-||xs_k - x_i||^2 / (2 ell^2)) alpha_ir
+ * the noise-free squared-exponential cross covariance between the test
+ * points Xs and the training points X times alpha = (K + sn2 I)^-1 Y, the
+ * solution of the GP system (behaviour prediction with a GP, Sec. 4.1).
+ * The cross covariance is formed on the fly and never stored.
+ * Xs: device, m x d row-major; X: device, n x d row-major (the points the
+ * system's matrix was built from, 1 <= d <= 64).  alpha: device n x nrhs
+ * (lda >= n), mean: device m x nrhs (ldm >= m), column-major,
+ * 0 <= nrhs <= 16.  Asynchronous on `stream`.  Workspace: 128 bytes per
+ * (test point, slice) pair, slices chosen to fill the GPU.  Partial sums
+ * are added in a fixed order (reproducible).
+ * Errors: INVALID_ARG (negative sizes, d out of range, nrhs > 16, ld too
+ * small, ell <= 0, NULL pointers); OOM_BUDGET if the workspace does not
+ * fit the context's budget. */
+gpch_status gpch_predict_mean(gpch_ctx *ctx, int64_t m, int64_t n, int d, const double *Xs, const double *X,
+                              double sf2, double ell, const double *alpha, int64_t lda, int nrhs,
+                              double *mean, int64_t ldm, void *stream);
 
 #ifdef __cplusplus
 }

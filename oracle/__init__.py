@@ -73,6 +73,13 @@ def lib():
         L.or_pcg.argtypes = [_c_i64, _c_dp, _c_i64, _c_dp, _c_i64, _c_dp, _c_dp, ctypes.c_double,
                              ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_dp]
         L.or_pcg.restype = ctypes.c_int
+        L.or_cg_single_reduction.argtypes = [_c_i64, _c_dp, _c_i64, _c_dp, _c_dp, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, _c_dp]
+        L.or_cg_single_reduction.restype = ctypes.c_int
+        L.or_logdet.argtypes = [_c_i64, _c_dp, _c_i64, _c_dp]
+        L.or_logdet.restype = _c_i64
+        L.or_predict_mean.argtypes = [_c_i64, _c_i64, ctypes.c_int, _c_dp, _c_dp, ctypes.c_double, ctypes.c_double,
+                                      _c_dp, _c_i64, ctypes.c_int, _c_dp, _c_i64]
         _lib = L
     return _lib
 
@@ -177,6 +184,48 @@ def cg(A, b, eps: float, maxit: int, R: int = 50, x0=None):
     rr = ctypes.c_double(0.0)
     it = lib().or_cg(n, _p(A), max(n, 1), _p(b), _p(x), eps, maxit, R, ctypes.byref(rr))
     return x, int(it), float(rr.value)
+
+
+def cg_single_reduction(A, b, eps: float, maxit: int, R: int = 50, x0=None):
+    """Chronopoulos-Gear single-reduction CG: Algorithm 1 (left) rearranged
+    so that an iteration's two inner products follow its one product with A
+    (the pipelined CG variants of the paper's related work, Sec. 1).
+    Returns (x, iterations, relres)."""
+    A = _fmat(A)
+    n = A.shape[0]
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    rr = ctypes.c_double(0.0)
+    it = lib().or_cg_single_reduction(n, _p(A), max(n, 1), _p(b), _p(x), eps, maxit, R, ctypes.byref(rr))
+    return x, int(it), float(rr.value)
+
+
+def logdet(A):
+    """log det A = 2 sum_i log L_ii from the textbook factor of an SPD A
+    (the GP log-likelihood term of the GP use of Sec. 4.1).  Returns
+    (logdet, info); logdet is NaN when info != 0."""
+    A = _fmat(A)
+    n = A.shape[0]
+    out = ctypes.c_double(0.0)
+    info = lib().or_logdet(n, _p(A), max(n, 1), ctypes.byref(out))
+    return float(out.value), int(info)
+
+
+def predict_mean(Xs, X, sf2: float, ell: float, alpha):
+    """GP predictive mean K(Xs, X) alpha with the noise-free SE cross
+    covariance (GP behaviour prediction, Sec. 4.1).  Xs: m x d, X: n x d,
+    alpha: n or n x nrhs.  Returns m or m x nrhs."""
+    Xs = np.ascontiguousarray(Xs, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    a = np.asarray(alpha, dtype=np.float64)
+    vec = a.ndim == 1
+    a2 = _fmat(a.reshape(-1, 1) if vec else a)
+    m, d = Xs.shape
+    n = X.shape[0]
+    nrhs = a2.shape[1]
+    out = np.zeros((m, nrhs), dtype=np.float64, order="F")
+    lib().or_predict_mean(m, n, d, _p(Xs), _p(X), sf2, ell, _p(a2), max(n, 1), nrhs, _p(out), max(m, 1))
+    return out[:, 0].copy() if vec else out
 
 
 def pcg(A, Lt, b, bwd_tol: float = 1e-12, eps: float = 1e-13, maxit: int = 500, R: int = 50, x0=None):

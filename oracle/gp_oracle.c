@@ -343,6 +343,48 @@ void or_back_sub(int64_t n, const double *L, int64_t ldl, double *B,
 }
 
 /* ------------------------------------------------------------------------ */
+/* GP quantities on the factor (the GP behaviour prediction of Sec. 4.1)      */
+/* ------------------------------------------------------------------------ */
+
+/* log det A of an SPD matrix from its Cholesky factor: A = L L^T gives
+ * det A = prod_i L_ii^2, so log det A = 2 sum_i log L_ii.  The factor is the
+ * textbook one above, taken on a private copy of A (lower triangle read).
+ * Returns 0 and *out, or the 1-based failing column (then *out is NaN). */
+int64_t or_logdet(int64_t n, const double *A, int64_t lda, double *out)
+{
+    double *L = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1));
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n; ++i) L[IDX(i, j, n)] = A[IDX(i, j, lda)];
+    int64_t info = or_cholesky(n, L, n > 0 ? n : 1);
+    double s = 0.0;
+    if (info == 0)
+        for (int64_t i = 0; i < n; ++i) s += log(L[IDX(i, i, n)]);
+    *out = info == 0 ? 2.0 * s : NAN;
+    free(L);
+    return info;
+}
+
+/* GP predictive mean at m test points: mean_k = sum_i k(x*_k, x_i) alpha_i
+ * with the noise-free squared-exponential covariance
+ * k(x, y) = sf2 exp(-||x - y||^2 / (2 ell^2)) between test and training
+ * points (the noise term belongs to the training covariance only) and
+ * alpha = (K + sn2 I)^-1 y the solution of the GP system.  Xs: m x d and
+ * X: n x d, row-major.  alpha: n x nrhs (lda_alpha), mean: m x nrhs (ldm),
+ * column-major. */
+void or_predict_mean(int64_t m, int64_t n, int d, const double *Xs, const double *X, double sf2,
+                     double ell, const double *alpha, int64_t lda_alpha, int nrhs, double *mean,
+                     int64_t ldm)
+{
+    for (int r = 0; r < nrhs; ++r)
+        for (int64_t k = 0; k < m; ++k) {
+            double s = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                s += or_se_entry(d, Xs + k * d, X + i * d, 0, sf2, ell, 0.0) * alpha[IDX(i, r, lda_alpha)];
+            mean[IDX(k, r, ldm)] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Conjugate gradients                                                        */
 /* ------------------------------------------------------------------------ */
 
@@ -401,6 +443,58 @@ int or_cg(int64_t n, const double *A, int64_t lda, const double *b, double *x,
     }
     if (relres_out) *relres_out = (u0 > 0.0) ? sqrt(u / u0) : 0.0;
     free(r); free(s); free(t);
+    return it;
+}
+
+/* Single-reduction CG (Chronopoulos and Gear's rearrangement of Algorithm 1
+ * (left); the pipelined CG variants the paper's related work cites, Sec. 1):
+ * the same iterates as classic CG in exact arithmetic, with the two inner
+ * products of an iteration taken together after its one product with A.
+ *   r = b - A x;  w = A r;  gamma = r^T r;  delta = w^T r
+ *   alpha = gamma / delta;  beta = 0;  p = 0;  s = 0
+ *   while gamma > eps^2 gamma_0:
+ *       p = r + beta p;  s = w + beta s          (s = A p)
+ *       x += alpha p;  r -= alpha s
+ *       r = b - A x and s = A p on the R-th, 2R-th, ... iteration (R > 0)
+ *       w = A r;  gamma' = r^T r;  delta = w^T r
+ *       beta = gamma' / gamma;  alpha = gamma' / (delta - beta gamma' / alpha)
+ *       gamma = gamma'
+ * Returns the iteration count; *relres_out = sqrt(gamma / gamma_0). */
+int or_cg_single_reduction(int64_t n, const double *A, int64_t lda, const double *b, double *x,
+                           double eps, int maxit, int R, double *relres_out)
+{
+    double *r = malloc(sizeof(double) * n), *w = malloc(sizeof(double) * n);
+    double *p = calloc((size_t)n, sizeof(double)), *s = calloc((size_t)n, sizeof(double));
+    or_matvec_full(n, A, lda, x, r);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    or_matvec_full(n, A, lda, r, w);
+    double gamma = or_dot(n, r, r), gamma0 = gamma, delta = or_dot(n, w, r);
+    double alpha = gamma > 0.0 ? gamma / delta : 0.0, beta = 0.0;
+    int it = 0;
+    while (gamma > eps * eps * gamma0 && it < maxit) {
+        for (int64_t i = 0; i < n; ++i) {
+            p[i] = r[i] + beta * p[i];
+            s[i] = w[i] + beta * s[i];
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * s[i];
+        }
+        ++it;
+        if (R > 0 && it % R == 0) {
+            or_matvec_full(n, A, lda, x, r);
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+            or_matvec_full(n, A, lda, p, s);
+        }
+        or_matvec_full(n, A, lda, r, w);
+        double g = or_dot(n, r, r);
+        delta = or_dot(n, w, r);
+        beta = g / gamma;
+        alpha = g / (delta - beta * g / alpha);
+        gamma = g;
+    }
+    if (relres_out) *relres_out = (gamma0 > 0.0) ? sqrt(gamma / gamma0) : 0.0;
+    free(r); free(w); free(p); free(s);
     return it;
 }
 

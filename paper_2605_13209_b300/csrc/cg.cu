@@ -1,37 +1,95 @@
 // cg.cu -- A6/A7: conjugate gradients, Algorithm 1 (left), with residual
 // replacement every R iterations (Sec. 2.1), for up to 16 right-hand sides
-// that share one pass over the matrix per iteration.
+// that share one pass over the matrix per iteration; and the
+// single-reduction rearrangement of the same iteration (Chronopoulos and
+// Gear), one of the pipelined CG variants the paper's related work cites.
 //
-// Per iteration three kernels run:
+// Classic CG, per iteration three kernels run:
 //   matvec  t = A s and the partial sums of s^T t; the last CTA to finish
 //           reduces the partials in a fixed order and sets alpha = u / s^T t
 //   update  x += alpha s, r -= alpha t, partial sums of r^T r; the last CTA
 //           sets beta = u_new / u, u = u_new and retires converged columns
 //   dir     s = r + beta s
 // On a replacement iteration `update` is split into x += alpha s, a matvec
-// of x, and r = b - A x.  All scalars stay on the device; the host reads
-// one "all done" word every few iterations.  Reductions are two-phase with
-// a fixed order, so results do not depend on CTA scheduling.
+// of x, and r = b - A x.
+//
+// Single-reduction CG, per iteration two kernels run:
+//   sr_vec  p = r + beta p, s = w + beta s (s = A p), x += alpha p,
+//           r -= alpha s
+//   matvec  w = A r and the partial sums of r^T r and w^T r together; the
+//           last CTA sets beta = gamma'/gamma and
+//           alpha = gamma' / (delta - beta gamma' / alpha), and retires
+//           converged columns
+// so an iteration has one reduction point instead of two.  On a
+// replacement iteration r = b - A x and s = A p are recomputed.
+//
+// All scalars stay on the device; the host reads one "all done" word every
+// few iterations.  Reductions are two-phase with a fixed order, so results
+// do not depend on CTA scheduling.
 //
 // The matvec uses A = A^T: t_j = sum_i A_ij s_i is a dot product down column
 // j, which is contiguous in column-major storage.  A CTA owns W consecutive
-// columns and walks all rows; each thread keeps the s values of its rows in
-// registers and reuses them across the W columns and NR right-hand sides.
+// columns and walks all rows with 16-byte loads (two FP64 or four FP32 rows
+// per thread and step); each thread reuses its rows' vector entries across
+// the W columns and NR right-hand sides.
+//
+// Two product arithmetics:
+//   PROD_FP64  one FP64 FMA per element and right-hand side.  This part
+//              issues FP64 at 2 FMAs per clock per SM, below the rate at
+//              which HBM delivers FP64 elements, so this path is FP64-pipe
+//              bound.
+//   PROD_DF    double-float products on the FP32 pipe: every FP64 entry of
+//              A is cut by integer operations into a float head (its top 24
+//              significand bits) and a float tail (the next 23), the
+//              vector is pre-split into float head + tail, and
+//              (a_h + a_t)(s_h + s_t) is formed as a_h s_h exactly (product
+//              and its FMA error term) plus a_h s_t + a_t s_h, summed per
+//              thread in an error-free double-float accumulator (two-sum).
+//              Per product the relative error is below about 2^-45, the
+//              accumulator adds about 2^-48 of the running sum, and the
+//              per-thread sums are combined and reduced in FP64.  FP32 A
+//              is exact in a float, so only the vector is split.  Powers
+//              of two bring A's largest entry and each column of the vector
+//              near 1 first, so FP32's exponent range holds them.
+//              True residuals b - A x (the start and every replacement)
+//              always take FP64 products: they bound the accuracy the
+//              iteration can reach, and they are 1/R of the products.
 
 #include "dense_fp64.cuh"
 
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int ROWS_PER_THREAD = 2;
 constexpr int MAXRHS = 16;
 
+enum Product : int { PROD_FP64 = 0, PROD_DF = 1 };
+enum Variant : int { VAR_CLASSIC = 0, VAR_SINGLE_REDUCTION = 1 };
+enum MvMode : int { MV_ALPHA = 0, MV_PLAIN = 1, MV_SR = 2 };
+
 struct CGState {
-    double *u, *u0, *alpha, *beta;   // [MAXRHS]
+    double *u, *u0, *alpha, *beta;   // [MAXRHS]  (u = gamma = r^T r in the single-reduction form)
     int *active, *iters;            // [MAXRHS]
     int *done;                      // [1]
-    unsigned *counter;              // [2]: matvec, update
+    unsigned *counter;              // [2]: matvec, vector kernels
     double *part;                   // per-CTA partials, part_doubles(n, nrhs)
+};
+
+// Inputs of the double-float path.  SS holds the pre-split vector,
+// row-major by row: the (head, tail) of 2^-es_r v_ir at SS[i * NR + r].
+// scale[r] = 2^(ea + es_r) restores the product's scale; inv[r] = 2^-es_r;
+// *ebias = 896 + ea is the exponent offset that maps A's FP64 exponent field
+// to the float exponent of 2^-ea A.
+struct DFArgs {
+    float2 *SS;
+    const double *scale;
+    const double *inv;
+    const int *ebias;
+};
+
+struct SRArgs {
+    double rtol2;
+    int maxit;
+    int first;   // the set-up product w = A r0: sets gamma_0, alpha_0, beta_0
 };
 
 __device__ inline double warp_sum(double v)
@@ -58,91 +116,307 @@ __device__ inline bool last_cta(unsigned *counter)
     return is_last;
 }
 
-template <typename TA, int W, int NR>
+// Sum of part[b * stride + idx] over the grid's CTAs b in a fixed order
+// (strided per thread, then warp and block); the result is valid in thread
+// 0.  All threads of the CTA must call it.
+__device__ inline double block_sum_partials(const double *part, size_t stride, int idx)
+{
+    __shared__ double red[THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double p = 0.0;
+    for (unsigned b = tid; b < gridDim.x; b += THREADS) p += __ldcg(&part[(size_t)b * stride + idx]);
+    p = warp_sum(p);
+    if (lane == 0) red[warp] = p;
+    __syncthreads();
+    double q = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < THREADS / 32; ++w) q += red[w];
+    __syncthreads();
+    return q;
+}
+
+// ------------------------------------------------ double-float arithmetic
+
+// hi + lo <- hi + lo + p + e, with hi + p taken exactly (two-sum).
+__device__ __forceinline__ void df_add(float &hi, float &lo, float p, float e)
+{
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += err + e;
+}
+
+// (hi, lo) += (h2, l2), two double-float values.
+__device__ __forceinline__ void df_add2(float &hi, float &lo, float h2, float l2)
+{
+    const float s = hi + h2;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (h2 - bp);
+    hi = s;
+    lo = lo + l2 + err;
+}
+
+// Head and tail of 2^-ea a for an FP64 a, from its bit pattern with integer
+// operations only (a float conversion would run on the FP64 pipe).  The
+// head is the top 24 significand bits (truncated), the tail the next 23,
+// so |2^-ea a - head - tail| < 2^-46 |2^-ea a|.  ebias = 896 + ea.  Scaled
+// values below 2^-126 give head 0 (and below 2^-103 tail 0); values at or
+// above 2^128 give an infinite head, so the product is not finite.
+__device__ __forceinline__ void df_split_a(double a, unsigned ebias, float &head, float &tail)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    const unsigned h = (unsigned)(bits >> 32), l = (unsigned)bits;
+    const unsigned t = h & 0x7fffffffu;      // exponent field E at bits 20..30
+    const unsigned sgn = h & 0x80000000u;
+    // (E << 23 | top 23 fraction bits) modulo 2^32, rebiased to E - ebias
+    const unsigned hb = __funnelshift_l(l, t, 3) - (ebias << 23);
+    const bool small = t < ((ebias + 1u) << 20);
+    const bool big = t >= ((ebias + 255u) << 20);
+    const unsigned hbits = small ? 0u : (big ? 0x7f800000u : hb);
+    head = __uint_as_float(hbits | sgn);
+    // tail: fraction bits 6..28 of the low word, weighted 2^(E - ebias - 150)
+    // as the difference of two floats with exponent field E - ebias - 23
+    const unsigned mb = (hb & 0x7f800000u) - (23u << 23);
+    const unsigned fb = mb | ((l >> 6) & 0x007fffffu);
+    const bool tail_ok = t >= ((ebias + 24u) << 20) && !big;
+    tail = tail_ok ? __uint_as_float(fb | sgn) - __uint_as_float(mb | sgn) : 0.0f;
+}
+
+// ------------------------------------------------------------- the matvec
+
+// T[:, r] = A S[:, r] on the CTA's W columns, then per mode:
+//   MV_ALPHA  partial s^T t; the last CTA sets alpha = u / s^T t
+//   MV_PLAIN  nothing more (t = A x for a true residual)
+//   MV_SR     partial r^T r and w^T r (S = r, T = w); the last CTA runs the
+//             single-reduction scalar step (SRArgs)
+// With DF the products read the pre-split DFArgs::SS; S itself is read only
+// for the CTA's own columns (the partial dot products).
+template <typename TA, int W, int NR, bool DF>
 __global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int nrhs, const TA *__restrict__ A,
                                                             int64_t lda, const double *__restrict__ S,
                                                             int64_t lds, double *T, int64_t ldt, CGState st,
-                                                            int mode)
+                                                            int mode, SRArgs sr, DFArgs df, int vec)
 {
-    // mode 0: t = A s, then alpha; mode 1: t = A s only (s is x here)
-    __shared__ double red[THREADS / 32][W * NR];
+    constexpr int RPT = 16 / sizeof(TA);            // rows per thread and step (one 16-byte load)
+    constexpr int STEP = THREADS * RPT;
+    constexpr bool SPLIT_A = DF && sizeof(TA) == 8;
     __shared__ double tcol[W * NR];
     if (*st.done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t j0 = (int64_t)blockIdx.x * W;
     const int wcols = (int)((n - j0 < W) ? n - j0 : W);
-    double acc[W][NR];
-#pragma unroll
-    for (int c = 0; c < W; ++c)
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[c][r] = 0.0;
 
-    for (int64_t base = 0; base < n; base += (int64_t)THREADS * ROWS_PER_THREAD) {
-        double sv[ROWS_PER_THREAD][NR];
-        int64_t rows[ROWS_PER_THREAD];
+    // FP64 path: acc[c][r]; DF path: head/tail pairs
+    double acc[DF ? 1 : W][DF ? 1 : NR];
+    float ah[DF ? W : 1][DF ? NR : 1], al[DF ? W : 1][DF ? NR : 1];
+    if constexpr (DF) {
 #pragma unroll
-        for (int q = 0; q < ROWS_PER_THREAD; ++q) {
-            rows[q] = base + tid + (int64_t)q * THREADS;
+        for (int c = 0; c < W; ++c)
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
-                sv[q][r] = (rows[q] < n && r < nrhs) ? S[rows[q] + r * lds] : 0.0;
+            for (int r = 0; r < NR; ++r) ah[c][r] = al[c][r] = 0.0f;
+    } else {
+#pragma unroll
+        for (int c = 0; c < W; ++c)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[c][r] = 0.0;
+    }
+    const unsigned ebias = SPLIT_A ? (unsigned)*df.ebias : 0u;
+
+    for (int64_t base = 0; base < n; base += STEP) {
+        const int64_t row0 = base + (int64_t)tid * RPT;
+        if (row0 >= n) continue;
+        const bool full = vec && row0 + RPT <= n;
+        // the rows' vector entries
+        double sv[DF ? 1 : RPT][DF ? 1 : NR];
+        float sh[DF ? RPT : 1][DF ? NR : 1], sl[DF ? RPT : 1][DF ? NR : 1];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const bool ok = row0 + q < n;
+            if constexpr (DF) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float2 v = ok ? df.SS[(row0 + q) * NR + r] : make_float2(0.0f, 0.0f);
+                    sh[q][r] = v.x;
+                    sl[q][r] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) sv[q][r] = (ok && r < nrhs) ? S[row0 + q + r * lds] : 0.0;
+            }
+        }
+        // the W columns' entries on these rows, all loads issued first
+        TA a[W][RPT];
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            const TA *col = A + (j0 + (c < wcols ? c : 0)) * lda + row0;
+            if (full) {
+                if constexpr (sizeof(TA) == 8) {
+                    const double2 v = __ldcs(reinterpret_cast<const double2 *>(col));
+                    a[c][0] = v.x;
+                    a[c][1] = v.y;
+                } else {
+                    const float4 v = __ldcs(reinterpret_cast<const float4 *>(col));
+                    a[c][0] = v.x;
+                    a[c][1] = v.y;
+                    a[c][2] = v.z;
+                    a[c][3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) a[c][q] = (row0 + q < n) ? col[q] : (TA)0;
+            }
         }
 #pragma unroll
         for (int c = 0; c < W; ++c) {
             if (c < wcols) {
 #pragma unroll
-                for (int q = 0; q < ROWS_PER_THREAD; ++q) {
-                    if (rows[q] < n) {
-                        const double a = (double)A[rows[q] + (j0 + c) * lda];
+                for (int q = 0; q < RPT; ++q) {
+                    if constexpr (DF) {
+                        float h, t = 0.0f;
+                        if constexpr (SPLIT_A) df_split_a((double)a[c][q], ebias, h, t);
+                        else h = (float)a[c][q];
 #pragma unroll
-                        for (int r = 0; r < NR; ++r) acc[c][r] = fma(a, sv[q][r], acc[c][r]);
+                        for (int r = 0; r < NR; ++r) {
+                            const float p = h * sh[q][r];
+                            float e = fmaf(h, sh[q][r], -p);
+                            e = fmaf(h, sl[q][r], e);
+                            if constexpr (SPLIT_A) e = fmaf(t, sh[q][r], e);
+                            df_add(ah[c][r], al[c][r], p, e);
+                        }
+                    } else {
+                        const double av = (double)a[c][q];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) acc[c][r] = fma(av, sv[q][r], acc[c][r]);
                     }
                 }
             }
         }
     }
+
+    // reduce over the CTA: warps by shuffles, then warps in warp order
+    if constexpr (DF) {
+        __shared__ float2 red2[THREADS / 32][W * NR];
 #pragma unroll
-    for (int c = 0; c < W; ++c)
+        for (int c = 0; c < W; ++c)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            double v = warp_sum(acc[c][r]);
-            if (lane == 0) red[warp][c * NR + r] = v;
+            for (int r = 0; r < NR; ++r) {
+                float h = ah[c][r], l = al[c][r];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    df_add2(h, l, __shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off));
+                if (lane == 0) red2[warp][c * NR + r] = make_float2(h, l);
+            }
+        __syncthreads();
+        if (tid < W * NR) {
+            float h = red2[0][tid].x, l = red2[0][tid].y;
+            for (int w = 1; w < THREADS / 32; ++w) df_add2(h, l, red2[w][tid].x, red2[w][tid].y);
+            const int r = tid % NR;
+            tcol[tid] = ((double)h + (double)l) * (r < nrhs ? df.scale[r] : 0.0);
         }
-    __syncthreads();
-    if (tid < W * NR) {
-        double v = 0.0;
+    } else {
+        __shared__ double red[THREADS / 32][W * NR];
 #pragma unroll
-        for (int w = 0; w < THREADS / 32; ++w) v += red[w][tid];
-        tcol[tid] = v;
-        const int c = tid / NR, r = tid % NR;
-        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = v;
+        for (int c = 0; c < W; ++c)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                double v = warp_sum(acc[c][r]);
+                if (lane == 0) red[warp][c * NR + r] = v;
+            }
+        __syncthreads();
+        if (tid < W * NR) {
+            double v = 0.0;
+#pragma unroll
+            for (int w = 0; w < THREADS / 32; ++w) v += red[w][tid];
+            tcol[tid] = v;
+        }
     }
-    if (mode != 0) return;
+    if (tid < W * NR) {
+        const int c = tid / NR, r = tid % NR;
+        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = tcol[tid];
+    }
+    if (mode == MV_PLAIN) return;
     __syncthreads();
+    if (mode == MV_ALPHA) {
+        if (tid < NR) {
+            double p = 0.0;
+            for (int c = 0; c < wcols; ++c)
+                if (tid < nrhs) p = fma(S[(j0 + c) + tid * lds], tcol[c * NR + tid], p);
+            st.part[(size_t)blockIdx.x * NR + tid] = p;
+        }
+        if (last_cta(&st.counter[0])) {
+            for (int r = 0; r < nrhs; ++r) {
+                const double q = block_sum_partials(st.part, NR, r);
+                if (tid == 0) st.alpha[r] = st.active[r] ? st.u[r] / q : 0.0;
+            }
+            if (tid == 0) st.counter[0] = 0;
+        }
+        return;
+    }
+    // MV_SR: S is r, T is w
     if (tid < NR) {
-        double p = 0.0;
+        double g = 0.0, d = 0.0;
         for (int c = 0; c < wcols; ++c)
-            if (tid < nrhs) p = fma(S[(j0 + c) + tid * lds], tcol[c * NR + tid], p);
-        st.part[(size_t)blockIdx.x * NR + tid] = p;
+            if (tid < nrhs) {
+                const double rj = S[(j0 + c) + tid * lds];
+                g = fma(rj, rj, g);
+                d = fma(tcol[c * NR + tid], rj, d);
+            }
+        st.part[(size_t)blockIdx.x * 2 * NR + tid] = g;
+        st.part[(size_t)blockIdx.x * 2 * NR + NR + tid] = d;
     }
     if (last_cta(&st.counter[0])) {
-        // every thread sums a fixed strided subset of the CTA partials, then
-        // one block reduction (a fixed order, so the result is reproducible)
+        __shared__ int any_active;
+        if (tid == 0) any_active = 0;
         for (int r = 0; r < nrhs; ++r) {
-            double p = 0.0;
-            for (unsigned b = tid; b < gridDim.x; b += THREADS) p += __ldcg(&st.part[(size_t)b * NR + r]);
-            p = warp_sum(p);
-            if (lane == 0) red[warp][0] = p;
-            __syncthreads();
+            const double g = block_sum_partials(st.part, 2 * NR, r);
+            const double d = block_sum_partials(st.part, 2 * NR, NR + r);
             if (tid == 0) {
-                double q = 0.0;
-                for (int w = 0; w < THREADS / 32; ++w) q += red[w][0];
-                st.alpha[r] = st.active[r] ? st.u[r] / q : 0.0;
+                if (sr.first) {
+                    st.u0[r] = g;
+                    st.u[r] = g;
+                    st.iters[r] = 0;
+                    st.beta[r] = 0.0;
+                    st.alpha[r] = g > 0.0 ? g / d : 0.0;
+                    st.active[r] = g > 0.0 ? 1 : 0;
+                } else if (st.active[r]) {
+                    const int it = st.iters[r] + 1;
+                    st.iters[r] = it;
+                    const double b = g / st.u[r];
+                    st.alpha[r] = g / (d - b * g / st.alpha[r]);
+                    st.beta[r] = b;
+                    st.u[r] = g;
+                    if (g <= sr.rtol2 * st.u0[r] || it >= sr.maxit) st.active[r] = 0;
+                }
+                any_active |= st.active[r];
             }
-            __syncthreads();
         }
-        if (tid == 0) st.counter[0] = 0;
+        if (tid == 0) {
+            *st.done = any_active ? 0 : 1;
+            st.counter[0] = 0;
+        }
     }
+}
+
+// SS[i * NR + r] = (head, tail) of inv[r] * V[i, r]: float(v) and
+// float(v - float(v)) (conversions on the FP64 pipe, once per entry).
+template <int NR>
+__global__ void __launch_bounds__(THREADS) df_split_vec_kernel(int64_t n, int nrhs, const double *__restrict__ V,
+                                                               int64_t ldv, float2 *__restrict__ SS,
+                                                               const double *__restrict__ inv, const int *done)
+{
+    if (done && *done) return;
+    const int64_t e = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    if (e >= n * NR) return;
+    const int64_t i = e / NR;
+    const int r = (int)(e % NR);
+    float2 o = make_float2(0.0f, 0.0f);
+    if (r < nrhs) {
+        const double v = V[i + r * ldv] * inv[r];
+        o.x = __double2float_rn(v);
+        o.y = __double2float_rn(v - (double)o.x);
+    }
+    SS[e] = o;
 }
 
 // Tail of update/replace: reduce r^T r partials, set beta, retire columns.
@@ -276,41 +550,175 @@ __global__ void __launch_bounds__(THREADS) cg_init_kernel(int64_t n, int nrhs, d
     }
 }
 
+// Single-reduction step on the vectors of active columns:
+// p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s (not on a
+// replacement iteration, whose r is recomputed from x).
+__global__ void __launch_bounds__(THREADS) cgsr_vec_kernel(int64_t n, int nrhs, double *X, int64_t ldx, double *R,
+                                                           const double *Wv, double *P, double *S, int64_t ldv,
+                                                           CGState st, int replace)
+{
+    if (*st.done) return;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    if (i >= n) return;
+    for (int r = 0; r < nrhs; ++r) {
+        if (!st.active[r]) continue;
+        const double a = st.alpha[r], b = st.beta[r];
+        const double p = fma(b, P[i + r * ldv], R[i + r * ldv]);
+        const double s = fma(b, S[i + r * ldv], Wv[i + r * ldv]);
+        P[i + r * ldv] = p;
+        S[i + r * ldv] = s;
+        X[i + r * ldx] = fma(a, p, X[i + r * ldx]);
+        if (!replace) R[i + r * ldv] = fma(-a, s, R[i + r * ldv]);
+    }
+}
+
+// r = b - t on active columns (all columns with `all`).
+__global__ void __launch_bounds__(THREADS) cg_resid_kernel(int64_t n, int nrhs, double *R, const double *T,
+                                                           const double *B, int64_t ldb, int64_t ldv, CGState st,
+                                                           int all)
+{
+    if (!all && *st.done) return;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    if (i >= n) return;
+    for (int r = 0; r < nrhs; ++r)
+        if (all || st.active[r]) R[i + r * ldv] = B[i + r * ldb] - T[i + r * ldv];
+}
+
+// Double-float set-up: ea from max_i A_ii (FP64 A; 0 for FP32 A), es_r from
+// max_i |B_ir|; writes scale, inv and ebias.  dmax: [0] max diagonal,
+// [1 + r] max |b_r| (bit patterns of non-negative doubles).
+__global__ void df_scales_kernel(int nrhs, const double *dmax, int split_a, double *scale, double *inv, int *ebias)
+{
+    const int r = threadIdx.x;
+    int ea = 0;
+    if (split_a && dmax[0] > 0.0) ea = ilogb(dmax[0]);
+    ea = ea < -800 ? -800 : (ea > 800 ? 800 : ea);
+    if (r == 0) *ebias = 896 + ea;
+    if (r < MAXRHS) {
+        const double bm = r < nrhs ? dmax[1 + r] : 0.0;
+        int es = bm > 0.0 ? ilogb(bm) : 0;
+        es = es < -900 ? -900 : (es > 900 ? 900 : es);
+        scale[r] = ldexp(1.0, ea + es);
+        inv[r] = ldexp(1.0, -es);
+    }
+}
+
+// Order-independent maxima of non-negative doubles through their bit
+// patterns (which order like the values).
+__device__ inline void atomic_max_nonneg(double *addr, double v)
+{
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// *out = max(0, max_i A_ii).
+template <typename TA>
+__global__ void __launch_bounds__(THREADS) diag_max_kernel(int64_t n, const TA *__restrict__ A, int64_t lda,
+                                                           double *out)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS)
+        m = fmax(m, (double)A[i + i * lda]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+// out[c] = max_i |V_ic|.
+__global__ void __launch_bounds__(THREADS) absmax_cols_kernel(int64_t n, int nrhs, const double *V, int64_t ldv,
+                                                              double *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+    for (int r = 0; r < nrhs; ++r) {
+        double m = (i < n) ? fabs(V[i + r * ldv]) : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&out[r], m);
+    }
+}
+
+// Column width per CTA and right-hand-side bucket of a matvec launch.
+// Narrow column blocks make many CTAs, so the last partial wave is a small
+// share of the launch; the double-float path reads the split vector once
+// per CTA, so it takes wider blocks.
+inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
+inline int mv_width(int nrhs, int prod)
+{
+    if (prod == PROD_DF) return nrhs <= 1 ? 8 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2;
+    return nrhs <= 1 ? 4 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2;
+}
+
+template <typename TA, bool DF>
+void launch_mv_kernel(int64_t n, int nrhs, const TA *A, int64_t lda, const double *S, int64_t lds, double *T,
+                      int64_t ldt, const CGState &st, int mode, SRArgs sr, DFArgs df, int vec, cudaStream_t s)
+{
+#define GPCH_MV(Wc, NRc)                                                                                     \
+    cg_matvec_kernel<TA, Wc, NRc, DF><<<(unsigned)((n + Wc - 1) / Wc), THREADS, 0, s>>>(n, nrhs, A, lda, S, lds, \
+                                                                                        T, ldt, st, mode, sr, \
+                                                                                        df, vec)
+    if constexpr (DF) {
+        if (nrhs <= 1) GPCH_MV(8, 1);
+        else if (nrhs <= 2) GPCH_MV(8, 2);
+        else if (nrhs <= 4) GPCH_MV(4, 4);
+        else if (nrhs <= 8) GPCH_MV(2, 8);
+        else GPCH_MV(2, 16);
+    } else {
+        if (nrhs <= 1) GPCH_MV(4, 1);
+        else if (nrhs <= 2) GPCH_MV(8, 2);
+        else if (nrhs <= 4) GPCH_MV(4, 4);
+        else if (nrhs <= 8) GPCH_MV(2, 8);
+        else GPCH_MV(2, 16);
+    }
+#undef GPCH_MV
+}
+
+// One matvec T = A S (plus the mode's reductions).  With PROD_DF the vector
+// S is split into df.SS first (one small launch).
 template <typename TA>
 gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64_t lda, const double *S,
-                          int64_t lds, double *T, int64_t ldt, const CGState &st, int mode, cudaStream_t s)
+                          int64_t lds, double *T, int64_t ldt, const CGState &st, int mode, cudaStream_t s,
+                          int prod = PROD_FP64, DFArgs df = DFArgs{}, SRArgs sr = SRArgs{0.0, 0, 0})
 {
+    const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((lda * (int64_t)sizeof(TA)) & 15) == 0) ? 1 : 0;
+    if (prod == PROD_DF) {
+        const int nr = mv_nr(nrhs);
+        const unsigned blocks = (unsigned)((n * nr + THREADS - 1) / THREADS);
+        // the set-up product of the single-reduction form runs before `done` is meaningful
+        const int *done = (mode == MV_SR && sr.first) ? nullptr : st.done;
+        switch (nr) {
+        case 1: df_split_vec_kernel<1><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, done); break;
+        case 2: df_split_vec_kernel<2><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, done); break;
+        case 4: df_split_vec_kernel<4><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, done); break;
+        case 8: df_split_vec_kernel<8><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, done); break;
+        default: df_split_vec_kernel<16><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, done); break;
+        }
+        GPCH_LAUNCH_CHECK(ctx);
+    }
     gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s,
                         (double)n * n * sizeof(TA) + 2.0 * (double)n * nrhs * sizeof(double));
-#define GPCH_MV(Wc, NRc)                                                                         \
-    cg_matvec_kernel<TA, Wc, NRc><<<(unsigned)((n + Wc - 1) / Wc), THREADS, 0, s>>>(n, nrhs, A, lda, S, \
-                                                                                    lds, T, ldt, st, mode)
-    // narrow column blocks make many CTAs (n / 4 for one right-hand side), so
-    // the last partial wave of CTAs is a small share of the launch
-    if (nrhs <= 1) GPCH_MV(4, 1);
-    else if (nrhs <= 2) GPCH_MV(8, 2);
-    else if (nrhs <= 4) GPCH_MV(4, 4);
-    else if (nrhs <= 8) GPCH_MV(2, 8);
-    else GPCH_MV(2, 16);
-#undef GPCH_MV
+    if (prod == PROD_DF)
+        launch_mv_kernel<TA, true>(n, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
+    else
+        launch_mv_kernel<TA, false>(n, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
 
-inline int mv_width(int nrhs) { return nrhs <= 1 ? 4 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2; }
-inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
-
-// Loads every kernel cg_run may launch on the current device.  Under lazy
-// module loading a kernel's code is placed in device memory at its first
-// launch; asking for its attributes loads it ahead of time.
+// Loads every kernel cg_run may launch on the current device for the
+// classic FP64-product solve.  Under lazy module loading a kernel's code is
+// placed in device memory at its first launch; asking for its attributes
+// loads it ahead of time.
 template <typename TA>
 cudaError_t cg_kernels_load()
 {
     cudaFuncAttributes a;
-    const void *fns[] = {(const void *)cg_matvec_kernel<TA, 4, 1>, (const void *)cg_matvec_kernel<TA, 8, 2>,
-                         (const void *)cg_matvec_kernel<TA, 4, 4>, (const void *)cg_matvec_kernel<TA, 2, 8>,
-                         (const void *)cg_matvec_kernel<TA, 2, 16>, (const void *)cg_init_kernel,
-                         (const void *)cg_update_kernel,           (const void *)cg_xupdate_kernel,
+    const void *fns[] = {(const void *)cg_matvec_kernel<TA, 4, 1, false>,
+                         (const void *)cg_matvec_kernel<TA, 8, 2, false>,
+                         (const void *)cg_matvec_kernel<TA, 4, 4, false>,
+                         (const void *)cg_matvec_kernel<TA, 2, 8, false>,
+                         (const void *)cg_matvec_kernel<TA, 2, 16, false>,
+                         (const void *)cg_init_kernel,
+                         (const void *)cg_update_kernel,
+                         (const void *)cg_xupdate_kernel,
                          (const void *)cg_dir_kernel};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncGetAttributes(&a, f);
@@ -319,84 +727,165 @@ cudaError_t cg_kernels_load()
     return cudaSuccess;
 }
 
-// Doubles of per-CTA partials: the matvec stores mv_nr per CTA, the vector
-// kernels (one CTA per THREADS rows) up to 2 * MAXRHS.
-inline size_t part_doubles(int64_t n, int nrhs)
+// Doubles of per-CTA partials: a matvec stores mv_nr (two sets in the
+// single-reduction form) per CTA, the vector kernels (one CTA per THREADS
+// rows) up to 3 * MAXRHS.
+inline size_t part_doubles(int64_t n, int nrhs, int prod = PROD_FP64, int variant = VAR_CLASSIC)
 {
-    const size_t mv = (size_t)((n + mv_width(nrhs) - 1) / mv_width(nrhs)) * mv_nr(nrhs);
+    const int sets = variant == VAR_SINGLE_REDUCTION ? 2 : 1;
+    const size_t mv = (size_t)((n + mv_width(nrhs, prod) - 1) / mv_width(nrhs, prod)) * mv_nr(nrhs) * sets;
     const size_t vec = (size_t)((n + THREADS - 1) / THREADS) * 3 * MAXRHS;
     return mv > vec ? mv : vec;
 }
 
-// Bytes of scratch one CG group of nrhs (<= 16) columns needs.
-size_t cg_scratch_bytes(int64_t n, int nrhs)
+struct CGBufs {
+    double *R, *S, *T, *P, *Wv;   // P, Wv: single-reduction form only
+    CGState st;
+    double *sc;
+    int *ic;
+    DFArgs df;
+    double *dmax;                 // [1 + MAXRHS]: max diagonal, max |b_r|
+};
+
+// Carves the scratch of one CG group; with a null base only sizes it.
+inline size_t cg_carve(void *base, int64_t n, int nrhs, int prod, int variant, CGBufs *b)
 {
-    gpch::Carver dry(nullptr);
-    dry.take<double>((size_t)3 * n * nrhs);
-    dry.take<double>(4 * MAXRHS);
-    dry.take<int>(2 * MAXRHS + 1);
-    dry.take<unsigned>(2);
-    dry.take<double>(part_doubles(n, nrhs));
-    return dry.off;
+    gpch::Carver cv(base);
+    CGBufs t;
+    t.R = cv.take<double>((size_t)n * nrhs);
+    t.S = cv.take<double>((size_t)n * nrhs);
+    t.T = cv.take<double>((size_t)n * nrhs);
+    t.P = t.Wv = nullptr;
+    if (variant == VAR_SINGLE_REDUCTION) {
+        t.P = cv.take<double>((size_t)n * nrhs);
+        t.Wv = cv.take<double>((size_t)n * nrhs);
+    }
+    t.sc = cv.take<double>(4 * MAXRHS);
+    t.st.u = t.sc;
+    t.st.u0 = t.sc + MAXRHS;
+    t.st.alpha = t.sc + 2 * MAXRHS;
+    t.st.beta = t.sc + 3 * MAXRHS;
+    t.ic = cv.take<int>(2 * MAXRHS + 1);
+    t.st.active = t.ic;
+    t.st.iters = t.ic + MAXRHS;
+    t.st.done = t.ic + 2 * MAXRHS;
+    t.st.counter = cv.take<unsigned>(2);
+    t.st.part = cv.take<double>(part_doubles(n, nrhs, prod, variant));
+    t.df = DFArgs{nullptr, nullptr, nullptr, nullptr};
+    t.dmax = nullptr;
+    if (prod == PROD_DF) {
+        t.df.SS = cv.take<float2>((size_t)n * mv_nr(nrhs));
+        double *d = cv.take<double>(2 * MAXRHS);
+        t.df.scale = d;
+        t.df.inv = d + MAXRHS;
+        t.df.ebias = cv.take<int>(1);
+        t.dmax = cv.take<double>(1 + MAXRHS);
+    }
+    if (b) *b = t;
+    return cv.off;
 }
 
-// One CG group on caller-provided scratch (cg_scratch_bytes(n, nrhs) bytes
-// of device memory at `scratch`) and a host staging block `hbuf` of at
-// least 64 + 4*16*8 + 33*4 bytes (pinned or pageable).
+// Bytes of scratch one CG group of nrhs (<= 16) columns needs.
+size_t cg_scratch_bytes(int64_t n, int nrhs, int prod = PROD_FP64, int variant = VAR_CLASSIC)
+{
+    return cg_carve(nullptr, n, nrhs, prod, variant, nullptr);
+}
+
+// Enqueues the double-float scales of one solve (ea from A's diagonal, es_r
+// from B's columns).
+template <typename TA>
+gpch_status df_prepare(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64_t lda, const double *B, int64_t ldb,
+                       const CGBufs &b, cudaStream_t s)
+{
+    GPCH_CUDA(ctx, cudaMemsetAsync(b.dmax, 0, (1 + MAXRHS) * sizeof(double), s));
+    const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
+    if (sizeof(TA) == 8) {
+        diag_max_kernel<TA><<<vec_ctas < 148 ? vec_ctas : 148, THREADS, 0, s>>>(n, A, lda, b.dmax);
+        GPCH_LAUNCH_CHECK(ctx);
+    }
+    absmax_cols_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, B, ldb, b.dmax + 1);
+    GPCH_LAUNCH_CHECK(ctx);
+    df_scales_kernel<<<1, 32, 0, s>>>(nrhs, b.dmax, sizeof(TA) == 8 ? 1 : 0, const_cast<double *>(b.df.scale),
+                                      const_cast<double *>(b.df.inv), const_cast<int *>(b.df.ebias));
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+// One CG group on caller-provided scratch (cg_scratch_bytes(n, nrhs, prod,
+// variant) bytes of device memory at `scratch`) and a host staging block
+// `hbuf` of at least 64 + 4*16*8 + 33*4 bytes (pinned or pageable).
 template <typename TA>
 gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb, double *X,
                    int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s, void *scratch, void *hbuf,
-                   int *h_iters, double *h_relres)
+                   int *h_iters, double *h_relres, int prod = PROD_FP64, int variant = VAR_CLASSIC)
 {
     const int64_t ldv = n;
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
-    gpch::Carver cv(scratch);
-    double *Rv = cv.take<double>((size_t)n * nrhs);
-    double *Sv = cv.take<double>((size_t)n * nrhs);
-    double *Tv = cv.take<double>((size_t)n * nrhs);
-    CGState st;
-    double *sc = cv.take<double>(4 * MAXRHS);
-    st.u = sc;
-    st.u0 = sc + MAXRHS;
-    st.alpha = sc + 2 * MAXRHS;
-    st.beta = sc + 3 * MAXRHS;
-    int *ic = cv.take<int>(2 * MAXRHS + 1);
-    st.active = ic;
-    st.iters = ic + MAXRHS;
-    st.done = ic + 2 * MAXRHS;
-    st.counter = cv.take<unsigned>(2);
-    st.part = cv.take<double>(part_doubles(n, nrhs));
+    CGBufs b;
+    cg_carve(scratch, n, nrhs, prod, variant, &b);
+    CGState &st = b.st;
     GPCH_CUDA(ctx, cudaMemsetAsync(st.counter, 0, 2 * sizeof(unsigned), s));
-    GPCH_CUDA(ctx, cudaMemsetAsync(ic, 0, (2 * MAXRHS + 1) * sizeof(int), s));
+    GPCH_CUDA(ctx, cudaMemsetAsync(b.ic, 0, (2 * MAXRHS + 1) * sizeof(int), s));
+    if (prod == PROD_DF) GPCH_CHECK(df_prepare<TA>(ctx, n, nrhs, A, lda, B, ldb, b, s));
+    const double rtol2 = rtol * rtol;
 
-    // line 1: s = r = b - A x
-    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
-    cg_init_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, Sv, Tv, B, ldb, ldv, st);
-    GPCH_LAUNCH_CHECK(ctx);
+    if (variant == VAR_CLASSIC) {
+        // line 1: s = r = b - A x
+        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+        cg_init_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.S, b.T, B, ldb, ldv, st);
+        GPCH_LAUNCH_CHECK(ctx);
+    } else {
+        // r = b - A x; w = A r with gamma_0, delta_0, alpha_0; p = s = 0
+        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+        cg_resid_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.T, B, ldb, ldv, st, 1);
+        GPCH_LAUNCH_CHECK(ctx);
+        GPCH_CUDA(ctx, cudaMemsetAsync(b.P, 0, (size_t)n * nrhs * sizeof(double), s));
+        GPCH_CUDA(ctx, cudaMemsetAsync(b.S, 0, (size_t)n * nrhs * sizeof(double), s));
+        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, b.R, ldv, b.Wv, ldv, st, MV_SR, s, prod, b.df,
+                                     SRArgs{rtol2, maxit, 1}));
+    }
 
     int *h_done = static_cast<int *>(hbuf);
-    const double rtol2 = rtol * rtol;
     const int chunk = 16;
     int it = 0;
     while (it < maxit) {
         const int k = (maxit - it < chunk) ? maxit - it : chunk;
         for (int q = 0; q < k; ++q) {
             const int iter = it + q + 1;   // 1-based number of the iteration being run
-            GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
-            gpch::PhaseScope phv(ctx, GPCH_PHASE_CG_VECTOR, s, 9.0 * (double)n * nrhs * sizeof(double));
-            if (R > 0 && iter % R == 0) {
-                cg_xupdate_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Sv, ldv, st);
+            const bool replace = R > 0 && iter % R == 0;
+            if (variant == VAR_CLASSIC) {
+                GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, b.S, ldv, b.T, ldv, st, MV_ALPHA, s, prod, b.df));
+                gpch::PhaseScope phv(ctx, GPCH_PHASE_CG_VECTOR, s, 9.0 * (double)n * nrhs * sizeof(double));
+                if (replace) {
+                    cg_xupdate_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, b.S, ldv, st);
+                    GPCH_LAUNCH_CHECK(ctx);
+                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+                    cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, b.R, b.S, b.T, B, ldb, ldv, st,
+                                                                  rtol2, maxit, 1);
+                } else {
+                    cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, b.R, b.S, b.T, B, ldb, ldv, st,
+                                                                  rtol2, maxit, 0);
+                }
                 GPCH_LAUNCH_CHECK(ctx);
-                GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
-                cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, B, ldb, ldv, st, rtol2,
-                                                              maxit, 1);
+                cg_dir_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.S, ldv, st);
+                GPCH_LAUNCH_CHECK(ctx);
             } else {
-                cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, B, ldb, ldv, st, rtol2,
-                                                              maxit, 0);
+                {
+                    gpch::PhaseScope phv(ctx, GPCH_PHASE_CG_VECTOR, s, 11.0 * (double)n * nrhs * sizeof(double));
+                    cgsr_vec_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, b.R, b.Wv, b.P, b.S, ldv, st,
+                                                                 replace ? 1 : 0);
+                    GPCH_LAUNCH_CHECK(ctx);
+                }
+                if (replace) {
+                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+                    cg_resid_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.T, B, ldb, ldv, st, 0);
+                    GPCH_LAUNCH_CHECK(ctx);
+                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, b.P, ldv, b.S, ldv, st, MV_PLAIN, s, prod,
+                                                 b.df));
+                }
+                GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, b.R, ldv, b.Wv, ldv, st, MV_SR, s, prod, b.df,
+                                             SRArgs{rtol2, maxit, 0}));
             }
-            GPCH_LAUNCH_CHECK(ctx);
-            cg_dir_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, Sv, ldv, st);
-            GPCH_LAUNCH_CHECK(ctx);
         }
         it += k;
         GPCH_CUDA(ctx, cudaMemcpyAsync(h_done, st.done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -406,8 +895,8 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
     // statistics
     double *h_sc = reinterpret_cast<double *>(static_cast<char *>(hbuf) + 64);
     int *h_ic = reinterpret_cast<int *>(static_cast<char *>(hbuf) + 64 + 4 * MAXRHS * sizeof(double));
-    GPCH_CUDA(ctx, cudaMemcpyAsync(h_sc, sc, 4 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
-    GPCH_CUDA(ctx, cudaMemcpyAsync(h_ic, ic, (2 * MAXRHS + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h_sc, b.sc, 4 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GPCH_CUDA(ctx, cudaMemcpyAsync(h_ic, b.ic, (2 * MAXRHS + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
     GPCH_CUDA(ctx, cudaStreamSynchronize(s));
     for (int r = 0; r < nrhs; ++r) {
         h_iters[r] = h_ic[MAXRHS + r];
@@ -421,11 +910,11 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
 template <typename TA>
 gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb,
                      double *X, int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s,
-                     int *h_iters, double *h_relres)
+                     int *h_iters, double *h_relres, int prod = PROD_FP64, int variant = VAR_CLASSIC)
 {
-    GPCH_CHECK(gpch::ws_reserve(ctx, cg_scratch_bytes(n, nrhs)));
+    GPCH_CHECK(gpch::ws_reserve(ctx, cg_scratch_bytes(n, nrhs, prod, variant)));
     return cg_run<TA>(ctx, n, A, lda, B, ldb, X, ldx, nrhs, rtol, maxit, R, s, ctx->ws, ctx->pinned, h_iters,
-                      h_relres);
+                      h_relres, prod, variant);
 }
 
 // ------------------------------------------------------------ PCG (A9)
@@ -587,38 +1076,6 @@ __global__ void __launch_bounds__(THREADS) pcg_dot_kernel(int64_t n, int nrhs, c
     }
 }
 
-// Order-independent maxima of non-negative doubles through their bit
-// patterns (which order like the values).
-__device__ inline void atomic_max_nonneg(double *addr, double v)
-{
-    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
-}
-
-// *out = max(0, max_i A_ii).
-__global__ void __launch_bounds__(THREADS) diag_max_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
-                                                           double *out)
-{
-    double m = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * THREADS)
-        m = fmax(m, A[i + i * lda]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
-}
-
-// out[c] = max_i |V_ic|.
-__global__ void __launch_bounds__(THREADS) absmax_cols_kernel(int64_t n, int nrhs, const double *V, int64_t ldv,
-                                                              double *out)
-{
-    const int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x;
-    for (int r = 0; r < nrhs; ++r) {
-        double m = (i < n) ? fabs(V[i + r * ldv]) : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-        if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&out[r], m);
-    }
-}
-
 struct RefineResult {
     int iterations = 0;
     double bwd[MAXRHS] = {0};
@@ -770,7 +1227,7 @@ gpch_status diag_max(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, dou
                      double *out)
 {
     GPCH_CUDA(ctx, cudaMemsetAsync(dev2, 0, 2 * sizeof(double), s));
-    diag_max_kernel<<<(unsigned)((n + THREADS - 1) / THREADS < 148 ? (n + THREADS - 1) / THREADS : 148), THREADS, 0,
+    diag_max_kernel<double><<<(unsigned)((n + THREADS - 1) / THREADS < 148 ? (n + THREADS - 1) / THREADS : 148), THREADS, 0,
                       s>>>(n, A, lda, dev2 + 1);
     GPCH_LAUNCH_CHECK(ctx);
     double *h = static_cast<double *>(ctx->pinned);
@@ -782,12 +1239,17 @@ gpch_status diag_max(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, dou
 
 }  // namespace
 
-extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
-                                     const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol,
-                                     int maxit, int replace_every, void *stream, gpch_cg_stats *stats)
+extern "C" gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
+                                        const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol,
+                                        int maxit, int replace_every, const gpch_cg_opts *opts, void *stream,
+                                        gpch_cg_stats *stats)
 {
     GPCH_ARG(ctx, ctx != nullptr, "null context");
     if (stats) *stats = gpch_cg_stats{0, 0, 0.0};
+    const int variant = opts ? opts->variant : GPCH_CG_CLASSIC;
+    const int prod = opts ? opts->products : GPCH_CG_PRODUCTS_FP64;
+    GPCH_ARG(ctx, variant == GPCH_CG_CLASSIC || variant == GPCH_CG_SINGLE_REDUCTION, "bad CG variant");
+    GPCH_ARG(ctx, prod == GPCH_CG_PRODUCTS_FP64 || prod == GPCH_CG_PRODUCTS_DOUBLE_FLOAT, "bad CG products");
     GPCH_ARG(ctx, n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
     GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
     GPCH_ARG(ctx, dtype == GPCH_F64 || dtype == GPCH_F32, "bad dtype");
@@ -796,6 +1258,8 @@ extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gp
     GPCH_ARG(ctx, A && B && X, "null pointer");
     GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
+    const int pv = prod == GPCH_CG_PRODUCTS_DOUBLE_FLOAT ? PROD_DF : PROD_FP64;
+    const int vv = variant == GPCH_CG_SINGLE_REDUCTION ? VAR_SINGLE_REDUCTION : VAR_CLASSIC;
     int max_it = 0, conv = 0;
     double rel_max = 0.0;
     for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
@@ -805,10 +1269,10 @@ extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gp
         gpch_status st;
         if (dtype == GPCH_F64)
             st = cg_group<double>(ctx, n, static_cast<const double *>(A), lda, B + r0 * ldb, ldb, X + r0 * ldx,
-                                  ldx, g, rtol, maxit, replace_every, s, iters, rel);
+                                  ldx, g, rtol, maxit, replace_every, s, iters, rel, pv, vv);
         else
             st = cg_group<float>(ctx, n, static_cast<const float *>(A), lda, B + r0 * ldb, ldb, X + r0 * ldx,
-                                 ldx, g, rtol, maxit, replace_every, s, iters, rel);
+                                 ldx, g, rtol, maxit, replace_every, s, iters, rel, pv, vv);
         if (st != GPCH_OK) return st;
         for (int r = 0; r < g; ++r) {
             if (iters[r] > max_it) max_it = iters[r];
@@ -821,6 +1285,14 @@ extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gp
         return gpch::fail(ctx, GPCH_NOT_CONVERGED, "%d of %d right-hand sides missed rtol within %d iterations",
                           nrhs - conv, nrhs, maxit);
     return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_cg_solve(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
+                                     const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol,
+                                     int maxit, int replace_every, void *stream, gpch_cg_stats *stats)
+{
+    return gpch_cg_solve_ex(ctx, n, A, dtype, lda, B, ldb, X, ldx, nrhs, rtol, maxit, replace_every, nullptr, stream,
+                            stats);
 }
 
 extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *B,

@@ -39,6 +39,14 @@ class CGStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("relres_max", ctypes.c_double)]
 
 
+class CGOpts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("products", ctypes.c_int32)]
+
+
+CG_CLASSIC, CG_SINGLE_REDUCTION = 0, 1
+CG_PRODUCTS_FP64, CG_PRODUCTS_DOUBLE_FLOAT = 0, 1
+
+
 class System(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
                 ("ldb", ctypes.c_int64), ("nrhs", ctypes.c_int32)]
@@ -96,6 +104,8 @@ def lib() -> ctypes.CDLL:
         L.gpch_chol_solve.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_cg_solve.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int, _vp,
                                     ctypes.POINTER(CGStats)]
+        L.gpch_cg_solve_ex.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int,
+                                       ctypes.POINTER(CGOpts), _vp, ctypes.POINTER(CGStats)]
         L.gpch_timing_enable.argtypes = [_vp, _int]
         L.gpch_timing_read.argtypes = [_vp, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
         L.gpch_launch_count.argtypes = [_vp]
@@ -114,7 +124,9 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(_i64)]
         L.gpch_solve_refined.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _int, _int, _dbl, _int,
                                          _vp, ctypes.POINTER(RefineStats)]
-        for name in ("gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
+        L.gpch_logdet.argtypes = [_vp, _i64, _vp, _i64, ctypes.POINTER(_dbl), _vp]
+        L.gpch_predict_mean.argtypes = [_vp, _i64, _i64, _int, _vp, _vp, _dbl, _dbl, _vp, _i64, _int, _vp, _i64, _vp]
+        for name in ("gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
                      "gpch_batched_solve", "gpch_server_create", "gpch_server_submit", "gpch_server_wait",
@@ -256,6 +268,40 @@ def chol_solve(L: torch.Tensor, B: torch.Tensor, ctx: Context | None = None, str
     return B
 
 
+def logdet(L: torch.Tensor, ctx: Context | None = None, stream=None) -> float:
+    """f3: log det A = 2 sum log L_ii from the column-major FP64 factor L
+    (as left by chol_factor).  Synchronizes the stream."""
+    ctx = ctx or default_context()
+    _check_cuda(L, torch.float64)
+    out = _dbl(0.0)
+    ctx.check(lib().gpch_logdet(ctx.handle, L.shape[0], L.data_ptr(), _ld(L), ctypes.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+def predict_mean(Xs: torch.Tensor, X: torch.Tensor, sf2: float, ell: float, alpha: torch.Tensor,
+                 mean: torch.Tensor | None = None, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """f3: GP predictive mean K(Xs, X) alpha (noise-free SE cross
+    covariance formed on the fly).  Xs: m x d, X: n x d (row-major float64
+    CUDA); alpha: n x nrhs column-major.  Returns mean (m x nrhs,
+    column-major)."""
+    ctx = ctx or default_context()
+    _check_cuda(Xs, torch.float64)
+    _check_cuda(X, torch.float64)
+    _check_cuda(alpha, torch.float64)
+    Xs = Xs.contiguous()
+    X = X.contiguous()
+    m, d = Xs.shape
+    n = X.shape[0]
+    if X.shape[1] != d or alpha.shape[0] != n:
+        raise ValueError("shape mismatch between Xs, X and alpha")
+    nrhs = alpha.shape[1]
+    if mean is None:
+        mean = colmajor(m, nrhs, device=Xs.device)
+    ctx.check(lib().gpch_predict_mean(ctx.handle, m, n, d, Xs.data_ptr(), X.data_ptr(), sf2, ell, alpha.data_ptr(),
+                                      _ld(alpha), nrhs, mean.data_ptr(), _ld(mean), _stream(stream)))
+    return mean
+
+
 @dataclass
 class CGResult:
     iterations: int
@@ -264,11 +310,17 @@ class CGResult:
     status: int
 
 
+_CG_VARIANT = {"classic": CG_CLASSIC, "single_reduction": CG_SINGLE_REDUCTION}
+_CG_PRODUCTS = {"fp64": CG_PRODUCTS_FP64, "double_float": CG_PRODUCTS_DOUBLE_FLOAT}
+
+
 def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e-10, maxit: int = 10000,
              replace_every: int = 50, ctx: Context | None = None, stream=None,
-             raise_on_not_converged: bool = True) -> CGResult:
+             raise_on_not_converged: bool = True, variant: str = "classic", products: str = "fp64") -> CGResult:
     """A6-A7: CG (Algorithm 1, left) on the full column-major A (float64 or
-    float32), right-hand sides B and start/solution X (n x nrhs, float64)."""
+    float32), right-hand sides B and start/solution X (n x nrhs, float64).
+    variant: "classic" or "single_reduction" (Chronopoulos-Gear); products:
+    "fp64" or "double_float" (FP32-pipe double-float products)."""
     ctx = ctx or default_context()
     if A.dtype not in (torch.float64, torch.float32):
         raise ValueError("A must be float64 or float32")
@@ -277,9 +329,10 @@ def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e
     _check_cuda(X, torch.float64)
     stats = CGStats()
     dt = GPCH_F64 if A.dtype == torch.float64 else GPCH_F32
-    st = lib().gpch_cg_solve(ctx.handle, A.shape[0], A.data_ptr(), dt, _ld(A), B.data_ptr(), _ld(B), X.data_ptr(),
-                             _ld(X), B.shape[1], rtol, int(maxit), int(replace_every), _stream(stream),
-                             ctypes.byref(stats))
+    opts = CGOpts(_CG_VARIANT[variant], _CG_PRODUCTS[products])
+    st = lib().gpch_cg_solve_ex(ctx.handle, A.shape[0], A.data_ptr(), dt, _ld(A), B.data_ptr(), _ld(B),
+                                X.data_ptr(), _ld(X), B.shape[1], rtol, int(maxit), int(replace_every),
+                                ctypes.byref(opts), _stream(stream), ctypes.byref(stats))
     if st != GPCH_OK and not (st == GPCH_NOT_CONVERGED and not raise_on_not_converged):
         ctx.check(st)
     return CGResult(stats.iterations, stats.converged, stats.relres_max, st)

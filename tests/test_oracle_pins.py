@@ -408,3 +408,152 @@ def test_solve_spd_matches_textbook_solve():
     kappa = np.linalg.cond(A)
     for r in range(2):
         assert oracle.forward_error(x[:, r], x_ref[:, r]) <= 50 * kappa * U
+
+
+# -------------------------------------------------- single-reduction CG (f2)
+def test_cg_single_reduction_first_step_by_hand():
+    """Same hand-worked first iteration as classic CG: r = b, w = A r =
+    (6, 7), gamma = 5, delta = w^T r = 20, alpha = 1/4, p = r, x_1 = r / 4;
+    two distinct eigenvalues, so the second iteration is exact."""
+    g = GOLD["cg_first_step"]
+    A = evm(g["A"])
+    b = np.array([ev(x) for x in g["b"]])
+    x1, it, _ = oracle.cg_single_reduction(A, b, 1e-14, 1, R=0)
+    assert it == 1
+    np.testing.assert_allclose(x1, [ev(s) for s in g["x1"]], rtol=4 * U)
+    x, it, _ = oracle.cg_single_reduction(A, b, 1e-14, 50, R=0)
+    assert it == g["iterations"]
+    np.testing.assert_allclose(x, [ev(s) for s in g["x"]], rtol=1e-14)
+
+
+def test_cg_single_reduction_diag_three_eigenvalues():
+    g = GOLD["cg_diag_123"]
+    A = np.diag([ev(x) for x in g["diag"]])
+    b = np.array([ev(x) for x in g["b"]])
+    x, it, _ = oracle.cg_single_reduction(A, b, 1e-14, 50, R=0)
+    assert it == g["iterations"]
+    np.testing.assert_allclose(x, [ev(s) for s in g["x"]], rtol=1e-14)
+
+
+def test_cg_single_reduction_scaled_identity_one_step():
+    b = np.array([1.0, -2.0, 3.0, 0.5])
+    x, it, rr = oracle.cg_single_reduction(4.0 * np.eye(4), b, 1e-12, 10, R=0)
+    assert it == 1 and rr == 0.0
+    np.testing.assert_array_equal(x, b / 4.0)
+
+
+@pytest.mark.parametrize("k", [2, 5, 9])
+def test_cg_single_reduction_k_distinct_eigenvalues(k):
+    """Householder Q diag(lambda) Q^T with k distinct eigenvalues: the Krylov
+    space is exhausted after k steps, so the residual reaches rounding level
+    by iteration k (one more allowed for rounding)."""
+    rng = np.random.default_rng(300 + k)
+    n = 40
+    v = rng.standard_normal(n)
+    Q = np.eye(n) - 2.0 * np.outer(v, v) / (v @ v)
+    lam = np.repeat(np.linspace(1.0, 10.0, k), int(np.ceil(n / k)))[:n]
+    A = Q @ np.diag(lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    b = rng.standard_normal(n)
+    x, it, rr = oracle.cg_single_reduction(A, b, 1e-12, 200, R=0)
+    assert it <= k + 1
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) < 1e-11
+
+
+def test_cg_single_reduction_iterates_equal_classic():
+    """The rearrangement changes no iterate in exact arithmetic: on a
+    well-conditioned SE system, after every iteration count j the two
+    algorithms' x agree to rounding level (a wrong beta, a stale alpha in
+    the delta - beta gamma / alpha correction, or s not tracking A p breaks
+    this at the second iteration)."""
+    sysm = inputs.gp_system(120, 8, 0.5, 0.5, seed=31)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    b = sysm.B[:, 0]
+    for j in (1, 2, 3, 5, 8):
+        xc, itc, _ = oracle.cg(A, b, 0.0, j, R=0)
+        xs, its, _ = oracle.cg_single_reduction(A, b, 0.0, j, R=0)
+        assert itc == its == j
+        assert oracle.forward_error(xs, xc) < 1e-12, j
+
+
+def test_cg_single_reduction_replacement_and_convergence():
+    """With replacement every 7 iterations the recurrence residual tracks
+    the true one, and the stop rule (relative recurrence residual <= eps)
+    holds for the true residual too."""
+    sysm = inputs.gp_system(200, 8, 0.5, 1e-2, seed=32)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    b = sysm.B[:, 0]
+    x, it, rr = oracle.cg_single_reduction(A, b, 1e-10, 5000, R=7)
+    assert rr <= 1e-10
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) < 1e-9
+    _, itc, _ = oracle.cg(A, b, 1e-10, 5000, R=7)
+    assert abs(it - itc) <= max(3, 0.05 * itc)
+
+
+# ------------------------------------------------------- GP quantities (f3)
+def test_logdet_hand_2x2():
+    g = GOLD["logdet_2x2"]
+    val, info = oracle.logdet(evm(g["A"]))
+    assert info == 0
+    assert abs(val - ev(g["logdet"])) <= 8 * U * abs(ev(g["logdet"]))
+
+
+def test_logdet_determinant_lemma():
+    g = GOLD["logdet_i_plus_vvt"]
+    v = np.array([ev(x) for x in g["v"]])
+    val, info = oracle.logdet(np.eye(3) + np.outer(v, v))
+    assert info == 0
+    assert abs(val - ev(g["logdet"])) <= 16 * U * abs(ev(g["logdet"]))
+    # a longer v: log(1 + v^T v), the factor still of size 50
+    rng = np.random.default_rng(41)
+    w = rng.standard_normal(50)
+    val, _ = oracle.logdet(np.eye(50) + np.outer(w, w))
+    assert abs(val - np.log1p(w @ w)) < 1e-12 * abs(np.log1p(w @ w))
+
+
+def test_logdet_diagonal_and_library():
+    a = np.array([0.5, 3.0, 7.0, 1e-3])
+    val, info = oracle.logdet(np.diag(a))
+    assert info == 0 and abs(val - np.sum(np.log(a))) < 1e-14 * np.sum(np.abs(np.log(a)))
+    sysm = inputs.gp_system(150, 8, 0.5, 1e-2, seed=42)
+    A = oracle.se_matrix(sysm.X, sysm.sf2, sysm.ell, sysm.sn2)
+    sign, ref = np.linalg.slogdet(A)
+    val, _ = oracle.logdet(A)
+    assert sign == 1.0 and abs(val - ref) < 1e-11 * abs(ref)
+
+
+def test_logdet_not_spd():
+    val, info = oracle.logdet(np.array([[1.0, 2.0], [2.0, 1.0]]))
+    assert info == 2 and np.isnan(val)
+
+
+def test_predict_mean_hand_1d():
+    g = GOLD["gp_mean_1d"]
+    X = np.array([[ev(x)] for x in g["X"]])
+    Xs = np.array([[ev(x)] for x in g["Xs"]])
+    alpha = np.array([ev(x) for x in g["alpha"]])
+    got = oracle.predict_mean(Xs, X, ev(g["sf2"]), ev(g["ell"]), alpha)
+    np.testing.assert_allclose(got, [ev(s) for s in g["mean"]], rtol=8 * U)
+
+
+def test_predict_mean_at_training_points():
+    """With alpha = (K + sn2 I)^-1 y the mean at the training points is
+    K alpha = y - sn2 alpha (the noise term is in the system, not in the
+    cross covariance): a dropped sf2, a wrong length scale (ell^2 for
+    2 ell^2), a transposed cross covariance or an added noise term each
+    break it."""
+    sysm = inputs.gp_system(180, 8, 0.5, 1e-1, nrhs=2, seed=43)
+    A = oracle.se_matrix(sysm.X, 1.7, sysm.ell, sysm.sn2)
+    alpha = np.linalg.solve(A, sysm.B)
+    mean = oracle.predict_mean(sysm.X, sysm.X, 1.7, sysm.ell, alpha)
+    np.testing.assert_allclose(mean, sysm.B - sysm.sn2 * alpha, rtol=0, atol=1e-11 * np.abs(sysm.B).max())
+
+
+def test_predict_mean_far_point_and_columns():
+    sysm = inputs.gp_system(40, 8, 0.5, 1e-2, nrhs=3, seed=44)
+    far = np.full((1, 8), 1e3)
+    np.testing.assert_array_equal(oracle.predict_mean(far, sysm.X, 1.0, 0.5, sysm.B), np.zeros((1, 3)))
+    Xs = inputs.points(7, 8, 45)
+    both = oracle.predict_mean(Xs, sysm.X, 1.0, 0.5, sysm.B)
+    for r in range(3):
+        np.testing.assert_array_equal(both[:, r], oracle.predict_mean(Xs, sysm.X, 1.0, 0.5, sysm.B[:, r]))
