@@ -46,9 +46,10 @@ FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032    # FFMA: 148 SMs x 128 lanes x 2 flop
 CPU_SAMPLE_N = 4096
 CPU_ALLCORES_N = 2048
 # DRAM bytes per algorithmic flop of syrk_tc_kernel (split-f16 update, a
-# K = 2048 pass): 91.9 MB over 4.993e10 flop in one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the n = 16384 update.
-SYRK_DRAM_BYTES_PER_FLOP = 1.841e-3
+# 16-panel long pass, K = 8192, m = 6656 rows x 512 columns): 248.4 MB over
+# 1.611e11 flop in one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the n = 16384 update.
+SYRK_DRAM_BYTES_PER_FLOP = 1.542e-3
 
 
 def ranks_max(v: float, dist=None, device: str = "cuda") -> float:
@@ -286,6 +287,157 @@ def roofline_of(phase_name, ms, launches, work, n, nrhs, pk):
             "frac": round(g / FP64_PEAK_GFLOPS, 4), "peak_source": "derived nominal FP64 rate"}
 
 
+def _cg_timed(ctx, A, B, X, variant, products, rtol, maxit, replace_every=50):
+    """One CG solve from x = 0, timed with CUDA events on the current
+    stream; returns (ms, result, matvec (ms, launches, bytes))."""
+    import torch
+    from paper_2605_13209_b300 import gpchol
+    X.zero_()
+    torch.cuda.synchronize()
+    ctx.timing_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = gpchol.cg_solve(A, B, X, rtol=rtol, maxit=maxit, replace_every=replace_every, ctx=ctx,
+                          raise_on_not_converged=False, variant=variant, products=products)
+    e1.record()
+    torch.cuda.synchronize()
+    mv = ctx.timing_read(gpchol.PHASE_CG_MATVEC)
+    ctx.timing_enable(False)
+    return e0.elapsed_time(e1), res, mv
+
+
+def _true_relres(A, B, X):
+    """max over columns of ||b - A x|| / ||b|| with the stored operator
+    (widened to FP64), on the device through torch (a check of the
+    solution, outside every timed region)."""
+    import torch
+    R = B - A.double() @ X if A.dtype != torch.float64 else B - A @ X
+    return float((R.norm(dim=0) / B.norm(dim=0)).max())
+
+
+def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
+    """CG measurements (Algorithm 1 left and its single-reduction form, FP64
+    or double-float products):
+      matrix2  the n = 32768 matrix, one RHS, args.cg_iters iterations of
+               each form (fixed count: rate, matvec GB/s against HBM)
+      config1  n = 2048 (33.5 MB, L2-resident), one RHS, solved to 1e-10
+      config3  n = 65536, ell = 0.3, sn2 = 0.1, 16 RHS, FP64-stored
+               (34.4 GB) and FP32-stored (17.2 GB) A, solved to 1e-10 with
+               replacement every 50 iterations (double-float products);
+               the FP64-product rate over a few iterations beside it"""
+    import torch
+    from paper_2605_13209_b300 import gpchol, inputs
+    hbm = pk.get("hbm_gbs", 6400.0)
+    out = {}
+    forms = [("classic", "fp64"), ("classic", "double_float"), ("single_reduction", "fp64"),
+             ("single_reduction", "double_float")]
+    X = gpchol.colmajor(n2, 1)
+    m2 = {}
+    for var, prod in forms:
+        _cg_timed(ctx, A2, b2, X, var, prod, 0.0, 3, 0)
+        ms, res, mv = _cg_timed(ctx, A2, b2, X, var, prod, 0.0, args.cg_iters, 0)
+        ms = max_over_ranks(ms)
+        mv_ms = mv[0] / max(mv[1], 1)
+        m2[f"{var}/{prod}"] = {"ms_per_iteration": round(ms / args.cg_iters, 4),
+                               "matvec_ms": round(mv_ms, 4),
+                               "matvec_gbs": round(n2 * n2 * 8 / (mv_ms / 1e3) / 1e9, 1),
+                               "matvec_frac_of_hbm": round(n2 * n2 * 8 / (mv_ms / 1e3) / 1e9 / hbm, 4)}
+    m2["what"] = (f"n={n2} FP64 matrix (8.6 GB), one RHS, {args.cg_iters} iterations from x = 0 per form; "
+                  "matvec GB/s = n^2 * 8 bytes / mean matvec launch time (CUDA events)")
+    out["matrix_n32768"] = m2
+
+    # config 1: n = 2048, L2-resident
+    s1 = inputs.config1()
+    A1 = gpchol.se_matrix(torch.from_numpy(s1.X).cuda(), s1.sf2, s1.ell, s1.sn2, ctx=ctx)
+    b1 = gpchol.as_colmajor(torch.from_numpy(s1.B).cuda())
+    X1 = gpchol.colmajor(2048, 1)
+    c1 = {}
+    for var, prod in forms:
+        _cg_timed(ctx, A1, b1, X1, var, prod, 1e-10, 100000)
+        ms, res, mv = _cg_timed(ctx, A1, b1, X1, var, prod, 1e-10, 100000)
+        mv_ms = mv[0] / max(mv[1], 1)
+        c1[f"{var}/{prod}"] = {"ms": round(ms, 3), "iterations": res.iterations, "converged": res.converged == 1,
+                               "us_per_iteration": round(1e3 * ms / max(res.iterations, 1), 2),
+                               "matvec_gbs_l2": round(2048 * 2048 * 8 / (mv_ms / 1e3) / 1e9, 1),
+                               "true_relres": _true_relres(A1, b1, X1)}
+    c1["what"] = ("n=2048 SE (ell=0.5, sn2=1e-2), one RHS, to relative residual 1e-10; the 33.5 MB matrix stays in "
+                  "L2, so matvec GB/s is an L2 rate")
+    out["config1"] = c1
+    del A1
+
+    # config 3: n = 65536, 16 RHS
+    if args.cg3_n > 0:
+        n3 = args.cg3_n
+        s3 = inputs.config3(n3, 16) if rank == 0 else inputs.gp_system(n3, 8, 0.3, 1e-1, nrhs=16, seed=3 + 1000 * rank)
+        A64 = gpchol.se_matrix(torch.from_numpy(s3.X).cuda(), s3.sf2, s3.ell, s3.sn2, ctx=ctx)
+        A32 = gpchol.colmajor(n3, n3, dtype=torch.float32)
+        A32.copy_(A64)                 # FP32 storage of the same operator (input preparation)
+        B3 = gpchol.as_colmajor(torch.from_numpy(s3.B).cuda())
+        X3 = gpchol.colmajor(n3, 16)
+        c3 = {}
+        for label, AA, el in (("fp64_stored", A64, 8), ("fp32_stored", A32, 4)):
+            _cg_timed(ctx, AA, B3, X3, "classic", "double_float", 0.0, 2, 0)
+            ms, res, mv = _cg_timed(ctx, AA, B3, X3, "classic", "double_float", 1e-10, 20000, 50)
+            ms = max_over_ranks(ms)
+            mv_ms = mv[0] / max(mv[1], 1)
+            gbs = n3 * n3 * el / (mv_ms / 1e3) / 1e9
+            ops = 4.0 * n3 * n3 * 16 / (mv_ms / 1e3) / 1e12
+            c3[label] = {"ms": round(ms, 1), "iterations": res.iterations, "converged": res.converged,
+                         "ms_per_iteration": round(ms / max(res.iterations, 1), 3),
+                         "matvec_ms_mean": round(mv_ms, 3), "matvec_gbs": round(gbs, 1),
+                         "matvec_frac_of_hbm": round(gbs / hbm, 4),
+                         "products_tera_per_s": round(ops / 4.0, 3),
+                         "true_relres_max": _true_relres(AA, B3, X3)}
+            # FP64 products on the same operator: rate over a few iterations
+            _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, 1, 0)
+            ms64, res64, mv64 = _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, args.cg3_fp64_iters, 0)
+            mv64_ms = mv64[0] / max(mv64[1], 1)
+            c3[label]["fp64_products"] = {
+                "iterations": args.cg3_fp64_iters, "ms_per_iteration": round(ms64 / args.cg3_fp64_iters, 3),
+                "matvec_ms_mean": round(mv64_ms, 3),
+                "frac_of_fp64_fma_rate": round(n3 * n3 * 16 / (mv64_ms / 1e3) / (FP64_PEAK_GFLOPS * 1e9 / 2), 4)}
+        c3["what"] = (f"n={n3} SE (ell=0.3, sn2=0.1), 16 RHS, classic CG with double-float products to relative "
+                      "residual 1e-10 (replacement every 50 iterations, FP64 true residuals); FP32-stored A is the "
+                      "FP32 rounding of the FP64 matrix; products_tera_per_s = n^2 * 16 / matvec time")
+        out["config3"] = c3
+        del A64, A32, B3, X3
+    return out
+
+
+def serve_run(device, solo, rate, count, nmax):
+    """One serving run: `count` requests of the seeded Poisson stream at
+    `rate` per second, submitted at their arrival times, all waited for."""
+    from paper_2605_13209_b300 import gpchol, inputs
+    rs = inputs.request_stream(count=count, rate_per_s=rate, nmin=512, nmax=nmax)
+    reqs = []
+    for i in range(count):
+        nq = int(rs.ns[i])
+        reqs.append((inputs.points(nq, 8, int(rs.seeds[i])), inputs.rhs(nq, int(rs.nrhs[i]), int(rs.seeds[i]) + 1),
+                     float(rs.ells[i]), float(rs.sn2s[i])))
+    srv = gpchol.Server(device, hbm_budget=160 << 30, lanes=4, batch_max_count=32, batch_max_n=2048,
+                        solo_prec=solo)
+    t0 = time.perf_counter()
+    tickets = []
+    for i, (Xr, Br, ell, sn2) in enumerate(reqs):
+        delay = t0 + float(rs.arrival_s[i]) - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(Xr, Br, 1.0, ell, sn2))
+    worst, paths = 0.0, {1: 0, 2: 0, 3: 0}
+    for t in tickets:
+        _, r = srv.wait(t)
+        worst = max(worst, r["backward_error"])
+        paths[r["path"]] = paths.get(r["path"], 0) + 1
+    st = srv.stats()
+    srv.close()
+    return {"requests": count, "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+            "max_ms": round(st["max_ms"], 2), "solves_per_s": round(st["solves_per_s"], 2),
+            "completed": st["completed"], "failed": st["failed"], "batches": st["batches"],
+            "batched_requests": st["batched_requests"], "solo_requests": paths.get(2, 0) + paths.get(3, 0),
+            "peak_reserved_gb": round(st["peak_reserved_bytes"] / 2 ** 30, 2),
+            "max_refined_backward_error": worst}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,14 +449,18 @@ def main():
     ap.add_argument("--prec", default="split_f16", choices=["split_f16", "split_bf16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cg-iters", type=int, default=100)
+    ap.add_argument("--cg3-n", type=int, default=65536, help="n of the 16-RHS CG leg (0 = skip)")
+    ap.add_argument("--cg3-fp64-iters", type=int, default=5)
     ap.add_argument("--cpu-sample-n", type=int, default=CPU_SAMPLE_N)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle check of the solutions")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-nmax", type=int, default=8192)
-    ap.add_argument("--serve-rates", default="20,80")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-nmax", type=int, default=16384)
+    ap.add_argument("--serve-rates", default="50,100,150,200")
+    ap.add_argument("--serve-fp64-requests", type=int, default=40)
+    ap.add_argument("--serve-fp64-rates", default="1,3")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -385,7 +541,7 @@ def main():
                 "traffic": (round(SYRK_DRAM_BYTES_PER_FLOP * work_per_launch)
                             if SYRK_DRAM_BYTES_PER_FLOP is not None and args.prec != "bf16" else None),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one syrk_tc_kernel launch "
-                                  "(split-f16, K = 2048, n = 16384), scaled by the launch's work"}
+                                  "(split-f16 long pass, K = 8192, n = 16384), scaled by the launch's work"}
     phases = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] / args.steps,
                   "roofline": roofline_of(k, *v, n, 1, pk)} for k, v in phase.items()}
 
@@ -416,33 +572,14 @@ def main():
                 "what": f"FP64 blocked Cholesky (tile {tile}) + forward/back substitution"}
         del Aw
 
-    # ---------------------------------------------------------- CG leg
+    # ---------------------------------------------------------- CG legs
     cg = None
     if args.cg_iters > 0:
-        Xc = gpchol.colmajor(n, 1)
-        Xc.zero_()
-        gpchol.cg_solve(A0, bd, Xc, rtol=0.0, maxit=5, replace_every=0, ctx=ctx, raise_on_not_converged=False)
-        Xc.zero_()
-        torch.cuda.synchronize()
-        ctx.timing_enable(True)
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record()
-        gpchol.cg_solve(A0, bd, Xc, rtol=0.0, maxit=args.cg_iters, replace_every=0, ctx=ctx,
-                        raise_on_not_converged=False)
-        g1.record()
-        torch.cuda.synchronize()
-        mv = ctx.timing_read(gpchol.PHASE_CG_MATVEC)
-        ctx.timing_enable(False)
-        gms = max_over_ranks(g0.elapsed_time(g1))
-        per_it = gms / args.cg_iters
-        cg = {"iterations": args.cg_iters, "ms_per_iteration": round(per_it, 4),
-              "gbs": round(world * n * n * 8 / (per_it / 1e3) / 1e9, 1),
-              "matvec_roofline": roofline_of("cg_matvec", *mv, n, 1, pk),
-              "what": "Algorithm 1 (left), FP64 full matrix, one RHS, fixed iteration count"}
+        cg = cg_legs(args, ctx, A0, bd, n, world, pk, max_over_ranks, rank)
 
     # ---------------------------------------------------------- batched leg
     batched = None
-    xs_batched = None
+    xs_batched = xs_mixed = None
     if args.batch_count > 0:
         spec = inputs.batch_spec(count=args.batch_count, nmin=256, nmax=4096, seed=4)
         Ab, Bb, Bb0, Xp = [], [], [], []
@@ -473,47 +610,45 @@ def main():
         bms = max_over_ranks(min(times))
         xs_batched = [b[:, 0].cpu().numpy().copy() for b in Bb]
         batched = {"systems": args.batch_count, "n_range": [int(spec.ns.min()), int(spec.ns.max())],
-                   "ms_per_batch": round(bms, 2), "gflops": round(world * bflops / (bms / 1e3) / 1e9, 2),
-                   "frac_of_fp64_peak": round(bflops / (bms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
-                   "what": "FP64 batched factor + solve of 256 SE systems, n log-uniform [256, 4096], one graph launch"}
+                   "fp64": {"ms_per_batch": round(bms, 2), "gflops": round(world * bflops / (bms / 1e3) / 1e9, 2),
+                            "frac_of_fp64_peak": round(bflops / (bms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
+                            "what": "FP64 blocked Cholesky (64-wide blocks) + substitution, one graph launch"}}
+        # mixed: FP32 factors with FP64 diagonal leaves, FP64 iterative refinement to 1e-12
+        refill()
+        Xb = [gpchol.colmajor(b.shape[0], 1) for b in Bb]
+        gpchol.batched_solve_mixed(Ab, Bb, Xb, bwd_tol=1e-12, maxit=30, ctx=ctx)   # captures the graphs
+        mtimes, mres = [], None
+        for _ in range(3):
+            for x in Xb:
+                x.zero_()
+            torch.cuda.synchronize()
+            ctx.timing_enable(True)
+            mres = gpchol.batched_solve_mixed(Ab, Bb, Xb, bwd_tol=1e-12, maxit=30, ctx=ctx)
+            mtimes.append(ctx.timing_read(gpchol.PHASE_BATCHED)[0])
+            ctx.timing_enable(False)
+        mms = max_over_ranks(min(mtimes))
+        xs_mixed = [x[:, 0].cpu().numpy().copy() for x in Xb]
+        batched["mixed"] = {"ms_per_batch": round(mms, 2), "gflops_equivalent": round(world * bflops / (mms / 1e3) / 1e9, 2),
+                            "speedup_vs_fp64": round(bms / mms, 2), "refinement_iterations_max": mres.iterations,
+                            "refinement_steps": mres.steps, "backward_error_lib": mres.backward_error_max,
+                            "what": "FP32 factor (64-wide blocks, FP64 diagonal leaves) + FP64 iterative refinement "
+                                    "to backward error 1e-12, one graph launch (+ replayed steps if needed)"}
+        del Xb
         del Ab, Bb, Bb0, Xp
 
     # ---------------------------------------------------------- serving leg
     serving = None
     if args.serve_requests > 0 and rank == 0:
         serving = {}
-        rates = [float(r) for r in args.serve_rates.split(",") if r]
-        for label, solo in (("mixed", args.prec), ("fp64_only", "fp64")):
-            for rate in rates:
-                rs = inputs.request_stream(count=args.serve_requests, rate_per_s=rate, nmin=512, nmax=args.serve_nmax)
-                reqs = []
-                for i in range(args.serve_requests):
-                    nq = int(rs.ns[i])
-                    reqs.append((inputs.points(nq, 8, int(rs.seeds[i])), inputs.rhs(nq, int(rs.nrhs[i]),
-                                 int(rs.seeds[i]) + 1), float(rs.ells[i]), float(rs.sn2s[i])))
-                srv = gpchol.Server(local, hbm_budget=160 << 30, lanes=4, batch_max_count=32, batch_max_n=2048,
-                                    solo_prec=solo)
-                t0 = time.perf_counter()
-                tickets = []
-                for i, (Xr, Br, ell, sn2) in enumerate(reqs):
-                    delay = t0 + float(rs.arrival_s[i]) - time.perf_counter()
-                    if delay > 0:
-                        time.sleep(delay)
-                    tickets.append(srv.submit(Xr, Br, 1.0, ell, sn2))
-                worst = 0.0
-                for t in tickets:
-                    _, r = srv.wait(t)
-                    worst = max(worst, r["backward_error"])
-                st = srv.stats()
-                srv.close()
-                serving[f"{label}@{rate:g}/s"] = {
-                    "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
-                    "solves_per_s": round(st["solves_per_s"], 2), "completed": st["completed"],
-                    "failed": st["failed"], "batches": st["batches"], "batched_requests": st["batched_requests"],
-                    "max_refined_backward_error": worst}
-        serving["what"] = (f"{args.serve_requests} Poisson requests per rate, n log-uniform [512, {args.serve_nmax}], "
-                           "1-8 RHS, 160 GB budget, 4 lanes, n <= 2048 batched (FP64); larger solo: mixed "
-                           f"{args.prec} refined vs FP64-only")
+        runs = [("mixed", args.prec, float(r), args.serve_requests) for r in args.serve_rates.split(",") if r]
+        runs += [("fp64_only", "fp64", float(r), args.serve_fp64_requests)
+                 for r in args.serve_fp64_rates.split(",") if r and args.serve_fp64_requests > 0]
+        for label, solo, rate, count in runs:
+            serving[f"{label}@{rate:g}/s"] = serve_run(local, solo, rate, count, args.serve_nmax)
+        serving["what"] = (f"seeded Poisson streams, n log-uniform [512, {args.serve_nmax}], 1-8 RHS, ell ~ U[0.2, 1], "
+                           "sn2 ~ U[1e-3, 1e-1]; 160 GB budget, 4 lanes; n <= 2048 grouped into batched FP64 launches "
+                           f"(up to 32 per batch); larger requests solo: mixed = {args.prec} refined to backward error "
+                           "1e-12, fp64_only = FP64 factor + solve; latency = completion - submission")
 
     # ---------------------------------------------------------- e2e
     Xh = torch.from_numpy(sysm.X).pin_memory()
@@ -546,7 +681,8 @@ def main():
 
     check = oracle_check(sysm, x_mixed, x_fp64, L_block) if not args.no_check else None
     if batched is not None and xs_batched is not None and not args.no_check:
-        batched["backward_error_max"] = batched_check(args.batch_count, xs_batched)
+        batched["fp64"]["backward_error_max"] = batched_check(args.batch_count, xs_batched)
+        batched["mixed"]["backward_error_max"] = batched_check(args.batch_count, xs_mixed)
         batched["backward_error_by"] = "oracle on every system (host, long-double residual)"
     if fp64 is not None and check is not None:
         fp64["backward_error"] = check["backward_error_fp64"]

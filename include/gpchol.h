@@ -243,6 +243,75 @@ gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype
                              int maxit, int replace_every, const gpch_cg_opts *opts, void *stream,
                              gpch_cg_stats *stats);
 
+/* ------------------------- row-split CG across ranks: local steps (f4) */
+
+/* A CG solve whose rows are split over ranks (one GPU each): the paper's
+ * horizontal split of the matrix between CPU and GPU (Sec. 3.1), carried
+ * to several GPUs.  Rank k owns rows r0 .. r0+m-1 of the symmetric A,
+ * stored as the n x m column block A[:, r0 : r0+m] (by symmetry the same
+ * numbers), and the matching m rows of x, b and every CG vector.  The
+ * single-reduction form of gpch_cg_solve_ex runs as:
+ *   setup  allgather x0 -> v;  t = Ablk^T v;  r = b - t          (residual, all = 1)
+ *          allgather r -> v;  w = Ablk^T v;  partials(r, w) -> sums;
+ *          allreduce(sums);  scalars(first = 1)
+ *   loop   vectors(replace);
+ *          on replacement iterations: allgather x -> v; t = Ablk^T v;
+ *              r = b - t (residual, all = 0); allgather p -> v; s = Ablk^T v
+ *          allgather r -> v;  w = Ablk^T v;  partials(r, w) -> sums;
+ *          allreduce(sums);  scalars(first = 0);  stop when state.done
+ * The caller moves the data between ranks (the allgather of one n x nrhs
+ * vector and the allreduce of 2 nrhs doubles per iteration, e.g. over
+ * NCCL); these calls make every arithmetic step on the rank's rows.  Every
+ * rank's scalar state evolves identically because it is computed from the
+ * same reduced sums.  All pointers are device memory; asynchronous on
+ * `stream`; nrhs <= 16. */
+
+/* Device-resident scalar state of one rank's solve (caller-allocated,
+ * sizeof(gpch_cgsr_state) bytes of device memory, 8-byte aligned). */
+typedef struct gpch_cgsr_state {
+    double gamma[16], gamma0[16], alpha[16], beta[16];
+    int32_t active[16], iters[16];
+    int32_t done, pad_;
+} gpch_cgsr_state;
+
+/* T = Ablk^T V: rows r0 .. r0+m-1 of A V for the symmetric n x n A whose
+ * columns r0 .. r0+m-1 are the n x m block Ablk (lda >= n; its diagonal
+ * entries are Ablk[r0 + j + j lda]).  V: n x nrhs (ldv >= n); T: m x nrhs
+ * (ldt >= m).  products: gpch_cg_products (FP64 or double-float, as in
+ * gpch_cg_solve_ex; the double-float scales come from the block's diagonal
+ * entries and V's columns).  With m = n and r0 = 0 this is A V.
+ * Workspace from the context arena.  Errors: INVALID_ARG. */
+gpch_status gpch_block_matvec(gpch_ctx *ctx, int64_t n, int64_t m, int64_t r0, const void *Ablk,
+                              gpch_dtype dtype, int64_t lda, const double *V, int64_t ldv, double *T,
+                              int64_t ldt, int nrhs, int32_t products, void *stream);
+
+/* sums[c] = sum_i R_ic^2 and sums[nrhs + c] = sum_i W_ic R_ic over the m
+ * local rows (fixed-order reduction).  sums: device, 2 nrhs doubles. */
+gpch_status gpch_cgsr_partials(gpch_ctx *ctx, int64_t m, int nrhs, const double *R, int64_t ldr,
+                               const double *W, int64_t ldw, double *sums, void *stream);
+
+/* Scalar step from the ranks' summed partials (gamma' = sums[c],
+ * delta = sums[nrhs + c]).  first = 1: gamma_0 = gamma = gamma',
+ * alpha = gamma'/delta, beta = 0, iters = 0, active = gamma' > 0.
+ * Otherwise, on active columns: iters += 1, beta = gamma'/gamma,
+ * alpha = gamma'/(delta - beta gamma'/alpha), gamma = gamma', and the
+ * column retires when gamma' <= rtol^2 gamma_0 or iters >= maxit.  done is
+ * set when no column is active. */
+gpch_status gpch_cgsr_scalars(gpch_ctx *ctx, int nrhs, const double *sums, gpch_cgsr_state *state,
+                              int first, double rtol, int maxit, void *stream);
+
+/* On active columns: p = r + beta p; s = w + beta s; x += alpha p; and,
+ * unless `replace`, r -= alpha s.  R, W, P, S: m x nrhs with leading
+ * dimension ld; X: m x nrhs (ldx).  P and S start at zero. */
+gpch_status gpch_cgsr_vectors(gpch_ctx *ctx, int64_t m, int nrhs, gpch_cgsr_state *state, double *X,
+                              int64_t ldx, double *R, const double *W, double *P, double *S, int64_t ld,
+                              int replace, void *stream);
+
+/* r = b - t on the active columns (on every column with all = 1).  B:
+ * m x nrhs (ldb); T and R: m x nrhs (ld). */
+gpch_status gpch_cgsr_residual(gpch_ctx *ctx, int64_t m, int nrhs, gpch_cgsr_state *state, const double *B,
+                               int64_t ldb, const double *T, double *R, int64_t ld, int all, void *stream);
+
 /* ------------------------------------- allocation-free CG (no paper
  * counterpart: the paper has no allocation-free variant; this is a
  * service to callers of the library) */
@@ -312,6 +381,50 @@ typedef struct gpch_system {
  * `stream`. */
 gpch_status gpch_batched_solve(gpch_ctx *ctx, int count, const gpch_system *systems, void *stream,
                                int64_t *info);
+
+/* One system of a mixed-precision batch: A (device, FP64, n x n, both
+ * triangles, lda >= n) and B (device, n x nrhs, ldb >= n) are read only;
+ * X (device, n x nrhs, ldx >= n) receives the solution.  nrhs <= 16. */
+typedef struct gpch_msystem {
+    int64_t n;
+    const double *A;
+    int64_t lda;
+    const double *B;
+    int64_t ldb;
+    double *X;
+    int64_t ldx;
+    int32_t nrhs;
+} gpch_msystem;
+
+typedef struct gpch_batch_stats {
+    int32_t iterations;          /* refinement corrections, max over systems  */
+    int32_t steps;               /* refinement steps the batch ran            */
+    double backward_error_max;   /* max over systems and columns at exit      */
+} gpch_batch_stats;
+
+/* Mixed-precision batched solve of `count` independent SPD systems: per
+ * system an FP32 Cholesky factor, Algorithm 1 (right) with 64-wide blocks
+ * (step 1 in FP64 on the widened 64 x 64 diagonal block, its FP64 inverse
+ * kept; step 2 as the product with that inverse; step 3 in FP32), then
+ * iterative refinement in FP64 until every column's normwise backward
+ * error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= bwd_tol:
+ * x_0 = L^-T L^-1 b, then r = b - A x (FP64 products, A intact) and
+ * x += L^-T L^-1 r.  Step k of all systems runs as one grouped launch per
+ * kernel kind, each system tiled by its own size only (a system's result
+ * does not depend on its batch-mates), and the launch sequence (set-up,
+ * factor, first solve, 4 refinement steps) is captured once as a CUDA graph
+ * per set of systems (same sizes and pointers), replayed by later calls; a
+ * batch that needs more steps replays a captured single step (at most
+ * maxit steps, maxit >= 4).  The context keeps up to 8 captured batches
+ * (their FP32 factors and work vectors, about 4 n^2 + 32 n nrhs bytes per
+ * system) until gpch_destroy.
+ * info (host, count entries): 0; the 1-based column where the FP32 factor
+ * broke down (returns GPCH_NOT_SPD); or -1 if refinement stopped improving
+ * (its error no longer halving per step) or reached maxit before bwd_tol
+ * (returns GPCH_NOT_CONVERGED).  stats (host, may be NULL).  Synchronizes
+ * `stream`. */
+gpch_status gpch_batched_solve_mixed(gpch_ctx *ctx, int count, const gpch_msystem *systems, double bwd_tol,
+                                     int maxit, void *stream, int64_t *info, gpch_batch_stats *stats);
 
 /* -------------------------------------------------- A11: serving loop */
 

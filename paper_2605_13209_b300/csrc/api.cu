@@ -105,6 +105,7 @@ gpch_status gpch_destroy(gpch_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     gpch::batched_release(ctx);
+    gpch::batched_mixed_release(ctx);
     for (auto &v : ctx->pending)
         for (auto &t : v) {
             cudaEventDestroy(t.start);

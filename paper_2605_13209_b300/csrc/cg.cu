@@ -185,7 +185,84 @@ __device__ __forceinline__ void df_split_a(double a, unsigned ebias, float &head
 
 // ------------------------------------------------------------- the matvec
 
-// T[:, r] = A S[:, r] on the CTA's W columns, then per mode:
+// Tail of a matvec CTA, once tcol[c * NR + r] holds (A s)_(j0 + c), r for
+// its W columns: store T, then the mode's partial sums and, in the last
+// CTA, the mode's scalar step (see cg_matvec_kernel).
+template <int W, int NR>
+__device__ __forceinline__ void mv_finish(int64_t j0, int wcols, int nrhs, const double *__restrict__ S, int64_t lds,
+                                          double *T, int64_t ldt, const CGState &st, int mode, const SRArgs &sr,
+                                          const double *tcol)
+{
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if (tid < W * NR) {
+        const int c = tid / NR, r = tid % NR;
+        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = tcol[tid];
+    }
+    if (mode == MV_PLAIN) return;
+    if (mode == MV_ALPHA) {
+        if (tid < NR) {
+            double p = 0.0;
+            for (int c = 0; c < wcols; ++c)
+                if (tid < nrhs) p = fma(S[(j0 + c) + tid * lds], tcol[c * NR + tid], p);
+            st.part[(size_t)blockIdx.x * NR + tid] = p;
+        }
+        if (last_cta(&st.counter[0])) {
+            for (int r = 0; r < nrhs; ++r) {
+                const double q = block_sum_partials(st.part, NR, r);
+                if (tid == 0) st.alpha[r] = st.active[r] ? st.u[r] / q : 0.0;
+            }
+            if (tid == 0) st.counter[0] = 0;
+        }
+        return;
+    }
+    // MV_SR: S is r, T is w
+    if (tid < NR) {
+        double g = 0.0, d = 0.0;
+        for (int c = 0; c < wcols; ++c)
+            if (tid < nrhs) {
+                const double rj = S[(j0 + c) + tid * lds];
+                g = fma(rj, rj, g);
+                d = fma(tcol[c * NR + tid], rj, d);
+            }
+        st.part[(size_t)blockIdx.x * 2 * NR + tid] = g;
+        st.part[(size_t)blockIdx.x * 2 * NR + NR + tid] = d;
+    }
+    if (last_cta(&st.counter[0])) {
+        __shared__ int any_active;
+        if (tid == 0) any_active = 0;
+        for (int r = 0; r < nrhs; ++r) {
+            const double g = block_sum_partials(st.part, 2 * NR, r);
+            const double d = block_sum_partials(st.part, 2 * NR, NR + r);
+            if (tid == 0) {
+                if (sr.first) {
+                    st.u0[r] = g;
+                    st.u[r] = g;
+                    st.iters[r] = 0;
+                    st.beta[r] = 0.0;
+                    st.alpha[r] = g > 0.0 ? g / d : 0.0;
+                    st.active[r] = g > 0.0 ? 1 : 0;
+                } else if (st.active[r]) {
+                    const int it = st.iters[r] + 1;
+                    st.iters[r] = it;
+                    const double b = g / st.u[r];
+                    st.alpha[r] = g / (d - b * g / st.alpha[r]);
+                    st.beta[r] = b;
+                    st.u[r] = g;
+                    if (g <= sr.rtol2 * st.u0[r] || it >= sr.maxit) st.active[r] = 0;
+                }
+                any_active |= st.active[r];
+            }
+        }
+        if (tid == 0) {
+            *st.done = any_active ? 0 : 1;
+            st.counter[0] = 0;
+        }
+    }
+}
+
+// T[:, r] = A^T S[:, r] on the CTA's W columns of the n x ncols matrix A
+// (ncols = n for a whole symmetric A, where A^T S = A S), then per mode:
 //   MV_ALPHA  partial s^T t; the last CTA sets alpha = u / s^T t
 //   MV_PLAIN  nothing more (t = A x for a true residual)
 //   MV_SR     partial r^T r and w^T r (S = r, T = w); the last CTA runs the
@@ -193,7 +270,7 @@ __device__ __forceinline__ void df_split_a(double a, unsigned ebias, float &head
 // With DF the products read the pre-split DFArgs::SS; S itself is read only
 // for the CTA's own columns (the partial dot products).
 template <typename TA, int W, int NR, bool DF>
-__global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int nrhs, const TA *__restrict__ A,
+__global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int64_t ncols, int nrhs, const TA *__restrict__ A,
                                                             int64_t lda, const double *__restrict__ S,
                                                             int64_t lds, double *T, int64_t ldt, CGState st,
                                                             int mode, SRArgs sr, DFArgs df, int vec)
@@ -205,7 +282,7 @@ __global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int nrhs,
     if (*st.done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t j0 = (int64_t)blockIdx.x * W;
-    const int wcols = (int)((n - j0 < W) ? n - j0 : W);
+    const int wcols = (int)((ncols - j0 < W) ? ncols - j0 : W);
 
     // FP64 path: acc[c][r]; DF path: head/tail pairs
     double acc[DF ? 1 : W][DF ? 1 : NR];
@@ -331,71 +408,139 @@ __global__ void __launch_bounds__(THREADS) cg_matvec_kernel(int64_t n, int nrhs,
             tcol[tid] = v;
         }
     }
-    if (tid < W * NR) {
-        const int c = tid / NR, r = tid % NR;
-        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = tcol[tid];
-    }
-    if (mode == MV_PLAIN) return;
-    __syncthreads();
-    if (mode == MV_ALPHA) {
-        if (tid < NR) {
-            double p = 0.0;
-            for (int c = 0; c < wcols; ++c)
-                if (tid < nrhs) p = fma(S[(j0 + c) + tid * lds], tcol[c * NR + tid], p);
-            st.part[(size_t)blockIdx.x * NR + tid] = p;
+    mv_finish<W, NR>(j0, wcols, nrhs, S, lds, T, ldt, st, mode, sr, tcol);
+}
+
+// Double-float matvec for several right-hand sides (NR = 4, 8, 16), tiled
+// so that the split vector is read from L2 once per 16 columns: a CTA owns
+// 16 columns, two per warp, and walks the rows in chunks of 32 * RPL rows
+// (RPL = 2 FP64 or 4 FP32 rows per lane, one 16-byte load per column).
+// Each chunk of the split vector is staged in shared memory, heads and
+// tails in separate arrays padded to NR + 1 floats per row so that the
+// lanes' rows fall in distinct banks; the next chunk's vector and matrix
+// entries are loaded while the current one is computed.  Every (column,
+// right-hand side) sum lives in one warp and is reduced by shuffles.
+constexpr int TW = 16;                     // columns per CTA of the tiled kernel
+
+template <typename TA, int NR>
+__global__ void __launch_bounds__(THREADS) cg_matvec_df_tiled_kernel(int64_t n, int64_t ncols, int nrhs,
+                                                                     const TA *__restrict__ A,
+                                                                     int64_t lda, const double *__restrict__ S,
+                                                                     int64_t lds, double *T, int64_t ldt,
+                                                                     CGState st, int mode, SRArgs sr, DFArgs df,
+                                                                     int vec)
+{
+    constexpr int RPL = 16 / sizeof(TA);           // rows per lane and chunk
+    constexpr int KC = 32 * RPL;                   // rows per chunk
+    constexpr int SPT = KC * NR / THREADS;         // split-vector pairs each thread stages per chunk
+    constexpr bool SPLIT_A = sizeof(TA) == 8;
+    static_assert(SPT >= 1 && KC * NR % THREADS == 0, "chunk must split evenly over the CTA");
+    __shared__ float sh_s[KC][NR + 1], sl_s[KC][NR + 1];
+    __shared__ double tcol[TW * NR];
+    if (*st.done) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t j0 = (int64_t)blockIdx.x * TW;
+    const int wcols = (int)((ncols - j0 < TW) ? ncols - j0 : TW);
+    const int c0 = 2 * warp;                       // this warp's two columns (local)
+    const unsigned ebias = SPLIT_A ? (unsigned)*df.ebias : 0u;
+    const TA *col[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) col[c] = A + (j0 + (c0 + c < wcols ? c0 + c : 0)) * lda;
+
+    float ah[2][NR], al[2][NR];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) ah[c][r] = al[c][r] = 0.0f;
+
+    // staged loads of one chunk: split-vector pairs and this lane's rows of
+    // the warp's two columns
+    float2 sv[SPT];
+    TA av[2][RPL];
+    auto load_chunk = [&](int64_t base) {
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+            const int64_t e = base * NR + (int64_t)q * THREADS + tid;   // element of SS, row-major by row
+            sv[q] = (e < n * NR) ? df.SS[e] : make_float2(0.0f, 0.0f);
         }
-        if (last_cta(&st.counter[0])) {
-            for (int r = 0; r < nrhs; ++r) {
-                const double q = block_sum_partials(st.part, NR, r);
-                if (tid == 0) st.alpha[r] = st.active[r] ? st.u[r] / q : 0.0;
-            }
-            if (tid == 0) st.counter[0] = 0;
-        }
-        return;
-    }
-    // MV_SR: S is r, T is w
-    if (tid < NR) {
-        double g = 0.0, d = 0.0;
-        for (int c = 0; c < wcols; ++c)
-            if (tid < nrhs) {
-                const double rj = S[(j0 + c) + tid * lds];
-                g = fma(rj, rj, g);
-                d = fma(tcol[c * NR + tid], rj, d);
-            }
-        st.part[(size_t)blockIdx.x * 2 * NR + tid] = g;
-        st.part[(size_t)blockIdx.x * 2 * NR + NR + tid] = d;
-    }
-    if (last_cta(&st.counter[0])) {
-        __shared__ int any_active;
-        if (tid == 0) any_active = 0;
-        for (int r = 0; r < nrhs; ++r) {
-            const double g = block_sum_partials(st.part, 2 * NR, r);
-            const double d = block_sum_partials(st.part, 2 * NR, NR + r);
-            if (tid == 0) {
-                if (sr.first) {
-                    st.u0[r] = g;
-                    st.u[r] = g;
-                    st.iters[r] = 0;
-                    st.beta[r] = 0.0;
-                    st.alpha[r] = g > 0.0 ? g / d : 0.0;
-                    st.active[r] = g > 0.0 ? 1 : 0;
-                } else if (st.active[r]) {
-                    const int it = st.iters[r] + 1;
-                    st.iters[r] = it;
-                    const double b = g / st.u[r];
-                    st.alpha[r] = g / (d - b * g / st.alpha[r]);
-                    st.beta[r] = b;
-                    st.u[r] = g;
-                    if (g <= sr.rtol2 * st.u0[r] || it >= sr.maxit) st.active[r] = 0;
+        const int64_t row0 = base + (int64_t)lane * RPL;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (vec && row0 + RPL <= n) {
+                if constexpr (sizeof(TA) == 8) {
+                    const double2 v = __ldcs(reinterpret_cast<const double2 *>(col[c] + row0));
+                    av[c][0] = v.x;
+                    av[c][1] = v.y;
+                } else {
+                    const float4 v = __ldcs(reinterpret_cast<const float4 *>(col[c] + row0));
+                    av[c][0] = v.x;
+                    av[c][1] = v.y;
+                    av[c][2] = v.z;
+                    av[c][3] = v.w;
                 }
-                any_active |= st.active[r];
+            } else {
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) av[c][q] = (row0 + q < n) ? col[c][row0 + q] : (TA)0;
             }
         }
-        if (tid == 0) {
-            *st.done = any_active ? 0 : 1;
-            st.counter[0] = 0;
+    };
+
+    load_chunk(0);
+    for (int64_t base = 0; base < n; base += KC) {
+        __syncthreads();                           // the previous chunk's readers are done
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+            const int e = q * THREADS + tid;
+            sh_s[e / NR][e % NR] = sv[q].x;
+            sl_s[e / NR][e % NR] = sv[q].y;
+        }
+        __syncthreads();
+        TA cur[2][RPL];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) cur[c][q] = av[c][q];
+        if (base + KC < n) load_chunk(base + KC);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int lr = lane * RPL + q;           // row within the chunk
+            float h[2], t[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if constexpr (SPLIT_A) {
+                    df_split_a((double)cur[c][q], ebias, h[c], t[c]);
+                } else {
+                    h[c] = (float)cur[c][q];
+                    t[c] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float shv = sh_s[lr][r], slv = sl_s[lr][r];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float p = h[c] * shv;
+                    float e = fmaf(h[c], shv, -p);
+                    e = fmaf(h[c], slv, e);
+                    if constexpr (SPLIT_A) e = fmaf(t[c], shv, e);
+                    df_add(ah[c][r], al[c][r], p, e);
+                }
+            }
         }
     }
+    // each (column, right-hand side) sum is spread over the warp's lanes
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float hh = ah[c][r], ll = al[c][r];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                df_add2(hh, ll, __shfl_xor_sync(0xffffffffu, hh, off), __shfl_xor_sync(0xffffffffu, ll, off));
+            if (lane == 0)
+                tcol[(c0 + c) * NR + r] = ((double)hh + (double)ll) * (r < nrhs ? df.scale[r] : 0.0);
+        }
+    mv_finish<TW, NR>(j0, wcols, nrhs, S, lds, T, ldt, st, mode, sr, tcol);
 }
 
 // SS[i * NR + r] = (head, tail) of inv[r] * V[i, r]: float(v) and
@@ -643,24 +788,27 @@ __global__ void __launch_bounds__(THREADS) absmax_cols_kernel(int64_t n, int nrh
 inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
 inline int mv_width(int nrhs, int prod)
 {
-    if (prod == PROD_DF) return nrhs <= 1 ? 8 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2;
+    if (prod == PROD_DF) return nrhs <= 2 ? 8 : TW;
     return nrhs <= 1 ? 4 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2;
 }
 
 template <typename TA, bool DF>
-void launch_mv_kernel(int64_t n, int nrhs, const TA *A, int64_t lda, const double *S, int64_t lds, double *T,
-                      int64_t ldt, const CGState &st, int mode, SRArgs sr, DFArgs df, int vec, cudaStream_t s)
+void launch_mv_kernel(int64_t n, int64_t ncols, int nrhs, const TA *A, int64_t lda, const double *S, int64_t lds,
+                      double *T, int64_t ldt, const CGState &st, int mode, SRArgs sr, DFArgs df, int vec,
+                      cudaStream_t s)
 {
-#define GPCH_MV(Wc, NRc)                                                                                     \
-    cg_matvec_kernel<TA, Wc, NRc, DF><<<(unsigned)((n + Wc - 1) / Wc), THREADS, 0, s>>>(n, nrhs, A, lda, S, lds, \
-                                                                                        T, ldt, st, mode, sr, \
-                                                                                        df, vec)
+#define GPCH_MV(Wc, NRc)                                                                                        \
+    cg_matvec_kernel<TA, Wc, NRc, DF><<<(unsigned)((ncols + Wc - 1) / Wc), THREADS, 0, s>>>(                  \
+        n, ncols, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec)
+#define GPCH_MVT(NRc)                                                                                           \
+    cg_matvec_df_tiled_kernel<TA, NRc><<<(unsigned)((ncols + TW - 1) / TW), THREADS, 0, s>>>(                 \
+        n, ncols, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec)
     if constexpr (DF) {
         if (nrhs <= 1) GPCH_MV(8, 1);
         else if (nrhs <= 2) GPCH_MV(8, 2);
-        else if (nrhs <= 4) GPCH_MV(4, 4);
-        else if (nrhs <= 8) GPCH_MV(2, 8);
-        else GPCH_MV(2, 16);
+        else if (nrhs <= 4) GPCH_MVT(4);
+        else if (nrhs <= 8) GPCH_MVT(8);
+        else GPCH_MVT(16);
     } else {
         if (nrhs <= 1) GPCH_MV(4, 1);
         else if (nrhs <= 2) GPCH_MV(8, 2);
@@ -669,6 +817,7 @@ void launch_mv_kernel(int64_t n, int nrhs, const TA *A, int64_t lda, const doubl
         else GPCH_MV(2, 16);
     }
 #undef GPCH_MV
+#undef GPCH_MVT
 }
 
 // One matvec T = A S (plus the mode's reductions).  With PROD_DF the vector
@@ -676,8 +825,10 @@ void launch_mv_kernel(int64_t n, int nrhs, const TA *A, int64_t lda, const doubl
 template <typename TA>
 gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64_t lda, const double *S,
                           int64_t lds, double *T, int64_t ldt, const CGState &st, int mode, cudaStream_t s,
-                          int prod = PROD_FP64, DFArgs df = DFArgs{}, SRArgs sr = SRArgs{0.0, 0, 0})
+                          int prod = PROD_FP64, DFArgs df = DFArgs{}, SRArgs sr = SRArgs{0.0, 0, 0},
+                          int64_t ncols = -1)
 {
+    if (ncols < 0) ncols = n;
     const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((lda * (int64_t)sizeof(TA)) & 15) == 0) ? 1 : 0;
     if (prod == PROD_DF) {
         const int nr = mv_nr(nrhs);
@@ -694,11 +845,11 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
         GPCH_LAUNCH_CHECK(ctx);
     }
     gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s,
-                        (double)n * n * sizeof(TA) + 2.0 * (double)n * nrhs * sizeof(double));
+                        (double)n * ncols * sizeof(TA) + (double)(n + ncols) * nrhs * sizeof(double));
     if (prod == PROD_DF)
-        launch_mv_kernel<TA, true>(n, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
+        launch_mv_kernel<TA, true>(n, ncols, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
     else
-        launch_mv_kernel<TA, false>(n, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
+        launch_mv_kernel<TA, false>(n, ncols, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -1381,6 +1532,246 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     if (!all_ok)
         return gpch::fail(ctx, GPCH_NOT_CONVERGED, "refinement missed the backward error %.1e within %d iterations",
                           bwd_tol, maxit);
+    return GPCH_OK;
+}
+
+// ---------------------------------------- row-split CG building blocks (f4)
+//
+// One rank of a CG solve whose rows are split over ranks (the paper's
+// horizontal split of Sec. 3.1, carried from CPU/GPU to GPU/GPU): a rank
+// owns rows r0 .. r0+m-1 of A, stored by symmetry as the n x m column block
+// A[:, r0 : r0+m], and the matching m rows of every vector.  The caller
+// moves data between ranks (an allgather of the vector fed to the product,
+// an allreduce of two sums per right-hand side); these calls do every
+// arithmetic step of the single-reduction iteration on the rank's rows.
+
+namespace {
+
+// per-CTA partial sums of r^T r and w^T r over the rank's rows; the last
+// CTA adds them in a fixed order into sums[0, nrhs) and sums[nrhs, 2 nrhs).
+__global__ void __launch_bounds__(THREADS) cgsr_partials_kernel(int64_t m, int nrhs, const double *R, int64_t ldr,
+                                                                const double *Wv, int64_t ldw, double *part,
+                                                                unsigned *counter, double *sums)
+{
+    __shared__ double red[THREADS / 32][2 * MAXRHS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * THREADS + tid;
+    for (int r = 0; r < nrhs; ++r) {
+        double g = 0.0, d = 0.0;
+        if (i < m) {
+            const double ri = R[i + r * ldr];
+            g = ri * ri;
+            d = Wv[i + r * ldw] * ri;
+        }
+        g = warp_sum(g);
+        d = warp_sum(d);
+        if (lane == 0) {
+            red[warp][r] = g;
+            red[warp][MAXRHS + r] = d;
+        }
+    }
+    __syncthreads();
+    if (tid < 2 * nrhs) {
+        const int q = tid < nrhs ? tid : MAXRHS + tid - nrhs;
+        double v = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) v += red[w][q];
+        part[(size_t)blockIdx.x * 2 * MAXRHS + q] = v;
+    }
+    if (last_cta(counter)) {
+        if (tid < 2 * nrhs) {
+            const int q = tid < nrhs ? tid : MAXRHS + tid - nrhs;
+            double v = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&part[(size_t)b * 2 * MAXRHS + q]);
+            sums[tid] = v;
+        }
+        if (tid == 0) *counter = 0;
+    }
+}
+
+// The scalar step of the single-reduction form from the ranks' reduced sums
+// (gamma' = sums[r], delta = sums[nrhs + r]); one thread per column.
+__global__ void cgsr_scalars_kernel(int nrhs, const double *sums, gpch_cgsr_state *st, int first, double rtol2,
+                                    int maxit)
+{
+    __shared__ int any_active;
+    const int r = threadIdx.x;
+    if (r == 0) any_active = 0;
+    __syncthreads();
+    if (r < nrhs) {
+        const double g = sums[r], d = sums[nrhs + r];
+        if (first) {
+            st->gamma0[r] = g;
+            st->gamma[r] = g;
+            st->iters[r] = 0;
+            st->beta[r] = 0.0;
+            st->alpha[r] = g > 0.0 ? g / d : 0.0;
+            st->active[r] = g > 0.0 ? 1 : 0;
+        } else if (st->active[r]) {
+            const int it = st->iters[r] + 1;
+            st->iters[r] = it;
+            const double b = g / st->gamma[r];
+            st->alpha[r] = g / (d - b * g / st->alpha[r]);
+            st->beta[r] = b;
+            st->gamma[r] = g;
+            if (g <= rtol2 * st->gamma0[r] || it >= maxit) st->active[r] = 0;
+        }
+        if (st->active[r]) atomicOr(&any_active, 1);
+    }
+    __syncthreads();
+    if (r == 0) st->done = any_active ? 0 : 1;
+}
+
+inline CGState state_view(gpch_cgsr_state *st)
+{
+    CGState v;
+    v.u = st->gamma;
+    v.u0 = st->gamma0;
+    v.alpha = st->alpha;
+    v.beta = st->beta;
+    v.active = st->active;
+    v.iters = st->iters;
+    v.done = &st->done;
+    v.counter = nullptr;
+    v.part = nullptr;
+    return v;
+}
+
+template <typename TA>
+gpch_status block_matvec(gpch_ctx *ctx, int64_t n, int64_t m, int64_t r0, const TA *A, int64_t lda, const double *V,
+                         int64_t ldv, double *T, int64_t ldt, int nrhs, int prod, cudaStream_t s)
+{
+    // scratch: a zero `done` word, and for double-float products the split
+    // vector and its scales
+    gpch::Carver dry(nullptr);
+    dry.take<int>(1);
+    if (prod == PROD_DF) {
+        dry.take<float2>((size_t)n * mv_nr(nrhs));
+        dry.take<double>(2 * MAXRHS);
+        dry.take<int>(1);
+        dry.take<double>(1 + MAXRHS);
+    }
+    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
+    gpch::Carver cv(ctx->ws);
+    CGState st{};
+    st.done = cv.take<int>(1);
+    GPCH_CUDA(ctx, cudaMemsetAsync(st.done, 0, sizeof(int), s));
+    DFArgs df{nullptr, nullptr, nullptr, nullptr};
+    if (prod == PROD_DF) {
+        df.SS = cv.take<float2>((size_t)n * mv_nr(nrhs));
+        double *d = cv.take<double>(2 * MAXRHS);
+        df.scale = d;
+        df.inv = d + MAXRHS;
+        df.ebias = cv.take<int>(1);
+        double *dmax = cv.take<double>(1 + MAXRHS);
+        GPCH_CUDA(ctx, cudaMemsetAsync(dmax, 0, (1 + MAXRHS) * sizeof(double), s));
+        const unsigned mc = (unsigned)((m + THREADS - 1) / THREADS), nc = (unsigned)((n + THREADS - 1) / THREADS);
+        if (sizeof(TA) == 8) {
+            // the block's diagonal entries A[r0 + j, j]
+            diag_max_kernel<TA><<<mc < 148 ? mc : 148, THREADS, 0, s>>>(m, A + r0, lda, dmax);
+            GPCH_LAUNCH_CHECK(ctx);
+        }
+        absmax_cols_kernel<<<nc, THREADS, 0, s>>>(n, nrhs, V, ldv, dmax + 1);
+        GPCH_LAUNCH_CHECK(ctx);
+        df_scales_kernel<<<1, 32, 0, s>>>(nrhs, dmax, sizeof(TA) == 8 ? 1 : 0, d, d + MAXRHS,
+                                          const_cast<int *>(df.ebias));
+        GPCH_LAUNCH_CHECK(ctx);
+    }
+    return launch_matvec<TA>(ctx, n, nrhs, A, lda, V, ldv, T, ldt, st, MV_PLAIN, s, prod, df, SRArgs{0.0, 0, 0}, m);
+}
+
+}  // namespace
+
+extern "C" gpch_status gpch_block_matvec(gpch_ctx *ctx, int64_t n, int64_t m, int64_t r0, const void *Ablk,
+                                         gpch_dtype dtype, int64_t lda, const double *V, int64_t ldv, double *T,
+                                         int64_t ldt, int nrhs, int32_t products, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, n >= 0 && m >= 0 && r0 >= 0 && r0 + m <= n, "need 0 <= r0 <= r0 + m <= n");
+    GPCH_ARG(ctx, nrhs >= 0 && nrhs <= MAXRHS, "need 0 <= nrhs <= 16");
+    GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldv >= (n > 0 ? n : 1) && ldt >= (m > 0 ? m : 1), "ld too small");
+    GPCH_ARG(ctx, dtype == GPCH_F64 || dtype == GPCH_F32, "bad dtype");
+    GPCH_ARG(ctx, products == GPCH_CG_PRODUCTS_FP64 || products == GPCH_CG_PRODUCTS_DOUBLE_FLOAT, "bad products");
+    if (n == 0 || m == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, Ablk && V && T, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int prod = products == GPCH_CG_PRODUCTS_DOUBLE_FLOAT ? PROD_DF : PROD_FP64;
+    if (dtype == GPCH_F64)
+        return block_matvec<double>(ctx, n, m, r0, static_cast<const double *>(Ablk), lda, V, ldv, T, ldt, nrhs, prod,
+                                    (cudaStream_t)stream);
+    return block_matvec<float>(ctx, n, m, r0, static_cast<const float *>(Ablk), lda, V, ldv, T, ldt, nrhs, prod,
+                               (cudaStream_t)stream);
+}
+
+extern "C" gpch_status gpch_cgsr_partials(gpch_ctx *ctx, int64_t m, int nrhs, const double *R, int64_t ldr,
+                                          const double *W, int64_t ldw, double *sums, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, m >= 0 && nrhs >= 0 && nrhs <= MAXRHS, "need m >= 0 and 0 <= nrhs <= 16");
+    GPCH_ARG(ctx, ldr >= (m > 0 ? m : 1) && ldw >= (m > 0 ? m : 1), "ld < m");
+    if (nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, sums != nullptr && (m == 0 || (R && W)), "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m == 0) {
+        GPCH_CUDA(ctx, cudaMemsetAsync(sums, 0, 2 * nrhs * sizeof(double), s));
+        return GPCH_OK;
+    }
+    const unsigned ctas = (unsigned)((m + THREADS - 1) / THREADS);
+    gpch::Carver dry(nullptr);
+    dry.take<unsigned>(1);
+    dry.take<double>((size_t)ctas * 2 * MAXRHS);
+    GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
+    gpch::Carver cv(ctx->ws);
+    unsigned *counter = cv.take<unsigned>(1);
+    double *part = cv.take<double>((size_t)ctas * 2 * MAXRHS);
+    GPCH_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    cgsr_partials_kernel<<<ctas, THREADS, 0, s>>>(m, nrhs, R, ldr, W, ldw, part, counter, sums);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_cgsr_scalars(gpch_ctx *ctx, int nrhs, const double *sums, gpch_cgsr_state *state,
+                                         int first, double rtol, int maxit, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, nrhs >= 0 && nrhs <= MAXRHS, "need 0 <= nrhs <= 16");
+    GPCH_ARG(ctx, rtol >= 0.0 && maxit > 0, "bad rtol / maxit");
+    GPCH_ARG(ctx, sums && state, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cgsr_scalars_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(nrhs, sums, state, first, rtol * rtol, maxit);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_cgsr_vectors(gpch_ctx *ctx, int64_t m, int nrhs, gpch_cgsr_state *state, double *X,
+                                         int64_t ldx, double *R, const double *W, double *P, double *S, int64_t ld,
+                                         int replace, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, m >= 0 && nrhs >= 0 && nrhs <= MAXRHS, "need m >= 0 and 0 <= nrhs <= 16");
+    GPCH_ARG(ctx, ldx >= (m > 0 ? m : 1) && ld >= (m > 0 ? m : 1), "ld < m");
+    if (m == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, state && X && R && W && P && S, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cgsr_vec_kernel<<<(unsigned)((m + THREADS - 1) / THREADS), THREADS, 0, (cudaStream_t)stream>>>(
+        m, nrhs, X, ldx, R, W, P, S, ld, state_view(state), replace ? 1 : 0);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_cgsr_residual(gpch_ctx *ctx, int64_t m, int nrhs, gpch_cgsr_state *state,
+                                          const double *B, int64_t ldb, const double *T, double *R, int64_t ld,
+                                          int all, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, m >= 0 && nrhs >= 0 && nrhs <= MAXRHS, "need m >= 0 and 0 <= nrhs <= 16");
+    GPCH_ARG(ctx, ldb >= (m > 0 ? m : 1) && ld >= (m > 0 ? m : 1), "ld < m");
+    if (m == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, state && B && T && R, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cg_resid_kernel<<<(unsigned)((m + THREADS - 1) / THREADS), THREADS, 0, (cudaStream_t)stream>>>(
+        m, nrhs, R, T, B, ldb, ld, state_view(state), all ? 1 : 0);
+    GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
 

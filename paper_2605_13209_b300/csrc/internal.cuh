@@ -75,8 +75,10 @@ cudaEvent_t take_event(gpch_ctx *ctx);
 // critical chain at the highest) and their ordering events (once).
 gpch_status aux_stream(gpch_ctx *ctx);
 
-// Free the batched solver's cached plans of a context (batched.cu).
+// Free the batched solvers' cached plans of a context (batched.cu,
+// batched_mixed.cu).
 void batched_release(gpch_ctx *ctx);
+void batched_mixed_release(gpch_ctx *ctx);
 
 // Batched FP64 solve launched directly, tables in the context workspace.
 gpch_status batched_solve_direct(gpch_ctx *ctx, int count, const gpch_system *systems, cudaStream_t st,

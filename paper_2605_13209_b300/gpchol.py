@@ -52,6 +52,15 @@ class System(ctypes.Structure):
                 ("ldb", ctypes.c_int64), ("nrhs", ctypes.c_int32)]
 
 
+class MSystem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64), ("nrhs", ctypes.c_int32)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("steps", ctypes.c_int32), ("backward_error_max", ctypes.c_double)]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("lanes", ctypes.c_int32), ("batch_max_count", ctypes.c_int32),
                 ("batch_max_n", ctypes.c_int64), ("solo_prec", ctypes.c_int), ("bwd_tol", ctypes.c_double)]
@@ -126,7 +135,16 @@ def lib() -> ctypes.CDLL:
                                          _vp, ctypes.POINTER(RefineStats)]
         L.gpch_logdet.argtypes = [_vp, _i64, _vp, _i64, ctypes.POINTER(_dbl), _vp]
         L.gpch_predict_mean.argtypes = [_vp, _i64, _i64, _int, _vp, _vp, _dbl, _dbl, _vp, _i64, _int, _vp, _i64, _vp]
-        for name in ("gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
+        L.gpch_batched_solve_mixed.argtypes = [_vp, _int, ctypes.POINTER(MSystem), _dbl, _int, _vp,
+                                                ctypes.POINTER(_i64), ctypes.POINTER(BatchStats)]
+        L.gpch_block_matvec.argtypes = [_vp, _i64, _i64, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int,
+                                         ctypes.c_int32, _vp]
+        L.gpch_cgsr_partials.argtypes = [_vp, _i64, _int, _vp, _i64, _vp, _i64, _vp, _vp]
+        L.gpch_cgsr_scalars.argtypes = [_vp, _int, _vp, _vp, _int, _dbl, _int, _vp]
+        L.gpch_cgsr_vectors.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _int, _vp]
+        L.gpch_cgsr_residual.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _i64, _int, _vp]
+        for name in ("gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
+                     "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
                      "gpch_batched_solve", "gpch_server_create", "gpch_server_submit", "gpch_server_wait",
@@ -338,6 +356,54 @@ def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e
     return CGResult(stats.iterations, stats.converged, stats.relres_max, st)
 
 
+def block_matvec(Ablk: torch.Tensor, r0: int, V: torch.Tensor, T: torch.Tensor, products: str = "fp64",
+                 ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """f4 local product: T = Ablk^T V, rows r0 .. r0+m-1 of A V for the
+    symmetric A whose columns r0 .. r0+m-1 are the n x m block Ablk."""
+    ctx = ctx or default_context()
+    if Ablk.dtype not in (torch.float64, torch.float32):
+        raise ValueError("Ablk must be float64 or float32")
+    _check_cuda(V, torch.float64)
+    _check_cuda(T, torch.float64)
+    n, m = Ablk.shape
+    dt = GPCH_F64 if Ablk.dtype == torch.float64 else GPCH_F32
+    ctx.check(lib().gpch_block_matvec(ctx.handle, n, m, int(r0), Ablk.data_ptr(), dt, _ld(Ablk), V.data_ptr(), _ld(V),
+                                      T.data_ptr(), _ld(T), V.shape[1], _CG_PRODUCTS[products], _stream(stream)))
+    return T
+
+
+def cgsr_partials(R: torch.Tensor, W: torch.Tensor, sums: torch.Tensor, ctx: Context | None = None, stream=None):
+    ctx = ctx or default_context()
+    ctx.check(lib().gpch_cgsr_partials(ctx.handle, R.shape[0], R.shape[1], R.data_ptr(), _ld(R), W.data_ptr(), _ld(W),
+                                       sums.data_ptr(), _stream(stream)))
+
+
+def cgsr_scalars(sums: torch.Tensor, state: torch.Tensor, nrhs: int, first: bool, rtol: float, maxit: int,
+                 ctx: Context | None = None, stream=None):
+    ctx = ctx or default_context()
+    ctx.check(lib().gpch_cgsr_scalars(ctx.handle, int(nrhs), sums.data_ptr(), state.data_ptr(), int(bool(first)),
+                                      float(rtol), int(maxit), _stream(stream)))
+
+
+def cgsr_vectors(state: torch.Tensor, X: torch.Tensor, R: torch.Tensor, W: torch.Tensor, P: torch.Tensor,
+                 S: torch.Tensor, replace: bool, ctx: Context | None = None, stream=None):
+    ctx = ctx or default_context()
+    ctx.check(lib().gpch_cgsr_vectors(ctx.handle, R.shape[0], R.shape[1], state.data_ptr(), X.data_ptr(), _ld(X),
+                                      R.data_ptr(), W.data_ptr(), P.data_ptr(), S.data_ptr(), _ld(R),
+                                      int(bool(replace)), _stream(stream)))
+
+
+def cgsr_residual(state: torch.Tensor, B: torch.Tensor, T: torch.Tensor, R: torch.Tensor, all_columns: bool,
+                  ctx: Context | None = None, stream=None):
+    ctx = ctx or default_context()
+    ctx.check(lib().gpch_cgsr_residual(ctx.handle, R.shape[0], R.shape[1], state.data_ptr(), B.data_ptr(), _ld(B),
+                                       T.data_ptr(), R.data_ptr(), _ld(R), int(bool(all_columns)), _stream(stream)))
+
+
+# layout of gpch_cgsr_state: four double[16] arrays, two int32[16] arrays, done, pad
+CGSR_STATE_BYTES = 4 * 16 * 8 + 2 * 16 * 4 + 8
+
+
 def cg_solve_noalloc(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e-10, maxit: int = 10000,
                      replace_every: int = 50, stream=None) -> CGResult:
     """gpch_cg_solve_noalloc: the CG solve without any device allocation
@@ -436,6 +502,39 @@ def batched_solve(As, Bs, ctx: Context | None = None, stream=None, raise_on_not_
     if not (st == GPCH_NOT_SPD and not raise_on_not_spd):
         ctx.check(st)
     return [int(info[i]) for i in range(len(As))]
+
+
+@dataclass
+class BatchResult:
+    info: list
+    iterations: int
+    steps: int
+    backward_error_max: float
+    status: int
+
+
+def batched_solve_mixed(As, Bs, Xs, bwd_tol: float = 1e-12, maxit: int = 30, ctx: Context | None = None,
+                        stream=None, raise_on_error: bool = True) -> BatchResult:
+    """A10 (mixed): FP32 factors with FP64 diagonal leaves and FP64
+    iterative refinement for a batch of systems.  As: n x n float64
+    (read only), Bs: n x nrhs float64 (read only), Xs: n x nrhs float64
+    (solutions), all column-major CUDA tensors."""
+    ctx = ctx or default_context()
+    if not (len(As) == len(Bs) == len(Xs)):
+        raise ValueError("As, Bs and Xs differ in length")
+    arr = (MSystem * max(len(As), 1))()
+    for i, (A, B, X) in enumerate(zip(As, Bs, Xs)):
+        for t in (A, B, X):
+            _check_cuda(t, torch.float64)
+        arr[i] = MSystem(A.shape[0], A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), B.shape[1])
+    info = (_i64 * max(len(As), 1))()
+    stats = BatchStats()
+    st = lib().gpch_batched_solve_mixed(ctx.handle, len(As), arr, float(bwd_tol), int(maxit), _stream(stream), info,
+                                        ctypes.byref(stats))
+    if raise_on_error:
+        ctx.check(st)
+    return BatchResult([int(info[i]) for i in range(len(As))], stats.iterations, stats.steps,
+                       stats.backward_error_max, st)
 
 
 class Server:

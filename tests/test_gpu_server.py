@@ -62,6 +62,41 @@ def test_server_alone_vs_mix():
     srv.close()
 
 
+def test_server_batches_queued_small_requests():
+    """Continuous batching: three large requests occupy the three lanes,
+    twelve small ones arrive meanwhile and queue; the first lane to free
+    takes up to batch_max_count of them in one batched launch, so at least
+    one batch holds several requests.  Each result still matches the
+    oracle, and every small result is bit-identical to the same request
+    solved alone."""
+    srv = gpchol.Server(0, hbm_budget=16 << 30, lanes=3, batch_max_count=8, batch_max_n=512,
+                        solo_prec="split_f16")
+    smalls = [req(int(n), 1 + i % 3, 600 + i) for i, n in enumerate(np.linspace(100, 512, 12).astype(int))]
+    alone = []
+    for s in smalls:
+        x, r = srv.wait(srv.submit(s.X, s.B, s.sf2, s.ell, s.sn2))
+        assert r["status"] == 0 and r["path"] == 1
+        alone.append(x)
+    before = srv.stats()
+    larges = [req(4096, 1, 700 + i, sn2=1e-3) for i in range(3)]
+    tl = [srv.submit(s.X, s.B, s.sf2, s.ell, s.sn2) for s in larges]
+    ts = [srv.submit(s.X, s.B, s.sf2, s.ell, s.sn2) for s in smalls]
+    for s, t, xa in zip(smalls, ts, alone):
+        x, r = srv.wait(t)
+        assert r["status"] == 0 and r["path"] == 1
+        assert np.array_equal(x, xa)
+    for s, t in zip(larges, tl):
+        x, r = srv.wait(t)
+        assert r["status"] == 0 and r["path"] == 2
+        assert r["backward_error"] <= 1e-12
+    after = srv.stats()
+    batches = after["batches"] - before["batches"]
+    grouped = after["batched_requests"] - before["batched_requests"]
+    assert grouped == 12
+    assert batches < grouped          # some batch held two or more requests
+    srv.close()
+
+
 def test_server_budget_and_fp64_path():
     budget = 64 << 20
     srv = gpchol.Server(0, hbm_budget=budget, lanes=2, batch_max_count=4, batch_max_n=300, solo_prec="fp64")
