@@ -577,6 +577,14 @@ def main():
     if args.cg_iters > 0:
         cg = cg_legs(args, ctx, A0, bd, n, world, pk, max_over_ranks, rank)
 
+    # ---------------------------------------------------------- autotuner
+    # tile choices of this GPU for the batched legs, the serving lanes and
+    # the refined solve's tile 0 (the headline above names its tile)
+    import tempfile
+    t0 = time.perf_counter()
+    tune = gpchol.autotune(os.path.join(tempfile.gettempdir(), "gpchol_tune.json"), nmax=32768, ctx=ctx)
+    tune["seconds"] = round(time.perf_counter() - t0, 2)
+
     # ---------------------------------------------------------- batched leg
     batched = None
     xs_batched = xs_mixed = None
@@ -710,6 +718,7 @@ def main():
                    "backward_error_lib": res.backward_error_max},
         "fp64": fp64,
         "cg": cg,
+        "autotune": tune,
         "batched": batched,
         "serving": serving,
         "phases": phases,

@@ -565,6 +565,9 @@ typedef struct gpch_refine_stats {
  * (ldb).  X: device n x nrhs (ldx), overwritten.  Workspace (context
  * arena): about 8 n^2 bytes, the FP32 factor and the 16-bit copies of its
  * panels.
+ * tile: the factor's block size, a multiple of 64 in [64, 1024], or 0 for
+ * the autotuned tile of n's size bucket (gpch_autotune; defaults 256 for
+ * n <= 4096, else 512, until the device is tuned).
  * stats (host, may be NULL).  Synchronizes `stream`.  Returns GPCH_NOT_SPD
  * if every shifted factorization broke down, GPCH_NOT_CONVERGED if some
  * column missed bwd_tol within maxit iterations. */
@@ -605,6 +608,45 @@ gpch_status gpch_logdet(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, 
 gpch_status gpch_predict_mean(gpch_ctx *ctx, int64_t m, int64_t n, int d, const double *Xs, const double *X,
                               double sf2, double ell, const double *alpha, int64_t lda, int nrhs,
                               double *mean, int64_t ldm, void *stream);
+
+/* ------------------------------------------------------- autotuner */
+
+/* Tile choices per problem-size bucket: bucket b holds n <= 512 * 2^b
+ * (b = 0..7), bucket 8 larger n. */
+#define GPCH_TUNE_BUCKETS 9
+
+typedef struct gpch_tune_info {
+    int32_t source;                              /* 0 defaults, 1 measured, 2 loaded */
+    int32_t refined_tile[GPCH_TUNE_BUCKETS];     /* gpch_solve_refined with tile = 0 */
+    int32_t batch_tile_fp64[GPCH_TUNE_BUCKETS];  /* trailing-update tile, FP64 batch  */
+    int32_t batch_tile_mixed[GPCH_TUNE_BUCKETS]; /* trailing-update tile, mixed batch */
+    char gpu[96];                                /* device name the table belongs to */
+} gpch_tune_info;
+
+/* Tile choices for the context's device (the block size is a paper
+ * parameter: Sec. 4 studies it per system size; no autotuner is in the
+ * paper).  Unless `force` is set, the table is loaded from cache_path
+ * (JSON, keyed by the GPU's name) when the file holds an entry for this
+ * device; otherwise every candidate is timed with CUDA events on synthetic
+ * squared-exponential systems generated on the device and the fastest
+ * kept:
+ *   - refined solve (split-f16): tiles 256, 384, 512 at n = 1024 ... nmax
+ *     (powers of two; nmax <= 65536, default 32768 when 0);
+ *   - batched FP64 and mixed solves: trailing-update tile 32 or 64, batches
+ *     of one size at n = 256 ... 4096 (the batched result does not depend
+ *     on it).
+ * Buckets not measured take the nearest measured one.  The table then
+ * applies to every context on this device in this process and, when
+ * cache_path is not NULL, is written there (other GPUs' entries kept).
+ * Measurement allocates its own device memory (about 17 n^2 bytes at the
+ * largest n) and takes a few seconds.  out (host, may be NULL) receives the
+ * table.  Synchronizes the device.  Errors: INVALID_ARG (nmax), CUDA_ERROR,
+ * OOM_BUDGET (allocation failed). */
+gpch_status gpch_autotune(gpch_ctx *ctx, const char *cache_path, int force, int64_t nmax, gpch_tune_info *out);
+
+/* The table in effect for the context's device (defaults, measured or
+ * loaded). */
+gpch_status gpch_tune_get(gpch_ctx *ctx, gpch_tune_info *out);
 
 #ifdef __cplusplus
 }

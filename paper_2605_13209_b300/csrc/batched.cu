@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(256) btrsm_kernel(const BSys *sys, StepTable t
                               local * 64, btsmem);
 }
 
+// Step 3: one BT x BT lower tile of the trailing matrix (BT = 32 or 64,
+// chosen per system size by the autotuner; every entry sums its products
+// in the same order for either tile, so the result does not depend on it).
+template <int BT>
 __global__ void __launch_bounds__(256, 3) bgemm_kernel(const BSys *sys, StepTable t, int k)
 {
     int64_t local;
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(256, 3) bgemm_kernel(const BSys *sys, StepTabl
     int64_t ti, tj;
     tri_index(local, ti, tj);
     const double *P = S.A + (o + LEAF) + o * S.lda;
-    gemm_nt_minus_body<double, true, 64>(m, m, LEAF, P, S.lda, P, S.lda, S.A + (o + LEAF) * (1 + S.lda), S.lda,
+    gemm_nt_minus_body<double, true, BT>(m, m, LEAF, P, S.lda, P, S.lda, S.A + (o + LEAF) * (1 + S.lda), S.lda,
                                          ti, tj);
 }
 
@@ -203,7 +207,7 @@ struct HostTables {
         int cnt;
         int64_t tasks;
     };
-    std::vector<Step> potrf, trsm, gemm, fwd, bwd;
+    std::vector<Step> potrf, trsm, gemm64, gemm32, fwd, bwd;
 };
 
 template <typename F>
@@ -227,13 +231,17 @@ struct Layout {
     HostTables h;
     std::vector<int64_t> ns;
     int64_t kmax = 0;
+    gpch::TuneTable tune{};
+    // trailing-update tile of a system of size n (autotuned, else 64)
+    int bt_of(int64_t n) const { return tune.batch_bt[0][gpch::tune_bucket(n)] == 32 ? 32 : 64; }
     size_t o_sys = 0, o_info = 0, o_tsys = 0, o_pref = 0, bytes = 0;
     std::vector<size_t> o_linv, o_y;
 };
 
-Layout make_layout(int count, const gpch_system *systems)
+Layout make_layout(int count, const gpch_system *systems, const gpch::TuneTable &tune)
 {
     Layout L;
+    L.tune = tune;
     L.ns.resize(count);
     for (int s = 0; s < count; ++s) {
         L.ns[s] = systems[s].n;
@@ -248,11 +256,15 @@ Layout make_layout(int count, const gpch_system *systems)
             const int64_t m = n - (k + 1) * LEAF;
             return m > 0 ? (m + 63) / 64 : 0;
         }));
-        h.gemm.push_back(add_step(h, count, ns, [&](int64_t n) {
-            const int64_t m = n - (k + 1) * LEAF;
-            const int64_t T = m > 0 ? (m + 63) / 64 : 0;
-            return T * (T + 1) / 2;
-        }));
+        for (int bt : {64, 32}) {
+            auto &dst = bt == 64 ? h.gemm64 : h.gemm32;
+            dst.push_back(add_step(h, count, ns, [&](int64_t n) {
+                if (L.bt_of(n) != bt) return (int64_t)0;
+                const int64_t m = n - (k + 1) * LEAF;
+                const int64_t T = m > 0 ? (m + bt - 1) / bt : 0;
+                return T * (T + 1) / 2;
+            }));
+        }
         h.fwd.push_back(add_step(h, count, ns, [&](int64_t n) {
             if (n <= k * LEAF) return (int64_t)0;
             const int64_t below = n - (k + 1) * LEAF;
@@ -338,8 +350,12 @@ int64_t enqueue_batch(const Layout &L, const DevTables &d, int count, cudaStream
             btrsm_kernel<<<(unsigned)h.trsm[k].tasks, 256, BTRSM_SMEM, st>>>(d.sys, table(h.trsm[k]), (int)k);
             ++launches;
         }
-        if (h.gemm[k].tasks) {
-            bgemm_kernel<<<(unsigned)h.gemm[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm[k]), (int)k);
+        if (h.gemm64[k].tasks) {
+            bgemm_kernel<64><<<(unsigned)h.gemm64[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm64[k]), (int)k);
+            ++launches;
+        }
+        if (h.gemm32[k].tasks) {
+            bgemm_kernel<32><<<(unsigned)h.gemm32[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm32[k]), (int)k);
             ++launches;
         }
     }
@@ -358,7 +374,7 @@ int64_t enqueue_batch(const Layout &L, const DevTables &d, int count, cudaStream
 
 gpch_status build_plan(gpch_ctx *ctx, int count, const gpch_system *systems, BatchPlan &plan, cudaStream_t st)
 {
-    Layout L = make_layout(count, systems);
+    Layout L = make_layout(count, systems, gpch::tune_table(ctx->device));
     if (ctx->budget && ctx->ws_bytes + L.bytes > ctx->budget)
         return gpch::fail(ctx, GPCH_OOM_BUDGET, "batch plan of %zu bytes exceeds the HBM budget", L.bytes);
     GPCH_CUDA(ctx, cudaMalloc(&plan.dev, L.bytes));
@@ -406,7 +422,7 @@ namespace gpch {
 gpch_status batched_solve_direct(gpch_ctx *ctx, int count, const gpch_system *systems, cudaStream_t st,
                                  int64_t *info)
 {
-    Layout L = make_layout(count, systems);
+    Layout L = make_layout(count, systems, gpch::tune_table(ctx->device));
     GPCH_CHECK(ws_reserve(ctx, L.bytes));
     DevTables d;
     GPCH_CHECK(upload(ctx, L, count, systems, static_cast<char *>(ctx->ws), d, st));
@@ -453,7 +469,11 @@ extern "C" gpch_status gpch_batched_solve(gpch_ctx *ctx, int count, const gpch_s
     GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     PlanKey key;
-    key.v.reserve(count * 6);
+    key.v.reserve(count * 6 + gpch::TUNE_BUCKETS);
+    {
+        const gpch::TuneTable tt = gpch::tune_table(ctx->device);   // plans differ by their update tiles
+        for (int b = 0; b < gpch::TUNE_BUCKETS; ++b) key.v.push_back(tt.batch_bt[0][b]);
+    }
     for (int s = 0; s < count; ++s) {
         const gpch_system &y = systems[s];
         key.v.insert(key.v.end(), {y.n, (int64_t)(uintptr_t)y.A, y.lda, (int64_t)(uintptr_t)y.B, y.ldb, y.nrhs});

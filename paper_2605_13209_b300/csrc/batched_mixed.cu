@@ -172,7 +172,10 @@ __global__ void __launch_bounds__(256) bm_trsm_kernel(const MSys *sys, StepTable
                              local * 64, bm_tsmem);
 }
 
-// Step 3: one 64 x 64 lower tile of the trailing matrix, FP32.
+// Step 3: one BT x BT lower tile of the trailing matrix, FP32 (BT = 32 or
+// 64, chosen per system size by the autotuner; the result does not depend
+// on it).
+template <int BT>
 __global__ void __launch_bounds__(256, 3) bm_gemm_kernel(const MSys *sys, StepTable t, int k)
 {
     int64_t local;
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(256, 3) bm_gemm_kernel(const MSys *sys, StepTa
     int64_t ti, tj;
     tri_index(local, ti, tj);
     const float *P = S.L + (o + LEAF) + o * S.n;
-    gemm_nt_minus_body<float, true, 64>(m, m, LEAF, P, S.n, P, S.n, S.L + (o + LEAF) * (1 + S.n), S.n, ti, tj);
+    gemm_nt_minus_body<float, true, BT>(m, m, LEAF, P, S.n, P, S.n, S.L + (o + LEAF) * (1 + S.n), S.n, ti, tj);
 }
 
 // Forward step k on W (in place): y_k = inv(L_kk) w_k (every CTA of the
@@ -359,7 +362,7 @@ struct HostTables {
         int cnt;
         int64_t tasks;
     };
-    std::vector<Step> potrf, trsm, gemm, fwd, bwd;
+    std::vector<Step> potrf, trsm, gemm64, gemm32, fwd, bwd;
     Step setup{}, rows{}, cols{};
 };
 
@@ -383,13 +386,17 @@ struct Layout {
     HostTables h;
     std::vector<int64_t> ns;
     int64_t kmax = 0;
+    gpch::TuneTable tune{};
+    // trailing-update tile of a system of size n (autotuned, else 64)
+    int bt_of(int64_t n) const { return tune.batch_bt[1][gpch::tune_bucket(n)] == 32 ? 32 : 64; }
     size_t o_sys = 0, o_info = 0, o_state = 0, o_tsys = 0, o_pref = 0, bytes = 0;
     std::vector<size_t> o_L, o_linv, o_stage, o_w, o_y;
 };
 
-Layout make_layout(int count, const gpch_msystem *systems)
+Layout make_layout(int count, const gpch_msystem *systems, const gpch::TuneTable &tune)
 {
     Layout L;
+    L.tune = tune;
     L.ns.resize(count);
     for (int s = 0; s < count; ++s) {
         L.ns[s] = systems[s].n;
@@ -407,11 +414,15 @@ Layout make_layout(int count, const gpch_msystem *systems)
             const int64_t m = n - (k + 1) * LEAF;
             return m > 0 ? (m + 63) / 64 : 0;
         }));
-        h.gemm.push_back(add_step(h, count, ns, [&](int64_t n) {
-            const int64_t m = n - (k + 1) * LEAF;
-            const int64_t T = m > 0 ? (m + 63) / 64 : 0;
-            return T * (T + 1) / 2;
-        }));
+        for (int bt : {64, 32}) {
+            auto &dst = bt == 64 ? h.gemm64 : h.gemm32;
+            dst.push_back(add_step(h, count, ns, [&](int64_t n) {
+                if (L.bt_of(n) != bt) return (int64_t)0;
+                const int64_t m = n - (k + 1) * LEAF;
+                const int64_t T = m > 0 ? (m + bt - 1) / bt : 0;
+                return T * (T + 1) / 2;
+            }));
+        }
         h.fwd.push_back(add_step(h, count, ns, [&](int64_t n) {
             if (n <= k * LEAF) return (int64_t)0;
             const int64_t below = n - (k + 1) * LEAF;
@@ -532,8 +543,12 @@ int64_t enqueue_batch(const Layout &L, const DevTables &d, int count, double tol
             bm_trsm_kernel<<<(unsigned)h.trsm[k].tasks, 256, BM_TRSM_SMEM, st>>>(d.sys, table(h.trsm[k]), (int)k);
             ++launches;
         }
-        if (h.gemm[k].tasks) {
-            bm_gemm_kernel<<<(unsigned)h.gemm[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm[k]), (int)k);
+        if (h.gemm64[k].tasks) {
+            bm_gemm_kernel<64><<<(unsigned)h.gemm64[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm64[k]), (int)k);
+            ++launches;
+        }
+        if (h.gemm32[k].tasks) {
+            bm_gemm_kernel<32><<<(unsigned)h.gemm32[k].tasks, 256, 0, st>>>(d.sys, table(h.gemm32[k]), (int)k);
             ++launches;
         }
     }
@@ -601,7 +616,7 @@ cudaError_t capture(cudaGraphExec_t *exec, F &&enqueue)
 gpch_status build_mplan(gpch_ctx *ctx, int count, const gpch_msystem *systems, double tol, int maxit, MPlan &plan,
                         cudaStream_t st)
 {
-    Layout L = make_layout(count, systems);
+    Layout L = make_layout(count, systems, gpch::tune_table(ctx->device));
     if (ctx->budget && ctx->ws_bytes + L.bytes > ctx->budget)
         return gpch::fail(ctx, GPCH_OOM_BUDGET, "batch plan of %zu bytes exceeds the HBM budget", L.bytes);
     GPCH_CUDA(ctx, cudaMalloc(&plan.dev, L.bytes));
@@ -667,7 +682,11 @@ extern "C" gpch_status gpch_batched_solve_mixed(gpch_ctx *ctx, int count, const 
     GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     MKey key;
-    key.v.reserve(count * 8 + 2);
+    key.v.reserve(count * 8 + 2 + gpch::TUNE_BUCKETS);
+    {
+        const gpch::TuneTable tt = gpch::tune_table(ctx->device);   // plans differ by their update tiles
+        for (int b = 0; b < gpch::TUNE_BUCKETS; ++b) key.v.push_back(tt.batch_bt[1][b]);
+    }
     key.v.push_back((int64_t)maxit);
     int64_t tbits;
     std::memcpy(&tbits, &bwd_tol, sizeof(tbits));

@@ -1456,8 +1456,10 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
     GPCH_ARG(ctx, prec == GPCH_PREC_BF16 || prec == GPCH_PREC_SPLIT_BF16 || prec == GPCH_PREC_SPLIT_F16,
              "prec must be BF16, SPLIT_BF16 or SPLIT_F16");
-    GPCH_ARG(ctx, tile >= 64 && tile <= 1024 && tile % 64 == 0, "tile must be a multiple of 64 in [64, 1024]");
+    GPCH_ARG(ctx, tile == 0 || (tile >= 64 && tile <= 1024 && tile % 64 == 0),
+             "tile must be 0 (tuned) or a multiple of 64 in [64, 1024]");
     GPCH_ARG(ctx, bwd_tol > 0.0 && maxit > 0, "bad bwd_tol / maxit");
+    if (tile == 0) tile = gpch::tune_table(ctx->device).refined_tile[gpch::tune_bucket(n)];
     GPCH_ARG(ctx, n < (int64_t)1 << 31, "n too large");
     if (n == 0 || nrhs == 0) return GPCH_OK;
     GPCH_ARG(ctx, A && B && X, "null pointer");

@@ -75,6 +75,20 @@ cudaEvent_t take_event(gpch_ctx *ctx);
 // critical chain at the highest) and their ordering events (once).
 gpch_status aux_stream(gpch_ctx *ctx);
 
+// Tile choices, by problem size: the refined solve's tile and the batched
+// factors' trailing-update tile (32 or 64 rows and columns per CTA; the
+// result does not depend on it, only the speed).  Defaults until the
+// autotuner (autotune.cu) has measured this device or loaded its cache.
+constexpr int TUNE_BUCKETS = 9;   // n <= 512, 1024, ..., 65536, larger
+struct TuneTable {
+    int refined_tile[TUNE_BUCKETS];
+    int batch_bt[2][TUNE_BUCKETS];   // [0] FP64 batch, [1] mixed batch
+    int tuned;                       // 0 defaults, 1 measured, 2 loaded
+};
+int tune_bucket(int64_t n);
+TuneTable tune_table(int device);
+void tune_set(int device, const TuneTable &t);
+
 // Free the batched solvers' cached plans of a context (batched.cu,
 // batched_mixed.cu).
 void batched_release(gpch_ctx *ctx);

@@ -119,7 +119,9 @@ gpch_status ensure(Lane *L, size_t bytes)
     return GPCH_OK;
 }
 
-int pick_tile(int64_t n) { return n >= 8192 ? 512 : 256; }
+// The tile of a solo request: the autotuned refined-solve tile of its size
+// bucket (the defaults until the device is tuned).
+int pick_tile_dev(int device, int64_t n) { return gpch::tune_table(device).refined_tile[gpch::tune_bucket(n)]; }
 
 // Solve one request alone on the lane.
 void run_solo(Lane *L, Req *q)
@@ -145,14 +147,14 @@ void run_solo(Lane *L, Req *q)
         if (mixed) {
             q->path = 2;
             gpch_refine_stats rs;
-            st = gpch_solve_refined(L->ctx, r.n, dA, r.n, dB, r.n, dO, r.n, r.nrhs, S->o.solo_prec, pick_tile(r.n),
+            st = gpch_solve_refined(L->ctx, r.n, dA, r.n, dB, r.n, dO, r.n, r.nrhs, S->o.solo_prec, pick_tile_dev(S->device, r.n),
                                     S->o.bwd_tol, 500, L->stream, &rs);
             q->iterations = rs.iterations;
             q->backward_error = rs.backward_error_max;
         } else {
             q->path = 3;
             int64_t info = 0;
-            st = gpch_chol_factor(L->ctx, r.n, pick_tile(r.n), dA, r.n, L->stream, &info);
+            st = gpch_chol_factor(L->ctx, r.n, pick_tile_dev(S->device, r.n), dA, r.n, L->stream, &info);
             if (st == GPCH_OK) {
                 cudaMemcpyAsync(dO, dB, n * r.nrhs * 8, cudaMemcpyDeviceToDevice, L->stream);
                 st = gpch_chol_solve(L->ctx, r.n, dA, r.n, dO, r.n, r.nrhs, L->stream);
@@ -265,7 +267,7 @@ void admit(gpch_server *S)
                 ++it;
                 continue;
             }
-            const size_t need = request_bytes(q->r, !small && S->o.solo_prec != GPCH_PREC_FP64, pick_tile(q->r.n));
+            const size_t need = request_bytes(q->r, !small && S->o.solo_prec != GPCH_PREC_FP64, pick_tile_dev(S->device, q->r.n));
             if (S->o.hbm_budget && S->mem_reserved + mem + need > S->o.hbm_budget) {
                 ++it;
                 continue;
@@ -344,7 +346,7 @@ gpch_status gpch_server_submit(gpch_server *S, const gpch_request *r, uint64_t *
     if (r->n < 1 || r->d < 1 || r->d > 64 || r->nrhs < 1 || r->ell <= 0.0 || !r->X || !r->B || !r->Xout)
         return GPCH_INVALID_ARG;
     const bool small = r->n <= S->o.batch_max_n;
-    const size_t need = request_bytes(*r, !small && S->o.solo_prec != GPCH_PREC_FP64, pick_tile(r->n));
+    const size_t need = request_bytes(*r, !small && S->o.solo_prec != GPCH_PREC_FP64, pick_tile_dev(S->device, r->n));
     if (S->o.hbm_budget && need > S->o.hbm_budget) return GPCH_OOM_BUDGET;
     Req *q = new Req();
     q->r = *r;

@@ -61,6 +61,12 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("steps", ctypes.c_int32), ("backward_error_max", ctypes.c_double)]
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("source", ctypes.c_int32), ("refined_tile", ctypes.c_int32 * 9),
+                ("batch_tile_fp64", ctypes.c_int32 * 9), ("batch_tile_mixed", ctypes.c_int32 * 9),
+                ("gpu", ctypes.c_char * 96)]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("lanes", ctypes.c_int32), ("batch_max_count", ctypes.c_int32),
                 ("batch_max_n", ctypes.c_int64), ("solo_prec", ctypes.c_int), ("bwd_tol", ctypes.c_double)]
@@ -135,6 +141,8 @@ def lib() -> ctypes.CDLL:
                                          _vp, ctypes.POINTER(RefineStats)]
         L.gpch_logdet.argtypes = [_vp, _i64, _vp, _i64, ctypes.POINTER(_dbl), _vp]
         L.gpch_predict_mean.argtypes = [_vp, _i64, _i64, _int, _vp, _vp, _dbl, _dbl, _vp, _i64, _int, _vp, _i64, _vp]
+        L.gpch_autotune.argtypes = [_vp, ctypes.c_char_p, _int, _i64, ctypes.POINTER(TuneInfo)]
+        L.gpch_tune_get.argtypes = [_vp, ctypes.POINTER(TuneInfo)]
         L.gpch_batched_solve_mixed.argtypes = [_vp, _int, ctypes.POINTER(MSystem), _dbl, _int, _vp,
                                                 ctypes.POINTER(_i64), ctypes.POINTER(BatchStats)]
         L.gpch_block_matvec.argtypes = [_vp, _i64, _i64, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int,
@@ -143,7 +151,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_cgsr_scalars.argtypes = [_vp, _int, _vp, _vp, _int, _dbl, _int, _vp]
         L.gpch_cgsr_vectors.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _int, _vp]
         L.gpch_cgsr_residual.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _i64, _int, _vp]
-        for name in ("gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
+        for name in ("gpch_autotune", "gpch_tune_get", "gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
                      "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
@@ -502,6 +510,32 @@ def batched_solve(As, Bs, ctx: Context | None = None, stream=None, raise_on_not_
     if not (st == GPCH_NOT_SPD and not raise_on_not_spd):
         ctx.check(st)
     return [int(info[i]) for i in range(len(As))]
+
+
+TUNE_SOURCES = {0: "defaults", 1: "measured", 2: "loaded"}
+
+
+def _tune_dict(t: TuneInfo) -> dict:
+    return {"source": TUNE_SOURCES.get(t.source, str(t.source)), "gpu": t.gpu.decode(),
+            "refined_tile": list(t.refined_tile), "batch_tile_fp64": list(t.batch_tile_fp64),
+            "batch_tile_mixed": list(t.batch_tile_mixed)}
+
+
+def autotune(cache_path: str | None = None, force: bool = False, nmax: int = 0, ctx: Context | None = None) -> dict:
+    """gpch_autotune: measure (or load from cache_path) the tile choices of
+    this device.  Bucket b of each list covers n <= 512 * 2^b."""
+    ctx = ctx or default_context()
+    t = TuneInfo()
+    ctx.check(lib().gpch_autotune(ctx.handle, cache_path.encode() if cache_path else None, int(bool(force)),
+                                  int(nmax), ctypes.byref(t)))
+    return _tune_dict(t)
+
+
+def tune_get(ctx: Context | None = None) -> dict:
+    ctx = ctx or default_context()
+    t = TuneInfo()
+    ctx.check(lib().gpch_tune_get(ctx.handle, ctypes.byref(t)))
+    return _tune_dict(t)
 
 
 @dataclass
