@@ -555,7 +555,9 @@ typedef struct gpch_refine_stats {
  * each breakdown, u = 2^-8, 2^-16, 2^-22 for BF16, SPLIT_BF16, SPLIT_F16; at
  * most 9 attempts), then preconditioned CG with M = Lt Lt^T in FP64 (A, x,
  * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
- * from x_0 = 0, replacing the recurrence residual by b - A x every 50
+ * from x_0 = 0 (the iteration's products A s formed as double-float
+ * products, as gpch_cg_solve_ex's GPCH_CG_PRODUCTS_DOUBLE_FLOAT; every true
+ * residual b - A x in FP64), replacing the recurrence residual by b - A x every 50
  * iterations and whenever an estimate of the backward error from the
  * recurrence residual (its ||r||_inf in place of the true residual's,
  * scaled by the truth-to-estimate ratio seen at the previous check)

@@ -1072,7 +1072,10 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
 //
 // Refined solve: preconditioned CG with M = Lt Lt^T, Lt the low-precision
 // factor (FP32 storage), applied by the forward/back substitution of
-// solve.cu.  A, x, r, dot products and recurrences stay in FP64.  The host
+// solve.cu.  A, x, r, dot products and recurrences stay in FP64; the
+// iteration's product t = A s takes double-float products (relative error
+// below about 2^-45 per product) and the true residuals b - A x FP64
+// products, so the backward error the stop rule measures is FP64's.  The host
 // reads a few scalars per iteration (an iteration already costs two
 // substitution sweeps), decides when to replace the recurrence residual by
 // the true one, and stops each column when its true backward error
@@ -1258,7 +1261,17 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     st.iters = ic + MAXRHS;
     st.done = ic + 2 * MAXRHS;
     st.counter = cv.take<unsigned>(2);
-    st.part = cv.take<double>(part_doubles(n, nrhs));
+    st.part = cv.take<double>(part_doubles(n, nrhs, PROD_DF));
+    // double-float products for t = A s (the true residuals stay FP64)
+    CGBufs dfb{};
+    dfb.df.SS = cv.take<float2>((size_t)n * mv_nr(nrhs));
+    {
+        double *d = cv.take<double>(2 * MAXRHS);
+        dfb.df.scale = d;
+        dfb.df.inv = d + MAXRHS;
+        dfb.df.ebias = cv.take<int>(1);
+        dfb.dmax = cv.take<double>(1 + MAXRHS);
+    }
     // ex: rr[16] xinf[16] rinf[16] binf[16] bb[16] norms[2] dots[16]
     double *ex = cv.take<double>(6 * MAXRHS + 2);
     double *d_rr = ex, *d_xinf = ex + MAXRHS, *d_rinf = ex + 2 * MAXRHS, *d_binf = ex + 3 * MAXRHS;
@@ -1282,6 +1295,7 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     GPCH_CUDA(ctx, cudaMemcpyAsync(d_norms, anorm_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
     absmax_cols_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, B, ldb, d_binf);
     GPCH_LAUNCH_CHECK(ctx);
+    GPCH_CHECK(df_prepare<double>(ctx, n, nrhs, A, lda, B, ldb, dfb, s));
     pcg_dot_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, Rv, ldv, Rv, ldv, st, d_bb, 0);
     GPCH_LAUNCH_CHECK(ctx);
     GPCH_CHECK(gpch::solve_prepare_f32(ctx, n, L, ldl, sw, s));
@@ -1312,7 +1326,7 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     double est_at_check[MAXRHS] = {0};
     int it = 0;
     while (nactive > 0 && it < maxit) {
-        GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, 0, s));
+        GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, MV_ALPHA, s, PROD_DF, dfb.df));
         pcg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, ldv, st, d_rr, d_xinf, d_rinf);
         GPCH_LAUNCH_CHECK(ctx);
         ++it;
@@ -1368,7 +1382,11 @@ size_t pcg_ws_bytes(int64_t n, int nrhs)
     dry.take<double>(4 * MAXRHS);
     dry.take<int>(2 * MAXRHS + 1);
     dry.take<unsigned>(2);
-    dry.take<double>(part_doubles(n, nrhs));
+    dry.take<double>(part_doubles(n, nrhs, PROD_DF));
+    dry.take<float2>((size_t)n * mv_nr(nrhs));
+    dry.take<double>(2 * MAXRHS);
+    dry.take<int>(1);
+    dry.take<double>(1 + MAXRHS);
     dry.take<double>(6 * MAXRHS + 2);
     return dry.off;
 }
