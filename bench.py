@@ -215,7 +215,7 @@ def run_reference(args):
 CHECK_BLOCK_N = 4096
 
 
-def oracle_check(sysm, x_mixed, x_fp64, L_block):
+def oracle_check(sysm, x_mixed, x_fp64, L_block, x_emu=None, L_block_emu=None):
     """Errors of the benchmark's solutions, from the oracle on the host:
     the system matrix rebuilt by the oracle from the same points, the
     backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) with
@@ -231,10 +231,14 @@ def oracle_check(sysm, x_mixed, x_fp64, L_block):
     if x_fp64 is not None:
         out["backward_error_fp64"] = oracle.backward_error(A, x_fp64, b)
         out["forward_error_mixed_vs_fp64"] = oracle.forward_error(x_mixed, x_fp64)
+    if x_emu is not None:
+        out["backward_error_fp64_emulated_update"] = oracle.backward_error(A, x_emu, b)
     if L_block is not None:
         nb = L_block.shape[0]
         Lref, info = oracle.cholesky(A[:nb, :nb])
         out["fp64_factor_error_leading_block"] = oracle.factor_error(L_block, Lref)
+        if L_block_emu is not None:
+            out["fp64_emulated_factor_error_leading_block"] = oracle.factor_error(L_block_emu, Lref)
         out["factor_block_n"] = nb
     return out
 
@@ -547,7 +551,7 @@ def main():
 
     # ---------------------------------------------------------- FP64 leg
     fp64 = None
-    x_fp64 = L_block = None
+    x_fp64 = L_block = x_emu = L_block_emu = None
     if not args.no_fp64:
         Aw = gpchol.colmajor(n, n)
         small = min(n, 2048)
@@ -570,6 +574,27 @@ def main():
         fp64 = {"ms_per_solve": round(fms, 2), "gflops": round(world * flops / (fms / 1e3) / 1e9, 2),
                 "speedup_mixed_vs_fp64": round(fms / ms, 2), "steps": 1,
                 "what": f"FP64 blocked Cholesky (tile {tile}) + forward/back substitution"}
+        # the same with step 3 on the FP64-accurate tensor-core product
+        Aw.copy_(A0)
+        torch.cuda.synchronize()
+        ctx.timing_enable(True)
+        f0.record()
+        gpchol.chol_factor(Aw, tile=tile, ctx=ctx, update="fp64_emulated")
+        Xe = bd.clone()
+        gpchol.chol_solve(Aw, Xe, ctx=ctx)
+        f1.record()
+        torch.cuda.synchronize()
+        tr = ctx.timing_read(gpchol.PHASE_TRAILING)
+        ctx.timing_enable(False)
+        ems = max_over_ranks(f0.elapsed_time(f1))
+        x_emu = Xe[:, 0].cpu().numpy().copy()
+        L_block_emu = np.tril(Aw[:nb, :nb].cpu().numpy())
+        fp64["emulated_update"] = {
+            "ms_per_solve": round(ems, 2), "gflops": round(world * flops / (ems / 1e3) / 1e9, 2),
+            "speedup_vs_fp64": round(fms / ems, 2),
+            "update_ms": round(tr[0], 2), "update_tflops_fp64_equiv": round(tr[2] / (tr[0] / 1e3) / 1e12, 2),
+            "what": "the same factor + solve with step 3 as FP64-accurate products on the bf16 tensor cores "
+                    "(8 base-128 digits per entry, 36 digit pairs, exact class sums)"}
         del Aw
 
     # ---------------------------------------------------------- CG legs
@@ -687,7 +712,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    check = oracle_check(sysm, x_mixed, x_fp64, L_block) if not args.no_check else None
+    check = oracle_check(sysm, x_mixed, x_fp64, L_block, x_emu, L_block_emu) if not args.no_check else None
     if batched is not None and xs_batched is not None and not args.no_check:
         batched["fp64"]["backward_error_max"] = batched_check(args.batch_count, xs_batched)
         batched["mixed"]["backward_error_max"] = batched_check(args.batch_count, xs_mixed)

@@ -161,6 +161,24 @@ gpch_status gpch_chol_solve(gpch_ctx *ctx, int64_t n, const double *L,
                             int64_t ldl, double *B, int64_t ldb, int nrhs,
                             void *stream);
 
+/* Arithmetic of step 3 in gpch_chol_factor_ex. */
+typedef enum gpch_update {
+    GPCH_UPDATE_FP64 = 0,           /* FP64 FMAs (gpch_chol_factor)              */
+    GPCH_UPDATE_FP64_EMULATED = 1   /* FP64-accurate products on the tensor cores
+                                       (gpch_gemm_fp64_emulated)                  */
+} gpch_update;
+
+/* gpch_chol_factor with a choice of step-3 arithmetic: GPCH_UPDATE_FP64 is
+ * gpch_chol_factor itself; GPCH_UPDATE_FP64_EMULATED computes every
+ * trailing update A_ik -= A_ij A_kj^T of Algorithm 1 (right) with the
+ * tensor-core product of gpch_gemm_fp64_emulated (per entry and block
+ * column an error below about tile 2^-48 times the product of the two
+ * rows' largest panel entries, one FP64 rounding), steps 1 and 2 in FP64 as
+ * before.  Extra workspace: 8 n * 1024 bytes.  Returns GPCH_TIMEOUT if a
+ * bounded tensor-core wait gave up; otherwise as gpch_chol_factor. */
+gpch_status gpch_chol_factor_ex(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, int32_t update,
+                                void *stream, int64_t *info);
+
 /* --------------------------------------------------- A6-A7: CG solve */
 
 typedef struct gpch_cg_stats {
@@ -610,6 +628,34 @@ gpch_status gpch_logdet(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, 
 gpch_status gpch_predict_mean(gpch_ctx *ctx, int64_t m, int64_t n, int d, const double *Xs, const double *X,
                               double sf2, double ell, const double *alpha, int64_t lda, int nrhs,
                               double *mean, int64_t ldm, void *stream);
+
+/* ------------------------- FP64-accurate products on tensor cores (f1) */
+
+/* C -= A B^T for FP64 A (m x k, lda >= m), B (n x k, ldb >= n) and C
+ * (m x n, ldc >= m), column-major, computed on the bf16 tensor cores by an
+ * error-free splitting in the manner of the Ozaki scheme (the paper names
+ * faster mixed/emulated arithmetic as future work, Sec. 5; the operation is
+ * Algorithm 1 step 3 at any size):
+ *   - each row of A (and of B) is scaled by a power of two from its
+ *     largest |entry| and rounded to a 54-bit integer, written as 8
+ *     balanced base-128 digits, each exact in bf16;
+ *   - the 36 digit pairs of weight 128^-(p+q), p + q <= 7, are multiplied
+ *     on the tensor cores; pairs of equal weight share one FP32 accumulator,
+ *     whose sums stay exact (integers below 2^24) over K passes of at most
+ *     512 columns;
+ *   - the 8 weighted sums are combined exactly and rounded once per pass
+ *     into C in FP64.
+ * Per entry and pass the error is below about k 2^-48 2^(e_i + f_j), with
+ * 2^e_i and 2^f_j the row scales (|A_ic| < 2^e_i): the size of FP64 GEMM's
+ * worst-case bound when a row's largest entries set its scale, though
+ * larger than FP64's for rows whose entries span many binades.
+ * lower != 0: C is square (m == n) and only its lower triangle (row >=
+ * column) is written.  A and B may be the same matrix (the SYRK case).
+ * Workspace (context arena): about 16 (m + n) * 512 bytes.
+ * Synchronizes `stream`; returns GPCH_TIMEOUT if a bounded pipeline wait
+ * gave up.  Errors: INVALID_ARG. */
+gpch_status gpch_gemm_fp64_emulated(gpch_ctx *ctx, int64_t m, int64_t n, int64_t k, const double *A, int64_t lda,
+                                    const double *B, int64_t ldb, double *C, int64_t ldc, int lower, void *stream);
 
 /* ------------------------------------------------------- autotuner */
 

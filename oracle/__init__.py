@@ -76,6 +76,7 @@ def lib():
         L.or_cg_single_reduction.argtypes = [_c_i64, _c_dp, _c_i64, _c_dp, _c_dp, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, _c_dp]
         L.or_cg_single_reduction.restype = ctypes.c_int
+        L.or_gemm_update.argtypes = [_c_i64, _c_i64, _c_i64, _c_dp, _c_i64, _c_dp, _c_i64, _c_dp, _c_i64, ctypes.c_int]
         L.or_logdet.argtypes = [_c_i64, _c_dp, _c_i64, _c_dp]
         L.or_logdet.restype = _c_i64
         L.or_predict_mean.argtypes = [_c_i64, _c_i64, ctypes.c_int, _c_dp, _c_dp, ctypes.c_double, ctypes.c_double,
@@ -198,6 +199,18 @@ def cg_single_reduction(A, b, eps: float, maxit: int, R: int = 50, x0=None):
     rr = ctypes.c_double(0.0)
     it = lib().or_cg_single_reduction(n, _p(A), max(n, 1), _p(b), _p(x), eps, maxit, R, ctypes.byref(rr))
     return x, int(it), float(rr.value)
+
+
+def gemm_update(C, A, B, lower: bool = False):
+    """C - A B^T with long-double sums, one rounding per entry (Algorithm 1
+    step 3 as a definition).  lower: only row >= column entries change."""
+    C = _fmat(C)
+    A = _fmat(A)
+    B = _fmat(B)
+    m, k = A.shape
+    n = B.shape[0]
+    lib().or_gemm_update(m, n, k, _p(A), max(m, 1), _p(B), max(n, 1), _p(C), max(m, 1), int(bool(lower)))
+    return C
 
 
 def logdet(A):

@@ -498,6 +498,24 @@ int or_cg_single_reduction(int64_t n, const double *A, int64_t lda, const double
     return it;
 }
 
+/* C -= A B^T (C: m x n, A: m x k, B: n x k, column-major), every entry's
+ * sum of products accumulated in long double and rounded once: the FP64
+ * trailing update of Algorithm 1 step 3 stated as a definition, with a
+ * rounding error (about k 2^-64 of sum |a b|) far below FP64's, so it can
+ * judge an FP64-accurate product.  lower != 0: only entries with row >=
+ * column (C square). */
+void or_gemm_update(int64_t m, int64_t n, int64_t k, const double *A, int64_t lda, const double *B,
+                    int64_t ldb, double *C, int64_t ldc, int lower)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) {
+            if (lower && i < j) continue;
+            long double s = 0.0L;
+            for (int64_t c = 0; c < k; ++c) s += (long double)A[IDX(i, c, lda)] * (long double)B[IDX(j, c, ldb)];
+            C[IDX(i, j, ldc)] = (double)((long double)C[IDX(i, j, ldc)] - s);
+        }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Error measures                                                             */
 /* ------------------------------------------------------------------------ */

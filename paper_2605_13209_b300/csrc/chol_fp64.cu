@@ -44,7 +44,7 @@ namespace gpch {
 // Linv: workspace of tile/64 * 64*64 doubles; info: device int64 (zeroed by
 // the caller).  Used by gpch_chol_factor and by the refined solve.
 gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *rinv,
-                              int64_t *info, cudaStream_t st, int64_t col_offset)
+                              int64_t *info, cudaStream_t st, int64_t col_offset, void *oz_ws, int **oz_err)
 {
     for (int64_t j0 = 0; j0 < n; j0 += tile) {
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
@@ -87,18 +87,23 @@ gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int
                                                    lda, Pan + (c0 + nc) * lda, lda, info, st));
             }
         }
-        // step 3: trailing lower triangle, K = tile
+        // step 3: trailing lower triangle, K = tile: FP64 FMAs, or with
+        // oz_ws the FP64-accurate tensor-core product (ozaki.cu)
         gpch::PhaseScope ph3(ctx, GPCH_PHASE_TRAILING, st, (double)nj * m * (m + 1));
-        GPCH_CHECK(launch_gemm<double>(ctx, true, m, m, (int)nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda), lda,
-                                       info, st));
+        if (oz_ws)
+            GPCH_CHECK(oz_gemm_enqueue(ctx, m, m, nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda), lda, true, oz_ws,
+                                       st, oz_err));
+        else
+            GPCH_CHECK(launch_gemm<double>(ctx, true, m, m, (int)nj, Pan, lda, Pan, lda, A + (j0 + nj) * (1 + lda),
+                                           lda, info, st));
     }
     return GPCH_OK;
 }
 
 }  // namespace gpch
 
-extern "C" gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda,
-                                        void *stream, int64_t *info)
+extern "C" gpch_status gpch_chol_factor_ex(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda,
+                                           int32_t update, void *stream, int64_t *info)
 {
     GPCH_ARG(ctx, ctx != nullptr, "null context");
     GPCH_ARG(ctx, info != nullptr, "info must not be NULL");
@@ -106,23 +111,37 @@ extern "C" gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, doub
     GPCH_ARG(ctx, n >= 0, "n < 0");
     GPCH_ARG(ctx, lda >= (n > 0 ? n : 1), "lda < n");
     GPCH_ARG(ctx, tile >= LEAF && tile <= 1024 && tile % LEAF == 0, "tile must be a multiple of 64 in [64, 1024]");
+    GPCH_ARG(ctx, update == GPCH_UPDATE_FP64 || update == GPCH_UPDATE_FP64_EMULATED, "bad update arithmetic");
     if (n == 0) return GPCH_OK;
     GPCH_ARG(ctx, A != nullptr, "null A");
     GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
+    const bool emu = update == GPCH_UPDATE_FP64_EMULATED;
     gpch::Carver dry(nullptr);
     dry.take<int64_t>(1);
     dry.take<double>((size_t)tile);
+    const size_t oz_off = dry.reserve(emu ? gpch::oz_ws_bytes(n, n, true) : 0);
     GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
     gpch::Carver cv(ctx->ws);
     int64_t *d_info = cv.take<int64_t>(1);
     double *rinv = cv.take<double>((size_t)tile);
+    void *oz_ws = emu ? static_cast<char *>(ctx->ws) + oz_off : nullptr;
+    int *oz_err = nullptr;
     GPCH_CUDA(ctx, cudaMemsetAsync(d_info, 0, sizeof(int64_t), st));
-    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, rinv, d_info, st, 0));
+    GPCH_CHECK(gpch::chol_fp64_enqueue(ctx, n, tile, A, lda, rinv, d_info, st, 0, oz_ws, &oz_err));
     int64_t *h = static_cast<int64_t *>(ctx->pinned);
     GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (oz_err) GPCH_CUDA(ctx, cudaMemcpyAsync(h + 1, oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GPCH_CUDA(ctx, cudaStreamSynchronize(st));
     *info = *h;
+    if (oz_err && *reinterpret_cast<int *>(h + 1) != 0)
+        return gpch::fail(ctx, GPCH_TIMEOUT, "tensor-core pipeline wait gave up");
     if (*info != 0) return gpch::fail(ctx, GPCH_NOT_SPD, "pivot %lld not positive", (long long)*info);
     return GPCH_OK;
+}
+
+extern "C" gpch_status gpch_chol_factor(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda,
+                                        void *stream, int64_t *info)
+{
+    return gpch_chol_factor_ex(ctx, n, tile, A, lda, GPCH_UPDATE_FP64, stream, info);
 }

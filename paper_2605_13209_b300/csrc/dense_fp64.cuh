@@ -846,9 +846,22 @@ namespace gpch {
 // Enqueue the FP64 blocked factorization (chol_fp64.cu).  rinv: workspace
 // of `tile` doubles that receives 1 / L_cc of the last diagonal tile
 // factored (a caller that factors one tile reads it afterwards).  A failed
-// pivot at local column c sets *info = col_offset + c + 1.
+// pivot at local column c sets *info = col_offset + c + 1.  With oz_ws
+// (oz_ws_bytes(n, n, true) bytes) step 3 takes the FP64-accurate
+// tensor-core product; *oz_err (nullptr on entry) then receives its status
+// word.
 gpch_status chol_fp64_enqueue(gpch_ctx *ctx, int64_t n, int tile, double *A, int64_t lda, double *rinv,
-                              int64_t *info, cudaStream_t st, int64_t col_offset);
+                              int64_t *info, cudaStream_t st, int64_t col_offset, void *oz_ws = nullptr,
+                              int **oz_err = nullptr);
+
+// FP64-accurate C -= A B^T on the tensor cores (ozaki.cu): workspace bytes,
+// and the enqueue.  *err_out receives the status word's address; it is
+// cleared on the stream when *err_out is nullptr on entry (a caller making
+// several calls keeps the first call's word, so no failure is lost).
+size_t oz_ws_bytes(int64_t m, int64_t n, bool same);
+gpch_status oz_gemm_enqueue(gpch_ctx *ctx, int64_t m, int64_t n, int64_t k, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, double *C, int64_t ldc, bool lower, void *ws,
+                            cudaStream_t st, int **err_out);
 
 // Forward/back substitution (solve.cu).  SolveWs is carved from
 // solve_ws_bytes(n, nrhs) bytes of workspace; solve_prepare inverts the

@@ -141,6 +141,8 @@ def lib() -> ctypes.CDLL:
                                          _vp, ctypes.POINTER(RefineStats)]
         L.gpch_logdet.argtypes = [_vp, _i64, _vp, _i64, ctypes.POINTER(_dbl), _vp]
         L.gpch_predict_mean.argtypes = [_vp, _i64, _i64, _int, _vp, _vp, _dbl, _dbl, _vp, _i64, _int, _vp, _i64, _vp]
+        L.gpch_chol_factor_ex.argtypes = [_vp, _i64, _int, _vp, _i64, ctypes.c_int32, _vp, ctypes.POINTER(_i64)]
+        L.gpch_gemm_fp64_emulated.argtypes = [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_autotune.argtypes = [_vp, ctypes.c_char_p, _int, _i64, ctypes.POINTER(TuneInfo)]
         L.gpch_tune_get.argtypes = [_vp, ctypes.POINTER(TuneInfo)]
         L.gpch_batched_solve_mixed.argtypes = [_vp, _int, ctypes.POINTER(MSystem), _dbl, _int, _vp,
@@ -151,7 +153,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_cgsr_scalars.argtypes = [_vp, _int, _vp, _vp, _int, _dbl, _int, _vp]
         L.gpch_cgsr_vectors.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _int, _vp]
         L.gpch_cgsr_residual.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _i64, _int, _vp]
-        for name in ("gpch_autotune", "gpch_tune_get", "gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
+        for name in ("gpch_chol_factor_ex", "gpch_gemm_fp64_emulated", "gpch_autotune", "gpch_tune_get", "gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
                      "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
@@ -270,14 +272,16 @@ def se_matrix(X: torch.Tensor, sf2: float, ell: float, sn2: float, A: torch.Tens
 
 
 def chol_factor(A: torch.Tensor, tile: int = 256, ctx: Context | None = None, stream=None,
-                raise_on_not_spd: bool = True) -> int:
+                raise_on_not_spd: bool = True, update: str = "fp64") -> int:
     """A2-A4: in-place FP64 blocked Cholesky of the column-major A (lower
-    triangle).  Returns info (0 on success)."""
+    triangle).  update: "fp64" (FP64 FMAs) or "fp64_emulated" (step 3 with
+    the FP64-accurate tensor-core product).  Returns info (0 on success)."""
     ctx = ctx or default_context()
     _check_cuda(A, torch.float64)
     info = _i64(0)
-    st = lib().gpch_chol_factor(ctx.handle, A.shape[0], int(tile), A.data_ptr(), _ld(A), _stream(stream),
-                                ctypes.byref(info))
+    upd = {"fp64": 0, "fp64_emulated": 1}[update]
+    st = lib().gpch_chol_factor_ex(ctx.handle, A.shape[0], int(tile), A.data_ptr(), _ld(A), upd, _stream(stream),
+                                   ctypes.byref(info))
     if st == GPCH_NOT_SPD and not raise_on_not_spd:
         return int(info.value)
     ctx.check(st)
@@ -510,6 +514,23 @@ def batched_solve(As, Bs, ctx: Context | None = None, stream=None, raise_on_not_
     if not (st == GPCH_NOT_SPD and not raise_on_not_spd):
         ctx.check(st)
     return [int(info[i]) for i in range(len(As))]
+
+
+def gemm_fp64_emulated(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, lower: bool = False,
+                       ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """f1: C -= A B^T with FP64-accurate products on the tensor cores (A: m x k,
+    B: n x k, C: m x n; column-major float64 CUDA tensors).  lower: only the
+    lower triangle of the square C."""
+    ctx = ctx or default_context()
+    for t in (A, B, C):
+        _check_cuda(t, torch.float64)
+    m, k = A.shape
+    n = B.shape[0]
+    if B.shape[1] != k or C.shape[0] != m or C.shape[1] != n:
+        raise ValueError("shape mismatch")
+    ctx.check(lib().gpch_gemm_fp64_emulated(ctx.handle, m, n, k, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B),
+                                            C.data_ptr(), _ld(C), int(bool(lower)), _stream(stream)))
+    return C
 
 
 TUNE_SOURCES = {0: "defaults", 1: "measured", 2: "loaded"}

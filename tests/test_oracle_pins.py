@@ -557,3 +557,30 @@ def test_predict_mean_far_point_and_columns():
     both = oracle.predict_mean(Xs, sysm.X, 1.0, 0.5, sysm.B)
     for r in range(3):
         np.testing.assert_array_equal(both[:, r], oracle.predict_mean(Xs, sysm.X, 1.0, 0.5, sysm.B[:, r]))
+
+
+# --------------------------------------------- long-double GEMM update (f1)
+def test_gemm_update_exact_rationals():
+    """Against exact rational arithmetic: C - A B^T entry by entry, rounded
+    once to FP64 (long double sums of 12 products carry no error here)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(61)
+    A = rng.standard_normal((5, 12)) * np.exp(rng.uniform(-20, 5, (5, 12)))
+    B = rng.standard_normal((4, 12))
+    C = rng.standard_normal((5, 4))
+    got = oracle.gemm_update(C, A, B)
+    for i in range(5):
+        for j in range(4):
+            ex = Fraction(C[i, j]) - sum(Fraction(A[i, c]) * Fraction(B[j, c]) for c in range(12))
+            assert abs(Fraction(got[i, j]) - ex) <= abs(ex) * Fraction(2) ** -52 + Fraction(2) ** -1070
+
+
+def test_gemm_update_lower_and_library():
+    rng = np.random.default_rng(62)
+    P = rng.standard_normal((30, 17))
+    C = rng.standard_normal((30, 30))
+    got = oracle.gemm_update(C, P, P, lower=True)
+    ref = C - P @ P.T
+    low = np.tril(np.ones((30, 30), dtype=bool))
+    np.testing.assert_allclose(got[low], ref[low], rtol=1e-13, atol=1e-13)
+    np.testing.assert_array_equal(got[~low], C[~low])      # upper entries untouched
