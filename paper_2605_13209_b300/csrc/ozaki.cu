@@ -21,8 +21,10 @@
 //
 // Combination.  T = sum_D S_D 2^(7(7-D)) is formed exactly as
 // H 2^28 + L with H = sum_{D<4} S_D 2^(7(3-D)) and L = sum_{D>=4} S_D
-// 2^(7(7-D)) (each below 2^47, exact in int64 and in FP64), then rounded
-// once: result = 2^(e_r + f_j - 59) (H 2^28 + L), subtracted from C in FP64.
+// 2^(7(7-D)) (each below 2^47) in 128-bit integer arithmetic, rounded once
+// to the FP64 value of 2^(e_r + f_j - 59) T with integer operations, and
+// subtracted from C in FP64 (one FP64 operation per entry: this part's FP64
+// pipe is slow).
 // Longer k is done in passes of at most 512 columns, each rounded once.
 //
 // Accuracy.  Per entry the error is at most about
@@ -129,6 +131,42 @@ namespace {
 // its lane 0 issues the MMAs, warps 2-5 combine the class sums (warp w:
 // tile rows 32 (w % 4) .. +31, its TMEM lanes).  err: device status word,
 // nonzero if a bounded wait gave up.
+// The FP64 value nearest to T 2^s for a signed integer T = H 2^28 + L
+// (|H|, |L| < 2^48), rounded to nearest even, from integer operations only
+// (this part runs FP64 conversions on its slow FP64 pipe).  Results outside
+// FP64's normal range take the FP64 route (never for a product of two
+// normal operands' digits; kept for completeness).
+__device__ __forceinline__ double oz_round_scaled(long long H, long long L, int s)
+{
+    const __int128 T = (__int128)H * ((__int128)1 << 28) + (__int128)L;
+    if (T == 0) return 0.0;
+    const bool neg = T < 0;
+    const unsigned __int128 U = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+    const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+    const int msb = 127 - lz;                       // U in [2^msb, 2^(msb+1))
+    const int ex = msb + s;                         // unbiased exponent of the result
+    if (ex < -1022 || ex > 1023)
+        return neg ? -ldexp((double)U, s) : ldexp((double)U, s);
+    // top 53 bits of U, then round to nearest even on the rest
+    unsigned long long mant;
+    bool round_up = false;
+    if (msb <= 52) {
+        mant = lo << (52 - msb);
+    } else {
+        const int sh = msb - 52;                    // bits below the 53
+        const unsigned __int128 q = U >> sh;
+        mant = (unsigned long long)q;
+        const unsigned __int128 rem = U - (q << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        round_up = rem > half || (rem == half && (mant & 1ull));
+    }
+    unsigned long long bits = ((unsigned long long)(ex + 1023) << 52) + (mant & 0xfffffffffffffull);
+    bits += round_up ? 1ull : 0ull;                 // a carry into the exponent is the right rounding
+    if (neg) bits |= 0x8000000000000000ull;
+    return __longlong_as_double((long long)bits);
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, int64_t m,
                    int64_t n, int kp, const int *__restrict__ ea, const int *__restrict__ eb, double *C, int64_t ldc,
@@ -247,6 +285,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int qw = warp & 3;
         const int64_t row = i0 + qw * 32 + lane;
         const bool row_ok = row < m;
+        // while the MMAs run: the tile's column exponents into shared
+        // memory, and its C lines (a warp's 32 rows of a column are one
+        // 256-byte piece) into L2
+        __shared__ int s_eb[OZ_BN];
+        if (warp == 2)
+            for (int j = lane; j < OZ_BN; j += 32) s_eb[j] = (j0 + j < n) ? eb[j0 + j] : 0;
+        if (row_ok)
+            for (int j = 0; j < OZ_BN; ++j)
+                if (j0 + j < n && !(lower && j0 + j > row))
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(C + row + (j0 + j) * ldc));
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
         bool ok = gpch::tc::mbar_wait(tfull, 0, 4 * OZ_SPIN);
         ok = __all_sync(0xffffffffu, ok);
         gpch::tc::tc_fence_after();
@@ -257,9 +306,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t tl = tmem + ((uint32_t)(qw * 32) << 16);
 #pragma unroll 1
             for (int cc = 0; cc < OZ_BN / 16; ++cc) {
-                float v[OZ_CLASSES][16];
+                uint32_t vr[OZ_CLASSES][16];
 #pragma unroll
-                for (int D = 0; D < OZ_CLASSES; ++D) gpch::tc::tmem_ld16(tl + D * OZ_BN + cc * 16, v[D]);
+                for (int D = 0; D < OZ_CLASSES; ++D) gpch::tc::tmem_ld16_nowait(tl + D * OZ_BN + cc * 16, vr[D]);
+                gpch::tc::tmem_ld_wait();
+                // the chunk's C entries, all loads in flight together
+                double cval[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t col = j0 + cc * 16 + j;
+                    const bool want = row_ok && col < n && !(lower && col > row);
+                    cval[j] = want ? C[row + col * ldc] : 0.0;
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int64_t col = j0 + cc * 16 + j;
@@ -267,13 +325,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     // exact class sums (integers of magnitude <= 2^24)
                     long long H = 0, L = 0;
 #pragma unroll
-                    for (int D = 0; D < 4; ++D) H = H * 128 + (long long)__float2ll_rn(v[D][j]);
+                    for (int D = 0; D < 4; ++D) H = H * 128 + __float2int_rn(__uint_as_float(vr[D][j]));
 #pragma unroll
-                    for (int D = 4; D < 8; ++D) L = L * 128 + (long long)__float2ll_rn(v[D][j]);
-                    const double tv = fma((double)H, 268435456.0, (double)L);   // H 2^28 + L, one rounding
-                    const double scale = ldexp(1.0, er + eb[col] - 59);
-                    double *cp = C + row + col * ldc;
-                    *cp = fma(-tv, scale, *cp);
+                    for (int D = 4; D < 8; ++D) L = L * 128 + __float2int_rn(__uint_as_float(vr[D][j]));
+                    // one rounding of the product, then C's
+                    C[row + col * ldc] = cval[j] - oz_round_scaled(H, L, er + s_eb[cc * 16 + j] - 59);
                 }
             }
         }
