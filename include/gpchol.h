@@ -161,6 +161,22 @@ gpch_status gpch_chol_solve(gpch_ctx *ctx, int64_t n, const double *L,
                             int64_t ldl, double *B, int64_t ldb, int nrhs,
                             void *stream);
 
+/* The same solve with an FP32 factor, e.g. the low-precision factor of
+ * gpch_chol_factor_mixed (the preconditioner application of the refined
+ * solve, z = (L L^T)^-1 r): block products in FP32, partial sums and the
+ * right-hand sides FP64.  With one or two right-hand sides, a 16-byte
+ * aligned L and ldl a multiple of 4, each sweep walks 128-row blocks and
+ * keeps one 128 x 128 product per block on its serial chain (coupling
+ * blocks inv(L_II) L_{I,I-1} and L_{I+1,I} inv(L_II), formed once per
+ * call); otherwise 64-row blocks.  L: device, lower triangle (the strict
+ * upper triangle is not read), ldl >= n.  B: device FP64, n x nrhs,
+ * ldb >= n, overwritten with X.  Synchronizes the stream.  Extra
+ * workspace: about 24 n * 128 + 16 n * 64 bytes.  Errors: INVALID_ARG,
+ * TIMEOUT (a bounded wait of a sweep gave up). */
+gpch_status gpch_chol_solve_f32(gpch_ctx *ctx, int64_t n, const float *L,
+                                int64_t ldl, double *B, int64_t ldb,
+                                int nrhs, void *stream);
+
 /* Arithmetic of step 3 in gpch_chol_factor_ex. */
 typedef enum gpch_update {
     GPCH_UPDATE_FP64 = 0,           /* FP64 FMAs (gpch_chol_factor)              */

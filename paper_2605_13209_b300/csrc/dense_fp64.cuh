@@ -874,6 +874,7 @@ struct SolveWs {
     unsigned long long *tagw;       // tagged (value, tag) words, FP32 sweeps
     size_t tagw_words;
     float *Linv128;                 // 128 x 128 diagonal-block inverses, FP32 factor
+    float *F128, *G128;             // forward and back coupling blocks of the 128-row FP32 sweeps
     int *err;
     unsigned epoch;
 };

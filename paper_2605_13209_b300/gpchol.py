@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_se_matrix.argtypes = [_vp, _i64, _int, _vp, _dbl, _dbl, _dbl, _vp, _i64, _vp]
         L.gpch_chol_factor.argtypes = [_vp, _i64, _int, _vp, _i64, _vp, ctypes.POINTER(_i64)]
         L.gpch_chol_solve.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
+        L.gpch_chol_solve_f32.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_cg_solve.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int, _vp,
                                     ctypes.POINTER(CGStats)]
         L.gpch_cg_solve_ex.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int,
@@ -154,7 +155,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_cgsr_vectors.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _int, _vp]
         L.gpch_cgsr_residual.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _i64, _int, _vp]
         for name in ("gpch_chol_factor_ex", "gpch_gemm_fp64_emulated", "gpch_autotune", "gpch_tune_get", "gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
-                     "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve",
+                     "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve", "gpch_chol_solve_f32",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
                      "gpch_batched_solve", "gpch_server_create", "gpch_server_submit", "gpch_server_wait",
@@ -295,6 +296,17 @@ def chol_solve(L: torch.Tensor, B: torch.Tensor, ctx: Context | None = None, str
     _check_cuda(B, torch.float64)
     ctx.check(lib().gpch_chol_solve(ctx.handle, L.shape[0], L.data_ptr(), _ld(L), B.data_ptr(), _ld(B), B.shape[1],
                                     _stream(stream)))
+    return B
+
+
+def chol_solve_f32(L: torch.Tensor, B: torch.Tensor, ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """A5 with an FP32 factor (e.g. from chol_factor_mixed): solve L L^T X = B
+    in place on the column-major FP64 B (n x nrhs).  Synchronizes the stream."""
+    ctx = ctx or default_context()
+    _check_cuda(L, torch.float32)
+    _check_cuda(B, torch.float64)
+    ctx.check(lib().gpch_chol_solve_f32(ctx.handle, L.shape[0], L.data_ptr(), _ld(L), B.data_ptr(), _ld(B),
+                                        B.shape[1], _stream(stream)))
     return B
 
 
