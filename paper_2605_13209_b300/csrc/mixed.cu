@@ -1,9 +1,8 @@
 // mixed.cu -- A8: the low-precision factor used as the preconditioner of the
 // refined solve.  Algorithm 1 (right) runs on an FP32 copy of the lower
 // triangle of A (+ shift * I):
-//   step 1  the diagonal tile is widened to FP64 and factored by the FP64
-//           nest (potrf leaf / unit-lower substitution / SYRK), then stored
-//           back in FP32;
+//   step 1  the diagonal tile is factored in FP32 as a nest of 32-wide
+//           steps (one-warp leaf / row-parallel substitution / SYRK);
 //   step 2  SPLIT_F16: the panel is the tensor-core product A_ij L_jj^-T,
 //           with L_jj^-1 from an FP32 forward substitution; the bf16 modes
 //           solve it in FP32, 64 columns at a time, against FP32 inverses
@@ -906,17 +905,91 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
     }
 }
 
-// Copy the nb x nb lower block between FP32 W and FP64 D (ld ldd).
+// Step 1 in FP32: the diagonal tile as a nest of 32-wide steps (leaf ->
+// substitution below it -> SYRK inside the tile), the same launch structure
+// as the FP64 nest with FP32 arithmetic, each kernel launched as a
+// programmatic dependent of the one before.
+//
+// Leaf: one warp factors the nb x nb block (nb <= 32) at A, lane i holding
+// row i; each pivot column is broadcast through shared memory.  A pivot
+// that is not positive sets *info = col0 + (its column) + 1 and leaves the
+// block as it is.
+__global__ void __launch_bounds__(32) leaf32_kernel(float *A, int64_t lda, int nb, int64_t col0, int64_t *info)
+{
+    gpch::pdl_wait();
+    gpch::pdl_trigger();
+    __shared__ float col[32];
+    if (*info != 0) return;   // the same value in every lane
+    const int lane = threadIdx.x;
+    float a[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = (j < nb && j <= lane && lane < nb) ? A[lane + j * lda] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < nb) {
+            const float d = __shfl_sync(0xffffffffu, a[j], j);
+            if (!(d > 0.0f)) {
+                if (lane == 0) *info = col0 + j + 1;
+                return;
+            }
+            const float ljj = sqrtf(d), r = 1.0f / ljj;
+            const float l = (lane == j) ? ljj : ((lane > j) ? a[j] * r : 0.0f);
+            a[j] = (lane >= j) ? l : a[j];
+            __syncwarp();
+            col[lane] = l;
+            __syncwarp();
+#pragma unroll
+            for (int k = j + 1; k < 32; ++k) a[k] = fmaf(-l, col[k], a[k]);
+        }
+    }
+    if (lane < nb) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nb && j <= lane) A[lane + j * lda] = a[j];
+    }
+}
+
+// Substitution: the m x nb block P (rows below the leaf) <- P L^-T with
+// the leaf's factor L (nb x nb lower, ld ldl), one thread per row.
+__global__ void __launch_bounds__(128) trsm32_kernel(float *P, int64_t ldp, int64_t m, int nb, const float *L,
+                                                     int64_t ldl, const int64_t *info)
+{
+    gpch::pdl_wait();
+    gpch::pdl_trigger();
+    __shared__ float Ls[32][33];   // Ls[j][k] = L(j, k)
+    __shared__ float rd[32];
+    if (*info != 0) return;
+    for (int e = threadIdx.x; e < 32 * 32; e += 128) {
+        const int j = e % 32, k = e / 32;
+        Ls[j][k] = (j < nb && k <= j) ? L[j + k * ldl] : 0.0f;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) rd[threadIdx.x] = threadIdx.x < nb ? 1.0f / Ls[threadIdx.x][threadIdx.x] : 0.0f;
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (r >= m) return;
+    float x[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = (j < nb) ? P[r + j * ldp] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < nb) {
+            const float v = x[j] * rd[j];
+            x[j] = v;
+#pragma unroll
+            for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-v, Ls[k][j], x[k]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j < nb) P[r + j * ldp] = x[j];
+}
+
+// Copy the nb x nb lower block of FP32 W into FP64 D (ld ldd).
 __global__ void tile_f32_to_f64(int64_t nb, const float *__restrict__ W, int64_t ldw, double *D, int64_t ldd)
 {
     const int64_t j = blockIdx.y;
     for (int64_t i = j + threadIdx.x; i < nb; i += blockDim.x) D[i + j * ldd] = (double)W[i + j * ldw];
-}
-
-__global__ void tile_f64_to_f32(int64_t nb, const double *__restrict__ D, int64_t ldd, float *W, int64_t ldw)
-{
-    const int64_t j = blockIdx.y;
-    for (int64_t i = j + threadIdx.x; i < nb; i += blockDim.x) W[i + j * ldw] = (float)D[i + j * ldd];
 }
 
 // Tensor map over a K-major 16-bit panel copy of m rows, `width` positions
@@ -1084,7 +1157,7 @@ namespace gpch {
 
 // Workspace layout of the mixed factor for n, tile.
 struct MixedWs {
-    double *D, *rinv, *Linv;
+    double *D, *Linv;
     float *Linv32;
     int64_t *info;
     __nv_bfloat16 *hi;        // 16-bit copies of all panels: row i, K column c at kpos(c) of hi + i * kpos(kpa)
@@ -1103,7 +1176,6 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.info = cv.take<int64_t>(1);
     w.err = cv.take<int>(4);
     w.D = cv.take<double>((size_t)tile * tile);
-    w.rinv = cv.take<double>((size_t)tile);
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
     w.Linv32 = cv.take<float>((size_t)(tile / LEAF) * LEAF * LEAF);
     const int64_t kpa = (n + BK - 1) / BK * BK;
@@ -1212,12 +1284,31 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t j0 = J * tile;
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         float *Wjj = W + j0 + j0 * ldw;
-        // step 1 in FP64 (timed inside chol_fp64_enqueue)
-        tile_f32_to_f64<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, Wjj, ldw, w.D, tile);
-        GPCH_LAUNCH_CHECK(ctx);
-        GPCH_CHECK(chol_fp64_enqueue(ctx, nj, tile, w.D, tile, w.rinv, w.info, st, j0));
-        tile_f64_to_f32<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, w.D, tile, Wjj, ldw);
-        GPCH_LAUNCH_CHECK(ctx);
+        {
+            // step 1 in FP32, 32-wide steps
+            PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
+            for (int64_t c0 = 0; c0 < nj; c0 += 32) {
+                const int nc = (int)((nj - c0 < 32) ? nj - c0 : 32);
+                float *Lcc = Wjj + c0 + c0 * ldw;
+                GPCH_CUDA(ctx, gpch::launch_pdl(leaf32_kernel, dim3(1), dim3(32), 0, st, Lcc, ldw, nc, j0 + c0, w.info));
+                GPCH_LAUNCH_CHECK(ctx);
+                const int64_t mr = nj - c0 - nc;
+                if (mr > 0) {
+                    float *Pb = Lcc + nc;
+                    GPCH_CUDA(ctx, gpch::launch_pdl(trsm32_kernel, dim3((unsigned)((mr + 127) / 128)), dim3(128), 0,
+                                                    st, Pb, ldw, mr, nc, (const float *)Lcc, ldw,
+                                                    (const int64_t *)w.info));
+                    GPCH_LAUNCH_CHECK(ctx);
+                    GPCH_CHECK(launch_gemm<float>(ctx, true, mr, mr, nc, Pb, ldw, Pb, ldw,
+                                                  Wjj + (c0 + nc) * (1 + ldw), ldw, w.info, st, true));
+                }
+            }
+        }
+        if (!tc_panel) {
+            // FP64 copy of the factored tile for the FP32 inverses of its 64 x 64 blocks
+            tile_f32_to_f64<<<dim3(1, (unsigned)nj), 256, 0, st>>>(nj, Wjj, ldw, w.D, tile);
+            GPCH_LAUNCH_CHECK(ctx);
+        }
         const int64_t m = n - j0 - nj;
         if (m <= 0) continue;
         float *Pan = W + (j0 + nj) + j0 * ldw;
