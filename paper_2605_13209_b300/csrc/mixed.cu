@@ -1,8 +1,8 @@
 // mixed.cu -- A8: the low-precision factor used as the preconditioner of the
 // refined solve.  Algorithm 1 (right) runs on an FP32 copy of the lower
 // triangle of A (+ shift * I):
-//   step 1  the diagonal tile is factored in FP32 as a nest of 32-wide
-//           steps (one-warp leaf / row-parallel substitution / SYRK);
+//   step 1  the diagonal tile is factored in FP32, left-looking, one
+//           launch per 32-column block (diag_step_kernel);
 //   step 2  SPLIT_F16: the panel is the tensor-core product A_ij L_jj^-T,
 //           with L_jj^-1 from an FP32 forward substitution; the bf16 modes
 //           solve it in FP32, 64 columns at a time, against FP32 inverses
@@ -905,84 +905,187 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
     }
 }
 
-// Step 1 in FP32: the diagonal tile as a nest of 32-wide steps (leaf ->
-// substitution below it -> SYRK inside the tile), the same launch structure
-// as the FP64 nest with FP32 arithmetic, each kernel launched as a
-// programmatic dependent of the one before.
-//
-// Leaf: one warp factors the nb x nb block (nb <= 32) at A, lane i holding
-// row i; each pivot column is broadcast through shared memory.  A pivot
-// that is not positive sets *info = col0 + (its column) + 1 and leaves the
-// block as it is.
-__global__ void __launch_bounds__(32) leaf32_kernel(float *A, int64_t lda, int nb, int64_t col0, int64_t *info)
+// Step 1 in FP32, left-looking, one launch per 32-column block of the
+// diagonal tile T (nb x nb, ld ldt): the launch for the block column at
+// c0 = 32 s forms, in every CTA b,
+//   D = T(c0.., c0..) - L(c0.., 0:c0) L(c0.., 0:c0)^T   (the 32 x 32 diagonal block)
+//   X = T(R.., c0..)  - L(R.., 0:c0)  L(c0.., 0:c0)^T   (its 32 rows, R = c0 + 32 (b + 1))
+// (warps 0-3 form D, warps 4-7 form X, 4 x 2 outputs per thread, the
+// columns 0:c0 of both row sets staged k-major in shared memory 32 at a
+// time by cp.async, four chunks in flight), factors D on one warp (each
+// pivot column broadcast through shared memory) and solves X L_ss^T = X,
+// one thread per row.  Every CTA forms and factors D itself, so the launch
+// needs no communication between CTAs.  L_ss may not be written into T
+// while other CTAs of the launch may still read T's block there as D's
+// input: with one CTA it is written at once, otherwise CTA 0 leaves it in
+// `lss` (32 x 32, ld 32) and the launch of the next block column (which
+// reads no entry of that block) copies it into T (prev_c0 >= 0).  A pivot
+// that is not positive sets *info = col0 + c0 + (its column) + 1 (CTA 0)
+// and ends every CTA.
+__device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
 {
-    gpch::pdl_wait();
-    gpch::pdl_trigger();
-    __shared__ float col[32];
-    if (*info != 0) return;   // the same value in every lane
-    const int lane = threadIdx.x;
-    float a[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = (j < nb && j <= lane && lane < nb) ? A[lane + j * lda] : 0.0f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j < nb) {
-            const float d = __shfl_sync(0xffffffffu, a[j], j);
-            if (!(d > 0.0f)) {
-                if (lane == 0) *info = col0 + j + 1;
-                return;
-            }
-            const float ljj = sqrtf(d), r = 1.0f / ljj;
-            const float l = (lane == j) ? ljj : ((lane > j) ? a[j] * r : 0.0f);
-            a[j] = (lane >= j) ? l : a[j];
-            __syncwarp();
-            col[lane] = l;
-            __syncwarp();
-#pragma unroll
-            for (int k = j + 1; k < 32; ++k) a[k] = fmaf(-l, col[k], a[k]);
-        }
-    }
-    if (lane < nb) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j < nb && j <= lane) A[lane + j * lda] = a[j];
-    }
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 
-// Substitution: the m x nb block P (rows below the leaf) <- P L^-T with
-// the leaf's factor L (nb x nb lower, ld ldl), one thread per row.
-__global__ void __launch_bounds__(128) trsm32_kernel(float *P, int64_t ldp, int64_t m, int nb, const float *L,
-                                                     int64_t ldl, const int64_t *info)
+constexpr int DS_THREADS = 256;
+constexpr int DS_KC = 32;       // K columns per staged chunk
+constexpr int DS_STAGES = 4;    // chunks in flight
+__global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t ldt, int nb, int c0, int64_t col0,
+                                                               int64_t *info, float *lss, int prev_c0)
 {
     gpch::pdl_wait();
     gpch::pdl_trigger();
-    __shared__ float Ls[32][33];   // Ls[j][k] = L(j, k)
+    __shared__ __align__(16) float Ad[DS_STAGES][DS_KC][32];   // Ad[.][k][i] = L(c0 + i, k0 + k)
+    __shared__ __align__(16) float Ar[DS_STAGES][DS_KC][32];   // Ar[.][k][r] = L(R + r, k0 + k)
+    __shared__ float Ds[32][33];                    // D, then L_ss (zero above the diagonal)
+    __shared__ float Xs[32][33];                    // X
     __shared__ float rd[32];
-    if (*info != 0) return;
-    for (int e = threadIdx.x; e < 32 * 32; e += 128) {
-        const int j = e % 32, k = e / 32;
-        Ls[j][k] = (j < nb && k <= j) ? L[j + k * ldl] : 0.0f;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) rd[threadIdx.x] = threadIdx.x < nb ? 1.0f / Ls[threadIdx.x][threadIdx.x] : 0.0f;
-    __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    if (r >= m) return;
-    float x[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = (j < nb) ? P[r + j * ldp] : 0.0f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j < nb) {
-            const float v = x[j] * rd[j];
-            x[j] = v;
-#pragma unroll
-            for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-v, Ls[k][j], x[k]);
+    __shared__ __align__(16) float colb[32];   // the pivot column being broadcast
+    __shared__ int bad;
+    if (*info != 0) return;   // the same value in every thread
+    const int tid = threadIdx.x;
+    if (prev_c0 >= 0 && blockIdx.x == 0) {
+        // the previous block column's diagonal block (32 columns: it was not the last)
+        for (int e = tid; e < 32 * 32; e += DS_THREADS) {
+            const int i = e % 32, j = e / 32;
+            if (j <= i) T[(prev_c0 + i) + (int64_t)(prev_c0 + j) * ldt] = lss[i + 32 * j];
         }
     }
+    const int nc = (nb - c0 < 32) ? nb - c0 : 32;
+    const int R = c0 + 32 * ((int)blockIdx.x + 1);
+    const int nr = (nb - R < 0) ? 0 : ((nb - R < 32) ? nb - R : 32);
+    const bool isD = tid < DS_THREADS / 2;
+    const int u = isD ? tid : tid - DS_THREADS / 2;
+    const int ri = 4 * (u % 8), cj = 2 * (u / 8);   // this thread's rows ri.., columns cj..
+    const int row0 = isD ? c0 : R, nrow = isD ? nc : nr;
+    float acc[4][2];
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-        if (j < nb) P[r + j * ldp] = x[j];
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int i = ri + a, j = cj + b;
+            // D: its lower triangle only (the tile's upper triangle is not read)
+            const bool in = i < nrow && j < nc && (!isD || j <= i);
+            acc[a][b] = in ? T[(row0 + i) + (int64_t)(c0 + j) * ldt] : 0.0f;
+        }
+    const int nchunk = (c0 + DS_KC - 1) / DS_KC;
+    // chunk ch (K columns 32 ch ..) into stage ch % DS_STAGES; one commit
+    // group per call, empty past the last chunk
+    auto stage = [&](int ch) {
+        if (ch < nchunk) {
+            const int k0 = ch * DS_KC, kc = (c0 - k0 < DS_KC) ? c0 - k0 : DS_KC, sb = ch % DS_STAGES;
+            for (int e = tid; e < kc * 32; e += DS_THREADS) {
+                const int r = e & 31, k = e >> 5;
+                const float *col = T + (int64_t)(k0 + k) * ldt;
+                if (r < nc) cp_async_f32(&Ad[sb][k][r], col + c0 + r);
+                else Ad[sb][k][r] = 0.0f;
+                if (r < nr) cp_async_f32(&Ar[sb][k][r], col + R + r);
+                else Ar[sb][k][r] = 0.0f;
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int ch = 0; ch < DS_STAGES - 1; ++ch) stage(ch);
+    for (int ch = 0; ch < nchunk; ++ch) {
+        stage(ch + DS_STAGES - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(DS_STAGES - 1) : "memory");
+        __syncthreads();
+        const int sb = ch % DS_STAGES, kc = (c0 - ch * DS_KC < DS_KC) ? c0 - ch * DS_KC : DS_KC;
+        const float(*Ao)[32] = isD ? Ad[sb] : Ar[sb];
+        const float(*Bo)[32] = Ad[sb];
+#pragma unroll 4
+        for (int k = 0; k < kc; ++k) {
+            const float4 av = *reinterpret_cast<const float4 *>(&Ao[k][ri]);
+            const float2 bv = *reinterpret_cast<const float2 *>(&Bo[k][cj]);
+            const float x[4] = {av.x, av.y, av.z, av.w}, y[2] = {bv.x, bv.y};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(-x[a], y[b], acc[a][b]);
+        }
+        __syncthreads();   // the stage is refilled at the next chunk
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (isD) Ds[ri + a][cj + b] = acc[a][b];
+            else Xs[ri + a][cj + b] = acc[a][b];
+        }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    if (tid < 32) {
+        // the leaf: lane i holds row i of D
+        const int lane = tid;
+        float a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = (j <= lane && lane < nc && j < nc) ? Ds[lane][j] : 0.0f;
+        int fail = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < nc && fail == 0) {
+                const float d = __shfl_sync(0xffffffffu, a[j], j);
+                if (!(d > 0.0f)) {
+                    fail = j + 1;
+                } else {
+                    const float r = rsqrtf(d), ljj = d * r;
+                    const float l = (lane == j) ? ljj : ((lane > j) ? a[j] * r : 0.0f);
+                    a[j] = (lane >= j) ? l : 0.0f;
+                    if (lane == j) rd[j] = r;
+                    __syncwarp();   // the previous column's broadcast has been read
+                    colb[lane] = l;
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (4 * q + 3 > j) {
+                            const float4 v = *reinterpret_cast<const float4 *>(&colb[4 * q]);
+                            const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * q + e > j) a[4 * q + e] = fmaf(-l, c[e], a[4 * q + e]);
+                        }
+                    }
+                }
+            }
+        }
+        if (fail != 0) {
+            if (lane == 0) {
+                bad = 1;
+                if (blockIdx.x == 0) *info = col0 + c0 + fail;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) Ds[lane][j] = a[j];
+        }
+    }
+    __syncthreads();
+    if (bad) return;
+    if (blockIdx.x == 0 && tid < nc) {
+        if (gridDim.x == 1) {
+            for (int j = 0; j <= tid; ++j) T[(c0 + tid) + (int64_t)(c0 + j) * ldt] = Ds[tid][j];
+        } else {
+            for (int j = 0; j <= tid; ++j) lss[tid + 32 * j] = Ds[tid][j];
+        }
+    }
+    if (tid < nr) {
+        float x[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = Xs[tid][j];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            if (j < nc) {
+                const float v = x[j] * rd[j];
+                x[j] = v;
+#pragma unroll
+                for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-v, Ds[k][j], x[k]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < nc) T[(R + tid) + (int64_t)(c0 + j) * ldt] = x[j];
+    }
 }
 
 // Copy the nb x nb lower block of FP32 W into FP64 D (ld ldd).
@@ -1158,6 +1261,7 @@ namespace gpch {
 // Workspace layout of the mixed factor for n, tile.
 struct MixedWs {
     double *D, *Linv;
+    float *lss;   // step 1: a diagonal 32 x 32 block on its way into W
     float *Linv32;
     int64_t *info;
     __nv_bfloat16 *hi;        // 16-bit copies of all panels: row i, K column c at kpos(c) of hi + i * kpos(kpa)
@@ -1176,6 +1280,7 @@ static MixedWs carve_mixed(Carver &cv, int64_t n, int tile)
     w.info = cv.take<int64_t>(1);
     w.err = cv.take<int>(4);
     w.D = cv.take<double>((size_t)tile * tile);
+    w.lss = cv.take<float>(32 * 32);
     w.Linv = cv.take<double>((size_t)(tile / LEAF) * LEAF * LEAF);
     w.Linv32 = cv.take<float>((size_t)(tile / LEAF) * LEAF * LEAF);
     const int64_t kpa = (n + BK - 1) / BK * BK;
@@ -1285,23 +1390,16 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         float *Wjj = W + j0 + j0 * ldw;
         {
-            // step 1 in FP32, 32-wide steps
+            // step 1 in FP32: one left-looking launch per 32-column block
             PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
-            for (int64_t c0 = 0; c0 < nj; c0 += 32) {
-                const int nc = (int)((nj - c0 < 32) ? nj - c0 : 32);
-                float *Lcc = Wjj + c0 + c0 * ldw;
-                GPCH_CUDA(ctx, gpch::launch_pdl(leaf32_kernel, dim3(1), dim3(32), 0, st, Lcc, ldw, nc, j0 + c0, w.info));
+            int prev = -1;   // block column whose diagonal block waits in w.lss
+            for (int c0 = 0; c0 < (int)nj; c0 += 32) {
+                const int64_t mr = nj - c0 - ((nj - c0 < 32) ? nj - c0 : 32);
+                const unsigned grid = mr > 0 ? (unsigned)((mr + 31) / 32) : 1u;
+                GPCH_CUDA(ctx, gpch::launch_pdl(diag_step_kernel, dim3(grid), dim3(DS_THREADS), 0, st, Wjj, ldw,
+                                                (int)nj, c0, j0, w.info, w.lss, prev));
                 GPCH_LAUNCH_CHECK(ctx);
-                const int64_t mr = nj - c0 - nc;
-                if (mr > 0) {
-                    float *Pb = Lcc + nc;
-                    GPCH_CUDA(ctx, gpch::launch_pdl(trsm32_kernel, dim3((unsigned)((mr + 127) / 128)), dim3(128), 0,
-                                                    st, Pb, ldw, mr, nc, (const float *)Lcc, ldw,
-                                                    (const int64_t *)w.info));
-                    GPCH_LAUNCH_CHECK(ctx);
-                    GPCH_CHECK(launch_gemm<float>(ctx, true, mr, mr, nc, Pb, ldw, Pb, ldw,
-                                                  Wjj + (c0 + nc) * (1 + ldw), ldw, w.info, st, true));
-                }
+                prev = grid > 1 ? c0 : -1;
             }
         }
         if (!tc_panel) {
