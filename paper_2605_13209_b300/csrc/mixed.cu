@@ -913,45 +913,48 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
 // (warps 0-3 form D, warps 4-7 form X, 4 x 2 outputs per thread, the
 // columns 0:c0 of both row sets staged k-major in shared memory 32 at a
 // time by cp.async, four chunks in flight), factors D on one warp (each
-// pivot column broadcast through shared memory) and solves X L_ss^T = X,
-// one thread per row.  Every CTA forms and factors D itself, so the launch
-// needs no communication between CTAs.  L_ss may not be written into T
-// while other CTAs of the launch may still read T's block there as D's
-// input: with one CTA it is written at once, otherwise CTA 0 leaves it in
-// `lss` (32 x 32, ld 32) and the launch of the next block column (which
-// reads no entry of that block) copies it into T (prev_c0 >= 0).  A pivot
-// that is not positive sets *info = col0 + c0 + (its column) + 1 (CTA 0)
-// and ends every CTA.
+// pivot column broadcast through shared memory), inverts L_ss on all eight
+// warps (four columns each) and forms X L_ss^-T as one 32 x 32 product.
+// Every CTA forms and factors D itself, so the launch needs no
+// communication between CTAs.  Launched as a programmatic dependent of the
+// previous block column's launch: what does not depend on it (the entries
+// of block column s, and K columns before the previous block column) is
+// loaded before the wait.  L_ss may not be written into T while other CTAs
+// of the launch may still read T's block there as D's input: with one CTA
+// it is written at once, otherwise CTA 0 leaves it in `lss` (32 x 32, ld
+// 32) and the launch of the next block column (which reads no entry of
+// that block) copies it into T (prev_c0 >= 0).  A pivot that is not
+// positive sets *info = col0 + c0 + (its column) + 1 (CTA 0) and ends
+// every CTA.
 __device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
 {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
+// wait until at most `pending` of this thread's cp.async groups are in flight
+__device__ __forceinline__ void cp_async_wait_upto(int pending)
+{
+    if (pending <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else if (pending == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else asm volatile("cp.async.wait_group 3;" ::: "memory");
+}
 
 constexpr int DS_THREADS = 256;
-constexpr int DS_KC = 32;       // K columns per staged chunk
-constexpr int DS_STAGES = 4;    // chunks in flight
+constexpr int DS_KC = 32;       // K columns per staged chunk (one block column)
+constexpr int DS_STAGES = 4;    // chunks in flight (cp_async_wait_upto covers up to 3 pending)
 __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t ldt, int nb, int c0, int64_t col0,
                                                                int64_t *info, float *lss, int prev_c0)
 {
-    gpch::pdl_wait();
-    gpch::pdl_trigger();
     __shared__ __align__(16) float Ad[DS_STAGES][DS_KC][32];   // Ad[.][k][i] = L(c0 + i, k0 + k)
     __shared__ __align__(16) float Ar[DS_STAGES][DS_KC][32];   // Ar[.][k][r] = L(R + r, k0 + k)
-    __shared__ float Ds[32][33];                    // D, then L_ss (zero above the diagonal)
-    __shared__ float Xs[32][33];                    // X
+    __shared__ float Ds[32][33];   // D, then L_ss (zero above the diagonal)
+    __shared__ float Xs[32][33];   // X
+    __shared__ float Ys[32][33];   // L_ss^-1
     __shared__ float rd[32];
     __shared__ __align__(16) float colb[32];   // the pivot column being broadcast
     __shared__ int bad;
-    if (*info != 0) return;   // the same value in every thread
-    const int tid = threadIdx.x;
-    if (prev_c0 >= 0 && blockIdx.x == 0) {
-        // the previous block column's diagonal block (32 columns: it was not the last)
-        for (int e = tid; e < 32 * 32; e += DS_THREADS) {
-            const int i = e % 32, j = e / 32;
-            if (j <= i) T[(prev_c0 + i) + (int64_t)(prev_c0 + j) * ldt] = lss[i + 32 * j];
-        }
-    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = (nb - c0 < 32) ? nb - c0 : 32;
     const int R = c0 + 32 * ((int)blockIdx.x + 1);
     const int nr = (nb - R < 0) ? 0 : ((nb - R < 32) ? nb - R : 32);
@@ -959,43 +962,62 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
     const int u = isD ? tid : tid - DS_THREADS / 2;
     const int ri = 4 * (u % 8), cj = 2 * (u / 8);   // this thread's rows ri.., columns cj..
     const int row0 = isD ? c0 : R, nrow = isD ? nc : nr;
+    const int nchunk = c0 / DS_KC;
     float acc[4][2];
+    auto init_acc = [&]() {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int i = ri + a, j = cj + b;
-            // D: its lower triangle only (the tile's upper triangle is not read)
-            const bool in = i < nrow && j < nc && (!isD || j <= i);
-            acc[a][b] = in ? T[(row0 + i) + (int64_t)(c0 + j) * ldt] : 0.0f;
-        }
-    const int nchunk = (c0 + DS_KC - 1) / DS_KC;
-    // chunk ch (K columns 32 ch ..) into stage ch % DS_STAGES; one commit
-    // group per call, empty past the last chunk
-    auto stage = [&](int ch) {
-        if (ch < nchunk) {
-            const int k0 = ch * DS_KC, kc = (c0 - k0 < DS_KC) ? c0 - k0 : DS_KC, sb = ch % DS_STAGES;
-            for (int e = tid; e < kc * 32; e += DS_THREADS) {
-                const int r = e & 31, k = e >> 5;
-                const float *col = T + (int64_t)(k0 + k) * ldt;
-                if (r < nc) cp_async_f32(&Ad[sb][k][r], col + c0 + r);
-                else Ad[sb][k][r] = 0.0f;
-                if (r < nr) cp_async_f32(&Ar[sb][k][r], col + R + r);
-                else Ar[sb][k][r] = 0.0f;
+            for (int b = 0; b < 2; ++b) {
+                const int i = ri + a, j = cj + b;
+                // D: its lower triangle only (the tile's upper triangle is not read)
+                const bool in = i < nrow && j < nc && (!isD || j <= i);
+                acc[a][b] = in ? T[(row0 + i) + (int64_t)(c0 + j) * ldt] : 0.0f;
             }
+    };
+    // chunk ch (K columns 32 ch ..) into stage ch % DS_STAGES, one commit group
+    auto stage = [&](int ch) {
+        const int k0 = ch * DS_KC, sb = ch % DS_STAGES;
+        for (int e = tid; e < DS_KC * 32; e += DS_THREADS) {
+            const int r = e & 31, k = e >> 5;
+            const float *col = T + (int64_t)(k0 + k) * ldt;
+            if (r < nc) cp_async_f32(&Ad[sb][k][r], col + c0 + r);
+            else Ad[sb][k][r] = 0.0f;
+            if (r < nr) cp_async_f32(&Ar[sb][k][r], col + R + r);
+            else Ar[sb][k][r] = 0.0f;
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    for (int ch = 0; ch < DS_STAGES - 1; ++ch) stage(ch);
+    int issued = 0;
+    const bool early = c0 > 0;   // the previous launch is this tile's block column s - 1
+    if (early) {
+        init_acc();
+        while (issued < DS_STAGES - 1 && issued < nchunk - 1) stage(issued++);
+    }
+    gpch::pdl_wait();
+    gpch::pdl_trigger();
+    if (*info != 0) {   // the same value in every thread
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        return;
+    }
+    if (prev_c0 >= 0 && blockIdx.x == 0) {
+        // the previous block column's diagonal block (32 columns: it was not the last)
+        for (int e = tid; e < 32 * 32; e += DS_THREADS) {
+            const int i = e % 32, j = e / 32;
+            if (j <= i) T[(prev_c0 + i) + (int64_t)(prev_c0 + j) * ldt] = lss[i + 32 * j];
+        }
+    }
+    if (!early) init_acc();
+    while (issued < DS_STAGES - 1 && issued < nchunk) stage(issued++);
     for (int ch = 0; ch < nchunk; ++ch) {
-        stage(ch + DS_STAGES - 1);
-        asm volatile("cp.async.wait_group %0;" ::"n"(DS_STAGES - 1) : "memory");
+        if (issued < nchunk && issued < ch + DS_STAGES) stage(issued++);
+        cp_async_wait_upto(issued - 1 - ch);
         __syncthreads();
-        const int sb = ch % DS_STAGES, kc = (c0 - ch * DS_KC < DS_KC) ? c0 - ch * DS_KC : DS_KC;
+        const int sb = ch % DS_STAGES;
         const float(*Ao)[32] = isD ? Ad[sb] : Ar[sb];
         const float(*Bo)[32] = Ad[sb];
 #pragma unroll 4
-        for (int k = 0; k < kc; ++k) {
+        for (int k = 0; k < DS_KC; ++k) {
             const float4 av = *reinterpret_cast<const float4 *>(&Ao[k][ri]);
             const float2 bv = *reinterpret_cast<const float2 *>(&Bo[k][cj]);
             const float x[4] = {av.x, av.y, av.z, av.w}, y[2] = {bv.x, bv.y};
@@ -1004,9 +1026,8 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
 #pragma unroll
                 for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(-x[a], y[b], acc[a][b]);
         }
-        __syncthreads();   // the stage is refilled at the next chunk
+        __syncthreads();   // the stage is refilled by a later chunk
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -1016,9 +1037,8 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
         }
     if (tid == 0) bad = 0;
     __syncthreads();
-    if (tid < 32) {
+    if (warp == 0) {
         // the leaf: lane i holds row i of D
-        const int lane = tid;
         float a[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) a[j] = (j <= lane && lane < nc && j < nc) ? Ds[lane][j] : 0.0f;
@@ -1069,22 +1089,43 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
             for (int j = 0; j <= tid; ++j) lss[tid + 32 * j] = Ds[tid][j];
         }
     }
-    if (tid < nr) {
-        float x[32];
+    if (nr == 0) return;   // (a block column with rows below it is 32 wide)
+    {
+        // Y = L_ss^-1: warp w solves L y = e_c for c = 4w .. 4w + 3, lane = row
+        float lrow[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x[j] = Xs[tid][j];
+        for (int k = 0; k < 32; ++k) lrow[k] = Ds[lane][k];
+        float y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] = (lane == 4 * warp + q) ? 1.0f : 0.0f;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            if (j < nc) {
-                const float v = x[j] * rd[j];
-                x[j] = v;
+            const float rj = rd[j];
 #pragma unroll
-                for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-v, Ds[k][j], x[k]);
+            for (int q = 0; q < 4; ++q) {
+                if (lane == j) y[q] *= rj;
+                const float yj = __shfl_sync(0xffffffffu, y[q], j);
+                if (lane > j) y[q] = fmaf(-lrow[j], yj, y[q]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j < nc) T[(R + tid) + (int64_t)(c0 + j) * ldt] = x[j];
+        for (int q = 0; q < 4; ++q) Ys[lane][4 * warp + q] = y[q];
+    }
+    __syncthreads();
+    {
+        // X L_ss^-T: thread (row r, columns 4 jg ..)
+        const int r = tid & 31, jg = tid >> 5;
+        float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const float x = Xs[r][k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = fmaf(x, Ys[4 * jg + q][k], o[q]);
+        }
+        if (r < nr) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) T[(R + r) + (int64_t)(c0 + 4 * jg + q) * ldt] = o[q];
+        }
     }
 }
 
