@@ -327,8 +327,9 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
       config1  n = 2048 (33.5 MB, L2-resident), one RHS, solved to 1e-10
       config3  n = 65536, ell = 0.3, sn2 = 0.1, 16 RHS, FP64-stored
                (34.4 GB) and FP32-stored (17.2 GB) A, solved to 1e-10 with
-               replacement every 50 iterations (double-float products);
-               the FP64-product rate over a few iterations beside it"""
+               replacement every 50 iterations (double-float products, and
+               FP64-accurate tensor-core products); the FP64-product rate
+               over a few iterations beside it"""
     import torch
     from paper_2605_13209_b300 import gpchol, inputs
     hbm = pk.get("hbm_gbs", 6400.0)
@@ -392,6 +393,19 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                          "matvec_frac_of_hbm": round(gbs / hbm, 4),
                          "products_tera_per_s": round(ops / 4.0, 3),
                          "true_relres_max": _true_relres(AA, B3, X3)}
+            # FP64-accurate tensor-core products (the digit copy of A, 16 bytes
+            # per entry, lives in a context of its own, released after)
+            ctx_t = gpchol.Context(ctx.device)
+            _cg_timed(ctx_t, AA, B3, X3, "classic", "tensor", 0.0, 2, 0)
+            mst, rest, mvt = _cg_timed(ctx_t, AA, B3, X3, "classic", "tensor", 1e-10, 20000, 50)
+            ctx_t.close()
+            mst = max_over_ranks(mst)
+            c3[label]["tensor_products"] = {
+                "ms": round(mst, 1), "iterations": rest.iterations, "converged": rest.converged,
+                "ms_per_iteration": round(mst / max(rest.iterations, 1), 3),
+                "speedup_vs_double_float": round(ms / max(mst, 1e-9), 2),
+                "digit_bytes_per_iteration": 16 * ((n3 + 127) // 128 * 128) * ((n3 + 511) // 512 * 512),
+                "true_relres_max": _true_relres(AA, B3, X3)}
             # FP64 products on the same operator: rate over a few iterations
             _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, 1, 0)
             ms64, res64, mv64 = _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, args.cg3_fp64_iters, 0)
@@ -402,7 +416,9 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                 "frac_of_fp64_fma_rate": round(n3 * n3 * 16 / (mv64_ms / 1e3) / (FP64_PEAK_GFLOPS * 1e9 / 2), 4)}
         c3["what"] = (f"n={n3} SE (ell=0.3, sn2=0.1), 16 RHS, classic CG with double-float products to relative "
                       "residual 1e-10 (replacement every 50 iterations, FP64 true residuals); FP32-stored A is the "
-                      "FP32 rounding of the FP64 matrix; products_tera_per_s = n^2 * 16 / matvec time")
+                      "FP32 rounding of the FP64 matrix; products_tera_per_s = n^2 * 16 / matvec time; "
+                      "tensor_products: the same solve with FP64-accurate tensor-core products (8 base-128 digits "
+                      "per entry, 36 digit pairs, exact per 512-entry pass), A's digits made once per solve")
         out["config3"] = c3
         del A64, A32, B3, X3
     return out

@@ -232,7 +232,8 @@ typedef enum gpch_cg_variant {
 
 typedef enum gpch_cg_products {
     GPCH_CG_PRODUCTS_FP64 = 0,         /* one FP64 FMA per entry and right-hand side  */
-    GPCH_CG_PRODUCTS_DOUBLE_FLOAT = 1  /* double-float products on the FP32 pipe      */
+    GPCH_CG_PRODUCTS_DOUBLE_FLOAT = 1, /* double-float products on the FP32 pipe      */
+    GPCH_CG_PRODUCTS_TENSOR = 2        /* FP64-accurate products on the tensor cores  */
 } gpch_cg_products;
 
 typedef struct gpch_cg_opts {
@@ -271,7 +272,22 @@ typedef struct gpch_cg_opts {
  * solve then reports NOT_CONVERGED).  The true residuals b - A x (at the
  * start and on replacement iterations) always use FP64 products, so the
  * accuracy the iteration reaches is that of FP64 CG.  The vector
- * recurrences, inner products and scalars stay FP64 in both forms. */
+ * recurrences, inner products and scalars stay FP64 in both forms.
+ *
+ * GPCH_CG_PRODUCTS_TENSOR: the iteration products on the bf16 tensor cores
+ * by an error-free splitting (as gpch_gemm_fp64_emulated): A is cut once
+ * per solve (and per group of 16 right-hand sides) into 8 base-128 digits
+ * per entry with a power-of-two scale per column of A and 512-entry pass,
+ * each vector once per product likewise; the 36 kept digit pairs are
+ * summed exactly per pass and rounded once, passes added in FP64.  Per
+ * entry of A s the error is at most about n 2^-48 max_j |A_ij| max |s|
+ * (per pass: 512 2^-48 times the pass's largest |A_ij| and |s_j|).  A must
+ * be symmetric (its columns serve as rows).  Extra workspace: 16 np kp
+ * bytes for A's digits (np = n rounded up to 128, kp = n rounded up to
+ * 512) plus 4 np kp / 512 bytes of exponents.  True residuals keep FP64
+ * products.  Errors as above, plus INVALID_ARG when np kp / 8 does not fit
+ * 31 bits (n above about 131000) and TIMEOUT when a bounded tensor-core
+ * wait gave up. */
 gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,
                              const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double rtol,
                              int maxit, int replace_every, const gpch_cg_opts *opts, void *stream,

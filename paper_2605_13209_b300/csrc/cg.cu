@@ -54,15 +54,29 @@
 //              True residuals b - A x (the start and every replacement)
 //              always take FP64 products: they bound the accuracy the
 //              iteration can reach, and they are 1/R of the products.
+//   PROD_OZ    FP64-accurate products on the bf16 tensor cores, the
+//              error-free splitting of ozaki.cu: A (as A^T, its columns)
+//              is cut once per solve into 8 base-128 digits per entry with
+//              one power-of-two scale per column and 512-row pass, the
+//              vectors every matvec likewise per right-hand side; a CTA
+//              forms 128 entries of A s for all right-hand sides (an
+//              M = 128, N = 16 tensor-core tile), the 36 kept digit pairs
+//              summed exactly in 8 FP32 class accumulators per pass and
+//              combined and rounded once per pass, passes added in FP64.
+//              The digit copy takes 16 bytes per entry of A.  True
+//              residuals keep FP64 products.
+
+#include <cuda_bf16.h>
 
 #include "dense_fp64.cuh"
+#include "ozaki.cuh"
 
 namespace {
 
 constexpr int THREADS = 256;
 constexpr int MAXRHS = 16;
 
-enum Product : int { PROD_FP64 = 0, PROD_DF = 1 };
+enum Product : int { PROD_FP64 = 0, PROD_DF = 1, PROD_OZ = 2 };
 enum Variant : int { VAR_CLASSIC = 0, VAR_SINGLE_REDUCTION = 1 };
 enum MvMode : int { MV_ALPHA = 0, MV_PLAIN = 1, MV_SR = 2 };
 
@@ -72,6 +86,23 @@ struct CGState {
     int *done;                      // [1]
     unsigned *counter;              // [2]: matvec, vector kernels
     double *part;                   // per-CTA partials, part_doubles(n, nrhs)
+};
+
+// Buffers of the tensor-core path: the digit copy of A^T, tile-major so
+// that a CTA streams contiguous memory: for row tile rt (128 rows, the
+// last padded with zeros to npad rows), K stage kc (32 columns) and plane
+// b (digits 2b, 2b + 1), a block of 128 rows of 64 positions (128 bytes:
+// digit p of column k at (p % 2) 32 + k % 32); its exponents
+// EA[t * npad + j] (column j, pass t); the vectors' copy DS (4 planes of 16
+// rows, 2 kpt positions per row, digit p of k at oz_pos(p, k) of plane
+// p / 2) and exponents ES[t * 16 + r]; the status word of the bounded
+// waits.  np passes of 512, kpt = 512 np.
+struct OzArgs {
+    __nv_bfloat16 *DA, *DS;
+    int *EA, *ES;
+    int *err;
+    int np;
+    int64_t kpt, npad;
 };
 
 // Inputs of the double-float path.  SS holds the pre-split vector,
@@ -84,6 +115,7 @@ struct DFArgs {
     const double *scale;
     const double *inv;
     const int *ebias;
+    OzArgs oz;   // the tensor-core path's buffers (PROD_OZ)
 };
 
 struct SRArgs {
@@ -91,6 +123,7 @@ struct SRArgs {
     int maxit;
     int first;   // the set-up product w = A r0: sets gamma_0, alpha_0, beta_0
 };
+
 
 __device__ inline double warp_sum(double v)
 {
@@ -195,9 +228,9 @@ __device__ __forceinline__ void mv_finish(int64_t j0, int wcols, int nrhs, const
 {
     const int tid = threadIdx.x;
     __syncthreads();
-    if (tid < W * NR) {
-        const int c = tid / NR, r = tid % NR;
-        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = tcol[tid];
+    for (int e = tid; e < W * NR; e += THREADS) {
+        const int c = e / NR, r = e % NR;
+        if (c < wcols && r < nrhs) T[(j0 + c) + r * ldt] = tcol[e];
     }
     if (mode == MV_PLAIN) return;
     if (mode == MV_ALPHA) {
@@ -543,6 +576,292 @@ __global__ void __launch_bounds__(THREADS) cg_matvec_df_tiled_kernel(int64_t n, 
     mv_finish<TW, NR>(j0, wcols, nrhs, S, lds, T, ldt, st, mode, sr, tcol);
 }
 
+// ----------------------------------------------- tensor-core products
+
+// N = round(x 2^(54 - e)) for |x| < 2^e from x's bit pattern (integer
+// operations only; FP64 or FP32 x).
+template <typename TX>
+__device__ __forceinline__ long long oz_fixed(TX x, int e)
+{
+    unsigned long long mant;
+    int ebits, bias;
+    bool neg;
+    if constexpr (sizeof(TX) == 8) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong((double)x);
+        const int E11 = (int)((bits >> 52) & 0x7ff);
+        mant = bits & 0xfffffffffffffull;
+        ebits = E11 == 0 ? 1 : E11;
+        if (E11 != 0) mant |= 1ull << 52;
+        bias = 1075;
+        neg = (bits >> 63) != 0;
+    } else {
+        const unsigned bits = __float_as_uint((float)x);
+        const int E8 = (int)((bits >> 23) & 0xff);
+        mant = bits & 0x7fffffu;
+        ebits = E8 == 0 ? 1 : E8;
+        if (E8 != 0) mant |= 1u << 23;
+        bias = 150;
+        neg = (bits >> 31) != 0;
+    }
+    // x = mant 2^(ebits - bias); shift to units of 2^(e - 54)
+    const int sh = ebits - bias + 54 - e;
+    unsigned long long a;
+    if (sh >= 0) a = mant << sh;   // sh <= 1 for FP64 (|x| < 2^e); FP32 mantissas are shorter
+    else if (sh > -64) a = (mant + (1ull << (-sh - 1))) >> (-sh);
+    else a = 0;
+    return neg ? -(long long)a : (long long)a;
+}
+
+// Digits of the columns of X (column c: its n entries, ld ldx) for the
+// tensor-core products: column c becomes row c of each of the 4 digit
+// planes (plane_rows rows each, row stride 2 kpt, digit p of entry k at
+// oz_pos(p, k) of plane p / 2; tiled: the tile-major layout of OzArgs::DA),
+// with exponent E[t * plane_rows + c] per pass t of 512 entries (the
+// smallest e with every |x| of the pass below 2^e; 0 for a zero pass).
+// Columns at or past ncols (and entries past n) are zero.  One warp per
+// (column, pass).
+template <typename TX>
+__global__ void __launch_bounds__(256) oz_split_cols_kernel(int64_t n, int np, int64_t kpt, const TX *__restrict__ X,
+                                                            int64_t ldx, int64_t ncols, int64_t plane_rows,
+                                                            __nv_bfloat16 *__restrict__ D, int *__restrict__ E,
+                                                            const int *done, int tiled)
+{
+    if (done && *done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t c = w / np;
+    const int t = (int)(w % np);
+    if (c >= plane_rows) return;
+    const bool valid = c < ncols;
+    const int64_t k0 = (int64_t)t * 512;
+    const TX *x = X + (valid ? c : 0) * ldx;
+    TX v[16];
+    TX mx = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t k = k0 + lane + 32 * i;
+        v[i] = (valid && k < n) ? x[k] : (TX)0;
+        mx = mx > (v[i] < 0 ? -v[i] : v[i]) ? mx : (v[i] < 0 ? -v[i] : v[i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const TX o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = mx > o ? mx : o;
+    }
+    int e = 0;
+    if (mx > (TX)0) {
+        if constexpr (sizeof(TX) == 8) frexp((double)mx, &e);
+        else frexpf((float)mx, &e);
+    }
+    if (lane == 0) E[(int64_t)t * plane_rows + c] = e;
+    const int64_t ld = 2 * kpt;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t k = k0 + lane + 32 * i;
+        long long N = oz_fixed<TX>(v[i], e);
+        // balanced base-128 digits, least significant first
+#pragma unroll
+        for (int p = 7; p >= 0; --p) {
+            long long d;
+            if (p > 0) {
+                d = ((N + 64) & 127) - 64;
+                N = (N - d) >> 7;
+            } else {
+                d = N;   // |N| <= 2^54 / 128^7 + 1 = 33
+            }
+            const int64_t at = tiled ? ((((c / 128) * (kpt / 32) + k / 32) * 4 + p / 2) * 128 + c % 128) * 64 +
+                                           (p & 1) * 32 + k % 32
+                                     : (int64_t)(p / 2) * plane_rows * ld + c * ld + gpch::oz_pos(p, k);
+            D[at] = __float2bfloat16_rn((float)d);
+        }
+    }
+}
+
+// T = A s for up to 16 right-hand sides with FP64-accurate tensor-core
+// products (PROD_OZ): CTA b forms rows 128 b .. 128 b + 127 of A s for all
+// right-hand sides, then the mode's reductions as the other matvecs do.
+// tm_a: the digit copy of A^T (tile-major, rows of 64 positions, 128-row
+// boxes); tm_s:
+// the vectors' ((4 16) x (2 kpt), 16-row boxes).  Roles: warp 0 lane 0 TMA
+// (3 stages of 4 + 4 boxes over 32 K columns), warp 1 the TMEM (two sets
+// of 8 class accumulators of 16 columns, one set per pass, alternating) and
+// its lane 0 the MMAs (36 digit pairs x 2 K steps per stage), warps 4-7
+// the epilogue (warp w: rows 32 (w % 4) .., its TMEM lanes), which per pass
+// combines the class sums exactly, rounds once and adds in FP64.  Bounded
+// waits set *oz.err.
+constexpr int OZM_BM = 128;
+constexpr int OZM_N = MAXRHS;
+constexpr int OZM_KSTAGE = 32;
+constexpr int OZM_SPP = 512 / OZM_KSTAGE;    // stages per pass
+constexpr int OZM_STAGES = 3;
+constexpr uint32_t OZM_ABOX = OZM_BM * 128, OZM_SBOX = OZM_N * 128;
+constexpr uint32_t OZM_STAGE = 4 * (OZM_ABOX + OZM_SBOX);   // 72 KB
+constexpr size_t OZM_SMEM = OZM_STAGES * OZM_STAGE + 1024 + 256;
+constexpr uint32_t OZM_TMEM = 256;
+constexpr uint32_t OZM_SPIN = 1u << 26;
+static_assert((size_t)OZM_BM * OZM_N * sizeof(double) <= OZM_STAGES * OZM_STAGE, "tcol fits the stages");
+
+__global__ void __launch_bounds__(THREADS, 1)
+    oz_matvec_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_s, int64_t n,
+                     int nrhs, const double *S, int64_t lds, double *T, int64_t ldt, CGState st, int mode, SRArgs sr,
+                     OzArgs oz)
+{
+    if (*st.done) return;
+    extern __shared__ __align__(1024) uint8_t ozm_smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ozm_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + OZM_STAGES * OZM_STAGE);
+    uint64_t *empty = full + OZM_STAGES;
+    uint64_t *tfull = empty + OZM_STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = (int64_t)blockIdx.x * OZM_BM;
+    const int np = oz.np;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZM_STAGES; ++s) {
+            gpch::tc::mbar_init(&full[s], 1);
+            gpch::tc::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            gpch::tc::mbar_init(&tfull[a], 1);
+            gpch::tc::mbar_init(&tempty[a], 4);
+        }
+        gpch::tc::fence_mbar_init();
+    }
+    if (warp == 1) gpch::tc::tmem_alloc<OZM_TMEM>(tmem_slot);
+    gpch::tc::tc_fence_before();
+    __syncthreads();
+    gpch::tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int NK = np * OZM_SPP;
+    double acc64[OZM_N];
+#pragma unroll
+    for (int j = 0; j < OZM_N; ++j) acc64[j] = 0.0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            gpch::tc::prefetch_tmap(&tm_a);
+            gpch::tc::prefetch_tmap(&tm_s);
+            int issued = 0;
+            for (int kc = 0; kc < NK; ++kc) {
+                const int s = kc % OZM_STAGES;
+                if (kc >= OZM_STAGES && !gpch::tc::mbar_wait(&empty[s], ((kc / OZM_STAGES) - 1) & 1, OZM_SPIN)) {
+                    atomicExch(oz.err, 1);
+                    break;
+                }
+                uint8_t *stg = smem + s * OZM_STAGE;
+                gpch::tc::mbar_arrive_expect_tx(&full[s], OZM_STAGE);
+                const int32_t x = (int32_t)(kc * 2 * OZM_KSTAGE);   // bf16 positions
+                for (int b = 0; b < 4; ++b) {
+                    gpch::tc::tma_load_2d(stg + b * OZM_ABOX, &tm_a, &full[s], 0,
+                                          (int32_t)((((int64_t)blockIdx.x * NK + kc) * 4 + b) * OZM_BM));
+                    gpch::tc::tma_load_2d(stg + 4 * OZM_ABOX + b * OZM_SBOX, &tm_s, &full[s], x,
+                                          (int32_t)(b * OZM_N));
+                }
+                ++issued;
+            }
+            // every copy this thread started has landed before the CTA exits
+            for (int s = 0; s < OZM_STAGES && s < issued; ++s) {
+                const int uses = (issued - 1 - s) / OZM_STAGES + 1;
+                if (!gpch::tc::mbar_wait(&full[s], (uses - 1) & 1, OZM_SPIN)) atomicExch(oz.err, 4);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = gpch::tc::idesc_bf16_f32(OZM_BM, OZM_N);
+            bool ok = true;
+            int kc = 0;
+            for (int t = 0; t < np && ok; ++t) {
+                // the set of pass t (t % 2) must have been read out for pass t - 2
+                const int set = t & 1, use = t >> 1;
+                if (use >= 1 && !gpch::tc::mbar_wait(&tempty[set], (use - 1) & 1, 4 * OZM_SPIN)) {
+                    atomicExch(oz.err, 2);
+                    break;
+                }
+                gpch::tc::tc_fence_after();
+                const uint32_t accs = tmem + (uint32_t)(set * 8 * OZM_N);
+                for (int q = 0; q < OZM_SPP; ++q, ++kc) {
+                    const int s = kc % OZM_STAGES;
+                    if (!gpch::tc::mbar_wait(&full[s], (kc / OZM_STAGES) & 1, OZM_SPIN)) {
+                        atomicExch(oz.err, 2);
+                        ok = false;
+                        break;
+                    }
+                    gpch::tc::tc_fence_after();
+                    const uint32_t sa = gpch::tc::smem_u32(smem + s * OZM_STAGE);
+                    const uint32_t sb = sa + 4 * OZM_ABOX;
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) {
+                        const uint64_t a = gpch::tc::sdesc_sw128(sa + (p / 2) * OZM_ABOX) + 4 * (p & 1);
+#pragma unroll
+                        for (int d = 0; d + p < 8; ++d) {
+                            const uint64_t b = gpch::tc::sdesc_sw128(sb + (d / 2) * OZM_SBOX) + 4 * (d & 1);
+                            const uint32_t acc = accs + (uint32_t)((p + d) * OZM_N);
+                            // the first product into a class (p = 0 starts every class) of the pass overwrites it
+#pragma unroll
+                            for (int k = 0; k < 2; ++k)
+                                gpch::tc::mma_bf16(acc, a + 2 * k, b + 2 * k, idesc, (q > 0 || k > 0 || p > 0) ? 1u : 0u);
+                        }
+                    }
+                    gpch::tc::mma_commit(&empty[s]);
+                }
+                if (ok) gpch::tc::mma_commit(&tfull[set]);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        const int qw = warp & 3;
+        const int64_t row = i0 + qw * 32 + lane;
+        const bool row_ok = row < n;
+        const uint32_t tl = tmem + ((uint32_t)(qw * 32) << 16);
+        for (int t = 0; t < np; ++t) {
+            const int set = t & 1, use = t >> 1;
+            bool ok = gpch::tc::mbar_wait(&tfull[set], use & 1, 4 * OZM_SPIN);
+            ok = __all_sync(0xffffffffu, ok);
+            gpch::tc::tc_fence_after();
+            if (!ok) {
+                if (lane == 0) atomicExch(oz.err, 3);
+                break;
+            }
+            uint32_t vr[8][16];
+#pragma unroll
+            for (int D = 0; D < 8; ++D) gpch::tc::tmem_ld16_nowait(tl + (uint32_t)(set * 8 * OZM_N + D * OZM_N), vr[D]);
+            gpch::tc::tmem_ld_wait();
+            // the set is read: the MMAs of pass t + 2 may use it
+            gpch::tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) gpch::tc::mbar_arrive(&tempty[set]);
+            const int er = row_ok ? oz.EA[(int64_t)t * oz.npad + row] : 0;
+#pragma unroll
+            for (int j = 0; j < OZM_N; ++j) {
+                // exact class sums (integers of magnitude <= 2^24)
+                long long H = 0, L = 0;
+#pragma unroll
+                for (int D = 0; D < 4; ++D) H = H * 128 + __float2int_rn(__uint_as_float(vr[D][j]));
+#pragma unroll
+                for (int D = 4; D < 8; ++D) L = L * 128 + __float2int_rn(__uint_as_float(vr[D][j]));
+                acc64[j] += gpch::oz_round_scaled(H, L, er + __ldg(&oz.ES[t * OZM_N + j]) - 59);
+            }
+        }
+    }
+    // the products are in; the stages' memory holds them for the reductions
+    gpch::tc::tc_fence_before();
+    __syncthreads();
+    double *tcol = reinterpret_cast<double *>(smem);
+    if (warp >= 4) {
+        const int r = (warp & 3) * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < OZM_N; ++j) tcol[r * OZM_N + j] = acc64[j];
+    }
+    const int64_t wrows = (n - i0 < OZM_BM) ? n - i0 : OZM_BM;
+    mv_finish<OZM_BM, OZM_N>(i0, (int)wrows, nrhs, S, lds, T, ldt, st, mode, sr, tcol);
+    __syncthreads();
+    if (warp == 1) {
+        gpch::tc::tc_fence_after();
+        gpch::tc::tmem_dealloc<OZM_TMEM>(tmem);
+    }
+}
+
 // SS[i * NR + r] = (head, tail) of inv[r] * V[i, r]: float(v) and
 // float(v - float(v)) (conversions on the FP64 pipe, once per entry).
 template <int NR>
@@ -788,6 +1107,7 @@ __global__ void __launch_bounds__(THREADS) absmax_cols_kernel(int64_t n, int nrh
 inline int mv_nr(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
 inline int mv_width(int nrhs, int prod)
 {
+    if (prod == PROD_OZ) return OZM_BM;
     if (prod == PROD_DF) return nrhs <= 2 ? 8 : TW;
     return nrhs <= 1 ? 4 : nrhs <= 2 ? 8 : nrhs <= 4 ? 4 : 2;
 }
@@ -830,6 +1150,30 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
 {
     if (ncols < 0) ncols = n;
     const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((lda * (int64_t)sizeof(TA)) & 15) == 0) ? 1 : 0;
+    if (prod == PROD_OZ) {
+        // the vectors' digits, then the tensor-core product (A's digits
+        // were made once per solve by oz_prepare)
+        const OzArgs &oz = df.oz;
+        const int *done = (mode == MV_SR && sr.first) ? nullptr : st.done;
+        oz_split_cols_kernel<double><<<(unsigned)((OZM_N * oz.np + 7) / 8), 256, 0, s>>>(
+            n, oz.np, oz.kpt, S, lds, nrhs, OZM_N, oz.DS, oz.ES, done, 0);
+        GPCH_LAUNCH_CHECK(ctx);
+        CUtensorMap ma, ms;
+        GPCH_CHECK(gpch::oz_map(ctx, &ma, oz.DA, oz.npad * (oz.kpt / OZM_KSTAGE) * 4, 64, OZM_BM));
+        GPCH_CHECK(gpch::oz_map(ctx, &ms, oz.DS, 4 * OZM_N, 2 * oz.kpt, OZM_N));
+        static gpch::DeviceOnce attr_once;
+        GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(oz_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)OZM_SMEM));
+            return GPCH_OK;
+        }));
+        gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s,
+                            (double)n * oz.kpt * 16.0 + (double)(n + ncols) * nrhs * sizeof(double));
+        oz_matvec_kernel<<<(unsigned)((n + OZM_BM - 1) / OZM_BM), THREADS, OZM_SMEM, s>>>(ma, ms, n, nrhs, S, lds, T,
+                                                                                       ldt, st, mode, sr, oz);
+        GPCH_LAUNCH_CHECK(ctx);
+        return GPCH_OK;
+    }
     if (prod == PROD_DF) {
         const int nr = mv_nr(nrhs);
         const unsigned blocks = (unsigned)((n * nr + THREADS - 1) / THREADS);
@@ -884,7 +1228,8 @@ cudaError_t cg_kernels_load()
 inline size_t part_doubles(int64_t n, int nrhs, int prod = PROD_FP64, int variant = VAR_CLASSIC)
 {
     const int sets = variant == VAR_SINGLE_REDUCTION ? 2 : 1;
-    const size_t mv = (size_t)((n + mv_width(nrhs, prod) - 1) / mv_width(nrhs, prod)) * mv_nr(nrhs) * sets;
+    const int nr = prod == PROD_OZ ? OZM_N : mv_nr(nrhs);
+    const size_t mv = (size_t)((n + mv_width(nrhs, prod) - 1) / mv_width(nrhs, prod)) * nr * sets;
     const size_t vec = (size_t)((n + THREADS - 1) / THREADS) * 3 * MAXRHS;
     return mv > vec ? mv : vec;
 }
@@ -922,8 +1267,19 @@ inline size_t cg_carve(void *base, int64_t n, int nrhs, int prod, int variant, C
     t.st.done = t.ic + 2 * MAXRHS;
     t.st.counter = cv.take<unsigned>(2);
     t.st.part = cv.take<double>(part_doubles(n, nrhs, prod, variant));
-    t.df = DFArgs{nullptr, nullptr, nullptr, nullptr};
+    t.df = DFArgs{nullptr, nullptr, nullptr, nullptr, OzArgs{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0}};
     t.dmax = nullptr;
+    if (prod == PROD_OZ) {
+        OzArgs &oz = t.df.oz;
+        oz.np = (int)((n + 511) / 512);
+        oz.kpt = (int64_t)oz.np * 512;
+        oz.npad = (n + OZM_BM - 1) / OZM_BM * OZM_BM;
+        oz.err = cv.take<int>(1);
+        oz.DA = cv.take<__nv_bfloat16>((size_t)4 * oz.npad * 2 * oz.kpt);
+        oz.EA = cv.take<int>((size_t)oz.np * oz.npad);
+        oz.DS = cv.take<__nv_bfloat16>((size_t)4 * OZM_N * 2 * oz.kpt);
+        oz.ES = cv.take<int>((size_t)oz.np * OZM_N);
+    }
     if (prod == PROD_DF) {
         t.df.SS = cv.take<float2>((size_t)n * mv_nr(nrhs));
         double *d = cv.take<double>(2 * MAXRHS);
@@ -962,9 +1318,22 @@ gpch_status df_prepare(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64_t 
     return GPCH_OK;
 }
 
+// Enqueues the digit copy of A^T for the tensor-core products of one solve
+// (A symmetric: A^T's rows are A's columns, read contiguously).
+template <typename TA>
+gpch_status oz_prepare(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const CGBufs &b, cudaStream_t s)
+{
+    const OzArgs &oz = b.df.oz;
+    GPCH_CUDA(ctx, cudaMemsetAsync(oz.err, 0, sizeof(int), s));
+    oz_split_cols_kernel<TA><<<(unsigned)((oz.npad * oz.np + 7) / 8), 256, 0, s>>>(
+        n, oz.np, oz.kpt, A, lda, n, oz.npad, oz.DA, oz.EA, nullptr, 1);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
 // One CG group on caller-provided scratch (cg_scratch_bytes(n, nrhs, prod,
 // variant) bytes of device memory at `scratch`) and a host staging block
-// `hbuf` of at least 64 + 4*16*8 + 33*4 bytes (pinned or pageable).
+// `hbuf` of at least 64 + 4*16*8 + 34*4 bytes (pinned or pageable).
 template <typename TA>
 gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const double *B, int64_t ldb, double *X,
                    int64_t ldx, int nrhs, double rtol, int maxit, int R, cudaStream_t s, void *scratch, void *hbuf,
@@ -978,6 +1347,7 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
     GPCH_CUDA(ctx, cudaMemsetAsync(st.counter, 0, 2 * sizeof(unsigned), s));
     GPCH_CUDA(ctx, cudaMemsetAsync(b.ic, 0, (2 * MAXRHS + 1) * sizeof(int), s));
     if (prod == PROD_DF) GPCH_CHECK(df_prepare<TA>(ctx, n, nrhs, A, lda, B, ldb, b, s));
+    if (prod == PROD_OZ) GPCH_CHECK(oz_prepare<TA>(ctx, n, A, lda, b, s));
     const double rtol2 = rtol * rtol;
 
     if (variant == VAR_CLASSIC) {
@@ -1048,7 +1418,11 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
     int *h_ic = reinterpret_cast<int *>(static_cast<char *>(hbuf) + 64 + 4 * MAXRHS * sizeof(double));
     GPCH_CUDA(ctx, cudaMemcpyAsync(h_sc, b.sc, 4 * MAXRHS * sizeof(double), cudaMemcpyDeviceToHost, s));
     GPCH_CUDA(ctx, cudaMemcpyAsync(h_ic, b.ic, (2 * MAXRHS + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    int *h_ozerr = h_ic + 2 * MAXRHS + 1;
+    if (prod == PROD_OZ) GPCH_CUDA(ctx, cudaMemcpyAsync(h_ozerr, b.df.oz.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     GPCH_CUDA(ctx, cudaStreamSynchronize(s));
+    if (prod == PROD_OZ && *h_ozerr != 0)
+        return gpch::fail(ctx, GPCH_TIMEOUT, "tensor-core product wait gave up (%d)", *h_ozerr);
     for (int r = 0; r < nrhs; ++r) {
         h_iters[r] = h_ic[MAXRHS + r];
         const double u = h_sc[r], u0 = h_sc[MAXRHS + r];
@@ -1418,8 +1792,12 @@ extern "C" gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A,
     const int variant = opts ? opts->variant : GPCH_CG_CLASSIC;
     const int prod = opts ? opts->products : GPCH_CG_PRODUCTS_FP64;
     GPCH_ARG(ctx, variant == GPCH_CG_CLASSIC || variant == GPCH_CG_SINGLE_REDUCTION, "bad CG variant");
-    GPCH_ARG(ctx, prod == GPCH_CG_PRODUCTS_FP64 || prod == GPCH_CG_PRODUCTS_DOUBLE_FLOAT, "bad CG products");
+    GPCH_ARG(ctx,
+             prod == GPCH_CG_PRODUCTS_FP64 || prod == GPCH_CG_PRODUCTS_DOUBLE_FLOAT || prod == GPCH_CG_PRODUCTS_TENSOR,
+             "bad CG products");
     GPCH_ARG(ctx, n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
+    GPCH_ARG(ctx, prod != GPCH_CG_PRODUCTS_TENSOR || (n + 127) / 128 * 128 * ((n + 511) / 512 * 16) * 4 < (int64_t)0x7fffffff,
+             "n too large for the tensor-core path");
     GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldb >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1), "ld < n");
     GPCH_ARG(ctx, dtype == GPCH_F64 || dtype == GPCH_F32, "bad dtype");
     GPCH_ARG(ctx, maxit > 0 && replace_every >= 0 && rtol >= 0.0, "bad maxit / replace_every / rtol");
@@ -1427,7 +1805,7 @@ extern "C" gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A,
     GPCH_ARG(ctx, A && B && X, "null pointer");
     GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    const int pv = prod == GPCH_CG_PRODUCTS_DOUBLE_FLOAT ? PROD_DF : PROD_FP64;
+    const int pv = prod == GPCH_CG_PRODUCTS_DOUBLE_FLOAT ? PROD_DF : prod == GPCH_CG_PRODUCTS_TENSOR ? PROD_OZ : PROD_FP64;
     const int vv = variant == GPCH_CG_SINGLE_REDUCTION ? VAR_SINGLE_REDUCTION : VAR_CLASSIC;
     int max_it = 0, conv = 0;
     double rel_max = 0.0;

@@ -44,7 +44,7 @@ class CGOpts(ctypes.Structure):
 
 
 CG_CLASSIC, CG_SINGLE_REDUCTION = 0, 1
-CG_PRODUCTS_FP64, CG_PRODUCTS_DOUBLE_FLOAT = 0, 1
+CG_PRODUCTS_FP64, CG_PRODUCTS_DOUBLE_FLOAT, CG_PRODUCTS_TENSOR = 0, 1, 2
 
 
 class System(ctypes.Structure):
@@ -353,7 +353,7 @@ class CGResult:
 
 
 _CG_VARIANT = {"classic": CG_CLASSIC, "single_reduction": CG_SINGLE_REDUCTION}
-_CG_PRODUCTS = {"fp64": CG_PRODUCTS_FP64, "double_float": CG_PRODUCTS_DOUBLE_FLOAT}
+_CG_PRODUCTS = {"fp64": CG_PRODUCTS_FP64, "double_float": CG_PRODUCTS_DOUBLE_FLOAT, "tensor": CG_PRODUCTS_TENSOR}
 
 
 def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e-10, maxit: int = 10000,
@@ -362,7 +362,8 @@ def cg_solve(A: torch.Tensor, B: torch.Tensor, X: torch.Tensor, rtol: float = 1e
     """A6-A7: CG (Algorithm 1, left) on the full column-major A (float64 or
     float32), right-hand sides B and start/solution X (n x nrhs, float64).
     variant: "classic" or "single_reduction" (Chronopoulos-Gear); products:
-    "fp64" or "double_float" (FP32-pipe double-float products)."""
+    "fp64", "double_float" (FP32-pipe double-float products) or "tensor"
+    (FP64-accurate products on the tensor cores; A symmetric)."""
     ctx = ctx or default_context()
     if A.dtype not in (torch.float64, torch.float32):
         raise ValueError("A must be float64 or float32")

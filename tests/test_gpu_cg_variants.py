@@ -1,6 +1,7 @@
 """GPU parity of the CG options of gpch_cg_solve_ex against the oracle:
-the single-reduction (Chronopoulos-Gear) form of Algorithm 1 (left) and the
-double-float product arithmetic, on FP64- and FP32-stored matrices, one to
+the single-reduction (Chronopoulos-Gear) form of Algorithm 1 (left), the
+double-float product arithmetic and the FP64-accurate tensor-core products
+(8 digits per entry, 512-entry passes), on FP64- and FP32-stored matrices, one to
 16 right-hand sides, ragged and unaligned shapes, and the CG-bound system's
 shape (ell = 0.3, sn2 = 0.1, 16 right-hand sides) at n = 4096.
 
@@ -20,7 +21,7 @@ from gpu_helpers import ctx, dev, host  # noqa: F401
 pytestmark = pytest.mark.gpu
 
 FORMS = [("classic", "fp64"), ("single_reduction", "fp64"), ("classic", "double_float"),
-         ("single_reduction", "double_float")]
+         ("single_reduction", "double_float"), ("classic", "tensor"), ("single_reduction", "tensor")]
 
 
 def se_system(n, ell=0.5, sn2=1e-2, nrhs=1, seed=0):
