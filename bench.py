@@ -400,12 +400,14 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
             mst, rest, mvt = _cg_timed(ctx_t, AA, B3, X3, "classic", "tensor", 1e-10, 20000, 50)
             ctx_t.close()
             mst = max_over_ranks(mst)
+            digit_bytes = 16 * ((n3 + 127) // 128 * 128) * ((n3 + 511) // 512 * 512)
             c3[label]["tensor_products"] = {
                 "ms": round(mst, 1), "iterations": rest.iterations, "converged": rest.converged,
                 "ms_per_iteration": round(mst / max(rest.iterations, 1), 3),
                 "speedup_vs_double_float": round(ms / max(mst, 1e-9), 2),
-                "digit_bytes_per_iteration": 16 * ((n3 + 127) // 128 * 128) * ((n3 + 511) // 512 * 512),
+                "digit_bytes_per_product": digit_bytes,
                 "true_relres_max": _true_relres(AA, B3, X3)}
+            tensor_phase = mvt   # matvec phase: tensor-core products and the FP64 true residuals
             # FP64 products on the same operator: rate over a few iterations
             _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, 1, 0)
             ms64, res64, mv64 = _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, args.cg3_fp64_iters, 0)
@@ -414,6 +416,16 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                 "iterations": args.cg3_fp64_iters, "ms_per_iteration": round(ms64 / args.cg3_fp64_iters, 3),
                 "matvec_ms_mean": round(mv64_ms, 3),
                 "frac_of_fp64_fma_rate": round(n3 * n3 * 16 / (mv64_ms / 1e3) / (FP64_PEAK_GFLOPS * 1e9 / 2), 4)}
+            # the tensor-core product alone: the matvec phase less its FP64
+            # true residuals (the start and one per 50 iterations), each
+            # taken at the FP64 products' mean time
+            n_true = 1 + rest.iterations // 50
+            t_ms = (tensor_phase[0] - n_true * mv64_ms) / max(tensor_phase[1] - n_true, 1)
+            c3[label]["tensor_products"].update({
+                "matvec_ms_mean": round(t_ms, 3),
+                "digit_gbs": round(digit_bytes / (t_ms / 1e3) / 1e9, 1),
+                "digit_frac_of_hbm": round(digit_bytes / (t_ms / 1e3) / 1e9 / hbm, 4),
+                "fp64_matrix_equivalent_gbs": round(n3 * n3 * 8 / (t_ms / 1e3) / 1e9, 1)})
         c3["what"] = (f"n={n3} SE (ell=0.3, sn2=0.1), 16 RHS, classic CG with double-float products to relative "
                       "residual 1e-10 (replacement every 50 iterations, FP64 true residuals); FP32-stored A is the "
                       "FP32 rounding of the FP64 matrix; products_tera_per_s = n^2 * 16 / matvec time; "

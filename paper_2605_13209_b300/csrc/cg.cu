@@ -93,10 +93,11 @@ struct CGState {
 // last padded with zeros to npad rows), K stage kc (32 columns) and plane
 // b (digits 2b, 2b + 1), a block of 128 rows of 64 positions (128 bytes:
 // digit p of column k at (p % 2) 32 + k % 32); its exponents
-// EA[t * npad + j] (column j, pass t); the vectors' copy DS (4 planes of 16
-// rows, 2 kpt positions per row, digit p of k at oz_pos(p, k) of plane
-// p / 2) and exponents ES[t * 16 + r]; the status word of the bounded
-// waits.  np passes of 512, kpt = 512 np.
+// EA[t * npad + j] (column j, pass t); the vectors' copy DS, stacked for
+// one product per digit of A: for K stage kc, digit d and right-hand side
+// r, row (8 kc + d) 16 + r of 32 positions (64 bytes, column k at k % 32),
+// and exponents ES[t * 16 + r]; the status word of the bounded waits.  np
+// passes of 512, kpt = 512 np.
 struct OzArgs {
     __nv_bfloat16 *DA, *DS;
     int *EA, *ES;
@@ -613,13 +614,11 @@ __device__ __forceinline__ long long oz_fixed(TX x, int e)
 }
 
 // Digits of the columns of X (column c: its n entries, ld ldx) for the
-// tensor-core products: column c becomes row c of each of the 4 digit
-// planes (plane_rows rows each, row stride 2 kpt, digit p of entry k at
-// oz_pos(p, k) of plane p / 2; tiled: the tile-major layout of OzArgs::DA),
-// with exponent E[t * plane_rows + c] per pass t of 512 entries (the
-// smallest e with every |x| of the pass below 2^e; 0 for a zero pass).
-// Columns at or past ncols (and entries past n) are zero.  One warp per
-// (column, pass).
+// tensor-core products, in the layouts of OzArgs: tiled (A's copy, rows
+// 0 .. plane_rows-1) or stacked (the vectors', plane_rows = 16), with
+// exponent E[t * plane_rows + c] per pass t of 512 entries (the smallest e
+// with every |x| of the pass below 2^e; 0 for a zero pass).  Columns at or
+// past ncols (and entries past n) are zero.  One warp per (column, pass).
 template <typename TX>
 __global__ void __launch_bounds__(256) oz_split_cols_kernel(int64_t n, int np, int64_t kpt, const TX *__restrict__ X,
                                                             int64_t ldx, int64_t ncols, int64_t plane_rows,
@@ -654,7 +653,6 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(int64_t n, int np, i
         else frexpf((float)mx, &e);
     }
     if (lane == 0) E[(int64_t)t * plane_rows + c] = e;
-    const int64_t ld = 2 * kpt;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int64_t k = k0 + lane + 32 * i;
@@ -671,7 +669,7 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(int64_t n, int np, i
             }
             const int64_t at = tiled ? ((((c / 128) * (kpt / 32) + k / 32) * 4 + p / 2) * 128 + c % 128) * 64 +
                                            (p & 1) * 32 + k % 32
-                                     : (int64_t)(p / 2) * plane_rows * ld + c * ld + gpch::oz_pos(p, k);
+                                     : (((k / 32) * 8 + p) * plane_rows + c) * 32 + k % 32;
             D[at] = __float2bfloat16_rn((float)d);
         }
     }
@@ -681,25 +679,33 @@ __global__ void __launch_bounds__(256) oz_split_cols_kernel(int64_t n, int np, i
 // products (PROD_OZ): CTA b forms rows 128 b .. 128 b + 127 of A s for all
 // right-hand sides, then the mode's reductions as the other matvecs do.
 // tm_a: the digit copy of A^T (tile-major, rows of 64 positions, 128-row
-// boxes); tm_s:
-// the vectors' ((4 16) x (2 kpt), 16-row boxes).  Roles: warp 0 lane 0 TMA
-// (3 stages of 4 + 4 boxes over 32 K columns), warp 1 the TMEM (two sets
-// of 8 class accumulators of 16 columns, one set per pass, alternating) and
-// its lane 0 the MMAs (36 digit pairs x 2 K steps per stage), warps 4-7
-// the epilogue (warp w: rows 32 (w % 4) .., its TMEM lanes), which per pass
-// combines the class sums exactly, rounds once and adds in FP64.  Bounded
-// waits set *oz.err.
+// boxes, 128-byte swizzle); tm_s: the vectors' stacked copy (rows of 32
+// positions, 128-row boxes: 8 digits x 16 right-hand sides, 64-byte
+// swizzle).  Per 32 K columns and K step of 16, digit p of A (p = 0..6)
+// meets digits d = 0 .. 6 - p of all vectors in ONE MMA (M = 128,
+// N = 16 (7 - p)), whose columns hold the pair sums S_pd; the 28 pairs with
+// p + d <= 6 are kept (the weight classes above 6, at most 2^-44 of the
+// scales' product per term, are dropped).  Roles: warp 0 lane 0 TMA (3
+// stages of 4 A boxes and 1 vector box), warp 1 the TMEM (448 of 512
+// columns) and its lane 0 the MMAs (14 per stage), warps 4-7 the epilogue
+// (warp w: rows 32 (w % 4) .., its TMEM lanes), which per pass of 512
+// forms the 7 class sums (exact: at most 7 pair sums of magnitude 2^21),
+// combines them exactly, rounds once and adds in FP64.  Bounded waits set
+// *oz.err.
 constexpr int OZM_BM = 128;
 constexpr int OZM_N = MAXRHS;
 constexpr int OZM_KSTAGE = 32;
 constexpr int OZM_SPP = 512 / OZM_KSTAGE;    // stages per pass
 constexpr int OZM_STAGES = 3;
-constexpr uint32_t OZM_ABOX = OZM_BM * 128, OZM_SBOX = OZM_N * 128;
-constexpr uint32_t OZM_STAGE = 4 * (OZM_ABOX + OZM_SBOX);   // 72 KB
+constexpr int OZM_CLASSES = 7;               // weight classes D = p + d kept (0..6)
+constexpr uint32_t OZM_ABOX = OZM_BM * 128, OZM_SBOX = 8 * OZM_N * 64;
+constexpr uint32_t OZM_STAGE = 4 * OZM_ABOX + OZM_SBOX;   // 72 KB
 constexpr size_t OZM_SMEM = OZM_STAGES * OZM_STAGE + 1024 + 256;
-constexpr uint32_t OZM_TMEM = 256;
+constexpr uint32_t OZM_TMEM = 512;
 constexpr uint32_t OZM_SPIN = 1u << 26;
 static_assert((size_t)OZM_BM * OZM_N * sizeof(double) <= OZM_STAGES * OZM_STAGE, "tcol fits the stages");
+// first TMEM column of digit p's product: 16 sum_{p' < p} (7 - p')
+__host__ __device__ constexpr int ozm_base(int p) { return OZM_N * (7 * p - p * (p - 1) / 2); }
 
 __global__ void __launch_bounds__(THREADS, 1)
     oz_matvec_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_s, int64_t n,
@@ -712,8 +718,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + OZM_STAGES * OZM_STAGE);
     uint64_t *empty = full + OZM_STAGES;
     uint64_t *tfull = empty + OZM_STAGES;
-    uint64_t *tempty = tfull + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    uint64_t *tempty = tfull + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i0 = (int64_t)blockIdx.x * OZM_BM;
     const int np = oz.np;
@@ -722,10 +728,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             gpch::tc::mbar_init(&full[s], 1);
             gpch::tc::mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
-            gpch::tc::mbar_init(&tfull[a], 1);
-            gpch::tc::mbar_init(&tempty[a], 4);
-        }
+        gpch::tc::mbar_init(tfull, 1);
+        gpch::tc::mbar_init(tempty, 4);
         gpch::tc::fence_mbar_init();
     }
     if (warp == 1) gpch::tc::tmem_alloc<OZM_TMEM>(tmem_slot);
@@ -751,13 +755,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 uint8_t *stg = smem + s * OZM_STAGE;
                 gpch::tc::mbar_arrive_expect_tx(&full[s], OZM_STAGE);
-                const int32_t x = (int32_t)(kc * 2 * OZM_KSTAGE);   // bf16 positions
-                for (int b = 0; b < 4; ++b) {
+                for (int b = 0; b < 4; ++b)
                     gpch::tc::tma_load_2d(stg + b * OZM_ABOX, &tm_a, &full[s], 0,
                                           (int32_t)((((int64_t)blockIdx.x * NK + kc) * 4 + b) * OZM_BM));
-                    gpch::tc::tma_load_2d(stg + 4 * OZM_ABOX + b * OZM_SBOX, &tm_s, &full[s], x,
-                                          (int32_t)(b * OZM_N));
-                }
+                gpch::tc::tma_load_2d(stg + 4 * OZM_ABOX, &tm_s, &full[s], 0, (int32_t)(kc * 8 * OZM_N));
                 ++issued;
             }
             // every copy this thread started has landed before the CTA exits
@@ -768,18 +769,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = gpch::tc::idesc_bf16_f32(OZM_BM, OZM_N);
             bool ok = true;
             int kc = 0;
             for (int t = 0; t < np && ok; ++t) {
-                // the set of pass t (t % 2) must have been read out for pass t - 2
-                const int set = t & 1, use = t >> 1;
-                if (use >= 1 && !gpch::tc::mbar_wait(&tempty[set], (use - 1) & 1, 4 * OZM_SPIN)) {
+                // the accumulators must have been read out for pass t - 1
+                if (t >= 1 && !gpch::tc::mbar_wait(tempty, (t - 1) & 1, 4 * OZM_SPIN)) {
                     atomicExch(oz.err, 2);
                     break;
                 }
                 gpch::tc::tc_fence_after();
-                const uint32_t accs = tmem + (uint32_t)(set * 8 * OZM_N);
                 for (int q = 0; q < OZM_SPP; ++q, ++kc) {
                     const int s = kc % OZM_STAGES;
                     if (!gpch::tc::mbar_wait(&full[s], (kc / OZM_STAGES) & 1, OZM_SPIN)) {
@@ -789,23 +787,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     gpch::tc::tc_fence_after();
                     const uint32_t sa = gpch::tc::smem_u32(smem + s * OZM_STAGE);
-                    const uint32_t sb = sa + 4 * OZM_ABOX;
+                    const uint64_t b = gpch::tc::sdesc_sw64(sa + 4 * OZM_ABOX);
 #pragma unroll
-                    for (int p = 0; p < 8; ++p) {
-                        const uint64_t a = gpch::tc::sdesc_sw128(sa + (p / 2) * OZM_ABOX) + 4 * (p & 1);
+                    for (int k = 0; k < 2; ++k) {
 #pragma unroll
-                        for (int d = 0; d + p < 8; ++d) {
-                            const uint64_t b = gpch::tc::sdesc_sw128(sb + (d / 2) * OZM_SBOX) + 4 * (d & 1);
-                            const uint32_t acc = accs + (uint32_t)((p + d) * OZM_N);
-                            // the first product into a class (p = 0 starts every class) of the pass overwrites it
-#pragma unroll
-                            for (int k = 0; k < 2; ++k)
-                                gpch::tc::mma_bf16(acc, a + 2 * k, b + 2 * k, idesc, (q > 0 || k > 0 || p > 0) ? 1u : 0u);
+                        for (int p = 0; p < OZM_CLASSES; ++p) {
+                            const uint64_t a = gpch::tc::sdesc_sw128(sa + (p / 2) * OZM_ABOX) + 4 * (p & 1);
+                            const uint32_t idesc = gpch::tc::idesc_bf16_f32(OZM_BM, OZM_N * (7 - p));
+                            // the pass's first K step overwrites the accumulators
+                            gpch::tc::mma_bf16(tmem + (uint32_t)ozm_base(p), a + 2 * k, b + 2 * k, idesc,
+                                               (q > 0 || k > 0) ? 1u : 0u);
                         }
                     }
                     gpch::tc::mma_commit(&empty[s]);
                 }
-                if (ok) gpch::tc::mma_commit(&tfull[set]);
+                if (ok) gpch::tc::mma_commit(tfull);
             }
         }
         __syncwarp();
@@ -815,32 +811,64 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool row_ok = row < n;
         const uint32_t tl = tmem + ((uint32_t)(qw * 32) << 16);
         for (int t = 0; t < np; ++t) {
-            const int set = t & 1, use = t >> 1;
-            bool ok = gpch::tc::mbar_wait(&tfull[set], use & 1, 4 * OZM_SPIN);
+            bool ok = gpch::tc::mbar_wait(tfull, t & 1, 4 * OZM_SPIN);
             ok = __all_sync(0xffffffffu, ok);
             gpch::tc::tc_fence_after();
             if (!ok) {
                 if (lane == 0) atomicExch(oz.err, 3);
                 break;
             }
-            uint32_t vr[8][16];
+            // class sums S_D = sum_{p + d = D} S_pd (exact in FP32: at most
+            // 7 integers of magnitude 2^21), four pair blocks per TMEM wait
+            float cs[OZM_CLASSES][OZM_N];
 #pragma unroll
-            for (int D = 0; D < 8; ++D) gpch::tc::tmem_ld16_nowait(tl + (uint32_t)(set * 8 * OZM_N + D * OZM_N), vr[D]);
-            gpch::tc::tmem_ld_wait();
-            // the set is read: the MMAs of pass t + 2 may use it
+            for (int D = 0; D < OZM_CLASSES; ++D)
+#pragma unroll
+                for (int j = 0; j < OZM_N; ++j) cs[D][j] = 0.0f;
+#pragma unroll
+            for (int g = 0; g < 28; g += 4) {
+                uint32_t v[4][16];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    // pair number g + u in the order p = 0 (d = 0..6), p = 1 (d = 0..5), ...
+                    int p = 0, d = g + u;
+#pragma unroll
+                    for (int pp = 0; pp < OZM_CLASSES; ++pp)
+                        if (d >= 7 - p) {
+                            d -= 7 - p;
+                            ++p;
+                        }
+                    gpch::tc::tmem_ld16_nowait(tl + (uint32_t)(ozm_base(p) + d * OZM_N), v[u]);
+                }
+                gpch::tc::tmem_ld_wait();
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    int p = 0, d = g + u;
+#pragma unroll
+                    for (int pp = 0; pp < OZM_CLASSES; ++pp)
+                        if (d >= 7 - p) {
+                            d -= 7 - p;
+                            ++p;
+                        }
+#pragma unroll
+                    for (int j = 0; j < OZM_N; ++j) cs[p + d][j] += __uint_as_float(v[u][j]);
+                }
+            }
+            // the accumulators are read: the MMAs of pass t + 1 may start
             gpch::tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) gpch::tc::mbar_arrive(&tempty[set]);
+            if (lane == 0) gpch::tc::mbar_arrive(tempty);
             const int er = row_ok ? oz.EA[(int64_t)t * oz.npad + row] : 0;
 #pragma unroll
             for (int j = 0; j < OZM_N; ++j) {
-                // exact class sums (integers of magnitude <= 2^24)
+                // T = sum_D S_D 128^(6 - D) = H 2^28 + L exactly; the
+                // product is 2^(e_r + f_j - 52) T
                 long long H = 0, L = 0;
 #pragma unroll
-                for (int D = 0; D < 4; ++D) H = H * 128 + __float2int_rn(__uint_as_float(vr[D][j]));
+                for (int D = 0; D < 3; ++D) H = H * 128 + __float2int_rn(cs[D][j]);
 #pragma unroll
-                for (int D = 4; D < 8; ++D) L = L * 128 + __float2int_rn(__uint_as_float(vr[D][j]));
-                acc64[j] += gpch::oz_round_scaled(H, L, er + __ldg(&oz.ES[t * OZM_N + j]) - 59);
+                for (int D = 3; D < 7; ++D) L = L * 128 + __float2int_rn(cs[D][j]);
+                acc64[j] += gpch::oz_round_scaled(H, L, er + __ldg(&oz.ES[t * OZM_N + j]) - 52);
             }
         }
     }
@@ -1160,7 +1188,7 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
         GPCH_LAUNCH_CHECK(ctx);
         CUtensorMap ma, ms;
         GPCH_CHECK(gpch::oz_map(ctx, &ma, oz.DA, oz.npad * (oz.kpt / OZM_KSTAGE) * 4, 64, OZM_BM));
-        GPCH_CHECK(gpch::oz_map(ctx, &ms, oz.DS, 4 * OZM_N, 2 * oz.kpt, OZM_N));
+        GPCH_CHECK(gpch::oz_map(ctx, &ms, oz.DS, (oz.kpt / OZM_KSTAGE) * 8 * OZM_N, 32, 8 * OZM_N, true));
         static gpch::DeviceOnce attr_once;
         GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
             GPCH_CUDA(ctx, cudaFuncSetAttribute(oz_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -57,18 +57,20 @@ __device__ __forceinline__ double oz_round_scaled(long long H, long long L, int 
 
 
 // Tensor map over a digit copy: `rows` rows of `width` bf16 positions,
-// boxes of 64 positions (128 bytes, 128-byte swizzle) by box_rows rows.
-inline gpch_status oz_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t rows, int64_t width, uint32_t box_rows)
+// boxes of 64 positions (128 bytes, 128-byte swizzle) by box_rows rows, or
+// with narrow, of 32 positions (64 bytes, 64-byte swizzle).
+inline gpch_status oz_map(gpch_ctx *ctx, CUtensorMap *map, const void *base, int64_t rows, int64_t width,
+                          uint32_t box_rows, bool narrow = false)
 {
     auto enc = gpch::tc::tmap_encoder();
     if (!enc) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled not available");
     cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)width * 2};
-    cuuint32_t box[2] = {64u, box_rows};
+    cuuint32_t box[2] = {narrow ? 32u : 64u, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, narrow ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return gpch::fail(ctx, GPCH_CUDA_ERROR, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return GPCH_OK;
 }

@@ -244,6 +244,21 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr)
     return d;
 }
 
+// The same for a tile written with 64-byte swizzling: rows of 32 bf16
+// (64 B), 8-row atoms of 512 B (stride-dimension offset 512 B), layout
+// code 4.  The tile base must be 512-byte aligned; a K step of 16 elements
+// adds 32 bytes to the start address.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t smem_addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: bf16 A and B (both K-major), fp32 D,
 // shape M x N.  bits 4-5 D format (1 = f32), 7-9 A format (1 = bf16),
 // 10-12 B format (1 = bf16), 15/16 A/B major (0 = K), 17-22 N >> 3,
