@@ -430,7 +430,7 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                       "residual 1e-10 (replacement every 50 iterations, FP64 true residuals); FP32-stored A is the "
                       "FP32 rounding of the FP64 matrix; products_tera_per_s = n^2 * 16 / matvec time; "
                       "tensor_products: the same solve with FP64-accurate tensor-core products (8 base-128 digits "
-                      "per entry, 36 digit pairs, exact per 512-entry pass), A's digits made once per solve")
+                      "per entry, 28 digit pairs of weight class <= 6, exact per 512-entry pass), A's digits made once per solve")
         out["config3"] = c3
         del A64, A32, B3, X3
     return out
@@ -622,7 +622,7 @@ def main():
             "speedup_vs_fp64": round(fms / ems, 2),
             "update_ms": round(tr[0], 2), "update_tflops_fp64_equiv": round(tr[2] / (tr[0] / 1e3) / 1e12, 2),
             "what": "the same factor + solve with step 3 as FP64-accurate products on the bf16 tensor cores "
-                    "(8 base-128 digits per entry, 36 digit pairs, exact class sums)"}
+                    "(8 base-128 digits per entry, 28 digit pairs, exact class sums)"}
         del Aw
 
     # ---------------------------------------------------------- CG legs

@@ -278,10 +278,12 @@ typedef struct gpch_cg_opts {
  * by an error-free splitting (as gpch_gemm_fp64_emulated): A is cut once
  * per solve (and per group of 16 right-hand sides) into 8 base-128 digits
  * per entry with a power-of-two scale per column of A and 512-entry pass,
- * each vector once per product likewise; the 36 kept digit pairs are
- * summed exactly per pass and rounded once, passes added in FP64.  Per
- * entry of A s the error is at most about n 2^-48 max_j |A_ij| max |s|
- * (per pass: 512 2^-48 times the pass's largest |A_ij| and |s_j|).  A must
+ * each vector once per product likewise; the 28 digit pairs of weight
+ * class p + d <= 6 are summed exactly per pass and rounded once, passes
+ * added in FP64.  The dropped pairs weigh at most 2^-44 of the two pass
+ * scales per term (each scale is the power of two just above the pass's
+ * largest magnitude), so per entry of A s the error is at most about
+ * n 2^-42 max_j |A_ij| max |s|.  A must
  * be symmetric (its columns serve as rows).  Extra workspace: 16 np kp
  * bytes for A's digits (np = n rounded up to 128, kp = n rounded up to
  * 512) plus 4 np kp / 512 bytes of exponents.  True residuals keep FP64

@@ -59,11 +59,15 @@
 //              is cut once per solve into 8 base-128 digits per entry with
 //              one power-of-two scale per column and 512-row pass, the
 //              vectors every matvec likewise per right-hand side; a CTA
-//              forms 128 entries of A s for all right-hand sides (an
-//              M = 128, N = 16 tensor-core tile), the 36 kept digit pairs
-//              summed exactly in 8 FP32 class accumulators per pass and
-//              combined and rounded once per pass, passes added in FP64.
-//              The digit copy takes 16 bytes per entry of A.  True
+//              forms 128 entries of A s for all right-hand sides.  The
+//              vectors' digits are stacked along N, so that one MMA takes
+//              digit p of A against every kept digit d <= 6 - p of all 16
+//              right-hand sides (N = 16 (7 - p)); the 28 kept digit pairs
+//              are summed exactly in FP32 per pass, gathered into 7 weight
+//              classes p + d in the epilogue, combined and rounded once per
+//              pass, and the passes added in FP64.  The dropped classes
+//              (p + d >= 7) weigh at most 2^-44 of the pass's scales per
+//              term.  The digit copy takes 16 bytes per entry of A.  True
 //              residuals keep FP64 products.
 
 #include <cuda_bf16.h>
