@@ -607,18 +607,21 @@ typedef struct gpch_refine_stats {
  * each breakdown, u = 2^-8, 2^-16, 2^-22 for BF16, SPLIT_BF16, SPLIT_F16; at
  * most 9 attempts), then preconditioned CG with M = Lt Lt^T in FP64 (A, x,
  * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
- * from x_0 = 0 (the iteration's products A s formed as double-float
- * products, as gpch_cg_solve_ex's GPCH_CG_PRODUCTS_DOUBLE_FLOAT; every true
- * residual b - A x in FP64), replacing the recurrence residual by b - A x every 50
+ * from x_0 = 0 (the products A s and the true residuals b - A x formed as
+ * double-float products: with one or two right-hand sides per group of 16
+ * as gpch_symv_lower, from A's lower triangle, else the iteration's
+ * products as gpch_cg_solve_ex's GPCH_CG_PRODUCTS_DOUBLE_FLOAT over all of
+ * A and the true residuals in FP64), replacing the recurrence residual by b - A x every 50
  * iterations and whenever an estimate of the backward error from the
  * recurrence residual (its ||r||_inf in place of the true residual's,
  * scaled by the truth-to-estimate ratio seen at the previous check)
  * reaches bwd_tol.
- * A: device FP64 full symmetric n x n (lda); the factor and ||A||_inf read
- * its lower triangle, the residual b - A x all of it.  B: device n x nrhs
+ * A: device FP64 symmetric n x n (lda); the factor, ||A||_inf and, with
+ * at most two right-hand sides, the products read its lower triangle only
+ * (with more, the products read all of it).  B: device n x nrhs
  * (ldb).  X: device n x nrhs (ldx), overwritten.  Workspace (context
  * arena): about 8 n^2 bytes, the FP32 factor and the 16-bit copies of its
- * panels.
+ * panels (plus gpch_symv_lower's partial sums).
  * tile: the factor's block size, a multiple of 64 in [64, 1024], or 0 for
  * the autotuned tile of n's size bucket (gpch_autotune; defaults 256 for
  * n <= 4096, else 512, until the device is tuned).
@@ -628,6 +631,29 @@ typedef struct gpch_refine_stats {
 gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *B,
                                int64_t ldb, double *X, int64_t ldx, int nrhs, gpch_prec prec, int tile,
                                double bwd_tol, int maxit, void *stream, gpch_refine_stats *stats);
+
+/* Y = A X for a symmetric A of which only the lower triangle (i >= j)
+ * affects the result: the product of the refined solve's CG iteration
+ * (Algorithm 1 (left), its A s and its true residuals b - A x).  Each
+ * stored entry serves twice, A_ij x_j in y_i and A_ij x_i in y_j, so the
+ * product reads about half of A's bytes.  The products are double-float
+ * products on the FP32 pipe (as gpch_cg_solve_ex's
+ * GPCH_CG_PRODUCTS_DOUBLE_FLOAT): each carries a relative error below about
+ * 2^-44, summed without further loss in double-float and added in FP64 in
+ * a fixed order, so y_i is within about 2^-44 sum_j |A_ij| |x_j| of the
+ * exact product and the result does not depend on scheduling.  Power-of-two
+ * scales come from A's largest diagonal entry and each column's largest
+ * |x|: entries of A at or above 2^127 times the largest diagonal entry make
+ * the product non-finite, entries below 2^-126 times it count as zero.
+ * A: device FP64, n x n column-major (lda); entries above the diagonal may
+ * be read but never change the result.  X: device n x nrhs (ldx).  Y:
+ * device n x nrhs (ldy), overwritten; it must not overlap X.  Work space
+ * from the context arena: about (n / 512 + n / 256) n 16 bytes.  Enqueued
+ * on `stream` (no synchronization); the context's arena is in use until it
+ * completes.  Errors: INVALID_ARG (n >= 2^24, ld < n, null pointers),
+ * OUT_OF_MEMORY, CUDA_ERROR. */
+gpch_status gpch_symv_lower(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *X, int64_t ldx,
+                            double *Y, int64_t ldy, int nrhs, void *stream);
 
 /* ------------------------------ GP quantities on a solved system (f3) */
 

@@ -1172,6 +1172,302 @@ void launch_mv_kernel(int64_t n, int64_t ncols, int nrhs, const TA *A, int64_t l
 #undef GPCH_MVT
 }
 
+// ------------------------------- symmetric matvec from the lower triangle
+//
+// T = A S for a symmetric A of which only the lower triangle (i >= j)
+// affects the result, with double-float products as cg_matvec_kernel's DF
+// path: every stored entry serves twice, A_ij s_i in t_j (down column j)
+// and, for i > j, A_ij s_j in t_i, so the product reads about half of A's
+// bytes.  The work is cut into units of one strip of SY_SW columns (J) by
+// one chunk of SY_R rows (c), from the strip's diagonal block down: rows
+// r0 = J SY_SW + c SY_R ..  In a unit, warp w takes the strip's columns
+// 32 w .. 32 w + 31, SY_CG at a time, and walks the chunk in 64-row
+// segments; each segment's SY_CG x 64 block is copied into the warp's
+// shared memory by cp.async (lane l: rows 2l, 2l + 1 of each column, 16
+// bytes), SY_ST segments in flight, so the loads of later segments overlap
+// the arithmetic on the current one.  Lane l works on rows 2l, 2l + 1.  The
+// column sums of a group stay in registers over the chunk and are reduced
+// over the warp at its end; the row sums of a segment are added into the
+// warp's slice of shared memory and summed over the warps in warp order
+// once per unit.  The partials, scaled back and widened to FP64, go to dotp
+// (column j, chunk c: dotp[(c n + j) NR + r]) and axp (row i, strip J:
+// axp[(J n + i) NR + r]); sym_mv_finish_kernel adds them in a fixed order.
+//
+// The source of the entries (SRC):
+//   SY_FP64   A itself; each entry is cut into its float head and tail
+//             (df_split_a, integer operations);
+//   SY_WRITE  as SY_FP64, and the heads and tails are also stored in the
+//             packed copy AP, so that later products with the same A
+//             skip the cutting;
+//   SY_PACKED the packed copy: strip J holds columns J SY_SW .. + SY_SW - 1,
+//             rows J SY_SW .. n2 - 1 (n2 = n rounded up to even), column
+//             major with ld n2 - J SY_SW, from float2 offset
+//             sy_off(n, J); entries above the diagonal and rows at or past
+//             n are zero.
+// In the diagonal chunk the entries above the diagonal are replaced by
+// zeros before they are used (from A they may be read, never used).
+constexpr int SY_SW = THREADS;   // columns per strip: one finishing CTA per strip
+constexpr int SY_R = 256;        // rows per chunk
+constexpr int SY_CG = 4;         // columns a warp takes at a time
+constexpr int SY_ST = 3;         // segments in flight per warp
+enum SySrc : int { SY_FP64 = 0, SY_WRITE = 1, SY_PACKED = 2 };
+template <bool B> struct SyTag { static constexpr bool value = B; };
+static_assert(SY_R % 64 == 0 && SY_R >= SY_SW && SY_SW == (THREADS / 32) * 32, "unit shape");
+
+inline int64_t sy_chunks(int64_t n) { return (n + SY_R - 1) / SY_R; }
+inline int64_t sy_strips(int64_t n) { return (n + SY_SW - 1) / SY_SW; }
+inline size_t sy_smem(int nr)
+{
+    return (size_t)(THREADS / 32) * (SY_ST * SY_CG * 64 * sizeof(double) + SY_R * nr * sizeof(float2));
+}
+// doubles of the two partial arrays
+inline size_t sy_part_doubles(int64_t n, int nr) { return (size_t)(sy_chunks(n) + sy_strips(n)) * n * nr; }
+// float2 offset of strip J in the packed copy (strip J' has SY_SW columns
+// of n2 - J' SY_SW entries); sy_off(n, sy_strips(n)) is its size
+__host__ __device__ inline int64_t sy_off(int64_t n, int64_t J)
+{
+    const int64_t n2 = (n + 1) & ~int64_t(1);
+    return (int64_t)SY_SW * (J * n2 - (int64_t)(SY_SW / 2) * J * (J - 1));
+}
+
+__device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, bool ok)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8_zfill(void *dst, const void *src, bool ok)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+
+template <int NR, int SRC>
+__global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
+                                                               float2 *AP, DFArgs df, double *__restrict__ dotp,
+                                                               double *__restrict__ axp, const int *done, int vec)
+{
+    extern __shared__ __align__(16) double sy_smem_raw[];
+    if (done && *done) return;
+    const int64_t J = blockIdx.y, c = blockIdx.x;
+    const int64_t cs = J * SY_SW;   // the strip's first column
+    const int64_t r0 = cs + c * SY_R;
+    if (r0 >= n) return;
+    const int rows = (int)((n - r0 < SY_R) ? n - r0 : SY_R);
+    const int nseg = (rows + 63) / 64;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool dg = c == 0;   // the chunk holds the strip's diagonal block
+    const int64_t n2 = (n + 1) & ~int64_t(1), ldp = n2 - cs;   // the packed strip's column length
+    float2 *APs = (SRC != SY_FP64) ? AP + sy_off(n, J) : nullptr;
+    const unsigned ebias = (SRC != SY_PACKED) ? (unsigned)*df.ebias : 0u;
+    // the warp's segment buffers [stage][column][64 rows] (16 bytes per
+    // lane and column: two doubles, or two head-tail pairs), then every
+    // warp's row sums
+    double *buf = sy_smem_raw + (size_t)warp * SY_ST * SY_CG * 64;
+    float2 *axs = reinterpret_cast<float2 *>(sy_smem_raw + (size_t)(THREADS / 32) * SY_ST * SY_CG * 64);
+    float2 *ax = axs + (size_t)warp * SY_R * NR;
+    for (int e = lane; e < SY_R * NR; e += 32) ax[e] = make_float2(0.0f, 0.0f);
+    for (int g = 0; g < 32 / SY_CG; ++g) {
+        const int64_t j0 = cs + warp * 32 + g * SY_CG;   // the group's first column
+        if (j0 >= n) break;
+        float ch[SY_CG][NR], cl[SY_CG][NR], dh[SY_CG][NR], dl[SY_CG][NR];
+#pragma unroll
+        for (int q = 0; q < SY_CG; ++q)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 v = (j0 + q < n) ? df.SS[(j0 + q) * NR + r] : make_float2(0.0f, 0.0f);
+                ch[q][r] = v.x;
+                cl[q][r] = v.y;
+                dh[q][r] = dl[q][r] = 0.0f;
+            }
+        // the group's columns: in A, or in the packed strip
+        const double *acol[SY_CG];
+        float2 *pcol[SY_CG];
+#pragma unroll
+        for (int q = 0; q < SY_CG; ++q) {
+            const int64_t jq = (j0 + q < n) ? j0 + q : j0;
+            acol[q] = A + jq * lda;
+            pcol[q] = (SRC != SY_FP64) ? APs + (jq - cs) * ldp - cs : nullptr;   // indexed by the row i
+        }
+        // in the diagonal chunk, segments wholly above the group's first column are skipped
+        const int s0 = dg ? (int)((j0 - r0) / 64) : 0;
+        // segment sg into stage sg % SY_ST: this lane's rows of the SY_CG columns
+        auto stage = [&](int sg) {
+            double *b = buf + (sg % SY_ST) * SY_CG * 64;
+            const int64_t i = r0 + sg * 64 + 2 * lane;
+#pragma unroll
+            for (int q = 0; q < SY_CG; ++q) {
+                const bool colok = j0 + q < n;
+                if constexpr (SRC == SY_PACKED) {
+                    cp_async16_zfill(b + q * 64 + 2 * lane, (i < n2 && colok) ? (const void *)(pcol[q] + i) : A,
+                                     i < n2 && colok);
+                } else if (vec) {
+                    cp_async16_zfill(b + q * 64 + 2 * lane, (i + 1 < n) ? acol[q] + i : A, i + 1 < n);
+                } else {
+                    cp_async8_zfill(b + q * 64 + 2 * lane, (i < n) ? acol[q] + i : A, i < n);
+                    cp_async8_zfill(b + q * 64 + 2 * lane + 1, (i + 1 < n) ? acol[q] + i + 1 : A, i + 1 < n);
+                }
+            }
+        };
+        __syncwarp();   // the previous group's reads of the stages are done
+        for (int k = 0; k < SY_ST - 1; ++k) {
+            if (s0 + k < nseg) stage(s0 + k);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        for (int sg = s0; sg < nseg; ++sg) {
+            if (sg + SY_ST - 1 < nseg) stage(sg + SY_ST - 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(SY_ST - 1) : "memory");
+            double *b = buf + (sg % SY_ST) * SY_CG * 64;
+            const int rl = sg * 64 + 2 * lane;   // the lane's first row, chunk-local
+            const int64_t i = r0 + rl;
+            if (SRC != SY_PACKED && vec && i + 1 == n) {
+                // n odd: the last row alone (the 16-byte copy was skipped)
+#pragma unroll
+                for (int q = 0; q < SY_CG; ++q) b[q * 64 + 2 * lane] = acol[q][i];
+            }
+            float rh[2][NR], rt[2][NR], uh[2][NR], ul[2][NR];
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float2 v = (i + p < n) ? df.SS[(i + p) * NR + r] : make_float2(0.0f, 0.0f);
+                    rh[p][r] = v.x;
+                    rt[p][r] = v.y;
+                    uh[p][r] = ul[p][r] = 0.0f;
+                }
+            // masks only where the segment meets the diagonal or the edges
+            auto products = [&](auto tag) {
+                constexpr bool MASKED = decltype(tag)::value;
+#pragma unroll
+                for (int q = 0; q < SY_CG; ++q) {
+                    float hv[2], tv[2];
+                    if constexpr (SRC == SY_PACKED) {
+                        const float4 v = *reinterpret_cast<const float4 *>(b + q * 64 + 2 * lane);
+                        hv[0] = v.x;
+                        tv[0] = v.y;
+                        hv[1] = v.z;
+                        tv[1] = v.w;
+                    } else {
+                        const double2 av = *reinterpret_cast<const double2 *>(b + q * 64 + 2 * lane);
+                        df_split_a(av.x, ebias, hv[0], tv[0]);
+                        df_split_a(av.y, ebias, hv[1], tv[1]);
+                    }
+                    float hd[2], td[2], hx[2], tx[2];
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        hd[p] = hx[p] = hv[p];
+                        td[p] = tx[p] = tv[p];
+                        if constexpr (MASKED) {
+                            const int64_t ii = i + p, jj = j0 + q;
+                            const bool in = ii < n && jj < n;
+                            const bool okd = in && (!dg || ii >= jj), okx = in && (!dg || ii > jj);
+                            hx[p] = okx ? hv[p] : 0.0f;
+                            tx[p] = okx ? tv[p] : 0.0f;
+                            hd[p] = okd ? hv[p] : 0.0f;
+                            td[p] = okd ? tv[p] : 0.0f;
+                        }
+                    }
+                    if constexpr (SRC == SY_WRITE) {
+                        // the masked heads and tails: zero above the diagonal and past n
+                        if (i < n2 && j0 + q < n)
+                            *reinterpret_cast<float4 *>(pcol[q] + i) = make_float4(hd[0], td[0], hd[1], td[1]);
+                    }
+#pragma unroll
+                    for (int p = 0; p < 2; ++p)
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            // t_j += A_ij s_i
+                            const float pd = hd[p] * rh[p][r];
+                            float ed = fmaf(hd[p], rh[p][r], -pd);
+                            ed = fmaf(hd[p], rt[p][r], ed);
+                            ed = fmaf(td[p], rh[p][r], ed);
+                            df_add(dh[q][r], dl[q][r], pd, ed);
+                            // t_i += A_ij s_j
+                            const float px = hx[p] * ch[q][r];
+                            float ex = fmaf(hx[p], ch[q][r], -px);
+                            ex = fmaf(hx[p], cl[q][r], ex);
+                            ex = fmaf(tx[p], ch[q][r], ex);
+                            df_add(uh[p][r], ul[p][r], px, ex);
+                        }
+                }
+            };
+            const bool clean = !(dg && r0 + sg * 64 < j0 + SY_CG) && r0 + sg * 64 + 64 <= n && j0 + SY_CG <= n;
+            if (clean) products(SyTag<false>{});
+            else products(SyTag<true>{});
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    float2 v = ax[(rl + p) * NR + r];
+                    df_add2(v.x, v.y, uh[p][r], ul[p][r]);
+                    ax[(rl + p) * NR + r] = v;
+                }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        // the group's column sums over the warp
+#pragma unroll
+        for (int q = 0; q < SY_CG; ++q)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                float h = dh[q][r], l = dl[q][r];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    df_add2(h, l, __shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off));
+                if (lane == 0 && j0 + q < n) dotp[(c * n + j0 + q) * NR + r] = ((double)h + (double)l) * df.scale[r];
+            }
+    }
+    __syncthreads();
+    // the row sums over the warps, in warp order
+    for (int e = tid; e < rows * NR; e += THREADS) {
+        float h = axs[e].x, l = axs[e].y;
+        for (int w = 1; w < THREADS / 32; ++w)
+            df_add2(h, l, axs[(size_t)w * SY_R * NR + e].x, axs[(size_t)w * SY_R * NR + e].y);
+        const int r = e % NR;
+        axp[(J * n + r0 + e / NR) * NR + r] = ((double)h + (double)l) * df.scale[r];
+    }
+}
+
+// t_i for the rows of strip blockIdx.x: the chunks' column sums of column
+// i and the strips' row sums of row i, in eight interleaved sums (index mod
+// 8) added in a fixed order; then the mode's reductions as the other
+// matvecs (mv_finish).
+template <int NR>
+__global__ void __launch_bounds__(THREADS) sym_mv_finish_kernel(int64_t n, int nrhs, const double *__restrict__ dotp,
+                                                                const double *__restrict__ axp,
+                                                                const double *__restrict__ S, int64_t lds, double *T,
+                                                                int64_t ldt, CGState st, int mode, SRArgs sr)
+{
+    __shared__ double tcol[SY_SW * NR];
+    if (*st.done) return;
+    const int64_t J = blockIdx.x, i0 = J * SY_SW;
+    const int wcols = (int)((n - i0 < SY_SW) ? n - i0 : SY_SW);
+    const int tid = threadIdx.x;
+    if (tid < wcols) {
+        const int64_t i = i0 + tid, nch = (n - i0 + SY_R - 1) / SY_R;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            // eight interleaved sums (independent loads in flight), added in a fixed order
+            double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            int64_t c = 0;
+            for (; c + 8 <= nch; c += 8)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] += dotp[((c + u) * n + i) * NR + r];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c + u < nch) v[u] += dotp[((c + u) * n + i) * NR + r];
+            int64_t K = 0;
+            for (; K + 8 <= J + 1; K += 8)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] += axp[((K + u) * n + i) * NR + r];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (K + u <= J) v[u] += axp[((K + u) * n + i) * NR + r];
+            tcol[tid * NR + r] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        }
+    }
+    mv_finish<SY_SW, NR>(i0, wcols, nrhs, S, lds, T, ldt, st, mode, sr, tcol);
+}
+
 // One matvec T = A S (plus the mode's reductions).  With PROD_DF the vector
 // S is split into df.SS first (one small launch).
 template <typename TA>
@@ -1226,6 +1522,64 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
         launch_mv_kernel<TA, true>(n, ncols, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
     else
         launch_mv_kernel<TA, false>(n, ncols, nrhs, A, lda, S, lds, T, ldt, st, mode, sr, df, vec, s);
+    GPCH_LAUNCH_CHECK(ctx);
+    return GPCH_OK;
+}
+
+// T = A S (nrhs <= 2) from A's lower triangle with double-float products
+// (sym_mv_df_kernel), plus the mode's reductions; S is split into df.SS
+// first.  src: SY_FP64 (AP unused), SY_WRITE (also fills the packed copy
+// AP, sy_off(n, sy_strips(n)) float2) or SY_PACKED (reads AP, made by an
+// SY_WRITE product of the same A with the same df scales).  part:
+// sy_part_doubles(n, mv_nr(nrhs)) doubles of scratch.
+gpch_status launch_symv_df(gpch_ctx *ctx, int64_t n, int nrhs, const double *A, int64_t lda, const double *S,
+                           int64_t lds, double *T, int64_t ldt, const CGState &st, int mode, cudaStream_t s,
+                           const DFArgs &df, double *part, float2 *AP = nullptr, int src = SY_FP64)
+{
+    if (nrhs < 1 || nrhs > 2) return gpch::fail(ctx, GPCH_INVALID_ARG, "symmetric matvec takes 1 or 2 columns");
+    if (src != SY_FP64 && AP == nullptr) return gpch::fail(ctx, GPCH_INVALID_ARG, "packed copy missing");
+    const int nr = mv_nr(nrhs);
+    const unsigned blocks = (unsigned)((n * nr + THREADS - 1) / THREADS);
+    if (nr == 1) df_split_vec_kernel<1><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, st.done);
+    else df_split_vec_kernel<2><<<blocks, THREADS, 0, s>>>(n, nrhs, S, lds, df.SS, df.inv, st.done);
+    GPCH_LAUNCH_CHECK(ctx);
+#define GPCH_SY_ATTR(NRc, SRCc)                                                                                 \
+    GPCH_CUDA(ctx, cudaFuncSetAttribute(sym_mv_df_kernel<NRc, SRCc>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)sy_smem(NRc)))
+    static gpch::DeviceOnce attr_once;
+    GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
+        GPCH_SY_ATTR(1, SY_FP64);
+        GPCH_SY_ATTR(1, SY_WRITE);
+        GPCH_SY_ATTR(1, SY_PACKED);
+        GPCH_SY_ATTR(2, SY_FP64);
+        GPCH_SY_ATTR(2, SY_WRITE);
+        GPCH_SY_ATTR(2, SY_PACKED);
+        return GPCH_OK;
+    }));
+#undef GPCH_SY_ATTR
+    const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
+    double *dotp = part, *axp = part + (size_t)sy_chunks(n) * n * nr;
+    const dim3 grid((unsigned)sy_chunks(n), (unsigned)sy_strips(n));
+    const double abytes = (src == SY_WRITE ? 2.0 : 1.0) * (double)n * (double)(n + 1) / 2.0 * sizeof(double);
+    gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s, abytes + 2.0 * n * nrhs * sizeof(double));
+#define GPCH_SY(NRc, SRCc)                                                                                      \
+    sym_mv_df_kernel<NRc, SRCc><<<grid, THREADS, sy_smem(NRc), s>>>(n, A, lda, AP, df, dotp, axp, st.done, vec)
+    if (nr == 1) {
+        if (src == SY_WRITE) GPCH_SY(1, SY_WRITE);
+        else if (src == SY_PACKED) GPCH_SY(1, SY_PACKED);
+        else GPCH_SY(1, SY_FP64);
+        GPCH_LAUNCH_CHECK(ctx);
+        sym_mv_finish_kernel<1><<<(unsigned)sy_strips(n), THREADS, 0, s>>>(n, nrhs, dotp, axp, S, lds, T, ldt, st,
+                                                                          mode, SRArgs{0.0, 0, 0});
+    } else {
+        if (src == SY_WRITE) GPCH_SY(2, SY_WRITE);
+        else if (src == SY_PACKED) GPCH_SY(2, SY_PACKED);
+        else GPCH_SY(2, SY_FP64);
+        GPCH_LAUNCH_CHECK(ctx);
+        sym_mv_finish_kernel<2><<<(unsigned)sy_strips(n), THREADS, 0, s>>>(n, nrhs, dotp, axp, S, lds, T, ldt, st,
+                                                                          mode, SRArgs{0.0, 0, 0});
+    }
+#undef GPCH_SY
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -1668,7 +2022,16 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     st.done = ic + 2 * MAXRHS;
     st.counter = cv.take<unsigned>(2);
     st.part = cv.take<double>(part_doubles(n, nrhs, PROD_DF));
-    // double-float products for t = A s (the true residuals stay FP64)
+    // double-float products for t = A s; with one or two right-hand sides
+    // the iteration products and the true residuals read A's lower
+    // triangle only (launch_symv_df), else the iteration products read all
+    // of A and the true residuals take FP64 products
+    // (the first of them also stores the heads and tails of A's lower
+    // triangle in a packed copy that the later ones read instead of A)
+    const bool sym = nrhs <= 2;
+    double *sym_part = sym ? cv.take<double>(sy_part_doubles(n, mv_nr(nrhs))) : nullptr;
+    float2 *sym_ap = sym ? cv.take<float2>((size_t)sy_off(n, sy_strips(n))) : nullptr;
+    bool sym_packed = false;   // the packed copy is made
     CGBufs dfb{};
     dfb.df.SS = cv.take<float2>((size_t)n * mv_nr(nrhs));
     {
@@ -1732,7 +2095,13 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     double est_at_check[MAXRHS] = {0};
     int it = 0;
     while (nactive > 0 && it < maxit) {
-        GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, MV_ALPHA, s, PROD_DF, dfb.df));
+        if (sym) {
+            GPCH_CHECK(launch_symv_df(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, MV_ALPHA, s, dfb.df, sym_part, sym_ap,
+                                      sym_packed ? SY_PACKED : SY_WRITE));
+            sym_packed = true;
+        } else {
+            GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, Sv, ldv, Tv, ldv, st, MV_ALPHA, s, PROD_DF, dfb.df));
+        }
         pcg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Sv, Tv, ldv, st, d_rr, d_xinf, d_rinf);
         GPCH_LAUNCH_CHECK(ctx);
         ++it;
@@ -1746,7 +2115,11 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
             if (est * ratio[c] <= bwd_tol || h[c] <= eps2 * bb[c]) replace = true;
         }
         if (replace) {
-            GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, 1, s));
+            if (sym)
+                GPCH_CHECK(launch_symv_df(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, MV_PLAIN, s, dfb.df, sym_part,
+                                          sym_ap, SY_PACKED));
+            else
+                GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, MV_PLAIN, s));
             pcg_replace_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Tv, B, ldb, ldv, st, d_rinf,
                                                             d_xinf);
             GPCH_LAUNCH_CHECK(ctx);
@@ -1789,6 +2162,10 @@ size_t pcg_ws_bytes(int64_t n, int nrhs)
     dry.take<int>(2 * MAXRHS + 1);
     dry.take<unsigned>(2);
     dry.take<double>(part_doubles(n, nrhs, PROD_DF));
+    if (nrhs <= 2) {
+        dry.take<double>(sy_part_doubles(n, mv_nr(nrhs)));
+        dry.take<float2>((size_t)sy_off(n, sy_strips(n)));
+    }
     dry.take<float2>((size_t)n * mv_nr(nrhs));
     dry.take<double>(2 * MAXRHS);
     dry.take<int>(1);
@@ -1900,7 +2277,13 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     dry.take<double>(3);
     dry.take<float>(gpch::anorm_ws_floats(n));
     const size_t fixed = dry.off;
-    const size_t mix = gpch::mixed_ws_bytes(n, tile), pcg = pcg_ws_bytes(n, g);
+    const size_t mix = gpch::mixed_ws_bytes(n, tile);
+    size_t pcg = pcg_ws_bytes(n, g);
+    if (nrhs > MAXRHS && nrhs % MAXRHS != 0) {
+        // the last group is smaller and may take the lower-triangle product's partials
+        const size_t last = pcg_ws_bytes(n, nrhs % MAXRHS);
+        if (last > pcg) pcg = last;
+    }
     GPCH_CHECK(gpch::ws_reserve(ctx, fixed + 256 + (mix > pcg ? mix : pcg)));
     gpch::Carver cv(ctx->ws);
     float *W = cv.take<float>((size_t)ldw * n);
@@ -1962,6 +2345,50 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     if (!all_ok)
         return gpch::fail(ctx, GPCH_NOT_CONVERGED, "refinement missed the backward error %.1e within %d iterations",
                           bwd_tol, maxit);
+    return GPCH_OK;
+}
+
+// Y = A X from A's lower triangle with double-float products, the product
+// of the refined solve's iteration (sym_mv_df_kernel), columns in pairs.
+extern "C" gpch_status gpch_symv_lower(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const double *X,
+                                       int64_t ldx, double *Y, int64_t ldy, int nrhs, void *stream)
+{
+    GPCH_ARG(ctx, ctx != nullptr, "null context");
+    GPCH_ARG(ctx, n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
+    GPCH_ARG(ctx, lda >= (n > 0 ? n : 1) && ldx >= (n > 0 ? n : 1) && ldy >= (n > 0 ? n : 1), "ld < n");
+    GPCH_ARG(ctx, n < (int64_t)1 << 24, "n too large");
+    if (n == 0 || nrhs == 0) return GPCH_OK;
+    GPCH_ARG(ctx, A && X && Y, "null pointer");
+    GPCH_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nr = nrhs >= 2 ? 2 : 1;
+    auto carve = [&](gpch::Carver &cv, CGBufs &b, double *&part) {
+        b.df.SS = cv.take<float2>((size_t)n * nr);
+        double *d = cv.take<double>(2 * MAXRHS);
+        b.df.scale = d;
+        b.df.inv = d + MAXRHS;
+        b.df.ebias = cv.take<int>(1);
+        b.dmax = cv.take<double>(1 + MAXRHS);
+        b.st.done = cv.take<int>(1);
+        b.st.counter = cv.take<unsigned>(2);
+        part = cv.take<double>(sy_part_doubles(n, nr));
+    };
+    CGBufs b{};
+    double *part = nullptr;
+    {
+        gpch::Carver dry(nullptr);
+        carve(dry, b, part);
+        GPCH_CHECK(gpch::ws_reserve(ctx, dry.off));
+    }
+    gpch::Carver cv(ctx->ws);
+    carve(cv, b, part);
+    GPCH_CUDA(ctx, cudaMemsetAsync(b.st.done, 0, sizeof(int), s));
+    for (int r0 = 0; r0 < nrhs; r0 += 2) {
+        const int g = (nrhs - r0 < 2) ? nrhs - r0 : 2;
+        GPCH_CHECK(df_prepare<double>(ctx, n, g, A, lda, X + (int64_t)r0 * ldx, ldx, b, s));
+        GPCH_CHECK(launch_symv_df(ctx, n, g, A, lda, X + (int64_t)r0 * ldx, ldx, Y + (int64_t)r0 * ldy, ldy, b.st,
+                                  MV_PLAIN, s, b.df, part));
+    }
     return GPCH_OK;
 }
 

@@ -433,20 +433,22 @@ __global__ void __launch_bounds__(256) panel_to_f16_kernel(const float *__restri
 // by atomicMax, so it must start at 0).  CTA b owns the 8 columns
 // 8b .. 8b+7 of Y (L y = e_c, forward
 // substitution) and keeps them in shared memory, rows in blocks of 32.
-// Block column K of L (rows 32K .. nb-1) is copied in by one or two 2-D
+// Block column K of L (rows 32K .. nb-1) arrives as one or two units, 2-D
 // TMA boxes of 256 rows x 32 columns through tmL (L as an nb x nb FP32
-// tensor; completion on an mbarrier; bounded waits set *err = 5) two
-// blocks ahead of its use (three buffers).  Per
-// block: warp w solves the 32 x 32 diagonal block for column w (lane = row;
-// one shuffle and one FMA per row), then the later rows are updated as a
-// GEMM, rows x 8 columns x 32, in 4 x 4 register tiles (two 16-byte loads
-// feed 16 FMAs).
+// tensor; completion on an mbarrier; bounded waits set *err = 5), two
+// units ahead of their use (three buffers, about 112 KB in all, so that a
+// CTA fits on an SM beside a CTA of the trailing update).  Per block:
+// warp w solves the 32 x 32 diagonal block for column w (lane = row; one
+// shuffle and one FMA per row), then the later rows are updated as a GEMM,
+// rows x 8 columns x 32, in 4 x 4 register tiles (two 16-byte loads feed 16
+// FMAs), the rows of each unit as it arrives.
 constexpr int TI_COLS = 8;
 constexpr int TI_MAXN = 512;
 constexpr int TI_THREADS = 256;
 constexpr int TI_BUFS = 3;
-constexpr int TI_BOX = 256;                     // rows of one TMA box
-constexpr size_t TI_SMEM = 128 + (size_t)(TI_BUFS * TI_MAXN * 32 + TI_MAXN * TI_COLS) * sizeof(float);
+constexpr int TI_BOX = 256;                     // rows of one TMA box (one unit)
+constexpr size_t TI_SMEM = 128 + (size_t)(TI_BUFS * TI_BOX * 32 + TI_MAXN * TI_COLS) * sizeof(float);
+static_assert(2 * TI_BOX >= TI_MAXN, "a block column is at most two units");
 __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_constant__ CUtensorMap tmL, int nb,
                                                                  float *Y, int64_t ldy, int *err, unsigned *absmax)
 {
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_co
     float *ti_smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(ti_smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t bar[TI_BUFS];
     if (nb % 32 != 0 || nb > TI_MAXN) return;
-    float *Ts = ti_smem + TI_BUFS * TI_MAXN * 32;   // Ts[r * TI_COLS + c]: row r of this CTA's columns
+    float *Ts = ti_smem + TI_BUFS * TI_BOX * 32;   // Ts[r * TI_COLS + c]: row r of this CTA's columns
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = blockIdx.x * TI_COLS;
     const int nK = nb / 32, K0 = c0 / 32;
@@ -463,31 +465,41 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_co
         gpch::tc::fence_mbar_init();
     }
     __syncthreads();
-    // block column K into buffer K % 3: rows 32K.. (q = row - 32K) of
-    // columns 32K + kk, box h = q / 256 at h * 32 * 256 + kk * 256 + q % 256
-    // (rows past nb read as zeros)
-    auto stage = [&](int K) {
-        if (tid != 0) return;
-        const bool two = 32 * K + TI_BOX < nb;
-        float *Ls = ti_smem + (K % TI_BUFS) * TI_MAXN * 32;
-        gpch::tc::mbar_arrive_expect_tx(&bar[K % TI_BUFS], (two ? 2u : 1u) * TI_BOX * 32u * 4u);
-        gpch::tc::tma_load_2d(Ls, &tmL, &bar[K % TI_BUFS], 32 * K, 32 * K);
-        if (two) gpch::tc::tma_load_2d(Ls + 32 * TI_BOX, &tmL, &bar[K % TI_BUFS], 32 * K + TI_BOX, 32 * K);
+    // unit (K, h): rows 32K + 256h .. 32K + 256h + 255 of block column K
+    // (h = 1 only when the column has more than 256 rows; rows past nb read
+    // as zeros), in buffer u % 3 for the u-th unit, row q of column 32K + kk
+    // at kk * 256 + q
+    auto next_unit = [&](int &K, int &h) {
+        if (h == 0 && 32 * K + TI_BOX < nb) {
+            h = 1;
+        } else {
+            ++K;
+            h = 0;
+        }
     };
-    auto lsat = [&](const float *Ls, int kk, int q) -> const float * {
-        return Ls + (q / TI_BOX) * (32 * TI_BOX) + kk * TI_BOX + (q % TI_BOX);
+    int sK = K0, sh = 0, nstaged = 0;   // the next unit to stage (every thread tracks it)
+    auto stage_next = [&]() {
+        if (sK >= nK) return;
+        if (tid == 0) {
+            const int b = nstaged % TI_BUFS;
+            gpch::tc::mbar_arrive_expect_tx(&bar[b], TI_BOX * 32u * 4u);
+            gpch::tc::tma_load_2d(ti_smem + b * TI_BOX * 32, &tmL, &bar[b], 32 * sK + TI_BOX * sh, 32 * sK);
+        }
+        ++nstaged;
+        next_unit(sK, sh);
     };
     uint32_t phases = 0;   // bit b: parity of buffer b's next phase
     bool ok = true;
-    if (K0 < nK) stage(K0);
-    if (K0 + 1 < nK) stage(K0 + 1);
+    stage_next();
+    stage_next();
     for (int e = tid; e < TI_MAXN * TI_COLS; e += TI_THREADS) {
         const int r = e / TI_COLS, cc = e % TI_COLS;
         Ts[e] = (r == c0 + cc) ? 1.0f : 0.0f;
     }
-    for (int K = K0; K < nK && ok; ++K) {
-        if (K + 2 < nK) stage(K + 2);
-        const int bk = K % TI_BUFS;
+    int K = K0, h = 0, ncons = 0;
+    while (K < nK) {
+        stage_next();
+        const int bk = ncons % TI_BUFS;
         ok = gpch::tc::mbar_wait(&bar[bk], (phases >> bk) & 1u, 1u << 24);
         phases ^= 1u << bk;
         ok = __syncthreads_and(ok);
@@ -495,34 +507,36 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_co
             if (tid == 0) atomicExch(err, 5);
             // let every copy this CTA started land before it exits
             gpch::tc::mbar_wait(&bar[bk], ((phases >> bk) & 1u) ^ 1u, 1u << 24);
-            for (int k2 = K + 1; k2 < nK && k2 <= K + 2; ++k2)
-                gpch::tc::mbar_wait(&bar[k2 % TI_BUFS], (phases >> (k2 % TI_BUFS)) & 1u, 1u << 24);
+            for (int u = ncons + 1; u < nstaged; ++u)
+                gpch::tc::mbar_wait(&bar[u % TI_BUFS], (phases >> (u % TI_BUFS)) & 1u, 1u << 24);
             break;
         }
-        const float *Ls = ti_smem + bk * TI_MAXN * 32;
-        {
+        const float *Ls = ti_smem + bk * TI_BOX * 32;
+        if (h == 0) {
             // diagonal block, column c0 + warp, row 32K + lane
             const int r = 32 * K + lane;
             float t = Ts[r * TI_COLS + warp];
-            const float rp = 1.0f / *lsat(Ls, lane, lane);
+            const float rp = 1.0f / Ls[lane * TI_BOX + lane];
 #pragma unroll 8
             for (int kk = 0; kk < 32; ++kk) {
-                const float l = *lsat(Ls, kk, lane);
+                const float l = Ls[kk * TI_BOX + lane];
                 const float y = __shfl_sync(0xffffffffu, t * rp, kk);
                 const float tn = fmaf(-l, y, t);
                 t = (lane == kk) ? y : ((lane > kk) ? tn : t);
             }
             Ts[r * TI_COLS + warp] = t;
+            __syncthreads();
         }
-        __syncthreads();
-        // later rows: T[r][:] -= L[r][32K..32K+31] Y[32K..32K+31][:]
-        const int rbeg = 32 * (K + 1), ntiles = (nb - rbeg) / 4 * (TI_COLS / 4);
+        // this unit's later rows: T[r][:] -= L[r][32K..32K+31] Y[32K..32K+31][:]
+        const int ubase = 32 * K + TI_BOX * h;
+        const int rbeg = h == 0 ? 32 * (K + 1) : ubase, rend = (ubase + TI_BOX < nb) ? ubase + TI_BOX : nb;
+        const int ntiles = (rend > rbeg ? rend - rbeg : 0) / 4 * (TI_COLS / 4);
         for (int tile = tid; tile < ntiles; tile += TI_THREADS) {
             const int r0 = rbeg + 4 * (tile / (TI_COLS / 4)), cg = 4 * (tile % (TI_COLS / 4));
             float acc[4][4] = {};
 #pragma unroll 8
             for (int kk = 0; kk < 32; ++kk) {
-                const float4 lv = *reinterpret_cast<const float4 *>(lsat(Ls, kk, r0 - 32 * K));
+                const float4 lv = *reinterpret_cast<const float4 *>(Ls + kk * TI_BOX + (r0 - ubase));
                 const float4 yv = *reinterpret_cast<const float4 *>(Ts + (32 * K + kk) * TI_COLS + cg);
                 const float la[4] = {lv.x, lv.y, lv.z, lv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
@@ -541,7 +555,9 @@ __global__ void __launch_bounds__(TI_THREADS) tri_inv_f32_kernel(const __grid_co
                 *tp = v;
             }
         }
-        __syncthreads();   // the buffer is refilled at the next step; Ts rows are read next block
+        __syncthreads();   // the buffer is refilled two units on; Ts rows are read by later units
+        ++ncons;
+        next_unit(K, h);
     }
     float mx = 0.0f;
     for (int e = tid; e < nb * TI_COLS; e += TI_THREADS) {
@@ -911,8 +927,8 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
 //   D = T(c0.., c0..) - L(c0.., 0:c0) L(c0.., 0:c0)^T   (the 32 x 32 diagonal block)
 //   X = T(R.., c0..)  - L(R.., 0:c0)  L(c0.., 0:c0)^T   (its 32 rows, R = c0 + 32 (b + 1))
 // (warps 0-3 form D, warps 4-7 form X, 4 x 2 outputs per thread, the
-// columns 0:c0 of both row sets staged k-major in shared memory 32 at a
-// time by cp.async, four chunks in flight), factors D on one warp (each
+// columns 0:c0 of both row sets staged k-major in shared memory 16 at a
+// time by cp.async, six chunks in flight), factors D on one warp (each
 // pivot column broadcast through shared memory), inverts L_ss on all eight
 // warps (four columns each) and forms X L_ss^-T as one 32 x 32 product.
 // Every CTA forms and factors D itself, so the launch needs no
@@ -925,7 +941,9 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
 // 32) and the launch of the next block column (which reads no entry of
 // that block) copies it into T (prev_c0 >= 0).  A pivot that is not
 // positive sets *info = col0 + c0 + (its column) + 1 (CTA 0) and ends
-// every CTA.
+// every CTA.  The 32 x 32 blocks used after the K loop share the stages'
+// shared memory, so that a CTA (about 25 KB) fits on an SM beside two
+// CTAs of the trailing update, which run meanwhile on other streams.
 __device__ __forceinline__ void cp_async_f32(float *dst, const float *src)
 {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -937,20 +955,27 @@ __device__ __forceinline__ void cp_async_wait_upto(int pending)
     if (pending <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
     else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
     else if (pending == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-    else asm volatile("cp.async.wait_group 3;" ::: "memory");
+    else if (pending == 3) asm volatile("cp.async.wait_group 3;" ::: "memory");
+    else if (pending == 4) asm volatile("cp.async.wait_group 4;" ::: "memory");
+    else asm volatile("cp.async.wait_group 5;" ::: "memory");
 }
 
 constexpr int DS_THREADS = 256;
-constexpr int DS_KC = 32;       // K columns per staged chunk (one block column)
-constexpr int DS_STAGES = 4;    // chunks in flight (cp_async_wait_upto covers up to 3 pending)
+constexpr int DS_KC = 16;       // K columns per staged chunk (block columns are 32 wide)
+constexpr int DS_STAGES = 6;    // chunks in flight (cp_async_wait_upto covers up to 5 pending)
+constexpr int DS_STAGE_FLOATS = DS_STAGES * DS_KC * 32;
+static_assert(3 * 32 * 33 <= 2 * DS_STAGE_FLOATS, "the post-loop blocks fit in the stages");
 __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t ldt, int nb, int c0, int64_t col0,
                                                                int64_t *info, float *lss, int prev_c0)
 {
-    __shared__ __align__(16) float Ad[DS_STAGES][DS_KC][32];   // Ad[.][k][i] = L(c0 + i, k0 + k)
-    __shared__ __align__(16) float Ar[DS_STAGES][DS_KC][32];   // Ar[.][k][r] = L(R + r, k0 + k)
-    __shared__ float Ds[32][33];   // D, then L_ss (zero above the diagonal)
-    __shared__ float Xs[32][33];   // X
-    __shared__ float Ys[32][33];   // L_ss^-1
+    __shared__ __align__(16) float stg[2 * DS_STAGE_FLOATS];
+    // K loop: Ad[.][k][i] = L(c0 + i, k0 + k), Ar[.][k][r] = L(R + r, k0 + k)
+    float(*Ad)[DS_KC][32] = reinterpret_cast<float(*)[DS_KC][32]>(stg);
+    float(*Ar)[DS_KC][32] = reinterpret_cast<float(*)[DS_KC][32]>(stg + DS_STAGE_FLOATS);
+    // after it: D, then L_ss (zero above the diagonal); X; L_ss^-1
+    float(*Ds)[33] = reinterpret_cast<float(*)[33]>(stg);
+    float(*Xs)[33] = reinterpret_cast<float(*)[33]>(stg + 32 * 33);
+    float(*Ys)[33] = reinterpret_cast<float(*)[33]>(stg + 2 * 32 * 33);
     __shared__ float rd[32];
     __shared__ __align__(16) float colb[32];   // the pivot column being broadcast
     __shared__ int bad;
@@ -992,7 +1017,8 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
     const bool early = c0 > 0;   // the previous launch is this tile's block column s - 1
     if (early) {
         init_acc();
-        while (issued < DS_STAGES - 1 && issued < nchunk - 1) stage(issued++);
+        // K columns before the previous block column (32 wide) only
+        while (issued < DS_STAGES - 1 && issued < nchunk - 32 / DS_KC) stage(issued++);
     }
     gpch::pdl_wait();
     gpch::pdl_trigger();

@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_chol_factor.argtypes = [_vp, _i64, _int, _vp, _i64, _vp, ctypes.POINTER(_i64)]
         L.gpch_chol_solve.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_chol_solve_f32.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
+        L.gpch_symv_lower.argtypes = [_vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _vp]
         L.gpch_cg_solve.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int, _vp,
                                     ctypes.POINTER(CGStats)]
         L.gpch_cg_solve_ex.argtypes = [_vp, _i64, _vp, _int, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int, _int,
@@ -155,7 +156,7 @@ def lib() -> ctypes.CDLL:
         L.gpch_cgsr_vectors.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _int, _vp]
         L.gpch_cgsr_residual.argtypes = [_vp, _i64, _int, _vp, _vp, _i64, _vp, _vp, _i64, _int, _vp]
         for name in ("gpch_chol_factor_ex", "gpch_gemm_fp64_emulated", "gpch_autotune", "gpch_tune_get", "gpch_batched_solve_mixed", "gpch_block_matvec", "gpch_cgsr_partials", "gpch_cgsr_scalars", "gpch_cgsr_vectors",
-                     "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve", "gpch_chol_solve_f32",
+                     "gpch_cgsr_residual", "gpch_cg_solve_ex", "gpch_logdet", "gpch_predict_mean", "gpch_create", "gpch_destroy", "gpch_se_matrix", "gpch_chol_factor", "gpch_chol_solve", "gpch_chol_solve_f32", "gpch_symv_lower",
                      "gpch_cg_solve", "gpch_timing_enable", "gpch_timing_read", "gpch_syrk_lowprec",
                      "gpch_chol_factor_mixed", "gpch_solve_refined", "gpch_cg_solve_noalloc",
                      "gpch_batched_solve", "gpch_server_create", "gpch_server_submit", "gpch_server_wait",
@@ -308,6 +309,25 @@ def chol_solve_f32(L: torch.Tensor, B: torch.Tensor, ctx: Context | None = None,
     ctx.check(lib().gpch_chol_solve_f32(ctx.handle, L.shape[0], L.data_ptr(), _ld(L), B.data_ptr(), _ld(B),
                                         B.shape[1], _stream(stream)))
     return B
+
+
+def symv_lower(A: torch.Tensor, X: torch.Tensor, Y: torch.Tensor | None = None, ctx: Context | None = None,
+               stream=None) -> torch.Tensor:
+    """Y = A X from the lower triangle of the column-major FP64 symmetric A
+    (entries above the diagonal never change the result), with double-float
+    products: the refined solve's CG product.  X: n x nrhs column-major
+    FP64.  Returns Y (n x nrhs, column-major; allocated when not given).
+    Enqueued on the stream."""
+    ctx = ctx or default_context()
+    _check_cuda(A, torch.float64)
+    _check_cuda(X, torch.float64)
+    n, nrhs = X.shape[0], X.shape[1]
+    if Y is None:
+        Y = colmajor(n, nrhs, device=X.device)
+    _check_cuda(Y, torch.float64)
+    ctx.check(lib().gpch_symv_lower(ctx.handle, n, A.data_ptr(), _ld(A), X.data_ptr(), _ld(X), Y.data_ptr(), _ld(Y),
+                                    nrhs, _stream(stream)))
+    return Y
 
 
 def logdet(L: torch.Tensor, ctx: Context | None = None, stream=None) -> float:
