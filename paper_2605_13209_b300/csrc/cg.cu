@@ -1189,9 +1189,12 @@ void launch_mv_kernel(int64_t n, int64_t ncols, int nrhs, const TA *A, int64_t l
 // column sums of a group stay in registers over the chunk and are reduced
 // over the warp at its end; the row sums of a segment are added into the
 // warp's slice of shared memory and summed over the warps in warp order
-// once per unit.  The partials, scaled back and widened to FP64, go to dotp
-// (column j, chunk c: dotp[(c n + j) NR + r]) and axp (row i, strip J:
-// axp[(J n + i) NR + r]); sym_mv_finish_kernel adds them in a fixed order.
+// once per unit.  The partials go out as double-float pairs of the scaled
+// products to dotp (column j, chunk c: dotp[(c n + j) NR + r]) and axp (row
+// i, strip J: axp[(J n + i) NR + r]); sym_mv_finish_kernel adds them in a
+// fixed order and scales back.  Nothing in the loop is FP64 arithmetic:
+// this part's FP64 pipe is slow enough that a few widenings per column
+// group held the loop back.
 //
 // The source of the entries (SRC):
 //   SY_FP64   A itself; each entry is cut into its float head and tail
@@ -1220,7 +1223,7 @@ inline size_t sy_smem(int nr)
 {
     return (size_t)(THREADS / 32) * (SY_ST * SY_CG * 64 * sizeof(double) + SY_R * nr * sizeof(float2));
 }
-// doubles of the two partial arrays
+// doubles (8-byte slots: double-float pairs) of the two partial arrays
 inline size_t sy_part_doubles(int64_t n, int nr) { return (size_t)(sy_chunks(n) + sy_strips(n)) * n * nr; }
 // float2 offset of strip J in the packed copy (strip J' has SY_SW columns
 // of n2 - J' SY_SW entries); sy_off(n, sy_strips(n)) is its size
@@ -1243,8 +1246,8 @@ __device__ __forceinline__ void cp_async8_zfill(void *dst, const void *src, bool
 
 template <int NR, int SRC>
 __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
-                                                               float2 *AP, DFArgs df, double *__restrict__ dotp,
-                                                               double *__restrict__ axp, const int *done, int vec)
+                                                               float2 *AP, DFArgs df, float2 *__restrict__ dotp,
+                                                               float2 *__restrict__ axp, const int *done, int vec)
 {
     extern __shared__ __align__(16) double sy_smem_raw[];
     if (done && *done) return;
@@ -1266,45 +1269,51 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
     float2 *axs = reinterpret_cast<float2 *>(sy_smem_raw + (size_t)(THREADS / 32) * SY_ST * SY_CG * 64);
     float2 *ax = axs + (size_t)warp * SY_R * NR;
     for (int e = lane; e < SY_R * NR; e += 32) ax[e] = make_float2(0.0f, 0.0f);
+    // Everything below indexes from the chunk's first row r0 with 32-bit
+    // offsets: 64-bit integer arithmetic shares the FP64 pipe on this part.
+    const int rows2 = (int)((n2 - r0 < SY_R) ? n2 - r0 : SY_R);   // rows of the packed strip in the chunk
+    const float2 *SSr = df.SS + r0 * NR;
     for (int g = 0; g < 32 / SY_CG; ++g) {
         const int64_t j0 = cs + warp * 32 + g * SY_CG;   // the group's first column
         if (j0 >= n) break;
+        const int ncg = (int)((n - j0 < SY_CG) ? n - j0 : SY_CG);   // columns of the group inside A
+        const int dlt = (int)(r0 - j0);   // row r0 + rl lies (rl + dlt - q) below column j0 + q's diagonal
         float ch[SY_CG][NR], cl[SY_CG][NR], dh[SY_CG][NR], dl[SY_CG][NR];
 #pragma unroll
         for (int q = 0; q < SY_CG; ++q)
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const float2 v = (j0 + q < n) ? df.SS[(j0 + q) * NR + r] : make_float2(0.0f, 0.0f);
+                const float2 v = (q < ncg) ? df.SS[(j0 + q) * NR + r] : make_float2(0.0f, 0.0f);
                 ch[q][r] = v.x;
                 cl[q][r] = v.y;
                 dh[q][r] = dl[q][r] = 0.0f;
             }
-        // the group's columns: in A, or in the packed strip
+        // the group's columns from row r0: in A, or in the packed strip
         const double *acol[SY_CG];
         float2 *pcol[SY_CG];
 #pragma unroll
         for (int q = 0; q < SY_CG; ++q) {
-            const int64_t jq = (j0 + q < n) ? j0 + q : j0;
-            acol[q] = A + jq * lda;
-            pcol[q] = (SRC != SY_FP64) ? APs + (jq - cs) * ldp - cs : nullptr;   // indexed by the row i
+            const int64_t jq = (q < ncg) ? j0 + q : j0;
+            acol[q] = A + jq * lda + r0;
+            pcol[q] = (SRC != SY_FP64) ? APs + (jq - cs) * ldp + (r0 - cs) : nullptr;
         }
         // in the diagonal chunk, segments wholly above the group's first column are skipped
-        const int s0 = dg ? (int)((j0 - r0) / 64) : 0;
+        const int s0 = dg ? (-dlt) / 64 : 0;
         // segment sg into stage sg % SY_ST: this lane's rows of the SY_CG columns
         auto stage = [&](int sg) {
             double *b = buf + (sg % SY_ST) * SY_CG * 64;
-            const int64_t i = r0 + sg * 64 + 2 * lane;
+            const int rl = sg * 64 + 2 * lane;
 #pragma unroll
             for (int q = 0; q < SY_CG; ++q) {
-                const bool colok = j0 + q < n;
+                const bool colok = q < ncg;
                 if constexpr (SRC == SY_PACKED) {
-                    cp_async16_zfill(b + q * 64 + 2 * lane, (i < n2 && colok) ? (const void *)(pcol[q] + i) : A,
-                                     i < n2 && colok);
+                    const bool ok = rl < rows2 && colok;
+                    cp_async16_zfill(b + q * 64 + 2 * lane, ok ? (const void *)(pcol[q] + rl) : A, ok);
                 } else if (vec) {
-                    cp_async16_zfill(b + q * 64 + 2 * lane, (i + 1 < n) ? acol[q] + i : A, i + 1 < n);
+                    cp_async16_zfill(b + q * 64 + 2 * lane, (rl + 1 < rows) ? acol[q] + rl : A, rl + 1 < rows);
                 } else {
-                    cp_async8_zfill(b + q * 64 + 2 * lane, (i < n) ? acol[q] + i : A, i < n);
-                    cp_async8_zfill(b + q * 64 + 2 * lane + 1, (i + 1 < n) ? acol[q] + i + 1 : A, i + 1 < n);
+                    cp_async8_zfill(b + q * 64 + 2 * lane, (rl < rows) ? acol[q] + rl : A, rl < rows);
+                    cp_async8_zfill(b + q * 64 + 2 * lane + 1, (rl + 1 < rows) ? acol[q] + rl + 1 : A, rl + 1 < rows);
                 }
             }
         };
@@ -1319,18 +1328,17 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
             asm volatile("cp.async.wait_group %0;" ::"n"(SY_ST - 1) : "memory");
             double *b = buf + (sg % SY_ST) * SY_CG * 64;
             const int rl = sg * 64 + 2 * lane;   // the lane's first row, chunk-local
-            const int64_t i = r0 + rl;
-            if (SRC != SY_PACKED && vec && i + 1 == n) {
+            if (SRC != SY_PACKED && vec && rl + 1 == rows && r0 + rows == n) {
                 // n odd: the last row alone (the 16-byte copy was skipped)
 #pragma unroll
-                for (int q = 0; q < SY_CG; ++q) b[q * 64 + 2 * lane] = acol[q][i];
+                for (int q = 0; q < SY_CG; ++q) b[q * 64 + 2 * lane] = acol[q][rl];
             }
             float rh[2][NR], rt[2][NR], uh[2][NR], ul[2][NR];
 #pragma unroll
             for (int p = 0; p < 2; ++p)
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    const float2 v = (i + p < n) ? df.SS[(i + p) * NR + r] : make_float2(0.0f, 0.0f);
+                    const float2 v = (rl + p < rows) ? SSr[(rl + p) * NR + r] : make_float2(0.0f, 0.0f);
                     rh[p][r] = v.x;
                     rt[p][r] = v.y;
                     uh[p][r] = ul[p][r] = 0.0f;
@@ -1358,9 +1366,10 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
                         hd[p] = hx[p] = hv[p];
                         td[p] = tx[p] = tv[p];
                         if constexpr (MASKED) {
-                            const int64_t ii = i + p, jj = j0 + q;
-                            const bool in = ii < n && jj < n;
-                            const bool okd = in && (!dg || ii >= jj), okx = in && (!dg || ii > jj);
+                            // row - column = rl + p + dlt - q
+                            const int below = rl + p + dlt - q;
+                            const bool in = rl + p < rows && q < ncg;
+                            const bool okd = in && (!dg || below >= 0), okx = in && (!dg || below > 0);
                             hx[p] = okx ? hv[p] : 0.0f;
                             tx[p] = okx ? tv[p] : 0.0f;
                             hd[p] = okd ? hv[p] : 0.0f;
@@ -1369,8 +1378,8 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
                     }
                     if constexpr (SRC == SY_WRITE) {
                         // the masked heads and tails: zero above the diagonal and past n
-                        if (i < n2 && j0 + q < n)
-                            *reinterpret_cast<float4 *>(pcol[q] + i) = make_float4(hd[0], td[0], hd[1], td[1]);
+                        if (rl < rows2 && q < ncg)
+                            *reinterpret_cast<float4 *>(pcol[q] + rl) = make_float4(hd[0], td[0], hd[1], td[1]);
                     }
 #pragma unroll
                     for (int p = 0; p < 2; ++p)
@@ -1391,7 +1400,7 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
                         }
                 }
             };
-            const bool clean = !(dg && r0 + sg * 64 < j0 + SY_CG) && r0 + sg * 64 + 64 <= n && j0 + SY_CG <= n;
+            const bool clean = !(dg && sg * 64 + dlt < SY_CG) && sg * 64 + 64 <= rows && ncg == SY_CG;
             if (clean) products(SyTag<false>{});
             else products(SyTag<true>{});
 #pragma unroll
@@ -1413,7 +1422,7 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1)
                     df_add2(h, l, __shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off));
-                if (lane == 0 && j0 + q < n) dotp[(c * n + j0 + q) * NR + r] = ((double)h + (double)l) * df.scale[r];
+                if (lane == 0 && q < ncg) dotp[(c * n + j0 + q) * NR + r] = make_float2(h, l);
             }
     }
     __syncthreads();
@@ -1422,18 +1431,17 @@ __global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const 
         float h = axs[e].x, l = axs[e].y;
         for (int w = 1; w < THREADS / 32; ++w)
             df_add2(h, l, axs[(size_t)w * SY_R * NR + e].x, axs[(size_t)w * SY_R * NR + e].y);
-        const int r = e % NR;
-        axp[(J * n + r0 + e / NR) * NR + r] = ((double)h + (double)l) * df.scale[r];
+        axp[(J * n + r0) * NR + e] = make_float2(h, l);
     }
 }
 
 // t_i for the rows of strip blockIdx.x: the chunks' column sums of column
-// i and the strips' row sums of row i, in eight interleaved sums (index mod
-// 8) added in a fixed order; then the mode's reductions as the other
-// matvecs (mv_finish).
+// i and the strips' row sums of row i, in four interleaved double-float
+// sums (index mod 4) combined in a fixed order, widened and scaled once;
+// then the mode's reductions as the other matvecs (mv_finish).
 template <int NR>
-__global__ void __launch_bounds__(THREADS) sym_mv_finish_kernel(int64_t n, int nrhs, const double *__restrict__ dotp,
-                                                                const double *__restrict__ axp,
+__global__ void __launch_bounds__(THREADS) sym_mv_finish_kernel(int64_t n, int nrhs, const float2 *__restrict__ dotp,
+                                                                const float2 *__restrict__ axp, const double *scale,
                                                                 const double *__restrict__ S, int64_t lds, double *T,
                                                                 int64_t ldt, CGState st, int mode, SRArgs sr)
 {
@@ -1443,26 +1451,42 @@ __global__ void __launch_bounds__(THREADS) sym_mv_finish_kernel(int64_t n, int n
     const int wcols = (int)((n - i0 < SY_SW) ? n - i0 : SY_SW);
     const int tid = threadIdx.x;
     if (tid < wcols) {
-        const int64_t i = i0 + tid, nch = (n - i0 + SY_R - 1) / SY_R;
+        const int nch = (int)((n - i0 + SY_R - 1) / SY_R), nst = (int)J + 1;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            // eight interleaved sums (independent loads in flight), added in a fixed order
-            double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            int64_t c = 0;
-            for (; c + 8 <= nch; c += 8)
+            const float2 *dp = dotp + (i0 + tid) * NR + r, *xp = axp + (i0 + tid) * NR + r;
+            const int64_t step = n * NR;
+            float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int c = 0;
+            for (; c + 4 <= nch; c += 4)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] += dotp[((c + u) * n + i) * NR + r];
+                for (int u = 0; u < 4; ++u) {
+                    const float2 v = dp[(int64_t)(c + u) * step];
+                    df_add2(h[u], l[u], v.x, v.y);
+                }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c + u < nch) v[u] += dotp[((c + u) * n + i) * NR + r];
-            int64_t K = 0;
-            for (; K + 8 <= J + 1; K += 8)
+            for (int u = 0; u < 4; ++u)
+                if (c + u < nch) {
+                    const float2 v = dp[(int64_t)(c + u) * step];
+                    df_add2(h[u], l[u], v.x, v.y);
+                }
+            int K = 0;
+            for (; K + 4 <= nst; K += 4)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] += axp[((K + u) * n + i) * NR + r];
+                for (int u = 0; u < 4; ++u) {
+                    const float2 v = xp[(int64_t)(K + u) * step];
+                    df_add2(h[u], l[u], v.x, v.y);
+                }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (K + u <= J) v[u] += axp[((K + u) * n + i) * NR + r];
-            tcol[tid * NR + r] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+            for (int u = 0; u < 4; ++u)
+                if (K + u < nst) {
+                    const float2 v = xp[(int64_t)(K + u) * step];
+                    df_add2(h[u], l[u], v.x, v.y);
+                }
+            df_add2(h[0], l[0], h[1], l[1]);
+            df_add2(h[2], l[2], h[3], l[3]);
+            df_add2(h[0], l[0], h[2], l[2]);
+            tcol[tid * NR + r] = ((double)h[0] + (double)l[0]) * scale[r];
         }
     }
     mv_finish<SY_SW, NR>(i0, wcols, nrhs, S, lds, T, ldt, st, mode, sr, tcol);
@@ -1558,7 +1582,7 @@ gpch_status launch_symv_df(gpch_ctx *ctx, int64_t n, int nrhs, const double *A, 
     }));
 #undef GPCH_SY_ATTR
     const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 1) == 0) ? 1 : 0;
-    double *dotp = part, *axp = part + (size_t)sy_chunks(n) * n * nr;
+    float2 *dotp = reinterpret_cast<float2 *>(part), *axp = dotp + (size_t)sy_chunks(n) * n * nr;
     const dim3 grid((unsigned)sy_chunks(n), (unsigned)sy_strips(n));
     const double abytes = (src == SY_WRITE ? 2.0 : 1.0) * (double)n * (double)(n + 1) / 2.0 * sizeof(double);
     gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s, abytes + 2.0 * n * nrhs * sizeof(double));
@@ -1569,15 +1593,15 @@ gpch_status launch_symv_df(gpch_ctx *ctx, int64_t n, int nrhs, const double *A, 
         else if (src == SY_PACKED) GPCH_SY(1, SY_PACKED);
         else GPCH_SY(1, SY_FP64);
         GPCH_LAUNCH_CHECK(ctx);
-        sym_mv_finish_kernel<1><<<(unsigned)sy_strips(n), THREADS, 0, s>>>(n, nrhs, dotp, axp, S, lds, T, ldt, st,
-                                                                          mode, SRArgs{0.0, 0, 0});
+        sym_mv_finish_kernel<1><<<(unsigned)sy_strips(n), THREADS, 0, s>>>(n, nrhs, dotp, axp, df.scale, S, lds, T,
+                                                                          ldt, st, mode, SRArgs{0.0, 0, 0});
     } else {
         if (src == SY_WRITE) GPCH_SY(2, SY_WRITE);
         else if (src == SY_PACKED) GPCH_SY(2, SY_PACKED);
         else GPCH_SY(2, SY_FP64);
         GPCH_LAUNCH_CHECK(ctx);
-        sym_mv_finish_kernel<2><<<(unsigned)sy_strips(n), THREADS, 0, s>>>(n, nrhs, dotp, axp, S, lds, T, ldt, st,
-                                                                          mode, SRArgs{0.0, 0, 0});
+        sym_mv_finish_kernel<2><<<(unsigned)sy_strips(n), THREADS, 0, s>>>(n, nrhs, dotp, axp, df.scale, S, lds, T,
+                                                                          ldt, st, mode, SRArgs{0.0, 0, 0});
     }
 #undef GPCH_SY
     GPCH_LAUNCH_CHECK(ctx);
