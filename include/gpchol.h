@@ -609,9 +609,10 @@ typedef struct gpch_refine_stats {
  * r and all dot products FP64; Algorithm 1 (left) with a preconditioner),
  * from x_0 = 0 (the products A s and the true residuals b - A x formed as
  * double-float products: with one or two right-hand sides per group of 16
- * as gpch_symv_lower, from A's lower triangle, else the iteration's
- * products as gpch_cg_solve_ex's GPCH_CG_PRODUCTS_DOUBLE_FLOAT over all of
- * A and the true residuals in FP64), replacing the recurrence residual by b - A x every 50
+ * as gpch_symv_lower, from A's lower triangle, else as gpch_cg_solve_ex's
+ * GPCH_CG_PRODUCTS_DOUBLE_FLOAT over all of A; each entry of a true
+ * residual is then within about 2^-44 sum_j |A_ij| |x_j| of the exact one,
+ * at most 2^-44 of the backward error's denominator), replacing the recurrence residual by b - A x every 50
  * iterations and whenever an estimate of the backward error from the
  * recurrence residual (its ||r||_inf in place of the true residual's,
  * scaled by the truth-to-estimate ratio seen at the previous check)

@@ -1857,9 +1857,11 @@ gpch_status cg_group(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const d
 // Refined solve: preconditioned CG with M = Lt Lt^T, Lt the low-precision
 // factor (FP32 storage), applied by the forward/back substitution of
 // solve.cu.  A, x, r, dot products and recurrences stay in FP64; the
-// iteration's product t = A s takes double-float products (relative error
-// below about 2^-45 per product) and the true residuals b - A x FP64
-// products, so the backward error the stop rule measures is FP64's.  The host
+// iteration's products t = A s and the true residuals b - A x take
+// double-float products (relative error below about 2^-44 per product,
+// summed without further loss), so each entry of the measured residual is
+// within about 2^-44 sum_j |A_ij| |x_j| of the exact one: at most 2^-44 of
+// the backward error's denominator ||A||_inf ||x||_inf.  The host
 // reads a few scalars per iteration (an iteration already costs two
 // substitution sweeps), decides when to replace the recurrence residual by
 // the true one, and stops each column when its true backward error
@@ -2046,12 +2048,11 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     st.done = ic + 2 * MAXRHS;
     st.counter = cv.take<unsigned>(2);
     st.part = cv.take<double>(part_doubles(n, nrhs, PROD_DF));
-    // double-float products for t = A s; with one or two right-hand sides
-    // the iteration products and the true residuals read A's lower
-    // triangle only (launch_symv_df), else the iteration products read all
-    // of A and the true residuals take FP64 products
-    // (the first of them also stores the heads and tails of A's lower
-    // triangle in a packed copy that the later ones read instead of A)
+    // double-float products for t = A s and the true residuals; with one
+    // or two right-hand sides they read A's lower triangle only
+    // (launch_symv_df; the first of them also stores the heads and tails of
+    // A's lower triangle in a packed copy that the later ones read instead
+    // of A), else all of A
     const bool sym = nrhs <= 2;
     double *sym_part = sym ? cv.take<double>(sy_part_doubles(n, mv_nr(nrhs))) : nullptr;
     float2 *sym_ap = sym ? cv.take<float2>((size_t)sy_off(n, sy_strips(n))) : nullptr;
@@ -2143,7 +2144,8 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
                 GPCH_CHECK(launch_symv_df(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, MV_PLAIN, s, dfb.df, sym_part,
                                           sym_ap, SY_PACKED));
             else
-                GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, MV_PLAIN, s));
+                GPCH_CHECK(launch_matvec<double>(ctx, n, nrhs, A, lda, X, ldx, Tv, ldv, st, MV_PLAIN, s, PROD_DF,
+                                                 dfb.df));
             pcg_replace_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, Rv, Tv, B, ldb, ldv, st, d_rinf,
                                                             d_xinf);
             GPCH_LAUNCH_CHECK(ctx);
