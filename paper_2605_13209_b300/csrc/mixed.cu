@@ -927,8 +927,8 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
 //   D = T(c0.., c0..) - L(c0.., 0:c0) L(c0.., 0:c0)^T   (the 32 x 32 diagonal block)
 //   X = T(R.., c0..)  - L(R.., 0:c0)  L(c0.., 0:c0)^T   (its 32 rows, R = c0 + 32 (b + 1))
 // (warps 0-3 form D, warps 4-7 form X, 4 x 2 outputs per thread, the
-// columns 0:c0 of both row sets staged k-major in shared memory 16 at a
-// time by cp.async, six chunks in flight), factors D on one warp (each
+// columns 0:c0 of both row sets staged k-major in shared memory 32 at a
+// time by cp.async, three chunks in flight), factors D on one warp (each
 // pivot column broadcast through shared memory), inverts L_ss on all eight
 // warps (four columns each) and forms X L_ss^-T as one 32 x 32 product.
 // Every CTA forms and factors D itself, so the launch needs no
@@ -961,8 +961,8 @@ __device__ __forceinline__ void cp_async_wait_upto(int pending)
 }
 
 constexpr int DS_THREADS = 256;
-constexpr int DS_KC = 16;       // K columns per staged chunk (block columns are 32 wide)
-constexpr int DS_STAGES = 6;    // chunks in flight (cp_async_wait_upto covers up to 5 pending)
+constexpr int DS_KC = 32;       // K columns per staged chunk (one block column)
+constexpr int DS_STAGES = 3;    // chunks in flight (cp_async_wait_upto covers up to 5 pending)
 constexpr int DS_STAGE_FLOATS = DS_STAGES * DS_KC * 32;
 static_assert(3 * 32 * 33 <= 2 * DS_STAGE_FLOATS, "the post-loop blocks fit in the stages");
 __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t ldt, int nb, int c0, int64_t col0,
