@@ -81,12 +81,24 @@ __host__ __device__ constexpr int64_t kpos(bool split, int64_t c) { return split
 // a split-f16 copy scaled by 2^oscale[1]: row r, column c at position
 // kpos(true, c) of ohi + r * ldo (the copy the later updates read; ohi and
 // ldo must make every row 16-byte aligned).
+// A second MODE 0 update in the same launch (first_tiles > 0): CTAs from
+// first_tiles on take the lower trapezoid of another block column, with its
+// own C, m, ncol, K range (kp positions from k_off) and operand copy (tm_b,
+// which MODE 0 does not otherwise read), so that a short pass and a long
+// pass share one grid.
+struct SyrkSecond {
+    float *C;
+    int64_t m, ncol;
+    int64_t first_tiles;
+    int kp, k_off;
+};
+
 template <int MODE>
 __global__ void __maxnreg__(112)
     syrk_tc_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, int64_t m,
                    int kp, int split, float *__restrict__ C, int64_t ldc, int64_t tk0, int64_t tk1, int *err,
                    int prefetch_c, int f16, const int *scale, int k_off, int64_t ncol, int panel_k,
-                   const int *scale_b, __half *ohi, int64_t ldo, const int *oscale)
+                   const int *scale_b, __half *ohi, int64_t ldo, const int *oscale, SyrkSecond sp)
 {
     constexpr bool rect = MODE != 0;   // rectangle of P Q^T
     constexpr bool sub = MODE != 1;    // C -= (else C = )
@@ -106,8 +118,17 @@ __global__ void __maxnreg__(112)
     // CTAs that read the same rows of P run at the same time and share them
     // through L2.  Rows tk0 .. tk1-2 hold 1, 2, ..., nc-1 tiles (the
     // triangle), every later row nc = tk1 - tk0 tiles.
+    const bool second = MODE == 0 && sp.first_tiles > 0 && (int64_t)blockIdx.x >= sp.first_tiles;
+    if (second) {
+        C = sp.C;
+        m = sp.m;
+        ncol = sp.ncol;
+        kp = sp.kp;
+        k_off = sp.k_off;
+    }
+    const CUtensorMap *tma = second ? &tm_b : &tm_a;   // the operand copy of this CTA's update
     const int64_t nc = tk1 - tk0, tri = nc * (nc - 1) / 2;
-    const int64_t t = (int64_t)blockIdx.x;
+    const int64_t t = second ? (int64_t)blockIdx.x - sp.first_tiles : (int64_t)blockIdx.x;
     int64_t ti, tk;
     if constexpr (rect) {
         ti = t / nc;
@@ -152,9 +173,9 @@ __global__ void __maxnreg__(112)
     if (warp == 0) {
         if (lane == 0) {
             // TMA producer
-            gpch::tc::prefetch_tmap(&tm_a);
+            gpch::tc::prefetch_tmap(tma);
             if constexpr (rect) gpch::tc::prefetch_tmap(&tm_b);
-            const CUtensorMap *mb = rect ? &tm_b : &tm_a;
+            const CUtensorMap *mb = rect ? &tm_b : tma;
             const uint32_t bytes = diag ? BOX_BYTES : STAGE_BYTES;
             int issued = 0;
             for (int kc = 0; kc < NK; ++kc) {
@@ -166,7 +187,7 @@ __global__ void __maxnreg__(112)
                 const int32_t x = (int32_t)kpos(split, k_off + (kc / spp) * panel_k + (kc % spp) * kstage);
                 uint8_t *st = smem + s * STAGE_BYTES;
                 gpch::tc::mbar_arrive_expect_tx(&full[s], bytes);
-                gpch::tc::tma_load_2d(st, &tm_a, &full[s], x, (int32_t)i0);
+                gpch::tc::tma_load_2d(st, tma, &full[s], x, (int32_t)i0);
                 if (!diag) gpch::tc::tma_load_2d(st + BOX_BYTES, mb, &full[s], x, (int32_t)c0);
                 ++issued;
             }
@@ -1239,40 +1260,85 @@ gpch_status panel_convert(gpch_ctx *ctx, int64_t m, int k, const float *P, int64
 // only C columns below ncol (< 0: m) are written.  panel_k > 0: the K range
 // is a sequence of panels of that many columns, subtracted one at a time
 // (panel_k must divide the padded k).
-gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float *C, int64_t ldc, int prec,
-                           const LowprecBuffers &buf, int64_t tk0, int64_t tk1, cudaStream_t st, int64_t ncol = -1,
-                           int panel_k = 0)
+// One update of the lower trapezoid restricted to tile columns [tk0, tk1)
+// (see syrk_tc_kernel), for syrk_tc_launch.
+struct SyrkUpdate {
+    int64_t m;
+    int k;
+    int64_t k_off;
+    float *C;
+    LowprecBuffers buf;
+    int64_t ncol = -1;   // columns at or past ncol are not written (-1: m)
+};
+
+// C_lower -= P P^T for one update u, or for u and a second update u2 of
+// another block column in the same grid (with u2.m > 0; the same ldc, tile
+// columns and panel_k).
+gpch_status syrk_tc_launch_pair(gpch_ctx *ctx, const SyrkUpdate &u, const SyrkUpdate &u2, int64_t ldc, int prec,
+                                int64_t tk0, int64_t tk1, cudaStream_t st, int panel_k)
 {
-    if (ncol < 0 || ncol > m) ncol = m;
-    const int kp = (k + BK - 1) / BK * BK;
     const bool split = prec != GPCH_PREC_BF16;
     const bool f16 = prec == GPCH_PREC_SPLIT_F16;
-    const int64_t T = (m + BM - 1) / BM;
-    if (tk1 < 0 || tk1 > T) tk1 = T;
-    if (tk0 >= tk1) return GPCH_OK;
-    CUtensorMap ma;
-    GPCH_CHECK(make_panel_map(ctx, &ma, buf.hi, m, kpos(split, k_off + kp), buf.ld, f16));
+    struct Shape {
+        int64_t tiles = 0, t1 = 0, ncol = 0;
+        int kp = 0;
+        double work = 0.0;
+        CUtensorMap map;
+    };
+    auto shape = [&](const SyrkUpdate &v, Shape &o) -> gpch_status {
+        o.kp = (v.k + BK - 1) / BK * BK;
+        const int64_t T = (v.m + BM - 1) / BM;
+        const int64_t t1 = (tk1 < 0 || tk1 > T) ? T : tk1;
+        o.t1 = t1;
+        if (tk0 >= t1) return GPCH_OK;
+        GPCH_CHECK(make_panel_map(ctx, &o.map, v.buf.hi, v.m, kpos(split, v.k_off + o.kp), v.buf.ld, f16));
+        auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
+        o.tiles = offset(t1) - offset(tk0);
+        // algorithmic work: the lower-triangle entries of the updated columns
+        o.ncol = (v.ncol < 0 || v.ncol > v.m) ? v.m : v.ncol;
+        const int64_t cA = tk0 * BN, cB = (t1 * BN < o.ncol) ? t1 * BN : o.ncol;
+        const double cols_entries =
+            (double)(cB - cA) * (double)v.m - ((double)cB * (cB - 1) - (double)cA * (cA - 1)) / 2.0;
+        o.work = 2.0 * (double)v.k * cols_entries * (split ? 3.0 : 1.0);
+        return GPCH_OK;
+    };
+    Shape a, b;
+    GPCH_CHECK(shape(u, a));
+    if (u2.m > 0) GPCH_CHECK(shape(u2, b));
+    if (a.tiles == 0 && b.tiles == 0) return GPCH_OK;
     static gpch::DeviceOnce attr_once;
     GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
         GPCH_CUDA(ctx, cudaFuncSetAttribute(syrk_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         return GPCH_OK;
     }));
-    auto offset = [&](int64_t c) { return c * T - c * (c - 1) / 2; };
-    const int64_t tiles = offset(tk1) - offset(tk0);
-    // algorithmic work: the lower-triangle entries of the updated columns
-    const int64_t cA = tk0 * BN, cB = (tk1 * BN < ncol) ? tk1 * BN : ncol;
-    const double cols_entries = (double)(cB - cA) * (double)m - ((double)cB * (cB - 1) - (double)cA * (cA - 1)) / 2.0;
-    const double work = 2.0 * (double)k * cols_entries * (split ? 3.0 : 1.0);
-    gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, work);
+    gpch::PhaseScope ph(ctx, GPCH_PHASE_MIXED_TRAILING, st, a.work + b.work);
     // the C-tile prefetch needs 16-byte aligned columns
-    const int prefetch_c = ((uintptr_t)C % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-    syrk_tc_kernel<0><<<(unsigned)tiles, TC_THREADS, TC_SMEM, st>>>(ma, ma, m, kp, split ? 1 : 0, C, ldc, tk0, tk1,
-                                                               buf.err, prefetch_c, f16 ? 1 : 0,
-                                                               f16 ? buf.scale : nullptr, (int)k_off, ncol,
-                                                               panel_k > 0 ? panel_k : kp, nullptr, nullptr, 0,
-                                                               nullptr);
+    const bool al = (uintptr_t)u.C % 16 == 0 && (u2.m <= 0 || (uintptr_t)u2.C % 16 == 0);
+    const int prefetch_c = (al && ldc % 4 == 0) ? 1 : 0;
+    // a first update without tiles hands the whole grid to the second
+    const bool only2 = a.tiles == 0;
+    const SyrkUpdate &f = only2 ? u2 : u;
+    const Shape &fa = only2 ? b : a;
+    const SyrkSecond sp = (only2 || b.tiles == 0) ? SyrkSecond{nullptr, 0, 0, 0, 0, 0}
+                                                  : SyrkSecond{u2.C, u2.m, b.ncol, a.tiles, b.kp, (int)u2.k_off};
+    // tile columns of the enumeration: the wider of the two (an update with
+    // fewer tile rows than that has all its tiles in the leading triangle,
+    // which the enumeration lays out the same way for any width)
+    const int64_t tk1k = (a.t1 > b.t1) ? a.t1 : b.t1;
+    syrk_tc_kernel<0><<<(unsigned)(a.tiles + b.tiles), TC_THREADS, TC_SMEM, st>>>(
+        fa.map, (only2 || b.tiles == 0) ? fa.map : b.map, f.m, fa.kp, split ? 1 : 0, f.C, ldc, tk0, tk1k, f.buf.err,
+        prefetch_c, f16 ? 1 : 0, f16 ? f.buf.scale : nullptr, (int)f.k_off, fa.ncol, panel_k > 0 ? panel_k : fa.kp,
+        nullptr, nullptr, 0, nullptr, sp);
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
+}
+
+gpch_status syrk_tc_launch(gpch_ctx *ctx, int64_t m, int k, int64_t k_off, float *C, int64_t ldc, int prec,
+                           const LowprecBuffers &buf, int64_t tk0, int64_t tk1, cudaStream_t st, int64_t ncol = -1,
+                           int panel_k = 0)
+{
+    return syrk_tc_launch_pair(ctx, SyrkUpdate{m, k, k_off, C, buf, ncol}, SyrkUpdate{0, 0, 0, nullptr, buf}, ldc,
+                               prec, tk0, tk1, st, panel_k);
 }
 
 // C (m x nq FP32, ldc) = P Q^T on tensor cores from split-f16 copies: P in
@@ -1307,7 +1373,7 @@ gpch_status panel_gemm_tc_launch(gpch_ctx *ctx, int64_t m, int64_t nq, int k, fl
         mp, mq, m, kp, 1, C, ldc, 0, tc, pb.err, prefetch_c, 1, pb.scale, 0, nq,
         (acc_k > 0 && kp % acc_k == 0) ? acc_k : kp, qb.scale,
         out ? reinterpret_cast<__half *>(out->hi) + kpos(true, out_col) : nullptr, out ? out->ld : 0,
-        out ? out->scale : nullptr);
+        out ? out->scale : nullptr, SyrkSecond{nullptr, 0, 0, 0, 0, 0});
     GPCH_LAUNCH_CHECK(ctx);
     return GPCH_OK;
 }
@@ -1603,18 +1669,27 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
             const int64_t r2 = j0 + nj + tile, m2 = n - r2;
             LowprecBuffers qb = all;
             qb.hi = all.hi + r2 * all.ld;
-            GPCH_CHECK(syrk_tc_launch(ctx, m2, (int)nj, j0, W + r2 * (1 + ldw), ldw, prec, qb, 0, blk_cols, sb, tile,
-                                      acc_k));
-            GPCH_CUDA(ctx, cudaEventRecord(ev_ready[(J + 2) % 2], sb));
+            const SyrkUpdate short_pass{m2, (int)nj, j0, W + r2 * (1 + ldw), qb, tile};
             if (m > 2 * tile) {
+                // the short pass shares one grid with the first piece of the
+                // long pass, whose tiles fill the waves the short tiles leave
                 const int64_t r3 = r2 + tile, m3 = n - r3, K = j0 + nj;
                 LowprecBuffers qb3 = all;
                 qb3.hi = all.hi + r3 * all.ld;
-                for (int64_t k0 = 0; k0 < K; k0 += LEFT_K) {
+                const int64_t kk0 = (K < LEFT_K) ? K : LEFT_K;
+                GPCH_CHECK(syrk_tc_launch_pair(ctx, short_pass,
+                                               SyrkUpdate{m3, (int)kk0, 0, W + r3 * (1 + ldw), qb3, tile}, ldw, prec, 0,
+                                               blk_cols, sb, acc_k));
+                GPCH_CUDA(ctx, cudaEventRecord(ev_ready[(J + 2) % 2], sb));
+                for (int64_t k0 = kk0; k0 < K; k0 += LEFT_K) {
                     const int64_t kk = (K - k0 < LEFT_K) ? K - k0 : LEFT_K;
                     GPCH_CHECK(syrk_tc_launch(ctx, m3, (int)kk, k0, W + r3 * (1 + ldw), ldw, prec, qb3, 0, blk_cols,
                                               sb, tile, acc_k));
                 }
+            } else {
+                GPCH_CHECK(syrk_tc_launch(ctx, m2, (int)nj, j0, W + r2 * (1 + ldw), ldw, prec, qb, 0, blk_cols, sb,
+                                          tile, acc_k));
+                GPCH_CUDA(ctx, cudaEventRecord(ev_ready[(J + 2) % 2], sb));
             }
         }
     }
