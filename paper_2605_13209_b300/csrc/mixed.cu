@@ -947,7 +947,8 @@ __global__ void __launch_bounds__(256) norm_reduce_kernel(int64_t n, const float
 // c0 = 32 s forms, in every CTA b,
 //   D = T(c0.., c0..) - L(c0.., 0:c0) L(c0.., 0:c0)^T   (the 32 x 32 diagonal block)
 //   X = T(R.., c0..)  - L(R.., 0:c0)  L(c0.., 0:c0)^T   (its 32 rows, R = c0 + 32 (b + 1))
-// (warps 0-3 form D, warps 4-7 form X, 4 x 2 outputs per thread, the
+// (warps 0-3 form D, warps 4-7 form X, 4 x 4 outputs per thread over
+// half of each chunk's K columns, the halves added at the end; the
 // columns 0:c0 of both row sets staged k-major in shared memory 32 at a
 // time by cp.async, three chunks in flight), factors D on one warp (each
 // pivot column broadcast through shared memory), inverts L_ss on all eight
@@ -1004,20 +1005,24 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
     const int nc = (nb - c0 < 32) ? nb - c0 : 32;
     const int R = c0 + 32 * ((int)blockIdx.x + 1);
     const int nr = (nb - R < 0) ? 0 : ((nb - R < 32) ? nb - R : 32);
+    // threads 0-127 form D, 128-255 X; within each, the first 64 take the
+    // even halves of every chunk's K columns and the last 64 the odd halves
+    // (4 x 4 outputs per thread), added together once after the K loop
     const bool isD = tid < DS_THREADS / 2;
     const int u = isD ? tid : tid - DS_THREADS / 2;
-    const int ri = 4 * (u % 8), cj = 2 * (u / 8);   // this thread's rows ri.., columns cj..
+    const int kh = u / 64, v = u % 64;
+    const int ri = 4 * (v % 8), cj = 4 * (v / 8);   // this thread's rows ri.., columns cj..
     const int row0 = isD ? c0 : R, nrow = isD ? nc : nr;
     const int nchunk = c0 / DS_KC;
-    float acc[4][2];
+    float acc[4][4];
     auto init_acc = [&]() {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < 4; ++b) {
                 const int i = ri + a, j = cj + b;
                 // D: its lower triangle only (the tile's upper triangle is not read)
-                const bool in = i < nrow && j < nc && (!isD || j <= i);
+                const bool in = kh == 0 && i < nrow && j < nc && (!isD || j <= i);
                 acc[a][b] = in ? T[(row0 + i) + (int64_t)(c0 + j) * ldt] : 0.0f;
             }
     };
@@ -1064,24 +1069,32 @@ __global__ void __launch_bounds__(DS_THREADS) diag_step_kernel(float *T, int64_t
         const float(*Ao)[32] = isD ? Ad[sb] : Ar[sb];
         const float(*Bo)[32] = Ad[sb];
 #pragma unroll 4
-        for (int k = 0; k < DS_KC; ++k) {
+        for (int k = kh * (DS_KC / 2); k < (kh + 1) * (DS_KC / 2); ++k) {
             const float4 av = *reinterpret_cast<const float4 *>(&Ao[k][ri]);
-            const float2 bv = *reinterpret_cast<const float2 *>(&Bo[k][cj]);
-            const float x[4] = {av.x, av.y, av.z, av.w}, y[2] = {bv.x, bv.y};
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bo[k][cj]);
+            const float x[4] = {av.x, av.y, av.z, av.w}, y[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) acc[a][b] = fmaf(-x[a], y[b], acc[a][b]);
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(-x[a], y[b], acc[a][b]);
         }
         __syncthreads();   // the stage is refilled by a later chunk
     }
+    // the two K halves: the odd halves' sums first, then the even halves add theirs
+    float(*Os)[33] = isD ? Ds : Xs;
+    if (kh == 1) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            if (isD) Ds[ri + a][cj + b] = acc[a][b];
-            else Xs[ri + a][cj + b] = acc[a][b];
-        }
+            for (int b = 0; b < 4; ++b) Os[ri + a][cj + b] = acc[a][b];
+    }
+    __syncthreads();
+    if (kh == 0) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Os[ri + a][cj + b] += acc[a][b];
+    }
     if (tid == 0) bad = 0;
     __syncthreads();
     if (warp == 0) {
