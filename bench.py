@@ -407,7 +407,7 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                 "speedup_vs_double_float": round(ms / max(mst, 1e-9), 2),
                 "digit_bytes_per_product": digit_bytes,
                 "true_relres_max": _true_relres(AA, B3, X3)}
-            tensor_phase = mvt   # matvec phase: tensor-core products and the FP64 true residuals
+            tensor_phase = mvt   # matvec phase: the iteration's products and the true residuals, all tensor-core
             # FP64 products on the same operator: rate over a few iterations
             _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, 1, 0)
             ms64, res64, mv64 = _cg_timed(ctx, AA, B3, X3, "classic", "fp64", 0.0, args.cg3_fp64_iters, 0)
@@ -416,11 +416,10 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                 "iterations": args.cg3_fp64_iters, "ms_per_iteration": round(ms64 / args.cg3_fp64_iters, 3),
                 "matvec_ms_mean": round(mv64_ms, 3),
                 "frac_of_fp64_fma_rate": round(n3 * n3 * 16 / (mv64_ms / 1e3) / (FP64_PEAK_GFLOPS * 1e9 / 2), 4)}
-            # the tensor-core product alone: the matvec phase less its FP64
-            # true residuals (the start and one per 50 iterations), each
-            # taken at the FP64 products' mean time
-            n_true = 1 + rest.iterations // 50
-            t_ms = (tensor_phase[0] - n_true * mv64_ms) / max(tensor_phase[1] - n_true, 1)
+            # the tensor-core product: every launch of the matvec phase (the
+            # true residuals' products also keep weight class 7, a few more
+            # MMAs on the same digit stream)
+            t_ms = tensor_phase[0] / max(tensor_phase[1], 1)
             c3[label]["tensor_products"].update({
                 "matvec_ms_mean": round(t_ms, 3),
                 "digit_gbs": round(digit_bytes / (t_ms / 1e3) / 1e9, 1),
@@ -430,7 +429,8 @@ def cg_legs(args, ctx, A2, b2, n2, world, pk, max_over_ranks, rank):
                       "residual 1e-10 (replacement every 50 iterations, FP64 true residuals); FP32-stored A is the "
                       "FP32 rounding of the FP64 matrix; products_tera_per_s = n^2 * 16 / matvec time; "
                       "tensor_products: the same solve with FP64-accurate tensor-core products (8 base-128 digits "
-                      "per entry, 28 digit pairs of weight class <= 6, exact per 512-entry pass), A's digits made once per solve")
+                      "per entry, 28 digit pairs of weight class <= 6, exact per 512-entry pass; its true residuals keep "
+                      "class 7 too), A's digits made once per solve")
         out["config3"] = c3
         del A64, A32, B3, X3
     return out

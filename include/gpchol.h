@@ -286,8 +286,10 @@ typedef struct gpch_cg_opts {
  * n 2^-42 max_j |A_ij| max |s|.  A must
  * be symmetric (its columns serve as rows).  Extra workspace: 16 np kp
  * bytes for A's digits (np = n rounded up to 128, kp = n rounded up to
- * 512) plus 4 np kp / 512 bytes of exponents.  True residuals keep FP64
- * products.  Errors as above, plus INVALID_ARG when np kp / 8 does not fit
+ * 512) plus 4 np kp / 512 bytes of exponents.  True residuals take the
+ * same tensor-core product with the 8 pairs of weight class 7 kept too, so
+ * the dropped pairs weigh at most about 2^-51 of the pass scales per term
+ * (FP64-level products).  Errors as above, plus INVALID_ARG when np kp / 8 does not fit
  * 31 bits (n above about 131000) and TIMEOUT when a bounded tensor-core
  * wait gave up. */
 gpch_status gpch_cg_solve_ex(gpch_ctx *ctx, int64_t n, const void *A, gpch_dtype dtype, int64_t lda,

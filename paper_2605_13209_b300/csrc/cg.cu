@@ -68,7 +68,9 @@
 //              pass, and the passes added in FP64.  The dropped classes
 //              (p + d >= 7) weigh at most 2^-44 of the pass's scales per
 //              term.  The digit copy takes 16 bytes per entry of A.  True
-//              residuals keep FP64 products.
+//              residuals take the same product with class 7 kept as well
+//              (the dropped classes then weigh at most 2^-51 of the scales
+//              per term, FP64-level).
 
 #include <cuda_bf16.h>
 
@@ -80,7 +82,9 @@ namespace {
 constexpr int THREADS = 256;
 constexpr int MAXRHS = 16;
 
-enum Product : int { PROD_FP64 = 0, PROD_DF = 1, PROD_OZ = 2 };
+// PROD_OZ_FULL (internal): PROD_OZ with weight class 7 kept as well, for
+// the true residuals of the tensor-core solve
+enum Product : int { PROD_FP64 = 0, PROD_DF = 1, PROD_OZ = 2, PROD_OZ_FULL = 3 };
 enum Variant : int { VAR_CLASSIC = 0, VAR_SINGLE_REDUCTION = 1 };
 enum MvMode : int { MV_ALPHA = 0, MV_PLAIN = 1, MV_SR = 2 };
 
@@ -711,6 +715,13 @@ static_assert((size_t)OZM_BM * OZM_N * sizeof(double) <= OZM_STAGES * OZM_STAGE,
 // first TMEM column of digit p's product: 16 sum_{p' < p} (7 - p')
 __host__ __device__ constexpr int ozm_base(int p) { return OZM_N * (7 * p - p * (p - 1) / 2); }
 
+// With FULL, the eight pairs of weight class 7 (p + d = 7) are summed too,
+// all into one more 16-column TMEM block (exact in FP32: at most 8 pair
+// sums of 2^21), and the pass's total gains one more base-128 place: the
+// dropped classes then weigh at most 2^-51 of the scales' product per term,
+// FP64-level products for the true residuals.
+constexpr uint32_t OZM_C7 = 448;   // TMEM column of the class-7 block
+template <bool FULL>
 __global__ void __launch_bounds__(THREADS, 1)
     oz_matvec_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_s, int64_t n,
                      int nrhs, const double *S, int64_t lds, double *T, int64_t ldt, CGState st, int mode, SRArgs sr,
@@ -802,6 +813,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                             gpch::tc::mma_bf16(tmem + (uint32_t)ozm_base(p), a + 2 * k, b + 2 * k, idesc,
                                                (q > 0 || k > 0) ? 1u : 0u);
                         }
+                        if constexpr (FULL) {
+                            // class 7: digit p of A against digit 7 - p of the
+                            // vectors (their 16 rows start (7 - p) 1024 bytes
+                            // into the stacked box: +64 in the descriptor)
+                            const uint32_t idesc7 = gpch::tc::idesc_bf16_f32(OZM_BM, OZM_N);
+#pragma unroll
+                            for (int p = 0; p < 8; ++p) {
+                                const uint64_t a = gpch::tc::sdesc_sw128(sa + (p / 2) * OZM_ABOX) + 4 * (p & 1);
+                                gpch::tc::mma_bf16(tmem + OZM_C7, a + 2 * k, b + (uint64_t)(64 * (7 - p)) + 2 * k,
+                                                   idesc7, (q > 0 || k > 0 || p > 0) ? 1u : 0u);
+                            }
+                        }
                     }
                     gpch::tc::mma_commit(&empty[s]);
                 }
@@ -858,6 +881,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int j = 0; j < OZM_N; ++j) cs[p + d][j] += __uint_as_float(v[u][j]);
                 }
             }
+            float c7[OZM_N];
+            if constexpr (FULL) {
+                uint32_t v7[16];
+                gpch::tc::tmem_ld16_nowait(tl + OZM_C7, v7);
+                gpch::tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < OZM_N; ++j) c7[j] = __uint_as_float(v7[j]);
+            }
             // the accumulators are read: the MMAs of pass t + 1 may start
             gpch::tc::tc_fence_before();
             __syncwarp();
@@ -872,7 +903,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int D = 0; D < 3; ++D) H = H * 128 + __float2int_rn(cs[D][j]);
 #pragma unroll
                 for (int D = 3; D < 7; ++D) L = L * 128 + __float2int_rn(cs[D][j]);
-                acc64[j] += gpch::oz_round_scaled(H, L, er + __ldg(&oz.ES[t * OZM_N + j]) - 52);
+                int sc = er + __ldg(&oz.ES[t * OZM_N + j]) - 52;
+                if constexpr (FULL) {
+                    // one more place: T 128 + S_7 = (128 H) 2^28 + (128 L + S_7)
+                    H *= 128;
+                    L = L * 128 + __float2int_rn(c7[j]);
+                    sc -= 7;
+                }
+                acc64[j] += gpch::oz_round_scaled(H, L, sc);
             }
         }
     }
@@ -1502,7 +1540,7 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
 {
     if (ncols < 0) ncols = n;
     const int vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((lda * (int64_t)sizeof(TA)) & 15) == 0) ? 1 : 0;
-    if (prod == PROD_OZ) {
+    if (prod == PROD_OZ || prod == PROD_OZ_FULL) {
         // the vectors' digits, then the tensor-core product (A's digits
         // were made once per solve by oz_prepare)
         const OzArgs &oz = df.oz;
@@ -1515,14 +1553,19 @@ gpch_status launch_matvec(gpch_ctx *ctx, int64_t n, int nrhs, const TA *A, int64
         GPCH_CHECK(gpch::oz_map(ctx, &ms, oz.DS, (oz.kpt / OZM_KSTAGE) * 8 * OZM_N, 32, 8 * OZM_N, true));
         static gpch::DeviceOnce attr_once;
         GPCH_CHECK(gpch::once_per_device(ctx, attr_once, [&]() -> gpch_status {
-            GPCH_CUDA(ctx, cudaFuncSetAttribute(oz_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(oz_matvec_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)OZM_SMEM));
+            GPCH_CUDA(ctx, cudaFuncSetAttribute(oz_matvec_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)OZM_SMEM));
             return GPCH_OK;
         }));
         gpch::PhaseScope ph(ctx, GPCH_PHASE_CG_MATVEC, s,
                             (double)n * oz.kpt * 16.0 + (double)(n + ncols) * nrhs * sizeof(double));
-        oz_matvec_kernel<<<(unsigned)((n + OZM_BM - 1) / OZM_BM), THREADS, OZM_SMEM, s>>>(ma, ms, n, nrhs, S, lds, T,
-                                                                                       ldt, st, mode, sr, oz);
+        const unsigned grid = (unsigned)((n + OZM_BM - 1) / OZM_BM);
+        if (prod == PROD_OZ_FULL)
+            oz_matvec_kernel<true><<<grid, THREADS, OZM_SMEM, s>>>(ma, ms, n, nrhs, S, lds, T, ldt, st, mode, sr, oz);
+        else
+            oz_matvec_kernel<false><<<grid, THREADS, OZM_SMEM, s>>>(ma, ms, n, nrhs, S, lds, T, ldt, st, mode, sr, oz);
         GPCH_LAUNCH_CHECK(ctx);
         return GPCH_OK;
     }
@@ -1759,15 +1802,18 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
     if (prod == PROD_DF) GPCH_CHECK(df_prepare<TA>(ctx, n, nrhs, A, lda, B, ldb, b, s));
     if (prod == PROD_OZ) GPCH_CHECK(oz_prepare<TA>(ctx, n, A, lda, b, s));
     const double rtol2 = rtol * rtol;
+    // the true residuals b - A x: FP64 products, or with the tensor-core
+    // products their form that keeps weight class 7 too (FP64-level)
+    const int tprod = prod == PROD_OZ ? PROD_OZ_FULL : PROD_FP64;
 
     if (variant == VAR_CLASSIC) {
         // line 1: s = r = b - A x
-        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s, tprod, b.df));
         cg_init_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.S, b.T, B, ldb, ldv, st);
         GPCH_LAUNCH_CHECK(ctx);
     } else {
         // r = b - A x; w = A r with gamma_0, delta_0, alpha_0; p = s = 0
-        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+        GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s, tprod, b.df));
         cg_resid_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.T, B, ldb, ldv, st, 1);
         GPCH_LAUNCH_CHECK(ctx);
         GPCH_CUDA(ctx, cudaMemsetAsync(b.P, 0, (size_t)n * nrhs * sizeof(double), s));
@@ -1790,7 +1836,8 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
                 if (replace) {
                     cg_xupdate_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, b.S, ldv, st);
                     GPCH_LAUNCH_CHECK(ctx);
-                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s, tprod,
+                                                 b.df));
                     cg_update_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, X, ldx, b.R, b.S, b.T, B, ldb, ldv, st,
                                                                   rtol2, maxit, 1);
                 } else {
@@ -1808,7 +1855,8 @@ gpch_status cg_run(gpch_ctx *ctx, int64_t n, const TA *A, int64_t lda, const dou
                     GPCH_LAUNCH_CHECK(ctx);
                 }
                 if (replace) {
-                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s));
+                    GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, X, ldx, b.T, ldv, st, MV_PLAIN, s, tprod,
+                                                 b.df));
                     cg_resid_kernel<<<vec_ctas, THREADS, 0, s>>>(n, nrhs, b.R, b.T, B, ldb, ldv, st, 0);
                     GPCH_LAUNCH_CHECK(ctx);
                     GPCH_CHECK(launch_matvec<TA>(ctx, n, nrhs, A, lda, b.P, ldv, b.S, ldv, st, MV_PLAIN, s, prod,
