@@ -651,7 +651,8 @@ gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double *A, int64_
  * A: device FP64, n x n column-major (lda); entries above the diagonal may
  * be read but never change the result.  X: device n x nrhs (ldx).  Y:
  * device n x nrhs (ldy), overwritten; it must not overlap X.  Work space
- * from the context arena: about (n / 512 + n / 256) n 16 bytes.  Enqueued
+ * from the context arena: about n^2 / 16 bytes per column of a pair (the
+ * partial sums of 256 x 256 units).  Enqueued
  * on `stream` (no synchronization); the context's arena is in use until it
  * completes.  Errors: INVALID_ARG (n >= 2^24, ld < n, null pointers),
  * OUT_OF_MEMORY, CUDA_ERROR. */
