@@ -49,6 +49,7 @@ gpch_status aux_stream(gpch_ctx *ctx)
     GPCH_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     GPCH_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, least));
     GPCH_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->crit, cudaStreamNonBlocking, greatest));
+    GPCH_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->pre, cudaStreamNonBlocking, least));
     GPCH_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking,
                                                 greatest < least ? greatest + 1 : greatest));
     for (auto &e : ctx->aux_ev) GPCH_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -117,6 +118,8 @@ gpch_status gpch_destroy(gpch_ctx *ctx)
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->crit) cudaStreamDestroy(ctx->crit);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->pre) cudaStreamDestroy(ctx->pre);
+    for (auto e : ctx->pre_ev) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;

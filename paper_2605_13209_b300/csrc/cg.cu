@@ -2376,10 +2376,12 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     int attempts = 0;
     int64_t info = 1;
     for (; attempts < 9; ++attempts) {
-        GPCH_CHECK(gpch::mixed_init_enqueue(ctx, n, A, lda, W, ldw, shift, s, dev2 + 2, norm_ws));
+        // W = A + shift I and ||A||_inf, run by the factor block column by
+        // block column ahead of its use
+        const gpch::MixedInit mi{A, lda, shift, dev2 + 2, norm_ws};
         int64_t *d_info;
         int *d_err;
-        GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, W, ldw, (int)prec, rest, &d_info, &d_err, s));
+        GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, W, ldw, (int)prec, rest, &d_info, &d_err, s, &mi));
         int64_t *h = static_cast<int64_t *>(ctx->pinned);
         GPCH_CUDA(ctx, cudaMemcpyAsync(h, d_info, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         GPCH_CUDA(ctx, cudaMemcpyAsync(h + 1, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -894,7 +894,18 @@ size_t mixed_ws_bytes(int64_t n, int tile);
 gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, float *W, int64_t ldw,
                                double shift, cudaStream_t st, double *anorm = nullptr, float *norm_ws = nullptr);
 size_t anorm_ws_floats(int64_t n);   // workspace of the ||A||_inf pieces (floats)
+// The input pass W = A + shift I (with ||A||_inf into *anorm through
+// norm_ws) run by the factor itself, block column by block column on a
+// stream of its own, each part of the factor waiting only for the block
+// columns it touches.
+struct MixedInit {
+    const double *A;
+    int64_t lda;
+    double shift;
+    double *anorm;
+    float *norm_ws;
+};
 gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
-                                 int64_t **info_out, int **err_out, cudaStream_t st);
+                                 int64_t **info_out, int **err_out, cudaStream_t st, const MixedInit *init = nullptr);
 
 }  // namespace gpch

@@ -34,6 +34,8 @@ struct gpch_ctx {
     cudaStream_t aux = nullptr;          // low-priority stream for bulk overlapped work
     cudaStream_t crit = nullptr;         // high-priority stream for the critical chain
     cudaStream_t side = nullptr;         // middle priority: work the critical chain needs one step later
+    cudaStream_t pre = nullptr;          // low priority: the factor's input pass, block column by block column
+    std::vector<cudaEvent_t> pre_ev;     // one per block column of that pass (no timing)
     cudaEvent_t aux_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 

@@ -624,6 +624,31 @@ __global__ void __launch_bounds__(256) factor_scale_kernel(int64_t n, const floa
     }
 }
 
+// The same scale words from A's diagonal: W_ii = fl32(A_ii + shift), the
+// value the input pass writes, so that the scale need not wait for it.
+__global__ void __launch_bounds__(256) factor_scale_from_a_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
+                                                                  double shift, int *scale, int *pscale)
+{
+    __shared__ float red[8];
+    float mx = 0.0f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, (float)(A[i + i * lda] + shift));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+        mx = fmaxf(mx, red[0]);
+        const float r = sqrtf(mx);
+        scale[0] = (int)__float_as_uint(r);
+        scale[1] = f16_scale_exp(__float_as_uint(r));
+        if (pscale) {
+            pscale[0] = (int)__float_as_uint(mx);
+            pscale[1] = f16_scale_exp(__float_as_uint(mx));
+        }
+    }
+}
+
 // FP32 inverses of the 64 x 64 diagonal blocks of the factored FP64 tile D
 // (nj x nj, ld ldd), for the FP32 panel solve: block b of the grid inverts
 // rows/columns [64b, 64b + 64), unit-padded, by right-looking substitution
@@ -861,10 +886,11 @@ constexpr int NW_THREADS = 256;
 constexpr int NW_PER = NW_ROWS / NW_THREADS;   // rows of a thread
 __global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, const double *__restrict__ A,
                                                                  int64_t lda, float *W, int64_t ldw, double shift,
-                                                                 float *part, float *colpart)
+                                                                 float *part, float *colpart, int64_t strip0)
 {
     __shared__ float red[NW_THREADS / 32][NW_COLS];
-    const int64_t c0 = (int64_t)blockIdx.x * NW_COLS, r0 = (int64_t)blockIdx.y * NW_ROWS;
+    const int64_t strip = strip0 + (int64_t)blockIdx.x;   // strips strip0.. (a block column's at a time)
+    const int64_t c0 = strip * NW_COLS, r0 = (int64_t)blockIdx.y * NW_ROWS;
     if (r0 + NW_ROWS <= c0) return;   // the chunk lies above the strip
     const int cw = (int)((n - c0 < NW_COLS) ? n - c0 : NW_COLS);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -899,7 +925,7 @@ __global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, cons
         for (int off = 16; off > 0; off >>= 1) cacc += __shfl_xor_sync(0xffffffffu, cacc, off);
         if (lane == 0) red[warp][c] = cacc;
     }
-    float *prow = part + (int64_t)blockIdx.x * n;
+    float *prow = part + strip * n;
 #pragma unroll
     for (int k = 0; k < NW_PER; ++k) {
         const int64_t row = r0 + threadIdx.x + NW_THREADS * k;
@@ -1463,7 +1489,7 @@ size_t mixed_ws_bytes(int64_t n, int tile)
 // stream) instead of once per panel, and the critical stream waits only for
 // the block it needs next.
 gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
-                                 int64_t **info_out, int **err_out, cudaStream_t st)
+                                 int64_t **info_out, int **err_out, cudaStream_t st, const MixedInit *init)
 {
     Carver cv(wsbase);
     MixedWs w = carve_mixed(cv, n, tile);
@@ -1484,7 +1510,10 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     all.ld = kpos(split, kpa);
     if (prec == GPCH_PREC_SPLIT_F16) {
         // one scale for every panel, from |L_ij| <= sqrt(max_i W_ii)
-        factor_scale_kernel<<<1, 256, 0, caller>>>(n, W, ldw, w.scale, w.pscale);
+        if (init)
+            factor_scale_from_a_kernel<<<1, 256, 0, caller>>>(n, init->A, init->lda, init->shift, w.scale, w.pscale);
+        else
+            factor_scale_kernel<<<1, 256, 0, caller>>>(n, W, ldw, w.scale, w.pscale);
         GPCH_LAUNCH_CHECK(ctx);
         all.fixed_scale = true;
     }
@@ -1520,6 +1549,40 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
     GPCH_CUDA(ctx, cudaStreamWaitEvent(st, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_start, 0));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(sc, ev_start, 0));
+    // the input pass, block column by block column on its own stream:
+    // block column J is in W once pre_ev[J] has fired (the critical stream
+    // waits for J + 1 at step J, the second stream for J + 3)
+    const int64_t nbc = (n + tile - 1) / tile;
+    if (init) {
+        if ((int64_t)ctx->pre_ev.size() < nbc + 1) {
+            ctx->pre_ev.reserve((size_t)(nbc + 1));
+            while ((int64_t)ctx->pre_ev.size() < nbc + 1) {
+                cudaEvent_t e = nullptr;
+                GPCH_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                ctx->pre_ev.push_back(e);
+            }
+        }
+        cudaStream_t sp = ctx->pre;
+        GPCH_CUDA(ctx, cudaStreamWaitEvent(sp, ev_start, 0));
+        GPCH_CUDA(ctx, cudaMemsetAsync(init->anorm, 0, sizeof(double), sp));
+        const int64_t nchunk = (n + NW_ROWS - 1) / NW_ROWS, nstrip_all = (n + NW_COLS - 1) / NW_COLS;
+        float *part = init->norm_ws, *colpart = init->norm_ws + nstrip_all * n;
+        for (int64_t J = 0; J < nbc; ++J) {
+            const int64_t j0 = J * tile, j1 = (n < j0 + tile) ? n : j0 + tile;
+            const int64_t s0 = j0 / NW_COLS, s1 = (j1 + NW_COLS - 1) / NW_COLS;
+            init_w_norm_kernel<<<dim3((unsigned)(s1 - s0), (unsigned)nchunk), NW_THREADS, 0, sp>>>(
+                n, init->A, init->lda, W, ldw, init->shift, part, colpart, s0);
+            GPCH_LAUNCH_CHECK(ctx);
+            GPCH_CUDA(ctx, cudaEventRecord(ctx->pre_ev[J], sp));
+        }
+        norm_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, sp>>>(n, part, colpart, init->anorm);
+        GPCH_LAUNCH_CHECK(ctx);
+        GPCH_CUDA(ctx, cudaEventRecord(ctx->pre_ev[nbc], sp));
+    }
+    auto wait_cols = [&](cudaStream_t s, int64_t J) -> gpch_status {
+        if (init) GPCH_CUDA(ctx, cudaStreamWaitEvent(s, ctx->pre_ev[J < nbc ? J : nbc - 1], 0));
+        return GPCH_OK;
+    };
     const int64_t blk_cols = (tile + BN - 1) / BN;   // tile columns of one block column
     // K columns (whole panels) per launch of the long pass: longer launches
     // read and write C fewer times and leave fewer partial waves (at
@@ -1535,6 +1598,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         const int64_t j0 = J * tile;
         const int64_t nj = (n - j0 < tile) ? n - j0 : tile;
         float *Wjj = W + j0 + j0 * ldw;
+        GPCH_CHECK(wait_cols(st, J + 1));
         {
             // step 1 in FP32: one left-looking launch per 32-column block
             PhaseScope ph1(ctx, GPCH_PHASE_DIAG, st, (double)nj * nj * nj / 3.0);
@@ -1679,6 +1743,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
         // block column J+3 <- panels 0..J in one long-K pass
         if (m > tile) {
             GPCH_CUDA(ctx, cudaStreamWaitEvent(sb, ev_conv, 0));
+            GPCH_CHECK(wait_cols(sb, J + 3));
             const int64_t r2 = j0 + nj + tile, m2 = n - r2;
             LowprecBuffers qb = all;
             qb.hi = all.hi + r2 * all.ld;
@@ -1706,7 +1771,9 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
             }
         }
     }
-    // the second stream's last pass (and the side stream) before the caller
+    // the second stream's last pass (and the side stream, and the input
+    // pass's norm) before the caller
+    if (init) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ctx->pre_ev[nbc], 0));
     GPCH_CUDA(ctx, cudaEventRecord(ev_ready[0], sb));
     GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_ready[0], 0));
     if (side_pending) GPCH_CUDA(ctx, cudaStreamWaitEvent(caller, ev_side, 0));
@@ -1733,7 +1800,7 @@ gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_
         const int64_t nstrip = (n + NW_COLS - 1) / NW_COLS, nchunk = (n + NW_ROWS - 1) / NW_ROWS;
         float *part = norm_ws, *colpart = norm_ws + nstrip * n;
         init_w_norm_kernel<<<dim3((unsigned)nstrip, (unsigned)nchunk), NW_THREADS, 0, st>>>(n, A, lda, W, ldw, shift,
-                                                                                           part, colpart);
+                                                                                           part, colpart, 0);
         GPCH_LAUNCH_CHECK(ctx);
         norm_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, part, colpart, anorm);
         GPCH_LAUNCH_CHECK(ctx);
