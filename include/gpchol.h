@@ -624,7 +624,9 @@ typedef struct gpch_refine_stats {
  * (with more, the products read all of it).  B: device n x nrhs
  * (ldb).  X: device n x nrhs (ldx), overwritten.  Workspace (context
  * arena): about 8 n^2 bytes, the FP32 factor and the 16-bit copies of its
- * panels (plus gpch_symv_lower's partial sums).
+ * panels (plus gpch_symv_lower's partial sums); with one or two right-hand
+ * sides 4 n^2 bytes more for the products' packed copy of A's lower
+ * triangle.
  * tile: the factor's block size, a multiple of 64 in [64, 1024], or 0 for
  * the autotuned tile of n's size bucket (gpch_autotune; defaults 256 for
  * n <= 4096, else 512, until the device is tuned).

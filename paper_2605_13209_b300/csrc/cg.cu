@@ -74,6 +74,8 @@
 
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "dense_fp64.cuh"
 #include "ozaki.cuh"
 
@@ -199,31 +201,7 @@ __device__ __forceinline__ void df_add2(float &hi, float &lo, float h2, float l2
     lo = lo + l2 + err;
 }
 
-// Head and tail of 2^-ea a for an FP64 a, from its bit pattern with integer
-// operations only (a float conversion would run on the FP64 pipe).  The
-// head is the top 24 significand bits (truncated), the tail the next 23,
-// so |2^-ea a - head - tail| < 2^-46 |2^-ea a|.  ebias = 896 + ea.  Scaled
-// values below 2^-126 give head 0 (and below 2^-103 tail 0); values at or
-// above 2^128 give an infinite head, so the product is not finite.
-__device__ __forceinline__ void df_split_a(double a, unsigned ebias, float &head, float &tail)
-{
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
-    const unsigned h = (unsigned)(bits >> 32), l = (unsigned)bits;
-    const unsigned t = h & 0x7fffffffu;      // exponent field E at bits 20..30
-    const unsigned sgn = h & 0x80000000u;
-    // (E << 23 | top 23 fraction bits) modulo 2^32, rebiased to E - ebias
-    const unsigned hb = __funnelshift_l(l, t, 3) - (ebias << 23);
-    const bool small = t < ((ebias + 1u) << 20);
-    const bool big = t >= ((ebias + 255u) << 20);
-    const unsigned hbits = small ? 0u : (big ? 0x7f800000u : hb);
-    head = __uint_as_float(hbits | sgn);
-    // tail: fraction bits 6..28 of the low word, weighted 2^(E - ebias - 150)
-    // as the difference of two floats with exponent field E - ebias - 23
-    const unsigned mb = (hb & 0x7f800000u) - (23u << 23);
-    const unsigned fb = mb | ((l >> 6) & 0x007fffffu);
-    const bool tail_ok = t >= ((ebias + 24u) << 20) && !big;
-    tail = tail_ok ? __uint_as_float(fb | sgn) - __uint_as_float(mb | sgn) : 0.0f;
-}
+using gpch::df_split_a;
 
 // ------------------------------------------------------------- the matvec
 
@@ -1263,13 +1241,8 @@ inline size_t sy_smem(int nr)
 }
 // doubles (8-byte slots: double-float pairs) of the two partial arrays
 inline size_t sy_part_doubles(int64_t n, int nr) { return (size_t)(sy_chunks(n) + sy_strips(n)) * n * nr; }
-// float2 offset of strip J in the packed copy (strip J' has SY_SW columns
-// of n2 - J' SY_SW entries); sy_off(n, sy_strips(n)) is its size
-__host__ __device__ inline int64_t sy_off(int64_t n, int64_t J)
-{
-    const int64_t n2 = (n + 1) & ~int64_t(1);
-    return (int64_t)SY_SW * (J * n2 - (int64_t)(SY_SW / 2) * J * (J - 1));
-}
+static_assert(SY_SW == gpch::SYM_STRIP, "the packed copy's strips are the units' strips");
+using gpch::sy_off;
 
 __device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, bool ok)
 {
@@ -2073,7 +2046,8 @@ struct RefineResult {
 // anorm_dev: ||A||_inf on the device (from mixed_init_enqueue).
 gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, const float *L, int64_t ldl,
                       const double *B, int64_t ldb, double *X, int64_t ldx, int nrhs, double bwd_tol, int maxit,
-                      int R, char *wsbase, cudaStream_t s, RefineResult &res, const double *anorm_dev)
+                      int R, char *wsbase, cudaStream_t s, RefineResult &res, const double *anorm_dev,
+                      float2 *packed_pre = nullptr)
 {
     const int64_t ldv = n;
     const unsigned vec_ctas = (unsigned)((n + THREADS - 1) / THREADS);
@@ -2103,8 +2077,9 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     // of A), else all of A
     const bool sym = nrhs <= 2;
     double *sym_part = sym ? cv.take<double>(sy_part_doubles(n, mv_nr(nrhs))) : nullptr;
-    float2 *sym_ap = sym ? cv.take<float2>((size_t)sy_off(n, sy_strips(n))) : nullptr;
-    bool sym_packed = false;   // the packed copy is made
+    // (a copy the input pass already wrote serves every product)
+    float2 *sym_ap = !sym ? nullptr : packed_pre ? packed_pre : cv.take<float2>((size_t)sy_off(n, sy_strips(n)));
+    bool sym_packed = packed_pre != nullptr;   // the packed copy is made
     CGBufs dfb{};
     dfb.df.SS = cv.take<float2>((size_t)n * mv_nr(nrhs));
     {
@@ -2227,7 +2202,7 @@ gpch_status pcg_group(gpch_ctx *ctx, int64_t n, const double *A, int64_t lda, co
     return GPCH_OK;
 }
 
-size_t pcg_ws_bytes(int64_t n, int nrhs)
+size_t pcg_ws_bytes(int64_t n, int nrhs, bool own_packed = true)
 {
     gpch::Carver dry(nullptr);
     for (int i = 0; i < 4; ++i) dry.take<double>((size_t)n * nrhs);
@@ -2238,7 +2213,7 @@ size_t pcg_ws_bytes(int64_t n, int nrhs)
     dry.take<double>(part_doubles(n, nrhs, PROD_DF));
     if (nrhs <= 2) {
         dry.take<double>(sy_part_doubles(n, mv_nr(nrhs)));
-        dry.take<float2>((size_t)sy_off(n, sy_strips(n)));
+        if (own_packed) dry.take<float2>((size_t)sy_off(n, sy_strips(n)));
     }
     dry.take<float2>((size_t)n * mv_nr(nrhs));
     dry.take<double>(2 * MAXRHS);
@@ -2346,13 +2321,19 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t ldw = (n + 31) / 32 * 32;
     const int g = nrhs < MAXRHS ? nrhs : MAXRHS;
+    // with one or two right-hand sides the input pass also writes the
+    // products' packed copy of A's lower triangle (next to W, outside the
+    // factor's workspace, which the products' partials reuse)
+    const bool pre_packed = nrhs <= 2;
+    const size_t packed_n = pre_packed ? (size_t)sy_off(n, sy_strips(n)) : 0;
     gpch::Carver dry(nullptr);
     dry.take<float>((size_t)ldw * n);
     dry.take<double>(3);
     dry.take<float>(gpch::anorm_ws_floats(n));
+    if (pre_packed) dry.take<float2>(packed_n);
     const size_t fixed = dry.off;
     const size_t mix = gpch::mixed_ws_bytes(n, tile);
-    size_t pcg = pcg_ws_bytes(n, g);
+    size_t pcg = pcg_ws_bytes(n, g, !pre_packed);
     if (nrhs > MAXRHS && nrhs % MAXRHS != 0) {
         // the last group is smaller and may take the lower-triangle product's partials
         const size_t last = pcg_ws_bytes(n, nrhs % MAXRHS);
@@ -2363,6 +2344,7 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
     float *W = cv.take<float>((size_t)ldw * n);
     double *dev2 = cv.take<double>(3);   // [0, 2): diag_max, [2]: ||A||_inf
     float *norm_ws = cv.take<float>(gpch::anorm_ws_floats(n));
+    float2 *packed = pre_packed ? cv.take<float2>(packed_n) : nullptr;
     char *rest = static_cast<char *>(ctx->ws) + ((cv.off + 255) & ~size_t(255));
 
     double dmax = 0.0;
@@ -2373,12 +2355,17 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
                         : (prec == GPCH_PREC_SPLIT_BF16) ? 1.0 / 65536.0
                                                          : 1.0 / 4194304.0;
     double shift = (prec == GPCH_PREC_BF16) ? 2.0 * ulow * dmax : 0.0;
+    // the packed copy's exponent offset, as df_scales_kernel derives it
+    // from the same largest diagonal entry
+    int pack_ea = dmax > 0.0 ? std::ilogb(dmax) : 0;
+    pack_ea = pack_ea < -800 ? -800 : (pack_ea > 800 ? 800 : pack_ea);
+    const unsigned pack_ebias = (unsigned)(896 + pack_ea);
     int attempts = 0;
     int64_t info = 1;
     for (; attempts < 9; ++attempts) {
         // W = A + shift I and ||A||_inf, run by the factor block column by
         // block column ahead of its use
-        const gpch::MixedInit mi{A, lda, shift, dev2 + 2, norm_ws};
+        const gpch::MixedInit mi{A, lda, shift, dev2 + 2, norm_ws, packed, pack_ebias};
         int64_t *d_info;
         int *d_err;
         GPCH_CHECK(gpch::mixed_factor_enqueue(ctx, n, tile, W, ldw, (int)prec, rest, &d_info, &d_err, s, &mi));
@@ -2407,7 +2394,7 @@ extern "C" gpch_status gpch_solve_refined(gpch_ctx *ctx, int64_t n, const double
         const int gg = (nrhs - r0 < MAXRHS) ? nrhs - r0 : MAXRHS;
         RefineResult rr;
         GPCH_CHECK(pcg_group(ctx, n, A, lda, W, ldw, B + r0 * ldb, ldb, X + r0 * ldx, ldx, gg, bwd_tol, maxit, 50,
-                             rest, s, rr, dev2 + 2));
+                             rest, s, rr, dev2 + 2, packed));
         if (rr.iterations > it_max) it_max = rr.iterations;
         for (int c = 0; c < gg; ++c) {
             if (rr.bwd[c] > bwd_max) bwd_max = rr.bwd[c];

@@ -887,6 +887,45 @@ gpch_status solve_apply(gpch_ctx *ctx, int64_t n, const double *L, int64_t ldl, 
 gpch_status solve_apply_f32(gpch_ctx *ctx, int64_t n, const float *L, int64_t ldl, double *B, int64_t ldb, int nrhs,
                             SolveWs &w, cudaStream_t st);
 
+// Head and tail of 2^-ea a for an FP64 a, from its bit pattern with integer
+// operations only (a float conversion would run on the FP64 pipe).  The
+// head is the top 24 significand bits (truncated), the tail the next 23,
+// so |2^-ea a - head - tail| < 2^-46 |2^-ea a|.  ebias = 896 + ea.  Scaled
+// values below 2^-126 give head 0 (and below 2^-103 tail 0); values at or
+// above 2^128 give an infinite head, so the product is not finite.
+__device__ __forceinline__ void df_split_a(double a, unsigned ebias, float &head, float &tail)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    const unsigned h = (unsigned)(bits >> 32), l = (unsigned)bits;
+    const unsigned t = h & 0x7fffffffu;      // exponent field E at bits 20..30
+    const unsigned sgn = h & 0x80000000u;
+    // (E << 23 | top 23 fraction bits) modulo 2^32, rebiased to E - ebias
+    const unsigned hb = __funnelshift_l(l, t, 3) - (ebias << 23);
+    const bool small = t < ((ebias + 1u) << 20);
+    const bool big = t >= ((ebias + 255u) << 20);
+    const unsigned hbits = small ? 0u : (big ? 0x7f800000u : hb);
+    head = __uint_as_float(hbits | sgn);
+    // tail: fraction bits 6..28 of the low word, weighted 2^(E - ebias - 150)
+    // as the difference of two floats with exponent field E - ebias - 23
+    const unsigned mb = (hb & 0x7f800000u) - (23u << 23);
+    const unsigned fb = mb | ((l >> 6) & 0x007fffffu);
+    const bool tail_ok = t >= ((ebias + 24u) << 20) && !big;
+    tail = tail_ok ? __uint_as_float(fb | sgn) - __uint_as_float(mb | sgn) : 0.0f;
+}
+
+// The packed copy of a symmetric A's lower triangle that the refinement's
+// products read (float2 (head, tail) of 2^-ea A_ij per stored entry, as
+// df_split_a cuts it): strip J holds columns SYM_STRIP J .. + SYM_STRIP - 1,
+// rows SYM_STRIP J .. n2 - 1 (n2 = n rounded up to even), column-major with
+// ld n2 - SYM_STRIP J, from float2 offset sy_off(n, J); sy_off(n, strips)
+// is its size.
+constexpr int SYM_STRIP = 256;
+__host__ __device__ inline int64_t sy_off(int64_t n, int64_t J)
+{
+    const int64_t n2 = (n + 1) & ~int64_t(1);
+    return (int64_t)SYM_STRIP * (J * n2 - (int64_t)(SYM_STRIP / 2) * J * (J - 1));
+}
+
 // Low-precision factor (mixed.cu): workspace size, W = A + shift I (and,
 // with anorm and norm_ws, ||A||_inf of the symmetric A into *anorm), and the
 // factorization of W in place (info / err device words returned).
@@ -904,6 +943,8 @@ struct MixedInit {
     double shift;
     double *anorm;
     float *norm_ws;
+    float2 *packed;      // optional: the refinement's packed copy, written in the same pass
+    unsigned ebias;      // its df_split_a exponent offset (896 + ea)
 };
 gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, int64_t ldw, int prec, void *wsbase,
                                  int64_t **info_out, int **err_out, cudaStream_t st, const MixedInit *init = nullptr);

@@ -879,14 +879,18 @@ __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__
 // CTAs whose chunk lies above the strip leave at once.  The magnitudes come
 // from the FP32 values written to W (one conversion per entry, which the
 // FP64 pipe performs); the norm only scales the refinement's stopping test
-// and reported backward error.
+// and reported backward error.  Strips from strip0 on (a block column's at a
+// time when the factor runs the pass).  With packed, each entry of the lower
+// triangle is also cut into the head and tail of 2^-ea A_ij (df_split_a,
+// ebias = 896 + ea) and stored in the refinement's packed copy.
 constexpr int NW_COLS = 64;
 constexpr int NW_ROWS = 4096;
 constexpr int NW_THREADS = 256;
 constexpr int NW_PER = NW_ROWS / NW_THREADS;   // rows of a thread
 __global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, const double *__restrict__ A,
                                                                  int64_t lda, float *W, int64_t ldw, double shift,
-                                                                 float *part, float *colpart, int64_t strip0)
+                                                                 float *part, float *colpart, int64_t strip0,
+                                                                 float2 *packed, unsigned ebias)
 {
     __shared__ float red[NW_THREADS / 32][NW_COLS];
     const int64_t strip = strip0 + (int64_t)blockIdx.x;   // strips strip0.. (a block column's at a time)
@@ -897,10 +901,14 @@ __global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, cons
     float racc[NW_PER];
 #pragma unroll
     for (int k = 0; k < NW_PER; ++k) racc[k] = 0.0f;
+    const int64_t n2 = (n + 1) & ~int64_t(1);
     for (int c = 0; c < cw; ++c) {
         const int64_t col = c0 + c;
         const double *a = A + col * lda;
         float *w = W + col * ldw;
+        // with packed: this column of the refinement's packed copy, by row
+        const int64_t pj = col / gpch::SYM_STRIP, ps = pj * gpch::SYM_STRIP;
+        float2 *pc = packed ? packed + gpch::sy_off(n, pj) + (col - ps) * (n2 - ps) - ps : nullptr;
         double v[NW_PER];
 #pragma unroll
         for (int k = 0; k < NW_PER; ++k) {
@@ -919,6 +927,11 @@ __global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, cons
             } else if (row == col) {
                 w[row] = (float)(v[k] + shift);
                 racc[k] += fabsf((float)v[k]);
+            }
+            if (pc && row >= col && row < n) {
+                float h, t;
+                gpch::df_split_a(v[k], ebias, h, t);
+                pc[row] = make_float2(h, t);
             }
         }
 #pragma unroll
@@ -1571,7 +1584,7 @@ gpch_status mixed_factor_enqueue(gpch_ctx *ctx, int64_t n, int tile, float *W, i
             const int64_t j0 = J * tile, j1 = (n < j0 + tile) ? n : j0 + tile;
             const int64_t s0 = j0 / NW_COLS, s1 = (j1 + NW_COLS - 1) / NW_COLS;
             init_w_norm_kernel<<<dim3((unsigned)(s1 - s0), (unsigned)nchunk), NW_THREADS, 0, sp>>>(
-                n, init->A, init->lda, W, ldw, init->shift, part, colpart, s0);
+                n, init->A, init->lda, W, ldw, init->shift, part, colpart, s0, init->packed, init->ebias);
             GPCH_LAUNCH_CHECK(ctx);
             GPCH_CUDA(ctx, cudaEventRecord(ctx->pre_ev[J], sp));
         }
@@ -1800,7 +1813,8 @@ gpch_status mixed_init_enqueue(gpch_ctx *ctx, int64_t n, const double *A, int64_
         const int64_t nstrip = (n + NW_COLS - 1) / NW_COLS, nchunk = (n + NW_ROWS - 1) / NW_ROWS;
         float *part = norm_ws, *colpart = norm_ws + nstrip * n;
         init_w_norm_kernel<<<dim3((unsigned)nstrip, (unsigned)nchunk), NW_THREADS, 0, st>>>(n, A, lda, W, ldw, shift,
-                                                                                           part, colpart, 0);
+                                                                                           part, colpart, 0, nullptr,
+                                                                                           0u);
         GPCH_LAUNCH_CHECK(ctx);
         norm_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, part, colpart, anorm);
         GPCH_LAUNCH_CHECK(ctx);

@@ -97,6 +97,15 @@ size_t request_bytes(const gpch_request &r, bool solo_mixed, int tile)
              // pieces of ||A||_inf: a row sum per 64-column strip, a column sum
              // per 4096-row chunk
              round_up(((n + 63) / 64 + (n + 4095) / 4096) * n * 4);
+    // with one or two right-hand sides: the products' packed copy of A's
+    // lower triangle and their partial sums
+    // (strips of 256 columns from their diagonal down, columns of n rounded
+    // up to even, 8 bytes per entry)
+    if (solo_mixed && r.nrhs <= 2) {
+        const size_t n2 = (n + 1) & ~size_t(1), strips = (n + 255) / 256;
+        b += round_up(256 * (strips * n2 - 128 * strips * (strips - 1)) * 8) +
+             round_up(2 * strips * n * 8 * (size_t)r.nrhs);
+    }
     return b;
 }
 
