@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(256) init_w_kernel(int64_t n, const double *__
 // triangle is also cut into the head and tail of 2^-ea A_ij (df_split_a,
 // ebias = 896 + ea) and stored in the refinement's packed copy.
 constexpr int NW_COLS = 64;
-constexpr int NW_ROWS = 4096;
+constexpr int NW_ROWS = 1024;   // short CTAs: the factor runs the pass beside its own kernels
 constexpr int NW_THREADS = 256;
 constexpr int NW_PER = NW_ROWS / NW_THREADS;   // rows of a thread
 __global__ void __launch_bounds__(NW_THREADS) init_w_norm_kernel(int64_t n, const double *__restrict__ A,

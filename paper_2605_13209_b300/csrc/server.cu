@@ -95,8 +95,8 @@ size_t request_bytes(const gpch_request &r, bool solo_mixed, int tile)
              // panel solve on tensor cores: L_jj^-T, its 16-bit copies, the panel's
              3 * round_up((size_t)tile * tile * 4) + 2 * round_up(n * (size_t)tile * 2) +
              // pieces of ||A||_inf: a row sum per 64-column strip, a column sum
-             // per 4096-row chunk
-             round_up(((n + 63) / 64 + (n + 4095) / 4096) * n * 4);
+             // per 1024-row chunk
+             round_up(((n + 63) / 64 + (n + 1023) / 1024) * n * 4);
     // with one or two right-hand sides: the products' packed copy of A's
     // lower triangle and their partial sums
     // (strips of 256 columns from their diagonal down, columns of n rounded
