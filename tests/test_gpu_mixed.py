@@ -145,3 +145,38 @@ def test_refined_solve_zero_rhs_and_shift(ctx):
     assert np.all(X[:, 0] == 0.0)
     assert oracle.backward_error(A, X[:, 1], B[:, 1]) <= 1e-12
     assert res.shift > 0.0 and res.factor_attempts >= 1
+
+
+@pytest.mark.parametrize("nrhs", [3, 17, 18])
+def test_refined_solve_many_rhs(ctx, nrhs):
+    """More than two right-hand sides: the products over all of A (groups of
+    up to 16), and with 17 and 18 a last group of one or two columns that
+    takes the lower-triangle products with a packed copy of its own."""
+    n = 700
+    s = inputs.gp_system(n, 8, 0.5, 1e-3, nrhs=nrhs, seed=60 + nrhs)
+    A = oracle.se_matrix(s.X, s.sf2, s.ell, s.sn2)
+    Xd = gpchol.colmajor(n, nrhs)
+    res = gpchol.solve_refined(dev(A), dev(s.B), Xd, prec="split_f16", tile=256, bwd_tol=1e-12, ctx=ctx)
+    X = host(Xd)
+    for r in range(nrhs):
+        assert oracle.backward_error(A, X[:, r], s.B[:, r]) <= 1e-12, r
+    assert res.backward_error_max <= 1e-12
+
+
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_refined_solve_reads_lower_triangle_only(ctx, nrhs):
+    """With one or two right-hand sides nothing of the refined solve reads
+    above A's diagonal (the factor, the norm and the products take the
+    lower triangle): NaN there leaves the result as accurate as before."""
+    n = 900
+    s = inputs.gp_system(n, 8, 0.5, 1e-3, nrhs=nrhs, seed=70 + nrhs)
+    A = oracle.se_matrix(s.X, s.sf2, s.ell, s.sn2)
+    Ad = dev(A)
+    Ad.copy_(Ad + torch.triu(torch.full_like(Ad, float("nan")), 1))
+    Xd = gpchol.colmajor(n, nrhs)
+    res = gpchol.solve_refined(Ad, dev(s.B), Xd, prec="split_f16", tile=256, bwd_tol=1e-12, ctx=ctx)
+    X = host(Xd)
+    assert np.all(np.isfinite(X))
+    for r in range(nrhs):
+        assert oracle.backward_error(A, X[:, r], s.B[:, r]) <= 1e-12, r
+    assert res.backward_error_max <= 1e-12
