@@ -45,11 +45,11 @@ FP64_PEAK_GFLOPS = 1250.0   # nominal B300 FP64 (DFMA): 148 SMs x 2 FMA/clk x 2 
 FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032    # FFMA: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 CPU_SAMPLE_N = 4096
 CPU_ALLCORES_N = 2048
-# DRAM bytes per algorithmic flop of syrk_tc_kernel (split-f16 update, a
-# 16-panel long pass, K = 8192, m = 6656 rows x 512 columns): 248.4 MB over
-# 1.611e11 flop in one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the n = 16384 update.
-SYRK_DRAM_BYTES_PER_FLOP = 1.542e-3
+# DRAM bytes per algorithmic flop of syrk_tc_kernel's trailing updates
+# (split-f16): 7.084 GB of dram__bytes_read.sum + dram__bytes_write.sum over
+# all 74 update launches of one n = 16384 refined solve (long passes, short
+# passes sharing their grids, next-tile updates) against their 3.818e12 flop.
+SYRK_DRAM_BYTES_PER_FLOP = 1.856e-3
 
 
 def ranks_max(v: float, dist=None, device: str = "cuda") -> float:
@@ -572,8 +572,8 @@ def main():
                 "avg_launch_ms": round(phase[dom][0] / max(phase[dom][1], 1), 4),
                 "traffic": (round(SYRK_DRAM_BYTES_PER_FLOP * work_per_launch)
                             if SYRK_DRAM_BYTES_PER_FLOP is not None and args.prec != "bf16" else None),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one syrk_tc_kernel launch "
-                                  "(split-f16 long pass, K = 8192, n = 16384), scaled by the launch's work"}
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per flop over all syrk_tc_kernel "
+                                  "update launches of one n = 16384 solve, times the average launch's work"}
     phases = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches_per_step": v[1] / args.steps,
                   "roofline": roofline_of(k, *v, n, 1, pk)} for k, v in phase.items()}
 
