@@ -1227,7 +1227,7 @@ void launch_mv_kernel(int64_t n, int64_t ncols, int nrhs, const TA *A, int64_t l
 // zeros before they are used (from A they may be read, never used).
 constexpr int SY_SW = THREADS;   // columns per strip: one finishing CTA per strip
 constexpr int SY_R = 256;        // rows per chunk
-constexpr int SY_CG = 4;         // columns a warp takes at a time
+constexpr int SY_CG = 8;         // columns a warp takes at a time
 constexpr int SY_ST = 3;         // segments in flight per warp
 enum SySrc : int { SY_FP64 = 0, SY_WRITE = 1, SY_PACKED = 2 };
 template <bool B> struct SyTag { static constexpr bool value = B; };
@@ -1256,7 +1256,7 @@ __device__ __forceinline__ void cp_async8_zfill(void *dst, const void *src, bool
 }
 
 template <int NR, int SRC>
-__global__ void __launch_bounds__(THREADS, 3) sym_mv_df_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
+__global__ void __launch_bounds__(THREADS, 2) sym_mv_df_kernel(int64_t n, const double *__restrict__ A, int64_t lda,
                                                                float2 *AP, DFArgs df, float2 *__restrict__ dotp,
                                                                float2 *__restrict__ axp, const int *done, int vec)
 {
